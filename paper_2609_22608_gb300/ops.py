@@ -1,0 +1,133 @@
+"""Python entry points with the C ABI's names (include/fn_api.h).
+
+Tensors are torch CUDA tensors (PyTorch provides device memory and streams);
+each call forwards pointers and the current stream to libfruitninja.so and
+returns the output tensors.  All arithmetic runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import FN_MODE_FIXED, FN_MODE_FULL, arm_struct, check, lib
+
+__all__ = ["time_edges", "rnea_dump", "knn_tree", "knn_workspace_bytes", "make_edges",
+           "FN_MODE_FULL", "FN_MODE_FIXED", "version"]
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _states(x, name):
+    if not (x.is_cuda and x.dtype == torch.float32 and x.dim() == 2 and x.shape[1] == 16
+            and x.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CUDA float32 [n][16] tensor")
+    return x
+
+
+def version() -> str:
+    return lib().fn_version().decode()
+
+
+def time_edges(arm, s0, s1, T_grid=None, S=32, mode=FN_MODE_FULL, T_fixed=None, T_cap=None,
+               out=None, stream=None, sample_count=None):
+    """fn_time_edges: returns dict(k_star i32, T_star f32, rho3 f32 [E,3], ok u8).
+    With `sample_count` (a CUDA int64 tensor of one element) the call goes
+    through fn_time_edges_counted and adds its torque evaluations to it."""
+    _states(s0, "s0"); _states(s1, "s1")
+    E = s0.shape[0]
+    A = arm_struct(arm)
+    if out is None:
+        dev = s0.device
+        out = dict(k_star=torch.empty(E, dtype=torch.int32, device=dev),
+                   T_star=torch.empty(E, dtype=torch.float32, device=dev),
+                   rho3=torch.empty(E, 3, dtype=torch.float32, device=dev),
+                   ok=torch.empty(E, dtype=torch.uint8, device=dev))
+    if T_grid is None:
+        grid = None
+        K = 0
+    else:
+        g = np.ascontiguousarray(np.asarray(T_grid, np.float32))
+        grid = g.ctypes.data_as(C.c_void_p)
+        K = int(g.size)
+    if sample_count is None:
+        st = lib().fn_time_edges(C.byref(A), _ptr(s0), _ptr(s1), E, grid, K, int(S), int(mode),
+                                 _ptr(T_fixed), _ptr(T_cap), _ptr(out["k_star"]),
+                                 _ptr(out["T_star"]), _ptr(out["rho3"]), _ptr(out["ok"]),
+                                 _stream(stream))
+    else:
+        st = lib().fn_time_edges_counted(C.byref(A), _ptr(s0), _ptr(s1), E, grid, K, int(S),
+                                         int(mode), _ptr(T_fixed), _ptr(T_cap),
+                                         _ptr(out["k_star"]), _ptr(out["T_star"]),
+                                         _ptr(out["rho3"]), _ptr(out["ok"]), _ptr(sample_count),
+                                         _stream(stream))
+    check(st, "fn_time_edges")
+    return out
+
+
+def make_edges(tree, t_node, cand, n_goal, nn_idx, T_req, t_best, out=None, stream=None):
+    """fn_make_edges: (s0, s1, T_param, parent) for B (k_nn+1) edges."""
+    B = cand.shape[0]
+    k_nn = 0 if nn_idx is None else nn_idx.shape[1]
+    E = B * (k_nn + 1)
+    if out is None:
+        d = cand.device
+        out = (torch.empty(E, 16, device=d), torch.empty(E, 16, device=d),
+               torch.empty(E, device=d), torch.empty(E, dtype=torch.int32, device=d))
+    st = lib().fn_make_edges(_ptr(tree), _ptr(t_node), _ptr(cand), B, int(n_goal), _ptr(nn_idx),
+                             k_nn, _ptr(T_req), float(t_best), _ptr(out[0]), _ptr(out[1]),
+                             _ptr(out[2]), _ptr(out[3]), _stream(stream))
+    check(st, "fn_make_edges")
+    return out
+
+
+def rnea_dump(arm, s0, s1, T, S, out=None, stream=None):
+    """fn_rnea_dump: torques [E][S][7] along each edge at duration T[e]."""
+    _states(s0, "s0"); _states(s1, "s1")
+    E = s0.shape[0]
+    if out is None:
+        out = torch.empty(E, S, 7, dtype=torch.float32, device=s0.device)
+    st = lib().fn_rnea_dump(C.byref(arm_struct(arm)), _ptr(s0), _ptr(s1), _ptr(T), E, int(S),
+                            _ptr(out), _stream(stream))
+    check(st, "fn_rnea_dump")
+    return out
+
+
+def knn_workspace_bytes(B, N, k) -> int:
+    return int(lib().fn_knn_workspace_bytes(int(B), int(N), int(k)))
+
+
+def knn_tree(tree, queries, k, w_vel, first=1, N=None, workspace=None, out=None, stream=None):
+    """fn_knn_tree: (idx i32 [B][k], d2 f32 [B][k]).  `workspace` may be a
+    uint8 CUDA tensor of knn_workspace_bytes(B, N, k) bytes; by default one is
+    allocated with torch for the call."""
+    _states(queries, "queries")
+    B = queries.shape[0]
+    if N is None:
+        N = tree.shape[0]
+    if out is None:
+        out = (torch.empty(B, k, dtype=torch.int32, device=queries.device),
+               torch.empty(B, k, dtype=torch.float32, device=queries.device))
+    need = knn_workspace_bytes(B, N, k)
+    if workspace is None and need > 0:
+        workspace = torch.empty(need + 256, dtype=torch.uint8, device=queries.device)
+    ws_ptr, ws_bytes = None, 0
+    if workspace is not None:
+        base = workspace.data_ptr()
+        aligned = (base + 255) & ~255
+        ws_ptr = C.c_void_p(aligned)
+        ws_bytes = workspace.numel() - (aligned - base)
+    st = lib().fn_knn_tree(_ptr(tree), int(N), int(first), _ptr(queries), B, int(k),
+                           float(w_vel), _ptr(out[0]), _ptr(out[1]), ws_ptr, ws_bytes,
+                           _stream(stream))
+    check(st, "fn_knn_tree")
+    return out
