@@ -30,7 +30,7 @@ METRIC = "verified min-time cubic edges/sec (FP32, oracle-matched) and p99 plann
 UNIT = "edges/s"
 FLOP_PER_SAMPLE = 1379  # algorithmic FP32 FLOP of one torque evaluation (FMA = 2), see the design doc
 N_TREE, B_CAND, K_PAR, K_GRID, S_COLL = 4096, 2048, 8, 128, 64
-WORKLOAD = "one planning iteration: tree 4096, batch 2048 (1024 free + 1024 goal), k=8, K=128, S=64"
+WORKLOAD = "one planning iteration: tree 4096, batch 2048 (1024 goal-chart + 1024 uniform), k=8, K=128, S=64"
 
 
 def parse():
@@ -106,52 +106,79 @@ class ClockSampler:
 # workload
 # ----------------------------------------------------------------------------
 def make_workload(seed: int):
+    """Seeded synthetic instance of one planning iteration: arm, toss, root,
+    a synthetic tree (random states, parent uniform among earlier nodes,
+    t = t_parent + U(0.05, 0.3))."""
     from paper_2609_22608_gb300 import synth
     arm = synth.make_arm(0)
-    tree, parent, t_node = synth.random_tree(arm, N_TREE, seed)
-    free = synth.uniform_candidates(arm, B_CAND // 2, seed)
-    goal = synth.uniform_candidates(arm, B_CAND // 2, seed + 1000)
-    rng = np.random.default_rng([0xBE, seed])
-    t_req = rng.uniform(0.2, 0.9, B_CAND // 2).astype(np.float32)
-    return dict(arm=arm, tree=tree, t_node=t_node, free=free, goal=goal, t_req=t_req,
-                grid=synth.duration_grid(K_GRID), t_best=np.float32(0.9))
+    toss = synth.random_toss(arm, seed)
+    root = synth.random_states(arm, 1, 7000 + seed)[0]
+    pr = synth.make_problem(toss, root=root)
+    tree, parent, t_node = synth.random_tree(arm, N_TREE, seed, root=root)
+    return dict(arm=arm, pr=pr, root=root, tree=tree, parent=parent, t_node=t_node,
+                grid=synth.duration_grid(K_GRID), seed=seed)
 
 
-def oracle_step(orc, w, n_free, n_goal):
-    """The same edge batch on the FP64 oracle (bounded sample): parents by
-    brute-force kNN (root + k-1 nearest), free edges by the capped full scan,
-    goal edges by the fixed-duration check."""
-    cand = np.concatenate([w["free"][:n_free], w["goal"][:n_goal]])
-    idx, _ = orc.knn(w["tree"], cand, K_PAR - 1, 0.1)
-    par = np.concatenate([np.zeros((cand.shape[0], 1), np.int64), idx], axis=1)
-    s0 = w["tree"][par.reshape(-1)]
-    s1 = np.repeat(cand, K_PAR, axis=0)
-    tp = w["t_node"][par.reshape(-1)]
-    nf = n_free * K_PAR
-    cap = (np.float32(w["t_best"]) - tp[:nf]).astype(np.float32)
-    rf = orc.time_edges(w["arm"], s0[:nf], s1[:nf], w["grid"], S_COLL, T_cap=cap)
-    Tg = (np.repeat(w["t_req"][:n_goal], K_PAR) - tp[nf:]).astype(np.float32)
-    rg = orc.time_edges(w["arm"], s0[nf:], s1[nf:], w["grid"], S_COLL, mode=1, T_fixed=Tg)
-    return rf, rg, s0, s1, cap, Tg
+def oracle_round(orc, w, n_goal_draw, n_free):
+    """One round of Algorithm 1 on the oracle over a bounded candidate sample
+    drawn by the oracle's own samplers (same Philox streams as the device
+    sampler): returns (edges timed, tree, incumbent, details, case)."""
+    import oracle.plan as OP
+    pr = w["pr"]
+    st, Tq, vr, valid = orc.sample_goals(w["arm"], pr, 1000 + w["seed"], 0, 0, 0, n_goal_draw)
+    gi = np.nonzero(valid)[0]
+    free = orc.sample_uniform(w["arm"], 1000 + w["seed"], 0, 0, B_CAND // 2, n_free, 0.5)
+    cand = np.concatenate([st[gi], free]).astype(np.float32)
+    case = dict(cand=cand, n_goal=len(gi), T_req=Tq[gi].astype(np.float32),
+                v_rel=vr[gi].astype(np.float32))
+    tree = OP.Tree(w["tree"], w["t_node"], w["parent"])
+    inc = dict(id=-1, J=-np.inf, t_best=float(np.float32(pr["t_fall"])))
+    out = OP.plan_round(w["arm"], pr, tree, cand, len(gi), case["T_req"], case["v_rel"], inc,
+                        K_PAR, w["grid"], S_COLL)
+    return cand.shape[0] * K_PAR, out, case
 
 
 def cpu_baseline(w, budget_s=15.0):
     import oracle as orc
     cores = os.cpu_count() or 1
     orc.set_threads(cores)
-    n = 16
     t0 = time.perf_counter()
-    oracle_step(orc, w, n, n)
+    e, _, _ = oracle_round(orc, w, 64, 16)
     dt = time.perf_counter() - t0
-    # grow the sample to ~budget_s of CPU work
-    n2 = int(min(B_CAND // 2, max(n, n * budget_s / max(dt, 1e-3) * 0.5)))
+    scale = max(1.0, budget_s / max(dt, 1e-3))
+    nf = int(min(B_CAND // 2, 16 * scale * 0.7))
+    ng = int(min(B_CAND // 2, 64 * scale * 0.7))
     t0 = time.perf_counter()
-    oracle_step(orc, w, n2, n2)
+    e, out, case = oracle_round(orc, w, ng, nf)
     dt = time.perf_counter() - t0
-    edges = 2 * n2 * K_PAR
-    return {"value": edges / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n2} free + {n2} goal candidates x {K_PAR} parents of the same workload "
-                      f"({edges} edges, FP64 C oracle, OpenMP over edges), {dt:.1f} s"}
+    return {"value": e / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one round of the same iteration on {case['cand'].shape[0]} candidates "
+                      f"({case['n_goal']} valid goals of {ng} drawn + {nf} free) x {K_PAR} "
+                      f"parents = {e} edges, FP64 C oracle (OpenMP over edges), {dt:.1f} s"}
+
+
+def verify_sample(w):
+    """The planner on a bounded external-candidate batch (drawn by the
+    oracle's samplers) against the oracle's round: attached nodes must agree
+    except where an edge sits within the 1e-4 limit margin."""
+    import oracle as orc
+    from paper_2609_22608_gb300 import planner as P
+    from tests.parity import compare_round
+    e, (rtree, rinc, det), case = oracle_round(orc, w, 256, 24)
+    B = case["cand"].shape[0]
+    pl = P.Planner(w["arm"], P=1, n_cap=N_TREE + B + 8, b_max=B, k=K_PAR, K=K_GRID, S=S_COLL)
+    prob = P.problem_struct(w["pr"], B, case["n_goal"], root=w["root"], seed=1000 + w["seed"])
+    pl.reset([prob])
+    pl.load_tree(0, w["tree"], w["t_node"], w["parent"])
+    pl.set_candidates(0, case["cand"], case["n_goal"], case["T_req"], case["v_rel"])
+    out = pl.iterate([prob], 0, P.FN_PLAN_EXTERNAL)[0]
+    g = pl.get_tree(0)
+    pl.close()
+    bad = compare_round(orc, w["arm"], case, g, rtree, det, N_TREE, w["grid"], S=S_COLL)
+    inc_ok = (rinc["id"] < 0 and out["incumbent"] < 0) or \
+        (rinc["id"] >= 0 and abs(out["J"] - rinc["J"]) <= 1e-4 * max(1, abs(rinc["J"])))
+    return {"edges_checked": e, "candidates": B, "mismatches": len(bad), "incumbent_ok": bool(inc_ok),
+            "rule": "attached nodes equal except where an edge is within the 1e-4 limit margin"}
 
 
 # ----------------------------------------------------------------------------
@@ -160,80 +187,105 @@ def cpu_baseline(w, budget_s=15.0):
 def run_ours(args, rank, world):
     import torch
 
-    from paper_2609_22608_gb300 import plan_edges
+    from paper_2609_22608_gb300 import planner as P
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
     dev = torch.device("cuda")
     w = make_workload(args.seed + rank)
-    runner = plan_edges.EdgeBatchRunner(w, K_PAR, S_COLL, dev)
-    stream = torch.cuda.current_stream()
+    pl = P.Planner(w["arm"], P=1, n_cap=N_TREE + 2 * B_CAND, b_max=B_CAND, k=K_PAR, K=K_GRID,
+                   S=S_COLL)
+    prob = P.problem_struct(w["pr"], B_CAND, B_CAND // 2, root=w["root"], seed=1000 + w["seed"])
+    stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
-    for _ in range(args.warmup):
-        runner.step()
-    torch.cuda.synchronize()
-    # work counter for the roofline (same inputs -> same work)
-    samples = runner.count_samples()
+    def reset_tree():
+        pl.reset([prob], stream=stream)
+        pl.load_tree(0, w["tree"], w["t_node"], w["parent"], stream=stream)
+
+    for i in range(args.warmup):
+        reset_tree()
+        pl.iterate([prob], i, 0, stream=stream)
+    # work counter of the edge kernel for one step (same inputs -> same work)
+    reset_tree()
+    pl.sample_count(reset=True)
+    pl.iterate([prob], 0, 0, stream=stream)
+    samples = pl.sample_count(reset=True)
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    k_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    k_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    edge_ms, added = [], []
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or 0) \
-        if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else torch.cuda.current_device()
+    gpu_index = torch.cuda.current_device()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    if vis and vis.split(",")[0].isdigit():
+        gpu_index = int(vis.split(",")[gpu_index])
     with ClockSampler(gpu_index) as clk:
         for i in range(args.steps):
-            flush.zero_()  # L2 flush between timed steps, outside the events
+            reset_tree()                              # restore the input tree (untimed)
+            with torch.cuda.stream(stream):
+                flush.zero_()                         # L2 flush between timed steps (untimed)
             starts[i].record(stream)
-            runner.step(kernel_events=(k_s[i], k_e[i]))
+            out = pl.iterate([prob], 0, 0, stream=stream)[0]
             ends[i].record(stream)
+            edge_ms.append(pl.phase_ms()["edges"])
+            added.append(out["n_added"])
         torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     step_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
-    kern_ms = np.array([s.elapsed_time(e) for s, e in zip(k_s, k_e)])
+    phases = pl.phase_ms()
 
-    # end to end through the public API with host buffers (pinned), copies inside
-    e2e_ms, h2d, d2h = runner.e2e(args.steps)
+    # end to end through the public API with host buffers: the tree and the
+    # problem go host -> device, the rendezvous comes back, every step
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        pl.reset([prob], stream=stream)
+        pl.load_tree(0, w["tree"], w["t_node"], w["parent"], stream=stream)
+        pl.iterate([prob], 0, 0, stream=stream)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    h2d = w["tree"].nbytes + w["t_node"].nbytes + w["parent"].nbytes + 2 * 416
+    d2h = 88
+    pl.close()
 
-    edges = runner.edges_per_step
+    edges = B_CAND * K_PAR
     tot_ms = float(step_ms.sum())
+    p99 = float(np.percentile(step_ms, 99))
     if world > 1:
-        t = torch.tensor([tot_ms, float(np.percentile(step_ms, 99)), e2e_ms], device=dev)
+        t = torch.tensor([tot_ms, p99, e2e_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         tot_ms, p99, e2e_ms = [float(x) for x in t.cpu()]
-    else:
-        p99 = float(np.percentile(step_ms, 99))
     if rank != 0:
         return None
     ms_per_step = tot_ms / args.steps
     value = edges * world / (ms_per_step / 1e3)
-    # dominant kernel: free-edge full scan
-    kavg_s = float(kern_ms.mean()) / 1e3
-    flops = samples["free"] * FLOP_PER_SAMPLE
+    kavg_s = float(np.mean(edge_ms)) / 1e3
+    flops = samples * FLOP_PER_SAMPLE
     peak = fp32_peak_tflops()
     ach = flops / kavg_s / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "p99_ms": p99,
         "p50_ms": float(np.median(step_ms)), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded arm, tree, candidates)",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded arm, toss, tree; candidates sampled on device)",
         "config": {"workload": WORKLOAD, "tree": N_TREE, "batch": B_CAND, "k": K_PAR,
                    "K": K_GRID, "S": S_COLL, "edges_per_step": edges,
+                   "nodes_added_mean": float(np.mean(added)),
                    "parallelism": f"replicas x{world}", "l2": "flushed between timed steps"},
+        "phases_ms": phases,
         "clocks": clk.summary(),
         "e2e": {"value": edges * world / (e2e_ms / 1e3), "unit": UNIT,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": runner.launches_per_step * args.steps,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": 9 * args.steps,
         "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                      "frac": ach / peak, "traffic": None,
-                     "kernel": "k_time_full (free-edge duration scan)",
-                     "flop_per_launch": flops, "samples_per_launch": samples["free"],
+                     "kernel": "k_plan_edges (edge timing: probes + verify + clearance)",
+                     "flop_per_launch": flops, "samples_per_launch": samples,
                      "kernel_ms": kavg_s * 1e3,
-                     "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz"},
+                     "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 FLOP x max SM clock (of derived)"},
     }
     return line, w
 
@@ -249,31 +301,33 @@ def fp32_peak_tflops():
 
 def run_reference(args, rank, world):
     """Reference arm: the FP64 oracle (the paper ships no code) on the host
-    cores, each step a bounded sample of the same workload."""
+    cores, each step one round of the same iteration on a bounded candidate
+    sample."""
     if rank != 0:
         return None
     import oracle as orc
     w = make_workload(args.seed)
     cores = os.cpu_count() or 1
     orc.set_threads(cores)
-    n = 24
+    ng, nf = 96, 24
     for _ in range(max(1, min(args.warmup, 1))):
-        oracle_step(orc, w, 4, 4)
-    times = []
+        oracle_round(orc, w, 16, 4)
+    times, edges = [], 0
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle_step(orc, w, n, n)
+        e, _, case = oracle_round(orc, w, ng, nf)
         times.append(time.perf_counter() - t0)
-    edges = 2 * n * K_PAR
+        edges += e
     dt = float(np.sum(times))
-    value = edges * args.steps / dt
+    value = edges / dt
     ms = dt / args.steps * 1e3
-    sample = f"{n} free + {n} goal candidates x {K_PAR} parents per step ({edges} edges)"
+    sample = (f"per step one round on {case['cand'].shape[0]} candidates ({case['n_goal']} valid "
+              f"goals of {ng} drawn + {nf} free) x {K_PAR} parents of the same workload")
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded arm, tree, candidates)",
+        "data": "synthetic (seeded arm, toss, tree)",
         "config": {"workload": WORKLOAD, "tree": N_TREE, "batch": B_CAND, "k": K_PAR,
                    "K": K_GRID, "S": S_COLL, "parallelism": "host cores"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -304,29 +358,6 @@ def main():
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()
-
-
-def verify_sample(w):
-    """Oracle check of a seeded sample of the timed step's edges (the numbers
-    above count as verified only if this passes)."""
-    import torch
-
-    import oracle as orc
-    from paper_2609_22608_gb300 import plan_edges
-    from tests.parity import kstar_mismatches
-    n = 12
-    rf, rg, s0, s1, cap, Tg = oracle_step(orc, w, n, n)
-    runner = plan_edges.EdgeBatchRunner(w, K_PAR, S_COLL, torch.device("cuda"))
-    gk_free, gk_goal = runner.results()
-    # the first n free / n goal candidates of the batch
-    kf = gk_free.reshape(-1, K_PAR)[:n].reshape(-1)
-    kg = gk_goal.reshape(-1, K_PAR)[:n].reshape(-1)
-    nf = n * K_PAR
-    bad = kstar_mismatches(orc, w["arm"], s0[:nf], s1[:nf], w["grid"], S_COLL, kf, rf["k_star"], cap)
-    clear = np.abs(np.maximum(rg["rho3"][:, 0], rg["rho3"][:, 1]) - 1) > 1e-4
-    bad_g = int(np.sum((kg != rg["k_star"]) & clear))
-    return {"edges_checked": 2 * nf, "mismatches": len(bad) + bad_g,
-            "rule": "k* equal except within a 1e-4 limit margin"}
 
 
 if __name__ == "__main__":

@@ -148,6 +148,22 @@ fn_status fn_time_edges_counted(const fn_arm_t* arm, const float* s0, const floa
                                 unsigned long long* sample_count, void* stream);
 
 /*
+ * fn_autotune_time_edges -- the schedule autotuner for fn_time_edges: runs
+ * the call (same arguments) with every compiled schedule variant of the edge
+ * kernel (register budget / resident blocks per SM), `reps` timed runs each
+ * after one warm-up, and records the fastest for this (mode, E bucket, K, S)
+ * on the current device; later fn_time_edges calls of that shape use it.
+ * The outputs are left as computed by the last variant (all variants compute
+ * identical results).  chosen: host, the winning variant index (may be NULL);
+ * variant_ms: host [3] mean ms per variant (may be NULL).  Synchronous.
+ */
+fn_status fn_autotune_time_edges(const fn_arm_t* arm, const float* s0, const float* s1, int E,
+                                 const float* T_grid, int K, int S, int mode,
+                                 const float* T_fixed, const float* T_cap, int32_t* k_star,
+                                 float* T_star, float* rho3, uint8_t* ok, int reps, int* chosen,
+                                 float* variant_ms, void* stream);
+
+/*
  * fn_rnea_dump -- torques of Eq. (torque) along each edge (diagnostic hook
  * for torque parity).  tau[e][s][j] = tau_j(t_s) of the cubic from s0[e] to
  * s1[e] with duration T[e], t_s = s T[e]/(S-1).
@@ -202,6 +218,151 @@ fn_status fn_make_edges(const float* tree, const float* t_node, const float* can
                         int n_goal, const int32_t* nn_idx, int k_nn, const float* T_req,
                         float t_best, float* s0, float* s1, float* T_param, int32_t* parent,
                         void* stream);
+
+
+/* ------------------------------------------------------------------------
+ * Planner: batched expansion of Algorithm 1 over P independent problems.
+ * ------------------------------------------------------------------------ */
+
+/* Static sizes of a planner (Sec. IV-E: the tree is preallocated as a
+ * struct of arrays; every buffer is sized here, once). */
+typedef struct {
+  int P;              /* independent problems (1..1024)                      */
+  int n_cap;          /* tree capacity per problem (2..1<<22)                */
+  int b_max;          /* largest candidate batch per problem (1..1<<16)      */
+  int k;              /* parents per candidate incl. the root (1..17)        */
+  int K;              /* duration grid size (1..FN_MAX_GRID)                 */
+  float T_lo, T_hi;   /* log grid T_i = T_lo (T_hi/T_lo)^(i/(K-1))           */
+  int S;              /* collocation points of the dynamics check            */
+  int S_clear;        /* collocation points of the clearance check (>= 2)    */
+  int reach_grid;     /* points of the Eq. (reach) grid (>= 2)               */
+  float w_vel;        /* velocity weight of the parent distance              */
+  float vel_frac;     /* free samples: |qd_j| <= vel_frac * qdbar_j(q_j)     */
+  float clear_margin; /* minimum clearance of an edge, metres                */
+  int edge_blocks;    /* persistent blocks of the edge kernel (0 = auto)     */
+} fn_planner_cfg_t;
+
+#define FN_MAX_OBS 8
+
+/* One planning problem (Def. "Interception planning"): the measured root
+ * state, the ballistic flight estimate of Eq. (ballistic) with the reach
+ * window, latency compensation (Sec. IV-F: plan time t corresponds to flight
+ * time t + t_offset), the uncertainty model of Sec. IV-B, the manifold
+ * thresholds of Def. 2, the objective constants of Eq. (objective), the
+ * end-effector speed bound of Eq. (reach), obstacle spheres, the batch of
+ * this problem and its goal share, and the Philox seed. */
+typedef struct {
+  float q0[7], qd0[7];
+  float x0[3], v0[3], g[3];
+  float t_enter, t_fall, t_offset;
+  float sig_p, sig_v, sig_a;
+  int sig_linear;            /* 1: sigma(t) = sig_lin_a + sig_lin_b t */
+  float sig_lin_a, sig_lin_b;
+  float a_min, v_min;
+  float w_v, v_target, w_p, w_r, w_x, r_catch, nu0, lam;
+  float v_tip;
+  int batch;                 /* candidates this round (<= b_max)      */
+  int n_goal;                /* goal candidates among them            */
+  int n_obs;                 /* obstacle spheres (<= FN_MAX_OBS)      */
+  float obs[FN_MAX_OBS][4];  /* centre xyz, radius                    */
+  unsigned long long seed;
+} fn_problem_t;
+
+/* Output of one iteration per problem (Algorithm 1's return value, D9). */
+typedef struct {
+  float q_g[7], qd_g[7];  /* end state of the incumbent plan's first edge  */
+  float T;                /* that edge's duration from the root            */
+  float J;                /* incumbent score (-inf if none)                */
+  float t_best;           /* incumbent arrival time (t_fall if none)       */
+  int incumbent;          /* incumbent node id (-1 if none)                */
+  int n_nodes;            /* tree size after the iteration                 */
+  int n_added;            /* nodes attached in this iteration              */
+  int status;             /* 0, or bit 1: tree full (candidates dropped)   */
+} fn_rendezvous_t;
+
+typedef struct fn_planner fn_planner_t;
+
+/* Allocates every device and pinned host buffer of the planner (the only
+ * allocating call).  `arm` is copied.  FN_ENOMEM if an allocation fails. */
+fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm_t* arm,
+                            fn_planner_t** out);
+fn_status fn_planner_destroy(fn_planner_t* pl);
+
+/* Algorithm 1, first line: each problem's tree becomes its root
+ * (q0, qd0, t = 0); the incumbent is cleared and t_best = t_fall.
+ * probs: host [P]. */
+fn_status fn_planner_reset(fn_planner_t* pl, const fn_problem_t* probs, void* stream);
+
+/* Replace problem p's tree with n host nodes (states [n][16], time-to-come
+ * t[n], parent[n] with parent[0] = -1 and parent[i] < i): used to start an
+ * iteration from a given tree.  Nodes carry no score and nu = 0. */
+fn_status fn_planner_load_tree(fn_planner_t* pl, int p, const float* states, const float* t,
+                               const int32_t* parent, int n, void* stream);
+
+/* Give problem p an explicit candidate batch for the next iteration that
+ * runs with FN_PLAN_EXTERNAL: host states [B][16]; the first n_goal are goal
+ * candidates with required arrival T_req[n_goal] and relative speed
+ * v_rel[n_goal] (|v_b - xdot(T)| of Eq. (terms)). */
+fn_status fn_planner_set_candidates(fn_planner_t* pl, int p, const float* states, int B,
+                                    int n_goal, const float* T_req, const float* v_rel,
+                                    void* stream);
+
+#define FN_PLAN_EXTERNAL 1u /* use the candidates given by fn_planner_set_candidates */
+#define FN_PLAN_PRUNE 2u    /* prune the trees after the round (Eq. (reach))          */
+
+/*
+ * fn_plan_iteration -- one round of Algorithm 1 for all P problems:
+ *   sample B_p candidates (unless FN_PLAN_EXTERNAL): the first n_goal by
+ *     the goal chart (Def. "Goal chart"), the rest uniform in the joint box
+ *     with |qd| <= vel_frac qdbar(q); Philox4x32-10 counter
+ *     (candidate, iter, problem, stream), key = seed;
+ *   Parents: root + (k-1) nearest nodes (fn_knn_tree's metric);
+ *   goal edges: one check at T_req - t(p); free edges: first feasible grid
+ *     duration with t(p) + T <= t_best (FN_MODE_FULL with a cap);
+ *   Clear: link capsules vs obstacle spheres at S_clear points of the edge,
+ *     rejected below clear_margin;
+ *   attach each candidate to the ok parent of least t(p) + T_p (ties: lower
+ *     parent slot), appended in candidate order;
+ *   incumbent = argmax J (Eq. (objective)) over rendezvous nodes (ties: lower
+ *     node id); t_best = its arrival time;
+ *   with FN_PLAN_PRUNE, Eq. (reach) pruning (root kept, descendants of
+ *     pruned nodes removed, order and parents preserved).
+ * Enqueued on `stream`; returns after the stream has finished and `out`
+ * (host [P]) holds each problem's rendezvous.  probs: host [P].
+ */
+fn_status fn_plan_iteration(fn_planner_t* pl, const fn_problem_t* probs, int iter,
+                            unsigned flags, fn_rendezvous_t* out, void* stream);
+
+/*
+ * CUDA-graph form of fn_plan_iteration: fn_planner_capture records one
+ * iteration (with `flags`) into a graph; fn_plan_replay refreshes the
+ * problems and the iteration counter through the planner's pinned staging
+ * buffer, launches the graph on `stream` and returns like fn_plan_iteration.
+ */
+fn_status fn_planner_capture(fn_planner_t* pl, unsigned flags, void* stream);
+fn_status fn_plan_replay(fn_planner_t* pl, const fn_problem_t* probs, int iter,
+                         fn_rendezvous_t* out, void* stream);
+
+/* Durations in ms of the last fn_plan_iteration's phases, from CUDA events
+ * recorded on its stream: [0] schedule, [1] sample, [2] parents (kNN),
+ * [3] edges (timing + clearance), [4] attach + score, [5] prune, [6] output.
+ * ms: host [7].  FN_EINVAL before the first fn_plan_iteration. */
+fn_status fn_planner_phase_ms(fn_planner_t* pl, float* ms);
+
+/* Torque evaluations (edge, duration, sample) performed by the planner's
+ * edge kernel since creation or the last reset (reset != 0 zeroes it). */
+fn_status fn_planner_sample_count(fn_planner_t* pl, unsigned long long* count, int reset);
+
+/* Copy problem p's tree to host (any pointer may be NULL): states [n][16],
+ * t[n], parent[n], J[n] (NaN for non-rendezvous nodes), nu[n]; *n = size.
+ * Synchronous. */
+fn_status fn_planner_get_tree(fn_planner_t* pl, int p, float* states, float* t,
+                              int32_t* parent, float* J, float* nu, int* n, int cap);
+/* Copy problem p's last candidate batch to host: states [B][16], T_req[B],
+ * v_rel[B], valid[B] (goal candidates whose chart decoding succeeded, and
+ * every free candidate).  Synchronous. */
+fn_status fn_planner_get_candidates(fn_planner_t* pl, int p, float* states, float* T_req,
+                                    float* v_rel, uint8_t* valid, int cap);
 
 #ifdef __cplusplus
 }

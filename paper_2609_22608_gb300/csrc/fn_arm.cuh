@@ -45,13 +45,19 @@ struct ArmK {
 bool make_armk(const fn_arm_t* a, ArmK* out);
 
 // ---------------------------------------------------------------------------
-// Cubic coefficients of one edge at duration T:
-//   sigma(t) = q0 + qd0 t + c2 t^2 + c3 t^3
-//   c2 = 3 d1/T^2 - d2/T,  c3 = d2/T^2 - 2 d1/T^3,
-//   d1 = q1 - q0 - qd0 T,  d2 = qd1 - qd0.
+// The cubic of Eq. (cubic) in normalised time u = t/T in [0, 1]:
+//   sigma(u)     = q0 + b1 u + b2 u^2 + b3 u^3,
+//   sigma_dot    = (b1 + 2 b2 u + 3 b3 u^2) / T,
+//   sigma_ddot   = (2 b2 + 6 b3 u) / T^2,
+//   b1 = qd0 T,  b2 = 3 d1 - d2 T,  b3 = d2 T - 2 d1,
+//   d1 = q1 - q0 - qd0 T,  d2 = qd1 - qd0
+// (identical to Eq. (cubic) with c2 = b2/T^2, c3 = b3/T^3).  In this form the
+// coefficients are O(|q|) at any T, so the short edges whose t-form terms
+// (~1e4 rad/s^2 at T = 0.05 s) cancel at mid-edge keep their accuracy.
 // ---------------------------------------------------------------------------
 struct Cubic {
-  float q0[7], qd0[7], c2[7], c3[7];
+  float q0[7], b1[7], b2[7], b3[7];
+  float iT, iT2;
 };
 
 struct EdgeStates {
@@ -66,43 +72,112 @@ __device__ __forceinline__ void load_state(const float4* __restrict__ p, float* 
   qd[4] = d.x; qd[5] = d.y; qd[6] = d.z;
 }
 
-__device__ __forceinline__ bool edge_finite(const EdgeStates& e) {
-  bool ok = true;
-#pragma unroll
-  for (int j = 0; j < 7; ++j)
-    ok = ok && isfinite(e.q0[j]) && isfinite(e.qd0[j]) && isfinite(e.q1[j]) && isfinite(e.qd1[j]);
-  return ok;
+// error-free transformations (Knuth TwoSum, FMA-based TwoProd)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = fmaf(a, b, -p);
+}
+
+// Coefficients of one joint.  ACC = true carries d1, d2 and the products as
+// unevaluated float pairs, so b2 and b3 come out (nearly) correctly rounded;
+// ACC = false is the plain FP32 evaluation used where a decision only needs
+// to hold up to the feasibility margin (the end-sample probes).
+template <bool ACC>
+__device__ __forceinline__ void joint_coef(float q0, float qd0, float q1, float qd1, float T,
+                                           float& b1, float& b2, float& b3) {
+  if (!ACC) {
+    const float d1 = fmaf(-qd0, T, q1 - q0);
+    const float d2 = qd1 - qd0;
+    b1 = qd0 * T;
+    b2 = fmaf(-d2, T, 3.0f * d1);
+    b3 = fmaf(d2, T, -2.0f * d1);
+    return;
+  }
+  float dqh, dql, ph, pl, d1h, d1l, d2h, d2l;
+  two_sum(q1, -q0, dqh, dql);
+  two_prod(qd0, T, ph, pl);
+  two_sum(dqh, -ph, d1h, d1l);
+  d1l = __fadd_rn(d1l, __fsub_rn(dql, pl));
+  two_sum(qd1, -qd0, d2h, d2l);
+  float t3h, t3l, mh, ml, b2h, b2l, b3h, b3l;
+  two_prod(3.0f, d1h, t3h, t3l);
+  t3l = fmaf(3.0f, d1l, t3l);
+  two_prod(d2h, T, mh, ml);
+  ml = fmaf(d2l, T, ml);
+  two_sum(t3h, -mh, b2h, b2l);
+  b2 = __fadd_rn(b2h, __fadd_rn(b2l, __fsub_rn(t3l, ml)));
+  two_sum(mh, -2.0f * d1h, b3h, b3l);
+  b3 = __fadd_rn(b3h, __fadd_rn(b3l, __fsub_rn(ml, 2.0f * d1l)));
+  b1 = ph;
 }
 
 // coefficients from an edge held in shared memory as two packed states
 // (sh[0..6] = q0, sh[8..14] = qd0, sh[16..22] = q1, sh[24..30] = qd1)
+template <bool ACC>
 __device__ __forceinline__ void cubic_coef_sh(const float* sh, float T, Cubic& c) {
-  const float iT = 1.0f / T;
-  const float iT2 = iT * iT;
+  c.iT = 1.0f / T;
+  c.iT2 = c.iT * c.iT;
 #pragma unroll
   for (int j = 0; j < 7; ++j) {
-    const float q0 = sh[j], qd0 = sh[8 + j], q1 = sh[16 + j], qd1 = sh[24 + j];
-    const float d1 = fmaf(-qd0, T, q1 - q0);
-    const float d2 = qd1 - qd0;
-    c.q0[j] = q0;
-    c.qd0[j] = qd0;
-    c.c2[j] = fmaf(3.0f * d1, iT2, -d2 * iT);
-    c.c3[j] = fmaf(-2.0f * d1, iT2 * iT, d2 * iT2);
+    c.q0[j] = sh[j];
+    joint_coef<ACC>(sh[j], sh[8 + j], sh[16 + j], sh[24 + j], T, c.b1[j], c.b2[j], c.b3[j]);
   }
 }
 
+template <bool ACC>
 __device__ __forceinline__ void cubic_coef(const EdgeStates& e, float T, Cubic& c) {
-  const float iT = 1.0f / T;
-  const float iT2 = iT * iT;
+  c.iT = 1.0f / T;
+  c.iT2 = c.iT * c.iT;
 #pragma unroll
   for (int j = 0; j < 7; ++j) {
-    const float d1 = fmaf(-e.qd0[j], T, e.q1[j] - e.q0[j]);
-    const float d2 = e.qd1[j] - e.qd0[j];
     c.q0[j] = e.q0[j];
-    c.qd0[j] = e.qd0[j];
-    c.c2[j] = fmaf(3.0f * d1, iT2, -d2 * iT);
-    c.c3[j] = fmaf(-2.0f * d1, iT2 * iT, d2 * iT2);
+    joint_coef<ACC>(e.q0[j], e.qd0[j], e.q1[j], e.qd1[j], T, c.b1[j], c.b2[j], c.b3[j]);
   }
+}
+
+// sigma, sigma_dot, sigma_ddot of joint j at normalised time u
+__device__ __forceinline__ void cubic_eval(const Cubic& c, int j, float u, float& q, float& v,
+                                           float& a) {
+  q = fmaf(fmaf(fmaf(c.b3[j], u, c.b2[j]), u, c.b1[j]), u, c.q0[j]);
+  v = fmaf(fmaf(3.0f * c.b3[j], u, 2.0f * c.b2[j]), u, c.b1[j]) * c.iT;
+  a = fmaf(6.0f * c.b3[j], u, 2.0f * c.b2[j]) * c.iT2;
+}
+
+// The same coefficients held in shared memory, one column per lane
+// (element (f, lane) at p[32 f]): frees ~30 registers in the hot loop.
+#define FN_CUBIC_WORDS 30
+struct CubicLane {
+  float* p;  // &buf[lane] of a [FN_CUBIC_WORDS][32] per-warp buffer
+  __device__ __forceinline__ float q0(int j) const { return p[32 * j]; }
+  __device__ __forceinline__ float b1(int j) const { return p[32 * (7 + j)]; }
+  __device__ __forceinline__ float b2(int j) const { return p[32 * (14 + j)]; }
+  __device__ __forceinline__ float b3(int j) const { return p[32 * (21 + j)]; }
+  __device__ __forceinline__ float iT() const { return p[32 * 28]; }
+  __device__ __forceinline__ float iT2() const { return p[32 * 29]; }
+  __device__ __forceinline__ void store(const Cubic& c) const {
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      p[32 * j] = c.q0[j];
+      p[32 * (7 + j)] = c.b1[j];
+      p[32 * (14 + j)] = c.b2[j];
+      p[32 * (21 + j)] = c.b3[j];
+    }
+    p[32 * 28] = c.iT;
+    p[32 * 29] = c.iT2;
+  }
+};
+
+__device__ __forceinline__ void cubic_eval(const CubicLane& c, int j, float u, float& q, float& v,
+                                           float& a) {
+  const float b2 = c.b2(j), b3 = c.b3(j);
+  q = fmaf(fmaf(fmaf(b3, u, b2), u, c.b1(j)), u, c.q0(j));
+  v = fmaf(fmaf(3.0f * b3, u, 2.0f * b2), u, c.b1(j)) * c.iT();
+  a = fmaf(6.0f * b3, u, 2.0f * b2) * c.iT2();
 }
 
 // ---------------------------------------------------------------------------
@@ -120,8 +195,8 @@ __device__ __forceinline__ void cubic_coef(const EdgeStates& e, float T, Cubic& 
 // Each tau_j is handed to `sink(j, tau_j, qd_j)` as soon as the inward pass
 // produces it, so no torque array is kept.
 // ---------------------------------------------------------------------------
-template <class Sink>
-__device__ __forceinline__ void torque_at(const ArmK& A, const Cubic& c, float t, Sink&& sink) {
+template <class Coef, class Sink>
+__device__ __forceinline__ void torque_at(const ArmK& A, const Coef& c, float u, Sink&& sink) {
   float qd[7], ex[7];
   float ct[7], st[7];
   float Fx[7], Fy[7], Fz[7], Nx[7], Ny[7], Nz[7];
@@ -130,9 +205,8 @@ __device__ __forceinline__ void torque_at(const ArmK& A, const Cubic& c, float t
   float ax = A.g0x, ay = A.g0y, az = A.g0z;
 #pragma unroll
   for (int j = 0; j < 7; ++j) {
-    const float q = fmaf(fmaf(fmaf(c.c3[j], t, c.c2[j]), t, c.qd0[j]), t, c.q0[j]);
-    const float v = fmaf(fmaf(3.0f * c.c3[j], t, 2.0f * c.c2[j]), t, c.qd0[j]);
-    const float acc = fmaf(6.0f * c.c3[j], t, 2.0f * c.c2[j]);
+    float q, v, acc;
+    cubic_eval(c, j, u, q, v, acc);
     qd[j] = v;
     // armature and friction (logistic with an IEEE division)
     const float e = expf(-A.f2[j] * (v + A.f3[j]));
@@ -213,11 +287,12 @@ __device__ __forceinline__ void torque_at(const ArmK& A, const Cubic& c, float t
   }
 }
 
-// ratios of one sample: rho_tau(s) and rho_P(s)
-__device__ __forceinline__ void sample_ratios(const ArmK& A, const Cubic& c, float t, float& rt,
+// ratios of one sample at normalised time u: rho_tau(s) and rho_P(s)
+template <class Coef>
+__device__ __forceinline__ void sample_ratios(const ArmK& A, const Coef& c, float u, float& rt,
                                               float& rp) {
   float r = 0.f, pw = 0.f;
-  torque_at(A, c, t, [&](int j, float tau, float v) {
+  torque_at(A, c, u, [&](int j, float tau, float v) {
     r = fmaxf(r, fabsf(tau) * A.inv_tau[j]);
     pw = fmaf(tau, v, pw);
   });
@@ -233,21 +308,22 @@ __device__ __forceinline__ float taper(const ArmK& A, int j, float q) {
 }
 
 // rho_v contribution of joint j: exact extremum of the quadratic velocity
-// qd(t) = qd0 + 2 c2 t + 3 c3 t^2 over [0, T] (ends and stationary point),
-// each compared with the taper at the joint's position at that time.
-__device__ __forceinline__ float rho_v_joint(const ArmK& A, const Cubic& c, int j, float T) {
+// (b1 + 2 b2 u + 3 b3 u^2)/T over u in [0, 1] (ends and the stationary point
+// u* = -b2/(3 b3)), each compared with the taper at the joint's position at
+// that same time.
+__device__ __forceinline__ float rho_v_joint(const ArmK& A, const Cubic& c, int j) {
   float best = 0.f;
-  float cand[3] = {0.f, T, -1.f};
-  if (c.c3[j] != 0.f) {
-    const float ts = -c.c2[j] / (3.0f * c.c3[j]);
-    if (ts > 0.f && ts < T) cand[2] = ts;
+  float cand[3] = {0.f, 1.f, -1.f};
+  if (c.b3[j] != 0.f) {
+    const float us = -c.b2[j] / (3.0f * c.b3[j]);
+    if (us > 0.f && us < 1.f) cand[2] = us;
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const float t = cand[i];
-    if (t < 0.f) continue;
-    const float pos = fmaf(fmaf(fmaf(c.c3[j], t, c.c2[j]), t, c.qd0[j]), t, c.q0[j]);
-    const float vel = fmaf(fmaf(3.0f * c.c3[j], t, 2.0f * c.c2[j]), t, c.qd0[j]);
+    const float u = cand[i];
+    if (u < 0.f) continue;
+    float pos, vel, acc;
+    cubic_eval(c, j, u, pos, vel, acc);
     const float b = taper(A, j, pos);
     float r;
     if (b > 0.f) r = fabsf(vel) / b;

@@ -48,32 +48,68 @@ __global__ void __launch_bounds__(128) k_knn_partial(const float4* __restrict__ 
   }
 }
 
+// Merge of the split lists with one warp per query: lane l holds split l's
+// sorted list; k rounds of a warp-wide (d, index) argmin over the list heads,
+// the winning lane drops its head.
 template <int KM>
-__global__ void __launch_bounds__(128) k_knn_merge(int B, int nsplit, int k,
+__global__ void __launch_bounds__(256) k_knn_merge(int B, int nsplit, int k,
                                                    const float* __restrict__ part_d,
                                                    const int32_t* __restrict__ part_i,
                                                    float* __restrict__ out_d,
                                                    int32_t* __restrict__ out_i) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const long b = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (b >= B) return;
-  TopK<KM> top;
-  top.init();
-  for (int s = 0; s < nsplit; ++s) {
-    const long off = ((long)s * B + b) * KM;
+  float d[KM];
+  int id[KM];
 #pragma unroll
-    for (int j = 0; j < KM; ++j) top.push(part_d[off + j], part_i[off + j]);
+  for (int j = 0; j < KM; ++j) {
+    d[j] = INFINITY;
+    id[j] = 0x7fffffff;
   }
-  top.store(out_d + (long)b * k, out_i + (long)b * k, k);
+  if (lane < nsplit) {
+    const long off = ((long)lane * B + b) * KM;
+#pragma unroll
+    for (int j = 0; j < KM; ++j) {
+      d[j] = part_d[off + j];
+      id[j] = part_i[off + j];
+    }
+  }
+  for (int r = 0; r < k; ++r) {
+    float md = d[0];
+    int mi = id[0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float od = __shfl_xor_sync(0xffffffffu, md, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, mi, o);
+      if (knn_less(od, oi, md, mi)) { md = od; mi = oi; }
+    }
+    if (lane == 0) {
+      const bool empty = (mi == 0x7fffffff);
+      out_d[b * k + r] = empty ? INFINITY : md;
+      out_i[b * k + r] = empty ? -1 : mi;
+    }
+    if (id[0] == mi && mi != 0x7fffffff) {  // the winner drops its head
+#pragma unroll
+      for (int j = 0; j + 1 < KM; ++j) {
+        d[j] = d[j + 1];
+        id[j] = id[j + 1];
+      }
+      d[KM - 1] = INFINITY;
+      id[KM - 1] = 0x7fffffff;
+    }
+  }
 }
 
 int knn_km(int k) { return k <= 8 ? 8 : 16; }
 
-// split count: enough blocks for ~4 per SM, at least one tile per split
+// split count: about two blocks per SM, each split at least 4 tiles of
+// nodes, at most 32 (one merge lane per split)
 int knn_nsplit(int B, int N) {
   const int qblocks = (B + 127) / 128;
-  const int want = (4 * num_sms() + qblocks - 1) / std::max(qblocks, 1);
-  const int tiles = std::max(1, (N + KNN_TILE - 1) / KNN_TILE);
-  return std::max(1, std::min(want, tiles));
+  const int want = (2 * num_sms() + qblocks - 1) / std::max(qblocks, 1);
+  const int chunks = std::max(1, N / (4 * KNN_TILE));
+  return std::max(1, std::min(std::min(want, chunks), 32));
 }
 
 size_t knn_ws_bytes(int B, int N, int k) {
@@ -93,12 +129,12 @@ fn_status knn_launch(const float* tree, int N, int first, const float* queries, 
     k_knn_partial<8><<<grid, 128, 0, st>>>((const float4*)tree, N, first, (const float4*)queries,
                                            B, w_vel, nsplit, k, part_d, part_i, d2, idx);
     if (nsplit > 1)
-      k_knn_merge<8><<<(B + 127) / 128, 128, 0, st>>>(B, nsplit, k, part_d, part_i, d2, idx);
+      k_knn_merge<8><<<(B + 7) / 8, 256, 0, st>>>(B, nsplit, k, part_d, part_i, d2, idx);
   } else {
     k_knn_partial<16><<<grid, 128, 0, st>>>((const float4*)tree, N, first, (const float4*)queries,
                                             B, w_vel, nsplit, k, part_d, part_i, d2, idx);
     if (nsplit > 1)
-      k_knn_merge<16><<<(B + 127) / 128, 128, 0, st>>>(B, nsplit, k, part_d, part_i, d2, idx);
+      k_knn_merge<16><<<(B + 7) / 8, 256, 0, st>>>(B, nsplit, k, part_d, part_i, d2, idx);
   }
   return launch_status();
 }

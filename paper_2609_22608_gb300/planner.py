@@ -1,0 +1,216 @@
+"""Python binding of the planner part of the C ABI (fn_planner_*, fn_plan_*).
+
+Argument marshalling only: every step of an iteration runs in libfruitninja.so.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from ._lib import arm_struct, check, lib
+
+FN_PLAN_EXTERNAL = 1
+FN_PLAN_PRUNE = 2
+FN_MAX_OBS = 8
+
+
+class FnPlannerCfg(C.Structure):
+    _fields_ = [("P", C.c_int), ("n_cap", C.c_int), ("b_max", C.c_int), ("k", C.c_int),
+                ("K", C.c_int), ("T_lo", C.c_float), ("T_hi", C.c_float), ("S", C.c_int),
+                ("S_clear", C.c_int), ("reach_grid", C.c_int), ("w_vel", C.c_float),
+                ("vel_frac", C.c_float), ("clear_margin", C.c_float), ("edge_blocks", C.c_int)]
+
+
+class FnProblem(C.Structure):
+    _fields_ = [("q0", C.c_float * 7), ("qd0", C.c_float * 7), ("x0", C.c_float * 3),
+                ("v0", C.c_float * 3), ("g", C.c_float * 3), ("t_enter", C.c_float),
+                ("t_fall", C.c_float), ("t_offset", C.c_float), ("sig_p", C.c_float),
+                ("sig_v", C.c_float), ("sig_a", C.c_float), ("sig_linear", C.c_int),
+                ("sig_lin_a", C.c_float), ("sig_lin_b", C.c_float), ("a_min", C.c_float),
+                ("v_min", C.c_float), ("w_v", C.c_float), ("v_target", C.c_float),
+                ("w_p", C.c_float), ("w_r", C.c_float), ("w_x", C.c_float),
+                ("r_catch", C.c_float), ("nu0", C.c_float), ("lam", C.c_float),
+                ("v_tip", C.c_float), ("batch", C.c_int), ("n_goal", C.c_int),
+                ("n_obs", C.c_int), ("obs", (C.c_float * 4) * FN_MAX_OBS),
+                ("seed", C.c_ulonglong)]
+
+
+class FnRendezvous(C.Structure):
+    _fields_ = [("q_g", C.c_float * 7), ("qd_g", C.c_float * 7), ("T", C.c_float),
+                ("J", C.c_float), ("t_best", C.c_float), ("incumbent", C.c_int),
+                ("n_nodes", C.c_int), ("n_added", C.c_int), ("status", C.c_int)]
+
+
+def _bind():
+    L = lib()
+    if getattr(L, "_planner_bound", False):
+        return L
+    vp, i32 = C.c_void_p, C.c_int
+    L.fn_planner_create.argtypes = [C.POINTER(FnPlannerCfg), vp, C.POINTER(vp)]
+    L.fn_planner_destroy.argtypes = [vp]
+    L.fn_planner_reset.argtypes = [vp, vp, vp]
+    L.fn_planner_load_tree.argtypes = [vp, i32, vp, vp, vp, i32, vp]
+    L.fn_planner_set_candidates.argtypes = [vp, i32, vp, i32, i32, vp, vp, vp]
+    L.fn_plan_iteration.argtypes = [vp, vp, i32, C.c_uint, vp, vp]
+    L.fn_planner_capture.argtypes = [vp, C.c_uint, vp]
+    L.fn_plan_replay.argtypes = [vp, vp, i32, vp, vp]
+    L.fn_planner_get_tree.argtypes = [vp, i32, vp, vp, vp, vp, vp, C.POINTER(C.c_int), i32]
+    L.fn_planner_get_candidates.argtypes = [vp, i32, vp, vp, vp, vp, i32]
+    L.fn_planner_sample_count.argtypes = [vp, C.POINTER(C.c_ulonglong), i32]
+    L.fn_planner_phase_ms.argtypes = [vp, vp]
+    for n in ("fn_planner_create", "fn_planner_destroy", "fn_planner_reset", "fn_planner_load_tree",
+              "fn_planner_set_candidates", "fn_plan_iteration", "fn_planner_capture",
+              "fn_plan_replay", "fn_planner_get_tree", "fn_planner_get_candidates",
+              "fn_planner_sample_count", "fn_planner_phase_ms"):
+        getattr(L, n).restype = i32
+    L._planner_bound = True
+    return L
+
+
+def problem_struct(pr: dict, batch: int, n_goal: int, root=None, obstacles=None,
+                   seed: int = 0) -> FnProblem:
+    """FnProblem from synth.make_problem's dict, a root state [16] and an
+    optional [n][4] obstacle array."""
+    s = FnProblem()
+    root = pr.get("root") if root is None else root
+    root = np.zeros(16, np.float32) if root is None else np.asarray(root, np.float32)
+    s.q0[:] = [float(x) for x in root[0:7]]
+    s.qd0[:] = [float(x) for x in root[8:15]]
+    for f in ("x0", "v0", "g"):
+        getattr(s, f)[:] = [float(x) for x in np.asarray(pr[f], np.float32)]
+    for f in ("t_enter", "t_fall", "t_offset", "sig_p", "sig_v", "sig_a", "sig_lin_a", "sig_lin_b",
+              "a_min", "v_min", "w_v", "v_target", "w_p", "w_r", "w_x", "r_catch", "nu0", "lam",
+              "v_tip"):
+        setattr(s, f, float(np.float32(pr[f])))
+    s.sig_linear = int(pr["sig_linear"])
+    s.batch = int(batch)
+    s.n_goal = int(n_goal)
+    obs = np.zeros((0, 4), np.float32) if obstacles is None else np.asarray(obstacles, np.float32)
+    if obs.shape[0] > FN_MAX_OBS:
+        raise ValueError("too many obstacles")
+    s.n_obs = int(obs.shape[0])
+    for i in range(obs.shape[0]):
+        s.obs[i][:] = [float(x) for x in obs[i]]
+    s.seed = int(seed)
+    return s
+
+
+def rendezvous_dict(r: FnRendezvous) -> dict:
+    return dict(q_g=np.array(r.q_g[:], np.float32), qd_g=np.array(r.qd_g[:], np.float32),
+                T=float(r.T), J=float(r.J), t_best=float(r.t_best), incumbent=int(r.incumbent),
+                n_nodes=int(r.n_nodes), n_added=int(r.n_added), status=int(r.status))
+
+
+class Planner:
+    def __init__(self, arm, P=1, n_cap=8192, b_max=2048, k=8, K=128, T_lo=0.05, T_hi=2.0, S=64,
+                 S_clear=8, reach_grid=256, w_vel=0.1, vel_frac=0.5, clear_margin=0.02,
+                 edge_blocks=0):
+        L = _bind()
+        self.cfg = FnPlannerCfg(P, n_cap, b_max, k, K, T_lo, T_hi, S, S_clear, reach_grid, w_vel,
+                                vel_frac, clear_margin, edge_blocks)
+        self.arm = arm_struct(arm)
+        h = C.c_void_p()
+        check(L.fn_planner_create(C.byref(self.cfg), C.byref(self.arm), C.byref(h)),
+              "fn_planner_create")
+        self.h = h
+        self.P = P
+        self._probs = (FnProblem * P)()
+        self._out = (FnRendezvous * P)()
+
+    def close(self):
+        if self.h:
+            lib().fn_planner_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stage(self, probs):
+        if len(probs) != self.P:
+            raise ValueError("need one problem per planner slot")
+        for i, p in enumerate(probs):
+            self._probs[i] = p
+
+    @staticmethod
+    def _stream(stream):
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return C.c_void_p(s.cuda_stream)
+
+    def reset(self, probs, stream=None):
+        self._stage(probs)
+        check(lib().fn_planner_reset(self.h, self._probs, self._stream(stream)), "fn_planner_reset")
+
+    def load_tree(self, p, states, t, parent, stream=None):
+        st = np.ascontiguousarray(states, np.float32)
+        t = np.ascontiguousarray(t, np.float32)
+        par = np.ascontiguousarray(parent, np.int32)
+        check(lib().fn_planner_load_tree(self.h, int(p), st.ctypes.data, t.ctypes.data,
+                                         par.ctypes.data, int(st.shape[0]), self._stream(stream)),
+              "fn_planner_load_tree")
+
+    def set_candidates(self, p, states, n_goal, T_req=None, v_rel=None, stream=None):
+        st = np.ascontiguousarray(states, np.float32)
+        tq = np.ascontiguousarray(np.zeros(0) if T_req is None else T_req, np.float32)
+        vr = np.ascontiguousarray(np.zeros(0) if v_rel is None else v_rel, np.float32)
+        check(lib().fn_planner_set_candidates(self.h, int(p), st.ctypes.data, int(st.shape[0]),
+                                              int(n_goal), tq.ctypes.data if n_goal else None,
+                                              vr.ctypes.data if n_goal else None,
+                                              self._stream(stream)), "fn_planner_set_candidates")
+
+    def iterate(self, probs, it=0, flags=0, stream=None):
+        self._stage(probs)
+        check(lib().fn_plan_iteration(self.h, self._probs, int(it), int(flags), self._out,
+                                      self._stream(stream)), "fn_plan_iteration")
+        return [rendezvous_dict(self._out[i]) for i in range(self.P)]
+
+    def capture(self, flags=0, stream=None):
+        check(lib().fn_planner_capture(self.h, int(flags), self._stream(stream)),
+              "fn_planner_capture")
+
+    def replay(self, probs, it=0, stream=None):
+        self._stage(probs)
+        check(lib().fn_plan_replay(self.h, self._probs, int(it), self._out, self._stream(stream)),
+              "fn_plan_replay")
+        return [rendezvous_dict(self._out[i]) for i in range(self.P)]
+
+    def get_tree(self, p, cap=None):
+        cap = self.cfg.n_cap if cap is None else cap
+        st = np.zeros((cap, 16), np.float32)
+        t = np.zeros(cap, np.float32)
+        par = np.zeros(cap, np.int32)
+        J = np.zeros(cap, np.float32)
+        nu = np.zeros(cap, np.float32)
+        n = C.c_int()
+        check(lib().fn_planner_get_tree(self.h, int(p), st.ctypes.data, t.ctypes.data,
+                                        par.ctypes.data, J.ctypes.data, nu.ctypes.data,
+                                        C.byref(n), int(cap)), "fn_planner_get_tree")
+        m = min(n.value, cap)
+        return dict(states=st[:m], t=t[:m], parent=par[:m], J=J[:m], nu=nu[:m], n=n.value)
+
+    def get_candidates(self, p, B):
+        st = np.zeros((B, 16), np.float32)
+        tq = np.zeros(B, np.float32)
+        vr = np.zeros(B, np.float32)
+        va = np.zeros(B, np.uint8)
+        check(lib().fn_planner_get_candidates(self.h, int(p), st.ctypes.data, tq.ctypes.data,
+                                              vr.ctypes.data, va.ctypes.data, int(B)),
+              "fn_planner_get_candidates")
+        return dict(states=st, T_req=tq, v_rel=vr, valid=va)
+
+    PHASES = ("schedule", "sample", "parents", "edges", "attach", "prune", "output")
+
+    def phase_ms(self):
+        ms = (C.c_float * 7)()
+        check(lib().fn_planner_phase_ms(self.h, ms), "fn_planner_phase_ms")
+        return dict(zip(self.PHASES, [float(x) for x in ms]))
+
+    def sample_count(self, reset=False):
+        c = C.c_ulonglong()
+        check(lib().fn_planner_sample_count(self.h, C.byref(c), int(bool(reset))),
+              "fn_planner_sample_count")
+        return int(c.value)

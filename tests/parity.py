@@ -68,3 +68,43 @@ def knn_mismatches(idx_gpu, d_gpu, idx_ref, d_ref):
         if not ok:
             bad.append(b)
     return bad
+
+
+def near_margin(orc, arm, s0, s1, grid, S):
+    """Is any admissible grid duration of this edge within the 1e-4 margin?"""
+    rr = orc.rho_batch(arm, np.repeat(s0[None], len(grid), 0), np.repeat(s1[None], len(grid), 0),
+                       grid.astype(np.float64), S)
+    m = np.maximum(rr[:, 0], rr[:, 1])
+    return bool(np.any(np.abs(m - 1) <= 1e-4) or np.any(np.abs(rr[:, 2] - 1) <= 1e-4))
+
+
+def compare_round(orc, arm, case, gpu_tree, ref_tree, ref_details, n_old, grid, S=16):
+    """Map new nodes to candidates by state and compare (parent, t)."""
+    cand = case["cand"]
+    g_new = {gpu_tree["states"][i].tobytes(): i for i in range(n_old, gpu_tree["n"])}
+    r_new = {ref_tree.states[i].tobytes(): i for i in range(n_old, ref_tree.n)}
+    bad = []
+    for b in range(cand.shape[0]):
+        key = cand[b].tobytes()
+        gi, ri = g_new.get(key), r_new.get(key)
+        if gi is None and ri is None:
+            continue
+        if gi is not None and ri is not None:
+            if gpu_tree["parent"][gi] == ref_tree.parent[ri] and \
+                    gpu_tree["t"][gi] == ref_tree.t[ri]:
+                continue
+        # disagreement: must be explained by a near-margin edge of this candidate
+        par = ref_details["parents"][b]
+        explained = False
+        for j, p in enumerate(par):
+            if p < 0:
+                continue
+            s0 = ref_tree.states[p] if p < n_old else None
+            if s0 is None:
+                continue
+            if near_margin(orc, arm, s0, cand[b], grid, S):
+                explained = True
+                break
+        if not explained:
+            bad.append(b)
+    return bad

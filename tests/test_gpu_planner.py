@@ -1,0 +1,245 @@
+"""Parity of the planner (fn_plan_iteration and friends) with one round of
+Algorithm 1 on the FP64 oracle (oracle/plan.py), through the C ABI.
+
+Candidates are drawn on the host by the oracle's own samplers and given to
+both sides (FN_PLAN_EXTERNAL), so the comparison covers parents, edge timing,
+clearance, attach, scoring, the incumbent and pruning.  A candidate may end
+up differently only where one of its edges sits within the 1e-4 limit margin
+in the oracle (the edge-timing parity rule)."""
+import numpy as np
+import pytest
+
+import oracle.plan as OP
+from paper_2609_22608_gb300 import synth
+from tests.parity import compare_round
+
+pytestmark = pytest.mark.gpu
+
+K_GRID, S_COLL = 32, 16
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2609_22608_gb300 import planner as pl
+    return pl
+
+
+def make_case(arm, orc, seed, N=300, n_goal_draw=512, n_free=96, obstacles=None):
+    toss = synth.random_toss(arm, seed)
+    root = synth.random_states(arm, 1, 5000 + seed)[0]
+    pr = synth.make_problem(toss, root=root)
+    states, parent, t = synth.random_tree(arm, N, seed, root=root)
+    st, Tq, vr, valid = orc.sample_goals(arm, pr, 100 + seed, 0, 0, 0, n_goal_draw)
+    gi = np.nonzero(valid)[0]
+    goal = st[gi].astype(np.float32)
+    free = orc.sample_uniform(arm, 200 + seed, 0, 0, 0, n_free, 0.5).astype(np.float32)
+    cand = np.concatenate([goal, free])
+    T_req = Tq[gi].astype(np.float32)
+    v_rel = vr[gi].astype(np.float32)
+    return dict(pr=pr, root=root, tree=(states, t, parent), cand=cand, n_goal=len(gi),
+                T_req=T_req, v_rel=v_rel, obstacles=obstacles)
+
+
+def run_pair(P, orc, arm, case, k=5, prune=False, obstacles=None):
+    grid = synth.duration_grid(K_GRID)
+    states, t, parent = case["tree"]
+    N = states.shape[0]
+    B = case["cand"].shape[0]
+    pl = P.Planner(arm, P=1, n_cap=N + B + 8, b_max=B, k=k, K=K_GRID, S=S_COLL, S_clear=8)
+    prob = P.problem_struct(case["pr"], B, case["n_goal"], root=case["root"], obstacles=obstacles)
+    pl.reset([prob])
+    pl.load_tree(0, states, t, parent)
+    pl.set_candidates(0, case["cand"], case["n_goal"], case["T_req"], case["v_rel"])
+    flags = P.FN_PLAN_EXTERNAL | (P.FN_PLAN_PRUNE if prune else 0)
+    out = pl.iterate([prob], 0, flags)[0]
+    gtree = pl.get_tree(0)
+    pl.close()
+    tree = OP.Tree(states, t, parent)
+    inc = dict(id=-1, J=-np.inf, t_best=float(np.float32(case["pr"]["t_fall"])))
+    rtree, rinc, det = OP.plan_round(arm, case["pr"], tree, case["cand"], case["n_goal"],
+                                     case["T_req"], case["v_rel"], inc, k, grid, S_COLL,
+                                     S_clear=8, obstacles=obstacles, prune=False)
+    return out, gtree, rtree, rinc, det, grid
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_plan_round_parity(P, orc, arm, seed):
+    case = make_case(arm, orc, seed)
+    assert case["n_goal"] >= 3
+    out, gtree, rtree, rinc, det, grid = run_pair(P, orc, arm, case)
+    N = case["tree"][0].shape[0]
+    bad = compare_round(orc, arm, case, gtree, rtree, det, N, grid)
+    assert not bad, f"candidates attached differently without a near-margin edge: {bad[:5]}"
+    assert gtree["n"] - N == out["n_added"]
+    assert abs((gtree["n"] - N) - (rtree.n - N)) <= 2
+    # incumbent
+    if rinc["id"] >= 0:
+        assert out["incumbent"] >= 0
+        assert out["J"] == pytest.approx(rinc["J"], rel=1e-4, abs=1e-4)
+        assert out["t_best"] == pytest.approx(rinc["t_best"], rel=1e-6)
+        seg = OP.first_segment(rtree, rinc)
+        assert np.array_equal(out["q_g"], seg[0][:7])
+    else:
+        assert out["incumbent"] == -1
+    # tree invariants: parents precede children, time-to-come adds up, J only on goals
+    par = gtree["parent"]
+    assert par[0] == -1 and np.all(par[1:] < np.arange(1, gtree["n"]))
+
+
+def test_plan_round_with_obstacles(P, orc, arm):
+    obs = synth.obstacles(5, 3)
+    case = make_case(arm, orc, 2, N=200, n_free=64)
+    out, gtree, rtree, rinc, det, grid = run_pair(P, orc, arm, case, obstacles=obs)
+    N = case["tree"][0].shape[0]
+    bad = compare_round(orc, arm, case, gtree, rtree, det, N, grid)
+    assert not bad
+
+
+def test_plan_prune_parity(P, orc, arm):
+    case = make_case(arm, orc, 3, N=400)
+    grid = synth.duration_grid(K_GRID)
+    states, t, parent = case["tree"]
+    N, B = states.shape[0], case["cand"].shape[0]
+    pl = P.Planner(arm, P=1, n_cap=N + B + 8, b_max=B, k=5, K=K_GRID, S=S_COLL)
+    prob = P.problem_struct(case["pr"], B, case["n_goal"], root=case["root"])
+    pl.reset([prob])
+    pl.load_tree(0, states, t, parent)
+    pl.set_candidates(0, case["cand"], case["n_goal"], case["T_req"], case["v_rel"])
+    pl.iterate([prob], 0, P.FN_PLAN_EXTERNAL)
+    before = pl.get_tree(0)
+    # prune the tree as it stands: an iteration with no candidates and the prune flag
+    prob0 = P.problem_struct(case["pr"], 0, 0, root=case["root"])
+    out = pl.iterate([prob0], 1, P.FN_PLAN_EXTERNAL | P.FN_PLAN_PRUNE)[0]
+    after = pl.get_tree(0)
+    pl.close()
+    tree = OP.Tree(before["states"], before["t"], before["parent"], before["J"], before["nu"])
+    inc = dict(id=out["incumbent"], J=out["J"], t_best=out["t_best"])
+    # the incumbent before pruning: the node whose J equals the reported score
+    if out["incumbent"] >= 0:
+        ids = np.nonzero(np.isclose(before["J"], out["J"], rtol=0, atol=0))[0]
+        inc["id"] = int(ids[0])
+    else:
+        inc["id"] = -1
+    rt, rinc, alive = OP.prune_tree(arm, case["pr"], tree, inc, 256)
+    # compare kept sets by state; disagreements only near the T_n <= t_best boundary
+    g_keys = {after["states"][i].tobytes() for i in range(after["n"])}
+    r_keys = {rt.states[i].tobytes() for i in range(rt.n)}
+    diff = g_keys ^ r_keys
+    for key in diff:
+        i = next(j for j in range(tree.n) if tree.states[j].tobytes() == key)
+        g, Tn = orc.reach_time(arm, case["pr"], tree.states[i, :7].astype(float), float(tree.t[i]))
+        assert g >= 0 and abs(Tn - inc["t_best"]) < 5e-3, (i, g, Tn, inc["t_best"])
+    assert len(diff) <= max(2, 0.01 * tree.n)
+
+
+def test_sampler_uniform_matches_oracle(P, orc, arm):
+    """Free candidates: same Philox counters, same formula -> equal to FP32
+    rounding."""
+    toss = synth.random_toss(arm, 4)
+    pr = synth.make_problem(toss, root=synth.random_states(arm, 1, 9)[0])
+    B, G = 600, 0
+    pl = P.Planner(arm, P=1, n_cap=64, b_max=B, k=1, K=8, S=8)
+    prob = P.problem_struct(pr, B, G, seed=1234)
+    pl.reset([prob])
+    pl.iterate([prob], 3, 0)
+    c = pl.get_candidates(0, B)
+    pl.close()
+    ref = orc.sample_uniform(arm, 1234, 3, 0, 0, B, 0.5)
+    assert np.allclose(c["states"], ref, rtol=1e-6, atol=1e-6)
+
+
+def test_sampler_goal_chart_on_manifold(P, orc, arm):
+    """Goal candidates decoded on the GPU satisfy Def. 2 (checked in FP64)
+    and agree with the oracle's decoding where both accept."""
+    toss = synth.random_toss(arm, 5)
+    pr = synth.make_problem(toss, root=synth.random_states(arm, 1, 10)[0])
+    B = 4096
+    pl = P.Planner(arm, P=1, n_cap=64, b_max=B, k=1, K=8, S=8)
+    prob = P.problem_struct(pr, B, B, seed=77)
+    pl.reset([prob])
+    pl.iterate([prob], 2, 0)
+    c = pl.get_candidates(0, B)
+    pl.close()
+    st, Tq, vr, valid = orc.sample_goals(arm, pr, 77, 2, 0, 0, B)
+    gv = c["valid"] == 1
+    assert gv.sum() >= 20
+    # acceptance agrees on all but a few near-tolerance samples
+    assert np.mean(gv != (valid == 1)) < 0.01
+    both = gv & (valid == 1)
+    assert np.allclose(c["T_req"][both], Tq[both], rtol=1e-6)
+    assert np.abs(c["states"][both, :7] - st[both, :7]).max() < 2e-3
+    g = np.asarray(pr["g"])
+    for i in np.nonzero(gv)[0]:
+        q, qd, T = c["states"][i, :7].astype(float), c["states"][i, 8:15].astype(float), float(c["T_req"][i])
+        x = pr["x0"] + pr["v0"] * T + 0.5 * g * T * T
+        xd = pr["v0"] + g * T
+        b0, b1 = orc.blade(arm, q)
+        u = np.clip((x - b0) @ (b1 - b0) / ((b1 - b0) @ (b1 - b0)), 0, 1)
+        assert np.linalg.norm(b0 + u * (b1 - b0) - x) < 1e-3
+        v6 = orc.jacobian_point(arm, q, x) @ qd
+        vrel = v6[:3] - xd
+        assert np.linalg.norm(vrel) >= pr["v_min"] - 1e-3
+        R, _ = orc.fk(arm, q)
+        nb = R[7] @ arm["blade_normal"].astype(float)
+        assert nb @ vrel / np.linalg.norm(vrel) >= pr["a_min"] - 3e-3
+        assert np.all(q >= arm["q_lo"] - 1e-6) and np.all(q <= arm["q_hi"] + 1e-6)
+
+
+def test_graph_replay_matches_iteration(P, orc, arm):
+    import torch
+    case = make_case(arm, orc, 6, N=500)
+    states, t, parent = case["tree"]
+    N = states.shape[0]
+    B = 512
+    res = []
+    for mode in ("iterate", "graph"):
+        pl = P.Planner(arm, P=2, n_cap=N + 4 * B, b_max=B, k=8, K=64, S=32)
+        probs = [P.problem_struct(case["pr"], B, B // 2, root=case["root"], seed=11 + i)
+                 for i in range(2)]
+        pl.reset(probs)
+        for p in range(2):
+            pl.load_tree(p, states, t, parent)
+        s = torch.cuda.Stream()
+        outs = []
+        if mode == "graph":
+            pl.capture(0, stream=s)
+            for it in range(3):
+                outs.append(pl.replay(probs, it, stream=s))
+        else:
+            for it in range(3):
+                outs.append(pl.iterate(probs, it, 0, stream=s))
+        res.append((outs, [pl.get_tree(p) for p in range(2)]))
+        pl.close()
+    (o1, t1), (o2, t2) = res
+    for a, b in zip(o1, o2):
+        for x, y in zip(a, b):
+            assert x["n_nodes"] == y["n_nodes"] and x["incumbent"] == y["incumbent"]
+    for x, y in zip(t1, t2):
+        assert np.array_equal(x["states"], y["states"]) and np.array_equal(x["parent"], y["parent"])
+
+
+def test_batched_uneven_problems(P, orc, arm):
+    """Three problems of different tree and batch sizes in one planner match
+    three single-problem rounds on the oracle."""
+    cases = [make_case(arm, orc, 10 + i, N=n, n_free=nf) for i, (n, nf) in
+             enumerate([(50, 40), (700, 150), (260, 8)])]
+    grid = synth.duration_grid(K_GRID)
+    Bmax = max(c["cand"].shape[0] for c in cases)
+    Nmax = max(c["tree"][0].shape[0] for c in cases)
+    pl = P.Planner(arm, P=3, n_cap=Nmax + Bmax + 8, b_max=Bmax, k=5, K=K_GRID, S=S_COLL)
+    probs = [P.problem_struct(c["pr"], c["cand"].shape[0], c["n_goal"], root=c["root"]) for c in cases]
+    pl.reset(probs)
+    for p, c in enumerate(cases):
+        pl.load_tree(p, *c["tree"])
+        pl.set_candidates(p, c["cand"], c["n_goal"], c["T_req"], c["v_rel"])
+    outs = pl.iterate(probs, 0, P.FN_PLAN_EXTERNAL)
+    for p, c in enumerate(cases):
+        g = pl.get_tree(p)
+        st, t, par = c["tree"]
+        inc = dict(id=-1, J=-np.inf, t_best=float(np.float32(c["pr"]["t_fall"])))
+        rtree, rinc, det = OP.plan_round(arm, c["pr"], OP.Tree(st, t, par), c["cand"], c["n_goal"],
+                                         c["T_req"], c["v_rel"], inc, 5, grid, S_COLL)
+        assert not compare_round(orc, arm, c, g, rtree, det, st.shape[0], grid)
+        if rinc["id"] >= 0:
+            assert outs[p]["J"] == pytest.approx(rinc["J"], rel=1e-4, abs=1e-4)
+    pl.close()
