@@ -108,3 +108,35 @@ def compare_round(orc, arm, case, gpu_tree, ref_tree, ref_details, n_old, grid, 
         if not explained:
             bad.append(b)
     return bad
+
+
+def arm_limits_moved(arm, delta):
+    """Copy of `arm` with every joint box widened by `delta` (narrowed if < 0)."""
+    a = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in arm.items()}
+    a["q_lo"] = (arm["q_lo"].astype(np.float64) - delta).astype(np.float32)
+    a["q_hi"] = (arm["q_hi"].astype(np.float64) + delta).astype(np.float32)
+    return a
+
+
+RHO_REL = 2e-5
+
+
+def rho_matches(orc, arm, s0, s1, T, S, rho_gpu, rho_ref, delta=4e-6):
+    """Per-edge check of (rho_tau, rho_P, rho_v) at duration T[e].
+
+    rho_tau and rho_P compare within RHO_REL (relative, absolute below 1).
+    rho_v divides by the sqrt taper, which is ill-conditioned next to a joint
+    limit (a one-ulp position change moves it by percents): the GPU value
+    must lie between the oracle's rho_v with the joint boxes widened and
+    narrowed by `delta` radians, widened by RHO_REL.  Returns the indices of
+    edges that fail."""
+    rho_gpu = np.asarray(rho_gpu, np.float64)
+    bad = []
+    tp_ok = np.all(np.abs(rho_gpu[:, :2] - rho_ref[:, :2]) <= RHO_REL * np.maximum(1, np.abs(rho_ref[:, :2])), axis=1)
+    lo = orc.rho_batch(arm_limits_moved(arm, delta), s0, s1, T, S)[:, 2]
+    hi = orc.rho_batch(arm_limits_moved(arm, -delta), s0, s1, T, S)[:, 2]
+    v = rho_gpu[:, 2]
+    v_ok = (v >= lo * (1 - RHO_REL) - 1e-12) & ((v <= hi * (1 + RHO_REL) + 1e-12) | np.isinf(hi))
+    for e in np.nonzero(~(tp_ok & v_ok))[0]:
+        bad.append(int(e))
+    return bad
