@@ -202,6 +202,8 @@ def run_ours(args, rank, world):
         pl.reset([prob], stream=stream)
         pl.load_tree(0, w["tree"], w["t_node"], w["parent"], stream=stream)
 
+    reset_tree()
+    tuned = pl.autotune([prob], 0, 0, reps=3, stream=stream)   # schedule autotuner
     for i in range(args.warmup):
         reset_tree()
         pl.iterate([prob], i, 0, stream=stream)
@@ -274,6 +276,7 @@ def run_ours(args, rank, world):
         "config": {"workload": WORKLOAD, "tree": N_TREE, "batch": B_CAND, "k": K_PAR,
                    "K": K_GRID, "S": S_COLL, "edges_per_step": edges,
                    "nodes_added_mean": float(np.mean(added)),
+                   "edge_variant": tuned[0], "edge_variant_ms": tuned[1],
                    "parallelism": f"replicas x{world}", "l2": "flushed between timed steps"},
         "phases_ms": phases,
         "clocks": clk.summary(),

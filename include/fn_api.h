@@ -343,6 +343,18 @@ fn_status fn_planner_capture(fn_planner_t* pl, unsigned flags, void* stream);
 fn_status fn_plan_replay(fn_planner_t* pl, const fn_problem_t* probs, int iter,
                          fn_rendezvous_t* out, void* stream);
 
+/* Schedule autotuner of the planner (the work pattern of an iteration is
+ * data dependent, so variants are timed on the caller's own problems): runs
+ * the iteration's sampling and parent search once, then times every compiled
+ * register-budget variant of the persistent edge kernel on that edge batch
+ * (`reps` runs each after a warm-up) and keeps the fastest for this planner
+ * and later planners of the same shape.  The trees are not modified.
+ * chosen: host (may be NULL); variant_ms: host [3] (may be NULL).
+ * Synchronous. */
+fn_status fn_planner_autotune(fn_planner_t* pl, const fn_problem_t* probs, int iter,
+                              unsigned flags, int reps, int* chosen, float* variant_ms,
+                              void* stream);
+
 /* Durations in ms of the last fn_plan_iteration's phases, from CUDA events
  * recorded on its stream: [0] schedule, [1] sample, [2] parents (kNN),
  * [3] edges (timing + clearance), [4] attach + score, [5] prune, [6] output.

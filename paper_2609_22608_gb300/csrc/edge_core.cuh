@@ -42,41 +42,6 @@ __device__ __forceinline__ bool stage_rows(const float* row0, const float* row1,
   return __all_sync(0xffffffffu, pad || isfinite(v));
 }
 
-// All S samples of duration T with lanes = samples.  exit_early stops at the
-// first violating batch.  Returns true iff every sample passes; rt/rp are the
-// warp maxima over the evaluated samples.
-__device__ __forceinline__ bool verify_duration(const ArmK& A, const float* es, CubicLane cb,
-                                                float T, int S, bool exit_early, float& rt,
-                                                float& rp, unsigned& nsamp) {
-  const int lane = threadIdx.x & 31;
-  {
-    Cubic c;
-    cubic_coef_sh<true>(es, T, c);
-    cb.store(c);
-  }
-  float mt = 0.f, mp = 0.f;
-  bool bad = false;
-  for (int s0 = 0; s0 < S; s0 += 32) {
-    const int s = s0 + lane;
-    bool viol = false;
-    if (s < S) {
-      float a, b;
-      sample_ratios(A, cb, sample_u(s, S), a, b);
-      mt = fmaxf(mt, a);
-      mp = fmaxf(mp, b);
-      viol = !(a <= 1.f && b <= 1.f);
-    }
-    nsamp += min(32, S - s0);
-    if (__any_sync(0xffffffffu, viol)) {
-      bad = true;
-      if (exit_early) break;
-    }
-  }
-  rt = warp_max(mt);
-  rp = warp_max(mp);
-  return !bad;
-}
-
 __device__ __forceinline__ float warp_rho_v(const ArmK& A, const float* es, float T) {
   const int lane = threadIdx.x & 31;
   float r = 0.f;
@@ -90,37 +55,107 @@ __device__ __forceinline__ float warp_rho_v(const ArmK& A, const float* es, floa
   return warp_max(r);
 }
 
-// first feasible grid index in [0, Kadm)
-__device__ __forceinline__ int first_feasible(const ArmK& A, const float* es, CubicLane cb,
-                                              const float* sT, int Kadm, int S, float& rt,
-                                              float& rp, unsigned& nsamp) {
+// Edge scan with a single torque-evaluation call site (the RNEA body is
+// ~1.2k instructions; inlining it at several call sites overflowed the
+// instruction cache).  Each pass evaluates at most one sample per lane:
+//   PROBE_LO : lanes = grid durations base+lane, sample u = 0
+//   PROBE_HI : the lanes whose u = 0 passed, sample u = 1
+//   VERIFY   : lanes = samples (s0 + lane) of one duration, compensated
+//              coefficients, until a violating batch or all S samples pass
+// Grid mode (fixed = false): returns the first feasible index in [0, Kadm).
+// Fixed mode: one duration Tfix is verified (all S samples when exact,
+// else up to the first violating batch); returns 0 if it passes, else -1.
+__device__ __forceinline__ int edge_scan(const ArmK& A, const float* es, CubicLane cb,
+                                         LaneWrench wr, const float* sT, int Kadm, int S,
+                                         bool fixed, float Tfix, bool exact, float& rt, float& rp,
+                                         unsigned& nsamp) {
+  enum { PROBE_LO = 0, PROBE_HI = 1, VERIFY = 2 };
   const int lane = threadIdx.x & 31;
-  for (int base = 0; base < Kadm; base += 32) {
-    const int k = base + lane;
-    bool first_end = false, pass = false;
-    if (k < Kadm) {
-      {
-        Cubic c;
-        cubic_coef_sh<false>(es, sT[k], c);
-        cb.store(c);
-      }
-      float a, b;
-      sample_ratios(A, cb, 0.f, a, b);
-      first_end = (a <= 1.f && b <= 1.f);
-      if (first_end) {
-        sample_ratios(A, cb, 1.f, a, b);
-        pass = (a <= 1.f && b <= 1.f);
-      }
-    }
-    nsamp += min(32, Kadm - base) + __popc(__ballot_sync(0xffffffffu, first_end));
-    unsigned mask = __ballot_sync(0xffffffffu, pass);
-    while (mask) {
-      const int kk = base + __ffs(mask) - 1;
-      if (verify_duration(A, es, cb, sT[kk], S, true, rt, rp, nsamp)) return kk;
-      mask &= mask - 1;
-    }
+  int mode = PROBE_LO, base = 0, kk = 0, s0 = 0;
+  unsigned cand = 0u;   // PROBE_HI: lanes to evaluate; VERIFY: durations left in the chunk
+  float mt = 0.f, mp = 0.f;
+  bool bad = false;
+  if (fixed) {
+    mode = VERIFY;
+    Cubic c;
+    cubic_coef_sh<true>(es, Tfix, c);
+    cb.store(c);
+  } else {
+    if (Kadm <= 0) return -1;
+    Cubic c;
+    if (lane < Kadm) cubic_coef_sh<false>(es, sT[lane], c);
+    cb.store(c);
   }
-  return -1;
+  for (;;) {
+    bool active;
+    float u;
+    if (mode == VERIFY) {
+      active = s0 + lane < S;
+      u = sample_u(s0 + lane, S);
+    } else {
+      active = mode == PROBE_LO ? (base + lane < Kadm) : ((cand >> lane) & 1u);
+      u = mode == PROBE_LO ? 0.f : 1.f;
+    }
+    float a = 0.f, b = 0.f;
+    if (active) sample_ratios(A, cb, u, a, b, wr);   // the single call site
+    const bool pass = active && a <= 1.f && b <= 1.f;
+    const unsigned act = __ballot_sync(0xffffffffu, active);
+    const unsigned ok = __ballot_sync(0xffffffffu, pass);
+    nsamp += __popc(act);
+    int next_dur = -1;  // duration to verify next, if any
+    if (mode == PROBE_LO) {
+      if (ok) {
+        cand = ok;
+        mode = PROBE_HI;
+        continue;
+      }
+    } else if (mode == PROBE_HI) {
+      cand = ok;                       // durations whose two ends pass
+      if (cand) next_dur = base + __ffs(cand) - 1;
+    } else {
+      if (active) { mt = fmaxf(mt, a); mp = fmaxf(mp, b); }
+      const bool viol = (act & ~ok) != 0u;
+      if (fixed) {
+        bad = bad || viol;
+        if ((!viol || exact) && s0 + 32 < S) {
+          s0 += 32;
+          continue;
+        }
+        rt = warp_max(mt);
+        rp = warp_max(mp);
+        return bad ? -1 : 0;
+      }
+      if (viol) {                      // kk is infeasible
+        cand &= cand - 1;
+        if (cand) next_dur = base + __ffs(cand) - 1;
+      } else if (s0 + 32 < S) {
+        s0 += 32;
+        continue;
+      } else {
+        rt = warp_max(mt);
+        rp = warp_max(mp);
+        return kk;
+      }
+    }
+    if (next_dur >= 0) {               // (re)start VERIFY on the next survivor
+      kk = next_dur;
+      s0 = 0;
+      mt = mp = 0.f;
+      mode = VERIFY;
+      Cubic c;
+      cubic_coef_sh<true>(es, sT[kk], c);
+      cb.store(c);
+      continue;
+    }
+    // nothing left in this chunk of 32 durations: probe the next one
+    base += 32;
+    if (base >= Kadm) return -1;
+    mode = PROBE_LO;
+    cand = 0u;
+    Cubic c;
+    if (base + lane < Kadm) cubic_coef_sh<false>(es, sT[base + lane], c);
+    cb.store(c);
+  }
 }
 
 // admissible prefix of the ascending grid: #{k : T_k <= cap}
@@ -140,7 +175,7 @@ __device__ __forceinline__ int grid_prefix(const float* sT, int K, float cap) {
 // exact = false lets a fixed-duration check stop at the first violating batch
 // (its ratios are then lower bounds; ok is exact either way).
 __device__ __forceinline__ EdgeResult time_edge(const ArmK& A, const float* es, CubicLane cb,
-                                                bool finite, bool fixed, float Tp,
+                                                LaneWrench wr, bool finite, bool fixed, float Tp,
                                                 const float* sT, int K, int S, bool exact,
                                                 unsigned& nsamp) {
   EdgeResult r;
@@ -152,7 +187,7 @@ __device__ __forceinline__ EdgeResult time_edge(const ArmK& A, const float* es, 
       r.T = NAN;
       return r;
     }
-    const bool pass = verify_duration(A, es, cb, Tp, S, !exact, r.rt, r.rp, nsamp);
+    const bool pass = edge_scan(A, es, cb, wr, sT, 0, S, true, Tp, exact, r.rt, r.rp, nsamp) == 0;
     if (exact || pass) r.rv = warp_rho_v(A, es, Tp);
     r.k = pass ? 0 : -1;
     r.T = Tp;
@@ -165,7 +200,7 @@ __device__ __forceinline__ EdgeResult time_edge(const ArmK& A, const float* es, 
     return r;
   }
   const int Kadm = grid_prefix(sT, K, Tp);
-  r.k = first_feasible(A, es, cb, sT, Kadm, S, r.rt, r.rp, nsamp);
+  r.k = edge_scan(A, es, cb, wr, sT, Kadm, S, false, 0.f, false, r.rt, r.rp, nsamp);
   if (r.k >= 0) {
     r.T = sT[r.k];
     r.rv = warp_rho_v(A, es, r.T);

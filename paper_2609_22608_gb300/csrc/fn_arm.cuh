@@ -195,11 +195,40 @@ __device__ __forceinline__ void cubic_eval(const CubicLane& c, int j, float u, f
 // Each tau_j is handed to `sink(j, tau_j, qd_j)` as soon as the inward pass
 // produces it, so no torque array is kept.
 // ---------------------------------------------------------------------------
-template <class Coef, class Sink>
-__device__ __forceinline__ void torque_at(const ArmK& A, const Coef& c, float u, Sink&& sink) {
+// Link wrenches of the outward pass, kept until the inward pass.  RegWrench
+// holds them in registers; LaneWrench in a per-lane column of shared memory
+// (42 words x 32 lanes per warp), which frees ~42 registers for occupancy.
+struct RegWrench {
+  float Fx[7], Fy[7], Fz[7], Nx[7], Ny[7], Nz[7];
+  __device__ __forceinline__ void put(int j, float fx, float fy, float fz, float nx, float ny,
+                                      float nz) {
+    Fx[j] = fx; Fy[j] = fy; Fz[j] = fz; Nx[j] = nx; Ny[j] = ny; Nz[j] = nz;
+  }
+  __device__ __forceinline__ void get(int j, float& fx, float& fy, float& fz, float& nx,
+                                      float& ny, float& nz) const {
+    fx = Fx[j]; fy = Fy[j]; fz = Fz[j]; nx = Nx[j]; ny = Ny[j]; nz = Nz[j];
+  }
+};
+#define FN_WRENCH_WORDS 42
+struct LaneWrench {
+  float* p;  // &buf[lane] of a [FN_WRENCH_WORDS][32] per-warp buffer
+  __device__ __forceinline__ void put(int j, float fx, float fy, float fz, float nx, float ny,
+                                      float nz) const {
+    p[32 * (6 * j + 0)] = fx; p[32 * (6 * j + 1)] = fy; p[32 * (6 * j + 2)] = fz;
+    p[32 * (6 * j + 3)] = nx; p[32 * (6 * j + 4)] = ny; p[32 * (6 * j + 5)] = nz;
+  }
+  __device__ __forceinline__ void get(int j, float& fx, float& fy, float& fz, float& nx,
+                                      float& ny, float& nz) const {
+    fx = p[32 * (6 * j + 0)]; fy = p[32 * (6 * j + 1)]; fz = p[32 * (6 * j + 2)];
+    nx = p[32 * (6 * j + 3)]; ny = p[32 * (6 * j + 4)]; nz = p[32 * (6 * j + 5)];
+  }
+};
+
+template <class Coef, class Sink, class Wr = RegWrench>
+__device__ __forceinline__ void torque_at(const ArmK& A, const Coef& c, float u, Sink&& sink,
+                                          Wr W = Wr()) {
   float qd[7], ex[7];
   float ct[7], st[7];
-  float Fx[7], Fy[7], Fz[7], Nx[7], Ny[7], Nz[7];
   float wx = 0.f, wy = 0.f, wz = 0.f;
   float dwx = 0.f, dwy = 0.f, dwz = 0.f;
   float ax = A.g0x, ay = A.g0y, az = A.g0z;
@@ -255,11 +284,9 @@ __device__ __forceinline__ void torque_at(const ArmK& A, const Coef& c, float u,
     const float vcy = (dwz * cx - dwx * cz) + (wz * wcx - wx * wcz) + ay;
     const float vcz = (dwx * cy - dwy * cx) + (wx * wcy - wy * wcx) + az;
     const float m = A.m[j];
-    Fx[j] = m * vcx; Fy[j] = m * vcy; Fz[j] = m * vcz;
     const float Iwx = A.Ix[j] * wx, Iwy = A.Iy[j] * wy, Iwz = A.Iz[j] * wz;
-    Nx[j] = fmaf(A.Ix[j], dwx, wy * Iwz - wz * Iwy);
-    Ny[j] = fmaf(A.Iy[j], dwy, wz * Iwx - wx * Iwz);
-    Nz[j] = fmaf(A.Iz[j], dwz, wx * Iwy - wy * Iwx);
+    W.put(j, m * vcx, m * vcy, m * vcz, fmaf(A.Ix[j], dwx, wy * Iwz - wz * Iwy),
+          fmaf(A.Iy[j], dwy, wz * Iwx - wx * Iwz), fmaf(A.Iz[j], dwz, wx * Iwy - wy * Iwx));
   }
   float fx = 0.f, fy = 0.f, fz = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
 #pragma unroll
@@ -277,25 +304,29 @@ __device__ __forceinline__ void torque_at(const ArmK& A, const Coef& c, float u,
       pRx = py * Rfz - pz * Rfy; pRy = pz * Rfx - px * Rfz; pRz = px * Rfy - py * Rfx;
     }
     const float cx = A.cx[j], cy = A.cy[j], cz = A.cz[j];
-    const float cFx = cy * Fz[j] - cz * Fy[j], cFy = cz * Fx[j] - cx * Fz[j],
-                cFz = cx * Fy[j] - cy * Fx[j];
-    fx = Fx[j] + Rfx; fy = Fy[j] + Rfy; fz = Fz[j] + Rfz;
-    nx = Nx[j] + Rnx + cFx + pRx;
-    ny = Ny[j] + Rny + cFy + pRy;
-    nz = Nz[j] + Rnz + cFz + pRz;
+    float Fx, Fy, Fz, Nx, Ny, Nz;
+    W.get(j, Fx, Fy, Fz, Nx, Ny, Nz);
+    const float cFx = cy * Fz - cz * Fy, cFy = cz * Fx - cx * Fz, cFz = cx * Fy - cy * Fx;
+    fx = Fx + Rfx; fy = Fy + Rfy; fz = Fz + Rfz;
+    nx = Nx + Rnx + cFx + pRx;
+    ny = Ny + Rny + cFy + pRy;
+    nz = Nz + Rnz + cFz + pRz;
     sink(j, nz + ex[j], qd[j]);
   }
 }
 
 // ratios of one sample at normalised time u: rho_tau(s) and rho_P(s)
-template <class Coef>
+template <class Coef, class Wr = RegWrench>
 __device__ __forceinline__ void sample_ratios(const ArmK& A, const Coef& c, float u, float& rt,
-                                              float& rp) {
+                                              float& rp, Wr W = Wr()) {
   float r = 0.f, pw = 0.f;
-  torque_at(A, c, u, [&](int j, float tau, float v) {
-    r = fmaxf(r, fabsf(tau) * A.inv_tau[j]);
-    pw = fmaf(tau, v, pw);
-  });
+  torque_at(
+      A, c, u,
+      [&](int j, float tau, float v) {
+        r = fmaxf(r, fabsf(tau) * A.inv_tau[j]);
+        pw = fmaf(tau, v, pw);
+      },
+      W);
   rt = r;
   rp = fabsf(pw) * A.inv_w;
 }

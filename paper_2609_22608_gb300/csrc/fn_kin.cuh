@@ -273,23 +273,27 @@ __device__ __forceinline__ void flight(const fn_problem_t& P, float t, float* x,
   }
 }
 
-// Goal chart phi(z) -> (q_g, qd_g, T_req, |v_rel|); false where undefined.
-// z0: arrival T in [t_enter, t_fall] and contact x(T + t_offset);
-// z1, z2: approach direction in the cone of half-angle acos(a_min) about
-//   -xdot (polar acos(1 - z1 (1 - a_min)), azimuth 2 pi z2);
-// z8: closing speed 0.5 + 1.5 z8 -> v_b; undefined if |v_b - xdot| < v_min;
-// z5, z4: cutting direction = v_rel direction tilted by z5 acos(a_min)
-//   towards roll 2 pi z4; z3: blade-axis spin 2 pi z3 about it;
-// z7: contact at z7 blade_len along the edge; z6: q7 in its range;
-// q_g by ik_solve (up to three starts), qd_g = J^T (J J^T)^-1 [v_b; 0] at
-// the contact point, undefined if any |qd_g,j| exceeds the taper.
-__device__ __forceinline__ bool goal_chart(const ArmK& A, const fn_problem_t& P, const float* z,
-                                           float* q, float* qd, float& T, float& vrel) {
-  T = fmaf(z[0], P.t_fall - P.t_enter, P.t_enter);
-  float c[3], xd[3];
-  flight(P, T + P.t_offset, c, xd);
+// Goal chart phi(z), decoding part: arrival T, contact c = x(T + t_offset),
+// blade velocity v_b, |v_rel| and the end-effector target pose (R_g, p_g).
+// Returns false where phi is undefined before the IK (|v_rel| < v_min).
+//   z0: T in [t_enter, t_fall];  z1, z2: approach direction in the cone of
+//   half-angle acos(a_min) about -xdot (polar acos(1 - z1 (1 - a_min)),
+//   azimuth 2 pi z2);  z8: closing speed 0.5 + 1.5 z8 -> v_b;
+//   z5, z4: cutting direction = v_rel direction tilted by z5 acos(a_min)
+//   towards roll 2 pi z4;  z3: blade-axis spin 2 pi z3 about it;
+//   z7: contact at z7 blade_len along the edge;  z6: q7 in its range.
+struct ChartPose {
+  float T, vrel, q7;
+  float c[3], vb[3], Rg[9], pg[3];
+};
+
+__device__ __forceinline__ bool chart_pose(const ArmK& A, const fn_problem_t& P, const float* z,
+                                           ChartPose& o) {
+  o.T = fmaf(z[0], P.t_fall - P.t_enter, P.t_enter);
+  float xd[3];
+  flight(P, o.T + P.t_offset, o.c, xd);
   const float sp = norm3(xd);
-  vrel = 0.f;
+  o.vrel = 0.f;
   if (!(sp > 0.f)) return false;
   const float u[3] = {-xd[0] / sp, -xd[1] / sp, -xd[2] / sp};
   float e1[3], e2[3];
@@ -298,17 +302,17 @@ __device__ __forceinline__ bool goal_chart(const ArmK& A, const fn_problem_t& P,
   const float st = sqrtf(fmaxf(0.f, fmaf(-ct, ct, 1.f)));
   float sph, cph;
   sincospif(2.f * z[2], &sph, &cph);
-  float vb[3], vr[3];
+  float vr[3];
   const float s = fmaf(1.5f, z[8], 0.5f);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const float d = fmaf(ct, u[k], st * fmaf(cph, e1[k], sph * e2[k]));
-    vb[k] = s * d;
-    vr[k] = vb[k] - xd[k];
+    o.vb[k] = s * d;
+    vr[k] = o.vb[k] - xd[k];
   }
-  vrel = norm3(vr);
-  if (!(vrel >= P.v_min)) return false;
-  const float nh[3] = {vr[0] / vrel, vr[1] / vrel, vr[2] / vrel};
+  o.vrel = norm3(vr);
+  if (!(o.vrel >= P.v_min)) return false;
+  const float nh[3] = {vr[0] / o.vrel, vr[1] / o.vrel, vr[2] / o.vrel};
   float m1[3], m2[3];
   complete_basis(nh, m1, m2);
   const float beta = z[5] * acosf(P.a_min);
@@ -330,33 +334,35 @@ __device__ __forceinline__ bool goal_chart(const ArmK& A, const fn_problem_t& P,
   const float en[3] = {A.bnm[0], A.bnm[1], A.bnm[2]};
   float ez[3];
   cross3(ea, en, ez);
-  float Rg[9];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) Rg[3 * i + j] = fmaf(bax[i], ea[j], fmaf(nb[i], en[j], bz[i] * ez[j]));
+    for (int j = 0; j < 3; ++j) o.Rg[3 * i + j] = fmaf(bax[i], ea[j], fmaf(nb[i], en[j], bz[i] * ez[j]));
   float pe[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) pe[k] = fmaf(z[7] * A.blen, A.bax[k], A.bb[k]);
-  float pg[3];
 #pragma unroll
   for (int r = 0; r < 3; ++r)
-    pg[r] = c[r] - fmaf(Rg[3 * r], pe[0], fmaf(Rg[3 * r + 1], pe[1], Rg[3 * r + 2] * pe[2]));
-  const float q7 = fmaf(z[6], A.q_hi[6] - A.q_lo[6], A.q_lo[6]);
-  bool found = false;
-  for (int stt = 0; stt < FN_IK_STARTS && !found; ++stt) found = ik_solve(A, Rg, pg, q7, stt, q);
-  if (!found) return false;
+    o.pg[r] = o.c[r] - fmaf(o.Rg[3 * r], pe[0], fmaf(o.Rg[3 * r + 1], pe[1], o.Rg[3 * r + 2] * pe[2]));
+  o.q7 = fmaf(z[6], A.q_hi[6] - A.q_lo[6], A.q_lo[6]);
+  return true;
+}
+
+// Goal chart phi(z), velocity part after the IK: the box check, then
+// qd_g = J^T (J J^T)^-1 [v_b; 0] at the contact point (all 7 joints),
+// undefined if any |qd_g,j| exceeds the taper.
+__device__ __forceinline__ bool chart_velocity(const ArmK& A, const ChartPose& o, const float* q,
+                                               float* qd) {
 #pragma unroll
   for (int j = 0; j < 7; ++j)
     if (!(q[j] >= A.q_lo[j] && q[j] <= A.q_hi[j])) return false;
-  // terminal velocity: J^+ [v_b; 0] at the contact point (all 7 joints)
   Axes ax;
   float Ree[9], oee[3];
   fk_axes(A, q, ax, Ree, oee);
   float J[6][7];
 #pragma unroll
   for (int m = 0; m < 7; ++m) {
-    const float r[3] = {c[0] - ax.o[m][0], c[1] - ax.o[m][1], c[2] - ax.o[m][2]};
+    const float r[3] = {o.c[0] - ax.o[m][0], o.c[1] - ax.o[m][1], o.c[2] - ax.o[m][2]};
     float v[3];
     cross3(ax.z[m], r, v);
     J[0][m] = v[0]; J[1][m] = v[1]; J[2][m] = v[2];
@@ -372,7 +378,7 @@ __device__ __forceinline__ bool goal_chart(const ArmK& A, const fn_problem_t& P,
       for (int m = 0; m < 7; ++m) sacc = fmaf(J[i][m], J[j][m], sacc);
       M[i][j] = sacc;
     }
-  const float vt[6] = {vb[0], vb[1], vb[2], 0.f, 0.f, 0.f};
+  const float vt[6] = {o.vb[0], o.vb[1], o.vb[2], 0.f, 0.f, 0.f};
   float y[6];
   if (!chol_solve6(M, vt, y)) return false;
 #pragma unroll

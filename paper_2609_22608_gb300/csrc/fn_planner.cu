@@ -183,7 +183,8 @@ __device__ __forceinline__ int find_problem(const int* off, int P, int x) {
 // ---------------------------------------------------------------------------
 // samplers
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_plan_sample(PlanDev D, ArmK A) {
+// Free candidates: one thread each (uniform in the box, |qd| <= vel_frac qdbar).
+__global__ void __launch_bounds__(128) k_plan_sample_free(PlanDev D, ArmK A) {
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int p = (int)(gid / D.BM);
   const int b = (int)(gid - (long)p * D.BM);
@@ -191,40 +192,82 @@ __global__ void __launch_bounds__(128) k_plan_sample(PlanDev D, ArmK A) {
   const fn_problem_t& P = D.prob[p];
   const int B = min(max(P.batch, 0), D.BM);
   const int G = min(max(P.n_goal, 0), B);
-  if (b >= B) return;
+  if (b < G || b >= B) return;
   const int it = *D.iter;
-  float* out = D.cand + ((long)p * D.BM + b) * 16;
-  float q[7], qd[7];
+  float u[16], q[7], qd[7];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) philox_u4(P.seed, b, it, p, s, u + 4 * s);
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    q[j] = fmaf(u[j], A.q_hi[j] - A.q_lo[j], A.q_lo[j]);
+    const float vb = D.vel_frac * taper(A, j, q[j]);
+    qd[j] = fmaf(2.f, u[7 + j], -1.f) * vb;
+  }
   const long ci = (long)p * D.BM + b;
-  if (b < G) {
+  D.treq[ci] = NAN;
+  D.vrel[ci] = NAN;
+  D.valid[ci] = 1;
+  float4* o4 = reinterpret_cast<float4*>(D.cand + ci * 16);
+  o4[0] = make_float4(q[0], q[1], q[2], q[3]);
+  o4[1] = make_float4(q[4], q[5], q[6], 0.f);
+  o4[2] = make_float4(qd[0], qd[1], qd[2], qd[3]);
+  o4[3] = make_float4(qd[4], qd[5], qd[6], 0.f);
+}
+
+// Goal candidates: a group of 4 lanes per candidate; lanes 0-2 run the three
+// IK starts in parallel and the lowest start that converges wins (the same
+// result as trying the starts in order).
+__global__ void __launch_bounds__(128) k_plan_sample_goal(PlanDev D, ArmK A) {
+  const long gid = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
+  const int sub = threadIdx.x & 3;
+  const int p = (int)(gid / D.BM);
+  const int b = (int)(gid - (long)p * D.BM);
+  bool live = p < D.P;
+  int G = 0;
+  if (live) {
+    const fn_problem_t& P0 = D.prob[p];
+    const int B = min(max(P0.batch, 0), D.BM);
+    G = min(max(P0.n_goal, 0), B);
+    live = b < G;
+  }
+  const unsigned gmask = 0xfu << (threadIdx.x & 28);
+  if (!__any_sync(0xffffffffu, live)) return;
+  bool defined = false, found = false;
+  ChartPose o;
+  float q[7];
+  const long ci = live ? (long)p * D.BM + b : 0;
+  if (live) {
+    const fn_problem_t& P = D.prob[p];
+    const int it = *D.iter;
     float u[12], z[9];
 #pragma unroll
     for (int s = 0; s < 3; ++s) philox_u4(P.seed, b, it, p, 8 + s, u + 4 * s);
 #pragma unroll
     for (int i = 0; i < 9; ++i) z[i] = u[i];
-    float T, vr;
-    const bool ok = goal_chart(A, P, z, q, qd, T, vr);
-    D.treq[ci] = T;
-    D.vrel[ci] = vr;
-    D.valid[ci] = ok ? 1 : 0;
-    if (!ok)
-#pragma unroll
-      for (int j = 0; j < 7; ++j) q[j] = qd[j] = 0.f;
-  } else {
-    float u[16];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) philox_u4(P.seed, b, it, p, s, u + 4 * s);
-#pragma unroll
-    for (int j = 0; j < 7; ++j) {
-      q[j] = fmaf(u[j], A.q_hi[j] - A.q_lo[j], A.q_lo[j]);
-      const float vb = D.vel_frac * taper(A, j, q[j]);
-      qd[j] = fmaf(2.f, u[7 + j], -1.f) * vb;
-    }
-    D.treq[ci] = NAN;
-    D.vrel[ci] = NAN;
-    D.valid[ci] = 1;
+    defined = chart_pose(A, P, z, o);
+    if (defined && sub < FN_IK_STARTS) found = ik_solve(A, o.Rg, o.pg, o.q7, sub, q);
   }
-  float4* o4 = reinterpret_cast<float4*>(out);
+  const unsigned won = __ballot_sync(0xffffffffu, found) & gmask;
+  const int winner = won ? __ffs(won) - 1 : -1;
+  const int lane = threadIdx.x & 31;
+  if (!live) return;
+  if (sub == 0 && winner < 0) {   // undefined: no IK start converged
+    D.treq[ci] = o.T;
+    D.vrel[ci] = o.vrel;
+    D.valid[ci] = 0;
+    float4* o4 = reinterpret_cast<float4*>(D.cand + ci * 16);
+    o4[0] = o4[1] = o4[2] = o4[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  if (lane != winner) return;
+  float qd[7];
+  const bool ok = chart_velocity(A, o, q, qd);
+  if (!ok)
+#pragma unroll
+    for (int j = 0; j < 7; ++j) q[j] = qd[j] = 0.f;
+  D.treq[ci] = o.T;
+  D.vrel[ci] = o.vrel;
+  D.valid[ci] = ok ? 1 : 0;
+  float4* o4 = reinterpret_cast<float4*>(D.cand + ci * 16);
   o4[0] = make_float4(q[0], q[1], q[2], q[3]);
   o4[1] = make_float4(q[4], q[5], q[6], 0.f);
   o4[2] = make_float4(qd[0], qd[1], qd[2], qd[3]);
@@ -333,11 +376,13 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_edges(PlanDev
   __shared__ float sT[FN_MAX_GRID];
   __shared__ float sEdge[PL_EDGE_WARPS][32];
   __shared__ float sCoef[PL_EDGE_WARPS][FN_CUBIC_WORDS * 32];
+  __shared__ float sWr[PL_EDGE_WARPS][FN_WRENCH_WORDS * 32];
   for (int i = threadIdx.x; i < D.K; i += blockDim.x) sT[i] = Gr.T[i];
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   float* es = sEdge[w];
   const CubicLane cb{&sCoef[w][lane]};
+  const LaneWrench wr{&sWr[w][lane]};
   Sched* S = D.sched;
   const int nfree = S->n_free_edges, ntot = S->n_edges;
   unsigned nsamp = 0;
@@ -351,11 +396,14 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_edges(PlanDev
     const int* off = goal ? S->goal_off : S->free_off;
     const int p = find_problem(off, D.P, x);
     const int local = x - off[p];
-    const int slot = local / D.KP;
-    const int j = local - slot * D.KP;
     const fn_problem_t& P = D.prob[p];
     const int B = min(max(P.batch, 0), D.BM);
     const int G = min(max(P.n_goal, 0), B);
+    // parent-slot-major order: every candidate's root edge (the longest
+    // scans, t(p) = 0) is queued before any nearest-node edge
+    const int nc = goal ? G : B - G;
+    const int j = local / nc;
+    const int slot = local - j * nc;
     const int b = goal ? slot : G + slot;
     const long ci = (long)p * D.BM + b;
     const long ei = ci * D.KP + j;
@@ -368,7 +416,7 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_edges(PlanDev
     const bool finite = stage_rows(D.st + node * 16, D.cand + ci * 16, es);
     const float tp = D.t[node];
     const float Tp = goal ? __fsub_rn(D.treq[ci], tp) : __fsub_rn(D.inc[p].t_best, tp);
-    EdgeResult r = time_edge(A, es, cb, finite, goal, Tp, sT, D.K, D.S, false, nsamp);
+    EdgeResult r = time_edge(A, es, cb, wr, finite, goal, Tp, sT, D.K, D.S, false, nsamp);
     bool ok = r.ok;
     if (ok && P.n_obs > 0) {
       // Clear: capsule clearance at S_clear points of the edge at T
@@ -867,7 +915,8 @@ static fn_status enqueue_iteration(fn_planner* pl, unsigned flags, cudaStream_t 
   mark(1);
   if (!(flags & FN_PLAN_EXTERNAL)) {
     const long n = (long)P * D.BM;
-    k_plan_sample<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(D, pl->arm);
+    k_plan_sample_goal<<<(unsigned)((4 * n + 127) / 128), 128, 0, st>>>(D, pl->arm);
+    k_plan_sample_free<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(D, pl->arm);
   }
   mark(2);
   if (pl->cfg.k > 1) {
@@ -1011,5 +1060,72 @@ extern "C" fn_status fn_planner_sample_count(fn_planner_t* pl, unsigned long lon
     return FN_ECUDA;
   if (reset && cudaMemset(pl->D.samples, 0, sizeof(unsigned long long)) != cudaSuccess)
     return FN_ECUDA;
+  return FN_OK;
+}
+
+// Autotuner of the planner's edge kernel: runs the iteration's prefix
+// (schedule, samplers unless FN_PLAN_EXTERNAL, parents) once, then times
+// every register-budget variant of the persistent edge kernel on that edge
+// batch (`reps` runs each, after one warm-up) and keeps the fastest for this
+// planner and for planners created later with the same shape.  The tree is
+// not modified.  chosen: host (may be NULL); variant_ms: host [3] (may be NULL).
+extern "C" fn_status fn_planner_autotune(fn_planner_t* pl, const fn_problem_t* probs, int iter,
+                                         unsigned flags, int reps, int* chosen,
+                                         float* variant_ms, void* stream) {
+  if (!pl || !probs || reps < 1) return FN_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  fn_status rc = stage_problems(pl, probs, st);
+  if (rc != FN_OK) return rc;
+  *pl->h_iter = iter;
+  if (cudaMemcpyAsync(pl->D.iter, pl->h_iter, sizeof(int), cudaMemcpyHostToDevice, st) !=
+      cudaSuccess)
+    return FN_ECUDA;
+  PlanDev& D = pl->D;
+  const int P = pl->cfg.P;
+  k_plan_schedule<<<1, 32, 0, st>>>(D);
+  if (!(flags & FN_PLAN_EXTERNAL)) {
+    const long n = (long)P * D.BM;
+    k_plan_sample_goal<<<(unsigned)((4 * n + 127) / 128), 128, 0, st>>>(D, pl->arm);
+    k_plan_sample_free<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(D, pl->arm);
+  }
+  if (pl->cfg.k > 1) {
+    const long nn = (long)P * D.BM * D.KN;
+    k_plan_nn_empty<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(D);
+    const int kb = 2 * num_sms();
+    if (D.KM == 8) {
+      k_plan_knn<8><<<kb, 128, 0, st>>>(D);
+      k_plan_knn_merge<8><<<(unsigned)(((long)P * D.BM + 7) / 8), 256, 0, st>>>(D);
+    } else {
+      k_plan_knn<16><<<kb, 128, 0, st>>>(D);
+      k_plan_knn_merge<16><<<(unsigned)(((long)P * D.BM + 7) / 8), 256, 0, st>>>(D);
+    }
+  }
+  if ((rc = launch_status()) != FN_OK) return rc;
+  float best_ms = INFINITY;
+  int best = pl->edge_variant;
+  for (int v = 0; v < kEdgeVariants; ++v) {
+    const int blocks = pl->cfg.edge_blocks > 0 ? pl->cfg.edge_blocks : plan_edge_blocks(pl, v);
+    float tot = 0.f;
+    for (int r = 0; r <= reps; ++r) {
+      k_plan_schedule<<<1, 32, 0, st>>>(D);  // resets the work queue
+      cudaEventRecord(pl->ev[0], st);
+      plan_edge_variant(v)<<<blocks, 32 * PL_EDGE_WARPS, 0, st>>>(D, pl->arm, pl->grid);
+      cudaEventRecord(pl->ev[1], st);
+      if (cudaEventSynchronize(pl->ev[1]) != cudaSuccess) return FN_ECUDA;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, pl->ev[0], pl->ev[1]);
+      if (r > 0) tot += ms;
+    }
+    if ((rc = launch_status()) != FN_OK) return rc;
+    const float ms = tot / reps;
+    if (variant_ms) variant_ms[v] = ms;
+    if (ms < best_ms) { best_ms = ms; best = v; }
+  }
+  pl->edge_variant = best;
+  pl->edge_blocks = pl->cfg.edge_blocks > 0 ? pl->cfg.edge_blocks : plan_edge_blocks(pl, best);
+  set_tuned_variant(TUNE_PLAN_EDGES, (long)pl->cfg.P * pl->cfg.b_max * pl->cfg.k, pl->cfg.K,
+                    pl->cfg.S, best);
+  if (chosen) *chosen = best;
+  pl->timing = false;  // the phase events were reused
   return FN_OK;
 }

@@ -89,7 +89,18 @@ __device__ __forceinline__ void knn_scan_range(const float4* __restrict__ tree, 
     __syncthreads();
     for (int x = threadIdx.x; x < cnt * 4; x += blockDim.x) tile[x] = __ldg(tree + 4L * base + x);
     __syncthreads();
-    for (int n = 0; n < cnt; ++n) top.push(knn_dist(qv, tile + 4 * n, w), base + n);
+    int n = 0;
+    for (; n + 4 <= cnt; n += 4) {   // four independent distance chains
+      const float d0 = knn_dist(qv, tile + 4 * n, w);
+      const float d1 = knn_dist(qv, tile + 4 * (n + 1), w);
+      const float d2 = knn_dist(qv, tile + 4 * (n + 2), w);
+      const float d3 = knn_dist(qv, tile + 4 * (n + 3), w);
+      top.push(d0, base + n);
+      top.push(d1, base + n + 1);
+      top.push(d2, base + n + 2);
+      top.push(d3, base + n + 3);
+    }
+    for (; n < cnt; ++n) top.push(knn_dist(qv, tile + 4 * n, w), base + n);
   }
 }
 

@@ -60,10 +60,11 @@ def _bind():
     L.fn_planner_get_candidates.argtypes = [vp, i32, vp, vp, vp, vp, i32]
     L.fn_planner_sample_count.argtypes = [vp, C.POINTER(C.c_ulonglong), i32]
     L.fn_planner_phase_ms.argtypes = [vp, vp]
+    L.fn_planner_autotune.argtypes = [vp, vp, i32, C.c_uint, i32, vp, vp, vp]
     for n in ("fn_planner_create", "fn_planner_destroy", "fn_planner_reset", "fn_planner_load_tree",
               "fn_planner_set_candidates", "fn_plan_iteration", "fn_planner_capture",
               "fn_plan_replay", "fn_planner_get_tree", "fn_planner_get_candidates",
-              "fn_planner_sample_count", "fn_planner_phase_ms"):
+              "fn_planner_sample_count", "fn_planner_phase_ms", "fn_planner_autotune"):
         getattr(L, n).restype = i32
     L._planner_bound = True
     return L
@@ -201,6 +202,16 @@ class Planner:
                                               vr.ctypes.data, va.ctypes.data, int(B)),
               "fn_planner_get_candidates")
         return dict(states=st, T_req=tq, v_rel=vr, valid=va)
+
+    def autotune(self, probs, it=0, flags=0, reps=3, stream=None):
+        """fn_planner_autotune: returns (chosen variant, ms per variant)."""
+        self._stage(probs)
+        chosen = C.c_int()
+        ms = (C.c_float * 3)()
+        check(lib().fn_planner_autotune(self.h, self._probs, int(it), int(flags), int(reps),
+                                        C.byref(chosen), ms, self._stream(stream)),
+              "fn_planner_autotune")
+        return chosen.value, [float(x) for x in ms]
 
     PHASES = ("schedule", "sample", "parents", "edges", "attach", "prune", "output")
 

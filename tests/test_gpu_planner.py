@@ -252,3 +252,25 @@ def test_batched_uneven_problems(P, orc, arm):
         if rinc["id"] >= 0:
             assert outs[p]["J"] == pytest.approx(rinc["J"], rel=1e-4, abs=1e-4)
     pl.close()
+
+
+def test_autotune_keeps_results(P, orc, arm):
+    """Every schedule variant computes the same iteration."""
+    case = make_case(arm, orc, 8, N=600)
+    states, t, parent = case["tree"]
+    B = 256
+    trees = []
+    for tune in (False, True):
+        pl = P.Planner(arm, P=1, n_cap=states.shape[0] + B + 8, b_max=B, k=8, K=64, S=32)
+        prob = P.problem_struct(case["pr"], B, B // 2, root=case["root"], seed=5)
+        pl.reset([prob])
+        pl.load_tree(0, states, t, parent)
+        if tune:
+            chosen, ms = pl.autotune([prob], 0, 0, reps=2)
+            assert 0 <= chosen < 3 and all(m > 0 for m in ms)
+        pl.iterate([prob], 0, 0)
+        trees.append(pl.get_tree(0))
+        pl.close()
+    a, b = trees
+    assert a["n"] == b["n"] and np.array_equal(a["states"], b["states"])
+    assert np.array_equal(a["parent"], b["parent"]) and np.array_equal(a["t"], b["t"])
