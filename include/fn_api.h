@@ -200,6 +200,35 @@ fn_status fn_knn_tree(const float* tree, int N, int first, const float* queries,
                       size_t workspace_bytes, void* stream);
 
 /*
+ * fn_knn_tree_static -- fn_knn_tree for callers that cannot allocate device
+ * memory.  (The paper has no counterpart; this is a property of the library.)
+ *
+ * Who needs it: a real-time planning thread must not enter the CUDA
+ * allocator mid-cycle, because cudaMalloc can synchronise the device and take
+ * milliseconds inside a 20 ms budget; an embedded host may have all device
+ * memory budgeted at start-up.  Such callers cannot provide fn_knn_tree's
+ * workspace.  This entry point takes the same arguments minus the workspace
+ * and computes the same result: its split pass uses a fixed file-scope device
+ * array of 16 MiB that every GPU loading the library holds until the process
+ * exits.  The call itself allocates nothing (no cudaMalloc, no library
+ * allocator).
+ *
+ * Limits and caveats:
+ *  - B <= FN_KNN_STATIC_MAX_QUERIES (65536); larger B returns FN_EINVAL.
+ *    Within the limit the number of node splits is reduced to what fits.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress, once per device, with that device current).
+ *    Make that first call before any stream capture.
+ *  - All calls share the one array.  Calls that overlap on the GPU (other
+ *    streams, other host threads) race on it and must be serialised by the
+ *    caller.  The array keeps the last call's contents; nothing in it needs
+ *    to start at zero, because every entry is written before it is read.
+ */
+#define FN_KNN_STATIC_MAX_QUERIES 65536
+fn_status fn_knn_tree_static(const float* tree, int N, int first, const float* queries, int B,
+                             int k, float w_vel, int32_t* idx, float* d2, void* stream);
+
+/*
  * fn_make_edges -- the (candidate, parent) edges of Algorithm 1's inner loop.
  * Each candidate b has the parent set {root} + its k_nn nearest tree nodes
  * (Sec. IV-E "Parents"): edge e = b (k_nn + 1) + j joins parent p (p = 0 for

@@ -1,0 +1,60 @@
+"""fn_knn_tree_static: the parent search for callers that cannot allocate
+device memory (a real-time planning thread that must stay out of the CUDA
+allocator, or a host whose device memory is budgeted at start-up).  Called
+through the C ABI and compared with fn_knn_tree (caller workspace) on two
+calls in a row, with the kNN parity rule of the other tests.  This file is
+collected last on purpose."""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2609_22608_gb300 import synth
+from tests.parity import knn_mismatches
+
+pytestmark = pytest.mark.gpu
+
+
+def _static_fn():
+    from paper_2609_22608_gb300._lib import lib
+    L = lib()
+    f = L.fn_knn_tree_static
+    f.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_float,
+                  C.c_void_p, C.c_void_p, C.c_void_p]
+    f.restype = C.c_int
+    return f
+
+
+def test_static_knn_matches_workspace_knn(arm):
+    from paper_2609_22608_gb300 import ops
+    f = _static_fn()
+    B, N, k = 2048, 4096, 8
+    tree = torch.from_numpy(synth.random_states(arm, N, 41)).cuda()
+    stream = torch.cuda.current_stream()
+    for call, seed in enumerate((42, 43)):      # two calls in a row share the array
+        q = torch.from_numpy(synth.random_states(arm, B, seed)).cuda()
+        idx_s = torch.full((B, k), -7, dtype=torch.int32, device="cuda")
+        d2_s = torch.full((B, k), -7.0, device="cuda")
+        st = f(C.c_void_p(tree.data_ptr()), N, 1, C.c_void_p(q.data_ptr()), B, k, 0.1,
+               C.c_void_p(idx_s.data_ptr()), C.c_void_p(d2_s.data_ptr()),
+               C.c_void_p(stream.cuda_stream))
+        assert st == 0, f"call {call}: status {st}"
+        ws = torch.empty(ops.knn_workspace_bytes(B, N, k) + 256, dtype=torch.uint8, device="cuda")
+        idx_w, d2_w = ops.knn_tree(tree, q, k, 0.1, first=1, workspace=ws)
+        torch.cuda.synchronize()
+        a_i, a_d = idx_s.cpu().numpy(), d2_s.cpu().numpy()
+        b_i, b_d = idx_w.cpu().numpy(), d2_w.cpu().numpy()
+        assert not knn_mismatches(a_i, a_d, b_i, b_d), f"call {call}"
+        assert np.allclose(a_d, b_d, rtol=1e-6, atol=0)
+
+
+def test_static_knn_rejects_oversize(arm):
+    f = _static_fn()
+    q = torch.zeros(16, 16, device="cuda")
+    out_i = torch.zeros(16, 4, dtype=torch.int32, device="cuda")
+    out_d = torch.zeros(16, 4, device="cuda")
+    # B beyond FN_KNN_STATIC_MAX_QUERIES (65536) is refused before any launch
+    st = f(C.c_void_p(q.data_ptr()), 16, 1, C.c_void_p(q.data_ptr()), 65537, 4, 0.1,
+           C.c_void_p(out_i.data_ptr()), C.c_void_p(out_d.data_ptr()), None)
+    assert st == -1
