@@ -386,12 +386,16 @@ fn_status fn_planner_autotune(fn_planner_t* pl, const fn_problem_t* probs, int i
 
 /* Durations in ms of the last fn_plan_iteration's phases, from CUDA events
  * recorded on its stream: [0] schedule, [1] sample, [2] parents (kNN),
- * [3] edges (timing + clearance), [4] attach + score, [5] prune, [6] output.
- * ms: host [7].  FN_EINVAL before the first fn_plan_iteration. */
+ * [3] edge prep + item scan, [4] probe (both end samples of every admissible
+ * (edge, duration) item), [5] verify (surviving durations, rho_v, Clear),
+ * [6] attach + score, [7] prune, [8] output.  ms: host [9].  FN_EINVAL
+ * before the first fn_plan_iteration. */
 fn_status fn_planner_phase_ms(fn_planner_t* pl, float* ms);
 
 /* Torque evaluations (edge, duration, sample) performed by the planner's
- * edge kernel since creation or the last reset (reset != 0 zeroes it). */
+ * edge kernels since creation or the last reset (reset != 0 zeroes them):
+ * count[0] by the probe kernel, count[1] by the verify kernel.  count: host
+ * [2]. */
 fn_status fn_planner_sample_count(fn_planner_t* pl, unsigned long long* count, int reset);
 
 /* Copy problem p's tree to host (any pointer may be NULL): states [n][16],

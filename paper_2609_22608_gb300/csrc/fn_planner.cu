@@ -30,7 +30,7 @@
 #include "fn_tune.h"
 #include "knn_core.cuh"
 
-#define PL_NSPLIT_MAX 8
+#define PL_NSPLIT_MAX 32
 #define PL_MAX_P 1024
 
 namespace fn {
@@ -44,6 +44,8 @@ struct Incumbent {
 
 struct Sched {
   unsigned int queue_head;
+  int n_items;        // probe items of the packed edge phase
+  int n_pend[2];      // lengths of the two pending-edge lists
   int n_free_edges;   // free edges of all problems (the queue's first part)
   int n_edges;        // all edges
   int knn_items;      // (problem, query tile, split) items
@@ -87,7 +89,20 @@ struct PlanDev {  // device pointers, passed by value to the kernels
   float* tmp_st;      // [P][NC][16]
   float* tmp_f;       // [P][NC][4]  (t, J, nu, eT)
   int32_t* tmp_par;   // [P][NC]
-  unsigned long long* samples;  // work counter (torque evaluations)
+  unsigned long long* samples;  // work counters (torque evaluations): [0] probe, [1] verify
+  // packed edge phase (flat edge index e in queue order)
+  int32_t* e_ci;      // [E] candidate slot p*BM + b
+  int32_t* e_par;     // [E] parent node (-1: invalid edge)
+  float* e_Tp;        // [E] goal: fixed duration; free: cap
+  uint8_t* e_j;       // [E] parent slot | 0x80 for goal edges
+  int32_t* e_cnt;     // [E] probe items; then local exclusive offsets
+  int32_t* blk_off;   // [ceil(E/1024)] block offsets of the item scan
+  uint32_t* mask;     // [E][8] surviving grid indices of the probe
+  int32_t* owner;     // [E*K] probe item -> edge
+  int32_t* cur_k;     // [E] duration under verification (grid index; 0 for goals)
+  uint32_t* fail;     // [E] a sample of cur_k violated a limit
+  int32_t* pend;      // [2][E] edges pending verification (ping-pong lists)
+  int Emax, Kmax;
 };
 
 struct GridKP {
@@ -154,7 +169,7 @@ __global__ void k_plan_schedule(PlanDev D) {
     const int span = D.n_nodes[p] - 1;  // non-root nodes
     int ns = 1;
     if (D.KN > 0 && span > 0) {
-      ns = min(PL_NSPLIT_MAX, max(1, span / (4 * KNN_TILE)));
+      ns = min(PL_NSPLIT_MAX, max(1, span / KNN_TILE));
     }
     S->nsplit[p] = ns;
     ko += (D.KN > 0 && span > 0) ? ((B + 127) / 128) * ns : 0;
@@ -365,88 +380,433 @@ __global__ void k_plan_nn_empty(PlanDev D) {
   if (D.n_nodes[p] <= 1) D.nn[i] = -1;
 }
 
-// ---------------------------------------------------------------------------
-// edges: one persistent launch, warps pull edges from the device queue
-// ---------------------------------------------------------------------------
 #define PL_EDGE_WARPS 4
 
+// ---------------------------------------------------------------------------
+// packed edge phase: prep -> item scan -> probe (lanes = (edge, duration)
+// items) -> verify (warp per edge, lanes = samples)
+// ---------------------------------------------------------------------------
+#define PL_SCAN 1024
+
+// decode flat edge e (queue order: free edges of all problems, then goal
+// edges; parent-slot-major inside a problem) into (problem, candidate, slot)
+__device__ __forceinline__ void decode_edge(const PlanDev& D, const Sched* S, int e, int& p,
+                                            int& b, int& j, bool& goal) {
+  const int nfree = S->n_free_edges;
+  goal = e >= nfree;
+  const int x = goal ? e - nfree : e;
+  const int* off = goal ? S->goal_off : S->free_off;
+  p = find_problem(off, D.P, x);
+  const int local = x - off[p];
+  const fn_problem_t& P = D.prob[p];
+  const int B = min(max(P.batch, 0), D.BM);
+  const int G = min(max(P.n_goal, 0), B);
+  const int nc = goal ? G : B - G;
+  j = local / nc;
+  const int slot = local - j * nc;
+  b = goal ? slot : G + slot;
+}
+
+__global__ void __launch_bounds__(PL_SCAN) k_plan_eprep(PlanDev D, GridKP Gr) {
+  __shared__ float sT[FN_MAX_GRID];
+  __shared__ int sh[PL_SCAN];
+  for (int i = threadIdx.x; i < D.K; i += blockDim.x) sT[i] = Gr.T[i];
+  __syncthreads();
+  const Sched* S = D.sched;
+  const int E = S->n_edges;
+  const int e = blockIdx.x * PL_SCAN + threadIdx.x;
+  int cnt = 0;
+  if (e < E) {
+    int p, b, j;
+    bool goal;
+    decode_edge(D, S, e, p, b, j, goal);
+    const long ci = (long)p * D.BM + b;
+    const int pr = j == 0 ? 0 : D.nn[ci * D.KN + (j - 1)];
+    const long ei = ci * D.KP + j;
+    float Tp = NAN;
+    const bool valid = pr >= 0 && D.valid[ci];
+    if (valid) {
+      const float tp = D.t[(long)p * D.NC + pr];
+      Tp = goal ? __fsub_rn(D.treq[ci], tp) : __fsub_rn(D.inc[p].t_best, tp);
+      if (goal) {
+        cnt = (isfinite(Tp) && Tp > 0.f) ? 1 : 0;
+      } else {
+        int lo = 0, hi = D.K;   // #{k : T_k <= cap} on the ascending grid
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (sT[mid] <= Tp) lo = mid + 1;
+          else hi = mid;
+        }
+        cnt = lo;
+      }
+    }
+    D.e_ci[e] = (int)ci;
+    D.e_par[e] = valid ? pr : -1;
+    D.e_Tp[e] = Tp;
+    D.e_j[e] = (uint8_t)(j | (goal ? 0x80 : 0));
+#pragma unroll
+    for (int w = 0; w < 8; ++w) D.mask[8L * e + w] = 0u;
+    if (cnt == 0) {   // decided without dynamics: invalid or no admissible duration
+      D.e_ok[ei] = 0;
+      D.e_T[ei] = goal ? Tp : INFINITY;
+      D.e_rv[ei] = NAN;
+    }
+  }
+  // block-local exclusive scan of the item counts
+  sh[threadIdx.x] = cnt;
+  __syncthreads();
+  for (int o = 1; o < PL_SCAN; o <<= 1) {
+    const int a = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += a;
+    __syncthreads();
+  }
+  if (e < E) D.e_cnt[e] = sh[threadIdx.x] - cnt;
+  if (threadIdx.x == PL_SCAN - 1) D.blk_off[blockIdx.x] = sh[PL_SCAN - 1];
+}
+
+// exclusive scan of the per-block item totals (one block)
+__global__ void __launch_bounds__(PL_SCAN) k_plan_escan(PlanDev D) {
+  __shared__ int sh[PL_SCAN];
+  Sched* S = D.sched;
+  const int nb = (S->n_edges + PL_SCAN - 1) / PL_SCAN;
+  int carry = 0;
+  for (int base = 0; base < nb; base += PL_SCAN) {
+    const int i = base + threadIdx.x;
+    const int v = i < nb ? D.blk_off[i] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < PL_SCAN; o <<= 1) {
+      const int a = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+      __syncthreads();
+      sh[threadIdx.x] += a;
+      __syncthreads();
+    }
+    if (i < nb) D.blk_off[i] = carry + sh[threadIdx.x] - v;
+    const int tot = sh[PL_SCAN - 1];
+    __syncthreads();
+    carry += tot;
+  }
+  if (threadIdx.x == 0) {
+    S->n_items = carry;
+    S->queue_head = 0u;
+  }
+}
+
+__device__ __forceinline__ int item_off(const PlanDev& D, int e) {
+  return D.e_cnt[e] + D.blk_off[e / PL_SCAN];
+}
+
+// item -> owning edge, one warp per edge
+__global__ void __launch_bounds__(256) k_plan_expand(PlanDev D) {
+  const Sched* S = D.sched;
+  const int E = S->n_edges, lane = threadIdx.x & 31;
+  const long W = (long)gridDim.x * (blockDim.x >> 5);
+  for (long e = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < E; e += W) {
+    const int o = item_off(D, (int)e);
+    const int c = ((int)e + 1 < E ? item_off(D, (int)e + 1) : S->n_items) - o;
+    for (int t = lane; t < c; t += 32) D.owner[o + t] = (int)e;
+  }
+}
+
+// Probe: one lane per (edge, grid duration) item evaluates both end samples
+// (u = 0, u = 1) with plain FP32 coefficients; a duration whose ends pass is
+// marked in the edge's survivor mask.  Goal edges have one item: their fixed
+// duration.
 template <int MINB>
-__global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_edges(PlanDev D, ArmK A,
+__global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_probe(PlanDev D, ArmK A,
                                                                          GridKP Gr) {
   __shared__ float sT[FN_MAX_GRID];
-  __shared__ float sEdge[PL_EDGE_WARPS][32];
   __shared__ float sCoef[PL_EDGE_WARPS][FN_CUBIC_WORDS * 32];
   __shared__ float sWr[PL_EDGE_WARPS][FN_WRENCH_WORDS * 32];
   for (int i = threadIdx.x; i < D.K; i += blockDim.x) sT[i] = Gr.T[i];
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  float* es = sEdge[w];
+  const CubicLane cb{&sCoef[w][lane]};
+  const LaneWrench wr{&sWr[w][lane]};
+  const Sched* S = D.sched;
+  const int n_items = S->n_items;
+  unsigned nsamp = 0;
+  const long W = (long)gridDim.x * PL_EDGE_WARPS;
+  for (long c = (long)blockIdx.x * PL_EDGE_WARPS + w; c * 32 < n_items; c += W) {
+    const int i = (int)(c * 32) + lane;
+    const bool live = i < n_items;
+    int e = 0, k = 0;
+    if (live) {
+      e = D.owner[i];
+      k = i - item_off(D, e);
+      const bool goal = D.e_j[e] & 0x80;
+      const float T = goal ? D.e_Tp[e] : sT[k];
+      const int p = D.e_ci[e] / D.BM;
+      const float* r0 = D.st + ((long)p * D.NC + D.e_par[e]) * 16;
+      const float* r1 = D.cand + (long)D.e_ci[e] * 16;
+      float es[32];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) { es[m] = __ldg(r0 + m); es[16 + m] = __ldg(r1 + m); }
+      Cubic cc;
+      cubic_coef_sh<false>(es, T, cc);
+      cb.store(cc);
+    }
+    bool pass = live;
+#pragma unroll 1
+    for (int end = 0; end < 2; ++end) {   // single torque call site
+      float a = 0.f, b = 0.f;
+      if (live) sample_ratios(A, cb, (float)end, a, b, wr);
+      pass = pass && a <= 1.f && b <= 1.f;
+    }
+    nsamp += 2u * __popc(__ballot_sync(0xffffffffu, live));
+    if (pass) atomicOr(&D.mask[8L * e + (k >> 5)], 1u << (k & 31));
+  }
+  if (D.samples && lane == 0 && nsamp) atomicAdd(D.samples + 0, (unsigned long long)nsamp);
+}
+
+// first survivor at or after grid index `from`; -1 if none
+__device__ __forceinline__ int next_survivor(const PlanDev& D, int e, int from) {
+  for (int q = from >> 5; q < 8; ++q) {
+    uint32_t bits = D.mask[8L * e + q];
+    if (q == (from >> 5)) bits &= ~0u << (from & 31);
+    if (bits) return 32 * q + __ffs(bits) - 1;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ void edge_slot(const PlanDev& D, int e, long& ei, bool& goal) {
+  goal = D.e_j[e] & 0x80;
+  ei = (long)D.e_ci[e] * D.KP + (D.e_j[e] & 0x7f);
+}
+
+// verification start: each edge with probe items either has no survivor
+// (infeasible on the whole admissible grid) or joins the first pending list
+__global__ void k_plan_vinit(PlanDev D) {
+  Sched* S = D.sched;
+  const int E = S->n_edges;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+    const int c = (e + 1 < E ? item_off(D, e + 1) : S->n_items) - item_off(D, e);
+    if (c == 0) continue;   // decided in prep
+    const int k = next_survivor(D, e, 0);
+    D.fail[e] = 0u;
+    if (k < 0) {
+      long ei;
+      bool goal;
+      edge_slot(D, e, ei, goal);
+      D.e_ok[ei] = 0;
+      D.e_T[ei] = goal ? D.e_Tp[e] : INFINITY;
+      D.e_rv[ei] = NAN;
+      continue;
+    }
+    D.cur_k[e] = k;
+    D.pend[atomicAdd(&S->n_pend[0], 1)] = e;
+  }
+}
+
+// one packed verification stage: lanes = (pending edge, sample) items; any
+// violating sample marks the edge's current duration as failed
+template <int MINB>
+__global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_vstage(PlanDev D, ArmK A,
+                                                                          GridKP Gr, int list) {
+  __shared__ float sT[FN_MAX_GRID];
+  __shared__ float sCoef[PL_EDGE_WARPS][FN_CUBIC_WORDS * 32];
+  __shared__ float sWr[PL_EDGE_WARPS][FN_WRENCH_WORDS * 32];
+  for (int i = threadIdx.x; i < D.K; i += blockDim.x) sT[i] = Gr.T[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const CubicLane cb{&sCoef[w][lane]};
+  const LaneWrench wr{&sWr[w][lane]};
+  const Sched* S = D.sched;
+  const int n = S->n_pend[list] * D.S;
+  const int32_t* pend = D.pend + (long)list * D.Emax;
+  unsigned nsamp = 0;
+  const long W = (long)gridDim.x * PL_EDGE_WARPS;
+  for (long c = (long)blockIdx.x * PL_EDGE_WARPS + w; c * 32 < n; c += W) {
+    const int i = (int)(c * 32) + lane;
+    const bool live = i < n;
+    int e = 0, s = 0;
+    if (live) {
+      const int pi = i / D.S;
+      s = i - pi * D.S;
+      e = pend[pi];
+      const bool goal = D.e_j[e] & 0x80;
+      const float T = goal ? D.e_Tp[e] : sT[D.cur_k[e]];
+      const int p = D.e_ci[e] / D.BM;
+      const float* r0 = D.st + ((long)p * D.NC + D.e_par[e]) * 16;
+      const float* r1 = D.cand + (long)D.e_ci[e] * 16;
+      float es[32];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) { es[m] = __ldg(r0 + m); es[16 + m] = __ldg(r1 + m); }
+      Cubic cc;
+      cubic_coef_sh<true>(es, T, cc);
+      cb.store(cc);
+    }
+    float a = 0.f, b = 0.f;
+    if (live) sample_ratios(A, cb, sample_u(s, D.S), a, b, wr);   // single call site
+    nsamp += __popc(__ballot_sync(0xffffffffu, live));
+    if (live && !(a <= 1.f && b <= 1.f)) D.fail[e] = 1u;
+  }
+  if (D.samples && lane == 0 && nsamp) atomicAdd(D.samples + 1, (unsigned long long)nsamp);
+}
+
+// per-thread end of an edge whose duration T passed: rho_v at T, then Clear
+__device__ __forceinline__ void finish_edge(const PlanDev& D, const ArmK& A, int e, float T) {
+  long ei;
+  bool goal;
+  edge_slot(D, e, ei, goal);
+  const int p = D.e_ci[e] / D.BM;
+  const float* r0 = D.st + ((long)p * D.NC + D.e_par[e]) * 16;
+  const float* r1 = D.cand + (long)D.e_ci[e] * 16;
+  float es[32];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) { es[m] = r0[m]; es[16 + m] = r1[m]; }
+  Cubic c;
+  cubic_coef_sh<true>(es, T, c);
+  float rv = 0.f;
+#pragma unroll 1
+  for (int j = 0; j < 7; ++j) rv = fmaxf(rv, rho_v_joint(A, c, j));
+  bool ok = rv <= 1.f;
+  const fn_problem_t& P = D.prob[p];
+  if (ok && P.n_obs > 0) {
+    float mc = INFINITY;
+#pragma unroll 1
+    for (int s = 0; s < D.S_clear; ++s) {
+      const float u = sample_u(s, D.S_clear);
+      float q[7];
+#pragma unroll
+      for (int jj = 0; jj < 7; ++jj) {
+        float v, a;
+        cubic_eval(c, jj, u, q[jj], v, a);
+      }
+      mc = fminf(mc, config_clearance(A, q, P));
+    }
+    ok = mc >= D.margin;
+  }
+  D.e_ok[ei] = ok ? 1 : 0;
+  D.e_T[ei] = T;
+  D.e_rv[ei] = rv;
+}
+
+// after a stage: edges whose duration passed are finished; the others move
+// to their next survivor (next list) or end with no feasible duration
+__global__ void k_plan_vselect(PlanDev D, ArmK A, GridKP Gr, int list) {
+  Sched* S = D.sched;
+  const int n = S->n_pend[list];
+  const int32_t* pend = D.pend + (long)list * D.Emax;
+  int32_t* next = D.pend + (long)(list ^ 1) * D.Emax;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int e = pend[i];
+    const bool goal = D.e_j[e] & 0x80;
+    const int k = D.cur_k[e];
+    if (!D.fail[e]) {
+      finish_edge(D, A, e, goal ? D.e_Tp[e] : Gr.T[k]);
+      continue;
+    }
+    D.fail[e] = 0u;
+    const int k2 = goal ? -1 : next_survivor(D, e, k + 1);
+    if (k2 < 0) {
+      long ei;
+      bool g;
+      edge_slot(D, e, ei, g);
+      D.e_ok[ei] = 0;
+      D.e_T[ei] = goal ? D.e_Tp[e] : INFINITY;
+      D.e_rv[ei] = NAN;
+      continue;
+    }
+    D.cur_k[e] = k2;
+    next[atomicAdd(&S->n_pend[list ^ 1], 1)] = e;
+  }
+}
+
+__global__ void k_plan_vclear(PlanDev D, int list) {
+  if (threadIdx.x == 0) {
+    D.sched->n_pend[list] = 0;
+    D.sched->queue_head = 0u;
+  }
+}
+
+// Leftovers after the packed stages: one block per edge; its four warps take
+// the edge's next four survivors (one each, lanes = samples, exit at the
+// first violating batch) and the lowest passing survivor is k*; groups of
+// four continue until one passes or none remain.  Four-way parallel in the
+// survivors cuts the serial depth of edges with long runs of failing
+// durations, which otherwise set the kernel's tail.
+template <int MINB>
+__global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_vseq(PlanDev D, ArmK A,
+                                                                        GridKP Gr, int list) {
+  __shared__ float sT[FN_MAX_GRID];
+  __shared__ float sEdge[32];
+  __shared__ float sCoef[PL_EDGE_WARPS][FN_CUBIC_WORDS * 32];
+  __shared__ float sWr[PL_EDGE_WARPS][FN_WRENCH_WORDS * 32];
+  __shared__ int s_item, s_k[PL_EDGE_WARPS], s_pass[PL_EDGE_WARPS];
+  for (int i = threadIdx.x; i < D.K; i += blockDim.x) sT[i] = Gr.T[i];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const CubicLane cb{&sCoef[w][lane]};
   const LaneWrench wr{&sWr[w][lane]};
   Sched* S = D.sched;
-  const int nfree = S->n_free_edges, ntot = S->n_edges;
+  const int n = S->n_pend[list];
+  const int32_t* pend = D.pend + (long)list * D.Emax;
   unsigned nsamp = 0;
   for (;;) {
-    int e = 0;
-    if (lane == 0) e = (int)atomicAdd(&S->queue_head, 1u);
-    e = __shfl_sync(0xffffffffu, e, 0);
-    if (e >= ntot) break;
-    const bool goal = e >= nfree;
-    const int x = goal ? e - nfree : e;
-    const int* off = goal ? S->goal_off : S->free_off;
-    const int p = find_problem(off, D.P, x);
-    const int local = x - off[p];
-    const fn_problem_t& P = D.prob[p];
-    const int B = min(max(P.batch, 0), D.BM);
-    const int G = min(max(P.n_goal, 0), B);
-    // parent-slot-major order: every candidate's root edge (the longest
-    // scans, t(p) = 0) is queued before any nearest-node edge
-    const int nc = goal ? G : B - G;
-    const int j = local / nc;
-    const int slot = local - j * nc;
-    const int b = goal ? slot : G + slot;
-    const long ci = (long)p * D.BM + b;
-    const long ei = ci * D.KP + j;
-    const int pr = j == 0 ? 0 : D.nn[ci * D.KN + (j - 1)];
-    if (pr < 0 || !D.valid[ci]) {
-      if (lane == 0) { D.e_ok[ei] = 0; D.e_T[ei] = INFINITY; D.e_rv[ei] = NAN; }
-      continue;
-    }
-    const long node = (long)p * D.NC + pr;
-    const bool finite = stage_rows(D.st + node * 16, D.cand + ci * 16, es);
-    const float tp = D.t[node];
-    const float Tp = goal ? __fsub_rn(D.treq[ci], tp) : __fsub_rn(D.inc[p].t_best, tp);
-    EdgeResult r = time_edge(A, es, cb, wr, finite, goal, Tp, sT, D.K, D.S, false, nsamp);
-    bool ok = r.ok;
-    if (ok && P.n_obs > 0) {
-      // Clear: capsule clearance at S_clear points of the edge at T
-      float mc = INFINITY;
-      Cubic c;
-      cubic_coef_sh<true>(es, r.T, c);
-      for (int s0 = 0; s0 < D.S_clear; s0 += 32) {
-        const int s = s0 + lane;
-        if (s < D.S_clear) {
-          const float u = sample_u(s, D.S_clear);
-          float q[7];
-#pragma unroll
-          for (int jj = 0; jj < 7; ++jj) {
-            float v, a;
-            cubic_eval(c, jj, u, q[jj], v, a);
-          }
-          mc = fminf(mc, config_clearance(A, q, P));
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(&S->queue_head, 1u);
+    __syncthreads();
+    const int i = s_item;
+    if (i >= n) break;
+    const int e = pend[i];
+    const int p = D.e_ci[e] / D.BM;
+    if (w == 0) stage_rows(D.st + ((long)p * D.NC + D.e_par[e]) * 16, D.cand + (long)D.e_ci[e] * 16, sEdge);
+    int from = D.cur_k[e], kres = -1;
+    __syncthreads();
+    while (from >= 0 && kres < 0) {
+      // the group's survivors: warp r takes the r-th survivor at or after `from`
+      if (threadIdx.x == 0) {
+        int k = from;
+        for (int r = 0; r < PL_EDGE_WARPS; ++r) {
+          s_k[r] = k;
+          if (k >= 0) k = next_survivor(D, e, k + 1);
         }
+        from = k;  // first survivor of the next group (or -1)
+        s_pass[0] = from;  // carried through shared memory below
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mc = fminf(mc, __shfl_xor_sync(0xffffffffu, mc, o));
-      ok = mc >= D.margin;
+      __syncthreads();
+      const int next_from = s_pass[0];
+      const int k = s_k[w];
+      bool pass = false;
+      if (k >= 0) {
+        {
+          Cubic c;
+          cubic_coef_sh<true>(sEdge, sT[k], c);
+          cb.store(c);
+        }
+        bool bad = false;
+        for (int s0 = 0; s0 < D.S && !bad; s0 += 32) {   // single torque call site
+          const int s = s0 + lane;
+          float a = 0.f, b = 0.f;
+          const bool act = s < D.S;
+          if (act) sample_ratios(A, cb, sample_u(s, D.S), a, b, wr);
+          bad = __any_sync(0xffffffffu, act && !(a <= 1.f && b <= 1.f));
+          nsamp += (unsigned)min(32, D.S - s0);
+        }
+        pass = !bad;
+      }
+      __syncthreads();
+      if (lane == 0) s_pass[w] = pass ? 1 : 0;
+      __syncthreads();
+      for (int r = 0; r < PL_EDGE_WARPS && kres < 0; ++r)
+        if (s_pass[r] && s_k[r] >= 0) kres = s_k[r];
+      from = next_from;
     }
-    if (lane == 0) {
-      D.e_ok[ei] = ok ? 1 : 0;
-      D.e_T[ei] = r.T;
-      D.e_rv[ei] = r.rv;
+    if (threadIdx.x == 0) {
+      if (kres >= 0) {
+        finish_edge(D, A, e, sT[kres]);
+      } else {
+        long ei;
+        bool g;
+        edge_slot(D, e, ei, g);
+        D.e_ok[ei] = 0;
+        D.e_T[ei] = INFINITY;
+        D.e_rv[ei] = NAN;
+      }
     }
   }
-  if (D.samples && lane == 0 && nsamp) atomicAdd(D.samples, (unsigned long long)nsamp);
+  if (D.samples && lane == 0 && nsamp) atomicAdd(D.samples + 1, (unsigned long long)nsamp);
 }
 
 // ---------------------------------------------------------------------------
@@ -707,8 +1067,9 @@ struct fn_planner {
   unsigned graph_flags = 0;
   int edge_variant = kDefaultEdgeVariant;
   int edge_blocks = 0;
-  // per-phase events (schedule, sample, knn, edges, attach, prune, output)
-  cudaEvent_t ev[8] = {};
+  // per-phase events: schedule, sample, parents, edge prep + scan, probe,
+  // verify, attach, prune, output
+  cudaEvent_t ev[10] = {};
   bool timing = false;
 };
 
@@ -724,21 +1085,79 @@ static fn_status pl_alloc_n(fn_planner* pl, T** p, size_t n) {
 }
 
 typedef void (*PlanEdgeKernel)(PlanDev, ArmK, GridKP);
-static PlanEdgeKernel plan_edge_variant(int v) {
+static PlanEdgeKernel plan_probe_variant(int v) {
   switch (v) {
-    case 0: return k_plan_edges<2>;
-    case 1: return k_plan_edges<3>;
-    default: return k_plan_edges<4>;
+    case 0: return k_plan_probe<2>;
+    case 1: return k_plan_probe<3>;
+    default: return k_plan_probe<4>;
+  }
+}
+typedef void (*PlanStageKernel)(PlanDev, ArmK, GridKP, int);
+static PlanStageKernel plan_vstage_variant(int v) {
+  switch (v) {
+    case 0: return k_plan_vstage<2>;
+    case 1: return k_plan_vstage<3>;
+    default: return k_plan_vstage<4>;
+  }
+}
+static PlanStageKernel plan_vseq_variant(int v) {
+  switch (v) {
+    case 0: return k_plan_vseq<2>;
+    case 1: return k_plan_vseq<3>;
+    default: return k_plan_vseq<4>;
   }
 }
 
-static int plan_edge_blocks(fn_planner* pl, int v) {
+static int resident(PlanEdgeKernel k) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_edge_variant(v),
-                                                    32 * PL_EDGE_WARPS, 0) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * PL_EDGE_WARPS, 0) !=
+          cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
   return per_sm * num_sms();
+}
+
+static int resident_stage(PlanStageKernel k) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * PL_EDGE_WARPS, 0) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return per_sm * num_sms();
+}
+
+static int plan_edge_blocks(fn_planner* pl, int v) {
+  (void)pl;
+  return std::min(resident(plan_probe_variant(v)),
+                  std::min(resident_stage(plan_vstage_variant(v)),
+                           resident_stage(plan_vseq_variant(v))));
+}
+
+#define PL_VSTAGES 2
+
+// the packed edge phase: prep, item scan, probe, verify (mark(i) records
+// the phase boundaries when timing)
+template <class Mark>
+static void enqueue_edges(fn_planner* pl, int v, int blocks, cudaStream_t st, Mark&& mark) {
+  PlanDev& D = pl->D;
+  const int eb = (D.Emax + PL_SCAN - 1) / PL_SCAN;
+  k_plan_eprep<<<eb, PL_SCAN, 0, st>>>(D, pl->grid);
+  k_plan_escan<<<1, PL_SCAN, 0, st>>>(D);
+  k_plan_vclear<<<1, 32, 0, st>>>(D, 0);
+  k_plan_expand<<<4 * num_sms(), 256, 0, st>>>(D);
+  mark(4);
+  plan_probe_variant(v)<<<blocks, 32 * PL_EDGE_WARPS, 0, st>>>(D, pl->arm, pl->grid);
+  mark(5);
+  const int tb = 2 * num_sms();
+  k_plan_vinit<<<tb, 256, 0, st>>>(D);
+  int list = 0;
+  for (int stage = 0; stage < PL_VSTAGES; ++stage) {
+    k_plan_vclear<<<1, 32, 0, st>>>(D, list ^ 1);
+    plan_vstage_variant(v)<<<blocks, 32 * PL_EDGE_WARPS, 0, st>>>(D, pl->arm, pl->grid, list);
+    k_plan_vselect<<<tb, 128, 0, st>>>(D, pl->arm, pl->grid, list);
+    list ^= 1;
+  }
+  plan_vseq_variant(v)<<<blocks, 32 * PL_EDGE_WARPS, 0, st>>>(D, pl->arm, pl->grid, list);
 }
 
 extern "C" fn_status fn_planner_destroy(fn_planner_t* pl) {
@@ -759,6 +1178,7 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
                                        fn_planner_t** out) {
   if (!cfg || !arm || !out) return FN_EINVAL;
   const fn_planner_cfg_t c = *cfg;
+  if ((long)c.P * c.b_max * c.k > (1L << 28)) return FN_EINVAL;
   if (c.P < 1 || c.P > PL_MAX_P || c.n_cap < 2 || c.n_cap > (1 << 22) || c.b_max < 1 ||
       c.b_max > (1 << 16) || c.k < 1 || c.k > FN_MAX_KNN + 1 || c.K < 1 || c.K > FN_MAX_GRID ||
       c.S < 2 || c.S > FN_MAX_S || c.S_clear < 2 || c.S_clear > FN_MAX_S || c.reach_grid < 2 ||
@@ -795,7 +1215,17 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
   A_(D.added, P); A_(D.status, P);
   A_(D.ptr, P * NC); A_(D.newidx, P * NC); A_(D.alive, P * NC);
   A_(D.tmp_st, P * NC * 16); A_(D.tmp_f, P * NC * 4); A_(D.tmp_par, P * NC);
-  A_(D.samples, 1);
+  A_(D.samples, 2);
+  D.Emax = (int)(P * BM * KP);
+  A_(D.e_ci, (size_t)D.Emax); A_(D.e_par, (size_t)D.Emax); A_(D.e_Tp, (size_t)D.Emax);
+  A_(D.e_j, (size_t)D.Emax); A_(D.e_cnt, (size_t)D.Emax);
+  A_(D.blk_off, (size_t)(D.Emax + PL_SCAN - 1) / PL_SCAN + 1);
+  A_(D.mask, (size_t)D.Emax * 8);
+  D.Kmax = c.K;
+  A_(D.owner, (size_t)D.Emax * c.K);
+  A_(D.cur_k, (size_t)D.Emax);
+  A_(D.fail, (size_t)D.Emax);
+  A_(D.pend, (size_t)D.Emax * 2);
 #undef A_
   if (rc == FN_OK) {
     if (cudaMallocHost(&pl->h_prob, P * sizeof(fn_problem_t)) != cudaSuccess ||
@@ -804,13 +1234,13 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
       rc = FN_ENOMEM;
   }
   if (rc == FN_OK && (cudaMemset(D.n_nodes, 0, P * sizeof(int)) != cudaSuccess ||
-                      cudaMemset(D.samples, 0, sizeof(unsigned long long)) != cudaSuccess))
+                      cudaMemset(D.samples, 0, 2 * sizeof(unsigned long long)) != cudaSuccess))
     rc = FN_ECUDA;
   if (rc != FN_OK) {
     fn_planner_destroy(pl);
     return rc;
   }
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < 10; ++i)
     if (cudaEventCreate(&pl->ev[i]) != cudaSuccess) {
       fn_planner_destroy(pl);
       return FN_ECUDA;
@@ -932,15 +1362,14 @@ static fn_status enqueue_iteration(fn_planner* pl, unsigned flags, cudaStream_t 
     }
   }
   mark(3);
-  plan_edge_variant(pl->edge_variant)<<<pl->edge_blocks, 32 * PL_EDGE_WARPS, 0, st>>>(
-      D, pl->arm, pl->grid);
-  mark(4);
-  k_plan_attach<<<P, PL_ATTACH_THREADS, 0, st>>>(D);
-  mark(5);
-  if (flags & FN_PLAN_PRUNE) k_plan_prune<<<P, PL_ATTACH_THREADS, 0, st>>>(D, pl->arm);
+  enqueue_edges(pl, pl->edge_variant, pl->edge_blocks, st, mark);
   mark(6);
-  k_plan_output<<<(P + 127) / 128, 128, 0, st>>>(D);
+  k_plan_attach<<<P, PL_ATTACH_THREADS, 0, st>>>(D);
   mark(7);
+  if (flags & FN_PLAN_PRUNE) k_plan_prune<<<P, PL_ATTACH_THREADS, 0, st>>>(D, pl->arm);
+  mark(8);
+  k_plan_output<<<(P + 127) / 128, 128, 0, st>>>(D);
+  mark(9);
   if (cudaMemcpyAsync(pl->h_out, D.out, sizeof(fn_rendezvous_t) * P, cudaMemcpyDeviceToHost, st) !=
       cudaSuccess)
     return FN_ECUDA;
@@ -966,11 +1395,11 @@ extern "C" fn_status fn_plan_iteration(fn_planner_t* pl, const fn_problem_t* pro
 }
 
 // durations (ms) of the last fn_plan_iteration's phases, measured with CUDA
-// events on its stream: schedule, sample, parents, edges, attach, prune, output
+// events on its stream
 extern "C" fn_status fn_planner_phase_ms(fn_planner_t* pl, float* ms) {
   if (!pl || !ms) return FN_EINVAL;
   if (!pl->timing) return FN_EINVAL;
-  for (int i = 0; i < 7; ++i)
+  for (int i = 0; i < 9; ++i)
     if (cudaEventElapsedTime(&ms[i], pl->ev[i], pl->ev[i + 1]) != cudaSuccess) return FN_ECUDA;
   return FN_OK;
 }
@@ -1051,14 +1480,15 @@ extern "C" fn_status fn_planner_get_candidates(fn_planner_t* pl, int p, float* s
   return ok ? FN_OK : FN_ECUDA;
 }
 
-// work counter of the edge kernel (torque evaluations since the last reset)
+// work counters of the edge kernels (torque evaluations since the last
+// reset): count[0] probe, count[1] verify
 extern "C" fn_status fn_planner_sample_count(fn_planner_t* pl, unsigned long long* count,
                                              int reset) {
   if (!pl || !count) return FN_EINVAL;
-  if (cudaMemcpy(count, pl->D.samples, sizeof(unsigned long long), cudaMemcpyDeviceToHost) !=
+  if (cudaMemcpy(count, pl->D.samples, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost) !=
       cudaSuccess)
     return FN_ECUDA;
-  if (reset && cudaMemset(pl->D.samples, 0, sizeof(unsigned long long)) != cudaSuccess)
+  if (reset && cudaMemset(pl->D.samples, 0, 2 * sizeof(unsigned long long)) != cudaSuccess)
     return FN_ECUDA;
   return FN_OK;
 }
@@ -1107,9 +1537,8 @@ extern "C" fn_status fn_planner_autotune(fn_planner_t* pl, const fn_problem_t* p
     const int blocks = pl->cfg.edge_blocks > 0 ? pl->cfg.edge_blocks : plan_edge_blocks(pl, v);
     float tot = 0.f;
     for (int r = 0; r <= reps; ++r) {
-      k_plan_schedule<<<1, 32, 0, st>>>(D);  // resets the work queue
       cudaEventRecord(pl->ev[0], st);
-      plan_edge_variant(v)<<<blocks, 32 * PL_EDGE_WARPS, 0, st>>>(D, pl->arm, pl->grid);
+      enqueue_edges(pl, v, blocks, st, [](int) {});
       cudaEventRecord(pl->ev[1], st);
       if (cudaEventSynchronize(pl->ev[1]) != cudaSuccess) return FN_ECUDA;
       float ms = 0.f;

@@ -58,7 +58,7 @@ def _bind():
     L.fn_plan_replay.argtypes = [vp, vp, i32, vp, vp]
     L.fn_planner_get_tree.argtypes = [vp, i32, vp, vp, vp, vp, vp, C.POINTER(C.c_int), i32]
     L.fn_planner_get_candidates.argtypes = [vp, i32, vp, vp, vp, vp, i32]
-    L.fn_planner_sample_count.argtypes = [vp, C.POINTER(C.c_ulonglong), i32]
+    L.fn_planner_sample_count.argtypes = [vp, vp, i32]
     L.fn_planner_phase_ms.argtypes = [vp, vp]
     L.fn_planner_autotune.argtypes = [vp, vp, i32, C.c_uint, i32, vp, vp, vp]
     for n in ("fn_planner_create", "fn_planner_destroy", "fn_planner_reset", "fn_planner_load_tree",
@@ -213,15 +213,17 @@ class Planner:
               "fn_planner_autotune")
         return chosen.value, [float(x) for x in ms]
 
-    PHASES = ("schedule", "sample", "parents", "edges", "attach", "prune", "output")
+    PHASES = ("schedule", "sample", "parents", "edge_prep", "probe", "verify", "attach",
+              "prune", "output")
 
     def phase_ms(self):
-        ms = (C.c_float * 7)()
+        ms = (C.c_float * 9)()
         check(lib().fn_planner_phase_ms(self.h, ms), "fn_planner_phase_ms")
         return dict(zip(self.PHASES, [float(x) for x in ms]))
 
     def sample_count(self, reset=False):
-        c = C.c_ulonglong()
-        check(lib().fn_planner_sample_count(self.h, C.byref(c), int(bool(reset))),
+        """Torque evaluations of the edge kernels: dict(probe=..., verify=...)."""
+        c = (C.c_ulonglong * 2)()
+        check(lib().fn_planner_sample_count(self.h, c, int(bool(reset))),
               "fn_planner_sample_count")
-        return int(c.value)
+        return {"probe": int(c[0]), "verify": int(c[1])}
