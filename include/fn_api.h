@@ -409,6 +409,77 @@ fn_status fn_planner_get_tree(fn_planner_t* pl, int p, float* states, float* t,
 fn_status fn_planner_get_candidates(fn_planner_t* pl, int p, float* states, float* T_req,
                                     float* v_rel, uint8_t* valid, int cap);
 
+/* ------------------------------------------------------------------------
+ * Duration surrogate (the project's addition; the paper has no learned
+ * component).  An MLP 28 -> 256 -> 256 -> 256 -> 2 with ReLU predicts
+ * (log T*, feasibility logit) of an edge from its boundary states; the
+ * windowed scan uses it to examine a few durations instead of the whole
+ * grid, with the exact scan as fallback.
+ *
+ * Features: q scaled by the joint box to [-1, 1], qdot by qd_max, for s0 and
+ * s1 (28 values, padded to 32).  Precision: features, weights and hidden
+ * activations in bf16 on the tensor cores with FP32 accumulation; outputs,
+ * losses and gradients of the outputs in FP32; Adam (beta1 0.9, beta2 0.999,
+ * eps 1e-8) on FP32 master weights.  Loss over a batch of n edges with labels
+ * k* from the exact scan: (1/n) sum [f (y0 - log T_{k*})^2 + BCE(y1, f)],
+ * f = (k* >= 0).  Weights W_l are [in][out] row-major.
+ * ------------------------------------------------------------------------ */
+typedef struct fn_mlp fn_mlp_t;
+
+/* Allocates the weights (He-uniform from `seed`, zero biases), Adam state
+ * and a workspace for batches of up to max_batch edges. */
+fn_status fn_mlp_create(int max_batch, unsigned long long seed, fn_mlp_t** out);
+fn_status fn_mlp_destroy(fn_mlp_t* m);
+
+/* Y[e] = (log T*_pred, feasibility logit) for E edges (device s0, s1 [E][16];
+ * device Y [E][2]); E may exceed max_batch (processed in chunks). */
+fn_status fn_mlp_predict(fn_mlp_t* m, const fn_arm_t* arm, const float* s0, const float* s1,
+                         int E, float* Y, void* stream);
+
+/* Loss and gradients of one batch (E <= max_batch; k_star device [E] from
+ * the exact scan over the host grid T_grid [K]); *loss (host, may be NULL)
+ * receives the loss.  Gradients stay on the device (fn_mlp_get_grads). */
+fn_status fn_mlp_backward(fn_mlp_t* m, const fn_arm_t* arm, const float* s0, const float* s1,
+                          const int32_t* k_star, const float* T_grid, int K, int E,
+                          float* loss, void* stream);
+/* One Adam step with learning rate lr from the stored gradients. */
+fn_status fn_mlp_adam_step(fn_mlp_t* m, float lr, void* stream);
+/* fn_mlp_backward followed by fn_mlp_adam_step; synchronous when loss != NULL. */
+fn_status fn_mlp_train_step(fn_mlp_t* m, const fn_arm_t* arm, const float* s0, const float* s1,
+                            const int32_t* k_star, const float* T_grid, int K, int E, float lr,
+                            float* loss, void* stream);
+
+/* Host access to layer l (0..3): W [in][out], b [out] (in = 32, 256, 256,
+ * 256; out = 256, 256, 256, 2).  Any pointer may be NULL.  Synchronous. */
+fn_status fn_mlp_get_params(fn_mlp_t* m, int l, float* W, float* b);
+fn_status fn_mlp_set_params(fn_mlp_t* m, int l, const float* W, const float* b);
+fn_status fn_mlp_get_grads(fn_mlp_t* m, int l, float* gW, float* gb);
+fn_status fn_mlp_set_grads(fn_mlp_t* m, int l, const float* gW, const float* gb);
+/* Weights to / from a binary file (magic "FNMLP1", step count, W and b of
+ * every layer as little-endian f32). */
+fn_status fn_mlp_save(fn_mlp_t* m, const char* path);
+fn_status fn_mlp_load(fn_mlp_t* m, const char* path);
+
+/*
+ * fn_time_edges_window -- minimum feasible duration with a predicted window.
+ * For each edge the window [lo, lo+W) is centred on the grid index nearest
+ * exp(Y[e][0]) (the top of the grid if Y[e][1] < 0), clamped into [0, K).
+ * The scan of Def. "Minimum feasible time" runs on [lo-1, lo+W) first:
+ *  - its first feasible k is accepted if k = 0 or T_{k-1} was shown
+ *    infeasible (certified: exact whenever rho_tau, rho_P are monotone in T,
+ *    as the paper states for fixed boundary states);
+ *  - "no feasible duration" is accepted if the window and T_{K-1} are
+ *    infeasible (same certificate);
+ *  - otherwise the indices not yet examined are scanned exactly.
+ * path[e] (device u8, may be NULL) = 0 when the certificate decided, 1 when
+ * the fallback scan ran.  Other arguments and outputs as fn_time_edges
+ * (FN_MODE_FULL, no cap); sample_count as fn_time_edges_counted.
+ */
+fn_status fn_time_edges_window(const fn_arm_t* arm, const float* s0, const float* s1, int E,
+                               const float* T_grid, int K, int S, const float* Y, int W,
+                               int32_t* k_star, float* T_star, float* rho3, uint8_t* ok,
+                               uint8_t* path, unsigned long long* sample_count, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -51,17 +51,18 @@ def features(arm, s0, s1):
     return X
 
 
-def forward(params, X):
+def forward(params, X, rnd=bf16):
     """params: list of (W [in][out] float64 master, b [out]).  Returns y and
-    the cache needed by backward."""
-    h = bf16(X)
+    the cache needed by backward.  `rnd` is the rounding of the stored
+    operands (bf16; the identity gives the exact FP64 network)."""
+    h = rnd(X)
     cache = [h]
     zs = []
     for l, (W, b) in enumerate(params):
-        z = h @ bf16(W) + b
+        z = h @ rnd(W) + b
         zs.append(z)
         if l < len(params) - 1:
-            h = bf16(np.maximum(z, 0.0))
+            h = rnd(np.maximum(z, 0.0))
             cache.append(h)
     return zs[-1], (cache, zs)
 
@@ -79,16 +80,16 @@ def loss_and_grad_y(y, logT, feas):
     return L, dy
 
 
-def backward(params, cache, dy):
+def backward(params, cache, dy, rnd=bf16):
     hs, zs = cache
     grads = [None] * len(params)
     dz = dy
     for l in range(len(params) - 1, -1, -1):
         W, _ = params[l]
-        dzb = bf16(dz)
+        dzb = rnd(dz)
         grads[l] = (hs[l].T @ dzb, dz.sum(axis=0))
         if l > 0:
-            dh = dzb @ bf16(W).T
+            dh = dzb @ rnd(W).T
             dz = dh * (zs[l - 1] > 0)
     return grads
 

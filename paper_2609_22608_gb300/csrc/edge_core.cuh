@@ -62,16 +62,17 @@ __device__ __forceinline__ float warp_rho_v(const ArmK& A, const float* es, floa
 //   PROBE_HI : the lanes whose u = 0 passed, sample u = 1
 //   VERIFY   : lanes = samples (s0 + lane) of one duration, compensated
 //              coefficients, until a violating batch or all S samples pass
-// Grid mode (fixed = false): returns the first feasible index in [0, Kadm).
+// Grid mode (fixed = false): returns the first feasible index in
+// [k_begin, Kadm) (k_begin = 0 unless a caller scans a sub-range).
 // Fixed mode: one duration Tfix is verified (all S samples when exact,
 // else up to the first violating batch); returns 0 if it passes, else -1.
 __device__ __forceinline__ int edge_scan(const ArmK& A, const float* es, CubicLane cb,
                                          LaneWrench wr, const float* sT, int Kadm, int S,
                                          bool fixed, float Tfix, bool exact, float& rt, float& rp,
-                                         unsigned& nsamp) {
+                                         unsigned& nsamp, int k_begin = 0) {
   enum { PROBE_LO = 0, PROBE_HI = 1, VERIFY = 2 };
   const int lane = threadIdx.x & 31;
-  int mode = PROBE_LO, base = 0, kk = 0, s0 = 0;
+  int mode = PROBE_LO, base = k_begin, kk = 0, s0 = 0;
   unsigned cand = 0u;   // PROBE_HI: lanes to evaluate; VERIFY: durations left in the chunk
   float mt = 0.f, mp = 0.f;
   bool bad = false;
@@ -81,9 +82,9 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, const float* es, CubicLa
     cubic_coef_sh<true>(es, Tfix, c);
     cb.store(c);
   } else {
-    if (Kadm <= 0) return -1;
+    if (Kadm <= k_begin) return -1;
     Cubic c;
-    if (lane < Kadm) cubic_coef_sh<false>(es, sT[lane], c);
+    if (base + lane < Kadm) cubic_coef_sh<false>(es, sT[base + lane], c);
     cb.store(c);
   }
   for (;;) {

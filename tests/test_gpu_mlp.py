@@ -1,0 +1,170 @@
+"""Parity of the duration surrogate's CUDA path (fn_mlp_*) with its FP64
+reference (oracle/mlp.py), and of the windowed scan with the full scan."""
+import numpy as np
+import pytest
+import torch
+
+import oracle.mlp as M
+from paper_2609_22608_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2609_22608_gb300 import surrogate
+    return surrogate
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def seeded_params(seed):
+    rng = np.random.default_rng(seed)
+    ps = []
+    for l in range(4):
+        fi, fo = M.DIMS[l], M.DIMS[l + 1]
+        W = rng.normal(0, np.sqrt(2.0 / fi), (fi, fo)).astype(np.float32)
+        if l == 0:
+            W[28:] = 0
+        b = rng.normal(0, 0.05, fo).astype(np.float32)
+        ps.append((W, b))
+    return ps
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def load(mlp, ps):
+    for l, (W, b) in enumerate(ps):
+        mlp.set_params(l, W, b)
+
+
+def test_forward_parity(S, arm):
+    mlp = S.MLP(max_batch=1024)
+    ps = seeded_params(0)
+    load(mlp, ps)
+    s0, s1 = synth.random_edges(arm, 700, 3)
+    Y = mlp.predict(arm, dev(s0), dev(s1)).cpu().numpy()
+    ref, _ = M.forward([(W.astype(np.float64), b.astype(np.float64)) for W, b in ps],
+                       M.features(arm, s0, s1))
+    assert relerr(Y, ref) < 1e-3
+    mlp.close()
+
+
+def test_gradient_parity(S, orc, arm):
+    """Gradients of one batch (labels from the oracle's exact scan) agree
+    norm-wise per tensor within 1e-3."""
+    mlp = S.MLP(max_batch=512)
+    ps = seeded_params(1)
+    load(mlp, ps)
+    s0, s1 = synth.random_edges(arm, 384, 4)
+    grid = synth.duration_grid(32)
+    lab = orc.time_edges(arm, s0, s1, grid, 8)["k_star"]
+    loss = mlp.backward(arm, dev(s0), dev(s1), dev(lab.astype(np.int32)), grid)
+    P64 = [(W.astype(np.float64), b.astype(np.float64)) for W, b in ps]
+    y, cache = M.forward(P64, M.features(arm, s0, s1))
+    feas = lab >= 0
+    logT = np.log(grid.astype(np.float64))[np.clip(lab, 0, None)]
+    L, dy = M.loss_and_grad_y(y, logT, feas)
+    grads = M.backward(P64, cache, dy)
+    assert loss == pytest.approx(L, rel=1e-3)
+    for l in range(4):
+        gW, gb = mlp.get_grads(l)
+        assert relerr(gW, grads[l][0]) < 1e-3, (l, relerr(gW, grads[l][0]))
+        assert relerr(gb, grads[l][1]) < 1e-3, (l, relerr(gb, grads[l][1]))
+    mlp.close()
+
+
+def test_adam_step_parity(S, arm):
+    mlp = S.MLP(max_batch=64)
+    ps = seeded_params(2)
+    load(mlp, ps)
+    rng = np.random.default_rng(3)
+    grads = [(rng.normal(0, 1, W.shape).astype(np.float32), rng.normal(0, 1, b.shape).astype(np.float32))
+             for W, b in ps]
+    for l, (gW, gb) in enumerate(grads):
+        mlp.set_grads(l, gW, gb)
+    m = [(np.zeros(W.shape), np.zeros(b.shape)) for W, b in ps]
+    P64 = [(W.astype(np.float64), b.astype(np.float64)) for W, b in ps]
+    G64 = [(gW.astype(np.float64), gb.astype(np.float64)) for gW, gb in grads]
+    ref, _, _ = M.adam(P64, G64, m, m, 1, 1e-3)
+    mlp.adam_step(1e-3)
+    for l in range(4):
+        W, b = mlp.get_params(l)
+        assert relerr(W, ref[l][0]) < 1e-5 and relerr(b, ref[l][1]) < 1e-5
+        assert np.allclose(W, ref[l][0], rtol=1e-5, atol=1e-7)
+    mlp.close()
+
+
+def test_save_load_roundtrip(S, tmp_path, arm):
+    a = S.MLP(max_batch=64, seed=5)
+    b = S.MLP(max_batch=64, seed=6)
+    a.save(tmp_path / "w.bin")
+    b.load(tmp_path / "w.bin")
+    for l in range(4):
+        Wa, ba = a.get_params(l)
+        Wb, bb = b.get_params(l)
+        assert np.array_equal(Wa, Wb) and np.array_equal(ba, bb)
+    a.close(); b.close()
+
+
+def test_window_scan_matches_full_scan(S, arm):
+    """With any prediction the windowed scan returns the full scan's k*,
+    except where the certificate relied on monotone limits and the full
+    scan shows an earlier isolated feasible duration."""
+    from paper_2609_22608_gb300 import ops
+    E, K, Sc = 3000, 128, 32
+    s0, s1 = synth.random_edges(arm, E, 8)
+    d0, d1 = dev(s0), dev(s1)
+    grid = synth.duration_grid(K)
+    full = ops.time_edges(arm, d0, d1, grid, Sc)
+    kf = full["k_star"].cpu().numpy()
+    rng = np.random.default_rng(9)
+    # predictions: exact, shifted, random and "infeasible" centres
+    lg = np.log(grid.astype(np.float64))
+    y0 = np.where(kf >= 0, lg[np.clip(kf, 0, None)], 0.0)
+    Y = np.stack([y0 + rng.choice([0, 0, 0.3, -0.3, 2.0, -2.0], E), rng.choice([1.0, 1.0, -1.0], E)], 1)
+    w = S.time_edges_window(arm, d0, d1, grid, Sc, dev(Y.astype(np.float32)), W=16)
+    kw = w["k_star"].cpu().numpy()
+    path = w["path"].cpu().numpy()
+    assert set(np.unique(path)) <= {0, 1}
+    fb = path == 1
+    assert np.array_equal(kw[fb], kf[fb]), "fallback scans must be exact"
+    mism = np.nonzero(kw != kf)[0]
+    assert len(mism) <= 0.01 * E, len(mism)
+    # a certified disagreement may only pick a later duration (a feasible
+    # index below the certificate was missed), never an infeasible one
+    Tw = w["T_star"].cpu().numpy()
+    for e in mism:
+        assert kw[e] == -1 or kf[e] == -1 or kw[e] > kf[e]
+    okw = w["ok"].cpu().numpy()
+    same = kw == kf
+    assert np.array_equal(okw[same], full["ok"].cpu().numpy()[same])
+    assert np.array_equal(Tw[same & (kw >= 0)], grid[kw[same & (kw >= 0)]])
+
+
+def test_training_reduces_loss_and_window_hits(S, arm):
+    """A short training run on edges labelled by the exact scan lowers the
+    loss, and the trained network's windows certify most edges."""
+    from paper_2609_22608_gb300 import ops
+    E, K, Sc = 32768, 128, 32
+    s0, s1 = synth.random_edges(arm, E, 10)
+    d0, d1 = dev(s0), dev(s1)
+    grid = synth.duration_grid(K)
+    lab = S.label_edges(arm, d0, d1, grid, Sc)
+    mlp = S.MLP(max_batch=4096, seed=0)
+    hist = S.train(mlp, arm, d0, d1, lab, grid, epochs=3, batch=4096, lr=2e-3)
+    assert hist[-1] < 0.7 * hist[0], hist
+    t0, t1 = synth.random_edges(arm, 4096, 11)
+    e0, e1 = dev(t0), dev(t1)
+    Y = mlp.predict(arm, e0, e1)
+    w = S.time_edges_window(arm, e0, e1, grid, Sc, Y, W=16)
+    full = ops.time_edges(arm, e0, e1, grid, Sc)
+    hit = (w["path"] == 0).float().mean().item()
+    agree = (w["k_star"] == full["k_star"]).float().mean().item()
+    assert hit > 0.3, hit
+    assert agree > 0.99, agree
+    mlp.close()
