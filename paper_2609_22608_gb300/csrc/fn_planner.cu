@@ -925,33 +925,38 @@ __global__ void __launch_bounds__(PL_ATTACH_THREADS) k_plan_attach(PlanDev D) {
 // ---------------------------------------------------------------------------
 // prune (Eq. (reach)): one block per problem
 // ---------------------------------------------------------------------------
+// Eq. (reach) for every node of every problem (one thread per node): keep
+// the root and the nodes that can reach the object by t_best
+__global__ void __launch_bounds__(128) k_plan_reach(PlanDev D, ArmK A) {
+  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = (int)(gid / D.NC);
+  const int i = (int)(gid - (long)p * D.NC);
+  if (p >= D.P || i >= D.n_nodes[p]) return;
+  const long nb = (long)p * D.NC;
+  bool keep = i == 0;
+  if (!keep) {
+    const fn_problem_t& P = D.prob[p];
+    float q[7];
+#pragma unroll
+    for (int j = 0; j < 7; ++j) q[j] = D.st[(nb + i) * 16 + j];
+    const int g = reach_index(A, P, q, D.t[nb + i], D.G);
+    if (g >= 0) {
+      const float Tg = fmaf((float)g, (P.t_fall - P.t_enter) / (float)(D.G - 1), P.t_enter);
+      keep = Tg <= D.inc[p].t_best;
+    }
+  }
+  D.alive[nb + i] = keep ? 1 : 0;
+  D.ptr[nb + i] = D.par[nb + i];
+}
+
 __global__ void __launch_bounds__(PL_ATTACH_THREADS) k_plan_prune(PlanDev D, ArmK A) {
   __shared__ int sh[PL_ATTACH_THREADS];
   __shared__ int s_flag;
   const int p = blockIdx.x;
-  const fn_problem_t& P = D.prob[p];
   const int N = D.n_nodes[p];
   const long nb = (long)p * D.NC;
   const Incumbent in = D.inc[p];
-  const float tb = in.t_best;
-  // keep mask: root, the incumbent's path, and nodes that can reach the
-  // object by t_best
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    bool keep = i == 0;
-    if (!keep) {
-      float q[7];
-#pragma unroll
-      for (int j = 0; j < 7; ++j) q[j] = D.st[(nb + i) * 16 + j];
-      const int g = reach_index(A, P, q, D.t[nb + i], D.G);
-      if (g >= 0) {
-        const float Tg = fmaf((float)g, (P.t_fall - P.t_enter) / (float)(D.G - 1), P.t_enter);
-        keep = Tg <= tb;
-      }
-    }
-    D.alive[nb + i] = keep ? 1 : 0;
-    D.ptr[nb + i] = D.par[nb + i];
-  }
-  __syncthreads();
+  (void)A;
   if (threadIdx.x == 0) {
     for (int c = in.id; c > 0; c = D.par[nb + c]) D.alive[nb + c] = 1;
   }
@@ -1366,7 +1371,11 @@ static fn_status enqueue_iteration(fn_planner* pl, unsigned flags, cudaStream_t 
   mark(6);
   k_plan_attach<<<P, PL_ATTACH_THREADS, 0, st>>>(D);
   mark(7);
-  if (flags & FN_PLAN_PRUNE) k_plan_prune<<<P, PL_ATTACH_THREADS, 0, st>>>(D, pl->arm);
+  if (flags & FN_PLAN_PRUNE) {
+    const long nn = (long)P * D.NC;
+    k_plan_reach<<<(unsigned)((nn + 127) / 128), 128, 0, st>>>(D, pl->arm);
+    k_plan_prune<<<P, PL_ATTACH_THREADS, 0, st>>>(D, pl->arm);
+  }
   mark(8);
   k_plan_output<<<(P + 127) / 128, 128, 0, st>>>(D);
   mark(9);
