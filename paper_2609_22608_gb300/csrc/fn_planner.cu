@@ -46,6 +46,7 @@ struct Sched {
   unsigned int queue_head;
   int n_items;        // probe items of the packed edge phase
   int n_pend[2];      // lengths of the two pending-edge lists
+  int n_surv;         // probe survivors appended (may exceed surv_cap)
   int n_free_edges;   // free edges of all problems (the queue's first part)
   int n_edges;        // all edges
   int knn_items;      // (problem, query tile, split) items
@@ -102,7 +103,8 @@ struct PlanDev {  // device pointers, passed by value to the kernels
   int32_t* cur_k;     // [E] duration under verification (grid index; 0 for goals)
   uint32_t* fail;     // [E] a sample of cur_k violated a limit
   int32_t* pend;      // [2][E] edges pending verification (ping-pong lists)
-  int Emax, Kmax;
+  int2* surv;         // [surv_cap] probe survivors (edge, grid index)
+  int Emax, Kmax, surv_cap;
 };
 
 struct GridKP {
@@ -555,7 +557,64 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_probe(PlanDev
       pass = pass && a <= 1.f && b <= 1.f;
     }
     nsamp += 2u * __popc(__ballot_sync(0xffffffffu, live));
-    if (pass) atomicOr(&D.mask[8L * e + (k >> 5)], 1u << (k & 31));
+    const unsigned pm = __ballot_sync(0xffffffffu, pass);
+    int slot0 = 0;
+    if (lane == 0 && pm) slot0 = atomicAdd(&D.sched->n_surv, __popc(pm));
+    slot0 = __shfl_sync(0xffffffffu, slot0, 0);
+    if (pass) {
+      atomicOr(&D.mask[8L * e + (k >> 5)], 1u << (k & 31));
+      const int slot = slot0 + __popc(pm & ((1u << lane) - 1u));
+      if (slot < D.surv_cap) D.surv[slot] = make_int2(e, k);
+    }
+  }
+  if (D.samples && lane == 0 && nsamp) atomicAdd(D.samples + 0, (unsigned long long)nsamp);
+}
+
+// Mid-probe: lanes = (survivor, interior probe sample) items; a violation
+// at any of the four interior points drops the duration from the edge's
+// survivor mask before the (much costlier) full verification.  Survivors
+// beyond the list's capacity are simply not filtered.
+template <int MINB>
+__global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_mprobe(PlanDev D, ArmK A,
+                                                                          GridKP Gr) {
+  __shared__ float sT[FN_MAX_GRID];
+  __shared__ float sCoef[PL_EDGE_WARPS][FN_CUBIC_WORDS * 32];
+  __shared__ float sWr[PL_EDGE_WARPS][FN_WRENCH_WORDS * 32];
+  for (int i = threadIdx.x; i < D.K; i += blockDim.x) sT[i] = Gr.T[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const CubicLane cb{&sCoef[w][lane]};
+  const LaneWrench wr{&sWr[w][lane]};
+  const int ns = min(D.sched->n_surv, D.surv_cap);
+  const int n = D.S > 2 ? ns * FN_MID_PROBES : 0;
+  unsigned nsamp = 0;
+  const long W = (long)gridDim.x * PL_EDGE_WARPS;
+  for (long c = (long)blockIdx.x * PL_EDGE_WARPS + w; c * 32 < n; c += W) {
+    const int i = (int)(c * 32) + lane;
+    const bool live = i < n;
+    int e = 0, k = 0, j = 0;
+    if (live) {
+      const int2 sv = D.surv[i / FN_MID_PROBES];
+      j = i % FN_MID_PROBES;
+      e = sv.x;
+      k = sv.y;
+      const bool goal = D.e_j[e] & 0x80;
+      const float T = goal ? D.e_Tp[e] : sT[k];
+      const int p = D.e_ci[e] / D.BM;
+      const float* r0 = D.st + ((long)p * D.NC + D.e_par[e]) * 16;
+      const float* r1 = D.cand + (long)D.e_ci[e] * 16;
+      float es[32];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) { es[m] = __ldg(r0 + m); es[16 + m] = __ldg(r1 + m); }
+      Cubic cc;
+      cubic_coef_sh<false>(es, T, cc);
+      cb.store(cc);
+    }
+    float a = 0.f, b = 0.f;
+    if (live) sample_ratios(A, cb, sample_u(mid_probe_index(j, D.S), D.S), a, b, wr);
+    nsamp += __popc(__ballot_sync(0xffffffffu, live));
+    if (live && !(a <= 1.f && b <= 1.f))
+      atomicAnd(&D.mask[8L * e + (k >> 5)], ~(1u << (k & 31)));
   }
   if (D.samples && lane == 0 && nsamp) atomicAdd(D.samples + 0, (unsigned long long)nsamp);
 }
@@ -716,7 +775,8 @@ __global__ void k_plan_vselect(PlanDev D, ArmK A, GridKP Gr, int list) {
 
 __global__ void k_plan_vclear(PlanDev D, int list) {
   if (threadIdx.x == 0) {
-    D.sched->n_pend[list] = 0;
+    if (list >= 0) D.sched->n_pend[list] = 0;
+    else D.sched->n_surv = 0;
     D.sched->queue_head = 0u;
   }
 }
@@ -1097,6 +1157,14 @@ static PlanEdgeKernel plan_probe_variant(int v) {
     default: return k_plan_probe<4>;
   }
 }
+static PlanEdgeKernel plan_mprobe_variant(int v) {
+  switch (v) {
+    case 0: return k_plan_mprobe<2>;
+    case 1: return k_plan_mprobe<3>;
+    default: return k_plan_mprobe<4>;
+  }
+}
+
 typedef void (*PlanStageKernel)(PlanDev, ArmK, GridKP, int);
 static PlanStageKernel plan_vstage_variant(int v) {
   switch (v) {
@@ -1149,9 +1217,11 @@ static void enqueue_edges(fn_planner* pl, int v, int blocks, cudaStream_t st, Ma
   k_plan_eprep<<<eb, PL_SCAN, 0, st>>>(D, pl->grid);
   k_plan_escan<<<1, PL_SCAN, 0, st>>>(D);
   k_plan_vclear<<<1, 32, 0, st>>>(D, 0);
+  k_plan_vclear<<<1, 32, 0, st>>>(D, -1);
   k_plan_expand<<<4 * num_sms(), 256, 0, st>>>(D);
   mark(4);
   plan_probe_variant(v)<<<blocks, 32 * PL_EDGE_WARPS, 0, st>>>(D, pl->arm, pl->grid);
+  plan_mprobe_variant(v)<<<blocks, 32 * PL_EDGE_WARPS, 0, st>>>(D, pl->arm, pl->grid);
   mark(5);
   const int tb = 2 * num_sms();
   k_plan_vinit<<<tb, 256, 0, st>>>(D);
@@ -1231,6 +1301,8 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
   A_(D.cur_k, (size_t)D.Emax);
   A_(D.fail, (size_t)D.Emax);
   A_(D.pend, (size_t)D.Emax * 2);
+  D.surv_cap = (int)std::min<long>((long)D.Emax * 16, 1L << 26);
+  A_(D.surv, (size_t)D.surv_cap);
 #undef A_
   if (rc == FN_OK) {
     if (cudaMallocHost(&pl->h_prob, P * sizeof(fn_problem_t)) != cudaSuccess ||
