@@ -257,7 +257,7 @@ fn_status fn_make_edges(const float* tree, const float* t_node, const float* can
  * struct of arrays; every buffer is sized here, once). */
 typedef struct {
   int P;              /* independent problems (1..1024)                      */
-  int n_cap;          /* tree capacity per problem (2..1<<22)                */
+  int n_cap;          /* tree capacity per problem (2..1<<22; P*n_cap <= 2^30) */
   int b_max;          /* largest candidate batch per problem (1..1<<16)      */
   int k;              /* parents per candidate incl. the root (1..17)        */
   int K;              /* duration grid size (1..FN_MAX_GRID)                 */
@@ -408,6 +408,12 @@ fn_status fn_planner_get_tree(fn_planner_t* pl, int p, float* states, float* t,
  * every free candidate).  Synchronous. */
 fn_status fn_planner_get_candidates(fn_planner_t* pl, int p, float* states, float* T_req,
                                     float* v_rel, uint8_t* valid, int cap);
+/* Copy problem p's last parent lists to host: nn [B][k-1] int32, row b the
+ * tree indices of candidate b's k-1 nearest non-root nodes under the
+ * distance of Sec. IV-E "Parents" (ascending, ties to the lower index; -1
+ * where the tree has fewer nodes).  The root, parent slot 0, is implicit.
+ * Rows beyond the batch of the last iteration are stale.  Synchronous. */
+fn_status fn_planner_get_parents(fn_planner_t* pl, int p, int32_t* nn, int cap);
 
 /* ------------------------------------------------------------------------
  * Duration surrogate (the project's addition; the paper has no learned

@@ -31,6 +31,10 @@
 #include "knn_core.cuh"
 
 #define PL_NSPLIT_MAX 32
+#define PL_KNN_WARPS 4
+#define PL_KNN_QW 1                           // queries per warp
+#define PL_KNN_GROUP (PL_KNN_WARPS * PL_KNN_QW)
+#define PL_KNN_SPAN 4096                      // nodes per split (at least)
 #define PL_MAX_P 1024
 
 namespace fn {
@@ -54,6 +58,8 @@ struct Sched {
   int goal_off[PL_MAX_P + 1];
   int knn_off[PL_MAX_P + 1];
   int nsplit[PL_MAX_P];
+  int pack_lo[PL_MAX_P];      // first node of problem p to (re)pack into the mirror
+  int pack_off[PL_MAX_P + 1]; // flattened offsets of the nodes to pack
 };
 
 struct PlanDev {  // device pointers, passed by value to the kernels
@@ -105,6 +111,10 @@ struct PlanDev {  // device pointers, passed by value to the kernels
   int32_t* pend;      // [2][E] edges pending verification (ping-pong lists)
   int2* surv;         // [surv_cap] probe survivors (edge, grid index)
   int Emax, Kmax, surv_cap;
+  // parents: node mirror laid out for lane-contiguous loads (see knn_mirror_index)
+  float4* mir;        // [P][NB][7][32]
+  int32_t* packed;    // [P] leading nodes whose mirror entries are current
+  int NB;             // 64-node blocks per problem
 };
 
 struct GridKP {
@@ -133,6 +143,7 @@ __global__ void k_plan_reset(PlanDev D) {
   D.nu[n0] = 0.f;
   D.eT[n0] = 0.f;
   D.n_nodes[p] = 1;
+  D.packed[p] = 0;
   D.inc[p] = Incumbent{-1, -INFINITY, P.t_fall, 0};
   D.status[p] = 0;
 }
@@ -147,6 +158,7 @@ __global__ void k_plan_loaded(PlanDev D, int p, int n) {
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     D.n_nodes[p] = n;
+    D.packed[p] = 0;
     D.inc[p] = Incumbent{-1, -INFINITY, D.prob[p].t_fall, 0};
     D.status[p] = 0;
   }
@@ -158,7 +170,7 @@ __global__ void k_plan_loaded(PlanDev D, int p, int n) {
 __global__ void k_plan_schedule(PlanDev D) {
   if (threadIdx.x != 0) return;
   Sched* S = D.sched;
-  int fo = 0, go = 0, ko = 0;
+  int fo = 0, go = 0, ko = 0, po = 0;
   for (int p = 0; p < D.P; ++p) {
     const fn_problem_t& P = D.prob[p];
     const int B = min(max(P.batch, 0), D.BM);
@@ -170,13 +182,17 @@ __global__ void k_plan_schedule(PlanDev D) {
     go += G * D.KP;
     const int span = D.n_nodes[p] - 1;  // non-root nodes
     int ns = 1;
-    if (D.KN > 0 && span > 0) {
-      ns = min(PL_NSPLIT_MAX, max(1, span / KNN_TILE));
-    }
+    if (D.KN > 0 && span > 0) ns = min(PL_NSPLIT_MAX, (span + PL_KNN_SPAN - 1) / PL_KNN_SPAN);
     S->nsplit[p] = ns;
-    ko += (D.KN > 0 && span > 0) ? ((B + 127) / 128) * ns : 0;
+    ko += (D.KN > 0 && span > 0) ? ((B + PL_KNN_GROUP - 1) / PL_KNN_GROUP) * ns : 0;
     D.added[p] = 0;
+    const int lo = min(D.packed[p], D.n_nodes[p]);
+    S->pack_lo[p] = lo;
+    S->pack_off[p] = po;
+    po += D.n_nodes[p] - lo;
+    D.packed[p] = D.n_nodes[p];
   }
+  S->pack_off[D.P] = po;
   S->free_off[D.P] = fo;
   S->goal_off[D.P] = go;
   S->knn_off[D.P] = ko;
@@ -292,45 +308,128 @@ __global__ void __launch_bounds__(128) k_plan_sample_goal(PlanDev D, ArmK A) {
 }
 
 // ---------------------------------------------------------------------------
-// parents: (problem, query tile, split) items over all problems
+// parents: (problem, query group, split) items over all problems.  A warp
+// takes PL_KNN_QW queries and sweeps the split's nodes 64 at a time; the k best
+// (d, index) pairs live across lanes 0..KM-1 in ascending order, and only
+// nodes that beat the current k-th pair enter the list, one at a time (a
+// ballot finds them; a shuffle-up opens their slot).
 // ---------------------------------------------------------------------------
+
 template <int KM>
-__global__ void __launch_bounds__(128) k_plan_knn(PlanDev D) {
-  __shared__ float4 tile[KNN_TILE * 4];
+struct WarpTopK {
+  float d = INFINITY;                         // lane j < KM: j-th best
+  int i = 0x7fffffff;
+  float td = INFINITY;                        // the k-th best, on every lane
+  int ti = 0x7fffffff;
+  // Offer the candidates (cd, ci) of the lanes in m (each beat the k-th
+  // pair when m was formed): in lane order, a candidate still better than
+  // the current k-th pair takes its sorted slot and the tail shifts down.
+  // Branch-free in the candidate (a candidate that no longer qualifies
+  // gets pos = 32, which moves nothing).
+  __device__ __forceinline__ void insert(unsigned m, float cd, int ci) {
+    const int lane = threadIdx.x & 31;
+    while (m) {
+      const int src = __ffs(m) - 1;
+      m &= m - 1u;
+      const float nd = __shfl_sync(0xffffffffu, cd, src);
+      const int ni = __shfl_sync(0xffffffffu, ci, src);
+      const bool ok = knn_less(nd, ni, td, ti);
+      const unsigned lt = __ballot_sync(0xffffffffu, knn_less(d, i, nd, ni)) & ((1u << KM) - 1u);
+      const int pos = ok ? __popc(lt) : 32;
+      const float ud = __shfl_up_sync(0xffffffffu, d, 1);
+      const int ui = __shfl_up_sync(0xffffffffu, i, 1);
+      d = lane < pos ? d : (lane == pos ? nd : ud);
+      i = lane < pos ? i : (lane == pos ? ni : ui);
+      td = __shfl_sync(0xffffffffu, d, KM - 1);
+      ti = __shfl_sync(0xffffffffu, i, KM - 1);
+    }
+  }
+};
+
+// One warp per (query group, split): lane j takes nodes 2j and 2j+1 of each
+// 64-node block of the split from the mirror and scores both against the
+// warp's queries with paired FP32 operations (each half rounds exactly like the
+// scalar knn_dist: t = q - x, dq and dv accumulated in component order,
+// d = w dv + dq).
+template <int KM>
+__global__ void __launch_bounds__(32 * PL_KNN_WARPS) k_plan_knn(PlanDev D) {
   const Sched* S = D.sched;
   const int items = S->knn_items;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const float2 w2 = make_float2(D.w_vel, D.w_vel);
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     const int p = find_problem(S->knn_off, D.P, item);
     const int local = item - S->knn_off[p];
     const int ns = S->nsplit[p];
-    const int qt = local / ns, split = local - qt * ns;
+    const int g = local / ns, split = local - g * ns;
     const int B = min(max(D.prob[p].batch, 0), D.BM);
+    const int b0 = (g * PL_KNN_WARPS + w) * PL_KNN_QW;
+    const bool wact = b0 < B;                  // warp-uniform
     const int N = D.n_nodes[p];
     const int span = N - 1;
     const int per = (span + ns - 1) / ns;
     const int lo = 1 + split * per, hi = min(N, lo + per);
-    const int b = qt * 128 + threadIdx.x;
-    const bool active = b < B;
-    float qv[14];
-    if (active) load_query(reinterpret_cast<const float4*>(D.cand) + 4 * ((long)p * D.BM + b), qv);
-    else
-      for (int j = 0; j < 14; ++j) qv[j] = 0.f;
-    TopK<KM> top;
-    top.init();
-    knn_scan_range<KM>(reinterpret_cast<const float4*>(D.st) + 4L * p * D.NC, lo, hi, qv,
-                       D.w_vel, top, tile);
-    if (active) {
-      if (ns == 1) {
-        const long off = ((long)p * D.BM + b) * D.KN;
+    float2 q2[PL_KNN_QW][14];
 #pragma unroll
-        for (int j = 0; j < KM; ++j)
-          if (j < D.KN) D.nn[off + j] = top.i[j] == 0x7fffffff ? -1 : top.i[j];
-      } else {
-        const long off = (((long)p * PL_NSPLIT_MAX + split) * D.BM + b) * KM;
-        top.store(D.part_d + off, D.part_i + off, KM);
+    for (int a = 0; a < PL_KNN_QW; ++a) {
+      float qv[14];
+      load_query(reinterpret_cast<const float4*>(D.cand) + 4 * ((long)p * D.BM + min(b0 + a, B - 1)),
+                 qv);
+#pragma unroll
+      for (int c = 0; c < 14; ++c) q2[a][c] = make_float2(qv[c], qv[c]);
+    }
+    WarpTopK<KM> top[PL_KNN_QW];
+    const float4* mir = D.mir + (long)p * D.NB * 7 * 32 + lane;
+    const int blk0 = lo >> 6, blk1 = (hi + 63) >> 6;
+    float4 nx[7];   // the next mirror block, loaded one round ahead
+    if (wact) {
+#pragma unroll
+      for (int cc = 0; cc < 7; ++cc) nx[cc] = __ldg(mir + (blk0 * 7 + cc) * 32);
+    }
+    for (int blk = blk0; wact && blk < blk1; ++blk) {
+      float4 x[7];
+#pragma unroll
+      for (int cc = 0; cc < 7; ++cc) x[cc] = nx[cc];
+      const int bn = min(blk + 1, blk1 - 1);
+#pragma unroll
+      for (int cc = 0; cc < 7; ++cc) nx[cc] = __ldg(mir + (bn * 7 + cc) * 32);
+      const int n0 = blk * 64 + 2 * lane;
+      const bool v0 = n0 >= lo && n0 < hi, v1 = n0 + 1 >= lo && n0 + 1 < hi;
+      float2 d[PL_KNN_QW];
+#pragma unroll
+      for (int a = 0; a < PL_KNN_QW; ++a) {
+        float2 dq = make_float2(0.f, 0.f), dv = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < 14; ++c) {
+          const float4 v = x[c >> 1];
+          const float2 nv = (c & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+          const float2 t = __fadd2_rn(q2[a][c], nv);
+          if (c < 7) dq = __ffma2_rn(t, t, dq);
+          else dv = __ffma2_rn(t, t, dv);
+        }
+        d[a] = __ffma2_rn(w2, dv, dq);
+      }
+#pragma unroll
+      for (int a = 0; a < PL_KNN_QW; ++a) {
+        top[a].insert(__ballot_sync(0xffffffffu, v0 && knn_less(d[a].x, n0, top[a].td, top[a].ti)),
+                      d[a].x, n0);
+        top[a].insert(__ballot_sync(0xffffffffu, v1 && knn_less(d[a].y, n0 + 1, top[a].td, top[a].ti)),
+                      d[a].y, n0 + 1);
       }
     }
-    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < PL_KNN_QW; ++a) {
+      const int b = b0 + a;
+      if (!wact || b >= B || lane >= KM) continue;
+      const int id = top[a].i;
+      if (ns == 1) {
+        if (lane < D.KN) D.nn[((long)p * D.BM + b) * D.KN + lane] = id == 0x7fffffff ? -1 : id;
+      } else {
+        const long off = (((long)p * PL_NSPLIT_MAX + split) * D.BM + b) * KM + lane;
+        D.part_d[off] = top[a].d;
+        D.part_i[off] = id;
+      }
+    }
   }
 }
 
@@ -373,13 +472,42 @@ __global__ void __launch_bounds__(256) k_plan_knn_merge(PlanDev D) {
   }
 }
 
-// tree has a single node: no neighbours
-__global__ void k_plan_nn_empty(PlanDev D) {
+// Mirror of the tree for the parent search: node n sits in 64-node block
+// n / 64 at pair slot j = (n % 64) / 2, half h = n % 2; for component pair
+// cc (components 2cc, 2cc+1 of (q_1..q_7, qd_1..qd_7)) the float4
+// (x_2j[2cc], x_2j+1[2cc], x_2j[2cc+1], x_2j+1[2cc+1]) holds the values
+// negated, so that lane j loads its two nodes' component pairs with seven
+// 16-byte loads (512 contiguous bytes per warp instruction) and forms
+// q - x as q + (-x), exactly.
+__device__ __forceinline__ float* knn_mirror_slot(const PlanDev& D, int p, int n, int cc) {
+  const long f4 = (((long)p * D.NB + (n >> 6)) * 7 + cc) * 32 + ((n >> 1) & 31);
+  return reinterpret_cast<float*>(D.mir + f4) + (n & 1);
+}
+
+// parents prep: neighbour lists of single-node trees are empty; tree nodes
+// added (or moved) since the last iteration enter the mirror
+__global__ void k_plan_parents_prep(PlanDev D) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long stride = (long)gridDim.x * blockDim.x;
   const long n = (long)D.P * D.BM * D.KN;
-  if (i >= n) return;
-  const int p = (int)(i / ((long)D.BM * D.KN));
-  if (D.n_nodes[p] <= 1) D.nn[i] = -1;
+  for (long x = i; x < n; x += stride) {
+    const int p = (int)(x / ((long)D.BM * D.KN));
+    if (D.n_nodes[p] <= 1) D.nn[x] = -1;
+  }
+  const Sched* S = D.sched;
+  const int total = S->pack_off[D.P];
+  for (long x = i; x < total; x += stride) {
+    const int p = find_problem(S->pack_off, D.P, (int)x);
+    const int node = S->pack_lo[p] + (int)(x - S->pack_off[p]);
+    const float* r = D.st + ((long)p * D.NC + node) * 16;
+#pragma unroll
+    for (int cc = 0; cc < 7; ++cc) {
+      const int c0 = 2 * cc, c1 = 2 * cc + 1;
+      float* slot = knn_mirror_slot(D, p, node, cc);
+      slot[0] = -r[c0 < 7 ? c0 : c0 + 1];
+      slot[2] = -r[c1 < 7 ? c1 : c1 + 1];
+    }
+  }
 }
 
 #define PL_EDGE_WARPS 4
@@ -389,6 +517,35 @@ __global__ void k_plan_nn_empty(PlanDev D) {
 // items) -> verify (warp per edge, lanes = samples)
 // ---------------------------------------------------------------------------
 #define PL_SCAN 1024
+
+// exclusive prefix sum over a block of PL_SCAN threads (shuffles within the
+// warps, one shared pass across them); *total = the block's sum
+__device__ __forceinline__ int block_scan(int v, int* sh, int* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  __syncthreads();
+  if (lane == 31) sh[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int t = sh[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    sh[lane] = t;
+  }
+  __syncthreads();
+  *total = sh[31];
+  const int ex = (w > 0 ? sh[w - 1] : 0) + x - v;
+  __syncthreads();   // sh may be reused as soon as this returns
+  return ex;
+}
 
 // decode flat edge e (queue order: free edges of all problems, then goal
 // edges; parent-slot-major inside a problem) into (problem, candidate, slot)
@@ -411,7 +568,7 @@ __device__ __forceinline__ void decode_edge(const PlanDev& D, const Sched* S, in
 
 __global__ void __launch_bounds__(PL_SCAN) k_plan_eprep(PlanDev D, GridKP Gr) {
   __shared__ float sT[FN_MAX_GRID];
-  __shared__ int sh[PL_SCAN];
+  __shared__ int sh[32];
   for (int i = threadIdx.x; i < D.K; i += blockDim.x) sT[i] = Gr.T[i];
   __syncthreads();
   const Sched* S = D.sched;
@@ -455,38 +612,24 @@ __global__ void __launch_bounds__(PL_SCAN) k_plan_eprep(PlanDev D, GridKP Gr) {
     }
   }
   // block-local exclusive scan of the item counts
-  sh[threadIdx.x] = cnt;
-  __syncthreads();
-  for (int o = 1; o < PL_SCAN; o <<= 1) {
-    const int a = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
-    __syncthreads();
-    sh[threadIdx.x] += a;
-    __syncthreads();
-  }
-  if (e < E) D.e_cnt[e] = sh[threadIdx.x] - cnt;
-  if (threadIdx.x == PL_SCAN - 1) D.blk_off[blockIdx.x] = sh[PL_SCAN - 1];
+  int tot;
+  const int ex = block_scan(cnt, sh, &tot);
+  if (e < E) D.e_cnt[e] = ex;
+  if (threadIdx.x == 0) D.blk_off[blockIdx.x] = tot;
 }
 
 // exclusive scan of the per-block item totals (one block)
 __global__ void __launch_bounds__(PL_SCAN) k_plan_escan(PlanDev D) {
-  __shared__ int sh[PL_SCAN];
+  __shared__ int sh[32];
   Sched* S = D.sched;
   const int nb = (S->n_edges + PL_SCAN - 1) / PL_SCAN;
   int carry = 0;
   for (int base = 0; base < nb; base += PL_SCAN) {
     const int i = base + threadIdx.x;
     const int v = i < nb ? D.blk_off[i] : 0;
-    sh[threadIdx.x] = v;
-    __syncthreads();
-    for (int o = 1; o < PL_SCAN; o <<= 1) {
-      const int a = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
-      __syncthreads();
-      sh[threadIdx.x] += a;
-      __syncthreads();
-    }
-    if (i < nb) D.blk_off[i] = carry + sh[threadIdx.x] - v;
-    const int tot = sh[PL_SCAN - 1];
-    __syncthreads();
+    int tot;
+    const int ex = block_scan(v, sh, &tot);
+    if (i < nb) D.blk_off[i] = carry + ex;
     carry += tot;
   }
   if (threadIdx.x == 0) {
@@ -704,28 +847,25 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_vstage(PlanDe
   if (D.samples && lane == 0 && nsamp) atomicAdd(D.samples + 1, (unsigned long long)nsamp);
 }
 
-// per-thread end of an edge whose duration T passed: rho_v at T, then Clear
-__device__ __forceinline__ void finish_edge(const PlanDev& D, const ArmK& A, int e, float T) {
+// warp-wide end of an edge whose duration T passed (es: its two states
+// staged in shared memory): rho_v at T (lane = joint), the clearance samples
+// (lane = sample), then Clear
+__device__ __forceinline__ void finish_edge(const PlanDev& D, const ArmK& A, int e, float T,
+                                            const float* es) {
+  const int lane = threadIdx.x & 31;
   long ei;
   bool goal;
   edge_slot(D, e, ei, goal);
   const int p = D.e_ci[e] / D.BM;
-  const float* r0 = D.st + ((long)p * D.NC + D.e_par[e]) * 16;
-  const float* r1 = D.cand + (long)D.e_ci[e] * 16;
-  float es[32];
-#pragma unroll
-  for (int m = 0; m < 16; ++m) { es[m] = r0[m]; es[16 + m] = r1[m]; }
-  Cubic c;
-  cubic_coef_sh<true>(es, T, c);
-  float rv = 0.f;
-#pragma unroll 1
-  for (int j = 0; j < 7; ++j) rv = fmaxf(rv, rho_v_joint(A, c, j));
+  const float rv = warp_rho_v(A, es, T);
   bool ok = rv <= 1.f;
   const fn_problem_t& P = D.prob[p];
   if (ok && P.n_obs > 0) {
+    Cubic c;
+    cubic_coef_sh<true>(es, T, c);
     float mc = INFINITY;
 #pragma unroll 1
-    for (int s = 0; s < D.S_clear; ++s) {
+    for (int s = lane; s < D.S_clear; s += 32) {
       const float u = sample_u(s, D.S_clear);
       float q[7];
 #pragma unroll
@@ -735,28 +875,39 @@ __device__ __forceinline__ void finish_edge(const PlanDev& D, const ArmK& A, int
       }
       mc = fminf(mc, config_clearance(A, q, P));
     }
+    mc = -warp_max(-mc);
     ok = mc >= D.margin;
   }
-  D.e_ok[ei] = ok ? 1 : 0;
-  D.e_T[ei] = T;
-  D.e_rv[ei] = rv;
+  if (lane == 0) {
+    D.e_ok[ei] = ok ? 1 : 0;
+    D.e_T[ei] = T;
+    D.e_rv[ei] = rv;
+  }
 }
 
 // after a stage: edges whose duration passed are finished; the others move
 // to their next survivor (next list) or end with no feasible duration
-__global__ void k_plan_vselect(PlanDev D, ArmK A, GridKP Gr, int list) {
+__global__ void __launch_bounds__(128) k_plan_vselect(PlanDev D, ArmK A, GridKP Gr, int list) {
+  __shared__ float sEs[4][32];
   Sched* S = D.sched;
   const int n = S->n_pend[list];
   const int32_t* pend = D.pend + (long)list * D.Emax;
   int32_t* next = D.pend + (long)(list ^ 1) * D.Emax;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nw = gridDim.x * 4;
+  for (int i = blockIdx.x * 4 + w; i < n; i += nw) {   // warp per pending edge
     const int e = pend[i];
     const bool goal = D.e_j[e] & 0x80;
     const int k = D.cur_k[e];
-    if (!D.fail[e]) {
-      finish_edge(D, A, e, goal ? D.e_Tp[e] : Gr.T[k]);
+    const bool failed = D.fail[e];
+    __syncwarp();
+    if (!failed) {
+      const int p = D.e_ci[e] / D.BM;
+      stage_rows(D.st + ((long)p * D.NC + D.e_par[e]) * 16, D.cand + (long)D.e_ci[e] * 16, sEs[w]);
+      finish_edge(D, A, e, goal ? D.e_Tp[e] : Gr.T[k], sEs[w]);
       continue;
     }
+    if (lane != 0) continue;
     D.fail[e] = 0u;
     const int k2 = goal ? -1 : next_survivor(D, e, k + 1);
     if (k2 < 0) {
@@ -853,10 +1004,9 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_vseq(PlanDev 
         if (s_pass[r] && s_k[r] >= 0) kres = s_k[r];
       from = next_from;
     }
+    if (w == 0 && kres >= 0) finish_edge(D, A, e, sT[kres], sEdge);
     if (threadIdx.x == 0) {
-      if (kres >= 0) {
-        finish_edge(D, A, e, sT[kres]);
-      } else {
+      if (kres < 0) {
         long ei;
         bool g;
         edge_slot(D, e, ei, g);
@@ -873,23 +1023,6 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_vseq(PlanDev 
 // attach + score + incumbent: one block per problem
 // ---------------------------------------------------------------------------
 #define PL_ATTACH_THREADS 1024
-
-__device__ __forceinline__ int block_scan_excl(int v, int* sh, int& total) {
-  // exclusive scan of one int per thread (blockDim = PL_ATTACH_THREADS)
-  const int t = threadIdx.x;
-  sh[t] = v;
-  __syncthreads();
-  for (int o = 1; o < blockDim.x; o <<= 1) {
-    const int a = t >= o ? sh[t - o] : 0;
-    __syncthreads();
-    sh[t] += a;
-    __syncthreads();
-  }
-  total = sh[blockDim.x - 1];
-  const int incl = sh[t];
-  __syncthreads();
-  return incl - v;
-}
 
 __global__ void __launch_bounds__(PL_ATTACH_THREADS) k_plan_attach(PlanDev D) {
   __shared__ int sh[PL_ATTACH_THREADS];
@@ -911,7 +1044,7 @@ __global__ void __launch_bounds__(PL_ATTACH_THREADS) k_plan_attach(PlanDev D) {
       if (D.e_ok[ci * D.KP + j]) { ++cnt; break; }
   }
   int total;
-  const int base = block_scan_excl(cnt, sh, total);
+  const int base = block_scan(cnt, sh, &total);
   // pass 2: attach in candidate order (Algorithm 1: argmin_p t(p) + T_p,
   // ties to the lower parent slot)
   float bestJ = -INFINITY;
@@ -1046,7 +1179,7 @@ __global__ void __launch_bounds__(PL_ATTACH_THREADS) k_plan_prune(PlanDev D, Arm
   int cnt = 0;
   for (int i = c0; i < c1; ++i) cnt += D.alive[nb + i];
   int total;
-  int r = block_scan_excl(cnt, sh, total);
+  int r = block_scan(cnt, sh, &total);
   for (int i = c0; i < c1; ++i) {
     D.newidx[nb + i] = D.alive[nb + i] ? r++ : -1;
   }
@@ -1074,6 +1207,7 @@ __global__ void __launch_bounds__(PL_ATTACH_THREADS) k_plan_prune(PlanDev D, Arm
   __syncthreads();
   if (threadIdx.x == 0) {
     D.n_nodes[p] = total;
+    if (total != N) D.packed[p] = 0;   // indices moved: repack the mirror
     if (in.id >= 0) {
       Incumbent o = in;
       o.id = D.newidx[nb + in.id];
@@ -1206,6 +1340,42 @@ static int plan_edge_blocks(fn_planner* pl, int v) {
                            resident_stage(plan_vseq_variant(v))));
 }
 
+template <int KM>
+static int knn_blocks(fn_planner* pl) {
+  (void)pl;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_plan_knn<KM>, 32 * PL_KNN_WARPS,
+                                                    0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return per_sm * num_sms();
+}
+
+// sampling and parents: candidates of every problem (unless given by the
+// caller), then their nearest tree nodes (mark(2) between the two)
+template <class Mark>
+static void enqueue_front(fn_planner* pl, unsigned flags, cudaStream_t st, Mark&& mark) {
+  PlanDev& D = pl->D;
+  const int P = pl->cfg.P;
+  if (!(flags & FN_PLAN_EXTERNAL)) {
+    const long n = (long)P * D.BM;
+    k_plan_sample_goal<<<(unsigned)((4 * n + 127) / 128), 128, 0, st>>>(D, pl->arm);
+    k_plan_sample_free<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(D, pl->arm);
+  }
+  mark(2);
+  if (pl->cfg.k > 1) {
+    k_plan_parents_prep<<<2 * num_sms(), 256, 0, st>>>(D);
+    const unsigned mb = (unsigned)(((long)P * D.BM + 7) / 8);
+    if (D.KM == 8) {
+      k_plan_knn<8><<<knn_blocks<8>(pl), 32 * PL_KNN_WARPS, 0, st>>>(D);
+      k_plan_knn_merge<8><<<mb, 256, 0, st>>>(D);
+    } else {
+      k_plan_knn<16><<<knn_blocks<16>(pl), 32 * PL_KNN_WARPS, 0, st>>>(D);
+      k_plan_knn_merge<16><<<mb, 256, 0, st>>>(D);
+    }
+  }
+}
+
 #define PL_VSTAGES 2
 
 // the packed edge phase: prep, item scan, probe, verify (mark(i) records
@@ -1254,6 +1424,7 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
   if (!cfg || !arm || !out) return FN_EINVAL;
   const fn_planner_cfg_t c = *cfg;
   if ((long)c.P * c.b_max * c.k > (1L << 28)) return FN_EINVAL;
+  if ((long)c.P * c.n_cap > (1L << 30)) return FN_EINVAL;
   if (c.P < 1 || c.P > PL_MAX_P || c.n_cap < 2 || c.n_cap > (1 << 22) || c.b_max < 1 ||
       c.b_max > (1 << 16) || c.k < 1 || c.k > FN_MAX_KNN + 1 || c.K < 1 || c.K > FN_MAX_GRID ||
       c.S < 2 || c.S > FN_MAX_S || c.S_clear < 2 || c.S_clear > FN_MAX_S || c.reach_grid < 2 ||
@@ -1303,6 +1474,10 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
   A_(D.pend, (size_t)D.Emax * 2);
   D.surv_cap = (int)std::min<long>((long)D.Emax * 16, 1L << 26);
   A_(D.surv, (size_t)D.surv_cap);
+  D.NB = (NC + 63) / 64;
+  A_(D.mir, (size_t)P * D.NB * 7 * 32);
+  A_(D.packed, (size_t)P);
+  if (rc == FN_OK && cudaMemset(D.packed, 0, sizeof(int32_t) * P) != cudaSuccess) rc = FN_ECUDA;
 #undef A_
   if (rc == FN_OK) {
     if (cudaMallocHost(&pl->h_prob, P * sizeof(fn_problem_t)) != cudaSuccess ||
@@ -1420,24 +1595,7 @@ static fn_status enqueue_iteration(fn_planner* pl, unsigned flags, cudaStream_t 
   mark(0);
   k_plan_schedule<<<1, 32, 0, st>>>(D);
   mark(1);
-  if (!(flags & FN_PLAN_EXTERNAL)) {
-    const long n = (long)P * D.BM;
-    k_plan_sample_goal<<<(unsigned)((4 * n + 127) / 128), 128, 0, st>>>(D, pl->arm);
-    k_plan_sample_free<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(D, pl->arm);
-  }
-  mark(2);
-  if (pl->cfg.k > 1) {
-    const long nn = (long)P * D.BM * D.KN;
-    k_plan_nn_empty<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(D);
-    const int kb = 2 * num_sms();
-    if (D.KM == 8) {
-      k_plan_knn<8><<<kb, 128, 0, st>>>(D);
-      k_plan_knn_merge<8><<<(unsigned)(((long)P * D.BM + 7) / 8), 256, 0, st>>>(D);
-    } else {
-      k_plan_knn<16><<<kb, 128, 0, st>>>(D);
-      k_plan_knn_merge<16><<<(unsigned)(((long)P * D.BM + 7) / 8), 256, 0, st>>>(D);
-    }
-  }
+  enqueue_front(pl, flags, st, mark);
   mark(3);
   enqueue_edges(pl, pl->edge_variant, pl->edge_blocks, st, mark);
   mark(6);
@@ -1561,6 +1719,18 @@ extern "C" fn_status fn_planner_get_candidates(fn_planner_t* pl, int p, float* s
   return ok ? FN_OK : FN_ECUDA;
 }
 
+extern "C" fn_status fn_planner_get_parents(fn_planner_t* pl, int p, int32_t* nn, int cap) {
+  if (!pl || !nn || p < 0 || p >= pl->cfg.P || cap < 0) return FN_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return FN_ECUDA;
+  const int KN = pl->D.KN;
+  const long m = std::min(cap, pl->cfg.b_max);
+  if (KN == 0 || m == 0) return FN_OK;
+  return cudaMemcpy(nn, pl->D.nn + (long)p * pl->cfg.b_max * KN, sizeof(int32_t) * m * KN,
+                    cudaMemcpyDeviceToHost) == cudaSuccess
+             ? FN_OK
+             : FN_ECUDA;
+}
+
 // work counters of the edge kernels (torque evaluations since the last
 // reset): count[0] probe, count[1] verify
 extern "C" fn_status fn_planner_sample_count(fn_planner_t* pl, unsigned long long* count,
@@ -1592,25 +1762,8 @@ extern "C" fn_status fn_planner_autotune(fn_planner_t* pl, const fn_problem_t* p
       cudaSuccess)
     return FN_ECUDA;
   PlanDev& D = pl->D;
-  const int P = pl->cfg.P;
   k_plan_schedule<<<1, 32, 0, st>>>(D);
-  if (!(flags & FN_PLAN_EXTERNAL)) {
-    const long n = (long)P * D.BM;
-    k_plan_sample_goal<<<(unsigned)((4 * n + 127) / 128), 128, 0, st>>>(D, pl->arm);
-    k_plan_sample_free<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(D, pl->arm);
-  }
-  if (pl->cfg.k > 1) {
-    const long nn = (long)P * D.BM * D.KN;
-    k_plan_nn_empty<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(D);
-    const int kb = 2 * num_sms();
-    if (D.KM == 8) {
-      k_plan_knn<8><<<kb, 128, 0, st>>>(D);
-      k_plan_knn_merge<8><<<(unsigned)(((long)P * D.BM + 7) / 8), 256, 0, st>>>(D);
-    } else {
-      k_plan_knn<16><<<kb, 128, 0, st>>>(D);
-      k_plan_knn_merge<16><<<(unsigned)(((long)P * D.BM + 7) / 8), 256, 0, st>>>(D);
-    }
-  }
+  enqueue_front(pl, flags, st, [](int) {});
   if ((rc = launch_status()) != FN_OK) return rc;
   float best_ms = INFINITY;
   int best = pl->edge_variant;

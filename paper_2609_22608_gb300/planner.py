@@ -58,12 +58,14 @@ def _bind():
     L.fn_plan_replay.argtypes = [vp, vp, i32, vp, vp]
     L.fn_planner_get_tree.argtypes = [vp, i32, vp, vp, vp, vp, vp, C.POINTER(C.c_int), i32]
     L.fn_planner_get_candidates.argtypes = [vp, i32, vp, vp, vp, vp, i32]
+    L.fn_planner_get_parents.argtypes = [vp, i32, vp, i32]
     L.fn_planner_sample_count.argtypes = [vp, vp, i32]
     L.fn_planner_phase_ms.argtypes = [vp, vp]
     L.fn_planner_autotune.argtypes = [vp, vp, i32, C.c_uint, i32, vp, vp, vp]
     for n in ("fn_planner_create", "fn_planner_destroy", "fn_planner_reset", "fn_planner_load_tree",
               "fn_planner_set_candidates", "fn_plan_iteration", "fn_planner_capture",
               "fn_plan_replay", "fn_planner_get_tree", "fn_planner_get_candidates",
+              "fn_planner_get_parents",
               "fn_planner_sample_count", "fn_planner_phase_ms", "fn_planner_autotune"):
         getattr(L, n).restype = i32
     L._planner_bound = True
@@ -202,6 +204,13 @@ class Planner:
                                               vr.ctypes.data, va.ctypes.data, int(B)),
               "fn_planner_get_candidates")
         return dict(states=st, T_req=tq, v_rel=vr, valid=va)
+
+    def get_parents(self, p, B):
+        """fn_planner_get_parents: [B][k-1] nearest non-root tree nodes."""
+        nn = np.zeros((B, max(self.cfg.k - 1, 0)), np.int32)
+        check(_bind().fn_planner_get_parents(self.h, int(p), nn.ctypes.data, int(B)),
+              "fn_planner_get_parents")
+        return nn
 
     def autotune(self, probs, it=0, flags=0, reps=3, stream=None):
         """fn_planner_autotune: returns (chosen variant, ms per variant)."""

@@ -132,6 +132,41 @@ def test_plan_prune_parity(P, orc, arm):
     assert len(diff) <= max(2, 0.01 * tree.n)
 
 
+@pytest.mark.parametrize("N,B,k", [(300, 97, 5), (4097, 64, 8), (13001, 150, 8), (9000, 40, 17)])
+def test_parents_match_brute_force(P, orc, arm, N, B, k):
+    """The planner's parent lists equal the oracle's brute-force kNN over the
+    non-root nodes (one split of the tree and several, k-1 = 4, 7, 16),
+    up to swaps among near-equal exact distances."""
+    from tests.parity import knn_mismatches
+    toss = synth.random_toss(arm, 21)
+    root = synth.random_states(arm, 1, 77)[0]
+    pr = synth.make_problem(toss, root=root)
+    states, parent, t = synth.random_tree(arm, N, 31, root=root)
+    cand = synth.random_states(arm, B, 32)
+    w_vel = 0.1
+    pl = P.Planner(arm, P=1, n_cap=N + B + 8, b_max=B, k=k, K=16, S=8, w_vel=w_vel)
+    prob = P.problem_struct(pr, B, 0, root=root)
+    pl.reset([prob])
+    pl.load_tree(0, states, t, parent)
+    pl.set_candidates(0, cand, 0, np.zeros(B, np.float32), np.zeros(B, np.float32))
+    pl.iterate([prob], 0, P.FN_PLAN_EXTERNAL)
+    nn = pl.get_parents(0, B)
+    pl.close()
+    idx, d = orc.knn(states, cand, k - 1, float(np.float32(w_vel)), first=1)
+    s64, c64 = states.astype(np.float64), cand.astype(np.float64)
+
+    def exact(b, i):
+        if i < 0:
+            return np.inf
+        dq = s64[i, 0:7] - c64[b, 0:7]
+        dv = s64[i, 8:15] - c64[b, 8:15]
+        return float(dq @ dq + np.float32(w_vel) * (dv @ dv))
+    dg = np.array([[exact(b, i) for i in nn[b]] for b in range(B)])
+    assert np.all(nn >= 1) and np.all(nn < N)
+    assert np.all(np.diff(dg, axis=1) >= -1e-6 * dg[:, 1:])
+    assert not knn_mismatches(nn, dg, idx, d)
+
+
 def test_sampler_uniform_matches_oracle(P, orc, arm):
     """Free candidates: same Philox counters, same formula -> equal to FP32
     rounding."""
