@@ -178,6 +178,44 @@ __device__ __forceinline__ bool chol_solve6(float (&A)[6][6], const float* b, fl
   return true;
 }
 
+// 6x6 symmetric positive definite solve by LDL^T (lower triangle of A read).
+// Returns false if a pivot is not positive.
+__device__ __forceinline__ bool ldlt_solve6(const float (&A)[6][6], const float* b, float* x) {
+  float L[6][6], W[6][6], r[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    float d = A[j][j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) d = fmaf(-L[j][k], W[j][k], d);
+    if (!(d > 0.f)) return false;
+    r[j] = __frcp_rn(d);
+#pragma unroll
+    for (int i = j + 1; i < 6; ++i) {
+      float w = A[i][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) w = fmaf(-L[i][k], W[j][k], w);
+      W[i][j] = w;            // L_ij d_j
+      L[i][j] = w * r[j];
+    }
+  }
+  float z[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    float t = b[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) t = fmaf(-L[i][k], z[k], t);
+    z[i] = t;
+  }
+#pragma unroll
+  for (int i = 5; i >= 0; --i) {
+    float t = z[i] * r[i];
+#pragma unroll
+    for (int k = i + 1; k < 6; ++k) t = fmaf(-L[k][i], x[k], t);
+    x[i] = t;
+  }
+  return true;
+}
+
 // unit vectors (e1, e2) completing u to a right-handed frame
 __device__ __forceinline__ void complete_basis(const float* u, float* e1, float* e2) {
   float h[3] = {0.f, 0.f, 1.f};
@@ -199,23 +237,79 @@ __device__ __forceinline__ void complete_basis(const float* u, float* e1, float*
 // joint 1 turned towards the target's azimuth; iterates are projected onto
 // the box; accepted when the position residual < 1e-4 m, the rotation
 // residual (half the sum of column cross products) < 1e-3 and the rotation
-// error is under 90 degrees (trace > 1).
-__device__ __forceinline__ bool ik_solve(const ArmK& A, const float* Rg, const float* pg, float q7,
-                                         int st, float* q) {
-  const float pattern[6] = {0.f, 0.5f, 0.f, -0.5f, 0.f, 0.5f};
+// error is under 90 degrees (trace > 1).  The damped system
+// (J J^T + lambda^2 I) y = e is solved by an LDL^T factorisation (six
+// reciprocals on the critical path instead of square roots and divisions).
+//
+// The work of one iteration is spread over a group of 8 lanes (aligned in
+// the warp; all 32 lanes must call this): lane s < 7 owns joint s, lane 7
+// the flange offset.  The frames are
+// the inclusive product scan of the 8 local transforms [Rx(alpha) Rz(theta),
+// p] (three shuffle steps), lanes 0..5 form the Jacobian columns and share
+// them, and every lane of the group solves the same 6x6 system; lane s < 6
+// then updates its own joint.  Returns (uniformly in the group) whether the
+// start converged; qs is the lane's own final joint value.
+__device__ __forceinline__ bool ik_solve_group(const ArmK& A, const float* Rg, const float* pg,
+                                               float q7, int st, float& qs) {
+  const int s = threadIdx.x & 7;
   const float sgn = st == 0 ? 0.f : (st == 1 ? 1.f : -1.f);
-#pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    const float c = 0.5f * (A.q_lo[j] + A.q_hi[j]);
-    const float h = 0.5f * (A.q_hi[j] - A.q_lo[j]);
-    q[j] = fmaf(sgn * pattern[j], h, c);
+  const float pat = (s & 1) ? (s == 3 ? -0.5f : 0.5f) : 0.f;   // (0, .5, 0, -.5, 0, .5)
+  float qj = 0.f;
+  if (s < 6) {
+    const float c = 0.5f * (A.q_lo[s] + A.q_hi[s]);
+    const float h = 0.5f * (A.q_hi[s] - A.q_lo[s]);
+    qj = fmaf(sgn * pat, h, c);
   }
-  q[6] = q7;
-  q[0] = fminf(fmaxf(atan2f(pg[1], pg[0]), A.q_lo[0]), A.q_hi[0]);
+  if (s == 6) qj = q7;
+  if (s == 0) qj = fminf(fmaxf(atan2f(pg[1], pg[0]), A.q_lo[0]), A.q_hi[0]);
+  const float lo = s < 7 ? A.q_lo[s] : 0.f, hi = s < 7 ? A.q_hi[s] : 0.f;
   float ep[3], er[3], Ree[9], oee[3];
+  bool failed = false;
   for (int it = 0; it <= FN_IK_ITERS; ++it) {
-    Axes ax;
-    fk_axes(A, q, ax, Ree, oee);
+    // local transform of this lane's link
+    float R[9], o[3];
+    if (s < 7) {
+      float sn, cs;
+      sincosf(qj + A.th0[s], &sn, &cs);
+      const float ca = A.ca[s], sa = A.sa[s];
+      R[0] = cs;      R[1] = -sn;     R[2] = 0.f;
+      R[3] = sn * ca; R[4] = cs * ca; R[5] = -sa;
+      R[6] = sn * sa; R[7] = cs * sa; R[8] = ca;
+      o[0] = A.px[s]; o[1] = A.py[s]; o[2] = A.pz[s];
+    } else {
+      R[0] = 1.f; R[1] = 0.f; R[2] = 0.f;
+      R[3] = 0.f; R[4] = 1.f; R[5] = 0.f;
+      R[6] = 0.f; R[7] = 0.f; R[8] = 1.f;
+      o[0] = 0.f; o[1] = 0.f; o[2] = A.flange_d;
+    }
+    // inclusive scan: [R, o] <- [Rl, ol] [R, o] = [Rl R, ol + Rl o]
+#pragma unroll
+    for (int d = 1; d < 8; d <<= 1) {
+      float Rl[9], ol[3];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Rl[k] = __shfl_up_sync(0xffffffffu, R[k], d, 8);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) ol[k] = __shfl_up_sync(0xffffffffu, o[k], d, 8);
+      if (s >= d) {
+        float Rn[9], on[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            Rn[3 * r + c] = fmaf(Rl[3 * r], R[c], fmaf(Rl[3 * r + 1], R[3 + c], Rl[3 * r + 2] * R[6 + c]));
+          on[r] = ol[r] + fmaf(Rl[3 * r], o[0], fmaf(Rl[3 * r + 1], o[1], Rl[3 * r + 2] * o[2]));
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) R[k] = Rn[k];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) o[k] = on[k];
+      }
+    }
+    // end-effector pose from lane 7 of the group
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Ree[k] = __shfl_sync(0xffffffffu, R[k], 7, 8);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) oee[k] = __shfl_sync(0xffffffffu, o[k], 7, 8);
     ep[0] = pg[0] - oee[0]; ep[1] = pg[1] - oee[1]; ep[2] = pg[2] - oee[2];
     er[0] = er[1] = er[2] = 0.f;
 #pragma unroll
@@ -226,38 +320,46 @@ __device__ __forceinline__ bool ik_solve(const ArmK& A, const float* Rg, const f
       cross3(rc, rg, x);
       er[0] = fmaf(0.5f, x[0], er[0]); er[1] = fmaf(0.5f, x[1], er[1]); er[2] = fmaf(0.5f, x[2], er[2]);
     }
-    if (it == FN_IK_ITERS) break;
+    if (it == FN_IK_ITERS || failed) break;
+    // own Jacobian column (joints 0..5), then everyone's
+    float Jc[6];
+    {
+      const float z[3] = {R[2], R[5], R[8]};
+      const float r[3] = {oee[0] - o[0], oee[1] - o[1], oee[2] - o[2]};
+      float v[3];
+      cross3(z, r, v);
+      Jc[0] = v[0]; Jc[1] = v[1]; Jc[2] = v[2]; Jc[3] = z[0]; Jc[4] = z[1]; Jc[5] = z[2];
+    }
     float J[6][6];
 #pragma unroll
-    for (int m = 0; m < 6; ++m) {
-      const float r[3] = {oee[0] - ax.o[m][0], oee[1] - ax.o[m][1], oee[2] - ax.o[m][2]};
-      float v[3];
-      cross3(ax.z[m], r, v);
-      J[0][m] = v[0]; J[1][m] = v[1]; J[2][m] = v[2];
-      J[3][m] = ax.z[m][0]; J[4][m] = ax.z[m][1]; J[5][m] = ax.z[m][2];
-    }
+    for (int m = 0; m < 6; ++m)
+#pragma unroll
+      for (int i = 0; i < 6; ++i) J[i][m] = __shfl_sync(0xffffffffu, Jc[i], m, 8);
     float M[6][6];
 #pragma unroll
     for (int i = 0; i < 6; ++i)
 #pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        float s = 0.f;
+      for (int j = 0; j <= i; ++j) {
+        float sacc = 0.f;
 #pragma unroll
-        for (int m = 0; m < 6; ++m) s = fmaf(J[i][m], J[j][m], s);
-        M[i][j] = s + (i == j ? FN_IK_LAMBDA * FN_IK_LAMBDA : 0.f);
+        for (int m = 0; m < 6; ++m) sacc = fmaf(J[i][m], J[j][m], sacc);
+        M[i][j] = sacc + (i == j ? FN_IK_LAMBDA * FN_IK_LAMBDA : 0.f);
       }
     const float e[6] = {ep[0], ep[1], ep[2], er[0], er[1], er[2]};
     float y[6];
-    if (!chol_solve6(M, e, y)) return false;
-#pragma unroll
-    for (int m = 0; m < 6; ++m) {
+    if (!ldlt_solve6(M, e, y)) {
+      failed = true;
+      break;
+    }
+    if (s < 6) {
       float dq = 0.f;
 #pragma unroll
-      for (int i = 0; i < 6; ++i) dq = fmaf(J[i][m], y[i], dq);
-      q[m] = fminf(fmaxf(q[m] + dq, A.q_lo[m]), A.q_hi[m]);
+      for (int i = 0; i < 6; ++i) dq = fmaf(Jc[i], y[i], dq);
+      qj = fminf(fmaxf(qj + dq, lo), hi);
     }
   }
-  if (!(norm3(ep) < FN_IK_POS_TOL && norm3(er) < FN_IK_ROT_TOL)) return false;
+  qs = qj;
+  if (failed || !(norm3(ep) < FN_IK_POS_TOL && norm3(er) < FN_IK_ROT_TOL)) return false;
   float tr = 0.f;
 #pragma unroll
   for (int i = 0; i < 9; ++i) tr = fmaf(Rg[i], Ree[i], tr);

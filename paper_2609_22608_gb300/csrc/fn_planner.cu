@@ -33,7 +33,6 @@
 #define PL_NSPLIT_MAX 32
 #define PL_KNN_WARPS 4
 #define PL_KNN_QW 1                           // queries per warp
-#define PL_KNN_GROUP (PL_KNN_WARPS * PL_KNN_QW)
 #define PL_KNN_SPAN 4096                      // nodes per split (at least)
 #define PL_MAX_P 1024
 
@@ -53,7 +52,8 @@ struct Sched {
   int n_surv;         // probe survivors appended (may exceed surv_cap)
   int n_free_edges;   // free edges of all problems (the queue's first part)
   int n_edges;        // all edges
-  int knn_items;      // (problem, query tile, split) items
+  int knn_items;      // (problem, query group, split) items, one per warp
+  int knn_head;       // next unclaimed parent-search item
   int free_off[PL_MAX_P + 1];
   int goal_off[PL_MAX_P + 1];
   int knn_off[PL_MAX_P + 1];
@@ -184,7 +184,7 @@ __global__ void k_plan_schedule(PlanDev D) {
     int ns = 1;
     if (D.KN > 0 && span > 0) ns = min(PL_NSPLIT_MAX, (span + PL_KNN_SPAN - 1) / PL_KNN_SPAN);
     S->nsplit[p] = ns;
-    ko += (D.KN > 0 && span > 0) ? ((B + PL_KNN_GROUP - 1) / PL_KNN_GROUP) * ns : 0;
+    ko += (D.KN > 0 && span > 0) ? ((B + PL_KNN_QW - 1) / PL_KNN_QW) * ns : 0;
     D.added[p] = 0;
     const int lo = min(D.packed[p], D.n_nodes[p]);
     S->pack_lo[p] = lo;
@@ -199,6 +199,7 @@ __global__ void k_plan_schedule(PlanDev D) {
   S->n_free_edges = fo;
   S->n_edges = fo + go;
   S->knn_items = ko;
+  S->knn_head = 0;
   S->queue_head = 0u;
 }
 
@@ -247,51 +248,48 @@ __global__ void __launch_bounds__(128) k_plan_sample_free(PlanDev D, ArmK A) {
   o4[3] = make_float4(qd[4], qd[5], qd[6], 0.f);
 }
 
-// Goal candidates: a group of 4 lanes per candidate; lanes 0-2 run the three
-// IK starts in parallel and the lowest start that converges wins (the same
-// result as trying the starts in order).
+// Goal candidates: one warp per candidate.  Every lane decodes the chart
+// pose; lane groups 0-2 (8 lanes each) run the three IK starts in parallel
+// (ik_solve_group) and the lowest start that converges wins, the same result
+// as trying the starts in order; group 3 repeats start 0 and is ignored.
 __global__ void __launch_bounds__(128) k_plan_sample_goal(PlanDev D, ArmK A) {
-  const long gid = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
-  const int sub = threadIdx.x & 3;
+  const long gid = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31, grp = lane >> 3;
   const int p = (int)(gid / D.BM);
   const int b = (int)(gid - (long)p * D.BM);
-  bool live = p < D.P;
-  int G = 0;
-  if (live) {
-    const fn_problem_t& P0 = D.prob[p];
-    const int B = min(max(P0.batch, 0), D.BM);
-    G = min(max(P0.n_goal, 0), B);
-    live = b < G;
-  }
-  const unsigned gmask = 0xfu << (threadIdx.x & 28);
-  if (!__any_sync(0xffffffffu, live)) return;
-  bool defined = false, found = false;
+  if (p >= D.P) return;                               // warp-uniform
+  const fn_problem_t& P = D.prob[p];
+  const int B = min(max(P.batch, 0), D.BM);
+  const int G = min(max(P.n_goal, 0), B);
+  if (b >= G) return;                                 // warp-uniform
+  const long ci = (long)p * D.BM + b;
+  const int it = *D.iter;
+  float u[12], z[9];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) philox_u4(P.seed, b, it, p, 8 + s, u + 4 * s);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) z[i] = u[i];
   ChartPose o;
+  const bool defined = chart_pose(A, P, z, o);        // warp-uniform
+  int winner = -1;
   float q[7];
-  const long ci = live ? (long)p * D.BM + b : 0;
-  if (live) {
-    const fn_problem_t& P = D.prob[p];
-    const int it = *D.iter;
-    float u[12], z[9];
+  if (defined) {
+    float qs;
+    const bool found = ik_solve_group(A, o.Rg, o.pg, o.q7, grp < FN_IK_STARTS ? grp : 0, qs);
+    const unsigned won = __ballot_sync(0xffffffffu, found && (lane & 7) == 0 && grp < FN_IK_STARTS);
+    winner = won ? (__ffs(won) - 1) : -1;             // first lane of the winning group
 #pragma unroll
-    for (int s = 0; s < 3; ++s) philox_u4(P.seed, b, it, p, 8 + s, u + 4 * s);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) z[i] = u[i];
-    defined = chart_pose(A, P, z, o);
-    if (defined && sub < FN_IK_STARTS) found = ik_solve(A, o.Rg, o.pg, o.q7, sub, q);
+    for (int j = 0; j < 7; ++j) q[j] = __shfl_sync(0xffffffffu, qs, winner < 0 ? j : winner + j);
   }
-  const unsigned won = __ballot_sync(0xffffffffu, found) & gmask;
-  const int winner = won ? __ffs(won) - 1 : -1;
-  const int lane = threadIdx.x & 31;
-  if (!live) return;
-  if (sub == 0 && winner < 0) {   // undefined: no IK start converged
+  if (lane != 0) return;
+  if (winner < 0) {   // undefined: |v_rel| too small or no IK start converged
     D.treq[ci] = o.T;
     D.vrel[ci] = o.vrel;
     D.valid[ci] = 0;
     float4* o4 = reinterpret_cast<float4*>(D.cand + ci * 16);
     o4[0] = o4[1] = o4[2] = o4[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
   }
-  if (lane != winner) return;
   float qd[7];
   const bool ok = chart_velocity(A, o, q, qd);
   if (!ok)
@@ -308,8 +306,9 @@ __global__ void __launch_bounds__(128) k_plan_sample_goal(PlanDev D, ArmK A) {
 }
 
 // ---------------------------------------------------------------------------
-// parents: (problem, query group, split) items over all problems.  A warp
-// takes PL_KNN_QW queries and sweeps the split's nodes 64 at a time; the k best
+// parents: (problem, query group, split) items over all problems, claimed
+// by warps one at a time.  A warp takes PL_KNN_QW queries and sweeps the
+// split's nodes 64 at a time; the k best
 // (d, index) pairs live across lanes 0..KM-1 in ascending order, and only
 // nodes that beat the current k-th pair enter the list, one at a time (a
 // ballot finds them; a shuffle-up opens their slot).
@@ -346,25 +345,55 @@ struct WarpTopK {
   }
 };
 
+// asynchronous 16-byte global -> shared copy (completion tracked per thread)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+#define PL_KNN_RING 3   // mirror blocks per warp in flight (shared-memory ring)
+constexpr int kKnnSmem = PL_KNN_WARPS * PL_KNN_RING * 7 * 32 * 16;
+
 // One warp per (query group, split): lane j takes nodes 2j and 2j+1 of each
 // 64-node block of the split from the mirror and scores both against the
-// warp's queries with paired FP32 operations (each half rounds exactly like the
-// scalar knn_dist: t = q - x, dq and dv accumulated in component order,
-// d = w dv + dq).
+// warp's queries with paired FP32 operations (each half rounds exactly like
+// the scalar knn_dist: t = q - x, dq and dv accumulated in component order,
+// d = w dv + dq).  The mirror blocks stream through a per-warp ring in
+// shared memory, PL_KNN_RING - 1 blocks ahead; each lane copies (cp.async)
+// and later reads only its own 16-byte words, so the ring needs no barrier.
 template <int KM>
 __global__ void __launch_bounds__(32 * PL_KNN_WARPS) k_plan_knn(PlanDev D) {
+  extern __shared__ float4 knn_ring[];   // [warp][slot][7][32]
   const Sched* S = D.sched;
   const int items = S->knn_items;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float4* ring = knn_ring + (long)w * PL_KNN_RING * 7 * 32 + lane;
   const float2 w2 = make_float2(D.w_vel, D.w_vel);
-  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+  Sched* Sw = D.sched;
+  for (;;) {   // each warp claims items until none are left
+    int item = 0;
+    if (lane == 0) item = atomicAdd(&Sw->knn_head, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= items) break;
     const int p = find_problem(S->knn_off, D.P, item);
     const int local = item - S->knn_off[p];
     const int ns = S->nsplit[p];
     const int g = local / ns, split = local - g * ns;
     const int B = min(max(D.prob[p].batch, 0), D.BM);
-    const int b0 = (g * PL_KNN_WARPS + w) * PL_KNN_QW;
-    const bool wact = b0 < B;                  // warp-uniform
+    const int b0 = g * PL_KNN_QW;
+    // candidates whose decoding failed get no parents (their edges are
+    // invalid whatever the lists hold)
+    bool wact = false;                         // warp-uniform
+#pragma unroll
+    for (int a = 0; a < PL_KNN_QW; ++a)
+      wact |= b0 + a < B && D.valid[(long)p * D.BM + b0 + a];
     const int N = D.n_nodes[p];
     const int span = N - 1;
     const int per = (span + ns - 1) / ns;
@@ -380,19 +409,33 @@ __global__ void __launch_bounds__(32 * PL_KNN_WARPS) k_plan_knn(PlanDev D) {
     }
     WarpTopK<KM> top[PL_KNN_QW];
     const float4* mir = D.mir + (long)p * D.NB * 7 * 32 + lane;
-    const int blk0 = lo >> 6, blk1 = (hi + 63) >> 6;
-    float4 nx[7];   // the next mirror block, loaded one round ahead
-    if (wact) {
+    const int blk0 = lo >> 6, nblk = wact ? ((hi + 63) >> 6) - blk0 : 0;
 #pragma unroll
-      for (int cc = 0; cc < 7; ++cc) nx[cc] = __ldg(mir + (blk0 * 7 + cc) * 32);
+    for (int r = 0; r < PL_KNN_RING - 1; ++r) {   // prologue: blocks 0 .. RING-2
+      if (r < nblk)
+#pragma unroll
+        for (int cc = 0; cc < 7; ++cc)
+          cp_async16(ring + (r * 7 + cc) * 32, mir + ((blk0 + r) * 7 + cc) * 32);
+      cp_async_commit();
     }
-    for (int blk = blk0; wact && blk < blk1; ++blk) {
+    for (int r = 0; r < nblk; ++r) {
+      __syncwarp();   // last round's reads of the slot precede its refill
+      {
+        const int rn = r + PL_KNN_RING - 1;         // refill the slot freed last round
+        if (rn < nblk) {
+          const int slot = rn % PL_KNN_RING;
+#pragma unroll
+          for (int cc = 0; cc < 7; ++cc)
+            cp_async16(ring + (slot * 7 + cc) * 32, mir + ((blk0 + rn) * 7 + cc) * 32);
+        }
+        cp_async_commit();
+      }
+      cp_async_wait<PL_KNN_RING - 1>();             // this lane's copies of block r landed
       float4 x[7];
+      const int slot = r % PL_KNN_RING;
 #pragma unroll
-      for (int cc = 0; cc < 7; ++cc) x[cc] = nx[cc];
-      const int bn = min(blk + 1, blk1 - 1);
-#pragma unroll
-      for (int cc = 0; cc < 7; ++cc) nx[cc] = __ldg(mir + (bn * 7 + cc) * 32);
+      for (int cc = 0; cc < 7; ++cc) x[cc] = ring[(slot * 7 + cc) * 32];
+      const int blk = blk0 + r;
       const int n0 = blk * 64 + 2 * lane;
       const bool v0 = n0 >= lo && n0 < hi, v1 = n0 + 1 >= lo && n0 + 1 < hi;
       float2 d[PL_KNN_QW];
@@ -417,11 +460,12 @@ __global__ void __launch_bounds__(32 * PL_KNN_WARPS) k_plan_knn(PlanDev D) {
                       d[a].y, n0 + 1);
       }
     }
+    cp_async_wait<0>();
 #pragma unroll
     for (int a = 0; a < PL_KNN_QW; ++a) {
       const int b = b0 + a;
-      if (!wact || b >= B || lane >= KM) continue;
-      const int id = top[a].i;
+      if (b >= B || lane >= KM) continue;
+      const int id = D.valid[(long)p * D.BM + b] ? top[a].i : 0x7fffffff;
       if (ns == 1) {
         if (lane < D.KN) D.nn[((long)p * D.BM + b) * D.KN + lane] = id == 0x7fffffff ? -1 : id;
       } else {
@@ -1343,12 +1387,20 @@ static int plan_edge_blocks(fn_planner* pl, int v) {
 template <int KM>
 static int knn_blocks(fn_planner* pl) {
   (void)pl;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_plan_knn<KM>, 32 * PL_KNN_WARPS,
-                                                    0) != cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
-  return per_sm * num_sms();
+  static int blocks[64] = {0};   // per device: resident blocks of k_plan_knn<KM>
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (blocks[dev] == 0) {
+    cudaFuncSetAttribute(k_plan_knn<KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, kKnnSmem);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_plan_knn<KM>, 32 * PL_KNN_WARPS,
+                                                      kKnnSmem) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    blocks[dev] = per_sm * num_sms();
+  }
+  return blocks[dev];
 }
 
 // sampling and parents: candidates of every problem (unless given by the
@@ -1359,7 +1411,7 @@ static void enqueue_front(fn_planner* pl, unsigned flags, cudaStream_t st, Mark&
   const int P = pl->cfg.P;
   if (!(flags & FN_PLAN_EXTERNAL)) {
     const long n = (long)P * D.BM;
-    k_plan_sample_goal<<<(unsigned)((4 * n + 127) / 128), 128, 0, st>>>(D, pl->arm);
+    k_plan_sample_goal<<<(unsigned)((32 * n + 127) / 128), 128, 0, st>>>(D, pl->arm);
     k_plan_sample_free<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(D, pl->arm);
   }
   mark(2);
@@ -1367,10 +1419,10 @@ static void enqueue_front(fn_planner* pl, unsigned flags, cudaStream_t st, Mark&
     k_plan_parents_prep<<<2 * num_sms(), 256, 0, st>>>(D);
     const unsigned mb = (unsigned)(((long)P * D.BM + 7) / 8);
     if (D.KM == 8) {
-      k_plan_knn<8><<<knn_blocks<8>(pl), 32 * PL_KNN_WARPS, 0, st>>>(D);
+      k_plan_knn<8><<<knn_blocks<8>(pl), 32 * PL_KNN_WARPS, kKnnSmem, st>>>(D);
       k_plan_knn_merge<8><<<mb, 256, 0, st>>>(D);
     } else {
-      k_plan_knn<16><<<knn_blocks<16>(pl), 32 * PL_KNN_WARPS, 0, st>>>(D);
+      k_plan_knn<16><<<knn_blocks<16>(pl), 32 * PL_KNN_WARPS, kKnnSmem, st>>>(D);
       k_plan_knn_merge<16><<<mb, 256, 0, st>>>(D);
     }
   }
