@@ -117,6 +117,15 @@ struct PlanDev {  // device pointers, passed by value to the kernels
   int NB;             // 64-node blocks per problem
 };
 
+// Programmatic dependent launch: a kernel launched with programmatic
+// stream serialization may be scheduled while its predecessor drains; it
+// touches nothing the predecessor writes before this wait (a no-op for a
+// plain launch), and then lets its own successor be scheduled.
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 struct GridKP {
   float T[FN_MAX_GRID];
 };
@@ -168,6 +177,7 @@ __global__ void k_plan_loaded(PlanDev D, int p, int n) {
 // schedule: per-problem offsets of every flattened work list
 // ---------------------------------------------------------------------------
 __global__ void k_plan_schedule(PlanDev D) {
+  pdl_begin();
   if (threadIdx.x != 0) return;
   Sched* S = D.sched;
   int fo = 0, go = 0, ko = 0, po = 0;
@@ -219,6 +229,7 @@ __device__ __forceinline__ int find_problem(const int* off, int P, int x) {
 // ---------------------------------------------------------------------------
 // Free candidates: one thread each (uniform in the box, |qd| <= vel_frac qdbar).
 __global__ void __launch_bounds__(128) k_plan_sample_free(PlanDev D, ArmK A) {
+  pdl_begin();
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int p = (int)(gid / D.BM);
   const int b = (int)(gid - (long)p * D.BM);
@@ -253,6 +264,7 @@ __global__ void __launch_bounds__(128) k_plan_sample_free(PlanDev D, ArmK A) {
 // (ik_solve_group) and the lowest start that converges wins, the same result
 // as trying the starts in order; group 3 repeats start 0 and is ignored.
 __global__ void __launch_bounds__(128) k_plan_sample_goal(PlanDev D, ArmK A) {
+  pdl_begin();
   const long gid = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31, grp = lane >> 3;
   const int p = (int)(gid / D.BM);
@@ -370,6 +382,7 @@ constexpr int kKnnSmem = PL_KNN_WARPS * PL_KNN_RING * 7 * 32 * 16;
 // and later reads only its own 16-byte words, so the ring needs no barrier.
 template <int KM>
 __global__ void __launch_bounds__(32 * PL_KNN_WARPS) k_plan_knn(PlanDev D) {
+  pdl_begin();
   extern __shared__ float4 knn_ring[];   // [warp][slot][7][32]
   const Sched* S = D.sched;
   const int items = S->knn_items;
@@ -479,6 +492,7 @@ __global__ void __launch_bounds__(32 * PL_KNN_WARPS) k_plan_knn(PlanDev D) {
 
 template <int KM>
 __global__ void __launch_bounds__(256) k_plan_knn_merge(PlanDev D) {
+  pdl_begin();
   const int lane = threadIdx.x & 31;
   const long w = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int p = (int)(w / D.BM);
@@ -531,6 +545,7 @@ __device__ __forceinline__ float* knn_mirror_slot(const PlanDev& D, int p, int n
 // parents prep: neighbour lists of single-node trees are empty; tree nodes
 // added (or moved) since the last iteration enter the mirror
 __global__ void k_plan_parents_prep(PlanDev D) {
+  pdl_begin();
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long stride = (long)gridDim.x * blockDim.x;
   const long n = (long)D.P * D.BM * D.KN;
@@ -611,6 +626,7 @@ __device__ __forceinline__ void decode_edge(const PlanDev& D, const Sched* S, in
 }
 
 __global__ void __launch_bounds__(PL_SCAN) k_plan_eprep(PlanDev D, GridKP Gr) {
+  pdl_begin();
   __shared__ float sT[FN_MAX_GRID];
   __shared__ int sh[32];
   for (int i = threadIdx.x; i < D.K; i += blockDim.x) sT[i] = Gr.T[i];
@@ -664,6 +680,7 @@ __global__ void __launch_bounds__(PL_SCAN) k_plan_eprep(PlanDev D, GridKP Gr) {
 
 // exclusive scan of the per-block item totals (one block)
 __global__ void __launch_bounds__(PL_SCAN) k_plan_escan(PlanDev D) {
+  pdl_begin();
   __shared__ int sh[32];
   Sched* S = D.sched;
   const int nb = (S->n_edges + PL_SCAN - 1) / PL_SCAN;
@@ -688,6 +705,7 @@ __device__ __forceinline__ int item_off(const PlanDev& D, int e) {
 
 // item -> owning edge, one warp per edge
 __global__ void __launch_bounds__(256) k_plan_expand(PlanDev D) {
+  pdl_begin();
   const Sched* S = D.sched;
   const int E = S->n_edges, lane = threadIdx.x & 31;
   const long W = (long)gridDim.x * (blockDim.x >> 5);
@@ -705,6 +723,7 @@ __global__ void __launch_bounds__(256) k_plan_expand(PlanDev D) {
 template <int MINB>
 __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_probe(PlanDev D, ArmK A,
                                                                          GridKP Gr) {
+  pdl_begin();
   __shared__ float sT[FN_MAX_GRID];
   __shared__ float sCoef[PL_EDGE_WARPS][FN_CUBIC_WORDS * 32];
   __shared__ float sWr[PL_EDGE_WARPS][FN_WRENCH_WORDS * 32];
@@ -764,6 +783,7 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_probe(PlanDev
 template <int MINB>
 __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_mprobe(PlanDev D, ArmK A,
                                                                           GridKP Gr) {
+  pdl_begin();
   __shared__ float sT[FN_MAX_GRID];
   __shared__ float sCoef[PL_EDGE_WARPS][FN_CUBIC_WORDS * 32];
   __shared__ float sWr[PL_EDGE_WARPS][FN_WRENCH_WORDS * 32];
@@ -824,6 +844,7 @@ __device__ __forceinline__ void edge_slot(const PlanDev& D, int e, long& ei, boo
 // verification start: each edge with probe items either has no survivor
 // (infeasible on the whole admissible grid) or joins the first pending list
 __global__ void k_plan_vinit(PlanDev D) {
+  pdl_begin();
   Sched* S = D.sched;
   const int E = S->n_edges;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
@@ -850,6 +871,7 @@ __global__ void k_plan_vinit(PlanDev D) {
 template <int MINB>
 __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_vstage(PlanDev D, ArmK A,
                                                                           GridKP Gr, int list) {
+  pdl_begin();
   __shared__ float sT[FN_MAX_GRID];
   __shared__ float sCoef[PL_EDGE_WARPS][FN_CUBIC_WORDS * 32];
   __shared__ float sWr[PL_EDGE_WARPS][FN_WRENCH_WORDS * 32];
@@ -932,6 +954,7 @@ __device__ __forceinline__ void finish_edge(const PlanDev& D, const ArmK& A, int
 // after a stage: edges whose duration passed are finished; the others move
 // to their next survivor (next list) or end with no feasible duration
 __global__ void __launch_bounds__(128) k_plan_vselect(PlanDev D, ArmK A, GridKP Gr, int list) {
+  pdl_begin();
   __shared__ float sEs[4][32];
   Sched* S = D.sched;
   const int n = S->n_pend[list];
@@ -969,6 +992,7 @@ __global__ void __launch_bounds__(128) k_plan_vselect(PlanDev D, ArmK A, GridKP 
 }
 
 __global__ void k_plan_vclear(PlanDev D, int list) {
+  pdl_begin();
   if (threadIdx.x == 0) {
     if (list >= 0) D.sched->n_pend[list] = 0;
     else D.sched->n_surv = 0;
@@ -985,6 +1009,7 @@ __global__ void k_plan_vclear(PlanDev D, int list) {
 template <int MINB>
 __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_vseq(PlanDev D, ArmK A,
                                                                         GridKP Gr, int list) {
+  pdl_begin();
   __shared__ float sT[FN_MAX_GRID];
   __shared__ float sEdge[32];
   __shared__ float sCoef[PL_EDGE_WARPS][FN_CUBIC_WORDS * 32];
@@ -1069,6 +1094,7 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_vseq(PlanDev 
 #define PL_ATTACH_THREADS 1024
 
 __global__ void __launch_bounds__(PL_ATTACH_THREADS) k_plan_attach(PlanDev D) {
+  pdl_begin();
   __shared__ int sh[PL_ATTACH_THREADS];
   __shared__ float sJ[PL_ATTACH_THREADS];
   __shared__ int sI[PL_ATTACH_THREADS];
@@ -1165,6 +1191,7 @@ __global__ void __launch_bounds__(PL_ATTACH_THREADS) k_plan_attach(PlanDev D) {
 // Eq. (reach) for every node of every problem (one thread per node): keep
 // the root and the nodes that can reach the object by t_best
 __global__ void __launch_bounds__(128) k_plan_reach(PlanDev D, ArmK A) {
+  pdl_begin();
   const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int p = (int)(gid / D.NC);
   const int i = (int)(gid - (long)p * D.NC);
@@ -1187,6 +1214,7 @@ __global__ void __launch_bounds__(128) k_plan_reach(PlanDev D, ArmK A) {
 }
 
 __global__ void __launch_bounds__(PL_ATTACH_THREADS) k_plan_prune(PlanDev D, ArmK A) {
+  pdl_begin();
   __shared__ int sh[PL_ATTACH_THREADS];
   __shared__ int s_flag;
   const int p = blockIdx.x;
@@ -1264,6 +1292,7 @@ __global__ void __launch_bounds__(PL_ATTACH_THREADS) k_plan_prune(PlanDev D, Arm
 // output: the first segment of the incumbent plan (Algorithm 1's return)
 // ---------------------------------------------------------------------------
 __global__ void k_plan_output(PlanDev D) {
+  pdl_begin();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= D.P) return;
   const long nb = (long)p * D.NC;
@@ -1384,6 +1413,24 @@ static int plan_edge_blocks(fn_planner* pl, int v) {
                            resident_stage(plan_vseq_variant(v))));
 }
 
+// Launch with programmatic stream serialization (see pdl_begin): the
+// kernel may be scheduled while the previous kernel on the stream drains.
+template <class... KArgs, class... Args>
+static void pl_launch(void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                      cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 template <int KM>
 static int knn_blocks(fn_planner* pl) {
   (void)pl;
@@ -1411,19 +1458,19 @@ static void enqueue_front(fn_planner* pl, unsigned flags, cudaStream_t st, Mark&
   const int P = pl->cfg.P;
   if (!(flags & FN_PLAN_EXTERNAL)) {
     const long n = (long)P * D.BM;
-    k_plan_sample_goal<<<(unsigned)((32 * n + 127) / 128), 128, 0, st>>>(D, pl->arm);
-    k_plan_sample_free<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(D, pl->arm);
+    pl_launch(k_plan_sample_goal, (unsigned)((32 * n + 127) / 128), 128, 0, st, D, pl->arm);
+    pl_launch(k_plan_sample_free, (unsigned)((n + 127) / 128), 128, 0, st, D, pl->arm);
   }
   mark(2);
   if (pl->cfg.k > 1) {
-    k_plan_parents_prep<<<2 * num_sms(), 256, 0, st>>>(D);
+    pl_launch(k_plan_parents_prep, 2 * num_sms(), 256, 0, st, D);
     const unsigned mb = (unsigned)(((long)P * D.BM + 7) / 8);
     if (D.KM == 8) {
-      k_plan_knn<8><<<knn_blocks<8>(pl), 32 * PL_KNN_WARPS, kKnnSmem, st>>>(D);
-      k_plan_knn_merge<8><<<mb, 256, 0, st>>>(D);
+      pl_launch(k_plan_knn<8>, knn_blocks<8>(pl), 32 * PL_KNN_WARPS, kKnnSmem, st, D);
+      pl_launch(k_plan_knn_merge<8>, mb, 256, 0, st, D);
     } else {
-      k_plan_knn<16><<<knn_blocks<16>(pl), 32 * PL_KNN_WARPS, kKnnSmem, st>>>(D);
-      k_plan_knn_merge<16><<<mb, 256, 0, st>>>(D);
+      pl_launch(k_plan_knn<16>, knn_blocks<16>(pl), 32 * PL_KNN_WARPS, kKnnSmem, st, D);
+      pl_launch(k_plan_knn_merge<16>, mb, 256, 0, st, D);
     }
   }
 }
@@ -1436,25 +1483,25 @@ template <class Mark>
 static void enqueue_edges(fn_planner* pl, int v, int blocks, cudaStream_t st, Mark&& mark) {
   PlanDev& D = pl->D;
   const int eb = (D.Emax + PL_SCAN - 1) / PL_SCAN;
-  k_plan_eprep<<<eb, PL_SCAN, 0, st>>>(D, pl->grid);
-  k_plan_escan<<<1, PL_SCAN, 0, st>>>(D);
-  k_plan_vclear<<<1, 32, 0, st>>>(D, 0);
-  k_plan_vclear<<<1, 32, 0, st>>>(D, -1);
-  k_plan_expand<<<4 * num_sms(), 256, 0, st>>>(D);
+  pl_launch(k_plan_eprep, eb, PL_SCAN, 0, st, D, pl->grid);
+  pl_launch(k_plan_escan, 1, PL_SCAN, 0, st, D);
+  pl_launch(k_plan_vclear, 1, 32, 0, st, D, 0);
+  pl_launch(k_plan_vclear, 1, 32, 0, st, D, -1);
+  pl_launch(k_plan_expand, 4 * num_sms(), 256, 0, st, D);
   mark(4);
-  plan_probe_variant(v)<<<blocks, 32 * PL_EDGE_WARPS, 0, st>>>(D, pl->arm, pl->grid);
-  plan_mprobe_variant(v)<<<blocks, 32 * PL_EDGE_WARPS, 0, st>>>(D, pl->arm, pl->grid);
+  pl_launch(plan_probe_variant(v), blocks, 32 * PL_EDGE_WARPS, 0, st, D, pl->arm, pl->grid);
+  pl_launch(plan_mprobe_variant(v), blocks, 32 * PL_EDGE_WARPS, 0, st, D, pl->arm, pl->grid);
   mark(5);
   const int tb = 2 * num_sms();
-  k_plan_vinit<<<tb, 256, 0, st>>>(D);
+  pl_launch(k_plan_vinit, tb, 256, 0, st, D);
   int list = 0;
   for (int stage = 0; stage < PL_VSTAGES; ++stage) {
-    k_plan_vclear<<<1, 32, 0, st>>>(D, list ^ 1);
-    plan_vstage_variant(v)<<<blocks, 32 * PL_EDGE_WARPS, 0, st>>>(D, pl->arm, pl->grid, list);
-    k_plan_vselect<<<tb, 128, 0, st>>>(D, pl->arm, pl->grid, list);
+    pl_launch(k_plan_vclear, 1, 32, 0, st, D, list ^ 1);
+    pl_launch(plan_vstage_variant(v), blocks, 32 * PL_EDGE_WARPS, 0, st, D, pl->arm, pl->grid, list);
+    pl_launch(k_plan_vselect, tb, 128, 0, st, D, pl->arm, pl->grid, list);
     list ^= 1;
   }
-  plan_vseq_variant(v)<<<blocks, 32 * PL_EDGE_WARPS, 0, st>>>(D, pl->arm, pl->grid, list);
+  pl_launch(plan_vseq_variant(v), blocks, 32 * PL_EDGE_WARPS, 0, st, D, pl->arm, pl->grid, list);
 }
 
 extern "C" fn_status fn_planner_destroy(fn_planner_t* pl) {
@@ -1651,15 +1698,15 @@ static fn_status enqueue_iteration(fn_planner* pl, unsigned flags, cudaStream_t 
   mark(3);
   enqueue_edges(pl, pl->edge_variant, pl->edge_blocks, st, mark);
   mark(6);
-  k_plan_attach<<<P, PL_ATTACH_THREADS, 0, st>>>(D);
+  pl_launch(k_plan_attach, P, PL_ATTACH_THREADS, 0, st, D);
   mark(7);
   if (flags & FN_PLAN_PRUNE) {
     const long nn = (long)P * D.NC;
-    k_plan_reach<<<(unsigned)((nn + 127) / 128), 128, 0, st>>>(D, pl->arm);
-    k_plan_prune<<<P, PL_ATTACH_THREADS, 0, st>>>(D, pl->arm);
+    pl_launch(k_plan_reach, (unsigned)((nn + 127) / 128), 128, 0, st, D, pl->arm);
+    pl_launch(k_plan_prune, P, PL_ATTACH_THREADS, 0, st, D, pl->arm);
   }
   mark(8);
-  k_plan_output<<<(P + 127) / 128, 128, 0, st>>>(D);
+  pl_launch(k_plan_output, (P + 127) / 128, 128, 0, st, D);
   mark(9);
   if (cudaMemcpyAsync(pl->h_out, D.out, sizeof(fn_rendezvous_t) * P, cudaMemcpyDeviceToHost, st) !=
       cudaSuccess)

@@ -86,6 +86,38 @@ def test_plan_round_parity(P, orc, arm, seed):
     assert par[0] == -1 and np.all(par[1:] < np.arange(1, gtree["n"]))
 
 
+@pytest.mark.parametrize("seed,delta", [(0, 0.05), (1, 0.1)])
+def test_plan_round_goal_attach(P, orc, arm, seed, delta):
+    """Goal edges that succeed: the tree holds, for each decoded goal, an
+    approach node delta seconds earlier on the goal's velocity line
+    (q_g - delta qd_g, qd_g).  The rendezvous nodes, their scores and the
+    incumbent (Eq. (objective), the t_best update and the first segment)
+    must match the oracle's round."""
+    case = make_case(arm, orc, 40 + seed, N=150, n_free=32)
+    states, t, parent = case["tree"]
+    G = case["n_goal"]
+    g = case["cand"][:G].astype(np.float64)
+    appr = g.copy()
+    appr[:, :7] = g[:, :7] - delta * g[:, 8:15]
+    appr = appr.astype(np.float32)
+    t_app = (case["T_req"] - np.float32(delta)).astype(np.float32)
+    case["tree"] = (np.concatenate([states, appr]), np.concatenate([t, t_app]),
+                    np.concatenate([parent, np.zeros(G, parent.dtype)]))
+    out, gtree, rtree, rinc, det, grid = run_pair(P, orc, arm, case)
+    N = case["tree"][0].shape[0]
+    assert rinc["id"] >= 0, "the oracle attached no goal: the case does not exercise the incumbent"
+    bad = compare_round(orc, arm, case, gtree, rtree, det, N, grid)
+    assert not bad, f"candidates attached differently without a near-margin edge: {bad[:5]}"
+    assert out["incumbent"] >= 0
+    assert out["J"] == pytest.approx(rinc["J"], rel=1e-4, abs=1e-4)
+    assert out["t_best"] == pytest.approx(rinc["t_best"], rel=1e-6)
+    seg = OP.first_segment(rtree, rinc)
+    assert np.array_equal(out["q_g"], seg[0][:7])
+    # scores: rendezvous nodes carry finite J, the others NaN
+    Jg = gtree["J"][N:gtree["n"]]
+    assert np.sum(np.isfinite(Jg)) >= 1
+
+
 def test_plan_round_with_obstacles(P, orc, arm):
     obs = synth.obstacles(5, 3)
     case = make_case(arm, orc, 2, N=200, n_free=64)
