@@ -6,10 +6,10 @@ python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 One step = one pass of the planning iteration's hot path over one batch of
 seeded synthetic input (tree of 4096 nodes, batch of 2048 candidates, k = 8
-parents, K = 128 durations, S = 64 collocation points).  Timing follows the
-contract in the project notes: W untimed warm-up steps, then K steps timed
-with CUDA events on the launching stream, L2 flushed between timed steps
-(outside the events), max over ranks, one JSON line from rank 0.
+parents, K = 128 durations, S = 64 collocation points).  Timing: W untimed
+warm-up steps, then K steps timed with CUDA events on the launching stream,
+L2 flushed between timed steps (outside the events), max over ranks, one
+JSON line from rank 0.
 """
 from __future__ import annotations
 
@@ -28,7 +28,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "verified min-time cubic edges/sec (FP32, oracle-matched) and p99 planning-iteration ms"
 UNIT = "edges/s"
-FLOP_PER_SAMPLE = 1379  # algorithmic FP32 FLOP of one torque evaluation (FMA = 2), see the design doc
+FLOP_PER_SAMPLE = 1379  # algorithmic FP32 FLOP of one torque evaluation (FMA = 2)
 N_TREE, B_CAND, K_PAR, K_GRID, S_COLL = 4096, 2048, 8, 128, 64
 WORKLOAD = "one planning iteration: tree 4096, batch 2048 (1024 goal-chart + 1024 uniform), k=8, K=128, S=64"
 
@@ -212,15 +212,24 @@ def run_ours(args, rank, world):
     for i in range(args.warmup):
         reset_tree()
         pl.iterate([prob], i, 0, stream=stream)
-    # work counter of the edge kernel for one step (same inputs -> same work)
+    # one traced iteration (not timed as a step): the kernels' work counters
+    # and the duration of every launch from CUDA events on the stream
     reset_tree()
-    pl.sample_count(reset=True)
+    pl.work_counts(reset=True)
     pl.iterate([prob], 0, 0, stream=stream)
-    samples = pl.sample_count(reset=True)
+    work = pl.work_counts(reset=True)
+    traced = pl.kernel_ms()
+    phases = pl.phase_ms()
+    # the timed path: the iteration captured once as a CUDA graph, replayed
+    reset_tree()
+    pl.capture(0, stream=stream)
+    for i in range(max(args.warmup, 3)):
+        reset_tree()
+        pl.replay([prob], 0, stream=stream)
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    probe_ms, verify_ms, added = [], [], []
+    added = []
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -234,17 +243,13 @@ def run_ours(args, rank, world):
             with torch.cuda.stream(stream):
                 flush.zero_()                         # L2 flush between timed steps (untimed)
             starts[i].record(stream)
-            out = pl.iterate([prob], 0, 0, stream=stream)[0]
+            out = pl.replay([prob], 0, stream=stream)[0]
             ends[i].record(stream)
-            ph = pl.phase_ms()
-            probe_ms.append(ph["probe"])
-            verify_ms.append(ph["verify"])
             added.append(out["n_added"])
         torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     step_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
-    phases = pl.phase_ms()
 
     # end to end through the public API with host buffers: the tree and the
     # problem go host -> device, the rendezvous comes back, every step
@@ -253,7 +258,7 @@ def run_ours(args, rank, world):
     for i in range(args.steps):
         pl.reset([prob], stream=stream)
         pl.load_tree(0, w["tree"], w["t_node"], w["parent"], stream=stream)
-        pl.iterate([prob], 0, 0, stream=stream)
+        pl.replay([prob], 0, stream=stream)
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
     h2d = w["tree"].nbytes + w["t_node"].nbytes + w["parent"].nbytes + 2 * 416
@@ -271,14 +276,7 @@ def run_ours(args, rank, world):
         return None
     ms_per_step = tot_ms / args.steps
     value = edges * world / (ms_per_step / 1e3)
-    # dominant kernel of the edge phase (probe or verify): its own launch time
-    dom = "probe" if np.mean(probe_ms) >= np.mean(verify_ms) else "verify"
-    kavg_s = float(np.mean(probe_ms if dom == "probe" else verify_ms)) / 1e3
-    flops = samples[dom] * FLOP_PER_SAMPLE
-    peak = fp32_peak_tflops()
-    ach = flops / kavg_s / 1e12
-    other = "verify" if dom == "probe" else "probe"
-    other_s = float(np.mean(verify_ms if dom == "probe" else probe_ms)) / 1e3
+    roof = roofline_from_trace(traced, work)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "p99_ms": p99,
@@ -288,23 +286,73 @@ def run_ours(args, rank, world):
                    "K": K_GRID, "S": S_COLL, "edges_per_step": edges,
                    "nodes_added_mean": float(np.mean(added)),
                    "edge_variant": tuned[0], "edge_variant_ms": tuned[1],
+                   "timed_path": "fn_planner_capture once, fn_plan_replay per step (CUDA graph)",
                    "parallelism": f"replicas x{world}", "l2": "flushed between timed steps"},
         "phases_ms": phases,
+        "kernels_ms": kernel_table(traced),
+        "work": work,
         "clocks": clk.summary(),
         "e2e": {"value": edges * world / (e2e_ms / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": 9 * args.steps,
-        "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                     "frac": ach / peak, "traffic": None,
-                     "kernel": f"k_plan_{dom}",
-                     "flop_per_launch": flops, "samples_per_launch": samples[dom],
-                     "kernel_ms": kavg_s * 1e3,
-                     "other_edge_kernel": {"kernel": f"k_plan_{other}", "ms": other_s * 1e3,
-                                           "samples": samples[other],
-                                           "tflops": samples[other] * FLOP_PER_SAMPLE / max(other_s, 1e-12) / 1e12},
-                     "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 FLOP x max SM clock (of derived)"},
+        "gpu_launches": len(traced) * args.steps,
+        "roofline": roof,
     }
     return line, w
+
+
+# algorithmic work per unit of each kernel (FLOP; FMA = 2): a distance is
+# 14 subtractions, 14 FMAs and one FMA for the weight; an IK start is 24
+# iterations of (FK 475, residual 48, Jacobian 72, J J^T 237, LDL^T 91,
+# solves 66, update 72) plus a final FK and residual (523)
+FLOP_PER_PAIR = 44             # one (query, node) distance of the parent search
+FLOP_PER_IK_START = 25987      # one damped-least-squares start, 24 iterations + final check
+
+
+def kernel_table(traced):
+    """{kernel: {"launches": n, "ms": total}} of one traced iteration."""
+    tab = {}
+    for name, ms in traced:
+        t = tab.setdefault(name, {"launches": 0, "ms": 0.0})
+        t["launches"] += 1
+        t["ms"] += ms
+    return tab
+
+
+def roofline_from_trace(traced, work):
+    """Roofline object for the kernel with the largest share of the traced
+    iteration: its algorithmic FLOP (work counter x FLOP per unit) over its
+    own event-timed duration, against the derived FP32 peak."""
+    tab = kernel_table(traced)
+    units = {"k_plan_probe": (work["probe"], FLOP_PER_SAMPLE, "torque evaluations"),
+             "k_plan_mprobe": (work["mprobe"], FLOP_PER_SAMPLE, "torque evaluations"),
+             "k_plan_vstage": (None, FLOP_PER_SAMPLE, "torque evaluations"),
+             "k_plan_knn": (work["knn_pairs"], FLOP_PER_PAIR, "(query, node) pairs"),
+             "k_plan_sample_goal": (work["ik_starts"], FLOP_PER_IK_START, "IK starts")}
+    dom = max(tab, key=lambda k: tab[k]["ms"])
+    peak = fp32_peak_tflops()
+    total = sum(t["ms"] for t in tab.values())
+    out = {"bound": "alu", "peak": peak, "unit": "TFLOP/s", "traffic": None, "kernel": dom,
+           "launches": tab[dom]["launches"], "kernel_ms": tab[dom]["ms"] / tab[dom]["launches"],
+           "share_of_traced_iteration": tab[dom]["ms"] / total,
+           "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 FLOP x max SM clock (of derived)"}
+    n, f, what = units.get(dom, (None, None, None))
+    if n is None:
+        out.update({"achieved": None, "frac": None,
+                    "note": "no algorithmic work counter for this kernel"})
+    else:
+        flops = n * f / tab[dom]["launches"]
+        ach = flops / (out["kernel_ms"] / 1e3) / 1e12
+        out.update({"achieved": ach, "frac": ach / peak, "flop_per_launch": flops,
+                    "units_per_launch": n / tab[dom]["launches"], "unit_of_work": what,
+                    "flop_per_unit": f})
+    # the edge-timing kernels (the RNEA hot path) for reference
+    edge = {}
+    for k in ("k_plan_probe", "k_plan_mprobe"):
+        if k in tab:
+            n, f, _ = units[k]
+            edge[k] = {"ms": tab[k]["ms"], "tflops": n * f / (tab[k]["ms"] / 1e3) / 1e12}
+    out["edge_kernels"] = edge
+    return out
 
 
 def fp32_peak_tflops():

@@ -392,11 +392,26 @@ fn_status fn_planner_autotune(fn_planner_t* pl, const fn_problem_t* probs, int i
  * before the first fn_plan_iteration. */
 fn_status fn_planner_phase_ms(fn_planner_t* pl, float* ms);
 
+/* Durations in ms of every kernel launch of the last fn_plan_iteration, in
+ * launch order, from CUDA events recorded on its stream after each launch
+ * (so a launch's time includes its wait for the previous one to drain).
+ * names[i]: the kernel's name (static strings owned by the library).
+ * ms, names: host [cap]; *n = launches traced (up to 40; min(n, cap)
+ * written).  FN_EINVAL before the first fn_plan_iteration. */
+fn_status fn_planner_kernel_ms(fn_planner_t* pl, float* ms, const char** names, int cap, int* n);
+
 /* Torque evaluations (edge, duration, sample) performed by the planner's
- * edge kernels since creation or the last reset (reset != 0 zeroes them):
- * count[0] by the probe kernel, count[1] by the verify kernel.  count: host
- * [2]. */
+ * edge kernels since creation or the last reset (reset != 0 zeroes every
+ * work counter): count[0] by the probe stages (end and interior samples),
+ * count[1] by the verify stages.  count: host [2]. */
 fn_status fn_planner_sample_count(fn_planner_t* pl, unsigned long long* count, int reset);
+
+/* All work counters of the planner's kernels since creation or the last
+ * reset: [0] torque evaluations of the end-sample probe, [1] of the verify
+ * stages, [2] of the interior-sample probe, [3] (query, node) distance
+ * evaluations of the parent search, [4] IK starts run by the goal sampler.
+ * count: host [n] (n <= 5 written).  reset != 0 zeroes them all. */
+fn_status fn_planner_work_counts(fn_planner_t* pl, unsigned long long* count, int n, int reset);
 
 /* Copy problem p's tree to host (any pointer may be NULL): states [n][16],
  * t[n], parent[n], J[n] (NaN for non-rendezvous nodes), nu[n]; *n = size.

@@ -35,6 +35,8 @@
 #define PL_KNN_QW 1                           // queries per warp
 #define PL_KNN_SPAN 4096                      // nodes per split (at least)
 #define PL_MAX_P 1024
+#define PL_MAX_KEV 40                         // launches traced per iteration
+#define PL_NCOUNT 5   // work counters: probe, verify, mid-probe, kNN pairs, IK starts
 
 namespace fn {
 
@@ -96,7 +98,8 @@ struct PlanDev {  // device pointers, passed by value to the kernels
   float* tmp_st;      // [P][NC][16]
   float* tmp_f;       // [P][NC][4]  (t, J, nu, eT)
   int32_t* tmp_par;   // [P][NC]
-  unsigned long long* samples;  // work counters (torque evaluations): [0] probe, [1] verify
+  unsigned long long* samples;  // work counters: torque evaluations [0] probe, [1] verify,
+                                // [2] mid-probe; [3] kNN (query, node) pairs; [4] IK starts
   // packed edge phase (flat edge index e in queue order)
   int32_t* e_ci;      // [E] candidate slot p*BM + b
   int32_t* e_par;     // [E] parent node (-1: invalid edge)
@@ -286,6 +289,7 @@ __global__ void __launch_bounds__(128) k_plan_sample_goal(PlanDev D, ArmK A) {
   int winner = -1;
   float q[7];
   if (defined) {
+    if (D.samples && lane == 0) atomicAdd(D.samples + 4, (unsigned long long)FN_IK_STARTS);
     float qs;
     const bool found = ik_solve_group(A, o.Rg, o.pg, o.q7, grp < FN_IK_STARTS ? grp : 0, qs);
     const unsigned won = __ballot_sync(0xffffffffu, found && (lane & 7) == 0 && grp < FN_IK_STARTS);
@@ -474,6 +478,12 @@ __global__ void __launch_bounds__(32 * PL_KNN_WARPS) k_plan_knn(PlanDev D) {
       }
     }
     cp_async_wait<0>();
+    if (D.samples && lane == 0 && wact) {
+      int nq = 0;
+#pragma unroll
+      for (int a = 0; a < PL_KNN_QW; ++a) nq += b0 + a < B && D.valid[(long)p * D.BM + b0 + a];
+      atomicAdd(D.samples + 3, (unsigned long long)nq * (unsigned long long)max(hi - lo, 0));
+    }
 #pragma unroll
     for (int a = 0; a < PL_KNN_QW; ++a) {
       const int b = b0 + a;
@@ -823,7 +833,7 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_mprobe(PlanDe
     if (live && !(a <= 1.f && b <= 1.f))
       atomicAnd(&D.mask[8L * e + (k >> 5)], ~(1u << (k & 31)));
   }
-  if (D.samples && lane == 0 && nsamp) atomicAdd(D.samples + 0, (unsigned long long)nsamp);
+  if (D.samples && lane == 0 && nsamp) atomicAdd(D.samples + 2, (unsigned long long)nsamp);
 }
 
 // first survivor at or after grid index `from`; -1 if none
@@ -1343,7 +1353,19 @@ struct fn_planner {
   // verify, attach, prune, output
   cudaEvent_t ev[10] = {};
   bool timing = false;
+  // per-launch events of a timed iteration (kev[0] before the first launch)
+  cudaEvent_t kev[PL_MAX_KEV + 1] = {};
+  const char* kname[PL_MAX_KEV] = {};
+  int nk = 0;
+  bool tracing = false;
 };
+
+// record the end of the launch just issued (timed iterations only)
+static void trace(fn_planner* pl, cudaStream_t st, const char* name) {
+  if (!pl->tracing || pl->nk >= PL_MAX_KEV) return;
+  pl->kname[pl->nk] = name;
+  cudaEventRecord(pl->kev[++pl->nk], st);
+}
 
 static fn_status pl_alloc(fn_planner* pl, void** p, size_t bytes) {
   if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) return FN_ENOMEM;
@@ -1459,18 +1481,25 @@ static void enqueue_front(fn_planner* pl, unsigned flags, cudaStream_t st, Mark&
   if (!(flags & FN_PLAN_EXTERNAL)) {
     const long n = (long)P * D.BM;
     pl_launch(k_plan_sample_goal, (unsigned)((32 * n + 127) / 128), 128, 0, st, D, pl->arm);
+    trace(pl, st, "k_plan_sample_goal");
     pl_launch(k_plan_sample_free, (unsigned)((n + 127) / 128), 128, 0, st, D, pl->arm);
+    trace(pl, st, "k_plan_sample_free");
   }
   mark(2);
   if (pl->cfg.k > 1) {
     pl_launch(k_plan_parents_prep, 2 * num_sms(), 256, 0, st, D);
+    trace(pl, st, "k_plan_parents_prep");
     const unsigned mb = (unsigned)(((long)P * D.BM + 7) / 8);
     if (D.KM == 8) {
       pl_launch(k_plan_knn<8>, knn_blocks<8>(pl), 32 * PL_KNN_WARPS, kKnnSmem, st, D);
+      trace(pl, st, "k_plan_knn");
       pl_launch(k_plan_knn_merge<8>, mb, 256, 0, st, D);
+      trace(pl, st, "k_plan_knn_merge");
     } else {
       pl_launch(k_plan_knn<16>, knn_blocks<16>(pl), 32 * PL_KNN_WARPS, kKnnSmem, st, D);
+      trace(pl, st, "k_plan_knn");
       pl_launch(k_plan_knn_merge<16>, mb, 256, 0, st, D);
+      trace(pl, st, "k_plan_knn_merge");
     }
   }
 }
@@ -1484,29 +1513,43 @@ static void enqueue_edges(fn_planner* pl, int v, int blocks, cudaStream_t st, Ma
   PlanDev& D = pl->D;
   const int eb = (D.Emax + PL_SCAN - 1) / PL_SCAN;
   pl_launch(k_plan_eprep, eb, PL_SCAN, 0, st, D, pl->grid);
+  trace(pl, st, "k_plan_eprep");
   pl_launch(k_plan_escan, 1, PL_SCAN, 0, st, D);
+  trace(pl, st, "k_plan_escan");
   pl_launch(k_plan_vclear, 1, 32, 0, st, D, 0);
+  trace(pl, st, "k_plan_vclear");
   pl_launch(k_plan_vclear, 1, 32, 0, st, D, -1);
+  trace(pl, st, "k_plan_vclear");
   pl_launch(k_plan_expand, 4 * num_sms(), 256, 0, st, D);
+  trace(pl, st, "k_plan_expand");
   mark(4);
   pl_launch(plan_probe_variant(v), blocks, 32 * PL_EDGE_WARPS, 0, st, D, pl->arm, pl->grid);
+  trace(pl, st, "k_plan_probe");
   pl_launch(plan_mprobe_variant(v), blocks, 32 * PL_EDGE_WARPS, 0, st, D, pl->arm, pl->grid);
+  trace(pl, st, "k_plan_mprobe");
   mark(5);
   const int tb = 2 * num_sms();
   pl_launch(k_plan_vinit, tb, 256, 0, st, D);
+  trace(pl, st, "k_plan_vinit");
   int list = 0;
   for (int stage = 0; stage < PL_VSTAGES; ++stage) {
     pl_launch(k_plan_vclear, 1, 32, 0, st, D, list ^ 1);
+    trace(pl, st, "k_plan_vclear");
     pl_launch(plan_vstage_variant(v), blocks, 32 * PL_EDGE_WARPS, 0, st, D, pl->arm, pl->grid, list);
+    trace(pl, st, "k_plan_vstage");
     pl_launch(k_plan_vselect, tb, 128, 0, st, D, pl->arm, pl->grid, list);
+    trace(pl, st, "k_plan_vselect");
     list ^= 1;
   }
   pl_launch(plan_vseq_variant(v), blocks, 32 * PL_EDGE_WARPS, 0, st, D, pl->arm, pl->grid, list);
+  trace(pl, st, "k_plan_vseq");
 }
 
 extern "C" fn_status fn_planner_destroy(fn_planner_t* pl) {
   if (!pl) return FN_EINVAL;
   for (cudaEvent_t e : pl->ev)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : pl->kev)
     if (e) cudaEventDestroy(e);
   if (pl->graph_exec) cudaGraphExecDestroy(pl->graph_exec);
   if (pl->graph) cudaGraphDestroy(pl->graph);
@@ -1560,7 +1603,7 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
   A_(D.added, P); A_(D.status, P);
   A_(D.ptr, P * NC); A_(D.newidx, P * NC); A_(D.alive, P * NC);
   A_(D.tmp_st, P * NC * 16); A_(D.tmp_f, P * NC * 4); A_(D.tmp_par, P * NC);
-  A_(D.samples, 2);
+  A_(D.samples, PL_NCOUNT);
   D.Emax = (int)(P * BM * KP);
   A_(D.e_ci, (size_t)D.Emax); A_(D.e_par, (size_t)D.Emax); A_(D.e_Tp, (size_t)D.Emax);
   A_(D.e_j, (size_t)D.Emax); A_(D.e_cnt, (size_t)D.Emax);
@@ -1585,7 +1628,7 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
       rc = FN_ENOMEM;
   }
   if (rc == FN_OK && (cudaMemset(D.n_nodes, 0, P * sizeof(int)) != cudaSuccess ||
-                      cudaMemset(D.samples, 0, 2 * sizeof(unsigned long long)) != cudaSuccess))
+                      cudaMemset(D.samples, 0, PL_NCOUNT * sizeof(unsigned long long)) != cudaSuccess))
     rc = FN_ECUDA;
   if (rc != FN_OK) {
     fn_planner_destroy(pl);
@@ -1593,6 +1636,11 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
   }
   for (int i = 0; i < 10; ++i)
     if (cudaEventCreate(&pl->ev[i]) != cudaSuccess) {
+      fn_planner_destroy(pl);
+      return FN_ECUDA;
+    }
+  for (int i = 0; i <= PL_MAX_KEV; ++i)
+    if (cudaEventCreate(&pl->kev[i]) != cudaSuccess) {
       fn_planner_destroy(pl);
       return FN_ECUDA;
     }
@@ -1692,21 +1740,30 @@ static fn_status enqueue_iteration(fn_planner* pl, unsigned flags, cudaStream_t 
     if (timed) cudaEventRecord(pl->ev[i], st);
   };
   mark(0);
+  pl->tracing = timed;
+  pl->nk = 0;
+  if (timed) cudaEventRecord(pl->kev[0], st);
   k_plan_schedule<<<1, 32, 0, st>>>(D);
+  trace(pl, st, "k_plan_schedule");
   mark(1);
   enqueue_front(pl, flags, st, mark);
   mark(3);
   enqueue_edges(pl, pl->edge_variant, pl->edge_blocks, st, mark);
   mark(6);
   pl_launch(k_plan_attach, P, PL_ATTACH_THREADS, 0, st, D);
+  trace(pl, st, "k_plan_attach");
   mark(7);
   if (flags & FN_PLAN_PRUNE) {
     const long nn = (long)P * D.NC;
     pl_launch(k_plan_reach, (unsigned)((nn + 127) / 128), 128, 0, st, D, pl->arm);
+    trace(pl, st, "k_plan_reach");
     pl_launch(k_plan_prune, P, PL_ATTACH_THREADS, 0, st, D, pl->arm);
+    trace(pl, st, "k_plan_prune");
   }
   mark(8);
   pl_launch(k_plan_output, (P + 127) / 128, 128, 0, st, D);
+  trace(pl, st, "k_plan_output");
+  pl->tracing = false;
   mark(9);
   if (cudaMemcpyAsync(pl->h_out, D.out, sizeof(fn_rendezvous_t) * P, cudaMemcpyDeviceToHost, st) !=
       cudaSuccess)
@@ -1739,6 +1796,19 @@ extern "C" fn_status fn_planner_phase_ms(fn_planner_t* pl, float* ms) {
   if (!pl->timing) return FN_EINVAL;
   for (int i = 0; i < 9; ++i)
     if (cudaEventElapsedTime(&ms[i], pl->ev[i], pl->ev[i + 1]) != cudaSuccess) return FN_ECUDA;
+  return FN_OK;
+}
+
+// durations (ms) of every kernel launch of the last fn_plan_iteration
+extern "C" fn_status fn_planner_kernel_ms(fn_planner_t* pl, float* ms, const char** names, int cap,
+                                          int* n) {
+  if (!pl || !n || cap < 0 || (cap > 0 && (!ms || !names))) return FN_EINVAL;
+  if (!pl->timing) return FN_EINVAL;
+  *n = pl->nk;
+  for (int i = 0; i < pl->nk && i < cap; ++i) {
+    if (cudaEventElapsedTime(&ms[i], pl->kev[i], pl->kev[i + 1]) != cudaSuccess) return FN_ECUDA;
+    names[i] = pl->kname[i];
+  }
   return FN_OK;
 }
 
@@ -1832,14 +1902,25 @@ extern "C" fn_status fn_planner_get_parents(fn_planner_t* pl, int p, int32_t* nn
 
 // work counters of the edge kernels (torque evaluations since the last
 // reset): count[0] probe, count[1] verify
+extern "C" fn_status fn_planner_work_counts(fn_planner_t* pl, unsigned long long* count, int n,
+                                            int reset) {
+  if (!pl || !count || n < 0) return FN_EINVAL;
+  unsigned long long c[PL_NCOUNT];
+  if (cudaMemcpy(c, pl->D.samples, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return FN_ECUDA;
+  for (int i = 0; i < n && i < PL_NCOUNT; ++i) count[i] = c[i];
+  if (reset && cudaMemset(pl->D.samples, 0, sizeof(c)) != cudaSuccess) return FN_ECUDA;
+  return FN_OK;
+}
+
 extern "C" fn_status fn_planner_sample_count(fn_planner_t* pl, unsigned long long* count,
                                              int reset) {
   if (!pl || !count) return FN_EINVAL;
-  if (cudaMemcpy(count, pl->D.samples, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost) !=
-      cudaSuccess)
-    return FN_ECUDA;
-  if (reset && cudaMemset(pl->D.samples, 0, 2 * sizeof(unsigned long long)) != cudaSuccess)
-    return FN_ECUDA;
+  unsigned long long c[PL_NCOUNT];
+  const fn_status rc = fn_planner_work_counts(pl, c, PL_NCOUNT, reset);
+  if (rc != FN_OK) return rc;
+  count[0] = c[0] + c[2];   // both probe stages
+  count[1] = c[1];
   return FN_OK;
 }
 

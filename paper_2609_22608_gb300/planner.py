@@ -61,12 +61,15 @@ def _bind():
     L.fn_planner_get_parents.argtypes = [vp, i32, vp, i32]
     L.fn_planner_sample_count.argtypes = [vp, vp, i32]
     L.fn_planner_phase_ms.argtypes = [vp, vp]
+    L.fn_planner_kernel_ms.argtypes = [vp, vp, vp, i32, C.POINTER(C.c_int)]
+    L.fn_planner_work_counts.argtypes = [vp, vp, i32, i32]
     L.fn_planner_autotune.argtypes = [vp, vp, i32, C.c_uint, i32, vp, vp, vp]
     for n in ("fn_planner_create", "fn_planner_destroy", "fn_planner_reset", "fn_planner_load_tree",
               "fn_planner_set_candidates", "fn_plan_iteration", "fn_planner_capture",
               "fn_plan_replay", "fn_planner_get_tree", "fn_planner_get_candidates",
               "fn_planner_get_parents",
-              "fn_planner_sample_count", "fn_planner_phase_ms", "fn_planner_autotune"):
+              "fn_planner_sample_count", "fn_planner_phase_ms", "fn_planner_autotune",
+              "fn_planner_kernel_ms", "fn_planner_work_counts"):
         getattr(L, n).restype = i32
     L._planner_bound = True
     return L
@@ -229,6 +232,26 @@ class Planner:
         ms = (C.c_float * 9)()
         check(lib().fn_planner_phase_ms(self.h, ms), "fn_planner_phase_ms")
         return dict(zip(self.PHASES, [float(x) for x in ms]))
+
+    def kernel_ms(self):
+        """fn_planner_kernel_ms: [(kernel name, ms)] of every launch of the
+        last fn_plan_iteration, in launch order."""
+        cap = 64
+        ms = (C.c_float * cap)()
+        names = (C.c_char_p * cap)()
+        n = C.c_int()
+        check(_bind().fn_planner_kernel_ms(self.h, ms, names, cap, C.byref(n)),
+              "fn_planner_kernel_ms")
+        return [(names[i].decode(), float(ms[i])) for i in range(min(n.value, cap))]
+
+    WORK = ("probe", "verify", "mprobe", "knn_pairs", "ik_starts")
+
+    def work_counts(self, reset=False):
+        """fn_planner_work_counts: dict of the planner's work counters."""
+        c = (C.c_ulonglong * 5)()
+        check(_bind().fn_planner_work_counts(self.h, c, 5, int(bool(reset))),
+              "fn_planner_work_counts")
+        return dict(zip(self.WORK, [int(x) for x in c]))
 
     def sample_count(self, reset=False):
         """Torque evaluations of the edge kernels: dict(probe=..., verify=...)."""
