@@ -327,7 +327,9 @@ def roofline_from_trace(traced, work):
              "k_plan_mprobe": (work["mprobe"], FLOP_PER_SAMPLE, "torque evaluations"),
              "k_plan_vstage": (None, FLOP_PER_SAMPLE, "torque evaluations"),
              "k_plan_knn": (work["knn_pairs"], FLOP_PER_PAIR, "(query, node) pairs"),
-             "k_plan_sample_goal": (work["ik_starts"], FLOP_PER_IK_START, "IK starts")}
+             "k_plan_sample": (work["ik_starts"], FLOP_PER_IK_START,
+                               "IK starts (the goal chart's; the uniform draws and the tree "
+                               "mirror update in the same launch are not credited)")}
     dom = max(tab, key=lambda k: tab[k]["ms"])
     peak = fp32_peak_tflops()
     total = sum(t["ms"] for t in tab.values())

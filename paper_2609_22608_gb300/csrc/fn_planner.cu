@@ -6,18 +6,22 @@
 // per-problem counts (tree size, incumbent, t_best) live in device memory,
 // so an iteration never reads anything back before its end and can be
 // captured as a CUDA graph.  One iteration is a fixed sequence of launches
-// over all problems:
-//   schedule  : per-problem work offsets, work-queue reset
-//   sample    : goal chart / uniform candidates (Philox counters)
-//   knn       : flattened (problem, query tile, node split) work items
-//   knn_merge : warp-per-query merge of the node splits
-//   edges     : ONE persistent launch; warps pull (problem, candidate,
-//               parent) edges from a device work queue (free edges first),
-//               time them (edge_core.cuh) and check clearance
-//   attach    : block per problem: best parent, stable compaction, scoring,
-//               incumbent
-//   prune     : block per problem (optional): Eq. (reach)
-//   output    : rendezvous per problem
+// over all problems (each launched with programmatic dependent launch):
+//   schedule : per-problem work offsets, work-queue resets
+//   sample   : goal chart (warp per candidate, lane-parallel IK) and
+//              uniform candidates (Philox counters); parent-search prep
+//              (tree mirror) in the same launch
+//   knn      : warps claim (problem, query, node split) items; the warp
+//              finishing a query's last split merges the split lists
+//   edges    : prep + item scan (eprep, escan, expand), probe of both end
+//              samples of every (edge, admissible duration), probe of four
+//              interior samples of the survivors (mprobe), verification
+//              (vinit, two packed stages + selections, leftover stage),
+//              rho_v and clearance at the accepted duration
+//   attach   : block per problem: best parent, stable compaction, scoring,
+//              incumbent
+//   prune    : block per problem (optional): Eq. (reach)
+//   output   : rendezvous per problem
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -81,6 +85,7 @@ struct PlanDev {  // device pointers, passed by value to the kernels
   int32_t* nn;        // [P][BM][KN]
   float* part_d;      // [P][NSPLIT][BM][KM]
   int32_t* part_i;
+  int32_t* knn_cnt;   // [P][BM] splits finished per query (zero between iterations)
   float* e_T;         // [P][BM][KP]
   float* e_rv;
   uint8_t* e_ok;
@@ -230,17 +235,9 @@ __device__ __forceinline__ int find_problem(const int* off, int P, int x) {
 // ---------------------------------------------------------------------------
 // samplers
 // ---------------------------------------------------------------------------
-// Free candidates: one thread each (uniform in the box, |qd| <= vel_frac qdbar).
-__global__ void __launch_bounds__(128) k_plan_sample_free(PlanDev D, ArmK A) {
-  pdl_begin();
-  const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int p = (int)(gid / D.BM);
-  const int b = (int)(gid - (long)p * D.BM);
-  if (p >= D.P) return;
+// Free candidate (p, b): uniform in the box, |qd| <= vel_frac qdbar.
+__device__ __forceinline__ void sample_free(const PlanDev& D, const ArmK& A, int p, int b) {
   const fn_problem_t& P = D.prob[p];
-  const int B = min(max(P.batch, 0), D.BM);
-  const int G = min(max(P.n_goal, 0), B);
-  if (b < G || b >= B) return;
   const int it = *D.iter;
   float u[16], q[7], qd[7];
 #pragma unroll
@@ -262,21 +259,34 @@ __global__ void __launch_bounds__(128) k_plan_sample_free(PlanDev D, ArmK A) {
   o4[3] = make_float4(qd[4], qd[5], qd[6], 0.f);
 }
 
-// Goal candidates: one warp per candidate.  Every lane decodes the chart
-// pose; lane groups 0-2 (8 lanes each) run the three IK starts in parallel
+__device__ __forceinline__ void parents_prep(const PlanDev& D, long i, long stride);
+
+// Sampling launch: warp w < nslots (P * b_max, or 0 when the caller gives
+// the candidates) owns candidate slot (p, b).  A goal
+// slot is decoded by the whole warp: every lane decodes the chart pose, lane
+// groups 0-2 (8 lanes each) run the three IK starts in parallel
 // (ik_solve_group) and the lowest start that converges wins, the same result
-// as trying the starts in order; group 3 repeats start 0 and is ignored.
-__global__ void __launch_bounds__(128) k_plan_sample_goal(PlanDev D, ArmK A) {
+// as trying the starts in order; group 3 repeats start 0 and is ignored.  A
+// free slot is drawn by lane 0.  The warps past the slots prepare the parent
+// search (parents_prep), which reads nothing the samplers write.
+__global__ void __launch_bounds__(128) k_plan_sample(PlanDev D, ArmK A, long nslots,
+                                                     int prep_warps) {
   pdl_begin();
   const long gid = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31, grp = lane >> 3;
+  if (gid >= nslots) {                                // warp-uniform
+    parents_prep(D, (gid - nslots) * 32 + lane, (long)prep_warps * 32);
+    return;
+  }
   const int p = (int)(gid / D.BM);
   const int b = (int)(gid - (long)p * D.BM);
-  if (p >= D.P) return;                               // warp-uniform
   const fn_problem_t& P = D.prob[p];
   const int B = min(max(P.batch, 0), D.BM);
   const int G = min(max(P.n_goal, 0), B);
-  if (b >= G) return;                                 // warp-uniform
+  if (b >= G) {                                       // warp-uniform
+    if (b < B && lane == 0) sample_free(D, A, p, b);
+    return;
+  }
   const long ci = (long)p * D.BM + b;
   const int it = *D.iter;
   float u[12], z[9];
@@ -360,6 +370,40 @@ struct WarpTopK {
     }
   }
 };
+
+// Merge of a query's split lists (run by the warp that finishes its last
+// split): lane s < ns holds split s's list; KN rounds of a warp argmin.
+template <int KM>
+__device__ __forceinline__ void knn_merge_query(const PlanDev& D, int p, int b, int ns) {
+  const int lane = threadIdx.x & 31;
+  float d[KM];
+  int id[KM];
+#pragma unroll
+  for (int j = 0; j < KM; ++j) { d[j] = INFINITY; id[j] = 0x7fffffff; }
+  if (lane < ns) {
+    const long off = (((long)p * PL_NSPLIT_MAX + lane) * D.BM + b) * KM;
+#pragma unroll
+    for (int j = 0; j < KM; ++j) { d[j] = __ldcg(D.part_d + off + j); id[j] = __ldcg(D.part_i + off + j); }
+  }
+  const long out = ((long)p * D.BM + b) * D.KN;
+  for (int r = 0; r < D.KN; ++r) {
+    float md = d[0];
+    int mi = id[0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float od = __shfl_xor_sync(0xffffffffu, md, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, mi, o);
+      if (knn_less(od, oi, md, mi)) { md = od; mi = oi; }
+    }
+    if (lane == 0) D.nn[out + r] = mi == 0x7fffffff ? -1 : mi;
+    if (id[0] == mi && mi != 0x7fffffff) {
+#pragma unroll
+      for (int j = 0; j + 1 < KM; ++j) { d[j] = d[j + 1]; id[j] = id[j + 1]; }
+      d[KM - 1] = INFINITY;
+      id[KM - 1] = 0x7fffffff;
+    }
+  }
+}
 
 // asynchronous 16-byte global -> shared copy (completion tracked per thread)
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -497,48 +541,28 @@ __global__ void __launch_bounds__(32 * PL_KNN_WARPS) k_plan_knn(PlanDev D) {
         D.part_i[off] = id;
       }
     }
+    if (ns > 1) {
+      // the warp that completes a query's last split merges its lists
+#pragma unroll
+      for (int a = 0; a < PL_KNN_QW; ++a) {
+        const int b = b0 + a;
+        if (b >= B) continue;
+        __threadfence();
+        int last = 0;
+        if (lane == 0) {
+          int* cnt = D.knn_cnt + (long)p * D.BM + b;
+          last = atomicAdd(cnt, 1) == ns - 1;
+          if (last) *cnt = 0;   // ready for the next iteration
+        }
+        if (__shfl_sync(0xffffffffu, last, 0)) {
+          __threadfence();
+          knn_merge_query<KM>(D, p, b, ns);
+        }
+      }
+    }
   }
 }
 
-template <int KM>
-__global__ void __launch_bounds__(256) k_plan_knn_merge(PlanDev D) {
-  pdl_begin();
-  const int lane = threadIdx.x & 31;
-  const long w = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int p = (int)(w / D.BM);
-  const int b = (int)(w - (long)p * D.BM);
-  if (p >= D.P) return;
-  const int B = min(max(D.prob[p].batch, 0), D.BM);
-  const int ns = D.sched->nsplit[p];
-  if (b >= B || ns <= 1 || D.n_nodes[p] <= 1) return;
-  float d[KM];
-  int id[KM];
-#pragma unroll
-  for (int j = 0; j < KM; ++j) { d[j] = INFINITY; id[j] = 0x7fffffff; }
-  if (lane < ns) {
-    const long off = (((long)p * PL_NSPLIT_MAX + lane) * D.BM + b) * KM;
-#pragma unroll
-    for (int j = 0; j < KM; ++j) { d[j] = D.part_d[off + j]; id[j] = D.part_i[off + j]; }
-  }
-  const long out = ((long)p * D.BM + b) * D.KN;
-  for (int r = 0; r < D.KN; ++r) {
-    float md = d[0];
-    int mi = id[0];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float od = __shfl_xor_sync(0xffffffffu, md, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, mi, o);
-      if (knn_less(od, oi, md, mi)) { md = od; mi = oi; }
-    }
-    if (lane == 0) D.nn[out + r] = mi == 0x7fffffff ? -1 : mi;
-    if (id[0] == mi && mi != 0x7fffffff) {
-#pragma unroll
-      for (int j = 0; j + 1 < KM; ++j) { d[j] = d[j + 1]; id[j] = id[j + 1]; }
-      d[KM - 1] = INFINITY;
-      id[KM - 1] = 0x7fffffff;
-    }
-  }
-}
 
 // Mirror of the tree for the parent search: node n sits in 64-node block
 // n / 64 at pair slot j = (n % 64) / 2, half h = n % 2; for component pair
@@ -552,12 +576,10 @@ __device__ __forceinline__ float* knn_mirror_slot(const PlanDev& D, int p, int n
   return reinterpret_cast<float*>(D.mir + f4) + (n & 1);
 }
 
-// parents prep: neighbour lists of single-node trees are empty; tree nodes
-// added (or moved) since the last iteration enter the mirror
-__global__ void k_plan_parents_prep(PlanDev D) {
-  pdl_begin();
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long stride = (long)gridDim.x * blockDim.x;
+// parents prep (thread i of `stride`): neighbour lists of single-node trees
+// are empty; tree nodes added (or moved) since the last iteration enter the
+// mirror
+__device__ __forceinline__ void parents_prep(const PlanDev& D, long i, long stride) {
   const long n = (long)D.P * D.BM * D.KN;
   for (long x = i; x < n; x += stride) {
     const int p = (int)(x / ((long)D.BM * D.KN));
@@ -706,6 +728,8 @@ __global__ void __launch_bounds__(PL_SCAN) k_plan_escan(PlanDev D) {
   if (threadIdx.x == 0) {
     S->n_items = carry;
     S->queue_head = 0u;
+    S->n_pend[0] = S->n_pend[1] = 0;   // verification lists and probe survivors
+    S->n_surv = 0;
   }
 }
 
@@ -890,7 +914,11 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_vstage(PlanDe
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const CubicLane cb{&sCoef[w][lane]};
   const LaneWrench wr{&sWr[w][lane]};
-  const Sched* S = D.sched;
+  Sched* S = D.sched;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    S->n_pend[list ^ 1] = 0;   // filled by the following selection
+    S->queue_head = 0u;        // the leftover stage's queue
+  }
   const int n = S->n_pend[list] * D.S;
   const int32_t* pend = D.pend + (long)list * D.Emax;
   unsigned nsamp = 0;
@@ -998,15 +1026,6 @@ __global__ void __launch_bounds__(128) k_plan_vselect(PlanDev D, ArmK A, GridKP 
     }
     D.cur_k[e] = k2;
     next[atomicAdd(&S->n_pend[list ^ 1], 1)] = e;
-  }
-}
-
-__global__ void k_plan_vclear(PlanDev D, int list) {
-  pdl_begin();
-  if (threadIdx.x == 0) {
-    if (list >= 0) D.sched->n_pend[list] = 0;
-    else D.sched->n_surv = 0;
-    D.sched->queue_head = 0u;
   }
 }
 
@@ -1478,28 +1497,24 @@ template <class Mark>
 static void enqueue_front(fn_planner* pl, unsigned flags, cudaStream_t st, Mark&& mark) {
   PlanDev& D = pl->D;
   const int P = pl->cfg.P;
-  if (!(flags & FN_PLAN_EXTERNAL)) {
-    const long n = (long)P * D.BM;
-    pl_launch(k_plan_sample_goal, (unsigned)((32 * n + 127) / 128), 128, 0, st, D, pl->arm);
-    trace(pl, st, "k_plan_sample_goal");
-    pl_launch(k_plan_sample_free, (unsigned)((n + 127) / 128), 128, 0, st, D, pl->arm);
-    trace(pl, st, "k_plan_sample_free");
+  {
+    // external candidates: only the parent-search preparation runs
+    const long n = (flags & FN_PLAN_EXTERNAL) ? 0 : (long)P * D.BM;
+    const int prep = pl->cfg.k > 1 ? 4 * num_sms() : 0;
+    if (n + prep > 0) {
+      pl_launch(k_plan_sample, (unsigned)((32 * (n + prep) + 127) / 128), 128, 0, st, D, pl->arm,
+                n, prep);
+      trace(pl, st, "k_plan_sample");
+    }
   }
   mark(2);
   if (pl->cfg.k > 1) {
-    pl_launch(k_plan_parents_prep, 2 * num_sms(), 256, 0, st, D);
-    trace(pl, st, "k_plan_parents_prep");
-    const unsigned mb = (unsigned)(((long)P * D.BM + 7) / 8);
     if (D.KM == 8) {
       pl_launch(k_plan_knn<8>, knn_blocks<8>(pl), 32 * PL_KNN_WARPS, kKnnSmem, st, D);
       trace(pl, st, "k_plan_knn");
-      pl_launch(k_plan_knn_merge<8>, mb, 256, 0, st, D);
-      trace(pl, st, "k_plan_knn_merge");
     } else {
       pl_launch(k_plan_knn<16>, knn_blocks<16>(pl), 32 * PL_KNN_WARPS, kKnnSmem, st, D);
       trace(pl, st, "k_plan_knn");
-      pl_launch(k_plan_knn_merge<16>, mb, 256, 0, st, D);
-      trace(pl, st, "k_plan_knn_merge");
     }
   }
 }
@@ -1516,10 +1531,6 @@ static void enqueue_edges(fn_planner* pl, int v, int blocks, cudaStream_t st, Ma
   trace(pl, st, "k_plan_eprep");
   pl_launch(k_plan_escan, 1, PL_SCAN, 0, st, D);
   trace(pl, st, "k_plan_escan");
-  pl_launch(k_plan_vclear, 1, 32, 0, st, D, 0);
-  trace(pl, st, "k_plan_vclear");
-  pl_launch(k_plan_vclear, 1, 32, 0, st, D, -1);
-  trace(pl, st, "k_plan_vclear");
   pl_launch(k_plan_expand, 4 * num_sms(), 256, 0, st, D);
   trace(pl, st, "k_plan_expand");
   mark(4);
@@ -1533,8 +1544,6 @@ static void enqueue_edges(fn_planner* pl, int v, int blocks, cudaStream_t st, Ma
   trace(pl, st, "k_plan_vinit");
   int list = 0;
   for (int stage = 0; stage < PL_VSTAGES; ++stage) {
-    pl_launch(k_plan_vclear, 1, 32, 0, st, D, list ^ 1);
-    trace(pl, st, "k_plan_vclear");
     pl_launch(plan_vstage_variant(v), blocks, 32 * PL_EDGE_WARPS, 0, st, D, pl->arm, pl->grid, list);
     trace(pl, st, "k_plan_vstage");
     pl_launch(k_plan_vselect, tb, 128, 0, st, D, pl->arm, pl->grid, list);
@@ -1619,6 +1628,8 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
   D.NB = (NC + 63) / 64;
   A_(D.mir, (size_t)P * D.NB * 7 * 32);
   A_(D.packed, (size_t)P);
+  A_(D.knn_cnt, P * BM);
+  if (rc == FN_OK && cudaMemset(D.knn_cnt, 0, sizeof(int32_t) * P * BM) != cudaSuccess) rc = FN_ECUDA;
   if (rc == FN_OK && cudaMemset(D.packed, 0, sizeof(int32_t) * P) != cudaSuccess) rc = FN_ECUDA;
 #undef A_
   if (rc == FN_OK) {
