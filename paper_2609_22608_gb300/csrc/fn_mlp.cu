@@ -555,7 +555,7 @@ __device__ __forceinline__ int window_lo(float y0, float y1, float logT0, float 
 // under monotone rho_tau, rho_P); accept "none" if the window and T_{K-1}
 // are infeasible.  Otherwise fall back to the exact scan of the indices not
 // yet examined ([0, lo-1) then [lo+W, K)).
-__global__ void __launch_bounds__(128) k_time_window(ArmK A, GridW G, int K, int S,
+__global__ void __launch_bounds__(128, 3) k_time_window(ArmK A, GridW G, int K, int S,
                                                      const float* __restrict__ s0,
                                                      const float* __restrict__ s1, int E,
                                                      const float* __restrict__ Y, int Wn,
@@ -672,9 +672,10 @@ extern "C" fn_status fn_time_edges_window(const fn_arm_t* arm, const float* s0, 
   }
   const float logT0 = std::log(T_grid[0]);
   const float dlog = (std::log(T_grid[K - 1]) - logT0) / (float)(K - 1);
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_time_window, 128, 0);
-  const long blocks = std::max<long>(1, std::min<long>(((long)E + 3) / 4, (long)std::max(per_sm, 1) * num_sms()));
+  // one edge per warp and no grid stride: the block scheduler hands out
+  // blocks as others finish, which balances the few edges that fall back to
+  // the full scan
+  const long blocks = std::min<long>(((long)E + 3) / 4, 0x7fffffffL);
   k_time_window<<<(unsigned)blocks, 128, 0, (cudaStream_t)stream>>>(
       A, G, K, S, s0, s1, E, Y, std::min(W, K), logT0, dlog, k_star, T_star, rho3, ok, path,
       sample_count);
