@@ -452,10 +452,23 @@ typedef struct fn_mlp fn_mlp_t;
 fn_status fn_mlp_create(int max_batch, unsigned long long seed, fn_mlp_t** out);
 fn_status fn_mlp_destroy(fn_mlp_t* m);
 
-/* Y[e] = (log T*_pred, feasibility logit) for E edges (device s0, s1 [E][16];
- * device Y [E][2]); E may exceed max_batch (processed in chunks). */
+/* Y[e] = (log T*_pred, feasibility logit) for E edges (device s0, s1 [E][16],
+ * 16-byte aligned; device Y [E][2]), any E.  Runs on the 5th-generation
+ * tensor cores (tcgen05, accumulators in tensor memory), one fused launch;
+ * the packed weights are refreshed on the stream after any weight change.
+ * A timeout inside the kernel raises the flag read by fn_mlp_error. */
 fn_status fn_mlp_predict(fn_mlp_t* m, const fn_arm_t* arm, const float* s0, const float* s1,
                          int E, float* Y, void* stream);
+
+/* The same forward on the training kernels' path (mma.sync GEMMs through
+ * the model's workspace, chunks of max_batch).  Same rounding points; the
+ * two differ only by FP32 summation order. */
+fn_status fn_mlp_predict_ref(fn_mlp_t* m, const fn_arm_t* arm, const float* s0, const float* s1,
+                             int E, float* Y, void* stream);
+
+/* Error flag of the tensor-core kernel (1 after a timed-out wait); reset
+ * != 0 clears it.  Synchronous. */
+fn_status fn_mlp_error(fn_mlp_t* m, int* flag, int reset);
 
 /* Loss and gradients of one batch (E <= max_batch; k_star device [E] from
  * the exact scan over the host grid T_grid [K]); *loss (host, may be NULL)

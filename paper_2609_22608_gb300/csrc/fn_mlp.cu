@@ -25,6 +25,7 @@
 
 #include "edge_core.cuh"
 #include "fn_internal.h"
+#include "fn_mlp_tc.h"
 
 namespace fn {
 
@@ -263,6 +264,12 @@ struct fn_mlp {
   bf16* dZb;      // [n][256]
   float* loss;    // [1]
   float* logT;    // [FN_MAX_GRID]
+  // tensor-core inference: layers 1-3 packed for tcgen05 (refreshed lazily
+  // after any weight change) and the kernel's error flag
+  bf16* W1p;      // [16 KB]
+  bf16* W23p;     // [256 KB]
+  int* tc_err;    // [1]
+  bool packed;
   std::vector<void*> allocs;
 };
 
@@ -301,10 +308,13 @@ extern "C" fn_status fn_mlp_create(int max_batch, unsigned long long seed, fn_ml
   A((void**)&m->Y, n * 2 * 4); A((void**)&m->dY, n * 2 * 4); A((void**)&m->dYb, n * 2 * 2);
   A((void**)&m->dH, n * MLP_H * 4); A((void**)&m->dZb, n * MLP_H * 2);
   A((void**)&m->loss, 4); A((void**)&m->logT, FN_MAX_GRID * 4);
+  A((void**)&m->W1p, kTcW1Bytes); A((void**)&m->W23p, kTcW23Bytes); A((void**)&m->tc_err, 4);
+  m->packed = false;
   if (rc != FN_OK) {
     fn_mlp_destroy(m);
     return rc;
   }
+  cudaMemset(m->tc_err, 0, 4);
   // He-uniform initial weights (inputs 28 of 32 used), zero biases, zero moments
   std::mt19937_64 rng(seed);
   for (int l = 0; l < MLP_LAYERS; ++l) {
@@ -351,8 +361,29 @@ static fn_status mlp_features(fn_mlp* m, const fn_arm_t* arm, const float* s0, c
   return FN_OK;
 }
 
+// inference on the tcgen05 path (fused, no workspace, any E)
 extern "C" fn_status fn_mlp_predict(fn_mlp_t* m, const fn_arm_t* arm, const float* s0,
                                     const float* s1, int E, float* Y, void* stream) {
+  if (!m || E < 0 || !Y || (E > 0 && (!s0 || !s1))) return FN_EINVAL;
+  if (E == 0) return FN_OK;
+  if (!aligned16(s0) || !aligned16(s1)) return FN_EINVAL;
+  ArmK A;
+  if (!make_armk(arm, &A)) return FN_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!m->packed) {
+    mlp_tc_pack(m->Wb[0], 32, kTcK1, m->W1p, st);
+    mlp_tc_pack(m->Wb[1], 256, kTcKc, m->W23p, st);
+    mlp_tc_pack(m->Wb[2], 256, kTcKc, m->W23p + kTcW23Bytes / 4, st);
+    m->packed = true;
+  }
+  return mlp_tc_forward(A, s0, s1, E, m->W1p, m->W23p, m->b[0], m->b[1], m->b[2], m->Wb[3],
+                        m->b[3], Y, m->tc_err, st);
+}
+
+// the same forward on the mma.sync path (the training kernels), E <= max_batch
+// per internal batch
+extern "C" fn_status fn_mlp_predict_ref(fn_mlp_t* m, const fn_arm_t* arm, const float* s0,
+                                        const float* s1, int E, float* Y, void* stream) {
   if (!m || E < 0 || !Y || (E > 0 && (!s0 || !s1))) return FN_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   for (int e0 = 0; e0 < E; e0 += m->max_batch) {
@@ -365,6 +396,13 @@ extern "C" fn_status fn_mlp_predict(fn_mlp_t* m, const fn_arm_t* arm, const floa
       return FN_ECUDA;
   }
   return launch_status();
+}
+
+extern "C" fn_status fn_mlp_error(fn_mlp_t* m, int* flag, int reset) {
+  if (!m || !flag) return FN_EINVAL;
+  if (cudaMemcpy(flag, m->tc_err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return FN_ECUDA;
+  if (reset && cudaMemset(m->tc_err, 0, 4) != cudaSuccess) return FN_ECUDA;
+  return FN_OK;
 }
 
 // forward + loss + backward into m->gW / m->gb (no update)
@@ -429,6 +467,7 @@ extern "C" fn_status fn_mlp_adam_step(fn_mlp_t* m, float lr, void* stream) {
   if (!m || !(lr >= 0.f)) return FN_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   m->step += 1;
+  m->packed = false;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   const float c1 = (float)(1.0 - std::pow(0.9, m->step));
   const float c2 = (float)(1.0 - std::pow(0.999, m->step));
@@ -474,6 +513,7 @@ extern "C" fn_status fn_mlp_set_params(fn_mlp_t* m, int l, const float* W, const
   if (W && cudaMemcpy(m->W[l], W, nw * 4, cudaMemcpyHostToDevice) != cudaSuccess) return FN_ECUDA;
   if (b && cudaMemcpy(m->b[l], b, nb * 4, cudaMemcpyHostToDevice) != cudaSuccess) return FN_ECUDA;
   k_to_bf16<<<(unsigned)((nw + 255) / 256), 256>>>(m->W[l], m->Wb[l], (long)nw);
+  m->packed = false;
   return cudaDeviceSynchronize() == cudaSuccess ? FN_OK : FN_ECUDA;
 }
 

@@ -23,6 +23,8 @@ def _bind():
     L.fn_mlp_create.argtypes = [i32, C.c_ulonglong, C.POINTER(vp)]
     L.fn_mlp_destroy.argtypes = [vp]
     L.fn_mlp_predict.argtypes = [vp, vp, vp, vp, i32, vp, vp]
+    L.fn_mlp_predict_ref.argtypes = [vp, vp, vp, vp, i32, vp, vp]
+    L.fn_mlp_error.argtypes = [vp, C.POINTER(C.c_int), i32]
     L.fn_mlp_backward.argtypes = [vp, vp, vp, vp, vp, vp, i32, i32, vp, vp]
     L.fn_mlp_adam_step.argtypes = [vp, f32, vp]
     L.fn_mlp_train_step.argtypes = [vp, vp, vp, vp, vp, vp, i32, i32, f32, vp, vp]
@@ -32,7 +34,8 @@ def _bind():
     L.fn_mlp_load.argtypes = [vp, C.c_char_p]
     L.fn_time_edges_window.argtypes = [vp, vp, vp, i32, vp, i32, i32, vp, i32, vp, vp, vp, vp, vp,
                                        vp, vp]
-    for n in ("fn_mlp_create", "fn_mlp_destroy", "fn_mlp_predict", "fn_mlp_backward",
+    for n in ("fn_mlp_create", "fn_mlp_destroy", "fn_mlp_predict", "fn_mlp_predict_ref",
+              "fn_mlp_error", "fn_mlp_backward",
               "fn_mlp_adam_step", "fn_mlp_train_step", "fn_mlp_get_params", "fn_mlp_set_params",
               "fn_mlp_get_grads", "fn_mlp_set_grads", "fn_mlp_save", "fn_mlp_load",
               "fn_time_edges_window"):
@@ -82,6 +85,22 @@ class MLP:
         check(lib().fn_mlp_predict(self.h, C.byref(A), _p(s0), _p(s1), E, _p(out), _st(stream)),
               "fn_mlp_predict")
         return out
+
+    def predict_ref(self, arm, s0, s1, out=None, stream=None):
+        """fn_mlp_predict_ref: the forward on the training kernels' path."""
+        E = s0.shape[0]
+        if out is None:
+            out = torch.empty(E, 2, device=s0.device)
+        A = arm_struct(arm)
+        check(lib().fn_mlp_predict_ref(self.h, C.byref(A), _p(s0), _p(s1), E, _p(out),
+                                       _st(stream)), "fn_mlp_predict_ref")
+        return out
+
+    def error(self, reset=False):
+        """fn_mlp_error: 1 if the tensor-core kernel timed out on a wait."""
+        f = C.c_int()
+        check(lib().fn_mlp_error(self.h, C.byref(f), int(bool(reset))), "fn_mlp_error")
+        return int(f.value)
 
     def backward(self, arm, s0, s1, k_star, T_grid, stream=None):
         A = arm_struct(arm)

@@ -54,6 +54,50 @@ def test_forward_parity(S, arm):
     mlp.close()
 
 
+@pytest.mark.parametrize("E", [1, 128, 700, 152 * 128 * 2 + 77])
+def test_tensor_core_forward(S, arm, E):
+    """The tcgen05 inference (fused, tiles of 128 edges, several tiles per
+    CTA for the largest E) against the FP64 reference with the same bf16
+    rounding points, and against the mma.sync forward."""
+    mlp = S.MLP(max_batch=4096)
+    ps = seeded_params(11)
+    load(mlp, ps)
+    s0, s1 = synth.random_edges(arm, E, 12)
+    d0, d1 = dev(s0), dev(s1)
+    Y = mlp.predict(arm, d0, d1).cpu().numpy()
+    assert mlp.error() == 0
+    Yr = mlp.predict_ref(arm, d0, d1).cpu().numpy()
+    ref, _ = M.forward([(W.astype(np.float64), b.astype(np.float64)) for W, b in ps],
+                       M.features(arm, s0, s1))
+    assert relerr(Y, ref) < 1e-3, relerr(Y, ref)
+    assert relerr(Y, Yr) < 1e-3, relerr(Y, Yr)
+    # per edge: the two GPU paths differ only by FP32 summation order (and
+    # the bf16 roundings that order can flip)
+    assert np.abs(Y - Yr).max() <= 1e-2 * max(1.0, np.abs(Yr).max())
+    mlp.close()
+
+
+def test_tensor_core_forward_after_update(S, arm):
+    """Weights changed by an Adam step are repacked before the next
+    inference."""
+    mlp = S.MLP(max_batch=512)
+    load(mlp, seeded_params(13))
+    s0, s1 = synth.random_edges(arm, 300, 14)
+    d0, d1 = dev(s0), dev(s1)
+    mlp.predict(arm, d0, d1)
+    rng = np.random.default_rng(15)
+    for l in range(4):
+        W, b = mlp.get_params(l)
+        mlp.set_grads(l, rng.normal(0, 1, W.shape).astype(np.float32),
+                      rng.normal(0, 1, b.shape).astype(np.float32))
+    mlp.adam_step(1e-2)
+    Y = mlp.predict(arm, d0, d1).cpu().numpy()
+    Yr = mlp.predict_ref(arm, d0, d1).cpu().numpy()
+    assert relerr(Y, Yr) < 1e-3
+    assert mlp.error() == 0
+    mlp.close()
+
+
 def test_gradient_parity(S, orc, arm):
     """Gradients of one batch (labels from the oracle's exact scan) agree
     norm-wise per tensor within 1e-3."""
