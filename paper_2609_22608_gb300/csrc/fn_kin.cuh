@@ -178,8 +178,16 @@ __device__ __forceinline__ bool chol_solve6(float (&A)[6][6], const float* b, fl
   return true;
 }
 
-// 6x6 symmetric positive definite solve by LDL^T (lower triangle of A read).
-// Returns false if a pivot is not positive.
+// hardware reciprocal approximation (rcp.approx, relative error ~2^-23)
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// 6x6 symmetric positive definite solve by LDL^T (lower triangle of A read),
+// pivots inverted with the hardware reciprocal.  Returns false if a pivot is
+// not positive.
 __device__ __forceinline__ bool ldlt_solve6(const float (&A)[6][6], const float* b, float* x) {
   float L[6][6], W[6][6], r[6];
 #pragma unroll
@@ -188,7 +196,7 @@ __device__ __forceinline__ bool ldlt_solve6(const float (&A)[6][6], const float*
 #pragma unroll
     for (int k = 0; k < j; ++k) d = fmaf(-L[j][k], W[j][k], d);
     if (!(d > 0.f)) return false;
-    r[j] = __frcp_rn(d);
+    r[j] = rcp_approx(d);
 #pragma unroll
     for (int i = j + 1; i < 6; ++i) {
       float w = A[i][j];
@@ -239,7 +247,10 @@ __device__ __forceinline__ void complete_basis(const float* u, float* e1, float*
 // residual (half the sum of column cross products) < 1e-3 and the rotation
 // error is under 90 degrees (trace > 1).  The damped system
 // (J J^T + lambda^2 I) y = e is solved by an LDL^T factorisation (six
-// reciprocals on the critical path instead of square roots and divisions).
+// hardware reciprocals on the critical path instead of square roots and
+// divisions); the link rotations use the hardware sine/cosine.  Both are a
+// few ulp from the rounded values, three orders below the residual
+// tolerances that accept a start.
 //
 // The work of one iteration is spread over a group of 8 lanes (aligned in
 // the warp; all 32 lanes must call this): lane s < 7 owns joint s, lane 7
@@ -270,7 +281,7 @@ __device__ __forceinline__ bool ik_solve_group(const ArmK& A, const float* Rg, c
     float R[9], o[3];
     if (s < 7) {
       float sn, cs;
-      sincosf(qj + A.th0[s], &sn, &cs);
+      __sincosf(qj + A.th0[s], &sn, &cs);   // |angle| < 2 pi; error ~1e-6, far below the IK tolerances
       const float ca = A.ca[s], sa = A.sa[s];
       R[0] = cs;      R[1] = -sn;     R[2] = 0.f;
       R[3] = sn * ca; R[4] = cs * ca; R[5] = -sa;

@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(128) k_plan_sample(PlanDev D, ArmK A, long nsl
   const long gid = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31, grp = lane >> 3;
   if (gid >= nslots) {                                // warp-uniform
-    parents_prep(D, (gid - nslots) * 32 + lane, (long)prep_warps * 32);
+    if (gid - nslots < prep_warps) parents_prep(D, (gid - nslots) * 32 + lane, (long)prep_warps * 32);
     return;
   }
   const int p = (int)(gid / D.BM);
@@ -580,6 +580,7 @@ __device__ __forceinline__ float* knn_mirror_slot(const PlanDev& D, int p, int n
 // are empty; tree nodes added (or moved) since the last iteration enter the
 // mirror
 __device__ __forceinline__ void parents_prep(const PlanDev& D, long i, long stride) {
+  if (stride <= 0 || i < 0 || i >= stride) return;
   const long n = (long)D.P * D.BM * D.KN;
   for (long x = i; x < n; x += stride) {
     const int p = (int)(x / ((long)D.BM * D.KN));

@@ -224,6 +224,25 @@ def test_sampler_uniform_matches_oracle(P, orc, arm):
         assert np.allclose(c["states"][:, 8 + j], expect, rtol=0, atol=1e-5 * float(arm["qd_max"][j]))
 
 
+def test_sampler_single_parent_odd_batch(P, orc, arm):
+    """k = 1 (root only, no parent search) with a batch that is not a
+    multiple of the sampler's block: the sampling launch has spare warps and
+    no tree-mirror work; the iteration must still complete, with the same
+    uniform draws as the oracle."""
+    toss = synth.random_toss(arm, 6)
+    pr = synth.make_problem(toss, root=synth.random_states(arm, 1, 11)[0])
+    B = 601
+    pl = P.Planner(arm, P=1, n_cap=64, b_max=B, k=1, K=8, S=8)
+    prob = P.problem_struct(pr, B, 3, seed=99)
+    pl.reset([prob])
+    out = pl.iterate([prob], 1, 0)[0]
+    c = pl.get_candidates(0, B)
+    pl.close()
+    ref = orc.sample_uniform(arm, 99, 1, 0, 3, B - 3, 0.5)
+    assert np.allclose(c["states"][3:, :7].astype(np.float64), ref[:, :7], rtol=0, atol=1e-6)
+    assert out["n_nodes"] >= 1
+
+
 def test_sampler_goal_chart_on_manifold(P, orc, arm):
     """Goal candidates decoded on the GPU satisfy Def. 2 (checked in FP64)
     and agree with the oracle's decoding where both accept."""
