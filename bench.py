@@ -266,16 +266,12 @@ def run_ours(args, rank, world):
     pl.close()
 
     edges = B_CAND * K_PAR
-    tot_ms = float(step_ms.sum())
-    p99 = float(np.percentile(step_ms, 99))
-    if world > 1:
-        t = torch.tensor([tot_ms, p99, e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms, p99, e2e_ms = [float(x) for x in t.cpu()]
+    tot_ms, p99, e2e_ms = reduce_over_ranks(
+        [float(step_ms.sum()), float(np.percentile(step_ms, 99)), e2e_ms], world, dev)
     if rank != 0:
         return None
     ms_per_step = tot_ms / args.steps
-    value = edges * world / (ms_per_step / 1e3)
+    value = whole_job_rate(edges, world, ms_per_step)
     roof = roofline_from_trace(traced, work)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -292,12 +288,29 @@ def run_ours(args, rank, world):
         "kernels_ms": kernel_table(traced),
         "work": work,
         "clocks": clk.summary(),
-        "e2e": {"value": edges * world / (e2e_ms / 1e3), "unit": UNIT,
+        "e2e": {"value": whole_job_rate(edges, world, e2e_ms), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": len(traced) * args.steps,
         "roofline": roof,
     }
     return line, w
+
+
+def reduce_over_ranks(vals, world, device="cpu"):
+    """Per-rank timings -> their maximum over the ranks (the slowest rank sets
+    the whole job's time).  Collective only for world > 1."""
+    vals = [float(v) for v in vals]
+    if world <= 1:
+        return vals
+    import torch
+    t = torch.tensor(vals, dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Units all ranks processed per second over the (max-over-ranks) time."""
+    return units_per_rank * world / (ms / 1e3)
 
 
 # algorithmic work per unit of each kernel (FLOP; FMA = 2): a distance is
