@@ -431,6 +431,48 @@ fn_status fn_planner_get_candidates(fn_planner_t* pl, int p, float* states, floa
 fn_status fn_planner_get_parents(fn_planner_t* pl, int p, int32_t* nn, int cap);
 
 /* ------------------------------------------------------------------------
+ * Packed edge engine: the planner's edge pipeline (Sec. IV-D search as a
+ * probe of both end samples of every admissible (edge, duration), a probe of
+ * four interior samples of the survivors, then verification of each edge's
+ * lowest surviving duration, all with lanes packed over items) applied to
+ * edge arrays given by the caller.  Same result as fn_time_edges mode FULL
+ * (first feasible grid index, rho_v at it), without the (rho_tau, rho_P)
+ * ratios.
+ * ------------------------------------------------------------------------ */
+typedef struct fn_edges fn_edges_t;
+
+/* Sizes the engine once (up to max_E <= 65536 edges per pass; longer calls
+ * run in passes) for the grid T_grid (host [K], ascending, positive) and S
+ * collocation points.  Allocates; synchronous. */
+fn_status fn_edges_create(const fn_arm_t* arm, const float* T_grid, int K, int S, int max_E,
+                          fn_edges_t** out);
+fn_status fn_edges_destroy(fn_edges_t* eg);
+
+/* First feasible grid index with T_k <= T_cap[e] (T_cap device [E] or NULL
+ * for no cap) of each edge (device s0, s1 [E][16], 16-byte aligned).
+ * Outputs (device [E]): k_star (-1 none, -2 non-finite input), T_star
+ * (T_{k*}; +inf none; NaN invalid), rho_v (at k*; NaN otherwise), ok (k* >= 0
+ * and rho_v <= 1).  Asynchronous on `stream`; one engine serves one call at
+ * a time. */
+fn_status fn_edges_time(fn_edges_t* eg, const float* s0, const float* s1, int E,
+                        const float* T_cap, int32_t* k_star, float* T_star, float* rho_v,
+                        uint8_t* ok, void* stream);
+
+/* The windowed scan of the duration surrogate: per edge, the window of W
+ * grid durations around the prediction Y (device [E][2], fn_mlp_predict's
+ * output) plus the index below it; the window's first feasible index is
+ * accepted if it is 0 or the index below was infeasible, "none" if the
+ * window reached the top of the grid; every other edge is rescanned in
+ * full.  path (device [E] or NULL): 0 certified by the window, 1 rescanned.
+ * Outputs as fn_edges_time. */
+fn_status fn_edges_time_window(fn_edges_t* eg, const float* s0, const float* s1, int E,
+                               const float* Y, int W, int32_t* k_star, float* T_star,
+                               float* rho_v, uint8_t* ok, uint8_t* path, void* stream);
+
+/* The engine's work counters (as fn_planner_work_counts). */
+fn_status fn_edges_work_counts(fn_edges_t* eg, unsigned long long* count, int n, int reset);
+
+/* ------------------------------------------------------------------------
  * Duration surrogate (the project's addition; the paper has no learned
  * component).  An MLP 28 -> 256 -> 256 -> 256 -> 2 with ReLU predicts
  * (log T*, feasibility logit) of an edge from its boundary states; the

@@ -89,6 +89,7 @@ struct PlanDev {  // device pointers, passed by value to the kernels
   float* e_T;         // [P][BM][KP]
   float* e_rv;
   uint8_t* e_ok;
+  int32_t* e_k;       // [P][BM][KP] accepted grid index (-1 none, -2 invalid input)
   Incumbent* inc;     // [P]
   fn_problem_t* prob; // [P]
   Sched* sched;
@@ -111,6 +112,7 @@ struct PlanDev {  // device pointers, passed by value to the kernels
   float* e_Tp;        // [E] goal: fixed duration; free: cap
   uint8_t* e_j;       // [E] parent slot | 0x80 for goal edges
   int32_t* e_cnt;     // [E] probe items; then local exclusive offsets
+  int32_t* e_klo;     // [E] grid index of the edge's first probe item
   int32_t* blk_off;   // [ceil(E/1024)] block offsets of the item scan
   uint32_t* mask;     // [E][8] surviving grid indices of the probe
   int32_t* owner;     // [E*K] probe item -> edge
@@ -696,12 +698,14 @@ __global__ void __launch_bounds__(PL_SCAN) k_plan_eprep(PlanDev D, GridKP Gr) {
     D.e_par[e] = valid ? pr : -1;
     D.e_Tp[e] = Tp;
     D.e_j[e] = (uint8_t)(j | (goal ? 0x80 : 0));
+    D.e_klo[e] = 0;
 #pragma unroll
     for (int w = 0; w < 8; ++w) D.mask[8L * e + w] = 0u;
     if (cnt == 0) {   // decided without dynamics: invalid or no admissible duration
       D.e_ok[ei] = 0;
       D.e_T[ei] = goal ? Tp : INFINITY;
       D.e_rv[ei] = NAN;
+      D.e_k[ei] = -1;
     }
   }
   // block-local exclusive scan of the item counts
@@ -777,7 +781,7 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_probe(PlanDev
     int e = 0, k = 0;
     if (live) {
       e = D.owner[i];
-      k = i - item_off(D, e);
+      k = D.e_klo[e] + (i - item_off(D, e));
       const bool goal = D.e_j[e] & 0x80;
       const float T = goal ? D.e_Tp[e] : sT[k];
       const int p = D.e_ci[e] / D.BM;
@@ -894,6 +898,7 @@ __global__ void k_plan_vinit(PlanDev D) {
       D.e_ok[ei] = 0;
       D.e_T[ei] = goal ? D.e_Tp[e] : INFINITY;
       D.e_rv[ei] = NAN;
+      D.e_k[ei] = -1;
       continue;
     }
     D.cur_k[e] = k;
@@ -955,7 +960,7 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_vstage(PlanDe
 // warp-wide end of an edge whose duration T passed (es: its two states
 // staged in shared memory): rho_v at T (lane = joint), the clearance samples
 // (lane = sample), then Clear
-__device__ __forceinline__ void finish_edge(const PlanDev& D, const ArmK& A, int e, float T,
+__device__ __forceinline__ void finish_edge(const PlanDev& D, const ArmK& A, int e, int k, float T,
                                             const float* es) {
   const int lane = threadIdx.x & 31;
   long ei;
@@ -987,6 +992,7 @@ __device__ __forceinline__ void finish_edge(const PlanDev& D, const ArmK& A, int
     D.e_ok[ei] = ok ? 1 : 0;
     D.e_T[ei] = T;
     D.e_rv[ei] = rv;
+    D.e_k[ei] = k;
   }
 }
 
@@ -1010,7 +1016,7 @@ __global__ void __launch_bounds__(128) k_plan_vselect(PlanDev D, ArmK A, GridKP 
     if (!failed) {
       const int p = D.e_ci[e] / D.BM;
       stage_rows(D.st + ((long)p * D.NC + D.e_par[e]) * 16, D.cand + (long)D.e_ci[e] * 16, sEs[w]);
-      finish_edge(D, A, e, goal ? D.e_Tp[e] : Gr.T[k], sEs[w]);
+      finish_edge(D, A, e, goal ? 0 : k, goal ? D.e_Tp[e] : Gr.T[k], sEs[w]);
       continue;
     }
     if (lane != 0) continue;
@@ -1023,6 +1029,7 @@ __global__ void __launch_bounds__(128) k_plan_vselect(PlanDev D, ArmK A, GridKP 
       D.e_ok[ei] = 0;
       D.e_T[ei] = goal ? D.e_Tp[e] : INFINITY;
       D.e_rv[ei] = NAN;
+      D.e_k[ei] = -1;
       continue;
     }
     D.cur_k[e] = k2;
@@ -1103,7 +1110,7 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_vseq(PlanDev 
         if (s_pass[r] && s_k[r] >= 0) kres = s_k[r];
       from = next_from;
     }
-    if (w == 0 && kres >= 0) finish_edge(D, A, e, sT[kres], sEdge);
+    if (w == 0 && kres >= 0) finish_edge(D, A, e, kres, sT[kres], sEdge);
     if (threadIdx.x == 0) {
       if (kres < 0) {
         long ei;
@@ -1112,6 +1119,7 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_vseq(PlanDev 
         D.e_ok[ei] = 0;
         D.e_T[ei] = INFINITY;
         D.e_rv[ei] = NAN;
+        D.e_k[ei] = -1;
       }
     }
   }
@@ -1522,14 +1530,12 @@ static void enqueue_front(fn_planner* pl, unsigned flags, cudaStream_t st, Mark&
 
 #define PL_VSTAGES 2
 
-// the packed edge phase: prep, item scan, probe, verify (mark(i) records
-// the phase boundaries when timing)
+// the packed edge phase after the per-edge prep: item scan, probe, verify
+// (over the edges of the view D; mark(i) records the phase boundaries when
+// timing)
 template <class Mark>
-static void enqueue_edges(fn_planner* pl, int v, int blocks, cudaStream_t st, Mark&& mark) {
-  PlanDev& D = pl->D;
-  const int eb = (D.Emax + PL_SCAN - 1) / PL_SCAN;
-  pl_launch(k_plan_eprep, eb, PL_SCAN, 0, st, D, pl->grid);
-  trace(pl, st, "k_plan_eprep");
+static void enqueue_edge_body(fn_planner* pl, const PlanDev& D, int v, int blocks, cudaStream_t st,
+                              Mark&& mark) {
   pl_launch(k_plan_escan, 1, PL_SCAN, 0, st, D);
   trace(pl, st, "k_plan_escan");
   pl_launch(k_plan_expand, 4 * num_sms(), 256, 0, st, D);
@@ -1553,6 +1559,16 @@ static void enqueue_edges(fn_planner* pl, int v, int blocks, cudaStream_t st, Ma
   }
   pl_launch(plan_vseq_variant(v), blocks, 32 * PL_EDGE_WARPS, 0, st, D, pl->arm, pl->grid, list);
   trace(pl, st, "k_plan_vseq");
+}
+
+// the planner's packed edge phase: prep of the iteration's edges, then the body
+template <class Mark>
+static void enqueue_edges(fn_planner* pl, int v, int blocks, cudaStream_t st, Mark&& mark) {
+  PlanDev& D = pl->D;
+  const int eb = (D.Emax + PL_SCAN - 1) / PL_SCAN;
+  pl_launch(k_plan_eprep, eb, PL_SCAN, 0, st, D, pl->grid);
+  trace(pl, st, "k_plan_eprep");
+  enqueue_edge_body(pl, D, v, blocks, st, mark);
 }
 
 extern "C" fn_status fn_planner_destroy(fn_planner_t* pl) {
@@ -1609,6 +1625,7 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
   A_(D.nn, P * BM * KN);
   A_(D.part_d, P * PL_NSPLIT_MAX * BM * KM); A_(D.part_i, P * PL_NSPLIT_MAX * BM * KM);
   A_(D.e_T, P * BM * KP); A_(D.e_rv, P * BM * KP); A_(D.e_ok, P * BM * KP);
+  A_(D.e_k, P * BM * KP);
   A_(D.inc, P); A_(D.prob, P); A_(D.sched, 1); A_(D.out, P); A_(D.iter, 1);
   A_(D.added, P); A_(D.status, P);
   A_(D.ptr, P * NC); A_(D.newidx, P * NC); A_(D.alive, P * NC);
@@ -1616,6 +1633,7 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
   A_(D.samples, PL_NCOUNT);
   D.Emax = (int)(P * BM * KP);
   A_(D.e_ci, (size_t)D.Emax); A_(D.e_par, (size_t)D.Emax); A_(D.e_Tp, (size_t)D.Emax);
+  A_(D.e_klo, (size_t)D.Emax);
   A_(D.e_j, (size_t)D.Emax); A_(D.e_cnt, (size_t)D.Emax);
   A_(D.blk_off, (size_t)(D.Emax + PL_SCAN - 1) / PL_SCAN + 1);
   A_(D.mask, (size_t)D.Emax * 8);
@@ -1983,4 +2001,252 @@ extern "C" fn_status fn_planner_autotune(fn_planner_t* pl, const fn_problem_t* p
   if (chosen) *chosen = best;
   pl->timing = false;  // the phase events were reused
   return FN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Packed edge engine (fn_edges_*): the planner's packed edge pipeline over
+// edge arrays given by the caller.  A private planner (one problem, one
+// parent slot) owns the buffers and the tuned schedule; a view of its
+// device state points the rows at the caller's s0 / s1 and the results at
+// the caller's outputs (edge e's result slot is e).
+// ---------------------------------------------------------------------------
+namespace fn {
+
+// Per-edge prep of one pass: admissible count Kadm = #{k : T_k <= cap},
+// probe-item range, mask reset, and the result of edges decided without
+// dynamics (non-finite input: k = -2; empty range: k = -1).
+//   mode 0: full scan [0, Kadm)
+//   mode 1: window [max(lo - 1, 0), min(lo + W, Kadm)), lo from the
+//           prediction Y (grid index nearest exp(y0), the top of the grid if
+//           the logit says infeasible, window clamped into the grid);
+//           win[e] = (lo, Kadm) for the certificate
+//   mode 2: full scan of the listed edges (list, count *n_list)
+__global__ void __launch_bounds__(PL_SCAN) k_edges_prep(PlanDev D, GridKP Gr, int mode, int E,
+                                                        const float* __restrict__ cap,
+                                                        const float* __restrict__ Y, int W,
+                                                        float logT0, float dlog,
+                                                        const int32_t* __restrict__ list,
+                                                        const int* __restrict__ n_list,
+                                                        int2* __restrict__ win) {
+  pdl_begin();
+  __shared__ float sT[FN_MAX_GRID];
+  __shared__ int sh[32];
+  for (int i = threadIdx.x; i < D.K; i += blockDim.x) sT[i] = Gr.T[i];
+  __syncthreads();
+  const int n = mode == 2 ? min(*n_list, E) : E;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    D.sched->n_edges = n;
+    D.sched->n_free_edges = n;
+  }
+  const int e = blockIdx.x * PL_SCAN + threadIdx.x;
+  int cnt = 0;
+  if (e < n) {
+    const int src = mode == 2 ? list[e] : e;
+    const float* r0 = D.st + 16L * src;
+    const float* r1 = D.cand + 16L * src;
+    bool finite = true;
+#pragma unroll
+    for (int m = 0; m < 16; ++m)
+      if ((m & 7) != 7) finite = finite && isfinite(r0[m]) && isfinite(r1[m]);
+    const float c = cap ? cap[src] : INFINITY;
+    int lo = 0, hi = D.K;   // Kadm = #{k : T_k <= c} on the ascending grid
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (sT[mid] <= c) lo = mid + 1;
+      else hi = mid;
+    }
+    const int Kadm = lo;
+    int klo = 0, khi = Kadm;
+    if (mode == 1) {
+      const float y0 = Y[2L * src], y1 = Y[2L * src + 1];
+      int ctr = (y1 < 0.f || !isfinite(y0)) ? D.K - 1 : __float2int_rn((y0 - logT0) / dlog);
+      ctr = min(max(ctr, 0), D.K - 1);
+      const int wlo = min(max(ctr - W / 2, 0), max(D.K - W, 0));
+      klo = max(wlo - 1, 0);
+      khi = min(wlo + W, Kadm);
+      win[src] = make_int2(wlo, Kadm);
+    }
+    cnt = finite ? max(khi - klo, 0) : 0;
+    D.e_ci[e] = src;
+    D.e_par[e] = src;
+    D.e_Tp[e] = c;
+    D.e_j[e] = 0;
+    D.e_klo[e] = klo;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) D.mask[8L * e + w] = 0u;
+    if (cnt == 0) {
+      D.e_ok[src] = 0;
+      D.e_T[src] = finite ? INFINITY : NAN;
+      D.e_rv[src] = NAN;
+      D.e_k[src] = finite ? -1 : -2;
+    }
+  }
+  int tot;
+  const int ex = block_scan(cnt, sh, &tot);
+  if (e < n) D.e_cnt[e] = ex;
+  if (threadIdx.x == 0) D.blk_off[blockIdx.x] = tot;
+}
+
+// Window certificate (exact under monotone rho_tau, rho_P): the window's
+// first feasible index k is accepted if k = 0 or k >= lo (T_{k-1} was shown
+// infeasible); "none" is accepted if the window was scanned up to the top
+// admissible duration.  Any other edge joins the list for the exact scan.
+__global__ void k_edges_cert(PlanDev D, int E, int W, const int2* __restrict__ win,
+                             int32_t* __restrict__ list, int* __restrict__ n_list,
+                             uint8_t* __restrict__ path) {
+  pdl_begin();
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+    const int k = D.e_k[e];
+    bool cert;
+    if (k == -2) {
+      cert = true;                                   // invalid input, decided
+    } else {
+      const int lo = win[e].x, Kadm = win[e].y;
+      const int klo = max(lo - 1, 0), khi = min(lo + W, Kadm);
+      if (k >= 0) cert = k >= lo || lo == 0;
+      else cert = klo < khi && khi == Kadm;
+    }
+    if (path) path[e] = cert ? 0 : 1;
+    if (!cert) list[atomicAdd(n_list, 1)] = e;
+  }
+}
+
+}  // namespace fn
+
+using namespace fn;
+
+struct fn_edges {
+  fn_planner* pl = nullptr;
+  int maxE = 0;
+  int2* win = nullptr;
+  int32_t* list = nullptr;
+  int* n_list = nullptr;
+  float logT0 = 0.f, dlog = 0.f;
+};
+
+extern "C" fn_status fn_edges_destroy(fn_edges_t* eg) {
+  if (!eg) return FN_EINVAL;
+  if (eg->pl) fn_planner_destroy(eg->pl);
+  if (eg->win) cudaFree(eg->win);
+  if (eg->list) cudaFree(eg->list);
+  if (eg->n_list) cudaFree(eg->n_list);
+  delete eg;
+  return FN_OK;
+}
+
+extern "C" fn_status fn_edges_create(const fn_arm_t* arm, const float* T_grid, int K, int S,
+                                     int max_E, fn_edges_t** out) {
+  if (!arm || !T_grid || !out || K < 2 || K > FN_MAX_GRID || S < 2 || S > FN_MAX_S || max_E < 1 ||
+      max_E > (1 << 16))
+    return FN_EINVAL;
+  for (int k = 0; k < K; ++k) {
+    if (!(T_grid[k] > 0.f) || !std::isfinite(T_grid[k])) return FN_EINVAL;
+    if (k > 0 && !(T_grid[k] > T_grid[k - 1])) return FN_EINVAL;
+  }
+  fn_planner_cfg_t c = {};
+  c.P = 1; c.n_cap = 2; c.b_max = max_E; c.k = 1; c.K = K;
+  c.T_lo = T_grid[0]; c.T_hi = T_grid[K - 1]; c.S = S; c.S_clear = 2; c.reach_grid = 2;
+  c.w_vel = 0.1f; c.vel_frac = 0.5f; c.clear_margin = 0.f; c.edge_blocks = 0;
+  fn_edges* eg = new fn_edges();
+  eg->maxE = max_E;
+  fn_status rc = fn_planner_create(&c, arm, &eg->pl);
+  if (rc != FN_OK) {
+    delete eg;
+    return rc;
+  }
+  for (int k = 0; k < K; ++k) eg->pl->grid.T[k] = T_grid[k];
+  eg->logT0 = std::log(T_grid[0]);
+  eg->dlog = (std::log(T_grid[K - 1]) - eg->logT0) / (float)(K - 1);
+  fn_problem_t prob = {};   // no obstacles: the clearance check is off
+  prob.t_fall = 1.f;
+  prob.v_tip = 1.f;
+  if ((rc = fn_planner_reset(eg->pl, &prob, nullptr)) != FN_OK ||
+      cudaMalloc(&eg->win, sizeof(int2) * max_E) != cudaSuccess ||
+      cudaMalloc(&eg->list, sizeof(int32_t) * max_E) != cudaSuccess ||
+      cudaMalloc(&eg->n_list, sizeof(int)) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+    fn_edges_destroy(eg);
+    return rc != FN_OK ? rc : FN_ENOMEM;
+  }
+  *out = eg;
+  return FN_OK;
+}
+
+// the planner's device state viewed over a chunk of the caller's edges
+static PlanDev edges_view(fn_edges* eg, const float* s0, const float* s1, int32_t* k_star,
+                          float* T_star, float* rho_v, uint8_t* ok) {
+  PlanDev D = eg->pl->D;
+  D.st = const_cast<float*>(s0);
+  D.cand = const_cast<float*>(s1);
+  D.NC = eg->maxE;
+  D.BM = eg->maxE;
+  D.KP = 1;
+  D.e_k = k_star;
+  D.e_T = T_star;
+  D.e_rv = rho_v;
+  D.e_ok = ok;
+  return D;
+}
+
+static fn_status edges_check(fn_edges* eg, const float* s0, const float* s1, int E,
+                             const int32_t* k_star, const float* T_star, const float* rho_v,
+                             const uint8_t* ok) {
+  if (!eg || E < 0) return FN_EINVAL;
+  if (E > 0 && (!s0 || !s1 || !k_star || !T_star || !rho_v || !ok)) return FN_EINVAL;
+  if (E > 0 && (!aligned16(s0) || !aligned16(s1))) return FN_EINVAL;
+  return FN_OK;
+}
+
+extern "C" fn_status fn_edges_time(fn_edges_t* eg, const float* s0, const float* s1, int E,
+                                   const float* T_cap, int32_t* k_star, float* T_star, float* rho_v,
+                                   uint8_t* ok, void* stream) {
+  fn_status rc = edges_check(eg, s0, s1, E, k_star, T_star, rho_v, ok);
+  if (rc != FN_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  fn_planner* pl = eg->pl;
+  for (int e0 = 0; e0 < E; e0 += eg->maxE) {
+    const int n = std::min(eg->maxE, E - e0);
+    const PlanDev D = edges_view(eg, s0 + 16L * e0, s1 + 16L * e0, k_star + e0, T_star + e0,
+                                 rho_v + e0, ok + e0);
+    pl_launch(k_edges_prep, (n + PL_SCAN - 1) / PL_SCAN, PL_SCAN, 0, st, D, pl->grid, 0, n,
+              T_cap ? T_cap + e0 : (const float*)nullptr, (const float*)nullptr, 0, 0.f, 0.f,
+              (const int32_t*)nullptr, (const int*)nullptr, (int2*)nullptr);
+    enqueue_edge_body(pl, D, pl->edge_variant, pl->edge_blocks, st, [](int) {});
+  }
+  return launch_status();
+}
+
+extern "C" fn_status fn_edges_time_window(fn_edges_t* eg, const float* s0, const float* s1, int E,
+                                          const float* Y, int W, int32_t* k_star, float* T_star,
+                                          float* rho_v, uint8_t* ok, uint8_t* path, void* stream) {
+  fn_status rc = edges_check(eg, s0, s1, E, k_star, T_star, rho_v, ok);
+  if (rc != FN_OK) return rc;
+  if (E > 0 && !Y) return FN_EINVAL;
+  if (W < 1) return FN_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  fn_planner* pl = eg->pl;
+  W = std::min(W, pl->D.K);
+  for (int e0 = 0; e0 < E; e0 += eg->maxE) {
+    const int n = std::min(eg->maxE, E - e0);
+    const PlanDev D = edges_view(eg, s0 + 16L * e0, s1 + 16L * e0, k_star + e0, T_star + e0,
+                                 rho_v + e0, ok + e0);
+    const unsigned pb = (unsigned)((n + PL_SCAN - 1) / PL_SCAN);
+    // pass 1: the predicted windows (and their certificate index)
+    pl_launch(k_edges_prep, pb, PL_SCAN, 0, st, D, pl->grid, 1, n, (const float*)nullptr, Y + 2L * e0,
+              W, eg->logT0, eg->dlog, (const int32_t*)nullptr, (const int*)nullptr, eg->win);
+    enqueue_edge_body(pl, D, pl->edge_variant, pl->edge_blocks, st, [](int) {});
+    // certificate; uncertified edges -> exact scan of their full range
+    if (cudaMemsetAsync(eg->n_list, 0, sizeof(int), st) != cudaSuccess) return FN_ECUDA;
+    k_edges_cert<<<2 * num_sms(), 256, 0, st>>>(D, n, W, eg->win, eg->list, eg->n_list,
+                                                 path ? path + e0 : nullptr);
+    k_edges_prep<<<pb, PL_SCAN, 0, st>>>(D, pl->grid, 2, n, nullptr, nullptr, 0, 0.f, 0.f, eg->list,
+                                          eg->n_list, nullptr);
+    enqueue_edge_body(pl, D, pl->edge_variant, pl->edge_blocks, st, [](int) {});
+  }
+  return launch_status();
+}
+
+extern "C" fn_status fn_edges_work_counts(fn_edges_t* eg, unsigned long long* count, int n,
+                                          int reset) {
+  if (!eg) return FN_EINVAL;
+  return fn_planner_work_counts(eg->pl, count, n, reset);
 }

@@ -14,7 +14,7 @@ import torch
 from . import _lib
 from ._lib import FN_MODE_FIXED, FN_MODE_FULL, arm_struct, check, lib
 
-__all__ = ["time_edges", "rnea_dump", "knn_tree", "knn_workspace_bytes", "make_edges",
+__all__ = ["time_edges", "rnea_dump", "knn_tree", "knn_workspace_bytes", "make_edges", "EdgeEngine",
            "FN_MODE_FULL", "FN_MODE_FIXED", "version"]
 
 
@@ -131,3 +131,70 @@ def knn_tree(tree, queries, k, w_vel, first=1, N=None, workspace=None, out=None,
                            _stream(stream))
     check(st, "fn_knn_tree")
     return out
+
+
+class EdgeEngine:
+    """fn_edges_*: the planner's packed edge pipeline over caller-given edge
+    arrays (full scan with an optional cap, or the surrogate's window with
+    its certificate and exact rescan)."""
+
+    def __init__(self, arm, T_grid, S=64, max_E=65536):
+        L = lib()
+        vp, i32 = C.c_void_p, C.c_int
+        L.fn_edges_create.argtypes = [vp, vp, i32, i32, i32, C.POINTER(vp)]
+        L.fn_edges_destroy.argtypes = [vp]
+        L.fn_edges_time.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp]
+        L.fn_edges_time_window.argtypes = [vp, vp, vp, i32, vp, i32, vp, vp, vp, vp, vp, vp]
+        L.fn_edges_work_counts.argtypes = [vp, vp, i32, i32]
+        for n in ("fn_edges_create", "fn_edges_destroy", "fn_edges_time", "fn_edges_time_window",
+                  "fn_edges_work_counts"):
+            getattr(L, n).restype = i32
+        g = np.ascontiguousarray(np.asarray(T_grid, np.float32))
+        self.K = g.size
+        self.arm = arm_struct(arm)
+        h = C.c_void_p()
+        check(L.fn_edges_create(C.byref(self.arm), g.ctypes.data, int(g.size), int(S), int(max_E),
+                                C.byref(h)), "fn_edges_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().fn_edges_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _outs(self, E, dev):
+        return dict(k_star=torch.empty(E, dtype=torch.int32, device=dev),
+                    T_star=torch.empty(E, dtype=torch.float32, device=dev),
+                    rho_v=torch.empty(E, dtype=torch.float32, device=dev),
+                    ok=torch.empty(E, dtype=torch.uint8, device=dev))
+
+    def time(self, s0, s1, T_cap=None, stream=None):
+        _states(s0, "s0"), _states(s1, "s1")
+        E = s0.shape[0]
+        o = self._outs(E, s0.device)
+        check(lib().fn_edges_time(self.h, _ptr(s0), _ptr(s1), E, _ptr(T_cap), _ptr(o["k_star"]),
+                                  _ptr(o["T_star"]), _ptr(o["rho_v"]), _ptr(o["ok"]),
+                                  _stream(stream)), "fn_edges_time")
+        return o
+
+    def time_window(self, s0, s1, Y, W=16, stream=None):
+        _states(s0, "s0"), _states(s1, "s1")
+        E = s0.shape[0]
+        o = self._outs(E, s0.device)
+        o["path"] = torch.empty(E, dtype=torch.uint8, device=s0.device)
+        check(lib().fn_edges_time_window(self.h, _ptr(s0), _ptr(s1), E, _ptr(Y.contiguous()), int(W),
+                                         _ptr(o["k_star"]), _ptr(o["T_star"]), _ptr(o["rho_v"]),
+                                         _ptr(o["ok"]), _ptr(o["path"]), _stream(stream)),
+              "fn_edges_time_window")
+        return o
+
+    def work_counts(self, reset=False):
+        c = (C.c_ulonglong * 5)()
+        check(lib().fn_edges_work_counts(self.h, c, 5, int(bool(reset))), "fn_edges_work_counts")
+        return dict(zip(("probe", "verify", "mprobe", "knn_pairs", "ik_starts"), [int(x) for x in c]))
