@@ -467,15 +467,34 @@ def run_surrogate(args):
         torch.cuda.synchronize()
         return np.array([x.elapsed_time(y) for x, y in ev])
 
-    ms_full = timeit(lambda: ops.time_edges(arm, d0, d1, grid, S, out=full))
+    # warp-per-edge kernels (fn_time_edges, fn_time_edges_window)
+    ms_full_w = timeit(lambda: ops.time_edges(arm, d0, d1, grid, S, out=full))
     ms_pred = timeit(lambda: mlp.predict(arm, d0, d1, out=Y))
-    ms_win = timeit(lambda: (mlp.predict(arm, d0, d1, out=Y),
-                             surrogate.time_edges_window(arm, d0, d1, grid, S, Y, W=Wn, out=win)))
+    ms_win_w = timeit(lambda: (mlp.predict(arm, d0, d1, out=Y),
+                               surrogate.time_edges_window(arm, d0, d1, grid, S, Y, W=Wn, out=win)))
     kf = full["k_star"].cpu().numpy()
-    kw = win["k_star"].cpu().numpy()
-    path = win["path"].cpu().numpy()
-    agree = kw == kf
-    v_full = E / (np.mean(ms_full) / 1e3)
+    kw_w = win["k_star"].cpu().numpy()
+    # the packed engine (fn_edges_*): the same two scans with lanes packed over items
+    eng = ops.EdgeEngine(arm, grid, S=S, max_E=E)
+    eng.work_counts(reset=True)
+    pf = eng.time(d0, d1)
+    c = eng.work_counts(reset=True)
+    samp_full = c["probe"] + c["mprobe"] + c["verify"]
+    pw = eng.time_window(d0, d1, Y, W=Wn)
+    c = eng.work_counts(reset=True)
+    samp_win = c["probe"] + c["mprobe"] + c["verify"]
+    ms_full = timeit(lambda: eng.time(d0, d1))
+    ms_win = timeit(lambda: (mlp.predict(arm, d0, d1, out=Y), eng.time_window(d0, d1, Y, W=Wn)))
+    pw = eng.time_window(d0, d1, Y, W=Wn)
+    torch.cuda.synchronize()
+    eng.close()
+    kpf = pf["k_star"].cpu().numpy()
+    kpw = pw["k_star"].cpu().numpy()
+    path = pw["path"].cpu().numpy()
+    agree = kpw == kf            # the warp-per-edge full scan is the judge
+    # the window against the faster of the two full scans
+    best_full = min(float(np.mean(ms_full)), float(np.mean(ms_full_w)))
+    v_full = E / (best_full / 1e3)
     v_win = agree.sum() / (np.mean(ms_win) / 1e3)
     peak = fp32_peak_tflops()
     mlp.close()
@@ -488,17 +507,23 @@ def run_surrogate(args):
         "config": {"workload": "surrogate-windowed timing of 65536 random edges, K=128, S=64, "
                                "window 16 (+1 certificate index)",
                    "train_edges": ntr, "label_s": label_s, "train_s": train_s,
-                   "loss_per_epoch": hist},
-        "full_scan": {"edges_per_s": v_full, "ms": float(np.mean(ms_full)),
-                      "samples": int(cf.item()),
-                      "tflops": int(cf.item()) * FLOP_PER_SAMPLE / (np.mean(ms_full) / 1e3) / 1e12},
+                   "loss_per_epoch": hist,
+                   "engine": "packed (fn_edges_time / fn_edges_time_window)"},
+        "full_scan": {"edges_per_s": v_full, "ms": best_full,
+                      "packed": {"ms": float(np.mean(ms_full)), "samples": samp_full,
+                                 "tflops": samp_full * FLOP_PER_SAMPLE / (np.mean(ms_full) / 1e3) / 1e12,
+                                 "agreement_with_warp_scan": float((kpf == kf).mean())},
+                      "warp_per_edge": {"ms": float(np.mean(ms_full_w)), "samples": int(cf.item()),
+                                        "tflops": int(cf.item()) * FLOP_PER_SAMPLE / (np.mean(ms_full_w) / 1e3) / 1e12}},
         "window": {"edges_per_s_verified": v_win, "ms_total": float(np.mean(ms_win)),
-                   "ms_mlp_predict": float(np.mean(ms_pred)), "samples": int(cw.item()),
+                   "ms_mlp_predict": float(np.mean(ms_pred)), "samples": samp_win,
                    "certified_fraction": float((path == 0).mean()),
                    "agreement_with_full_scan": float(agree.mean()),
                    "unverified_edges": int((~agree).sum()),
-                   "speedup_vs_full": float(np.mean(ms_full) / np.mean(ms_win)),
+                   "speedup_vs_full": float(best_full / np.mean(ms_win)),
                    "mlp_tflops": 2 * E * (32 * 256 + 256 * 256 * 2 + 256 * 2) / (np.mean(ms_pred) / 1e3) / 1e12},
+        "window_warp_per_edge": {"ms": float(np.mean(ms_win_w)), "samples": int(cw.item()),
+                                 "agreement": float((kw_w == kf).mean())},
         "fp32_peak_tflops": peak,
     }
 
