@@ -430,6 +430,17 @@ fn_status fn_planner_get_candidates(fn_planner_t* pl, int p, float* states, floa
  * Rows beyond the batch of the last iteration are stale.  Synchronous. */
 fn_status fn_planner_get_parents(fn_planner_t* pl, int p, int32_t* nn, int cap);
 
+/* Routes the free edges of the following iterations (those with an
+ * admissible duration) through the duration surrogate: the model predicts a
+ * window of W grid durations per edge, the window is scanned with its
+ * certificate and uncertified edges are rescanned in full (as
+ * fn_edges_time_window); goal edges keep their fixed-duration check.  The
+ * planner keeps the pointer (the model must outlive the planner or be
+ * detached with mlp = NULL) and uses the weights current at each iteration.
+ * Capture graphs after setting it.  Allocates on the first call. */
+struct fn_mlp;
+fn_status fn_planner_set_surrogate(fn_planner_t* pl, struct fn_mlp* mlp, int W);
+
 /* ------------------------------------------------------------------------
  * Packed edge engine: the planner's edge pipeline (Sec. IV-D search as a
  * probe of both end samples of every admissible (edge, duration), a probe of

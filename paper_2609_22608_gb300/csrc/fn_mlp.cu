@@ -380,6 +380,22 @@ extern "C" fn_status fn_mlp_predict(fn_mlp_t* m, const fn_arm_t* arm, const floa
                         m->b[3], Y, m->tc_err, st);
 }
 
+namespace fn {
+fn_status mlp_forward_rows(fn_mlp* m, const ArmK& A, const float* s0, const float* s1, int E_max,
+                           const int* E_dev, float* Y, cudaStream_t st) {
+  if (!m || E_max < 0) return FN_EINVAL;
+  if (E_max == 0) return FN_OK;
+  if (!m->packed) {
+    mlp_tc_pack(m->Wb[0], 32, kTcK1, m->W1p, st);
+    mlp_tc_pack(m->Wb[1], 256, kTcKc, m->W23p, st);
+    mlp_tc_pack(m->Wb[2], 256, kTcKc, m->W23p + kTcW23Bytes / 4, st);
+    m->packed = true;
+  }
+  return mlp_tc_forward(A, s0, s1, E_max, m->W1p, m->W23p, m->b[0], m->b[1], m->b[2], m->Wb[3],
+                        m->b[3], Y, m->tc_err, st, E_dev);
+}
+}  // namespace fn
+
 // the same forward on the mma.sync path (the training kernels), E <= max_batch
 // per internal batch
 extern "C" fn_status fn_mlp_predict_ref(fn_mlp_t* m, const fn_arm_t* arm, const float* s0,

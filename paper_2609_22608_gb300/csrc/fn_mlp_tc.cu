@@ -147,9 +147,11 @@ __global__ void __launch_bounds__(128, 1)
              const bf16* __restrict__ W1p, const bf16* __restrict__ W23p,
              const float* __restrict__ b1, const float* __restrict__ b2,
              const float* __restrict__ b3, const bf16* __restrict__ W4b,
-             const float* __restrict__ b4, float* __restrict__ Y, int* __restrict__ err) {
+             const float* __restrict__ b4, float* __restrict__ Y, int* __restrict__ err,
+             const int* __restrict__ E_dev) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5;
+  if (E_dev) E = min(E, *E_dev);   // rows counted on the device (at most the launch's E)
   const int ntiles = (E + kTcM - 1) / kTcM;
   if ((int)blockIdx.x >= ntiles) return;   // block-uniform, before any barrier
   const int my_tiles = (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1;
@@ -360,7 +362,8 @@ void mlp_tc_pack(const bf16* W, int K, int Kt, bf16* out, cudaStream_t st) {
 
 fn_status mlp_tc_forward(const ArmK& A, const float* s0, const float* s1, int E, const bf16* W1p,
                          const bf16* W23p, const float* b1, const float* b2, const float* b3,
-                         const bf16* W4b, const float* b4, float* Y, int* err, cudaStream_t st) {
+                         const bf16* W4b, const float* b4, float* Y, int* err, cudaStream_t st,
+                         const int* E_dev) {
   if (E <= 0) return FN_OK;
   static bool attr[64] = {false};
   int dev = 0;
@@ -373,7 +376,8 @@ fn_status mlp_tc_forward(const ArmK& A, const float* s0, const float* s1, int E,
   }
   const int ntiles = (E + kTcM - 1) / kTcM;
   const int grid = ntiles < num_sms() ? ntiles : num_sms();
-  k_mlp_tc<<<grid, 128, kTcSmem, st>>>(A, s0, s1, E, W1p, W23p, b1, b2, b3, W4b, b4, Y, err);
+  k_mlp_tc<<<grid, 128, kTcSmem, st>>>(A, s0, s1, E, W1p, W23p, b1, b2, b3, W4b, b4, Y, err,
+                                        E_dev);
   return launch_status();
 }
 

@@ -29,9 +29,23 @@ void mlp_tc_pack(const __nv_bfloat16* W, int K, int Kt, __nv_bfloat16* out, cuda
 // Y[e] = MLP(features(s0[e], s1[e])) for e < E with the packed layers 1-3,
 // the bf16 layer-4 weights W4b [256][2] and the FP32 biases.  *err is set
 // to 1 if a wait on the tensor core or a copy timed out.  Y: device [E][2].
+// E_dev (device, may be NULL): the rows actually present, at most E.
 fn_status mlp_tc_forward(const ArmK& A, const float* s0, const float* s1, int E,
                          const __nv_bfloat16* W1p, const __nv_bfloat16* W23p, const float* b1,
                          const float* b2, const float* b3, const __nv_bfloat16* W4b,
-                         const float* b4, float* Y, int* err, cudaStream_t st);
+                         const float* b4, float* Y, int* err, cudaStream_t st,
+                         const int* E_dev = nullptr);
+
+}  // namespace fn
+
+struct fn_mlp;
+
+namespace fn {
+
+// The model's tensor-core forward over rows counted on the device (for a
+// caller inside a captured sequence): refreshes the packed weights first if
+// they changed.  Stream-ordered, no host synchronisation.
+fn_status mlp_forward_rows(fn_mlp* m, const ArmK& A, const float* s0, const float* s1, int E_max,
+                           const int* E_dev, float* Y, cudaStream_t st);
 
 }  // namespace fn

@@ -31,6 +31,7 @@
 #include "edge_core.cuh"
 #include "fn_internal.h"
 #include "fn_kin.cuh"
+#include "fn_mlp_tc.h"
 #include "fn_tune.h"
 #include "knn_core.cuh"
 
@@ -121,6 +122,11 @@ struct PlanDev {  // device pointers, passed by value to the kernels
   int32_t* pend;      // [2][E] edges pending verification (ping-pong lists)
   int2* surv;         // [surv_cap] probe survivors (edge, grid index)
   int Emax, Kmax, surv_cap;
+  // duration surrogate: free edges with admissible durations routed to the
+  // window pass (sur != 0), listed in sur_list (count *sur_n)
+  int sur;
+  int32_t* sur_list;  // [E]
+  int* sur_n;         // [1]
   // parents: node mirror laid out for lane-contiguous loads (see knn_mirror_index)
   float4* mir;        // [P][NB][7][32]
   int32_t* packed;    // [P] leading nodes whose mirror entries are current
@@ -220,6 +226,7 @@ __global__ void k_plan_schedule(PlanDev D) {
   S->n_edges = fo + go;
   S->knn_items = ko;
   S->knn_head = 0;
+  if (D.sur_n) *D.sur_n = 0;
   S->queue_head = 0u;
 }
 
@@ -670,6 +677,7 @@ __global__ void __launch_bounds__(PL_SCAN) k_plan_eprep(PlanDev D, GridKP Gr) {
   const int E = S->n_edges;
   const int e = blockIdx.x * PL_SCAN + threadIdx.x;
   int cnt = 0;
+  bool routed = false;
   if (e < E) {
     int p, b, j;
     bool goal;
@@ -692,6 +700,12 @@ __global__ void __launch_bounds__(PL_SCAN) k_plan_eprep(PlanDev D, GridKP Gr) {
           else hi = mid;
         }
         cnt = lo;
+        if (D.sur && cnt > 0) {   // timed by the surrogate pass instead
+          const int slot = atomicAdd(D.sur_n, 1);
+          if (slot < D.Emax) D.sur_list[slot] = e;
+          cnt = 0;
+          routed = true;
+        }
       }
     }
     D.e_ci[e] = (int)ci;
@@ -701,7 +715,7 @@ __global__ void __launch_bounds__(PL_SCAN) k_plan_eprep(PlanDev D, GridKP Gr) {
     D.e_klo[e] = 0;
 #pragma unroll
     for (int w = 0; w < 8; ++w) D.mask[8L * e + w] = 0u;
-    if (cnt == 0) {   // decided without dynamics: invalid or no admissible duration
+    if (cnt == 0 && !routed) {   // decided without dynamics: invalid or no admissible duration
       D.e_ok[ei] = 0;
       D.e_T[ei] = goal ? Tp : INFINITY;
       D.e_rv[ei] = NAN;
@@ -957,6 +971,28 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_vstage(PlanDe
   if (D.samples && lane == 0 && nsamp) atomicAdd(D.samples + 1, (unsigned long long)nsamp);
 }
 
+// least link-capsule clearance to problem P's obstacles along the edge
+// (staged states es) at duration T, over S_clear points (lane = point)
+__device__ __forceinline__ float warp_clearance(const PlanDev& D, const ArmK& A,
+                                                const fn_problem_t& P, const float* es, float T) {
+  const int lane = threadIdx.x & 31;
+  Cubic c;
+  cubic_coef_sh<true>(es, T, c);
+  float mc = INFINITY;
+#pragma unroll 1
+  for (int s = lane; s < D.S_clear; s += 32) {
+    const float u = sample_u(s, D.S_clear);
+    float q[7];
+#pragma unroll
+    for (int jj = 0; jj < 7; ++jj) {
+      float v, a;
+      cubic_eval(c, jj, u, q[jj], v, a);
+    }
+    mc = fminf(mc, config_clearance(A, q, P));
+  }
+  return -warp_max(-mc);
+}
+
 // warp-wide end of an edge whose duration T passed (es: its two states
 // staged in shared memory): rho_v at T (lane = joint), the clearance samples
 // (lane = sample), then Clear
@@ -970,24 +1006,7 @@ __device__ __forceinline__ void finish_edge(const PlanDev& D, const ArmK& A, int
   const float rv = warp_rho_v(A, es, T);
   bool ok = rv <= 1.f;
   const fn_problem_t& P = D.prob[p];
-  if (ok && P.n_obs > 0) {
-    Cubic c;
-    cubic_coef_sh<true>(es, T, c);
-    float mc = INFINITY;
-#pragma unroll 1
-    for (int s = lane; s < D.S_clear; s += 32) {
-      const float u = sample_u(s, D.S_clear);
-      float q[7];
-#pragma unroll
-      for (int jj = 0; jj < 7; ++jj) {
-        float v, a;
-        cubic_eval(c, jj, u, q[jj], v, a);
-      }
-      mc = fminf(mc, config_clearance(A, q, P));
-    }
-    mc = -warp_max(-mc);
-    ok = mc >= D.margin;
-  }
+  if (ok && P.n_obs > 0) ok = warp_clearance(D, A, P, es, T) >= D.margin;
   if (lane == 0) {
     D.e_ok[ei] = ok ? 1 : 0;
     D.e_T[ei] = T;
@@ -1381,6 +1400,21 @@ struct fn_planner {
   // verify, attach, prune, output
   cudaEvent_t ev[10] = {};
   bool timing = false;
+  // duration surrogate (fn_planner_set_surrogate): the model, the window and
+  // the surrogate pass's buffers (its own schedule, compacted rows, results)
+  fn_mlp* sur_mlp = nullptr;
+  int sur_W = 16;
+  Sched* sched2 = nullptr;
+  fn_problem_t* no_obs = nullptr;       // device: a problem without obstacles
+  float *g_s0 = nullptr, *g_s1 = nullptr, *g_cap = nullptr, *g_Y = nullptr;
+  int32_t* g_k = nullptr;
+  float *g_T = nullptr, *g_rv = nullptr;
+  uint8_t *g_ok = nullptr, *g_path = nullptr;
+  int2* g_win = nullptr;
+  int32_t* g_fb = nullptr;
+  int* g_fbn = nullptr;
+  int32_t* g_slot = nullptr;
+  float logT0 = 0.f, dlog = 0.f;
   // per-launch events of a timed iteration (kev[0] before the first launch)
   cudaEvent_t kev[PL_MAX_KEV + 1] = {};
   const char* kname[PL_MAX_KEV] = {};
@@ -1647,6 +1681,9 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
   D.NB = (NC + 63) / 64;
   A_(D.mir, (size_t)P * D.NB * 7 * 32);
   A_(D.packed, (size_t)P);
+  D.sur = 0;
+  D.sur_list = nullptr;
+  A_(D.sur_n, 1);
   A_(D.knn_cnt, P * BM);
   if (rc == FN_OK && cudaMemset(D.knn_cnt, 0, sizeof(int32_t) * P * BM) != cudaSuccess) rc = FN_ECUDA;
   if (rc == FN_OK && cudaMemset(D.packed, 0, sizeof(int32_t) * P) != cudaSuccess) rc = FN_ECUDA;
@@ -1761,6 +1798,8 @@ extern "C" fn_status fn_planner_set_candidates(fn_planner_t* pl, int p, const fl
   return cudaStreamSynchronize(st) == cudaSuccess ? FN_OK : FN_ECUDA;
 }
 
+static void enqueue_surrogate(fn_planner* pl, cudaStream_t st);
+
 // enqueue one iteration (problems and iteration counter already staged)
 static fn_status enqueue_iteration(fn_planner* pl, unsigned flags, cudaStream_t st,
                                    bool timed) {
@@ -1779,6 +1818,7 @@ static fn_status enqueue_iteration(fn_planner* pl, unsigned flags, cudaStream_t 
   enqueue_front(pl, flags, st, mark);
   mark(3);
   enqueue_edges(pl, pl->edge_variant, pl->edge_blocks, st, mark);
+  if (pl->sur_mlp) enqueue_surrogate(pl, st);
   mark(6);
   pl_launch(k_plan_attach, P, PL_ATTACH_THREADS, 0, st, D);
   trace(pl, st, "k_plan_attach");
@@ -2020,7 +2060,8 @@ namespace fn {
 //           prediction Y (grid index nearest exp(y0), the top of the grid if
 //           the logit says infeasible, window clamped into the grid);
 //           win[e] = (lo, Kadm) for the certificate
-//   mode 2: full scan of the listed edges (list, count *n_list)
+//   mode 2: full scan of the listed edges (list)
+// n_list (device, may be NULL): the number of edges of the pass, at most E.
 __global__ void __launch_bounds__(PL_SCAN) k_edges_prep(PlanDev D, GridKP Gr, int mode, int E,
                                                         const float* __restrict__ cap,
                                                         const float* __restrict__ Y, int W,
@@ -2033,7 +2074,7 @@ __global__ void __launch_bounds__(PL_SCAN) k_edges_prep(PlanDev D, GridKP Gr, in
   __shared__ int sh[32];
   for (int i = threadIdx.x; i < D.K; i += blockDim.x) sT[i] = Gr.T[i];
   __syncthreads();
-  const int n = mode == 2 ? min(*n_list, E) : E;
+  const int n = n_list ? min(*n_list, E) : E;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     D.sched->n_edges = n;
     D.sched->n_free_edges = n;
@@ -2093,8 +2134,9 @@ __global__ void __launch_bounds__(PL_SCAN) k_edges_prep(PlanDev D, GridKP Gr, in
 // admissible duration.  Any other edge joins the list for the exact scan.
 __global__ void k_edges_cert(PlanDev D, int E, int W, const int2* __restrict__ win,
                              int32_t* __restrict__ list, int* __restrict__ n_list,
-                             uint8_t* __restrict__ path) {
+                             uint8_t* __restrict__ path, const int* __restrict__ n_dev) {
   pdl_begin();
+  if (n_dev) E = min(E, *n_dev);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
     const int k = D.e_k[e];
     bool cert;
@@ -2108,6 +2150,61 @@ __global__ void k_edges_cert(PlanDev D, int E, int W, const int2* __restrict__ w
     }
     if (path) path[e] = cert ? 0 : 1;
     if (!cert) list[atomicAdd(n_list, 1)] = e;
+  }
+}
+
+// ---- the planner's surrogate pass (free edges routed by k_plan_eprep)
+
+// rows, caps and result slots of the routed edges, compacted (the pass's
+// prep reuses the per-edge arrays, so the slots are recorded here)
+__global__ void k_sur_gather(PlanDev D, float* __restrict__ s0, float* __restrict__ s1,
+                             float* __restrict__ cap, int32_t* __restrict__ slot) {
+  pdl_begin();
+  const long n = (long)min(*D.sur_n, D.Emax) * 16;
+  for (long x = (long)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(x >> 4), m = (int)(x & 15);
+    const int e = D.sur_list[i];
+    const int p = D.e_ci[e] / D.BM;
+    s0[x] = D.st[((long)p * D.NC + D.e_par[e]) * 16 + m];
+    s1[x] = D.cand[(long)D.e_ci[e] * 16 + m];
+    if (m == 0) {
+      long ei;
+      bool goal;
+      edge_slot(D, e, ei, goal);
+      cap[i] = D.e_Tp[e];
+      slot[i] = (int32_t)ei;
+    }
+  }
+}
+
+// results of the surrogate pass into the edges' slots (warp per edge), with
+// the clearance check of the edge's own problem for accepted durations
+__global__ void __launch_bounds__(128) k_sur_scatter(PlanDev D, ArmK A, const int32_t* __restrict__ gk,
+                                                     const float* __restrict__ gT,
+                                                     const float* __restrict__ grv,
+                                                     const uint8_t* __restrict__ gok,
+                                                     const float* __restrict__ s0,
+                                                     const float* __restrict__ s1,
+                                                     const int32_t* __restrict__ slot) {
+  pdl_begin();
+  __shared__ float sEs[4][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int n = min(*D.sur_n, D.Emax);
+  for (int i = blockIdx.x * 4 + w; i < n; i += gridDim.x * 4) {
+    const long ei = slot[i];
+    bool ok = gok[i] != 0;
+    const float T = gT[i];
+    const fn_problem_t& P = D.prob[ei / ((long)D.KP * D.BM)];
+    if (ok && P.n_obs > 0) {           // warp-uniform
+      stage_rows(s0 + 16L * i, s1 + 16L * i, sEs[w]);
+      ok = warp_clearance(D, A, P, sEs[w], T) >= D.margin;
+    }
+    if (lane == 0) {
+      D.e_ok[ei] = ok ? 1 : 0;
+      D.e_T[ei] = T;
+      D.e_rv[ei] = grv[i];
+      D.e_k[ei] = gk[i];
+    }
   }
 }
 
@@ -2237,7 +2334,7 @@ extern "C" fn_status fn_edges_time_window(fn_edges_t* eg, const float* s0, const
     // certificate; uncertified edges -> exact scan of their full range
     if (cudaMemsetAsync(eg->n_list, 0, sizeof(int), st) != cudaSuccess) return FN_ECUDA;
     k_edges_cert<<<2 * num_sms(), 256, 0, st>>>(D, n, W, eg->win, eg->list, eg->n_list,
-                                                 path ? path + e0 : nullptr);
+                                                 path ? path + e0 : nullptr, nullptr);
     k_edges_prep<<<pb, PL_SCAN, 0, st>>>(D, pl->grid, 2, n, nullptr, nullptr, 0, 0.f, 0.f, eg->list,
                                           eg->n_list, nullptr);
     enqueue_edge_body(pl, D, pl->edge_variant, pl->edge_blocks, st, [](int) {});
@@ -2249,4 +2346,83 @@ extern "C" fn_status fn_edges_work_counts(fn_edges_t* eg, unsigned long long* co
                                           int reset) {
   if (!eg) return FN_EINVAL;
   return fn_planner_work_counts(eg->pl, count, n, reset);
+}
+
+// ---------------------------------------------------------------------------
+// Duration surrogate inside the planner iteration: the free edges routed by
+// k_plan_eprep go through the packed window pass (predicted windows, their
+// certificate, an exact rescan of the uncertified ones), on a view of the
+// planner's buffers with its own schedule; their results land in the edges'
+// slots before attach.
+// ---------------------------------------------------------------------------
+static void enqueue_surrogate(fn_planner* pl, cudaStream_t st) {
+  PlanDev& D = pl->D;
+  const int E = D.Emax;
+  pl_launch(k_sur_gather, 4 * num_sms(), 256, 0, st, D, pl->g_s0, pl->g_s1, pl->g_cap,
+            pl->g_slot);
+  trace(pl, st, "k_sur_gather");
+  mlp_forward_rows(pl->sur_mlp, pl->arm, pl->g_s0, pl->g_s1, E, D.sur_n, pl->g_Y, st);
+  trace(pl, st, "k_mlp_tc");
+  PlanDev V = D;                       // the pass's view
+  V.sched = pl->sched2;
+  V.st = pl->g_s0;
+  V.cand = pl->g_s1;
+  V.NC = E;
+  V.BM = E;
+  V.KP = 1;
+  V.prob = pl->no_obs;                 // clearance: checked per problem in the scatter
+  V.e_k = pl->g_k;
+  V.e_T = pl->g_T;
+  V.e_rv = pl->g_rv;
+  V.e_ok = pl->g_ok;
+  const unsigned pb = (unsigned)((E + PL_SCAN - 1) / PL_SCAN);
+  const int v = pl->edge_variant, blocks = pl->edge_blocks;
+  k_edges_prep<<<pb, PL_SCAN, 0, st>>>(V, pl->grid, 1, E, pl->g_cap, pl->g_Y, pl->sur_W, pl->logT0,
+                                        pl->dlog, nullptr, D.sur_n, pl->g_win);
+  trace(pl, st, "k_edges_prep");
+  enqueue_edge_body(pl, V, v, blocks, st, [](int) {});
+  cudaMemsetAsync(pl->g_fbn, 0, sizeof(int), st);
+  k_edges_cert<<<2 * num_sms(), 256, 0, st>>>(V, E, pl->sur_W, pl->g_win, pl->g_fb, pl->g_fbn,
+                                               pl->g_path, D.sur_n);
+  trace(pl, st, "k_edges_cert");
+  k_edges_prep<<<pb, PL_SCAN, 0, st>>>(V, pl->grid, 2, E, pl->g_cap, nullptr, 0, 0.f, 0.f, pl->g_fb,
+                                        pl->g_fbn, nullptr);
+  trace(pl, st, "k_edges_prep");
+  enqueue_edge_body(pl, V, v, blocks, st, [](int) {});
+  pl_launch(k_sur_scatter, 4 * num_sms(), 128, 0, st, D, pl->arm, pl->g_k, pl->g_T, pl->g_rv,
+            pl->g_ok, pl->g_s0, pl->g_s1, pl->g_slot);
+  trace(pl, st, "k_sur_scatter");
+}
+
+extern "C" fn_status fn_planner_set_surrogate(fn_planner_t* pl, fn_mlp_t* mlp, int W) {
+  if (!pl || (mlp && (W < 1 || W > pl->D.K))) return FN_EINVAL;
+  if (!mlp) {
+    pl->sur_mlp = nullptr;
+    pl->D.sur = 0;
+    return FN_OK;
+  }
+  const size_t E = (size_t)pl->D.Emax;
+  if (!pl->sched2) {
+    fn_status rc = FN_OK;
+#define B_(ptr, n) if (rc == FN_OK) rc = pl_alloc_n(pl, &(ptr), (n))
+    B_(pl->sched2, 1); B_(pl->no_obs, 1);
+    B_(pl->g_s0, E * 16); B_(pl->g_s1, E * 16); B_(pl->g_cap, E); B_(pl->g_Y, E * 2);
+    B_(pl->g_k, E); B_(pl->g_T, E); B_(pl->g_rv, E); B_(pl->g_ok, E); B_(pl->g_path, E);
+    B_(pl->g_win, E); B_(pl->g_fb, E); B_(pl->g_fbn, 1); B_(pl->D.sur_list, E);
+    B_(pl->g_slot, E);
+#undef B_
+    if (rc != FN_OK) return rc;
+    fn_problem_t z = {};
+    z.t_fall = 1.f;
+    z.v_tip = 1.f;
+    if (cudaMemcpy(pl->no_obs, &z, sizeof(z), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(pl->sched2, 0, sizeof(Sched)) != cudaSuccess)
+      return FN_ECUDA;
+  }
+  pl->logT0 = std::log(pl->grid.T[0]);
+  pl->dlog = (std::log(pl->grid.T[pl->D.K - 1]) - pl->logT0) / (float)(pl->D.K - 1);
+  pl->sur_mlp = reinterpret_cast<fn_mlp*>(mlp);
+  pl->sur_W = W;
+  pl->D.sur = 1;
+  return FN_OK;
 }

@@ -62,6 +62,7 @@ def _bind():
     L.fn_planner_sample_count.argtypes = [vp, vp, i32]
     L.fn_planner_phase_ms.argtypes = [vp, vp]
     L.fn_planner_kernel_ms.argtypes = [vp, vp, vp, i32, C.POINTER(C.c_int)]
+    L.fn_planner_set_surrogate.argtypes = [vp, vp, i32]
     L.fn_planner_work_counts.argtypes = [vp, vp, i32, i32]
     L.fn_planner_autotune.argtypes = [vp, vp, i32, C.c_uint, i32, vp, vp, vp]
     for n in ("fn_planner_create", "fn_planner_destroy", "fn_planner_reset", "fn_planner_load_tree",
@@ -69,7 +70,7 @@ def _bind():
               "fn_plan_replay", "fn_planner_get_tree", "fn_planner_get_candidates",
               "fn_planner_get_parents",
               "fn_planner_sample_count", "fn_planner_phase_ms", "fn_planner_autotune",
-              "fn_planner_kernel_ms", "fn_planner_work_counts"):
+              "fn_planner_kernel_ms", "fn_planner_work_counts", "fn_planner_set_surrogate"):
         getattr(L, n).restype = i32
     L._planner_bound = True
     return L
@@ -232,6 +233,13 @@ class Planner:
         ms = (C.c_float * 9)()
         check(lib().fn_planner_phase_ms(self.h, ms), "fn_planner_phase_ms")
         return dict(zip(self.PHASES, [float(x) for x in ms]))
+
+    def set_surrogate(self, mlp, W=16):
+        """fn_planner_set_surrogate: route free edges through the duration
+        surrogate's window pass (mlp = None turns it off)."""
+        self._sur = mlp                      # keep the model alive
+        check(_bind().fn_planner_set_surrogate(self.h, mlp.h if mlp is not None else None, int(W)),
+              "fn_planner_set_surrogate")
 
     def kernel_ms(self):
         """fn_planner_kernel_ms: [(kernel name, ms)] of every launch of the

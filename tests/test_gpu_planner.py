@@ -118,6 +118,48 @@ def test_plan_round_goal_attach(P, orc, arm, seed, delta):
     assert np.sum(np.isfinite(Jg)) >= 1
 
 
+@pytest.mark.parametrize("trained", [False, True])
+def test_surrogate_round_matches_plain_round(P, orc, arm, trained):
+    """Free edges routed through the surrogate's window pass attach the same
+    candidates as the plain pass (uncertified windows are rescanned exactly;
+    a certified window can differ only where the limits are not monotone in
+    T), with obstacles so that the clearance of the routed edges is checked
+    against each edge's own problem."""
+    from paper_2609_22608_gb300 import surrogate as SG
+    import torch
+    obs = synth.obstacles(5, 3)
+    case = make_case(arm, orc, 50, N=400, n_free=200)
+    grid = synth.duration_grid(K_GRID)
+    mlp = SG.MLP(max_batch=4096, seed=3)
+    if trained:
+        a, b = synth.random_edges(arm, 8192, 51)
+        da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+        lab = SG.label_edges(arm, da, db, grid, S_COLL)
+        SG.train(mlp, arm, da, db, lab, grid, epochs=3, batch=2048, lr=2e-3)
+    states, t, parent = case["tree"]
+    N, B = states.shape[0], case["cand"].shape[0]
+    trees = []
+    for use in (False, True):
+        pl = P.Planner(arm, P=1, n_cap=N + B + 8, b_max=B, k=5, K=K_GRID, S=S_COLL, S_clear=8)
+        if use:
+            pl.set_surrogate(mlp, 8)
+        # a generous t_best so that most free edges have admissible durations
+        pr = dict(case["pr"])
+        prob = P.problem_struct(pr, B, case["n_goal"], root=case["root"], obstacles=obs)
+        pl.reset([prob])
+        pl.load_tree(0, states, t, parent)
+        pl.set_candidates(0, case["cand"], case["n_goal"], case["T_req"], case["v_rel"])
+        out = pl.iterate([prob], 0, P.FN_PLAN_EXTERNAL)[0]
+        trees.append((pl.get_tree(0), out))
+        pl.close()
+    (g0, o0), (g1, o1) = trees
+    k0 = {g0["states"][i].tobytes() for i in range(N, g0["n"])}
+    k1 = {g1["states"][i].tobytes() for i in range(N, g1["n"])}
+    assert len(k0 ^ k1) <= max(2, 0.02 * B), (len(k0), len(k1), len(k0 ^ k1))
+    assert o0["incumbent"] == o1["incumbent"] or abs(o0["J"] - o1["J"]) < 1e-4
+    mlp.close()
+
+
 def test_plan_round_with_obstacles(P, orc, arm):
     obs = synth.obstacles(5, 3)
     case = make_case(arm, orc, 2, N=200, n_free=64)
