@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="iteration",
-                    choices=["iteration", "surrogate", "batched", "anytime"],
+                    choices=["iteration", "surrogate", "batched", "batched-surrogate", "anytime"],
                     help="iteration (default, the headline line), or one of the other "
                          "workloads, each printing its own line")
     ap.add_argument("--train-edges", type=int, default=2_000_000)
@@ -544,11 +544,30 @@ def _timed_replays(pl, probs, n, stream, first_it=0, between=None):
     return np.array(ms), out
 
 
-def run_batched(args):
+def train_surrogate(arm, n_edges, seed):
+    """A duration surrogate trained on random edges labelled by the exact
+    scan (K = 128, S = 64)."""
+    import torch
+
+    from paper_2609_22608_gb300 import surrogate, synth
+    grid = synth.duration_grid(128)
+    a, b = synth.random_edges(arm, n_edges, 100 + seed)
+    a, b = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    lab = surrogate.label_edges(arm, a, b, grid, 64)
+    mlp = surrogate.MLP(max_batch=8192, seed=seed)
+    surrogate.train(mlp, arm, a, b, lab, grid, epochs=4, batch=8192, lr=2e-3)
+    surrogate.train(mlp, arm, a, b, lab, grid, epochs=1, batch=8192, lr=4e-4, seed=1)
+    torch.cuda.synchronize()
+    return mlp
+
+
+def run_batched(args, surrogate_W=0):
     """64 independent problems of uneven size in one CUDA-graph replay: tree
     sizes log-uniform 256-16384, batches log-uniform 128-4096 (half goal),
     k = 8, K = 128, S = 64.  Trees are restored every 4 replays (untimed) so
-    the workload stays stationary."""
+    the workload stays stationary.  surrogate_W > 0: the free edges go
+    through the duration surrogate's window pass (C6); the plain iteration
+    is timed alongside."""
     import torch
 
     from paper_2609_22608_gb300 import planner as P
@@ -577,13 +596,37 @@ def run_batched(args):
 
     restore()
     tuned = pl.autotune(probs, 0, 0, reps=2, stream=stream)
-    restore()
-    pl.capture(0, stream=stream)
-    for i in range(args.warmup):
-        restore(i * 4)
-        pl.replay(probs, i, stream=stream)
     steps = max(args.steps, 20)
-    ms, out = _timed_replays(pl, probs, steps, stream, 100, restore)
+
+    def timed():
+        restore()
+        pl.capture(0, stream=stream)
+        for i in range(args.warmup):
+            restore(i * 4)
+            pl.replay(probs, i, stream=stream)
+        pl.work_counts(reset=True)
+        return _timed_replays(pl, probs, steps, stream, 100, restore)
+
+    extra = {}
+    if surrogate_W > 0:
+        ms_plain, _ = timed()
+        t0 = time.perf_counter()
+        mlp = train_surrogate(arm, args.train_edges // 4, args.seed)
+        train_s = time.perf_counter() - t0
+        pl.set_surrogate(mlp, surrogate_W)
+        ms, out = timed()
+        wc = pl.work_counts()
+        pl.set_surrogate(None)
+        mlp.close()
+        extra = {"surrogate": {"window": surrogate_W, "train_edges": args.train_edges // 4,
+                               "train_s": train_s,
+                               "routed_edges_per_step": wc["surrogate_edges"] / steps,
+                               "rescanned_fraction": wc["surrogate_rescans"] / max(1, wc["surrogate_edges"])},
+                 "plain": {"ms_per_step": float(np.mean(ms_plain)),
+                           "p99_ms": float(np.percentile(ms_plain, 99))},
+                 "speedup_vs_plain": float(np.mean(ms_plain) / np.mean(ms))}
+    else:
+        ms, out = timed()
     pl.close()
     edges = int(B.sum()) * 8
     return {
@@ -600,6 +643,7 @@ def run_batched(args):
                    "edges_per_step": edges, "edge_variant": tuned[0],
                    "edge_variant_ms": tuned[1]},
         "nodes_added_last": int(sum(o["n_added"] for o in out)),
+        **extra,
     }
 
 
@@ -662,6 +706,14 @@ def main():
         return
     if args.workload == "batched":
         print(json.dumps(run_batched(args)))
+        return
+    if args.workload == "batched-surrogate":
+        line = run_batched(args, surrogate_W=16)
+        line["metric"] = ("verified min-time cubic edges/sec and p99 planning-iteration ms (64 "
+                          "uneven problems, one CUDA-graph replay, free edges through the "
+                          "duration surrogate's window)")
+        line["config"]["workload"] += ", surrogate window 16"
+        print(json.dumps(line))
         return
     if args.workload == "anytime":
         print(json.dumps(run_anytime(args)))

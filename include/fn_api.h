@@ -409,8 +409,10 @@ fn_status fn_planner_sample_count(fn_planner_t* pl, unsigned long long* count, i
 /* All work counters of the planner's kernels since creation or the last
  * reset: [0] torque evaluations of the end-sample probe, [1] of the verify
  * stages, [2] of the interior-sample probe, [3] (query, node) distance
- * evaluations of the parent search, [4] IK starts run by the goal sampler.
- * count: host [n] (n <= 5 written).  reset != 0 zeroes them all. */
+ * evaluations of the parent search, [4] IK starts run by the goal sampler,
+ * [5] edges timed by the surrogate's window pass, [6] of those rescanned
+ * in full (certificate failed).  count: host [n] (n <= 7 written).  reset
+ * != 0 zeroes them all. */
 fn_status fn_planner_work_counts(fn_planner_t* pl, unsigned long long* count, int n, int reset);
 
 /* Copy problem p's tree to host (any pointer may be NULL): states [n][16],

@@ -41,7 +41,8 @@
 #define PL_KNN_SPAN 4096                      // nodes per split (at least)
 #define PL_MAX_P 1024
 #define PL_MAX_KEV 40                         // launches traced per iteration
-#define PL_NCOUNT 5   // work counters: probe, verify, mid-probe, kNN pairs, IK starts
+#define PL_NCOUNT 7   // work counters: probe, verify, mid-probe, kNN pairs, IK starts,
+                      // surrogate-routed edges, surrogate rescans
 
 namespace fn {
 
@@ -106,7 +107,8 @@ struct PlanDev {  // device pointers, passed by value to the kernels
   float* tmp_f;       // [P][NC][4]  (t, J, nu, eT)
   int32_t* tmp_par;   // [P][NC]
   unsigned long long* samples;  // work counters: torque evaluations [0] probe, [1] verify,
-                                // [2] mid-probe; [3] kNN (query, node) pairs; [4] IK starts
+                                // [2] mid-probe; [3] kNN (query, node) pairs; [4] IK starts;
+                                // [5] edges timed by the surrogate pass, [6] of them rescanned
   // packed edge phase (flat edge index e in queue order)
   int32_t* e_ci;      // [E] candidate slot p*BM + b
   int32_t* e_par;     // [E] parent node (-1: invalid edge)
@@ -2057,8 +2059,9 @@ namespace fn {
 // dynamics (non-finite input: k = -2; empty range: k = -1).
 //   mode 0: full scan [0, Kadm)
 //   mode 1: window [max(lo - 1, 0), min(lo + W, Kadm)), lo from the
-//           prediction Y (grid index nearest exp(y0), the top of the grid if
-//           the logit says infeasible, window clamped into the grid);
+//           prediction Y (grid index nearest exp(y0), the top admissible
+//           index if the logit says infeasible, window clamped into
+//           [0, Kadm));
 //           win[e] = (lo, Kadm) for the certificate
 //   mode 2: full scan of the listed edges (list)
 // n_list (device, may be NULL): the number of edges of the pass, at most E.
@@ -2099,10 +2102,13 @@ __global__ void __launch_bounds__(PL_SCAN) k_edges_prep(PlanDev D, GridKP Gr, in
     const int Kadm = lo;
     int klo = 0, khi = Kadm;
     if (mode == 1) {
+      // the window is clamped into the admissible range, so that a
+      // prediction above the cap puts it at the top admissible duration
       const float y0 = Y[2L * src], y1 = Y[2L * src + 1];
-      int ctr = (y1 < 0.f || !isfinite(y0)) ? D.K - 1 : __float2int_rn((y0 - logT0) / dlog);
-      ctr = min(max(ctr, 0), D.K - 1);
-      const int wlo = min(max(ctr - W / 2, 0), max(D.K - W, 0));
+      const int top = max(Kadm, 1);
+      int ctr = (y1 < 0.f || !isfinite(y0)) ? top - 1 : __float2int_rn((y0 - logT0) / dlog);
+      ctr = min(max(ctr, 0), top - 1);
+      const int wlo = min(max(ctr - W / 2, 0), max(top - W, 0));
       klo = max(wlo - 1, 0);
       khi = min(wlo + W, Kadm);
       win[src] = make_int2(wlo, Kadm);
@@ -2149,7 +2155,10 @@ __global__ void k_edges_cert(PlanDev D, int E, int W, const int2* __restrict__ w
       else cert = klo < khi && khi == Kadm;
     }
     if (path) path[e] = cert ? 0 : 1;
-    if (!cert) list[atomicAdd(n_list, 1)] = e;
+    if (!cert) {
+      list[atomicAdd(n_list, 1)] = e;
+      if (D.samples) atomicAdd(D.samples + 6, 1ull);
+    }
   }
 }
 
@@ -2190,6 +2199,7 @@ __global__ void __launch_bounds__(128) k_sur_scatter(PlanDev D, ArmK A, const in
   __shared__ float sEs[4][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int n = min(*D.sur_n, D.Emax);
+  if (D.samples && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(D.samples + 5, (unsigned long long)n);
   for (int i = blockIdx.x * 4 + w; i < n; i += gridDim.x * 4) {
     const long ei = slot[i];
     bool ok = gok[i] != 0;

@@ -195,6 +195,7 @@ class EdgeEngine:
         return o
 
     def work_counts(self, reset=False):
-        c = (C.c_ulonglong * 5)()
-        check(lib().fn_edges_work_counts(self.h, c, 5, int(bool(reset))), "fn_edges_work_counts")
-        return dict(zip(("probe", "verify", "mprobe", "knn_pairs", "ik_starts"), [int(x) for x in c]))
+        c = (C.c_ulonglong * 7)()
+        check(lib().fn_edges_work_counts(self.h, c, 7, int(bool(reset))), "fn_edges_work_counts")
+        return dict(zip(("probe", "verify", "mprobe", "knn_pairs", "ik_starts", "window_edges",
+                         "rescans"), [int(x) for x in c]))

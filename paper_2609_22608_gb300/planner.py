@@ -252,12 +252,13 @@ class Planner:
               "fn_planner_kernel_ms")
         return [(names[i].decode(), float(ms[i])) for i in range(min(n.value, cap))]
 
-    WORK = ("probe", "verify", "mprobe", "knn_pairs", "ik_starts")
+    WORK = ("probe", "verify", "mprobe", "knn_pairs", "ik_starts", "surrogate_edges",
+            "surrogate_rescans")
 
     def work_counts(self, reset=False):
         """fn_planner_work_counts: dict of the planner's work counters."""
-        c = (C.c_ulonglong * 5)()
-        check(_bind().fn_planner_work_counts(self.h, c, 5, int(bool(reset))),
+        c = (C.c_ulonglong * 7)()
+        check(_bind().fn_planner_work_counts(self.h, c, 7, int(bool(reset))),
               "fn_planner_work_counts")
         return dict(zip(self.WORK, [int(x) for x in c]))
 
