@@ -320,6 +320,11 @@ def whole_job_rate(units_per_rank, world, ms):
 FLOP_PER_PAIR = 44             # one (query, node) distance of the parent search
 FLOP_PER_IK_START = 25987      # one damped-least-squares start, 24 iterations + final check
 
+# DRAM bytes (read + written) per launch from one ncu capture of the kernel on
+# this workload (profiles/plan_kernels_tree4096_batch2048.md); an entry is
+# removed when its kernel changes, and the roofline then reports null
+MEASURED_DRAM_BYTES = {"k_plan_sample": 340224, "k_plan_knn": 318976, "k_plan_probe": 1097984}
+
 
 def kernel_table(traced):
     """{kernel: {"launches": n, "ms": total}} of one traced iteration."""
@@ -331,7 +336,7 @@ def kernel_table(traced):
     return tab
 
 
-def roofline_from_trace(traced, work):
+def roofline_from_trace(traced, work, workload="iteration"):
     """Roofline object for the kernel with the largest share of the traced
     iteration: its algorithmic FLOP (work counter x FLOP per unit) over its
     own event-timed duration, against the derived FP32 peak."""
@@ -346,10 +351,13 @@ def roofline_from_trace(traced, work):
     dom = max(tab, key=lambda k: tab[k]["ms"])
     peak = fp32_peak_tflops()
     total = sum(t["ms"] for t in tab.values())
-    out = {"bound": "alu", "peak": peak, "unit": "TFLOP/s", "traffic": None, "kernel": dom,
+    traffic = MEASURED_DRAM_BYTES.get(dom) if workload == "iteration" else None
+    out = {"bound": "alu", "peak": peak, "unit": "TFLOP/s", "traffic": traffic, "kernel": dom,
            "launches": tab[dom]["launches"], "kernel_ms": tab[dom]["ms"] / tab[dom]["launches"],
            "share_of_traced_iteration": tab[dom]["ms"] / total,
-           "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 FLOP x max SM clock (of derived)"}
+           "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 FLOP x max SM clock (of derived)",
+           "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum per launch, one ncu "
+                           "capture of this kernel on this workload (L2-resident inputs)"}
     n, f, what = units.get(dom, (None, None, None))
     if n is None:
         out.update({"achieved": None, "frac": None,
