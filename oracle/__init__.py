@@ -73,6 +73,10 @@ def lib():
         L.or_time_edges.argtypes = [P(OrArm), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                     C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_void_p, C.c_void_p]
+        L.or_time_edges_nary.argtypes = [P(OrArm), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_int, C.c_int, C.c_void_p, C.c_float, C.c_int,
+                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_void_p]
         L.or_rho_batch.argtypes = [P(OrArm), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                    C.c_void_p]
         L.or_torque_dump.argtypes = [P(OrArm), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -192,6 +196,29 @@ def time_edges(arm, s0, s1, T_grid, S, mode=0, T_fixed=None, T_cap=None):
                     None if Tf is None else _p(Tf), None if Tc is None else _p(Tc),
                     _p(k), _p(Ts), _p(r3), _p(ok))
     return dict(k_star=k, T_star=Ts, rho3=r3, ok=ok)
+
+
+def time_edges_nary(arm, s0, s1, T_grid, S, eps, max_rounds=8, T_cap=None):
+    """Grid scan refined by the N-ary search (N = 32) to a bracket
+    (T_lo, T_star] no wider than eps; rho3/ok at the refined T_star."""
+    L = lib()
+    A = arm_struct(arm)
+    s0 = np.ascontiguousarray(s0, np.float32)
+    s1 = np.ascontiguousarray(s1, np.float32)
+    E = s0.shape[0]
+    T_grid = np.ascontiguousarray(T_grid, np.float32)
+    Tc = None if T_cap is None else np.ascontiguousarray(T_cap, np.float32)
+    k = np.zeros(E, np.int32)
+    Ts = np.zeros(E, np.float32)
+    Tl = np.zeros(E, np.float32)
+    r3 = np.zeros((E, 3), np.float64)
+    ok = np.zeros(E, np.uint8)
+    rounds = np.zeros(E, np.int32)
+    margin = np.zeros(E, np.float64)
+    L.or_time_edges_nary(C.byref(A), E, _p(s0), _p(s1), _p(T_grid), len(T_grid), int(S),
+                         None if Tc is None else _p(Tc), float(np.float32(eps)), int(max_rounds),
+                         _p(k), _p(Ts), _p(Tl), _p(r3), _p(ok), _p(rounds), _p(margin))
+    return dict(k_star=k, T_star=Ts, T_lo=Tl, rho3=r3, ok=ok, rounds=rounds, margin=margin)
 
 
 def rho_batch(arm, s0, s1, T, S):

@@ -307,6 +307,104 @@ void or_time_edges(const or_arm* arm, int E, const float* s0, const float* s1,
   }
 }
 
+/* Def. "Minimum feasible time" refined by the N-ary search that the paper
+ * describes after it: the bracket is split into N equal slots, every slot
+ * boundary is checked, and the slot where the check first passes is split
+ * again, until the bracket is no wider than eps.  Readings:
+ *   - the first bracket is the grid cell of the grid scan's k*:
+ *     (T_{k*-1}, T_{k*}], with T_{-1} = 0; its upper end is feasible;
+ *   - a round checks the N - 1 interior points t_j = a + j w (w = (b - a)/N)
+ *     in ascending order and keeps [t_{j-1}, t_j] for the first feasible t_j
+ *     (or [t_{N-1}, b] if none is); like the grid scan, it assumes no
+ *     monotonicity;
+ *   - N = 32; the points are formed in single precision (w = (b - a) * 2^-5,
+ *     t_j = fmaf(j, w, a)) so that both implementations check the same
+ *     durations; the checks themselves are in double precision here;
+ *   - rounds run while b - a > eps (single precision), at most max_rounds;
+ *   - rho_v is checked once, at the refined T* = b.
+ * margin[e] (may be NULL): the smallest |max(rho_tau, rho_P) - 1| over every
+ * duration this routine checked for the edge (grid and rounds), +inf if none. */
+#define OR_NARY_N 32
+void or_time_edges_nary(const or_arm* arm, int E, const float* s0, const float* s1,
+                        const float* T_grid, int K, int S, const float* T_cap, float eps,
+                        int max_rounds, int* k_star, float* T_star, float* T_lo, double* rho3,
+                        unsigned char* ok, int* rounds, double* margin) {
+  int n = arm->dof;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int e = 0; e < E; ++e) {
+    const float* sa = s0 + 16 * (size_t)e;
+    const float* sb = s1 + 16 * (size_t)e;
+    double* r3 = rho3 + 3 * (size_t)e;
+    double mg = INFINITY;
+    k_star[e] = -1;
+    T_star[e] = INFINITY;
+    T_lo[e] = NAN;
+    rounds[e] = 0;
+    r3[0] = r3[1] = r3[2] = NAN;
+    ok[e] = 0;
+    if (!state_finite(sa, n) || !state_finite(sb, n)) {
+      k_star[e] = -2;
+      T_star[e] = NAN;
+      if (margin) margin[e] = mg;
+      continue;
+    }
+    double q0[7], qd0[7], q1[7], qd1[7];
+    unpack(sa, n, q0, qd0);
+    unpack(sb, n, q1, qd1);
+    double rt = NAN, rp = NAN;
+    for (int k = 0; k < K; ++k) {
+      if (T_cap && !(T_grid[k] <= T_cap[e])) break;
+      double t_rt, t_rp;
+      rho_tp(arm, q0, qd0, q1, qd1, (double)T_grid[k], S, &t_rt, &t_rp);
+      double m = fmax(t_rt, t_rp);
+      if (fabs(m - 1.0) < mg) mg = fabs(m - 1.0);
+      if (t_rt <= 1.0 && t_rp <= 1.0) {
+        k_star[e] = k;
+        rt = t_rt;
+        rp = t_rp;
+        break;
+      }
+    }
+    if (k_star[e] < 0) {
+      if (margin) margin[e] = mg;
+      continue;
+    }
+    float a = k_star[e] > 0 ? T_grid[k_star[e] - 1] : 0.0f;
+    float b = T_grid[k_star[e]];
+    int r = 0;
+    while (r < max_rounds && (b - a) > eps) {
+      float w = (b - a) * 0.03125f;
+      int js = OR_NARY_N;
+      for (int j = 1; j < OR_NARY_N; ++j) {
+        float t = fmaf((float)j, w, a);
+        double t_rt, t_rp;
+        rho_tp(arm, q0, qd0, q1, qd1, (double)t, S, &t_rt, &t_rp);
+        double m = fmax(t_rt, t_rp);
+        if (fabs(m - 1.0) < mg) mg = fabs(m - 1.0);
+        if (t_rt <= 1.0 && t_rp <= 1.0) {
+          js = j;
+          rt = t_rt;
+          rp = t_rp;
+          break;
+        }
+      }
+      float lo = js == 1 ? a : fmaf((float)(js - 1), w, a);
+      float hi = js == OR_NARY_N ? b : fmaf((float)js, w, a);
+      a = lo;
+      b = hi;
+      ++r;
+    }
+    T_star[e] = b;
+    T_lo[e] = a;
+    rounds[e] = r;
+    r3[0] = rt;
+    r3[1] = rp;
+    r3[2] = rho_v_of(arm, q0, qd0, q1, qd1, (double)b);
+    ok[e] = r3[2] <= 1.0 ? 1 : 0;
+    if (margin) margin[e] = mg;
+  }
+}
+
 void or_torque_dump(const or_arm* arm, int E, const float* s0, const float* s1,
                     const float* T, int S, double* tau) {
   int n = arm->dof;

@@ -10,7 +10,8 @@
  *   cubic edge ............ Def. "Cubic edge", Eq. (cubic)
  *   torque ................ Eq. (torque) = RNEA + reflected rotor inertia + Eq. (friction)
  *   feasibility ratios .... Def. "Feasibility Check", Eq. (rho)
- *   minimum feasible time . Def. "Minimum feasible time" over a duration grid
+ *   minimum feasible time . Def. "Minimum feasible time" over a duration grid,
+ *                           refined by the N-ary search that follows it
  *   nearest parents ....... Sec. IV-E "Batched expansion" (brute-force scan)
  *   goal chart ............ Def. "Goal chart" and the decoding described after it
  *   objective ............. Eq. (objective), Eq. (terms)
@@ -77,6 +78,16 @@ void or_time_edges(const or_arm* arm, int E, const float* s0, const float* s1,
                    const float* T_grid, int K, int S, int mode, const float* T_fixed,
                    const float* T_cap, int* k_star, float* T_star, double* rho3,
                    unsigned char* ok);
+
+/* The grid scan refined by the N-ary search (N = 32) to a bracket
+ * (T_lo, T_star] no wider than eps (at most max_rounds rounds; rounds[e]
+ * counts them).  k_star is the grid scan's index; rho3 and ok are taken at
+ * the refined T_star.  margin (may be NULL) reports the smallest
+ * |max(rho_tau, rho_P) - 1| over the durations checked. */
+void or_time_edges_nary(const or_arm* arm, int E, const float* s0, const float* s1,
+                        const float* T_grid, int K, int S, const float* T_cap, float eps,
+                        int max_rounds, int* k_star, float* T_star, float* T_lo, double* rho3,
+                        unsigned char* ok, int* rounds, double* margin);
 
 /* rho3 at an arbitrary per-edge duration T[e] (all S samples). */
 void or_rho_batch(const or_arm* arm, int E, const float* s0, const float* s1,
