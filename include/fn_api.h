@@ -148,6 +148,44 @@ fn_status fn_time_edges_counted(const fn_arm_t* arm, const float* s0, const floa
                                 unsigned long long* sample_count, void* stream);
 
 /*
+ * fn_time_edges_nary -- minimum feasible duration refined by the N-ary
+ * search of Sec. IV-D (the search after Def. "Minimum feasible time").
+ *
+ * First the grid scan of FN_MODE_FULL (same grid, cap and k_star rule).
+ * For an edge with k* >= 0 the bracket [a, b] = [T_{k*-1}, T_{k*}]
+ * (a = 0 for k* = 0) is then refined in rounds while b - a > eps and fewer
+ * than max_rounds rounds ran: with w = (b - a) / 32 the interior points
+ * t_j = fmaf(j, w, a), j = 1..31 (single precision) are checked in
+ * ascending order (rho_tau <= 1 and rho_P <= 1, S samples each), and the
+ * bracket becomes [t_{j-1}, t_j] for the first passing t_j (t_0 = a), or
+ * [t_31, b] if none passes.  No monotonicity is assumed, as in the grid
+ * scan.  rho_v is checked once at the refined T* = b.  A round takes about
+ * log2(32) = 5 bits of T*: ceil(log_32(width / eps)) rounds in all.
+ *
+ * Arguments (as fn_time_edges unless stated)
+ *   T_grid, K   host [K] f32 ascending grid, 1 <= K <= FN_MAX_GRID.
+ *   T_cap       device [E] f32 or NULL.
+ *   eps         bracket width to reach (seconds, f32, > 0, finite).
+ *   max_rounds  0..16 (0: the grid result).
+ *   k_star      device [E] i32: the grid index (-1 none, -2 invalid input).
+ *   T_star      device [E] f32: refined duration b (+inf none, NaN invalid).
+ *   T_lo        device [E] f32 or NULL: the bracket's lower end a, the last
+ *               duration shown infeasible (0 if none was); NaN if k* < 0.
+ *   rho3, ok    device: (rho_tau, rho_P, rho_v) and ok at T_star.
+ *   rounds      device [E] i32 or NULL: rounds run.
+ *   sample_count device, one u64 or NULL: torque evaluations are ADDED.
+ *   stream      cudaStream_t or NULL.
+ * Ownership: all device buffers are the caller's; nothing is allocated.
+ * Errors: FN_EINVAL for a bad argument (nothing launched), FN_ECUDA on a
+ * launch error.  Non-finite states give k_star = -2 for that edge only.
+ */
+fn_status fn_time_edges_nary(const fn_arm_t* arm, const float* s0, const float* s1, int E,
+                             const float* T_grid, int K, int S, const float* T_cap, float eps,
+                             int max_rounds, int32_t* k_star, float* T_star, float* T_lo,
+                             float* rho3, uint8_t* ok, int32_t* rounds,
+                             unsigned long long* sample_count, void* stream);
+
+/*
  * fn_autotune_time_edges -- the schedule autotuner for fn_time_edges: runs
  * the call (same arguments) with every compiled schedule variant of the edge
  * kernel (register budget / resident blocks per SM), `reps` timed runs each

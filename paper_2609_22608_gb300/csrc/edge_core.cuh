@@ -12,6 +12,11 @@
 //           = samples (compensated coefficients), warp-ballot exit at the first
 //           violating batch; the first duration that passes is k*, every lower
 //           index having been shown infeasible by a violating sample;
+//   witness: (optional) when a verify fails, its first violating sample is
+//           probed at every remaining survivor before the next verify; on
+//           closely spaced durations (the N-ary rounds) neighbours tend to
+//           violate at the same sample, on the log grid they do not often
+//           enough to pay;
 //   rho_v : lane j < 7 takes joint j's exact velocity extremum at T_{k*}.
 #pragma once
 
@@ -74,6 +79,9 @@ __device__ __forceinline__ float warp_rho_v(const ArmK& A, const float* es, floa
 //   PROBE_MID: the lanes still passing, interior samples mid_probe_index(j)
 //   VERIFY   : lanes = samples (s0 + lane) of one duration, compensated
 //              coefficients, until a violating batch or all S samples pass
+//   PROBE_W  : (witness = true) after a failed verify, the remaining
+//              survivors at the failed duration's first violating sample
+//              (plain coefficients)
 // Grid mode (fixed = false): returns the first feasible index in
 // [k_begin, Kadm) (k_begin = 0 unless a caller scans a sub-range).
 // Fixed mode: one duration Tfix is verified (all S samples when exact,
@@ -81,10 +89,11 @@ __device__ __forceinline__ float warp_rho_v(const ArmK& A, const float* es, floa
 __device__ __forceinline__ int edge_scan(const ArmK& A, const float* es, CubicLane cb,
                                          LaneWrench wr, const float* sT, int Kadm, int S,
                                          bool fixed, float Tfix, bool exact, float& rt, float& rp,
-                                         unsigned& nsamp, int k_begin = 0) {
-  enum { PROBE_LO = 0, PROBE_HI = 1, VERIFY = 2, PROBE_MID = 3 };
+                                         unsigned& nsamp, int k_begin = 0,
+                                         bool witness = false) {
+  enum { PROBE_LO = 0, PROBE_HI = 1, VERIFY = 2, PROBE_MID = 3, PROBE_W = 4 };
   const int lane = threadIdx.x & 31;
-  int mode = PROBE_LO, base = k_begin, kk = 0, s0 = 0, mj = 0;
+  int mode = PROBE_LO, base = k_begin, kk = 0, s0 = 0, mj = 0, sw = 0;
   unsigned cand = 0u;   // PROBE_HI: lanes to evaluate; VERIFY: durations left in the chunk
   float mt = 0.f, mp = 0.f;
   bool bad = false;
@@ -105,9 +114,9 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, const float* es, CubicLa
     if (mode == VERIFY) {
       active = s0 + lane < S;
       u = sample_u(s0 + lane, S);
-    } else if (mode == PROBE_MID) {
+    } else if (mode == PROBE_MID || mode == PROBE_W) {
       active = (cand >> lane) & 1u;
-      u = sample_u(mid_probe_index(mj, S), S);
+      u = sample_u(mode == PROBE_MID ? mid_probe_index(mj, S) : sw, S);
     } else {
       active = mode == PROBE_LO ? (base + lane < Kadm) : ((cand >> lane) & 1u);
       u = mode == PROBE_LO ? 0.f : 1.f;
@@ -125,7 +134,7 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, const float* es, CubicLa
         mode = PROBE_HI;
         continue;
       }
-    } else if (mode == PROBE_HI || mode == PROBE_MID) {
+    } else if (mode == PROBE_HI || mode == PROBE_MID || mode == PROBE_W) {
       cand = ok;                       // durations whose probes so far pass
       if (cand && mode == PROBE_HI && S > 2) {
         mode = PROBE_MID;
@@ -149,6 +158,14 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, const float* es, CubicLa
       }
       if (viol) {                      // kk is infeasible
         cand &= cand - 1;
+        if (cand && witness) {         // probe its witness sample at the rest
+          sw = s0 + __ffs(act & ~ok) - 1;
+          mode = PROBE_W;
+          Cubic c;
+          if (base + lane < Kadm) cubic_coef_sh<false>(es, sT[base + lane], c);
+          cb.store(c);
+          continue;
+        }
         if (cand) next_dur = base + __ffs(cand) - 1;
       } else if (s0 + 32 < S) {
         s0 += 32;

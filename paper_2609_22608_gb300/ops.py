@@ -14,7 +14,7 @@ import torch
 from . import _lib
 from ._lib import FN_MODE_FIXED, FN_MODE_FULL, arm_struct, check, lib
 
-__all__ = ["time_edges", "rnea_dump", "knn_tree", "knn_workspace_bytes", "make_edges", "EdgeEngine",
+__all__ = ["time_edges", "time_edges_nary", "autotune_time_edges", "rnea_dump", "knn_tree", "knn_workspace_bytes", "make_edges", "EdgeEngine",
            "FN_MODE_FULL", "FN_MODE_FIXED", "version"]
 
 
@@ -71,6 +71,56 @@ def time_edges(arm, s0, s1, T_grid=None, S=32, mode=FN_MODE_FULL, T_fixed=None, 
                                          _ptr(out["rho3"]), _ptr(out["ok"]), _ptr(sample_count),
                                          _stream(stream))
     check(st, "fn_time_edges")
+    return out
+
+
+def autotune_time_edges(arm, s0, s1, T_grid, S, reps=3, T_cap=None, stream=None):
+    """fn_autotune_time_edges (FULL mode): times every register-budget variant
+    of the edge kernels on this workload and keeps the fastest for its shape
+    (the N-ary refinement follows the same choice).  Returns (variant, ms[3])."""
+    _states(s0, "s0"); _states(s1, "s1")
+    E = s0.shape[0]
+    A = arm_struct(arm)
+    dev = s0.device
+    out = dict(k_star=torch.empty(E, dtype=torch.int32, device=dev),
+               T_star=torch.empty(E, dtype=torch.float32, device=dev),
+               rho3=torch.empty(E, 3, dtype=torch.float32, device=dev),
+               ok=torch.empty(E, dtype=torch.uint8, device=dev))
+    g = np.ascontiguousarray(np.asarray(T_grid, np.float32))
+    chosen = C.c_int(-1)
+    ms = (C.c_float * 3)()
+    st = lib().fn_autotune_time_edges(C.byref(A), _ptr(s0), _ptr(s1), E,
+                                      g.ctypes.data_as(C.c_void_p), int(g.size), int(S),
+                                      FN_MODE_FULL, None, _ptr(T_cap), _ptr(out["k_star"]),
+                                      _ptr(out["T_star"]), _ptr(out["rho3"]), _ptr(out["ok"]),
+                                      int(reps), C.byref(chosen), ms, _stream(stream))
+    check(st, "fn_autotune_time_edges")
+    return int(chosen.value), [float(x) for x in ms]
+
+
+def time_edges_nary(arm, s0, s1, T_grid, S, eps, max_rounds=8, T_cap=None, out=None,
+                    stream=None, sample_count=None):
+    """fn_time_edges_nary: grid scan refined by the N-ary search (N = 32) to a
+    bracket (T_lo, T_star] no wider than eps.  Returns dict(k_star, T_star,
+    T_lo, rho3, ok, rounds)."""
+    _states(s0, "s0"); _states(s1, "s1")
+    E = s0.shape[0]
+    A = arm_struct(arm)
+    if out is None:
+        dev = s0.device
+        out = dict(k_star=torch.empty(E, dtype=torch.int32, device=dev),
+                   T_star=torch.empty(E, dtype=torch.float32, device=dev),
+                   T_lo=torch.empty(E, dtype=torch.float32, device=dev),
+                   rho3=torch.empty(E, 3, dtype=torch.float32, device=dev),
+                   ok=torch.empty(E, dtype=torch.uint8, device=dev),
+                   rounds=torch.empty(E, dtype=torch.int32, device=dev))
+    g = np.ascontiguousarray(np.asarray(T_grid, np.float32))
+    st = lib().fn_time_edges_nary(C.byref(A), _ptr(s0), _ptr(s1), E, g.ctypes.data_as(C.c_void_p),
+                                  int(g.size), int(S), _ptr(T_cap), float(eps), int(max_rounds),
+                                  _ptr(out["k_star"]), _ptr(out["T_star"]), _ptr(out.get("T_lo")),
+                                  _ptr(out["rho3"]), _ptr(out["ok"]), _ptr(out.get("rounds")),
+                                  _ptr(sample_count), _stream(stream))
+    check(st, "fn_time_edges_nary")
     return out
 
 
