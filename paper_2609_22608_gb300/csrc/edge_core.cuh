@@ -12,8 +12,8 @@
 //           = samples (compensated coefficients), warp-ballot exit at the first
 //           violating batch; the first duration that passes is k*, every lower
 //           index having been shown infeasible by a violating sample;
-//   witness: (optional) when a verify fails, its first violating sample is
-//           probed at every remaining survivor before the next verify; on
+//   witness: (optional) the sample that proved a duration infeasible is
+//           probed at the other candidates before any verify of them; on
 //           closely spaced durations (the N-ary rounds) neighbours tend to
 //           violate at the same sample, on the log grid they do not often
 //           enough to pay;
@@ -79,24 +79,34 @@ __device__ __forceinline__ float warp_rho_v(const ArmK& A, const float* es, floa
 //   PROBE_MID: the lanes still passing, interior samples mid_probe_index(j)
 //   VERIFY   : lanes = samples (s0 + lane) of one duration, compensated
 //              coefficients, until a violating batch or all S samples pass
-//   PROBE_W  : (witness = true) after a failed verify, the remaining
-//              survivors at the failed duration's first violating sample
-//              (plain coefficients)
+//   PROBE_W  : (wmode 2) one sample, the witness, at the remaining survivors
+//              (plain coefficients): after a failed verify, that duration's
+//              first violating sample; at the start, the caller's w_in
 // Grid mode (fixed = false): returns the first feasible index in
 // [k_begin, Kadm) (k_begin = 0 unless a caller scans a sub-range).
 // Fixed mode: one duration Tfix is verified (all S samples when exact,
 // else up to the first violating batch); returns 0 if it passes, else -1.
+// Witness modes (grid mode only; callers other than the N-ary refinement
+// pass 0 and the code folds away):
+//   wmode 1: record, per duration, the sample that proved it infeasible, and
+//            return in *w_out that of the duration just below the result
+//            (of the last admissible duration if none passes; -1 if it was
+//            not in the result's chunk of 32);
+//   wmode 2: as 1, plus the witness probes (PROBE_W), starting with w_in
+//            (if >= 0) at every duration in place of the end probes.
 __device__ __forceinline__ int edge_scan(const ArmK& A, const float* es, CubicLane cb,
                                          LaneWrench wr, const float* sT, int Kadm, int S,
                                          bool fixed, float Tfix, bool exact, float& rt, float& rp,
-                                         unsigned& nsamp, int k_begin = 0,
-                                         bool witness = false) {
+                                         unsigned& nsamp, int k_begin = 0, int wmode = 0,
+                                         int w_in = -1, int* w_out = nullptr) {
   enum { PROBE_LO = 0, PROBE_HI = 1, VERIFY = 2, PROBE_MID = 3, PROBE_W = 4 };
   const int lane = threadIdx.x & 31;
   int mode = PROBE_LO, base = k_begin, kk = 0, s0 = 0, mj = 0, sw = 0;
+  int kill = -1;        // wmode > 0: sample that proved duration base + lane infeasible
   unsigned cand = 0u;   // PROBE_HI: lanes to evaluate; VERIFY: durations left in the chunk
   float mt = 0.f, mp = 0.f;
   bool bad = false;
+  if (w_out) *w_out = -1;
   if (fixed) {
     mode = VERIFY;
     Cubic c;
@@ -107,26 +117,33 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, const float* es, CubicLa
     Cubic c;
     if (base + lane < Kadm) cubic_coef_sh<false>(es, sT[base + lane], c);
     cb.store(c);
+    if (wmode == 2 && w_in >= 0) {
+      mode = PROBE_W;
+      sw = w_in;
+      cand = __ballot_sync(0xffffffffu, base + lane < Kadm);
+    }
   }
   for (;;) {
     bool active;
-    float u;
+    int si;               // sample index of this pass (probes)
     if (mode == VERIFY) {
       active = s0 + lane < S;
-      u = sample_u(s0 + lane, S);
+      si = s0 + lane;
     } else if (mode == PROBE_MID || mode == PROBE_W) {
       active = (cand >> lane) & 1u;
-      u = sample_u(mode == PROBE_MID ? mid_probe_index(mj, S) : sw, S);
+      si = mode == PROBE_MID ? mid_probe_index(mj, S) : sw;
     } else {
       active = mode == PROBE_LO ? (base + lane < Kadm) : ((cand >> lane) & 1u);
-      u = mode == PROBE_LO ? 0.f : 1.f;
+      si = mode == PROBE_LO ? 0 : S - 1;
     }
+    const float u = sample_u(si, S);
     float a = 0.f, b = 0.f;
     if (active) sample_ratios(A, cb, u, a, b, wr);   // the single call site
     const bool pass = active && a <= 1.f && b <= 1.f;
     const unsigned act = __ballot_sync(0xffffffffu, active);
     const unsigned ok = __ballot_sync(0xffffffffu, pass);
     nsamp += __popc(act);
+    if (wmode > 0 && mode != VERIFY && active && !pass) kill = si;
     int next_dur = -1;  // duration to verify next, if any
     if (mode == PROBE_LO) {
       if (ok) {
@@ -157,9 +174,12 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, const float* es, CubicLa
         return bad ? -1 : 0;
       }
       if (viol) {                      // kk is infeasible
-        cand &= cand - 1;
-        if (cand && witness) {         // probe its witness sample at the rest
+        if (wmode > 0) {
           sw = s0 + __ffs(act & ~ok) - 1;
+          if (lane == kk - base) kill = sw;
+        }
+        cand &= cand - 1;
+        if (cand && wmode == 2) {      // probe its witness sample at the rest
           mode = PROBE_W;
           Cubic c;
           if (base + lane < Kadm) cubic_coef_sh<false>(es, sT[base + lane], c);
@@ -173,6 +193,11 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, const float* es, CubicLa
       } else {
         rt = warp_max(mt);
         rp = warp_max(mp);
+        if (w_out) {
+          const int below = kk - 1 - base;
+          const int w = __shfl_sync(0xffffffffu, kill, below >= 0 ? below : 0);
+          *w_out = below >= 0 ? w : -1;
+        }
         return kk;
       }
     }
@@ -187,8 +212,14 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, const float* es, CubicLa
       continue;
     }
     // nothing left in this chunk of 32 durations: probe the next one
+    if (w_out) {
+      const int last = Kadm - 1 - base;
+      const int w = __shfl_sync(0xffffffffu, kill, last < 32 ? last : 0);
+      *w_out = last < 32 ? w : -1;
+    }
     base += 32;
     if (base >= Kadm) return -1;
+    kill = -1;
     mode = PROBE_LO;
     cand = 0u;
     Cubic c;

@@ -10,9 +10,10 @@
 // (edge_core.cuh) run over a 31-entry duration list in the warp's shared
 // slot, so the kernel keeps a single torque-evaluation call site: the grid
 // pass and every round go through the same edge_scan call in one loop.  The
-// rounds turn on witness probing: the 31 points are so close together that
-// a point below T* that survives the probes usually violates at the same
-// sample as the one verified before it.
+// rounds use witness probing: the 31 points are so close together that the
+// points below T* usually violate at the sample that proved the bracket's
+// lower end infeasible, so a round starts by probing that sample at every
+// point, and a failed verify passes its violating sample on the same way.
 #include <cuda_runtime.h>
 
 #include "edge_core.cuh"
@@ -61,25 +62,33 @@ __global__ void __launch_bounds__(32 * NARY_WARPS, MINB)
     if (finite) {
       const float* dur = sT;                 // the grid, then each round's points
       int n = grid_prefix(sT, K, Tp);
+      int wit = -1;                          // sample that proved a infeasible
       for (;;) {
         float t_rt = NAN, t_rp = NAN;
+        int w_out = -1;
+        const bool grid = dur == sT;
         const int idx = edge_scan(A, es, cb, wr, dur, n, S, false, 0.f, false, t_rt, t_rp, nsamp,
-                                  0, dur != sT);
-        if (dur == sT) {
+                                  0, grid ? 1 : 2, wit, &w_out);
+        if (grid) {
           k = idx;
           if (idx < 0) break;
           a = idx > 0 ? sT[idx - 1] : 0.f;
           b = sT[idx];
+          wit = idx > 0 ? w_out : -1;
           rt = t_rt;
           rp = t_rp;
         } else {
           if (idx >= 0) {                    // interior point idx + 1 is the first to pass
-            a = idx > 0 ? sub[idx - 1] : a;
+            if (idx > 0) {
+              a = sub[idx - 1];
+              wit = w_out;
+            }
             b = sub[idx];
             rt = t_rt;
             rp = t_rp;
           } else {                           // only the known-feasible upper end passes
             a = sub[NARY_N - 2];
+            wit = w_out;
           }
           ++r;
         }
