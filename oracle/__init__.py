@@ -77,6 +77,12 @@ def lib():
                                          C.c_int, C.c_int, C.c_void_p, C.c_float, C.c_int,
                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_void_p, C.c_void_p]
+        L.or_controller_torque.argtypes = [P(OrArm), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                           C.c_void_p, C.c_double, C.c_void_p, C.c_void_p,
+                                           C.c_void_p, C.c_void_p]
+        L.or_check_edges.argtypes = [P(OrArm), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                     C.c_int, C.c_void_p, C.c_int, C.c_double, C.c_void_p,
+                                     C.c_void_p, C.c_void_p]
         L.or_rho_batch.argtypes = [P(OrArm), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                    C.c_void_p]
         L.or_torque_dump.argtypes = [P(OrArm), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -219,6 +225,43 @@ def time_edges_nary(arm, s0, s1, T_grid, S, eps, max_rounds=8, T_cap=None):
                          None if Tc is None else _p(Tc), float(np.float32(eps)), int(max_rounds),
                          _p(k), _p(Ts), _p(Tl), _p(r3), _p(ok), _p(rounds), _p(margin))
     return dict(k_star=k, T_star=Ts, T_lo=Tl, rho3=r3, ok=ok, rounds=rounds, margin=margin)
+
+
+def controller_torque(arm, state, goal, T, dt, tau_prev=None, rate=None):
+    """Eq. (controller) for B instances; returns dict(tau, qdd [B][7] f64,
+    flags [B] u8)."""
+    A = arm_struct(arm)
+    state = np.ascontiguousarray(state, np.float32)
+    goal = np.ascontiguousarray(goal, np.float32)
+    T = np.ascontiguousarray(T, np.float32)
+    B = state.shape[0]
+    tp = None if tau_prev is None else np.ascontiguousarray(tau_prev, np.float32)
+    rt = None if rate is None else _d(rate)
+    tau = np.zeros((B, 7), np.float64)
+    qdd = np.zeros((B, 7), np.float64)
+    flags = np.zeros(B, np.uint8)
+    lib().or_controller_torque(C.byref(A), B, _p(state), _p(goal), _p(T),
+                               None if tp is None else _p(tp), float(dt),
+                               None if rt is None else _p(rt), _p(tau), _p(qdd), _p(flags))
+    return dict(tau=tau, qdd=qdd, flags=flags)
+
+
+def check_edges(arm, s0, s1, T, S, S_clear, obs, margin):
+    """Full-resolution recheck of edges at their own durations; returns
+    dict(rho3 [E][3], clearance [E], ok [E])."""
+    A = arm_struct(arm)
+    s0 = np.ascontiguousarray(s0, np.float32)
+    s1 = np.ascontiguousarray(s1, np.float32)
+    T = np.ascontiguousarray(T, np.float32)
+    E = s0.shape[0]
+    ob = np.ascontiguousarray(np.asarray(obs, np.float32).reshape(-1, 4))
+    r3 = np.zeros((E, 3), np.float64)
+    cl = np.zeros(E, np.float64)
+    ok = np.zeros(E, np.uint8)
+    lib().or_check_edges(C.byref(A), E, _p(s0), _p(s1), _p(T), int(S), int(S_clear),
+                         _p(ob) if len(ob) else None, len(ob), float(margin), _p(r3), _p(cl),
+                         _p(ok))
+    return dict(rho3=r3, clearance=cl, ok=ok)
 
 
 def rho_batch(arm, s0, s1, T, S):

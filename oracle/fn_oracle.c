@@ -898,3 +898,101 @@ double or_edge_clearance(const or_arm* arm, const float* s0, const float* s1, do
   }
   return best;
 }
+
+/* The tracking controller of Eq. (controller), one control cycle per
+ * instance b.  From the measured state (q, qd) it refits the cubic to the
+ * rendezvous (q_g, qd_g) over the horizon T and takes its initial
+ * acceleration 6 (q_g - q) / T^2 - (4 qd + 2 qd_g) / T, clipped to [l, u];
+ * Eq. (torque) gives the command, which is clipped to the torque, power and
+ * slew limits.  Readings:
+ *   - [l, u] keeps the velocity after one control period dt inside the
+ *     taper: l = (-qdbar(q) - qd) / dt, u = (qdbar(q) - qd) / dt;
+ *   - torque: each tau_i clamped to [-tau_max_i, tau_max_i];
+ *   - power: if |sum_i tau_i qd_i| > W_max the whole vector is scaled by
+ *     W_max / |sum| (its direction is kept);
+ *   - slew (if tau_prev and rate are given): each tau_i clamped to
+ *     tau_prev_i +- rate_i dt, last, so the rate limit always holds;
+ *   - flags: bit 0 acceleration clipped, 1 torque, 2 power, 3 slew;
+ *     0x80 invalid input (non-finite values, T <= 0): tau and qdd are NaN. */
+void or_controller_torque(const or_arm* arm, int B, const float* state, const float* goal,
+                          const float* T, const float* tau_prev, double dt, const double* rate,
+                          double* tau, double* qdd, unsigned char* flags) {
+  int n = arm->dof;
+  for (int b = 0; b < B; ++b) {
+    const float* sx = state + 16 * (size_t)b;
+    const float* sg = goal + 16 * (size_t)b;
+    double* tb = tau + 7 * (size_t)b;
+    double* ab = qdd + 7 * (size_t)b;
+    double Tb = (double)T[b];
+    unsigned char f = 0;
+    if (!state_finite(sx, n) || !state_finite(sg, n) || !isfinite(Tb) || !(Tb > 0.0)) {
+      for (int i = 0; i < 7; ++i) tb[i] = ab[i] = NAN;
+      flags[b] = 0x80;
+      continue;
+    }
+    double q[7], qd[7], qg[7], qdg[7];
+    unpack(sx, n, q, qd);
+    unpack(sg, n, qg, qdg);
+    for (int i = 0; i < n; ++i) {
+      double a = 6.0 * (qg[i] - q[i]) / (Tb * Tb) - (4.0 * qd[i] + 2.0 * qdg[i]) / Tb;
+      double bound = or_taper(arm, i, q[i]);
+      double lo = (-bound - qd[i]) / dt, hi = (bound - qd[i]) / dt;
+      double c = a < lo ? lo : (a > hi ? hi : a);
+      if (c != a) f |= 1;
+      ab[i] = c;
+    }
+    double t7[7];
+    or_torque(arm, q, qd, ab, t7);
+    for (int i = 0; i < n; ++i) {
+      double m = arm->tau_max[i];
+      if (t7[i] > m) { t7[i] = m; f |= 2; }
+      if (t7[i] < -m) { t7[i] = -m; f |= 2; }
+    }
+    double pw = 0.0;
+    for (int i = 0; i < n; ++i) pw += t7[i] * qd[i];
+    if (fabs(pw) > arm->w_max) {
+      double sc = arm->w_max / fabs(pw);
+      for (int i = 0; i < n; ++i) t7[i] *= sc;
+      f |= 4;
+    }
+    if (tau_prev && rate) {
+      const float* tp = tau_prev + 7 * (size_t)b;
+      for (int i = 0; i < n; ++i) {
+        double lo = (double)tp[i] - rate[i] * dt, hi = (double)tp[i] + rate[i] * dt;
+        if (t7[i] < lo) { t7[i] = lo; f |= 8; }
+        if (t7[i] > hi) { t7[i] = hi; f |= 8; }
+      }
+    }
+    for (int i = 0; i < 7; ++i) tb[i] = i < n ? t7[i] : 0.0;
+    for (int i = n; i < 7; ++i) ab[i] = 0.0;
+    flags[b] = f;
+  }
+}
+
+/* The full-resolution recheck of a plan's edges (Sec. IV-E: the plan sent to
+ * the controller is rechecked at full resolution): each edge at its own
+ * duration T[e], all three ratios of Def. "Feasibility Check" over S samples
+ * and the clearance of or_edge_clearance over S_clear points;
+ * ok = rho_tau, rho_P, rho_v <= 1 and (no obstacles or clearance >= margin).
+ * Non-finite states or T <= 0: NaN ratios and clearance, ok = 0. */
+void or_check_edges(const or_arm* arm, int E, const float* s0, const float* s1, const float* T,
+                    int S, int S_clear, const float* obs, int n_obs, double margin, double* rho3,
+                    double* clearance, unsigned char* ok) {
+  int n = arm->dof;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int e = 0; e < E; ++e) {
+    const float* a = s0 + 16 * (size_t)e;
+    const float* b = s1 + 16 * (size_t)e;
+    double* r3 = rho3 + 3 * (size_t)e;
+    if (!state_finite(a, n) || !state_finite(b, n) || !isfinite(T[e]) || !(T[e] > 0.0f)) {
+      r3[0] = r3[1] = r3[2] = NAN;
+      clearance[e] = NAN;
+      ok[e] = 0;
+      continue;
+    }
+    or_rho(arm, a, b, (double)T[e], S, r3);
+    double c = n_obs > 0 ? or_edge_clearance(arm, a, b, (double)T[e], S_clear, obs, n_obs) : INFINITY;
+    clearance[e] = c;
+    ok[e] = (r3[0] <= 1.0 && r3[1] <= 1.0 && r3[2] <= 1.0 && (n_obs == 0 || c >= margin)) ? 1 : 0;
+  }
+}

@@ -16,6 +16,8 @@
  *   goal chart ............ Def. "Goal chart" and the decoding described after it
  *   objective ............. Eq. (objective), Eq. (terms)
  *   arrival-time pruning .. Eq. (reach)
+ *   tracking controller ... Eq. (controller) with the torque, power and slew clips
+ *   plan recheck .......... Sec. IV-E (the plan sent to the controller, full resolution)
  * Readings of passages that the paper leaves open are listed beside each
  * function in fn_oracle.c.
  */
@@ -137,6 +139,20 @@ int or_reach_time(const or_arm* arm, const or_problem* pr, const double* q, doub
  * along an edge at duration T over S collocation points (incl. both ends) */
 double or_edge_clearance(const or_arm* arm, const float* s0, const float* s1, double T,
                          int S, const float* obs, int n_obs);
+
+/* Eq. (controller) for B instances: state/goal [B][16] (q, pad, qd, pad),
+ * horizon T [B], tau_prev [B][7] and rate [7] (both NULL: no slew limit),
+ * control period dt; outputs tau, qdd [B][7] and flags [B] (bit 0 acc,
+ * 1 torque, 2 power, 3 slew clipped; 0x80 invalid input). */
+void or_controller_torque(const or_arm* arm, int B, const float* state, const float* goal,
+                          const float* T, const float* tau_prev, double dt, const double* rate,
+                          double* tau, double* qdd, unsigned char* flags);
+
+/* Full-resolution recheck: ratios over S samples, clearance over S_clear
+ * points (obs [n_obs][4]), ok per edge at its own duration T[e]. */
+void or_check_edges(const or_arm* arm, int E, const float* s0, const float* s1, const float* T,
+                    int S, int S_clear, const float* obs, int n_obs, double margin, double* rho3,
+                    double* clearance, unsigned char* ok);
 
 #ifdef __cplusplus
 }
