@@ -186,6 +186,60 @@ fn_status fn_time_edges_nary(const fn_arm_t* arm, const float* s0, const float* 
                              unsigned long long* sample_count, void* stream);
 
 /*
+ * fn_check_edges_full -- the full-resolution recheck of a plan's edges
+ * (Sec. IV-E: clearance and dynamics are checked coarsely during the search
+ * and the plan sent to the controller is rechecked at full resolution).
+ * Each edge at its own duration T[e]: rho_tau, rho_P over all S samples and
+ * rho_v (Def. "Feasibility Check", Eq. (rho)), and the least link-capsule
+ * clearance to the obstacle spheres over S_clear equally spaced points
+ * (both ends included).  ok[e] = rho_tau, rho_P, rho_v <= 1 and (no
+ * obstacles, or clearance >= margin).
+ *   s0, s1     device [E][16] f32 (16-byte aligned); T device [E] f32.
+ *   E          capacity; E_dev (device, one int, or NULL): the edges actually
+ *              present (min(E, *E_dev) are checked), for chaining after
+ *              fn_planner_incumbent_path without a host synchronisation.
+ *   S          2..FN_MAX_S; S_clear >= 2 when n_obs > 0.
+ *   n_obs, obs 0..FN_MAX_OBS spheres, host [n_obs][4] (centre, radius).
+ *   rho3       device [E][3] f32; clearance device [E] f32 (+inf without
+ *              obstacles); ok device [E] u8.
+ * Non-finite states or T <= 0 give NaN ratios and clearance and ok = 0.
+ * Errors: FN_EINVAL for a bad argument, FN_ECUDA on a launch error.
+ */
+fn_status fn_check_edges_full(const fn_arm_t* arm, const float* s0, const float* s1,
+                              const float* T, int E, const int* E_dev, int S, int S_clear,
+                              int n_obs, const float* obs, float margin, float* rho3,
+                              float* clearance, uint8_t* ok, void* stream);
+
+/*
+ * fn_controller_torque -- one cycle of the tracking controller of
+ * Eq. (controller) for B independent instances.
+ *
+ * From the measured state (q, qd) the cubic is refitted to the rendezvous
+ * (q_g, qd_g) over the horizon T; its initial acceleration
+ * 6 (q_g - q) / T^2 - (4 qd + 2 qd_g) / T is clipped per joint to [l, u],
+ * the box that keeps the velocity after one control period dt inside the
+ * taper: l = (-qdbar(q) - qd) / dt, u = (qdbar(q) - qd) / dt.  Eq. (torque)
+ * (RNEA + armature + friction) at (q, qd, qdd_des) gives the command, which
+ * is clipped to the arm's torque limits, then scaled as a whole onto W_max
+ * if |sum_j tau_j qd_j| exceeds it, then (with tau_prev) held within
+ * tau_rate_max dt of the previous command.
+ *   state, goal  device [B][16] f32: (q, pad, qd, pad) measured / rendezvous.
+ *   T            device [B] f32 horizons (> 0).
+ *   tau_prev     device [B][7] f32 or NULL (no slew clip).
+ *   dt           control period (s, > 0).
+ *   tau_rate_max host [7] f32 (N m/s, >= 0); required with tau_prev.
+ *   tau          device [B][7] f32; qdd_des device [B][7] f32 or NULL.
+ *   flags        device [B] u8 or NULL: bit 0 acceleration clipped, 1 torque,
+ *                2 power, 3 slew; 0x80 invalid input (non-finite values or
+ *                T <= 0), whose tau and qdd_des are NaN.
+ * Errors: FN_EINVAL for a bad argument, FN_ECUDA on a launch error.
+ */
+fn_status fn_controller_torque(const fn_arm_t* arm, int B, const float* state, const float* goal,
+                               const float* T, const float* tau_prev, float dt,
+                               const float* tau_rate_max, float* tau, float* qdd_des,
+                               uint8_t* flags, void* stream);
+
+/*
  * fn_autotune_time_edges -- the schedule autotuner for fn_time_edges: runs
  * the call (same arguments) with every compiled schedule variant of the edge
  * kernel (register budget / resident blocks per SM), `reps` timed runs each
@@ -458,6 +512,26 @@ fn_status fn_planner_work_counts(fn_planner_t* pl, unsigned long long* count, in
  * Synchronous. */
 fn_status fn_planner_get_tree(fn_planner_t* pl, int p, float* states, float* t,
                               int32_t* parent, float* J, float* nu, int* n, int cap);
+/*
+ * fn_planner_incumbent_path -- the incumbent plan of problem p as a list of
+ * edges, root first: edge i runs from node nodes[i] to nodes[i + 1] with the
+ * duration stored with its end node (the plan that Sec. IV-E rechecks at
+ * full resolution before it goes to the controller).
+ *   max_edges  capacity of the outputs (edges).
+ *   s0, s1     device [max_edges][16] f32 (16-byte aligned): edge states.
+ *   T          device [max_edges] f32: edge durations (NaN for edges into
+ *              nodes given by fn_planner_load_tree, which carry none).
+ *   nodes      device [max_edges + 1] i32 or NULL.
+ *   n_edges    device, one i32: the path length L (0: no incumbent; -1: the
+ *              parent links do not reach the root).  The arrays are written
+ *              only when 0 < L <= max_edges.
+ * Stream-ordered after the iteration that produced the incumbent; no host
+ * synchronisation (chain fn_check_edges_full with E_dev = n_edges).
+ * Errors: FN_EINVAL for a bad argument.
+ */
+fn_status fn_planner_incumbent_path(fn_planner_t* pl, int p, int max_edges, float* s0, float* s1,
+                                    float* T, int32_t* nodes, int32_t* n_edges, void* stream);
+
 /* Copy problem p's last candidate batch to host: states [B][16], T_req[B],
  * v_rel[B], valid[B] (goal candidates whose chart decoding succeeded, and
  * every free candidate).  Synchronous. */

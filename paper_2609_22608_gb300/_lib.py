@@ -69,8 +69,13 @@ def lib():
                                      vp, vp, vp, vp, vp, vp, vp, vp]
     L.fn_autotune_time_edges.argtypes = [C.POINTER(FnArm), vp, vp, i32, vp, i32, i32, i32, vp,
                                          vp, vp, vp, vp, vp, i32, vp, vp, vp]
+    L.fn_check_edges_full.argtypes = [C.POINTER(FnArm), vp, vp, vp, i32, vp, i32, i32, i32, vp,
+                                      f32, vp, vp, vp, vp]
+    L.fn_controller_torque.argtypes = [C.POINTER(FnArm), i32, vp, vp, vp, vp, f32, vp, vp, vp,
+                                       vp, vp]
     for name in ("fn_time_edges", "fn_rnea_dump", "fn_knn_tree", "fn_time_edges_counted",
-                 "fn_make_edges", "fn_time_edges_nary", "fn_autotune_time_edges"):
+                 "fn_make_edges", "fn_time_edges_nary", "fn_autotune_time_edges",
+                 "fn_check_edges_full", "fn_controller_torque"):
         getattr(L, name).restype = i32
     _lib = L
     return L

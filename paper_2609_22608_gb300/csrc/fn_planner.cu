@@ -1348,6 +1348,50 @@ __global__ void __launch_bounds__(PL_ATTACH_THREADS) k_plan_prune(PlanDev D, Arm
 }
 
 // ---------------------------------------------------------------------------
+// the incumbent plan of problem p as edges, root first (the plan that the
+// full-resolution recheck of Sec. IV-E takes): edge i runs from nodes[i] to
+// nodes[i + 1], with the duration stored with its end node.  *n_edges = the
+// path length L (0: no incumbent), -1 if the parent links do not lead to
+// the root; the arrays are written when 0 < L <= max_edges.  One thread: a
+// path is a few dozen edges.
+__global__ void k_plan_path(PlanDev D, int p, int max_edges, float* __restrict__ s0,
+                            float* __restrict__ s1, float* __restrict__ T,
+                            int32_t* __restrict__ nodes, int32_t* __restrict__ n_edges) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const long nb = (long)p * D.NC;
+  const int n = D.n_nodes[p];
+  const int inc = D.inc[p].id;
+  int L = 0;
+  if (inc >= n) {
+    L = -1;
+  } else if (inc > 0) {
+    int v = inc;
+    while (v != 0) {
+      const int pv = D.par[nb + v];
+      if (pv < 0 || pv >= n || L >= n) {
+        L = -1;
+        break;
+      }
+      v = pv;
+      ++L;
+    }
+  }
+  *n_edges = L;
+  if (L <= 0 || L > max_edges) return;
+  int v = inc;
+  for (int i = L; i > 0; --i) {
+    const int pv = D.par[nb + v];
+    if (nodes) nodes[i] = v;
+    T[i - 1] = D.eT[nb + v];
+    for (int j = 0; j < 16; ++j) {
+      s0[16L * (i - 1) + j] = D.st[(nb + pv) * 16 + j];
+      s1[16L * (i - 1) + j] = D.st[(nb + v) * 16 + j];
+    }
+    v = pv;
+  }
+  if (nodes) nodes[0] = 0;
+}
+
 // output: the first segment of the incumbent plan (Algorithm 1's return)
 // ---------------------------------------------------------------------------
 __global__ void k_plan_output(PlanDev D) {
@@ -1943,6 +1987,16 @@ extern "C" fn_status fn_planner_get_tree(fn_planner_t* pl, int p, float* states,
   if (J) ok &= cudaMemcpy(J, pl->D.J + nb, sizeof(float) * m, cudaMemcpyDeviceToHost) == cudaSuccess;
   if (nu) ok &= cudaMemcpy(nu, pl->D.nu + nb, sizeof(float) * m, cudaMemcpyDeviceToHost) == cudaSuccess;
   return ok ? FN_OK : FN_ECUDA;
+}
+
+extern "C" fn_status fn_planner_incumbent_path(fn_planner_t* pl, int p, int max_edges,
+                                               float* s0, float* s1, float* T, int32_t* nodes,
+                                               int32_t* n_edges, void* stream) {
+  if (!pl || p < 0 || p >= pl->cfg.P || max_edges < 0 || !n_edges) return FN_EINVAL;
+  if (max_edges > 0 && (!s0 || !s1 || !T)) return FN_EINVAL;
+  if ((s0 && !aligned16(s0)) || (s1 && !aligned16(s1))) return FN_EINVAL;
+  k_plan_path<<<1, 32, 0, (cudaStream_t)stream>>>(pl->D, p, max_edges, s0, s1, T, nodes, n_edges);
+  return launch_status();
 }
 
 extern "C" fn_status fn_planner_get_candidates(fn_planner_t* pl, int p, float* states,

@@ -14,7 +14,8 @@ import torch
 from . import _lib
 from ._lib import FN_MODE_FIXED, FN_MODE_FULL, arm_struct, check, lib
 
-__all__ = ["time_edges", "time_edges_nary", "autotune_time_edges", "rnea_dump", "knn_tree", "knn_workspace_bytes", "make_edges", "EdgeEngine",
+__all__ = ["time_edges", "time_edges_nary", "autotune_time_edges", "check_edges_full",
+           "controller_torque", "rnea_dump", "knn_tree", "knn_workspace_bytes", "make_edges", "EdgeEngine",
            "FN_MODE_FULL", "FN_MODE_FIXED", "version"]
 
 
@@ -121,6 +122,53 @@ def time_edges_nary(arm, s0, s1, T_grid, S, eps, max_rounds=8, T_cap=None, out=N
                                   _ptr(out["rho3"]), _ptr(out["ok"]), _ptr(out.get("rounds")),
                                   _ptr(sample_count), _stream(stream))
     check(st, "fn_time_edges_nary")
+    return out
+
+
+def check_edges_full(arm, s0, s1, T, S, S_clear=64, obs=None, margin=0.02, E_dev=None,
+                     out=None, stream=None):
+    """fn_check_edges_full: the full-resolution recheck of edges at their own
+    durations.  Returns dict(rho3 f32 [E,3], clearance f32 [E], ok u8 [E])."""
+    _states(s0, "s0"); _states(s1, "s1")
+    E = s0.shape[0]
+    A = arm_struct(arm)
+    if out is None:
+        dev = s0.device
+        out = dict(rho3=torch.empty(E, 3, dtype=torch.float32, device=dev),
+                   clearance=torch.empty(E, dtype=torch.float32, device=dev),
+                   ok=torch.empty(E, dtype=torch.uint8, device=dev))
+    ob = np.zeros((0, 4), np.float32) if obs is None else np.ascontiguousarray(
+        np.asarray(obs, np.float32).reshape(-1, 4))
+    st = lib().fn_check_edges_full(C.byref(A), _ptr(s0), _ptr(s1), _ptr(T), E, _ptr(E_dev),
+                                   int(S), int(S_clear), len(ob),
+                                   ob.ctypes.data_as(C.c_void_p) if len(ob) else None,
+                                   float(margin), _ptr(out["rho3"]), _ptr(out["clearance"]),
+                                   _ptr(out["ok"]), _stream(stream))
+    check(st, "fn_check_edges_full")
+    return out
+
+
+def controller_torque(arm, state, goal, T, dt=1e-3, tau_prev=None, tau_rate_max=None, out=None,
+                      stream=None):
+    """fn_controller_torque: one cycle of Eq. (controller) for B instances.
+    Returns dict(tau f32 [B,7], qdd f32 [B,7], flags u8 [B])."""
+    _states(state, "state"); _states(goal, "goal")
+    B = state.shape[0]
+    A = arm_struct(arm)
+    if out is None:
+        dev = state.device
+        out = dict(tau=torch.empty(B, 7, dtype=torch.float32, device=dev),
+                   qdd=torch.empty(B, 7, dtype=torch.float32, device=dev),
+                   flags=torch.empty(B, dtype=torch.uint8, device=dev))
+    rate = None
+    if tau_rate_max is not None:
+        rate = np.ascontiguousarray(np.asarray(tau_rate_max, np.float32).reshape(7))
+    st = lib().fn_controller_torque(C.byref(A), B, _ptr(state), _ptr(goal), _ptr(T),
+                                    _ptr(tau_prev), float(dt),
+                                    None if rate is None else rate.ctypes.data_as(C.c_void_p),
+                                    _ptr(out["tau"]), _ptr(out.get("qdd")),
+                                    _ptr(out.get("flags")), _stream(stream))
+    check(st, "fn_controller_torque")
     return out
 
 

@@ -65,12 +65,14 @@ def _bind():
     L.fn_planner_set_surrogate.argtypes = [vp, vp, i32]
     L.fn_planner_work_counts.argtypes = [vp, vp, i32, i32]
     L.fn_planner_autotune.argtypes = [vp, vp, i32, C.c_uint, i32, vp, vp, vp]
+    L.fn_planner_incumbent_path.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp]
     for n in ("fn_planner_create", "fn_planner_destroy", "fn_planner_reset", "fn_planner_load_tree",
               "fn_planner_set_candidates", "fn_plan_iteration", "fn_planner_capture",
               "fn_plan_replay", "fn_planner_get_tree", "fn_planner_get_candidates",
               "fn_planner_get_parents",
               "fn_planner_sample_count", "fn_planner_phase_ms", "fn_planner_autotune",
-              "fn_planner_kernel_ms", "fn_planner_work_counts", "fn_planner_set_surrogate"):
+              "fn_planner_kernel_ms", "fn_planner_work_counts", "fn_planner_set_surrogate",
+              "fn_planner_incumbent_path"):
         getattr(L, n).restype = i32
     L._planner_bound = True
     return L
@@ -233,6 +235,39 @@ class Planner:
         ms = (C.c_float * 9)()
         check(lib().fn_planner_phase_ms(self.h, ms), "fn_planner_phase_ms")
         return dict(zip(self.PHASES, [float(x) for x in ms]))
+
+    def incumbent_path(self, p, max_edges=64, stream=None):
+        """fn_planner_incumbent_path: the incumbent plan of problem p as edges,
+        root first.  Returns dict(s0, s1 [max_edges,16], T [max_edges],
+        nodes [max_edges+1], n_edges [1]) on the device (stream-ordered; the
+        first n_edges rows are valid when 0 < n_edges <= max_edges)."""
+        dev = torch.device("cuda")
+        m = max(int(max_edges), 1)
+        out = dict(s0=torch.zeros(m, 16, device=dev), s1=torch.zeros(m, 16, device=dev),
+                   T=torch.full((m,), float("nan"), device=dev),
+                   nodes=torch.full((m + 1,), -1, dtype=torch.int32, device=dev),
+                   n_edges=torch.zeros(1, dtype=torch.int32, device=dev))
+        check(lib().fn_planner_incumbent_path(self.h, int(p), int(max_edges),
+                                              C.c_void_p(out["s0"].data_ptr()),
+                                              C.c_void_p(out["s1"].data_ptr()),
+                                              C.c_void_p(out["T"].data_ptr()),
+                                              C.c_void_p(out["nodes"].data_ptr()),
+                                              C.c_void_p(out["n_edges"].data_ptr()),
+                                              self._stream(stream)), "fn_planner_incumbent_path")
+        return out
+
+    def recheck_incumbent(self, arm, p, S=256, S_clear=64, obs=None, margin=0.02, max_edges=64,
+                          stream=None):
+        """The full-resolution recheck of Sec. IV-E on the incumbent plan of
+        problem p: fn_planner_incumbent_path chained into fn_check_edges_full
+        on the device (no host synchronisation between them).  Returns the
+        path dict with rho3, clearance and ok added."""
+        from . import ops
+        path = self.incumbent_path(p, max_edges, stream=stream)
+        res = ops.check_edges_full(arm, path["s0"], path["s1"], path["T"], S, S_clear, obs,
+                                   margin, E_dev=path["n_edges"], stream=stream)
+        path.update(res)
+        return path
 
     def set_surrogate(self, mlp, W=16):
         """fn_planner_set_surrogate: route free edges through the duration
