@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="iteration",
                     choices=["iteration", "surrogate", "batched", "batched-surrogate", "anytime",
-                             "nary"],
+                             "nary", "control"],
                     help="iteration (default, the headline line), or one of the other "
                          "workloads, each printing its own line")
     ap.add_argument("--train-edges", type=int, default=2_000_000)
@@ -615,6 +615,73 @@ def run_nary(args):
     }
 
 
+def run_control(args):
+    """The control side: one cycle of Eq. (controller) for 64 instances (one
+    per problem of a batched planner; latency) and for 65536 (throughput),
+    and the full-resolution recheck (S = 256, S_clear = 64, 5 obstacles) of
+    a 16-edge plan.  The L2 is flushed between timed calls."""
+    import torch
+
+    from paper_2609_22608_gb300 import ops, synth
+    dev = torch.device("cuda")
+    arm = synth.make_arm(0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def timeit(fn):
+        for _ in range(args.warmup):
+            fn()
+        ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return np.array(ms)
+
+    rng = np.random.default_rng(args.seed)
+    rate = np.full(7, 1000.0, np.float32)
+    ctrl = {}
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for B in (64, 65536):
+            x = synth.random_states(arm, B, 11 + B)
+            g = synth.random_states(arm, B, 12 + B)
+            T = rng.uniform(0.1, 1.0, B).astype(np.float32)
+            prev = np.zeros((B, 7), np.float32)
+            d = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (x, g, T, prev)]
+            out = ops.controller_torque(arm, d[0], d[1], d[2], 1e-3, tau_prev=d[3], tau_rate_max=rate)
+            ms = timeit(lambda: ops.controller_torque(arm, d[0], d[1], d[2], 1e-3, tau_prev=d[3],
+                                                      tau_rate_max=rate, out=out))
+            t = float(np.mean(ms))
+            ctrl[str(B)] = {"ms": t, "p99_ms": float(np.percentile(ms, 99)),
+                            "instances_per_s": B / (t / 1e3),
+                            "tflops": B * FLOP_PER_SAMPLE / (t / 1e3) / 1e12}
+        E = 16
+        s0, s1 = synth.random_edges(arm, E, 21)
+        T = rng.uniform(0.4, 1.6, E).astype(np.float32)
+        obs = synth.obstacles(5, 3).astype(np.float32)
+        d0, d1, dT = (torch.from_numpy(a).to(dev) for a in (s0, s1, T))
+        res = ops.check_edges_full(arm, d0, d1, dT, 256, 64, obs, 0.02)
+        ms_rc = timeit(lambda: ops.check_edges_full(arm, d0, d1, dT, 256, 64, obs, 0.02, out=res))
+    t64 = ctrl["64"]["ms"]
+    return {
+        "metric": "controller cycle latency (64 instances) and full-resolution plan recheck ms",
+        "value": t64, "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t64, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded arm, states, edges, obstacles)",
+        "config": {"workload": "Eq. (controller) for 64 and 65536 instances with torque, power "
+                               "and slew clips; recheck of 16 edges at S=256, S_clear=64, "
+                               "5 obstacles", "l2": "flushed between timed calls"},
+        "clocks": clk.summary(),
+        "controller": ctrl,
+        "recheck_16_edges": {"ms": float(np.mean(ms_rc)), "p99_ms": float(np.percentile(ms_rc, 99)),
+                             "torque_evaluations": E * 256},
+    }
+
+
 def _timed_replays(pl, probs, n, stream, first_it=0, between=None):
     import torch
     ms = []
@@ -807,6 +874,9 @@ def main():
         return
     if args.workload == "nary":
         print(json.dumps(run_nary(args)))
+        return
+    if args.workload == "control":
+        print(json.dumps(run_control(args)))
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
