@@ -83,6 +83,13 @@ def lib():
         L.or_check_edges.argtypes = [P(OrArm), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                      C.c_int, C.c_void_p, C.c_int, C.c_double, C.c_void_p,
                                      C.c_void_p, C.c_void_p]
+        L.or_density_z.argtypes = [C.c_void_p, C.c_ulonglong, C.c_int, C.c_int, C.c_int, C.c_void_p]
+        L.or_sample_goals_density.argtypes = [P(OrArm), P(OrProblem), C.c_void_p, C.c_ulonglong,
+                                              C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.or_sample_chord.argtypes = [P(OrArm), C.c_ulonglong, C.c_int, C.c_int, C.c_int, C.c_int,
+                                      C.c_double, C.c_void_p, C.c_void_p, C.c_int, C.c_float,
+                                      C.c_double, C.c_void_p]
         L.or_rho_batch.argtypes = [P(OrArm), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                    C.c_void_p]
         L.or_torque_dump.argtypes = [P(OrArm), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -262,6 +269,60 @@ def check_edges(arm, s0, s1, T, S, S_clear, obs, margin):
                          _p(ob) if len(ob) else None, len(ob), float(margin), _p(r3), _p(cl),
                          _p(ok))
     return dict(rho3=r3, clearance=cl, ok=ok)
+
+
+class OrDensity(C.Structure):
+    _fields_ = [("C", C.c_int), ("w_u", C.c_float), ("pi", C.c_float * 4),
+                ("mu", (C.c_float * 9) * 4), ("sd", (C.c_float * 9) * 4)]
+
+
+def density_struct(theta):
+    """OrDensity from dict(C, w_u, pi [C], mu [C][9], sd [C][9])."""
+    d = OrDensity()
+    d.C = int(theta["C"])
+    d.w_u = float(theta["w_u"])
+    for c in range(d.C):
+        d.pi[c] = float(theta["pi"][c])
+        for i in range(9):
+            d.mu[c][i] = float(theta["mu"][c][i])
+            d.sd[c][i] = float(theta["sd"][c][i])
+    return d
+
+
+def density_z(theta, seed, index, it, problem):
+    d = density_struct(theta)
+    z = np.zeros(9)
+    lib().or_density_z(C.byref(d), seed, index, it, problem, _p(z))
+    return z
+
+
+def sample_goals_density(arm, pr, theta, seed, it, problem, first, n):
+    """Goal candidates drawn from p_theta and decoded: (states, T_req, v_rel,
+    valid, z)."""
+    A = arm_struct(arm)
+    Pr = problem_struct(pr)
+    d = density_struct(theta)
+    st = np.zeros((n, 16))
+    Tq = np.zeros(n)
+    vr = np.zeros(n)
+    valid = np.zeros(n, np.int32)
+    zs = np.zeros((n, 9))
+    lib().or_sample_goals_density(C.byref(A), C.byref(Pr), C.byref(d), seed, it, problem, first, n,
+                                  _p(st), _p(Tq), _p(vr), _p(valid), _p(zs))
+    return st, Tq, vr, valid, zs
+
+
+def sample_chord(arm, seed, it, problem, first, n, vel_frac, q0, goals, w_chord, sigma):
+    """Free candidates of the chord sampler; goals [n_goals][16] in candidate
+    order."""
+    A = arm_struct(arm)
+    q0 = _d(q0)
+    g = np.ascontiguousarray(np.asarray(goals, np.float64).reshape(-1, 16))
+    st = np.zeros((n, 16))
+    lib().or_sample_chord(C.byref(A), seed, it, problem, first, n, float(vel_frac), _p(q0),
+                          _p(g) if len(g) else None, len(g), float(np.float32(w_chord)),
+                          float(sigma), _p(st))
+    return st
 
 
 def rho_batch(arm, s0, s1, T, S):

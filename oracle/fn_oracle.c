@@ -996,3 +996,113 @@ void or_check_edges(const or_arm* arm, int E, const float* s0, const float* s1, 
     ok[e] = (r3[0] <= 1.0 && r3[1] <= 1.0 && r3[2] <= 1.0 && (n_obs == 0 || c >= margin)) ? 1 : 0;
   }
 }
+
+/* ------------------------------------------------------------------------
+ * Sampling densities of Sec. IV-E ("Batched expansion").
+ * Goal parameters come from p_theta, a Gaussian mixture over the chart's
+ * parameter cube Z = [0, 1]^9 mixed with a uniform component; free states
+ * are Gaussian perturbations of points on the joint-space chord from the
+ * root to a decoded goal of the same round, mixed with uniform draws.
+ * Readings:
+ *   - diagonal covariances, at most 4 components; the uniform weight w_u
+ *     is fixed, the mixture is refit (or_em in oracle/density.py);
+ *   - a Gaussian draw is folded back into Z: the three angle parameters
+ *     (z2, z3, z4) wrap modulo 1, the others reflect at 0 and 1;
+ *   - normals by Box-Muller from the candidate's own Philox uniforms;
+ *   - the integer decisions (uniform component or not, which component,
+ *     chord or uniform, which goal) are taken in single precision from the
+ *     exactly representable uniforms, as on the GPU;
+ *   - chord point: q0 + lambda (q_g - q0) + sigma * half-range * n, clamped
+ *     to the joint box; the velocity is drawn as for a uniform candidate.
+ * Philox streams of candidate (seed, index, iter, problem): 0-3 uniform free
+ * state, 4 chord decisions (choice, goal, lambda), 5-6 chord normals, 8-10
+ * chart parameters, 11 mixture decision, 12-14 mixture normals. */
+static int z_angle(int i) { return i == 2 || i == 3 || i == 4; }
+
+static double z_fold(int i, double z) {
+  if (z_angle(i)) return z - floor(z);
+  double t = z - 2.0 * floor(0.5 * z);
+  return t <= 1.0 ? t : 2.0 - t;
+}
+
+static void box_muller(double ua, double ub, double* n0, double* n1) {
+  double r = sqrt(-2.0 * log(1.0 - ua));
+  *n0 = r * cos(2.0 * M_PI * ub);
+  *n1 = r * sin(2.0 * M_PI * ub);
+}
+
+void or_density_z(const or_density* th, unsigned long long seed, int index, int iter, int problem,
+                  double* z) {
+  double u[12];
+  for (int s = 0; s < 3; ++s) philox_uniforms(seed, index, iter, problem, 8 + s, u + 4 * s);
+  for (int i = 0; i < 9; ++i) z[i] = u[i];
+  if (th == NULL || th->C <= 0) return;
+  double us[4];
+  philox_uniforms(seed, index, iter, problem, 11, us);
+  float sel = (float)us[0];
+  if (sel < th->w_u) return;                       /* the uniform component */
+  float v = (sel - th->w_u) / (1.0f - th->w_u);
+  int m = th->C - 1;
+  float acc = 0.0f;
+  for (int c = 0; c < th->C; ++c) {
+    acc += th->pi[c];
+    if (v < acc) { m = c; break; }
+  }
+  double un[12], nrm[10];
+  for (int s = 0; s < 3; ++s) philox_uniforms(seed, index, iter, problem, 12 + s, un + 4 * s);
+  for (int k = 0; k < 5; ++k) box_muller(un[2 * k], un[2 * k + 1], &nrm[2 * k], &nrm[2 * k + 1]);
+  for (int i = 0; i < 9; ++i)
+    z[i] = z_fold(i, (double)th->mu[m][i] + (double)th->sd[m][i] * nrm[i]);
+}
+
+void or_sample_goals_density(const or_arm* arm, const or_problem* pr, const or_density* th,
+                             unsigned long long seed, int iter, int problem, int first_index,
+                             int n, double* states, double* T_req, double* vrel, int* valid,
+                             double* zs) {
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int c = 0; c < n; ++c) {
+    double z[9], vb[3];
+    or_density_z(th, seed, first_index + c, iter, problem, z);
+    if (zs)
+      for (int i = 0; i < 9; ++i) zs[9 * (size_t)c + i] = z[i];
+    valid[c] = or_goal_chart(arm, pr, z, states + 16 * (size_t)c, &T_req[c], &vrel[c], vb);
+    if (!valid[c])
+      for (int i = 0; i < 16; ++i) states[16 * (size_t)c + i] = 0.0;
+  }
+}
+
+void or_sample_chord(const or_arm* arm, unsigned long long seed, int iter, int problem,
+                     int first_index, int n, double vel_frac, const double* q0,
+                     const double* goals, int n_goals, float w_chord, double sigma,
+                     double* states) {
+  for (int c = 0; c < n; ++c) {
+    const int index = first_index + c;
+    double u[16], uc[4];
+    for (int s = 0; s < 4; ++s) philox_uniforms(seed, index, iter, problem, s, u + 4 * s);
+    philox_uniforms(seed, index, iter, problem, 4, uc);
+    double* st = states + 16 * (size_t)c;
+    for (int i = 0; i < 16; ++i) st[i] = 0.0;
+    int chord = n_goals > 0 && (float)uc[0] < w_chord;
+    int g = 0;
+    double nrm[8];
+    if (chord) {
+      g = (int)floorf((float)uc[1] * (float)n_goals);
+      if (g > n_goals - 1) g = n_goals - 1;
+      double un[8];
+      for (int s = 0; s < 2; ++s) philox_uniforms(seed, index, iter, problem, 5 + s, un + 4 * s);
+      for (int k = 0; k < 4; ++k) box_muller(un[2 * k], un[2 * k + 1], &nrm[2 * k], &nrm[2 * k + 1]);
+    }
+    for (int j = 0; j < 7; ++j) {
+      double lo = arm->q_lo[j], hi = arm->q_hi[j], qj;
+      if (chord) {
+        const double qg = goals[16 * (size_t)g + j];
+        qj = q0[j] + uc[2] * (qg - q0[j]) + sigma * 0.5 * (hi - lo) * nrm[j];
+        qj = qj < lo ? lo : (qj > hi ? hi : qj);
+      } else {
+        qj = lo + u[j] * (hi - lo);
+      }
+      st[j] = qj;
+      st[8 + j] = (2.0 * u[7 + j] - 1.0) * vel_frac * or_taper(arm, j, qj);
+    }
+  }
+}

@@ -18,6 +18,7 @@
  *   arrival-time pruning .. Eq. (reach)
  *   tracking controller ... Eq. (controller) with the torque, power and slew clips
  *   plan recheck .......... Sec. IV-E (the plan sent to the controller, full resolution)
+ *   sampling densities .... Sec. IV-E "Batched expansion" (p_theta, chord sampler)
  * Readings of passages that the paper leaves open are listed beside each
  * function in fn_oracle.c.
  */
@@ -153,6 +154,33 @@ void or_controller_torque(const or_arm* arm, int B, const float* state, const fl
 void or_check_edges(const or_arm* arm, int E, const float* s0, const float* s1, const float* T,
                     int S, int S_clear, const float* obs, int n_obs, double margin, double* rho3,
                     double* clearance, unsigned char* ok);
+
+/* The goal density p_theta: C (<= 4) diagonal Gaussians over Z = [0, 1]^9
+ * with weights pi (summing to 1) mixed with the uniform component of weight
+ * w_u; single-precision parameters, as the planner keeps them. */
+typedef struct {
+  int C;
+  float w_u;
+  float pi[4];
+  float mu[4][9];
+  float sd[4][9];
+} or_density;
+
+/* chart parameters z [9] of goal candidate (seed, index, iter, problem) */
+void or_density_z(const or_density* th, unsigned long long seed, int index, int iter, int problem,
+                  double* z);
+/* goal candidates drawn from p_theta and decoded (as or_sample_goals; zs
+ * [n][9] may be NULL) */
+void or_sample_goals_density(const or_arm* arm, const or_problem* pr, const or_density* th,
+                             unsigned long long seed, int iter, int problem, int first_index,
+                             int n, double* states, double* T_req, double* vrel, int* valid,
+                             double* zs);
+/* free candidates from the chord sampler: goals [n_goals][16] are the
+ * round's valid decoded goals in candidate order, q0 [7] the root */
+void or_sample_chord(const or_arm* arm, unsigned long long seed, int iter, int problem,
+                     int first_index, int n, double vel_frac, const double* q0,
+                     const double* goals, int n_goals, float w_chord, double sigma,
+                     double* states);
 
 #ifdef __cplusplus
 }
