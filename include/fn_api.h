@@ -430,6 +430,11 @@ fn_status fn_planner_set_candidates(fn_planner_t* pl, int p, const float* states
 
 #define FN_PLAN_EXTERNAL 1u /* use the candidates given by fn_planner_set_candidates */
 #define FN_PLAN_PRUNE 2u    /* prune the trees after the round (Eq. (reach))          */
+#define FN_PLAN_DENSITY 4u  /* goal parameters drawn from p_theta (else uniform); the
+                               best-plans archive is updated after the round        */
+#define FN_PLAN_CHORD 8u    /* free candidates from the chord sampler (else uniform) */
+#define FN_PLAN_REFIT 16u   /* update the archive and refit p_theta to it after the
+                               round (the last round of an anytime iteration)       */
 
 /*
  * fn_plan_iteration -- one round of Algorithm 1 for all P problems:
@@ -512,6 +517,85 @@ fn_status fn_planner_work_counts(fn_planner_t* pl, unsigned long long* count, in
  * Synchronous. */
 fn_status fn_planner_get_tree(fn_planner_t* pl, int p, float* states, float* t,
                               int32_t* parent, float* J, float* nu, int* n, int cap);
+/*
+ * The sampling densities of Sec. IV-E ("Batched expansion").
+ *
+ * p_theta: goal parameters z in the chart's cube [0, 1]^9 come from a
+ * Gaussian mixture (C <= FN_DENSITY_MAX_C diagonal components) mixed with a
+ * uniform component of weight w_u.  A Gaussian draw is folded back into the
+ * cube (the angle parameters z2, z3, z4 wrap modulo 1, the others reflect
+ * at 0 and 1).  p_theta is kept per problem on the device; fn_planner_reset
+ * does not clear it (it persists across planning cycles).  C = 0 draws every
+ * z uniformly, exactly as without FN_PLAN_DENSITY.
+ *
+ * Best-plans archive: per problem, the FN_ARCHIVE_MAX (at most n_fit) best
+ * (J, z) of the rendezvous nodes attached since the last reset, best first
+ * (an earlier plan wins a tie).  It is updated after every round run with
+ * FN_PLAN_DENSITY or FN_PLAN_REFIT, from the new nodes whose z is known
+ * (device-drawn goals, or external ones given fn_planner_set_candidate_params).
+ *
+ * Refit (FN_PLAN_REFIT): em_iters EM iterations with diagonal covariances
+ * on the archive's z, starting from the current mixture (or, the first
+ * time, from the min(C, n) best z with deviation sd_init and equal weights);
+ * sd_floor^2 is added to every variance; a component whose responsibility
+ * sum falls below 1e-4 keeps its mean and deviation.  w_u is set from the
+ * configuration, not fit.
+ *
+ * Chord sampler (FN_PLAN_CHORD): a free candidate is, with probability
+ * w_chord and if the round decoded any valid goal, the point
+ * q0 + lambda (q_g - q0) + chord_sigma * half-range * n on the chord from the
+ * root q0 to a goal q_g of the round chosen uniformly (lambda uniform, n
+ * standard normal), clamped to the joint box; otherwise a uniform draw.
+ * Its velocity is drawn as for a uniform candidate.
+ */
+#define FN_DENSITY_MAX_C 4
+#define FN_ARCHIVE_MAX 64
+
+typedef struct {
+  int C;                          /* Gaussian components (0: uniform only)   */
+  float w_u;                      /* weight of the uniform component         */
+  float pi[FN_DENSITY_MAX_C];     /* component weights (sum 1)               */
+  float mu[FN_DENSITY_MAX_C][9];  /* means over the chart parameters         */
+  float sd[FN_DENSITY_MAX_C][9];  /* standard deviations (> 0)               */
+} fn_density_t;
+
+typedef struct {
+  float w_u;          /* uniform weight of p_theta (default 0.25)             */
+  int C;              /* components of a refit, 1..4 (4)                       */
+  int n_fit;          /* archive size, 1..FN_ARCHIVE_MAX (32)                  */
+  int em_iters;       /* EM iterations per refit, 1..64 (8)                    */
+  float sd_floor;     /* added in quadrature to every deviation (0.02)         */
+  float sd_init;      /* deviation of a first fit's components (0.1)           */
+  float w_chord;      /* probability of a chord draw for a free candidate (0.5) */
+  float chord_sigma;  /* chord spread, fraction of the joint half-range (0.1)  */
+} fn_sampler_cfg_t;
+
+/* Set the sampling configuration (before fn_planner_capture: a captured
+ * iteration keeps the configuration it was captured with). */
+fn_status fn_planner_set_sampler(fn_planner_t* pl, const fn_sampler_cfg_t* cfg);
+
+/* Set problem p's p_theta (host struct; validated: 0 <= C <= 4,
+ * 0 <= w_u <= 1, pi >= 0 summing to 1 within 1e-3, sd > 0, finite). */
+fn_status fn_planner_set_density(fn_planner_t* pl, int p, const fn_density_t* theta,
+                                 void* stream);
+
+/* Read problem p's p_theta and best-plans archive (host outputs, any may be
+ * NULL: archive_J [FN_ARCHIVE_MAX], archive_z [FN_ARCHIVE_MAX][9],
+ * archive_n).  Synchronises the device. */
+fn_status fn_planner_get_density(fn_planner_t* pl, int p, fn_density_t* theta,
+                                 float* archive_J, float* archive_z, int* archive_n);
+
+/* Chart parameters z (host [n_goal][9]) of the external goal candidates
+ * given by fn_planner_set_candidates (call after it), so that their plans
+ * can enter the archive; without it their z is unknown (NaN). */
+fn_status fn_planner_set_candidate_params(fn_planner_t* pl, int p, const float* z, int n_goal,
+                                          void* stream);
+
+/* Read the chart parameters of problem p's first n candidate slots (host
+ * [n][9]; NaN where unknown: free slots, external goals without parameters).
+ * Synchronises the device. */
+fn_status fn_planner_get_candidate_params(fn_planner_t* pl, int p, float* z, int n);
+
 /*
  * fn_planner_incumbent_path -- the incumbent plan of problem p as a list of
  * edges, root first: edge i runs from node nodes[i] to nodes[i + 1] with the

@@ -43,8 +43,17 @@
 #define PL_MAX_KEV 40                         // launches traced per iteration
 #define PL_NCOUNT 7   // work counters: probe, verify, mid-probe, kNN pairs, IK starts,
                       // surrogate-routed edges, surrogate rescans
+#define PL_CHORD_THREADS 1024  // block_scan spans 32 warps
 
 namespace fn {
+
+// best plans of a problem's tree: (J, z) best first, at most n_fit entries
+struct Archive {
+  int n;
+  int pad[3];
+  float J[FN_ARCHIVE_MAX];
+  float z[FN_ARCHIVE_MAX][9];
+};
 
 struct Incumbent {
   int id;
@@ -129,6 +138,13 @@ struct PlanDev {  // device pointers, passed by value to the kernels
   int sur;
   int32_t* sur_list;  // [E]
   int* sur_n;         // [1]
+  // sampling densities (Sec. IV-E, batched expansion)
+  fn_density_t* dens; // [P] goal density p_theta (kept across resets)
+  struct Archive* arch;  // [P] best plans of the current tree
+  float* cz;          // [P][BM][9] chart parameters of the goal candidates (NaN: unknown)
+  float* zn;          // [P][NC][9] chart parameters of goal nodes, written at attach
+  int32_t* glist;     // [P][BM] the round's valid goal candidates, in order
+  fn_sampler_cfg_t scfg;
   // parents: node mirror laid out for lane-contiguous loads (see knn_mirror_index)
   float4* mir;        // [P][NB][7][32]
   int32_t* packed;    // [P] leading nodes whose mirror entries are current
@@ -173,6 +189,7 @@ __global__ void k_plan_reset(PlanDev D) {
   D.packed[p] = 0;
   D.inc[p] = Incumbent{-1, -INFINITY, P.t_fall, 0};
   D.status[p] = 0;
+  D.arch[p].n = 0;
 }
 
 __global__ void k_plan_loaded(PlanDev D, int p, int n) {
@@ -188,6 +205,7 @@ __global__ void k_plan_loaded(PlanDev D, int p, int n) {
     D.packed[p] = 0;
     D.inc[p] = Incumbent{-1, -INFINITY, D.prob[p].t_fall, 0};
     D.status[p] = 0;
+    D.arch[p].n = 0;
   }
 }
 
@@ -246,6 +264,52 @@ __device__ __forceinline__ int find_problem(const int* off, int P, int x) {
 // ---------------------------------------------------------------------------
 // samplers
 // ---------------------------------------------------------------------------
+// Gaussian draws folded back into the chart's cube: the angle parameters
+// (z2, z3, z4) wrap modulo 1, the others reflect at 0 and 1
+__device__ __forceinline__ float z_fold(int i, float z) {
+  if (i == 2 || i == 3 || i == 4) return z - floorf(z);
+  const float t = z - 2.f * floorf(0.5f * z);
+  return t <= 1.f ? t : 2.f - t;
+}
+
+// two standard normals from two uniforms in [0, 1) (Box-Muller)
+__device__ __forceinline__ void box_muller(float ua, float ub, float& n0, float& n1) {
+  const float r = sqrtf(-2.f * logf(1.f - ua));
+  float sn, cs;
+  sincospif(2.f * ub, &sn, &cs);
+  n0 = r * cs;
+  n1 = r * sn;
+}
+
+// Goal parameters from p_theta: z holds the candidate's uniform draw (the
+// uniform component); with probability 1 - w_u a Gaussian component, chosen
+// by its weight, replaces it.  The choices are taken in single precision on
+// exactly representable uniforms (Philox streams 11-14 of the candidate).
+__device__ __forceinline__ void density_z(const fn_density_t& th, unsigned long long seed, int b,
+                                          int it, int p, float* z) {
+  if (th.C <= 0) return;
+  float us[4];
+  philox_u4(seed, b, it, p, 11, us);
+  if (us[0] < th.w_u) return;
+  const float v = (us[0] - th.w_u) / (1.f - th.w_u);
+  int m = th.C - 1;
+  float acc = 0.f;
+  for (int c = 0; c < th.C; ++c) {
+    acc += th.pi[c];
+    if (v < acc) {
+      m = c;
+      break;
+    }
+  }
+  float un[12], nrm[10];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) philox_u4(seed, b, it, p, 12 + s, un + 4 * s);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) box_muller(un[2 * k], un[2 * k + 1], nrm[2 * k], nrm[2 * k + 1]);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) z[i] = z_fold(i, fmaf(th.sd[m][i], nrm[i], th.mu[m][i]));
+}
+
 // Free candidate (p, b): uniform in the box, |qd| <= vel_frac qdbar.
 __device__ __forceinline__ void sample_free(const PlanDev& D, const ArmK& A, int p, int b) {
   const fn_problem_t& P = D.prob[p];
@@ -281,7 +345,7 @@ __device__ __forceinline__ void parents_prep(const PlanDev& D, long i, long stri
 // free slot is drawn by lane 0.  The warps past the slots prepare the parent
 // search (parents_prep), which reads nothing the samplers write.
 __global__ void __launch_bounds__(128) k_plan_sample(PlanDev D, ArmK A, long nslots,
-                                                     int prep_warps) {
+                                                     int prep_warps, int dens) {
   pdl_begin();
   const long gid = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31, grp = lane >> 3;
@@ -305,6 +369,10 @@ __global__ void __launch_bounds__(128) k_plan_sample(PlanDev D, ArmK A, long nsl
   for (int s = 0; s < 3; ++s) philox_u4(P.seed, b, it, p, 8 + s, u + 4 * s);
 #pragma unroll
   for (int i = 0; i < 9; ++i) z[i] = u[i];
+  if (dens) density_z(D.dens[p], P.seed, b, it, p, z);
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+    if (lane == i) D.cz[ci * 9 + i] = z[i];
   ChartPose o;
   const bool defined = chart_pose(A, P, z, o);        // warp-uniform
   int winner = -1;
@@ -1147,6 +1215,60 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_vseq(PlanDev 
   if (D.samples && lane == 0 && nsamp) atomicAdd(D.samples + 1, (unsigned long long)nsamp);
 }
 
+// Chord sampler (FN_PLAN_CHORD), one block per problem after the sampling
+// launch: the round's valid goals in candidate order, then every free
+// candidate whose chord draw succeeds (probability w_chord) is replaced by
+// q0 + lambda (q_g - q0) + chord_sigma * half-range * n (clamped to the box)
+// toward a goal chosen uniformly; its velocity as for a uniform draw.  Philox
+// streams: 0-3 as the uniform draw, 4 (choice, goal, lambda), 5-6 normals.
+__global__ void __launch_bounds__(PL_CHORD_THREADS) k_plan_chord(PlanDev D, ArmK A) {
+  pdl_begin();
+  __shared__ int sh[32];
+  const int p = blockIdx.x;
+  const fn_problem_t& P = D.prob[p];
+  const int B = min(max(P.batch, 0), D.BM);
+  const int G = min(max(P.n_goal, 0), B);
+  const long cb = (long)p * D.BM;
+  const int per = (G + blockDim.x - 1) / blockDim.x;
+  const int c0 = min(G, threadIdx.x * per), c1 = min(G, c0 + per);
+  int cnt = 0;
+  for (int b = c0; b < c1; ++b) cnt += D.valid[cb + b] ? 1 : 0;
+  int nv;
+  int r = block_scan(cnt, sh, &nv);
+  for (int b = c0; b < c1; ++b)
+    if (D.valid[cb + b]) D.glist[cb + r++] = b;
+  __syncthreads();
+  if (nv == 0) return;                 // the free candidates keep their uniform draws
+  const int it = *D.iter;
+  for (int b = G + threadIdx.x; b < B; b += blockDim.x) {
+    float uc[4];
+    philox_u4(P.seed, b, it, p, 4, uc);
+    if (!(uc[0] < D.scfg.w_chord)) continue;
+    const int g = min((int)floorf(uc[1] * (float)nv), nv - 1);
+    const float* qg = D.cand + (cb + D.glist[cb + g]) * 16;
+    float u[16], un[8], nrm[8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) philox_u4(P.seed, b, it, p, k, u + 4 * k);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) philox_u4(P.seed, b, it, p, 5 + k, un + 4 * k);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) box_muller(un[2 * k], un[2 * k + 1], nrm[2 * k], nrm[2 * k + 1]);
+    float q[7], qd[7];
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      const float lo = A.q_lo[j], hi = A.q_hi[j];
+      const float x = P.q0[j] + uc[2] * (qg[j] - P.q0[j]) + D.scfg.chord_sigma * 0.5f * (hi - lo) * nrm[j];
+      q[j] = fminf(fmaxf(x, lo), hi);
+      qd[j] = fmaf(2.f, u[7 + j], -1.f) * (D.vel_frac * taper(A, j, q[j]));
+    }
+    float4* o4 = reinterpret_cast<float4*>(D.cand + (cb + b) * 16);
+    o4[0] = make_float4(q[0], q[1], q[2], q[3]);
+    o4[1] = make_float4(q[4], q[5], q[6], 0.f);
+    o4[2] = make_float4(qd[0], qd[1], qd[2], qd[3]);
+    o4[3] = make_float4(qd[4], qd[5], qd[6], 0.f);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // attach + score + incumbent: one block per problem
 // ---------------------------------------------------------------------------
@@ -1213,6 +1335,9 @@ __global__ void __launch_bounds__(PL_ATTACH_THREADS) k_plan_attach(PlanDev D) {
       if (Jv > bestJ || (Jv == bestJ && node < bestI)) { bestJ = Jv; bestI = node; }
     }
     D.J[nd] = Jv;
+    if (b < G)
+#pragma unroll
+      for (int i = 0; i < 9; ++i) D.zn[nd * 9 + i] = D.cz[ci * 9 + i];
   }
   // incumbent: argmax J over the new rendezvous nodes (ties: lower id),
   // replacing the current one only if strictly better
@@ -1241,6 +1366,131 @@ __global__ void __launch_bounds__(PL_ATTACH_THREADS) k_plan_attach(PlanDev D) {
       in.t_best = D.t[nb + sI[0]];
       D.inc[p] = in;
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// goal density (FN_PLAN_DENSITY / FN_PLAN_REFIT): one block per problem after
+// attach.  Thread 0 inserts the round's new rendezvous nodes whose chart
+// parameters are known into the best-plans archive (best J first, a new
+// entry after equal ones, at most n_fit); with `refit`, p_theta is refit to
+// the archive by EM with diagonal covariances (E-step: thread per plan;
+// M-step: thread per (component, parameter)).
+// ---------------------------------------------------------------------------
+#define PL_DENSITY_THREADS 64   // >= FN_ARCHIVE_MAX and >= 9 * FN_DENSITY_MAX_C
+
+__global__ void __launch_bounds__(PL_DENSITY_THREADS) k_plan_density(PlanDev D, int refit) {
+  pdl_begin();
+  __shared__ float sz[FN_ARCHIVE_MAX][9];
+  __shared__ float sr[FN_ARCHIVE_MAX][FN_DENSITY_MAX_C];
+  __shared__ fn_density_t th;
+  __shared__ int sn;
+  const int p = blockIdx.x;
+  const int t = threadIdx.x;
+  Archive& ar = D.arch[p];
+  if (t == 0) {
+    const int N1 = D.n_nodes[p], add = D.added[p];
+    const long nb = (long)p * D.NC;
+    const int cap = min(max(D.scfg.n_fit, 1), FN_ARCHIVE_MAX);
+    int n = min(max(ar.n, 0), cap);
+    for (int nd = max(N1 - add, 0); nd < N1; ++nd) {
+      const float J = D.J[nb + nd];
+      const float* z = D.zn + (nb + nd) * 9;
+      bool known = isfinite(J);
+      for (int i = 0; i < 9; ++i) known = known && isfinite(z[i]);
+      if (!known) continue;
+      int pos = n;
+      for (int i = 0; i < n; ++i)
+        if (J > ar.J[i]) {
+          pos = i;
+          break;
+        }
+      if (pos >= cap) continue;
+      for (int i = min(n, cap - 1); i > pos; --i) {
+        ar.J[i] = ar.J[i - 1];
+        for (int k = 0; k < 9; ++k) ar.z[i][k] = ar.z[i - 1][k];
+      }
+      ar.J[pos] = J;
+      for (int k = 0; k < 9; ++k) ar.z[pos][k] = z[k];
+      n = min(n + 1, cap);
+    }
+    ar.n = n;
+    sn = n;
+    th = D.dens[p];
+    if (refit && n > 0 && th.C <= 0) {       // first fit: the best min(C, n) plans
+      const int C = min(max(D.scfg.C, 1), min(n, FN_DENSITY_MAX_C));
+      th.C = C;
+      for (int m = 0; m < C; ++m) {
+        th.pi[m] = 1.f / (float)C;
+        for (int k = 0; k < 9; ++k) {
+          th.mu[m][k] = ar.z[m][k];
+          th.sd[m][k] = D.scfg.sd_init;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const int n = sn;
+  if (!refit || n == 0) return;
+  if (t < n)
+    for (int k = 0; k < 9; ++k) sz[t][k] = ar.z[t][k];
+  __syncthreads();
+  const int C = th.C;
+  const float floor2 = D.scfg.sd_floor * D.scfg.sd_floor;
+  for (int itn = 0; itn < D.scfg.em_iters; ++itn) {
+    if (t < n) {                              // E-step: responsibilities of plan t
+      float lp[FN_DENSITY_MAX_C], top = -INFINITY;
+      for (int m = 0; m < C; ++m) {
+        float a = th.pi[m] > 0.f ? logf(th.pi[m]) : -INFINITY;
+        for (int k = 0; k < 9; ++k) {
+          const float d = (sz[t][k] - th.mu[m][k]) / th.sd[m][k];
+          a -= 0.5f * d * d + logf(th.sd[m][k]);
+        }
+        lp[m] = a;
+        top = fmaxf(top, a);
+      }
+      float sum = 0.f;
+      for (int m = 0; m < C; ++m) {
+        lp[m] = expf(lp[m] - top);
+        sum += lp[m];
+      }
+      for (int m = 0; m < C; ++m) sr[t][m] = lp[m] / sum;
+    }
+    __syncthreads();
+    float mu = 0.f, sd = 0.f, pw = 0.f;
+    bool upd = false;
+    const int m = t / 9, k = t - 9 * (t / 9);
+    if (t < 9 * C) {                          // M-step: component m, parameter k
+      float Nm = 0.f, s1 = 0.f;
+      for (int i = 0; i < n; ++i) {
+        Nm += sr[i][m];
+        s1 += sr[i][m] * sz[i][k];
+      }
+      pw = Nm / (float)n;
+      if (Nm >= 1e-4f) {
+        mu = s1 / Nm;
+        float s2 = 0.f;
+        for (int i = 0; i < n; ++i) {
+          const float d = sz[i][k] - mu;
+          s2 += sr[i][m] * d * d;
+        }
+        sd = sqrtf(s2 / Nm + floor2);
+        upd = true;
+      }
+    }
+    __syncthreads();
+    if (t < 9 * C) {
+      if (k == 0) th.pi[m] = pw;
+      if (upd) {
+        th.mu[m][k] = mu;
+        th.sd[m][k] = sd;
+      }
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    th.w_u = D.scfg.w_u;
+    D.dens[p] = th;
   }
 }
 
@@ -1592,8 +1842,12 @@ static void enqueue_front(fn_planner* pl, unsigned flags, cudaStream_t st, Mark&
     const int prep = pl->cfg.k > 1 ? 4 * num_sms() : 0;
     if (n + prep > 0) {
       pl_launch(k_plan_sample, (unsigned)((32 * (n + prep) + 127) / 128), 128, 0, st, D, pl->arm,
-                n, prep);
+                n, prep, (flags & FN_PLAN_DENSITY) ? 1 : 0);
       trace(pl, st, "k_plan_sample");
+    }
+    if (n > 0 && (flags & FN_PLAN_CHORD)) {
+      pl_launch(k_plan_chord, P, PL_CHORD_THREADS, 0, st, D, pl->arm);
+      trace(pl, st, "k_plan_chord");
     }
   }
   mark(2);
@@ -1667,6 +1921,19 @@ extern "C" fn_status fn_planner_destroy(fn_planner_t* pl) {
   return FN_OK;
 }
 
+static fn_sampler_cfg_t default_sampler_cfg() {
+  fn_sampler_cfg_t c;
+  c.w_u = 0.25f;
+  c.C = 4;
+  c.n_fit = 32;
+  c.em_iters = 8;
+  c.sd_floor = 0.02f;
+  c.sd_init = 0.1f;
+  c.w_chord = 0.5f;
+  c.chord_sigma = 0.1f;
+  return c;
+}
+
 extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm_t* arm,
                                        fn_planner_t** out) {
   if (!cfg || !arm || !out) return FN_EINVAL;
@@ -1731,6 +1998,20 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
   D.sur_list = nullptr;
   A_(D.sur_n, 1);
   A_(D.knn_cnt, P * BM);
+  A_(D.dens, P); A_(D.arch, P); A_(D.cz, P * BM * 9); A_(D.zn, P * NC * 9); A_(D.glist, P * BM);
+  D.scfg = default_sampler_cfg();
+  if (rc == FN_OK) {
+    std::vector<fn_density_t> th(P);
+    for (auto& x : th) {
+      memset(&x, 0, sizeof(x));
+      x.w_u = D.scfg.w_u;
+    }
+    if (cudaMemcpy(D.dens, th.data(), sizeof(fn_density_t) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(D.arch, 0, sizeof(Archive) * P) != cudaSuccess ||
+        cudaMemset(D.cz, 0xff, sizeof(float) * P * BM * 9) != cudaSuccess ||
+        cudaMemset(D.zn, 0xff, sizeof(float) * P * NC * 9) != cudaSuccess)
+      rc = FN_ECUDA;
+  }
   if (rc == FN_OK && cudaMemset(D.knn_cnt, 0, sizeof(int32_t) * P * BM) != cudaSuccess) rc = FN_ECUDA;
   if (rc == FN_OK && cudaMemset(D.packed, 0, sizeof(int32_t) * P) != cudaSuccess) rc = FN_ECUDA;
 #undef A_
@@ -1823,6 +2104,8 @@ extern "C" fn_status fn_planner_set_candidates(fn_planner_t* pl, int p, const fl
   const long cb = (long)p * pl->cfg.b_max;
   std::vector<uint8_t> ones(B, 1);
   std::vector<float> nanv(B, NAN);
+  if (B > 0 && cudaMemsetAsync(D.cz + cb * 9, 0xff, sizeof(float) * 9 * B, st) != cudaSuccess)
+    return FN_ECUDA;
   if (B > 0) {
     if (cudaMemcpyAsync(D.cand + cb * 16, states, sizeof(float) * 16 * B, cudaMemcpyHostToDevice,
                         st) != cudaSuccess ||
@@ -1868,6 +2151,10 @@ static fn_status enqueue_iteration(fn_planner* pl, unsigned flags, cudaStream_t 
   mark(6);
   pl_launch(k_plan_attach, P, PL_ATTACH_THREADS, 0, st, D);
   trace(pl, st, "k_plan_attach");
+  if (flags & (FN_PLAN_DENSITY | FN_PLAN_REFIT)) {
+    pl_launch(k_plan_density, P, PL_DENSITY_THREADS, 0, st, D, (flags & FN_PLAN_REFIT) ? 1 : 0);
+    trace(pl, st, "k_plan_density");
+  }
   mark(7);
   if (flags & FN_PLAN_PRUNE) {
     const long nn = (long)P * D.NC;
@@ -1987,6 +2274,80 @@ extern "C" fn_status fn_planner_get_tree(fn_planner_t* pl, int p, float* states,
   if (J) ok &= cudaMemcpy(J, pl->D.J + nb, sizeof(float) * m, cudaMemcpyDeviceToHost) == cudaSuccess;
   if (nu) ok &= cudaMemcpy(nu, pl->D.nu + nb, sizeof(float) * m, cudaMemcpyDeviceToHost) == cudaSuccess;
   return ok ? FN_OK : FN_ECUDA;
+}
+
+extern "C" fn_status fn_planner_set_sampler(fn_planner_t* pl, const fn_sampler_cfg_t* cfg) {
+  if (!pl || !cfg) return FN_EINVAL;
+  const fn_sampler_cfg_t c = *cfg;
+  if (!(c.w_u >= 0.f && c.w_u <= 1.f) || c.C < 1 || c.C > FN_DENSITY_MAX_C || c.n_fit < 1 ||
+      c.n_fit > FN_ARCHIVE_MAX || c.em_iters < 1 || c.em_iters > 64 ||
+      !(c.sd_floor >= 0.f && std::isfinite(c.sd_floor)) ||
+      !(c.sd_init > 0.f && std::isfinite(c.sd_init)) || !(c.w_chord >= 0.f && c.w_chord <= 1.f) ||
+      !(c.chord_sigma >= 0.f && std::isfinite(c.chord_sigma)))
+    return FN_EINVAL;
+  pl->D.scfg = c;
+  return FN_OK;
+}
+
+extern "C" fn_status fn_planner_set_density(fn_planner_t* pl, int p, const fn_density_t* theta,
+                                            void* stream) {
+  if (!pl || !theta || p < 0 || p >= pl->cfg.P) return FN_EINVAL;
+  const fn_density_t& t = *theta;
+  if (t.C < 0 || t.C > FN_DENSITY_MAX_C || !(t.w_u >= 0.f && t.w_u <= 1.f)) return FN_EINVAL;
+  double sum = 0.0;
+  for (int m = 0; m < t.C; ++m) {
+    if (!(t.pi[m] >= 0.f) || !std::isfinite(t.pi[m])) return FN_EINVAL;
+    sum += t.pi[m];
+    for (int k = 0; k < 9; ++k)
+      if (!std::isfinite(t.mu[m][k]) || !(t.sd[m][k] > 0.f) || !std::isfinite(t.sd[m][k]))
+        return FN_EINVAL;
+  }
+  if (t.C > 0 && std::fabs(sum - 1.0) > 1e-3) return FN_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(pl->D.dens + p, theta, sizeof(fn_density_t), cudaMemcpyHostToDevice, st) !=
+      cudaSuccess)
+    return FN_ECUDA;
+  return cudaStreamSynchronize(st) == cudaSuccess ? FN_OK : FN_ECUDA;
+}
+
+extern "C" fn_status fn_planner_get_density(fn_planner_t* pl, int p, fn_density_t* theta,
+                                            float* archive_J, float* archive_z, int* archive_n) {
+  if (!pl || p < 0 || p >= pl->cfg.P) return FN_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return FN_ECUDA;
+  Archive ar;
+  if (theta && cudaMemcpy(theta, pl->D.dens + p, sizeof(fn_density_t), cudaMemcpyDeviceToHost) !=
+                   cudaSuccess)
+    return FN_ECUDA;
+  if (cudaMemcpy(&ar, pl->D.arch + p, sizeof(Archive), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return FN_ECUDA;
+  if (archive_n) *archive_n = ar.n;
+  if (archive_J) memcpy(archive_J, ar.J, sizeof(ar.J));
+  if (archive_z) memcpy(archive_z, ar.z, sizeof(ar.z));
+  return FN_OK;
+}
+
+extern "C" fn_status fn_planner_set_candidate_params(fn_planner_t* pl, int p, const float* z,
+                                                     int n_goal, void* stream) {
+  if (!pl || p < 0 || p >= pl->cfg.P || n_goal < 0 || n_goal > pl->cfg.b_max) return FN_EINVAL;
+  if (n_goal == 0) return FN_OK;
+  if (!z) return FN_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long cb = (long)p * pl->cfg.b_max;
+  if (cudaMemcpyAsync(pl->D.cz + cb * 9, z, sizeof(float) * 9 * n_goal, cudaMemcpyHostToDevice,
+                      st) != cudaSuccess)
+    return FN_ECUDA;
+  return cudaStreamSynchronize(st) == cudaSuccess ? FN_OK : FN_ECUDA;
+}
+
+extern "C" fn_status fn_planner_get_candidate_params(fn_planner_t* pl, int p, float* z, int n) {
+  if (!pl || p < 0 || p >= pl->cfg.P || n < 0 || n > pl->cfg.b_max || (n > 0 && !z))
+    return FN_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return FN_ECUDA;
+  const long cb = (long)p * pl->cfg.b_max;
+  if (n > 0 && cudaMemcpy(z, pl->D.cz + cb * 9, sizeof(float) * 9 * n, cudaMemcpyDeviceToHost) !=
+                   cudaSuccess)
+    return FN_ECUDA;
+  return FN_OK;
 }
 
 extern "C" fn_status fn_planner_incumbent_path(fn_planner_t* pl, int p, int max_edges,

@@ -5,6 +5,7 @@ Argument marshalling only: every step of an iteration runs in libfruitninja.so.
 from __future__ import annotations
 
 import ctypes as C
+import ctypes as _ct
 
 import numpy as np
 import torch
@@ -13,7 +14,43 @@ from ._lib import arm_struct, check, lib
 
 FN_PLAN_EXTERNAL = 1
 FN_PLAN_PRUNE = 2
+FN_PLAN_DENSITY = 4
+FN_PLAN_CHORD = 8
+FN_PLAN_REFIT = 16
+FN_DENSITY_MAX_C = 4
+FN_ARCHIVE_MAX = 64
 FN_MAX_OBS = 8
+
+
+class FnDensity(C.Structure):
+    _fields_ = [("C", C.c_int), ("w_u", C.c_float), ("pi", C.c_float * FN_DENSITY_MAX_C),
+                ("mu", (C.c_float * 9) * FN_DENSITY_MAX_C),
+                ("sd", (C.c_float * 9) * FN_DENSITY_MAX_C)]
+
+
+class FnSamplerCfg(C.Structure):
+    _fields_ = [("w_u", C.c_float), ("C", C.c_int), ("n_fit", C.c_int), ("em_iters", C.c_int),
+                ("sd_floor", C.c_float), ("sd_init", C.c_float), ("w_chord", C.c_float),
+                ("chord_sigma", C.c_float)]
+
+
+def density_to_dict(d: FnDensity) -> dict:
+    Cn = int(d.C)
+    return dict(C=Cn, w_u=float(d.w_u), pi=np.array(d.pi[:Cn], np.float32),
+                mu=np.array([list(d.mu[m]) for m in range(Cn)], np.float32).reshape(Cn, 9),
+                sd=np.array([list(d.sd[m]) for m in range(Cn)], np.float32).reshape(Cn, 9))
+
+
+def density_from_dict(th: dict) -> FnDensity:
+    d = FnDensity()
+    d.C = int(th["C"])
+    d.w_u = float(th["w_u"])
+    for m in range(d.C):
+        d.pi[m] = float(th["pi"][m])
+        for k in range(9):
+            d.mu[m][k] = float(th["mu"][m][k])
+            d.sd[m][k] = float(th["sd"][m][k])
+    return d
 
 
 class FnPlannerCfg(C.Structure):
@@ -66,13 +103,20 @@ def _bind():
     L.fn_planner_work_counts.argtypes = [vp, vp, i32, i32]
     L.fn_planner_autotune.argtypes = [vp, vp, i32, C.c_uint, i32, vp, vp, vp]
     L.fn_planner_incumbent_path.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp]
+    L.fn_planner_set_sampler.argtypes = [vp, C.POINTER(FnSamplerCfg)]
+    L.fn_planner_set_density.argtypes = [vp, i32, C.POINTER(FnDensity), vp]
+    L.fn_planner_get_density.argtypes = [vp, i32, C.POINTER(FnDensity), vp, vp, C.POINTER(C.c_int)]
+    L.fn_planner_set_candidate_params.argtypes = [vp, i32, vp, i32, vp]
+    L.fn_planner_get_candidate_params.argtypes = [vp, i32, vp, i32]
     for n in ("fn_planner_create", "fn_planner_destroy", "fn_planner_reset", "fn_planner_load_tree",
               "fn_planner_set_candidates", "fn_plan_iteration", "fn_planner_capture",
               "fn_plan_replay", "fn_planner_get_tree", "fn_planner_get_candidates",
               "fn_planner_get_parents",
               "fn_planner_sample_count", "fn_planner_phase_ms", "fn_planner_autotune",
               "fn_planner_kernel_ms", "fn_planner_work_counts", "fn_planner_set_surrogate",
-              "fn_planner_incumbent_path"):
+              "fn_planner_incumbent_path", "fn_planner_set_sampler", "fn_planner_set_density",
+              "fn_planner_get_density", "fn_planner_set_candidate_params",
+              "fn_planner_get_candidate_params"):
         getattr(L, n).restype = i32
     L._planner_bound = True
     return L
@@ -235,6 +279,45 @@ class Planner:
         ms = (C.c_float * 9)()
         check(lib().fn_planner_phase_ms(self.h, ms), "fn_planner_phase_ms")
         return dict(zip(self.PHASES, [float(x) for x in ms]))
+
+    def set_sampler(self, w_u=0.25, C=4, n_fit=32, em_iters=8, sd_floor=0.02, sd_init=0.1,
+                    w_chord=0.5, chord_sigma=0.1):
+        """fn_planner_set_sampler (set before capture)."""
+        cfg = FnSamplerCfg(w_u, C, n_fit, em_iters, sd_floor, sd_init, w_chord, chord_sigma)
+        self._scfg = cfg
+        check(lib().fn_planner_set_sampler(self.h, _ct.byref(cfg)), "fn_planner_set_sampler")
+
+    def set_density(self, p, theta, stream=None):
+        """fn_planner_set_density from dict(C, w_u, pi, mu, sd)."""
+        d = density_from_dict(theta)
+        check(lib().fn_planner_set_density(self.h, int(p), C.byref(d), self._stream(stream)),
+              "fn_planner_set_density")
+
+    def get_density(self, p):
+        """fn_planner_get_density: (theta dict, archive J [n], archive z [n][9])."""
+        d = FnDensity()
+        J = np.zeros(FN_ARCHIVE_MAX, np.float32)
+        Z = np.zeros((FN_ARCHIVE_MAX, 9), np.float32)
+        n = C.c_int()
+        check(lib().fn_planner_get_density(self.h, int(p), C.byref(d), J.ctypes.data, Z.ctypes.data,
+                                           C.byref(n)), "fn_planner_get_density")
+        return density_to_dict(d), J[:n.value].copy(), Z[:n.value].copy()
+
+    def set_candidate_params(self, p, z, stream=None):
+        """fn_planner_set_candidate_params: chart parameters [n_goal][9] of the
+        external goal candidates."""
+        z = np.ascontiguousarray(z, np.float32).reshape(-1, 9)
+        check(lib().fn_planner_set_candidate_params(self.h, int(p), z.ctypes.data, int(z.shape[0]),
+                                                    self._stream(stream)),
+              "fn_planner_set_candidate_params")
+
+    def get_candidate_params(self, p, n):
+        """fn_planner_get_candidate_params: chart parameters [n][9] (NaN where
+        unknown)."""
+        z = np.zeros((n, 9), np.float32)
+        check(lib().fn_planner_get_candidate_params(self.h, int(p), z.ctypes.data, int(n)),
+              "fn_planner_get_candidate_params")
+        return z
 
     def incumbent_path(self, p, max_edges=64, stream=None):
         """fn_planner_incumbent_path: the incumbent plan of problem p as edges,
