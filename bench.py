@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="iteration",
                     choices=["iteration", "surrogate", "batched", "batched-surrogate", "anytime",
-                             "nary", "control"],
+                             "nary", "control", "batched-density"],
                     help="iteration (default, the headline line), or one of the other "
                          "workloads, each printing its own line")
     ap.add_argument("--train-edges", type=int, default=2_000_000)
@@ -53,7 +53,7 @@ def parse():
                     help="bracket width of the N-ary refinement (nary workload), seconds")
     args = ap.parse_args()
     if args.steps is None:
-        args.steps = 1000 if args.workload in ("batched", "batched-surrogate") else 50
+        args.steps = 1000 if args.workload.startswith("batched") else 50
     return args
 
 
@@ -331,7 +331,7 @@ FLOP_PER_IK_START = 25987      # one damped-least-squares start, 24 iterations +
 # DRAM bytes (read + written) per launch from one ncu capture of the kernel on
 # this workload (profiles/plan_kernels_tree4096_batch2048.md); an entry is
 # removed when its kernel changes, and the roofline then reports null
-MEASURED_DRAM_BYTES = {"k_plan_sample": 340224, "k_plan_knn": 318976, "k_plan_probe": 1097984}
+MEASURED_DRAM_BYTES = {"k_plan_knn": 318976, "k_plan_probe": 1097984}
 
 
 def kernel_table(traced):
@@ -715,13 +715,16 @@ def train_surrogate(arm, n_edges, seed):
     return mlp
 
 
-def run_batched(args, surrogate_W=0):
+def run_batched(args, surrogate_W=0, densities=False):
     """64 independent problems of uneven size in one CUDA-graph replay: tree
     sizes log-uniform 256-16384, batches log-uniform 128-4096 (half goal),
     k = 8, K = 128, S = 64.  Trees are restored every 4 replays (untimed) so
     the workload stays stationary.  surrogate_W > 0: the free edges go
     through the duration surrogate's window pass (C6); the plain iteration
-    is timed alongside."""
+    is timed alongside.  densities: goal parameters from each problem's
+    p_theta (a seeded 4-component mixture), chord free candidates and the
+    archive update with an EM refit every round; the plain iteration is
+    timed alongside."""
     import torch
 
     from paper_2609_22608_gb300 import planner as P
@@ -752,9 +755,9 @@ def run_batched(args, surrogate_W=0):
     tuned = pl.autotune(probs, 0, 0, reps=2, stream=stream)
     steps = max(args.steps, 20)
 
-    def timed():
+    def timed(flags=0):
         restore()
-        pl.capture(0, stream=stream)
+        pl.capture(flags, stream=stream)
         for i in range(args.warmup):
             restore(i * 4)
             pl.replay(probs, i, stream=stream)
@@ -779,6 +782,30 @@ def run_batched(args, surrogate_W=0):
                  "plain": {"ms_per_step": float(np.mean(ms_plain)),
                            "p99_ms": float(np.percentile(ms_plain, 99))},
                  "speedup_vs_plain": float(np.mean(ms_plain) / np.mean(ms))}
+    elif densities:
+        ms_plain, out_plain = timed()
+        wc_plain = pl.work_counts()
+        drng = np.random.default_rng([0xD5, args.seed])
+        for p in range(Pn):
+            pl.set_density(p, dict(C=4, w_u=0.25, pi=np.full(4, 0.25, np.float32),
+                                   mu=drng.uniform(0.1, 0.9, (4, 9)).astype(np.float32),
+                                   sd=np.full((4, 9), 0.08, np.float32)))
+        flags = P.FN_PLAN_DENSITY | P.FN_PLAN_CHORD | P.FN_PLAN_REFIT
+        ms, out = timed(flags)
+        wc = pl.work_counts()
+
+        def evals(w):
+            return (w["probe"] + w["mprobe"] + w["verify"]) / steps
+
+        extra = {"sampler": {"flags": "density | chord | refit", "components": 4,
+                             "w_u": 0.25, "w_chord": 0.5, "chord_sigma": 0.1,
+                             "torque_evaluations_per_step": evals(wc),
+                             "nodes_added_last": int(sum(o["n_added"] for o in out))},
+                 "plain": {"ms_per_step": float(np.mean(ms_plain)),
+                           "p99_ms": float(np.percentile(ms_plain, 99)),
+                           "torque_evaluations_per_step": evals(wc_plain),
+                           "nodes_added_last": int(sum(o["n_added"] for o in out_plain))},
+                 "cost_vs_plain": float(np.mean(ms) / np.mean(ms_plain))}
     else:
         ms, out = timed()
     pl.close()
@@ -867,6 +894,14 @@ def main():
                           "uneven problems, one CUDA-graph replay, free edges through the "
                           "duration surrogate's window)")
         line["config"]["workload"] += ", surrogate window 16"
+        print(json.dumps(line))
+        return
+    if args.workload == "batched-density":
+        line = run_batched(args, densities=True)
+        line["metric"] = ("verified min-time cubic edges/sec and p99 planning-iteration ms (64 "
+                          "uneven problems, one CUDA-graph replay, goal density, chord sampler "
+                          "and refit)")
+        line["config"]["workload"] += ", p_theta + chord sampler + archive/EM refit every round"
         print(json.dumps(line))
         return
     if args.workload == "anytime":
