@@ -435,6 +435,8 @@ fn_status fn_planner_set_candidates(fn_planner_t* pl, int p, const float* states
 #define FN_PLAN_CHORD 8u    /* free candidates from the chord sampler (else uniform) */
 #define FN_PLAN_REFIT 16u   /* update the archive and refit p_theta to it after the
                                round (the last round of an anytime iteration)       */
+#define FN_PLAN_NARY 32u    /* refine the free edges' durations by the N-ary search
+                               (fn_planner_set_refine)                              */
 
 /*
  * fn_plan_iteration -- one round of Algorithm 1 for all P problems:
@@ -508,8 +510,9 @@ fn_status fn_planner_sample_count(fn_planner_t* pl, unsigned long long* count, i
  * stages, [2] of the interior-sample probe, [3] (query, node) distance
  * evaluations of the parent search, [4] IK starts run by the goal sampler,
  * [5] edges timed by the surrogate's window pass, [6] of those rescanned
- * in full (certificate failed).  count: host [n] (n <= 7 written).  reset
- * != 0 zeroes them all. */
+ * in full (certificate failed), [7] torque evaluations of the N-ary
+ * refinement (FN_PLAN_NARY).  count: host [n] (n <= 8 written).  reset != 0
+ * zeroes them all. */
 fn_status fn_planner_work_counts(fn_planner_t* pl, unsigned long long* count, int n, int reset);
 
 /* Copy problem p's tree to host (any pointer may be NULL): states [n][16],
@@ -517,6 +520,18 @@ fn_status fn_planner_work_counts(fn_planner_t* pl, unsigned long long* count, in
  * Synchronous. */
 fn_status fn_planner_get_tree(fn_planner_t* pl, int p, float* states, float* t,
                               int32_t* parent, float* J, float* nu, int* n, int cap);
+/*
+ * fn_planner_set_refine -- the N-ary refinement of rounds run with
+ * FN_PLAN_NARY: every free edge that found a grid duration T_k is refined on
+ * (T_{k-1}, T_k] as fn_time_edges_nary does (N = 32, rounds while the
+ * bracket is wider than eps, at most max_rounds), and its rho_v and
+ * clearance are taken at the refined duration, which the attach then uses
+ * (Algorithm 1: T_p = min{T <= t_best : rho(T) <= 1}, then Clear at T_p).
+ * Defaults: eps = 1e-4 s, 8 rounds.  Set before fn_planner_capture.
+ * Errors: FN_EINVAL unless eps > 0 finite and 0 <= max_rounds <= 16.
+ */
+fn_status fn_planner_set_refine(fn_planner_t* pl, float eps, int max_rounds);
+
 /*
  * The sampling densities of Sec. IV-E ("Batched expansion").
  *

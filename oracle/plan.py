@@ -7,7 +7,8 @@ goal duration T_req - t(p), the time-to-come t(p) + T_p and its argmin), the
 decision is taken in FP32 like the library's kernels.  Readings:
   * parents are the root plus the k-1 nearest non-root nodes;
   * free candidates take the first feasible grid duration with
-    t(p) + T <= t_best (time-to-come bound);
+    t(p) + T <= t_best (time-to-come bound), refined by the N-ary search
+    when `nary` = (eps, max_rounds) is given (Clear then at the refined T);
   * ties of the attach argmin go to the lower parent slot, of the incumbent
     argmax to the lower node id; a new incumbent must be strictly better;
   * a rendezvous node's nu is the largest rho_v along its path;
@@ -50,7 +51,7 @@ class Tree:
 
 
 def plan_round(arm, pr, tree: Tree, cand, n_goal, T_req, v_rel, inc, k, grid, S, S_clear=8,
-               w_vel=0.1, obstacles=None, margin=0.02, prune=False, reach_grid=256):
+               w_vel=0.1, obstacles=None, margin=0.02, prune=False, reach_grid=256, nary=None):
     """Returns (tree, incumbent dict, details).  inc = dict(id, J, t_best)."""
     cand = np.asarray(cand, F32)
     B = cand.shape[0]
@@ -81,7 +82,10 @@ def plan_round(arm, pr, tree: Tree, cand, n_goal, T_req, v_rel, inc, k, grid, S,
     if B > n_goal:
         f = slice(n_goal * k, E)
         cap = np.array([fsub(inc["t_best"], tp[b, j]) for b in range(n_goal, B) for j in range(k)], F32)
-        rf = O.time_edges(arm, s0[f], s1[f], grid, S, T_cap=cap)
+        if nary is None:
+            rf = O.time_edges(arm, s0[f], s1[f], grid, S, T_cap=cap)
+        else:   # the grid duration refined by the N-ary search, rho_v at the refined T
+            rf = O.time_edges_nary(arm, s0[f], s1[f], grid, S, nary[0], nary[1], T_cap=cap)
         ok[n_goal:] = (rf["ok"] == 1).reshape(B - n_goal, k)
         Tedge[n_goal:] = rf["T_star"].reshape(B - n_goal, k)
         rv[n_goal:] = rf["rho3"][:, 2].reshape(B - n_goal, k)

@@ -16,8 +16,8 @@
 // point, and a failed verify passes its violating sample on the same way.
 #include <cuda_runtime.h>
 
-#include "edge_core.cuh"
 #include "fn_internal.h"
+#include "nary_core.cuh"
 #include "fn_tune.h"
 
 namespace fn {
@@ -27,7 +27,6 @@ struct NaryGrid {
 };
 
 #define NARY_WARPS 4
-#define NARY_N 32
 #define NARY_MAX_ROUNDS 16
 
 // Persistent: warp w takes edges w, w + W, ...  MINB sets the register
@@ -78,26 +77,11 @@ __global__ void __launch_bounds__(32 * NARY_WARPS, MINB)
           rt = t_rt;
           rp = t_rp;
         } else {
-          if (idx >= 0) {                    // interior point idx + 1 is the first to pass
-            if (idx > 0) {
-              a = sub[idx - 1];
-              wit = w_out;
-            }
-            b = sub[idx];
-            rt = t_rt;
-            rp = t_rp;
-          } else {                           // only the known-feasible upper end passes
-            a = sub[NARY_N - 2];
-            wit = w_out;
-          }
+          nary_bracket(sub, idx, w_out, t_rt, t_rp, a, b, wit, rt, rp);
           ++r;
         }
         if (r >= max_rounds || !(b - a > eps)) break;
-        // the next round's interior points t_j = a + j (b - a) / N, j = 1..N-1
-        const float wd = (b - a) * (1.f / NARY_N);
-        __syncwarp();
-        if (lane < NARY_N - 1) sub[lane] = fmaf(__int2float_rn(lane + 1), wd, a);
-        __syncwarp();
+        nary_points(sub, a, b);
         dur = sub;
         n = NARY_N - 1;
       }

@@ -31,6 +31,7 @@
 #include "edge_core.cuh"
 #include "fn_internal.h"
 #include "fn_kin.cuh"
+#include "nary_core.cuh"
 #include "fn_mlp_tc.h"
 #include "fn_tune.h"
 #include "knn_core.cuh"
@@ -41,8 +42,8 @@
 #define PL_KNN_SPAN 4096                      // nodes per split (at least)
 #define PL_MAX_P 1024
 #define PL_MAX_KEV 40                         // launches traced per iteration
-#define PL_NCOUNT 7   // work counters: probe, verify, mid-probe, kNN pairs, IK starts,
-                      // surrogate-routed edges, surrogate rescans
+#define PL_NCOUNT 8   // work counters: probe, verify, mid-probe, kNN pairs, IK starts,
+                      // surrogate-routed edges, surrogate rescans, refine evaluations
 #define PL_CHORD_THREADS 1024  // block_scan spans 32 warps
 
 namespace fn {
@@ -1269,6 +1270,49 @@ __global__ void __launch_bounds__(PL_CHORD_THREADS) k_plan_chord(PlanDev D, ArmK
   }
 }
 
+// N-ary refinement (FN_PLAN_NARY), after the verification stages: every free
+// edge that found a grid duration T_k gets the rounds of the N-ary search on
+// (T_{k-1}, T_k]; rho_v and the clearance are then taken at the refined T,
+// which replaces the grid value (Algorithm 1: T_p = min{T <= t_best :
+// rho(T) <= 1}, then Clear at T_p).  Persistent warps stride over the free
+// edges.
+__global__ void __launch_bounds__(32 * PL_EDGE_WARPS, 2)
+    k_plan_refine(PlanDev D, ArmK A, GridKP Gr, float eps, int max_rounds) {
+  pdl_begin();
+  __shared__ float sEs[PL_EDGE_WARPS][32];
+  __shared__ float sSub[PL_EDGE_WARPS][32];
+  __shared__ float sCoef[PL_EDGE_WARPS][FN_CUBIC_WORDS * 32];
+  __shared__ float sWr[PL_EDGE_WARPS][FN_WRENCH_WORDS * 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const CubicLane cb{&sCoef[w][lane]};
+  const LaneWrench wr{&sWr[w][lane]};
+  const int nfree = D.sched->n_free_edges;
+  unsigned nsamp = 0;
+  for (int e = blockIdx.x * PL_EDGE_WARPS + w; e < nfree; e += gridDim.x * PL_EDGE_WARPS) {
+    long ei;
+    bool goal;
+    edge_slot(D, e, ei, goal);
+    const int k = D.e_k[ei];
+    if (goal || k < 0) continue;                        // warp-uniform
+    const int ci = D.e_ci[e];
+    const int p = ci / D.BM;
+    stage_rows(D.st + ((long)p * D.NC + D.e_par[e]) * 16, D.cand + (long)ci * 16, sEs[w]);
+    float a = k > 0 ? Gr.T[k - 1] : 0.f, b = Gr.T[k];
+    float rt = NAN, rp = NAN;
+    nary_rounds(A, sEs[w], cb, wr, sSub[w], D.S, eps, max_rounds, a, b, -1, rt, rp, nsamp);
+    const float rv = warp_rho_v(A, sEs[w], b);
+    bool ok = rv <= 1.f;
+    const fn_problem_t& P = D.prob[p];
+    if (ok && P.n_obs > 0) ok = warp_clearance(D, A, P, sEs[w], b) >= D.margin;
+    if (lane == 0) {
+      D.e_T[ei] = b;
+      D.e_rv[ei] = rv;
+      D.e_ok[ei] = ok ? 1 : 0;
+    }
+  }
+  if (D.samples && lane == 0 && nsamp) atomicAdd(D.samples + 7, (unsigned long long)nsamp);
+}
+
 // ---------------------------------------------------------------------------
 // attach + score + incumbent: one block per problem
 // ---------------------------------------------------------------------------
@@ -1711,6 +1755,9 @@ struct fn_planner {
   int* g_fbn = nullptr;
   int32_t* g_slot = nullptr;
   float logT0 = 0.f, dlog = 0.f;
+  // N-ary refinement of the free edges (fn_planner_set_refine)
+  float nary_eps = 1e-4f;
+  int nary_rounds = 8;
   // per-launch events of a timed iteration (kev[0] before the first launch)
   cudaEvent_t kev[PL_MAX_KEV + 1] = {};
   const char* kname[PL_MAX_KEV] = {};
@@ -2148,6 +2195,11 @@ static fn_status enqueue_iteration(fn_planner* pl, unsigned flags, cudaStream_t 
   mark(3);
   enqueue_edges(pl, pl->edge_variant, pl->edge_blocks, st, mark);
   if (pl->sur_mlp) enqueue_surrogate(pl, st);
+  if (flags & FN_PLAN_NARY) {
+    pl_launch(k_plan_refine, 2 * num_sms(), 32 * PL_EDGE_WARPS, 0, st, D, pl->arm, pl->grid,
+              pl->nary_eps, pl->nary_rounds);
+    trace(pl, st, "k_plan_refine");
+  }
   mark(6);
   pl_launch(k_plan_attach, P, PL_ATTACH_THREADS, 0, st, D);
   trace(pl, st, "k_plan_attach");
@@ -2274,6 +2326,14 @@ extern "C" fn_status fn_planner_get_tree(fn_planner_t* pl, int p, float* states,
   if (J) ok &= cudaMemcpy(J, pl->D.J + nb, sizeof(float) * m, cudaMemcpyDeviceToHost) == cudaSuccess;
   if (nu) ok &= cudaMemcpy(nu, pl->D.nu + nb, sizeof(float) * m, cudaMemcpyDeviceToHost) == cudaSuccess;
   return ok ? FN_OK : FN_ECUDA;
+}
+
+extern "C" fn_status fn_planner_set_refine(fn_planner_t* pl, float eps, int max_rounds) {
+  if (!pl || !(eps > 0.f) || !std::isfinite(eps) || max_rounds < 0 || max_rounds > 16)
+    return FN_EINVAL;
+  pl->nary_eps = eps;
+  pl->nary_rounds = max_rounds;
+  return FN_OK;
 }
 
 extern "C" fn_status fn_planner_set_sampler(fn_planner_t* pl, const fn_sampler_cfg_t* cfg) {
@@ -2644,6 +2704,9 @@ struct fn_edges {
   int32_t* list = nullptr;
   int* n_list = nullptr;
   float logT0 = 0.f, dlog = 0.f;
+  // N-ary refinement of the free edges (fn_planner_set_refine)
+  float nary_eps = 1e-4f;
+  int nary_rounds = 8;
 };
 
 extern "C" fn_status fn_edges_destroy(fn_edges_t* eg) {

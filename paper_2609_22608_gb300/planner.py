@@ -17,6 +17,7 @@ FN_PLAN_PRUNE = 2
 FN_PLAN_DENSITY = 4
 FN_PLAN_CHORD = 8
 FN_PLAN_REFIT = 16
+FN_PLAN_NARY = 32
 FN_DENSITY_MAX_C = 4
 FN_ARCHIVE_MAX = 64
 FN_MAX_OBS = 8
@@ -108,6 +109,7 @@ def _bind():
     L.fn_planner_get_density.argtypes = [vp, i32, C.POINTER(FnDensity), vp, vp, C.POINTER(C.c_int)]
     L.fn_planner_set_candidate_params.argtypes = [vp, i32, vp, i32, vp]
     L.fn_planner_get_candidate_params.argtypes = [vp, i32, vp, i32]
+    L.fn_planner_set_refine.argtypes = [vp, C.c_float, i32]
     for n in ("fn_planner_create", "fn_planner_destroy", "fn_planner_reset", "fn_planner_load_tree",
               "fn_planner_set_candidates", "fn_plan_iteration", "fn_planner_capture",
               "fn_plan_replay", "fn_planner_get_tree", "fn_planner_get_candidates",
@@ -116,7 +118,7 @@ def _bind():
               "fn_planner_kernel_ms", "fn_planner_work_counts", "fn_planner_set_surrogate",
               "fn_planner_incumbent_path", "fn_planner_set_sampler", "fn_planner_set_density",
               "fn_planner_get_density", "fn_planner_set_candidate_params",
-              "fn_planner_get_candidate_params"):
+              "fn_planner_get_candidate_params", "fn_planner_set_refine"):
         getattr(L, n).restype = i32
     L._planner_bound = True
     return L
@@ -280,6 +282,11 @@ class Planner:
         check(lib().fn_planner_phase_ms(self.h, ms), "fn_planner_phase_ms")
         return dict(zip(self.PHASES, [float(x) for x in ms]))
 
+    def set_refine(self, eps=1e-4, max_rounds=8):
+        """fn_planner_set_refine (set before capture)."""
+        check(lib().fn_planner_set_refine(self.h, float(eps), int(max_rounds)),
+              "fn_planner_set_refine")
+
     def set_sampler(self, w_u=0.25, C=4, n_fit=32, em_iters=8, sd_floor=0.02, sd_init=0.1,
                     w_chord=0.5, chord_sigma=0.1):
         """fn_planner_set_sampler (set before capture)."""
@@ -371,12 +378,12 @@ class Planner:
         return [(names[i].decode(), float(ms[i])) for i in range(min(n.value, cap))]
 
     WORK = ("probe", "verify", "mprobe", "knn_pairs", "ik_starts", "surrogate_edges",
-            "surrogate_rescans")
+            "surrogate_rescans", "refine")
 
     def work_counts(self, reset=False):
         """fn_planner_work_counts: dict of the planner's work counters."""
-        c = (C.c_ulonglong * 7)()
-        check(_bind().fn_planner_work_counts(self.h, c, 7, int(bool(reset))),
+        c = (C.c_ulonglong * 8)()
+        check(_bind().fn_planner_work_counts(self.h, c, 8, int(bool(reset))),
               "fn_planner_work_counts")
         return dict(zip(self.WORK, [int(x) for x in c]))
 

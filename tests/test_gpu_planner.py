@@ -402,3 +402,70 @@ def test_autotune_keeps_results(P, orc, arm):
     a, b = trees
     assert a["n"] == b["n"] and np.array_equal(a["states"], b["states"])
     assert np.array_equal(a["parent"], b["parent"]) and np.array_equal(a["t"], b["t"])
+
+
+def test_plan_round_nary_refinement(P, orc, arm):
+    """FN_PLAN_NARY: the free edges' grid durations are refined by the N-ary
+    search before the attach.  Every attached free node must carry a valid
+    refined duration (its check passes in FP64 within the margin, eps below
+    it fails within the margin, and it is not above the grid duration), and
+    the round must match the oracle's refined round on nearly every
+    candidate (refined decisions sit within the margin of the boundary, so
+    a few may legitimately differ)."""
+    case = make_case(arm, orc, 3, N=400, n_goal_draw=256, n_free=192)
+    # free candidates near the root, so that short free edges exist
+    G = case["n_goal"]
+    rng = np.random.default_rng(3)
+    near = np.repeat(case["root"][None].astype(np.float64), case["cand"].shape[0] - G, axis=0)
+    near[:, :7] += rng.normal(0, 0.15, (len(near), 7))
+    near[:, 8:15] = rng.normal(0, 0.2, (len(near), 7))
+    near[:, 7] = near[:, 15] = 0
+    lo, hi = arm["q_lo"].astype(np.float64), arm["q_hi"].astype(np.float64)
+    near[:, :7] = np.clip(near[:, :7], lo + 0.05, hi - 0.05)
+    case["cand"] = np.concatenate([case["cand"][:G], near.astype(np.float32)])
+    grid = synth.duration_grid(K_GRID)
+    states, t, parent = case["tree"]
+    N, B, k, eps = states.shape[0], case["cand"].shape[0], 5, 2e-4
+    pl = P.Planner(arm, P=1, n_cap=N + B + 8, b_max=B, k=k, K=K_GRID, S=S_COLL, S_clear=8)
+    pl.set_refine(eps, 8)
+    prob = P.problem_struct(case["pr"], B, case["n_goal"], root=case["root"])
+    pl.reset([prob])
+    pl.load_tree(0, states, t, parent)
+    pl.set_candidates(0, case["cand"], case["n_goal"], case["T_req"], case["v_rel"])
+    pl.work_counts(reset=True)
+    pl.iterate([prob], 0, P.FN_PLAN_EXTERNAL | P.FN_PLAN_NARY)
+    wc = pl.work_counts()
+    gtree = pl.get_tree(0)
+    pl.close()
+    assert wc["refine"] > 0
+    inc = dict(id=-1, J=-np.inf, t_best=float(np.float32(case["pr"]["t_fall"])))
+    rtree, _, det = OP.plan_round(arm, case["pr"], OP.Tree(states, t, parent), case["cand"],
+                                  case["n_goal"], case["T_req"], case["v_rel"], inc, k, grid,
+                                  S_COLL, S_clear=8, nary=(eps, 8))
+    free_new = [i for i in range(N, gtree["n"]) if not np.isfinite(gtree["J"][i])]
+    assert len(free_new) >= 10
+    for i in free_new:
+        p = int(gtree["parent"][i])
+        T = float(gtree["t"][i]) - float(gtree["t"][p])
+        s0, s1 = gtree["states"][p][None], gtree["states"][i][None]
+        r_hi = orc.rho_batch(arm, s0, s1, [T], S_COLL)[0]
+        assert max(r_hi[0], r_hi[1]) <= 1 + 1e-4 + 1e-5
+        r_lo = orc.rho_batch(arm, s0, s1, [T - eps - 2e-6], S_COLL)[0]
+        kg = int(np.searchsorted(grid, np.float32(T) - np.float32(1e-6), side="left"))
+        assert kg < len(grid) and T <= float(grid[kg]) + 1e-6
+        if T - eps > 1e-3:
+            assert max(r_lo[0], r_lo[1]) > 1 - 1e-4
+    # against the oracle's refined round: parent and time per candidate
+    g_new = {gtree["states"][i].tobytes(): i for i in range(N, gtree["n"])}
+    r_new = {rtree.states[i].tobytes(): i for i in range(N, rtree.n)}
+    same, total = 0, 0
+    for b in range(G, B):
+        key = case["cand"][b].tobytes()
+        gi, ri = g_new.get(key), r_new.get(key)
+        if gi is None and ri is None:
+            continue
+        total += 1
+        if gi is not None and ri is not None and gtree["parent"][gi] == rtree.parent[ri] and \
+                abs(float(gtree["t"][gi]) - float(rtree.t[ri])) <= eps + 1e-4 * float(rtree.t[ri]):
+            same += 1
+    assert total >= 10 and same >= 0.95 * total, (same, total)
