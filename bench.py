@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="iteration",
                     choices=["iteration", "surrogate", "batched", "batched-surrogate", "anytime",
-                             "nary", "control", "batched-density"],
+                             "nary", "control", "batched-density", "batched-nary"],
                     help="iteration (default, the headline line), or one of the other "
                          "workloads, each printing its own line")
     ap.add_argument("--train-edges", type=int, default=2_000_000)
@@ -513,6 +513,7 @@ def run_surrogate(args):
     v_full = E / (best_full / 1e3)
     v_win = agree.sum() / (np.mean(ms_win) / 1e3)
     peak = fp32_peak_tflops()
+    mlp_err = bool(mlp.error())
     mlp.close()
     return {
         "metric": "verified min-time cubic edges/sec: surrogate window vs full scan (FP32 RNEA; "
@@ -537,7 +538,8 @@ def run_surrogate(args):
                    "agreement_with_full_scan": float(agree.mean()),
                    "unverified_edges": int((~agree).sum()),
                    "speedup_vs_full": float(best_full / np.mean(ms_win)),
-                   "mlp_tflops": 2 * E * (32 * 256 + 256 * 256 * 2 + 256 * 2) / (np.mean(ms_pred) / 1e3) / 1e12},
+                   "mlp_tflops": 2 * E * (32 * 256 + 256 * 256 * 2 + 256 * 2) / (np.mean(ms_pred) / 1e3) / 1e12,
+                   "tensor_core_wait_timeouts": mlp_err},
         "window_warp_per_edge": {"ms": float(np.mean(ms_win_w)), "samples": int(cw.item()),
                                  "agreement": float((kw_w == kf).mean())},
         "fp32_peak_tflops": peak,
@@ -715,7 +717,7 @@ def train_surrogate(arm, n_edges, seed):
     return mlp
 
 
-def run_batched(args, surrogate_W=0, densities=False):
+def run_batched(args, surrogate_W=0, densities=False, nary=False):
     """64 independent problems of uneven size in one CUDA-graph replay: tree
     sizes log-uniform 256-16384, batches log-uniform 128-4096 (half goal),
     k = 8, K = 128, S = 64.  Trees are restored every 4 replays (untimed) so
@@ -724,7 +726,9 @@ def run_batched(args, surrogate_W=0, densities=False):
     is timed alongside.  densities: goal parameters from each problem's
     p_theta (a seeded 4-component mixture), chord free candidates and the
     archive update with an EM refit every round; the plain iteration is
-    timed alongside."""
+    timed alongside.  nary: the free edges' durations refined by the N-ary
+    search (eps = --eps) before the attach; the plain iteration is timed
+    alongside."""
     import torch
 
     from paper_2609_22608_gb300 import planner as P
@@ -766,22 +770,45 @@ def run_batched(args, surrogate_W=0, densities=False):
 
     extra = {}
     if surrogate_W > 0:
+        t0 = time.perf_counter()
         ms_plain, _ = timed()
+        plain_s = time.perf_counter() - t0
         t0 = time.perf_counter()
         mlp = train_surrogate(arm, args.train_edges // 4, args.seed)
         train_s = time.perf_counter() - t0
+        mlp.error(reset=True)
         pl.set_surrogate(mlp, surrogate_W)
+        t0 = time.perf_counter()
         ms, out = timed()
+        sur_s = time.perf_counter() - t0
         wc = pl.work_counts()
+        mlp_err = bool(mlp.error())
         pl.set_surrogate(None)
         mlp.close()
         extra = {"surrogate": {"window": surrogate_W, "train_edges": args.train_edges // 4,
-                               "train_s": train_s,
+                               "train_s": train_s, "plain_wall_s": plain_s,
+                               "surrogate_wall_s": sur_s,
+                               "tensor_core_wait_timeouts": mlp_err,
                                "routed_edges_per_step": wc["surrogate_edges"] / steps,
                                "rescanned_fraction": wc["surrogate_rescans"] / max(1, wc["surrogate_edges"])},
                  "plain": {"ms_per_step": float(np.mean(ms_plain)),
                            "p99_ms": float(np.percentile(ms_plain, 99))},
                  "speedup_vs_plain": float(np.mean(ms_plain) / np.mean(ms))}
+    elif nary:
+        ms_plain, out_plain = timed()
+        wc_plain = pl.work_counts()
+        pl.set_refine(args.eps, 8)
+        ms, out = timed(P.FN_PLAN_NARY)
+        wc = pl.work_counts()
+        extra = {"refine": {"eps_s": args.eps, "max_rounds": 8,
+                            "refine_torque_evaluations_per_step": wc["refine"] / steps,
+                            "edge_torque_evaluations_per_step":
+                                (wc["probe"] + wc["mprobe"] + wc["verify"]) / steps,
+                            "nodes_added_last": int(sum(o["n_added"] for o in out))},
+                 "plain": {"ms_per_step": float(np.mean(ms_plain)),
+                           "p99_ms": float(np.percentile(ms_plain, 99)),
+                           "nodes_added_last": int(sum(o["n_added"] for o in out_plain))},
+                 "cost_vs_plain": float(np.mean(ms) / np.mean(ms_plain))}
     elif densities:
         ms_plain, out_plain = timed()
         wc_plain = pl.work_counts()
@@ -894,6 +921,14 @@ def main():
                           "uneven problems, one CUDA-graph replay, free edges through the "
                           "duration surrogate's window)")
         line["config"]["workload"] += ", surrogate window 16"
+        print(json.dumps(line))
+        return
+    if args.workload == "batched-nary":
+        line = run_batched(args, nary=True)
+        line["metric"] = ("verified min-time cubic edges/sec and p99 planning-iteration ms (64 "
+                          "uneven problems, one CUDA-graph replay, free-edge durations refined "
+                          "by the N-ary search)")
+        line["config"]["workload"] += f", N-ary refinement of free edges to eps={args.eps:g} s"
         print(json.dumps(line))
         return
     if args.workload == "batched-density":
