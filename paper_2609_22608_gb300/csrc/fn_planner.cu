@@ -1276,7 +1276,7 @@ __global__ void __launch_bounds__(PL_CHORD_THREADS) k_plan_chord(PlanDev D, ArmK
 // which replaces the grid value (Algorithm 1: T_p = min{T <= t_best :
 // rho(T) <= 1}, then Clear at T_p).  Persistent warps stride over the free
 // edges.
-__global__ void __launch_bounds__(32 * PL_EDGE_WARPS, 2)
+__global__ void __launch_bounds__(32 * PL_EDGE_WARPS, 3)
     k_plan_refine(PlanDev D, ArmK A, GridKP Gr, float eps, int max_rounds) {
   pdl_begin();
   __shared__ float sEs[PL_EDGE_WARPS][32];
@@ -2196,7 +2196,7 @@ static fn_status enqueue_iteration(fn_planner* pl, unsigned flags, cudaStream_t 
   enqueue_edges(pl, pl->edge_variant, pl->edge_blocks, st, mark);
   if (pl->sur_mlp) enqueue_surrogate(pl, st);
   if (flags & FN_PLAN_NARY) {
-    pl_launch(k_plan_refine, 2 * num_sms(), 32 * PL_EDGE_WARPS, 0, st, D, pl->arm, pl->grid,
+    pl_launch(k_plan_refine, 3 * num_sms(), 32 * PL_EDGE_WARPS, 0, st, D, pl->arm, pl->grid,
               pl->nary_eps, pl->nary_rounds);
     trace(pl, st, "k_plan_refine");
   }
