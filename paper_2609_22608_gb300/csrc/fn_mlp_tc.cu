@@ -4,10 +4,10 @@
 //   shared memory; layer 1 (K = 32) against the resident packed W1;
 //   layers 2 and 3 (K = 256) against weight chunks of 64 columns streamed by
 //   cp.async.bulk into a 4-deep ring, the accumulator (128 lanes x 256 FP32
-//   columns) in tensor memory; after each layer the four warps read their
-//   32 TMEM lanes back (tcgen05.ld), add the bias, apply ReLU, round to bf16
-//   and write the next A operand; layer 4 (256 -> 2) runs on the CUDA cores
-//   in the last epilogue.  Same rounding points as the mma.sync path (bf16
+//   columns) in tensor memory; after each layer sixteen warps read it back
+//   (tcgen05.ld; warp w takes lane quarter w % 4 and 64 of the 256 columns),
+//   add the bias, apply ReLU, round to bf16 and write the next A operand;
+//   layer 4 (256 -> 2) runs on the CUDA cores in the last epilogue.  Same rounding points as the mma.sync path (bf16
 //   operands, FP32 accumulation, bias then ReLU then bf16).
 //
 // One thread issues the copies and the MMAs; completion is tracked by
@@ -34,7 +34,13 @@ constexpr int kSW1 = kSB + 4 * kTcChunkBytes;   // packed W1 (16 KB)
 constexpr int kSBias = kSW1 + kTcW1Bytes;       // b1, b2, b3 (3 x 256 f32)
 constexpr int kSW4 = kSBias + 3 * 256 * 4;      // W4 [256][2] f32
 constexpr int kSBar = kSW4 + 512 * 4;           // mbarriers + TMEM address
-constexpr int kTcSmem = kSBar + 128;
+constexpr int kSY = kSBar + 128;                // layer-4 partial sums [4][128][2] f32
+constexpr int kTcSmem = kSY + 4 * kTcM * 2 * 4;
+
+// 16 warps: warp w reads TMEM lane quarter w % 4 (the tcgen05 access rule)
+// and column group w / 4 (64 of the 256 accumulator columns) in the
+// epilogues, so that four warps share each scheduler.
+constexpr int kTcThreads = 512;
 
 constexpr int kRing = 4;
 constexpr int kTmemCols = 256;
@@ -142,7 +148,7 @@ __global__ void k_mlp_tc_pack(const bf16* __restrict__ W, int K, int Kt, bf16* _
   out[off] = W[i];
 }
 
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kTcThreads, 1)
     k_mlp_tc(ArmK A, const float* __restrict__ s0, const float* __restrict__ s1, int E,
              const bf16* __restrict__ W1p, const bf16* __restrict__ W23p,
              const float* __restrict__ b1, const float* __restrict__ b2,
@@ -151,6 +157,8 @@ __global__ void __launch_bounds__(128, 1)
              const int* __restrict__ E_dev) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int lq = warp & 3, cg = warp >> 2;          // TMEM lane quarter, column group
+  const int trow = lq * 32 + (tid & 31);            // this thread's row of the tile
   if (E_dev) E = min(E, *E_dev);   // rows counted on the device (at most the launch's E)
   const int ntiles = (E + kTcM - 1) / kTcM;
   if ((int)blockIdx.x >= ntiles) return;   // block-uniform, before any barrier
@@ -158,6 +166,7 @@ __global__ void __launch_bounds__(128, 1)
   uint8_t* sA = smem + kSA;
   float* sBias = reinterpret_cast<float*>(smem + kSBias);
   float* sW4 = reinterpret_cast<float*>(smem + kSW4);
+  float* sY = reinterpret_cast<float*>(smem + kSY);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kSBar);
   // bars[0..3] chunk arrived, bars[4..7] chunk consumed, bars[8] layer done, bars[9] W1 arrived
   volatile uint32_t* s_tmem = reinterpret_cast<volatile uint32_t*>(smem + kSBar + 80);
@@ -187,7 +196,7 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *s_tmem;
-  const uint32_t tmem_lane = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's 32 lanes
+  const uint32_t tmem_lane = tmem + ((uint32_t)(lq * 32) << 16);   // this warp's 32 lanes
 
   const long total = (long)my_tiles * 8;   // streamed chunks (layers 2 and 3 of every tile)
   int issued[kRing] = {0, 0, 0, 0};        // thread 0: copies in flight per slot
@@ -207,9 +216,10 @@ __global__ void __launch_bounds__(128, 1)
   }
 
   for (int it = 0; it < my_tiles; ++it) {
-    const long row = ((long)blockIdx.x + (long)it * gridDim.x) * kTcM + tid;
-    // ---- features -> A (K = 32 layout: 4 core matrices per 8-row group)
-    {
+    const long row = ((long)blockIdx.x + (long)it * gridDim.x) * kTcM + trow;
+    // ---- features -> A (K = 32 layout: 4 core matrices per 8-row group):
+    // warps 0-3, whose thread tid owns row tid (= trow)
+    if (tid < kTcM) {
       float f[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) f[j] = 0.f;
@@ -259,9 +269,10 @@ __global__ void __launch_bounds__(128, 1)
       if (*s_fail) break;
       const float* bias = sBias + 256 * layer;
       if (layer < 2) {
-        // epilogue: bias, ReLU, bf16 -> A (K = 256 layout: 32 core matrices per 8-row group)
+        // epilogue: bias, ReLU, bf16 -> A (K = 256 layout: 32 core matrices per
+        // 8-row group); this warp's two 32-column blocks of its 32 rows
 #pragma unroll 1
-        for (int cb = 0; cb < 8; ++cb) {
+        for (int cb = 2 * cg; cb < 2 * cg + 2; ++cb) {
           uint32_t v[32];
           tmem_ld32(tmem_lane + cb * 32, v);
 #pragma unroll
@@ -275,7 +286,7 @@ __global__ void __launch_bounds__(128, 1)
             o.y = pack_bf16x2(x[2], x[3]);
             o.z = pack_bf16x2(x[4], x[5]);
             o.w = pack_bf16x2(x[6], x[7]);
-            *reinterpret_cast<uint4*>(sA + ((tid >> 3) * 32 + cb * 4 + q) * 128 + (tid & 7) * 16) = o;
+            *reinterpret_cast<uint4*>(sA + ((trow >> 3) * 32 + cb * 4 + q) * 128 + (trow & 7) * 16) = o;
           }
         }
         tc_fence_before();
@@ -313,10 +324,11 @@ __global__ void __launch_bounds__(128, 1)
         }
         __syncthreads();
       } else {
-        // last epilogue: h3 = bf16(ReLU(acc + b3)); y = h3 W4 + b4 on the CUDA cores
+        // last epilogue: h3 = bf16(ReLU(acc + b3)); y = h3 W4 + b4 on the CUDA
+        // cores, each warp over its 64 columns, the four groups summed in order
         float y0 = 0.f, y1 = 0.f;
 #pragma unroll 1
-        for (int cb = 0; cb < 8; ++cb) {
+        for (int cb = 2 * cg; cb < 2 * cg + 2; ++cb) {
           uint32_t v[32];
           tmem_ld32(tmem_lane + cb * 32, v);
 #pragma unroll
@@ -328,11 +340,20 @@ __global__ void __launch_bounds__(128, 1)
             y1 = fmaf(h, sW4[2 * k + 1], y1);
           }
         }
-        if (row < E) {
-          Y[2 * row] = y0 + b4[0];
-          Y[2 * row + 1] = y1 + b4[1];
-        }
+        sY[(cg * kTcM + trow) * 2] = y0;
+        sY[(cg * kTcM + trow) * 2 + 1] = y1;
         tc_fence_before();
+        __syncthreads();
+        if (cg == 0 && row < E) {
+          float z0 = 0.f, z1 = 0.f;
+#pragma unroll
+          for (int g2 = 0; g2 < 4; ++g2) {
+            z0 += sY[(g2 * kTcM + trow) * 2];
+            z1 += sY[(g2 * kTcM + trow) * 2 + 1];
+          }
+          Y[2 * row] = z0 + b4[0];
+          Y[2 * row + 1] = z1 + b4[1];
+        }
         __syncthreads();
       }
     }
@@ -376,8 +397,8 @@ fn_status mlp_tc_forward(const ArmK& A, const float* s0, const float* s1, int E,
   }
   const int ntiles = (E + kTcM - 1) / kTcM;
   const int grid = ntiles < num_sms() ? ntiles : num_sms();
-  k_mlp_tc<<<grid, 128, kTcSmem, st>>>(A, s0, s1, E, W1p, W23p, b1, b2, b3, W4b, b4, Y, err,
-                                        E_dev);
+  k_mlp_tc<<<grid, kTcThreads, kTcSmem, st>>>(A, s0, s1, E, W1p, W23p, b1, b2, b3, W4b, b4, Y,
+                                               err, E_dev);
   return launch_status();
 }
 
