@@ -331,7 +331,7 @@ FLOP_PER_IK_START = 25987      # one damped-least-squares start, 24 iterations +
 # DRAM bytes (read + written) per launch from one ncu capture of the kernel on
 # this workload (profiles/plan_kernels_tree4096_batch2048.md); an entry is
 # removed when its kernel changes, and the roofline then reports null
-MEASURED_DRAM_BYTES = {"k_plan_sample": 353024, "k_plan_knn": 320000, "k_plan_probe": 1097472}
+MEASURED_DRAM_BYTES = {"k_plan_probe": 1097472}
 
 
 def kernel_table(traced):

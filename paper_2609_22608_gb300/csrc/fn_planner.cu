@@ -40,6 +40,7 @@
 #define PL_KNN_WARPS 4
 #define PL_KNN_QW 1                           // queries per warp
 #define PL_KNN_SPAN 4096                      // nodes per split (at least)
+#define PL_KNN_SPAN_GOAL 512                  // the same for goal queries (few, and late)
 #define PL_MAX_P 1024
 #define PL_MAX_KEV 40                         // launches traced per iteration
 #define PL_NCOUNT 8   // work counters: probe, verify, mid-probe, kNN pairs, IK starts,
@@ -70,12 +71,17 @@ struct Sched {
   int n_surv;         // probe survivors appended (may exceed surv_cap)
   int n_free_edges;   // free edges of all problems (the queue's first part)
   int n_edges;        // all edges
-  int knn_items;      // (problem, query group, split) items, one per warp
-  int knn_head;       // next unclaimed parent-search item
+  // parent-search items (problem, query group, split), one per warp, in two
+  // lists: [0] free queries, [1] goal queries (searched after the goal
+  // chart has decoded them, in smaller splits)
+  int knn_items[2];   // [1] unused: goal items come from the decoded-goal list
+  int knn_head[2];    // next unclaimed item of each list
+  int gq_n;           // decoded goal queries appended to PlanDev::gq this round
+  int nsg_max;        // largest goal split count over the problems
   int free_off[PL_MAX_P + 1];
   int goal_off[PL_MAX_P + 1];
-  int knn_off[PL_MAX_P + 1];
-  int nsplit[PL_MAX_P];
+  int knn_off[2][PL_MAX_P + 1];
+  int nsplit[2][PL_MAX_P];
   int pack_lo[PL_MAX_P];      // first node of problem p to (re)pack into the mirror
   int pack_off[PL_MAX_P + 1]; // flattened offsets of the nodes to pack
 };
@@ -145,6 +151,7 @@ struct PlanDev {  // device pointers, passed by value to the kernels
   float* cz;          // [P][BM][9] chart parameters of the goal candidates (NaN: unknown)
   float* zn;          // [P][NC][9] chart parameters of goal nodes, written at attach
   int32_t* glist;     // [P][BM] the round's valid goal candidates, in order
+  int2* gq;           // [P * BM] (problem, slot) of the round's decoded goal queries
   fn_sampler_cfg_t scfg;
   // parents: node mirror laid out for lane-contiguous loads (see knn_mirror_index)
   float4* mir;        // [P][NB][7][32]
@@ -159,6 +166,12 @@ struct PlanDev {  // device pointers, passed by value to the kernels
 __device__ __forceinline__ void pdl_begin() {
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
 }
 
 struct GridKP {
@@ -217,21 +230,30 @@ __global__ void k_plan_schedule(PlanDev D) {
   pdl_begin();
   if (threadIdx.x != 0) return;
   Sched* S = D.sched;
-  int fo = 0, go = 0, ko = 0, po = 0;
+  int fo = 0, go = 0, ko = 0, kg = 0, po = 0, nsg_max = 1;
   for (int p = 0; p < D.P; ++p) {
     const fn_problem_t& P = D.prob[p];
     const int B = min(max(P.batch, 0), D.BM);
     const int G = min(max(P.n_goal, 0), B);
     S->free_off[p] = fo;
     S->goal_off[p] = go;
-    S->knn_off[p] = ko;
+    S->knn_off[0][p] = ko;
+    S->knn_off[1][p] = kg;
     fo += (B - G) * D.KP;
     go += G * D.KP;
     const int span = D.n_nodes[p] - 1;  // non-root nodes
-    int ns = 1;
-    if (D.KN > 0 && span > 0) ns = min(PL_NSPLIT_MAX, (span + PL_KNN_SPAN - 1) / PL_KNN_SPAN);
-    S->nsplit[p] = ns;
-    ko += (D.KN > 0 && span > 0) ? ((B + PL_KNN_QW - 1) / PL_KNN_QW) * ns : 0;
+    int ns = 1, nsg = 1;
+    if (D.KN > 0 && span > 0) {
+      ns = min(PL_NSPLIT_MAX, (span + PL_KNN_SPAN - 1) / PL_KNN_SPAN);
+      nsg = min(PL_NSPLIT_MAX, (span + PL_KNN_SPAN_GOAL - 1) / PL_KNN_SPAN_GOAL);
+    }
+    S->nsplit[0][p] = ns;
+    S->nsplit[1][p] = nsg;
+    nsg_max = max(nsg_max, nsg);
+    if (D.KN > 0 && span > 0) {
+      ko += ((B - G + PL_KNN_QW - 1) / PL_KNN_QW) * ns;
+      kg += ((G + PL_KNN_QW - 1) / PL_KNN_QW) * nsg;
+    }
     D.added[p] = 0;
     const int lo = min(D.packed[p], D.n_nodes[p]);
     S->pack_lo[p] = lo;
@@ -242,11 +264,16 @@ __global__ void k_plan_schedule(PlanDev D) {
   S->pack_off[D.P] = po;
   S->free_off[D.P] = fo;
   S->goal_off[D.P] = go;
-  S->knn_off[D.P] = ko;
+  S->knn_off[0][D.P] = ko;
+  S->knn_off[1][D.P] = kg;
   S->n_free_edges = fo;
   S->n_edges = fo + go;
-  S->knn_items = ko;
-  S->knn_head = 0;
+  S->knn_items[0] = ko;
+  S->knn_items[1] = kg;
+  S->knn_head[0] = 0;
+  S->knn_head[1] = 0;
+  S->gq_n = 0;
+  S->nsg_max = nsg_max;
   if (D.sur_n) *D.sur_n = 0;
   S->queue_head = 0u;
 }
@@ -337,32 +364,73 @@ __device__ __forceinline__ void sample_free(const PlanDev& D, const ArmK& A, int
 
 __device__ __forceinline__ void parents_prep(const PlanDev& D, long i, long stride);
 
-// Sampling launch: warp w < nslots (P * b_max, or 0 when the caller gives
-// the candidates) owns candidate slot (p, b).  A goal
-// slot is decoded by the whole warp: every lane decodes the chart pose, lane
-// groups 0-2 (8 lanes each) run the three IK starts in parallel
-// (ik_solve_group) and the lowest start that converges wins, the same result
-// as trying the starts in order; group 3 repeats start 0 and is ignored.  A
-// free slot is drawn by lane 0.  The warps past the slots prepare the parent
-// search (parents_prep), which reads nothing the samplers write.
+__device__ __forceinline__ void sample_goal(const PlanDev& D, const ArmK& A, int p, int b, int dens);
+
+// a goal query of this round: a decoded (valid) one joins the goal list of
+// the parent search; the others get empty parent lists here
+__device__ __forceinline__ void goal_query(const PlanDev& D, int p, int b, bool valid) {
+  if (D.KN <= 0) return;
+  const long ci = (long)p * D.BM + b;
+  if (valid && D.n_nodes[p] > 1) {
+    const int v = atomicAdd(&D.sched->gq_n, 1);
+    D.gq[v] = make_int2(p, b);
+  } else {
+    for (int j = 0; j < D.KN; ++j) D.nn[ci * D.KN + j] = -1;
+  }
+}
+
+// Sampling launches: warp w < nslots (P * b_max, or 0 when the caller gives
+// the candidates) owns candidate slot (p, b).
+//   role 0: a free slot is drawn by lane 0; the warps past the slots prepare
+//           the parent search (parents_prep: tree mirror, empty lists);
+//   role 1: a goal slot is decoded by the whole warp (sample_goal).
+// With `late`, a role-1 launch triggers its dependents at once and waits for
+// its predecessor (the free queries' parent search, which it neither reads
+// nor writes) only before it exits, so that the goal chart's IK runs beside
+// that search while the next launch still sees both complete.
 __global__ void __launch_bounds__(128) k_plan_sample(PlanDev D, ArmK A, long nslots,
-                                                     int prep_warps, int dens) {
-  pdl_begin();
+                                                     int prep_warps, int dens, int role,
+                                                     int late) {
+  if (late) pdl_trigger();
+  else pdl_begin();
   const long gid = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (role == 0) {
+    const long nsw = (nslots + 31) / 32;              // slot warps: one lane per slot
+    if (gid < nsw) {
+      const long x = gid * 32 + lane;
+      if (x < nslots) {
+        const int p = (int)(x / D.BM), b = (int)(x - (long)p * D.BM);
+        const int B = min(max(D.prob[p].batch, 0), D.BM);
+        if (b >= min(max(D.prob[p].n_goal, 0), B) && b < B) sample_free(D, A, p, b);
+      }
+    } else if (gid - nsw < prep_warps) {
+      const long i = (gid - nsw) * 32 + lane, stride = (long)prep_warps * 32;
+      parents_prep(D, i, stride);
+      if (nslots == 0)                                // external candidates: list their goals
+        for (long x = i; x < (long)D.P * D.BM; x += stride) {
+          const int p = (int)(x / D.BM), b = (int)(x - (long)p * D.BM);
+          const int B = min(max(D.prob[p].batch, 0), D.BM);
+          if (b < min(max(D.prob[p].n_goal, 0), B)) goal_query(D, p, b, D.valid[x] != 0);
+        }
+    }
+  } else if (gid < nslots) {
+    const int p = (int)(gid / D.BM);
+    const int b = (int)(gid - (long)p * D.BM);
+    const int B = min(max(D.prob[p].batch, 0), D.BM);
+    if (b < min(max(D.prob[p].n_goal, 0), B)) sample_goal(D, A, p, b, dens);   // warp-uniform
+  }
+  if (late) pdl_wait();
+}
+
+// A goal slot: every lane decodes the chart pose, lane groups 0-2 (8 lanes
+// each) run the three IK starts in parallel (ik_solve_group) and the lowest
+// start that converges wins, the same result as trying the starts in order;
+// group 3 repeats start 0 and is ignored.
+__device__ __forceinline__ void sample_goal(const PlanDev& D, const ArmK& A, int p, int b,
+                                            int dens) {
   const int lane = threadIdx.x & 31, grp = lane >> 3;
-  if (gid >= nslots) {                                // warp-uniform
-    if (gid - nslots < prep_warps) parents_prep(D, (gid - nslots) * 32 + lane, (long)prep_warps * 32);
-    return;
-  }
-  const int p = (int)(gid / D.BM);
-  const int b = (int)(gid - (long)p * D.BM);
   const fn_problem_t& P = D.prob[p];
-  const int B = min(max(P.batch, 0), D.BM);
-  const int G = min(max(P.n_goal, 0), B);
-  if (b >= G) {                                       // warp-uniform
-    if (b < B && lane == 0) sample_free(D, A, p, b);
-    return;
-  }
   const long ci = (long)p * D.BM + b;
   const int it = *D.iter;
   float u[12], z[9];
@@ -394,6 +462,7 @@ __global__ void __launch_bounds__(128) k_plan_sample(PlanDev D, ArmK A, long nsl
     D.valid[ci] = 0;
     float4* o4 = reinterpret_cast<float4*>(D.cand + ci * 16);
     o4[0] = o4[1] = o4[2] = o4[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+    goal_query(D, p, b, false);
     return;
   }
   float qd[7];
@@ -409,6 +478,7 @@ __global__ void __launch_bounds__(128) k_plan_sample(PlanDev D, ArmK A, long nsl
   o4[1] = make_float4(q[4], q[5], q[6], 0.f);
   o4[2] = make_float4(qd[0], qd[1], qd[2], qd[3]);
   o4[3] = make_float4(qd[4], qd[5], qd[6], 0.f);
+  goal_query(D, p, b, ok);
 }
 
 // ---------------------------------------------------------------------------
@@ -509,26 +579,39 @@ constexpr int kKnnSmem = PL_KNN_WARPS * PL_KNN_RING * 7 * 32 * 16;
 // shared memory, PL_KNN_RING - 1 blocks ahead; each lane copies (cp.async)
 // and later reads only its own 16-byte words, so the ring needs no barrier.
 template <int KM>
-__global__ void __launch_bounds__(32 * PL_KNN_WARPS) k_plan_knn(PlanDev D) {
+__global__ void __launch_bounds__(32 * PL_KNN_WARPS) k_plan_knn(PlanDev D, int kind) {
   pdl_begin();
   extern __shared__ float4 knn_ring[];   // [warp][slot][7][32]
   const Sched* S = D.sched;
-  const int items = S->knn_items;
+  const int items = kind == 0 ? S->knn_items[0] : S->gq_n * S->nsg_max;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   float4* ring = knn_ring + (long)w * PL_KNN_RING * 7 * 32 + lane;
   const float2 w2 = make_float2(D.w_vel, D.w_vel);
   Sched* Sw = D.sched;
   for (;;) {   // each warp claims items until none are left
     int item = 0;
-    if (lane == 0) item = atomicAdd(&Sw->knn_head, 1);
+    if (lane == 0) item = atomicAdd(&Sw->knn_head[kind], 1);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= items) break;
-    const int p = find_problem(S->knn_off, D.P, item);
-    const int local = item - S->knn_off[p];
-    const int ns = S->nsplit[p];
-    const int g = local / ns, split = local - g * ns;
-    const int B = min(max(D.prob[p].batch, 0), D.BM);
-    const int b0 = g * PL_KNN_QW;
+    int p, ns, split, b0, B;
+    if (kind == 0) {   // free queries [G, B) of problem p, PL_KNN_QW per item
+      p = find_problem(S->knn_off[0], D.P, item);
+      const int local = item - S->knn_off[0][p];
+      ns = S->nsplit[0][p];
+      const int g = local / ns;
+      split = local - g * ns;
+      B = min(max(D.prob[p].batch, 0), D.BM);
+      b0 = min(max(D.prob[p].n_goal, 0), B) + g * PL_KNN_QW;
+    } else {           // one decoded goal query per item: (list entry, split)
+      const int v = item / S->nsg_max;
+      split = item - v * S->nsg_max;
+      const int2 e = D.gq[v];
+      p = e.x;
+      ns = S->nsplit[1][p];
+      if (split >= ns) continue;                 // warp-uniform: a smaller tree
+      b0 = e.y;
+      B = e.y + 1;
+    }
     // candidates whose decoding failed get no parents (their edges are
     // invalid whatever the lists hold)
     bool wact = false;                         // warp-uniform
@@ -1883,30 +1966,50 @@ template <class Mark>
 static void enqueue_front(fn_planner* pl, unsigned flags, cudaStream_t st, Mark&& mark) {
   PlanDev& D = pl->D;
   const int P = pl->cfg.P;
-  {
-    // external candidates: only the parent-search preparation runs
-    const long n = (flags & FN_PLAN_EXTERNAL) ? 0 : (long)P * D.BM;
-    const int prep = pl->cfg.k > 1 ? 4 * num_sms() : 0;
-    if (n + prep > 0) {
-      pl_launch(k_plan_sample, (unsigned)((32 * (n + prep) + 127) / 128), 128, 0, st, D, pl->arm,
-                n, prep, (flags & FN_PLAN_DENSITY) ? 1 : 0);
-      trace(pl, st, "k_plan_sample");
-    }
-    if (n > 0 && (flags & FN_PLAN_CHORD)) {
-      pl_launch(k_plan_chord, P, PL_CHORD_THREADS, 0, st, D, pl->arm);
-      trace(pl, st, "k_plan_chord");
-    }
+  const bool knn = pl->cfg.k > 1;
+  // external candidates: only the parent-search preparation runs
+  const long n = (flags & FN_PLAN_EXTERNAL) ? 0 : (long)P * D.BM;
+  const int prep = knn ? 4 * num_sms() : 0;
+  const int dens = (flags & FN_PLAN_DENSITY) ? 1 : 0;
+  auto search = [&](int kind) {
+    if (!knn) return;
+    // the goal list is short (the decoded goals): a small grid claims it
+    const int gb = 2 * num_sms();
+    if (D.KM == 8)
+      pl_launch(k_plan_knn<8>, kind == 0 ? knn_blocks<8>(pl) : std::min(gb, knn_blocks<8>(pl)),
+                32 * PL_KNN_WARPS, kKnnSmem, st, D, kind);
+    else
+      pl_launch(k_plan_knn<16>, kind == 0 ? knn_blocks<16>(pl) : std::min(gb, knn_blocks<16>(pl)),
+                32 * PL_KNN_WARPS, kKnnSmem, st, D, kind);
+    trace(pl, st, "k_plan_knn");
+  };
+  auto goals = [&](int late) {
+    pl_launch(k_plan_sample, (unsigned)((32 * n + 127) / 128), 128, 0, st, D, pl->arm, n, 0, dens,
+              1, late);
+    trace(pl, st, "k_plan_sample");
+  };
+  if (n + prep > 0) {
+    const long warps = (n + 31) / 32 + prep;
+    pl_launch(k_plan_sample, (unsigned)((32 * warps + 127) / 128), 128, 0, st, D, pl->arm, n,
+              prep, dens, 0, 0);
+    trace(pl, st, "k_plan_prep");
+  }
+  if (n > 0 && knn && !(flags & FN_PLAN_CHORD) && !pl->tracing) {
+    // the free queries' parent search runs beside the goal chart's IK
+    mark(2);
+    search(0);
+    goals(1);
+    search(1);
+    return;
+  }
+  if (n > 0) goals(0);
+  if (n > 0 && (flags & FN_PLAN_CHORD)) {
+    pl_launch(k_plan_chord, P, PL_CHORD_THREADS, 0, st, D, pl->arm);
+    trace(pl, st, "k_plan_chord");
   }
   mark(2);
-  if (pl->cfg.k > 1) {
-    if (D.KM == 8) {
-      pl_launch(k_plan_knn<8>, knn_blocks<8>(pl), 32 * PL_KNN_WARPS, kKnnSmem, st, D);
-      trace(pl, st, "k_plan_knn");
-    } else {
-      pl_launch(k_plan_knn<16>, knn_blocks<16>(pl), 32 * PL_KNN_WARPS, kKnnSmem, st, D);
-      trace(pl, st, "k_plan_knn");
-    }
-  }
+  search(0);
+  search(1);
 }
 
 #define PL_VSTAGES 2
@@ -2045,7 +2148,7 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
   D.sur_list = nullptr;
   A_(D.sur_n, 1);
   A_(D.knn_cnt, P * BM);
-  A_(D.dens, P); A_(D.arch, P); A_(D.cz, P * BM * 9); A_(D.zn, P * NC * 9); A_(D.glist, P * BM);
+  A_(D.dens, P); A_(D.arch, P); A_(D.cz, P * BM * 9); A_(D.zn, P * NC * 9); A_(D.glist, P * BM); A_(D.gq, P * BM);
   D.scfg = default_sampler_cfg();
   if (rc == FN_OK) {
     std::vector<fn_density_t> th(P);
