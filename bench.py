@@ -329,9 +329,10 @@ FLOP_PER_PAIR = 44             # one (query, node) distance of the parent search
 FLOP_PER_IK_START = 25987      # one damped-least-squares start, 24 iterations + final check
 
 # DRAM bytes (read + written) per launch from one ncu capture of the kernel on
-# this workload (profiles/plan_kernels_tree4096_batch2048.md); an entry is
-# removed when its kernel changes, and the roofline then reports null
-MEASURED_DRAM_BYTES = {"k_plan_probe": 1097472}
+# this workload, the mean over its launches in one iteration, as `achieved`
+# is (profiles/plan_kernels_tree4096_batch2048.md); an entry is removed when
+# its kernel changes, and the roofline then reports null
+MEASURED_DRAM_BYTES = {"k_plan_knn": 287104, "k_plan_sample": 213888, "k_plan_probe": 1097472}
 
 
 def kernel_table(traced):
