@@ -333,6 +333,10 @@ FLOP_PER_IK_START = 25987      # one damped-least-squares start, 24 iterations +
 # is (profiles/plan_kernels_tree4096_batch2048.md); an entry is removed when
 # its kernel changes, and the roofline then reports null
 MEASURED_DRAM_BYTES = {"k_plan_knn": 287104, "k_plan_sample": 213888, "k_plan_probe": 1097472}
+# algorithmic bytes of one parent-search launch on this workload: the 4096
+# tree rows and the 2048 queries at 56 B (14 floats), the 2048 lists of 7
+# parents at 8 B per entry, halved over the iteration's two launches
+KNN_ALGO_BYTES = (56 * (4096 + 2048) + 8 * 2048 * 7) // 2
 
 
 def kernel_table(traced):
@@ -384,6 +388,17 @@ def roofline_from_trace(traced, work, workload="iteration"):
             n, f, _ = units[k]
             edge[k] = {"ms": tab[k]["ms"], "tflops": n * f / (tab[k]["ms"] / 1e3) / 1e12}
     out["edge_kernels"] = edge
+    # the parent search's memory side: its DRAM traffic (ncu) and its
+    # algorithmic bytes (tree rows and queries, 56 B each, and the k-lists)
+    # over its event-timed duration
+    if "k_plan_knn" in tab:
+        t = tab["k_plan_knn"]["ms"] / tab["k_plan_knn"]["launches"] / 1e3
+        b = MEASURED_DRAM_BYTES.get("k_plan_knn") if workload == "iteration" else None
+        out["knn_memory"] = {"dram_gbs": None if b is None else b / t / 1e9,
+                             "algorithmic_bytes_per_launch": KNN_ALGO_BYTES,
+                             "algorithmic_gbs": KNN_ALGO_BYTES / t / 1e9,
+                             "note": "the tree and its mirror are L2-resident: the search is "
+                                     "bound by latency, not by HBM"}
     return out
 
 

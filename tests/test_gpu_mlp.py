@@ -212,3 +212,40 @@ def test_training_reduces_loss_and_window_hits(S, arm):
     assert hit > 0.3, hit
     assert agree > 0.99, agree
     mlp.close()
+
+
+def test_trained_window_saves_work(S, arm):
+    """What the trained network gains over the method without it: on the same
+    edges, with identical chosen durations, its window pass needs fewer torque
+    evaluations than the full scan and than the window of an untrained
+    network (whose misses fall back to the full scan)."""
+    import torch
+    from paper_2609_22608_gb300 import ops
+    E, K, Sc = 32768, 128, 32
+    s0, s1 = synth.random_edges(arm, E, 20)
+    d0, d1 = dev(s0), dev(s1)
+    grid = synth.duration_grid(K)
+    lab = S.label_edges(arm, d0, d1, grid, Sc)
+    trained = S.MLP(max_batch=4096, seed=0)
+    S.train(trained, arm, d0, d1, lab, grid, epochs=3, batch=4096, lr=2e-3)
+    untrained = S.MLP(max_batch=4096, seed=0)
+    t0, t1 = synth.random_edges(arm, 4096, 21)
+    e0, e1 = dev(t0), dev(t1)
+
+    def evaluations(fn):
+        c = torch.zeros(1, dtype=torch.int64, device="cuda")
+        out = fn(c)
+        torch.cuda.synchronize()
+        return int(c.item()), out
+
+    n_full, full = evaluations(lambda c: ops.time_edges(arm, e0, e1, grid, Sc, sample_count=c))
+    n_tr, w_tr = evaluations(lambda c: S.time_edges_window(
+        arm, e0, e1, grid, Sc, trained.predict(arm, e0, e1), W=16, sample_count=c))
+    n_un, w_un = evaluations(lambda c: S.time_edges_window(
+        arm, e0, e1, grid, Sc, untrained.predict(arm, e0, e1), W=16, sample_count=c))
+    trained.close()
+    untrained.close()
+    assert (w_tr["k_star"] == full["k_star"]).float().mean().item() > 0.99
+    assert (w_un["k_star"] == full["k_star"]).float().mean().item() > 0.99
+    assert n_tr < 0.9 * n_full, (n_tr, n_full)
+    assert n_tr < n_un, (n_tr, n_un)
