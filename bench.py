@@ -164,10 +164,19 @@ def cpu_baseline(w, budget_s=15.0):
     t0 = time.perf_counter()
     e, out, case = oracle_round(orc, w, ng, nf)
     dt = time.perf_counter() - t0
+    # the same oracle on one core, on a smaller sample (about a fifth of the budget)
+    orc.set_threads(1)
+    n1 = max(4, nf // 8)
+    t0 = time.perf_counter()
+    e1, _, _ = oracle_round(orc, w, max(8, ng // 8), n1)
+    dt1 = time.perf_counter() - t0
+    orc.set_threads(cores)
     return {"value": e / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_core_value": e1 / dt1,
             "sample": f"one round of the same iteration on {case['cand'].shape[0]} candidates "
                       f"({case['n_goal']} valid goals of {ng} drawn + {nf} free) x {K_PAR} "
-                      f"parents = {e} edges, FP64 C oracle (OpenMP over edges), {dt:.1f} s"}
+                      f"parents = {e} edges, FP64 C oracle (OpenMP over edges), {dt:.1f} s; "
+                      f"single core: {e1} edges in {dt1:.1f} s"}
 
 
 def verify_sample(w):
