@@ -154,10 +154,16 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K,
         }
 }
 
+// The training GEMMs with a 256-wide output run on the tensor cores
+// (tcgen05, gemm_tc); the two-column ones of layer 4 on mma.sync tiles.
 template <bool TA, bool TB>
 static void gemm(int M, int N, int K, const bf16* A, int lda, const bf16* B, int ldb,
                  const float* bias, bool relu, bool accumulate, float* Cf, int ldcf, bf16* Cb,
-                 int ldcb, cudaStream_t st) {
+                 int ldcb, int* err, cudaStream_t st) {
+  if (N >= 128) {
+    gemm_tc<TA, TB>(M, N, K, A, lda, B, ldb, bias, relu, accumulate, Cf, ldcf, Cb, ldcb, err, st);
+    return;
+  }
   dim3 grid((N + 63) / 64, (M + 63) / 64);
   k_gemm_bf16<TA, TB><<<grid, 128, 0, st>>>(M, N, K, A, lda, B, ldb, bias, relu ? 1 : 0,
                                             accumulate ? 1 : 0, Cf, ldcf, Cb, ldcb);
@@ -343,13 +349,13 @@ extern "C" fn_status fn_mlp_create(int max_batch, unsigned long long seed, fn_ml
 // forward pass of n rows whose features are in m->X; Y = output
 static void mlp_forward(fn_mlp* m, int n, cudaStream_t st) {
   gemm<false, false>(n, 256, 32, m->X, 32, m->Wb[0], 256, m->b[0], true, false, nullptr, 0,
-                     m->Hb[0], 256, st);
+                     m->Hb[0], 256, m->tc_err, st);
   gemm<false, false>(n, 256, 256, m->Hb[0], 256, m->Wb[1], 256, m->b[1], true, false, nullptr, 0,
-                     m->Hb[1], 256, st);
+                     m->Hb[1], 256, m->tc_err, st);
   gemm<false, false>(n, 256, 256, m->Hb[1], 256, m->Wb[2], 256, m->b[2], true, false, nullptr, 0,
-                     m->Hb[2], 256, st);
+                     m->Hb[2], 256, m->tc_err, st);
   gemm<false, false>(n, 2, 256, m->Hb[2], 256, m->Wb[3], 2, m->b[3], false, false, m->Y, 2,
-                     nullptr, 0, st);
+                     nullptr, 0, m->tc_err, st);
 }
 
 static fn_status mlp_features(fn_mlp* m, const fn_arm_t* arm, const float* s0, const float* s1,
@@ -431,10 +437,10 @@ static fn_status mlp_backward(fn_mlp* m, int n, const int32_t* kstar, cudaStream
   }
   // layer 4 (linear): dz4 = dy
   gemm<true, false>(256, 2, n, m->Hb[2], 256, m->dYb, 2, nullptr, false, false, m->gW[3], 2,
-                    nullptr, 0, st);
+                    nullptr, 0, m->tc_err, st);
   k_mlp_colsum<<<64, 256, 0, st>>>(m->dY, n, 2, m->gb[3]);
   gemm<false, true>(n, 256, 2, m->dYb, 2, m->Wb[3], 2, nullptr, false, false, m->dH, 256, nullptr,
-                    0, st);
+                    0, m->tc_err, st);
   const int rb = std::max(1, std::min(512, (n + 63) / 64));
   for (int l = 2; l >= 0; --l) {
     // dz_l = dh_l * 1[h_l > 0]; dW_l = h_{l-1}^T dz_l; dh_{l-1} = dz_l W_l^T
@@ -442,10 +448,10 @@ static fn_status mlp_backward(fn_mlp* m, int n, const int32_t* kstar, cudaStream
     const bf16* hin = l == 0 ? m->X : m->Hb[l - 1];
     const int nin = kDims[l];
     gemm<true, false>(nin, 256, n, hin, nin, m->dZb, 256, nullptr, false, false, m->gW[l], 256,
-                      nullptr, 0, st);
+                      nullptr, 0, m->tc_err, st);
     if (l > 0)
       gemm<false, true>(n, 256, 256, m->dZb, 256, m->Wb[l], 256, nullptr, false, false, m->dH, 256,
-                        nullptr, 0, st);
+                        nullptr, 0, m->tc_err, st);
   }
   return launch_status();
 }

@@ -18,6 +18,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "fn_internal.h"
@@ -262,11 +263,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     for (int layer = 0; layer < 3; ++layer) {
       if (tid == 0 && fail) *s_fail = 1;
-      // wait for this layer's accumulator (all threads)
-      if (!*s_fail && !mbar_wait(bar_layer, ph_layer)) *s_fail = 1;
+      __syncthreads();
+      // wait for this layer's accumulator (all threads; a block vote keeps
+      // the decision uniform, so no thread is left at a barrier)
+      const bool lf = *s_fail || !mbar_wait(bar_layer, ph_layer);
       ph_layer ^= 1;
       tc_fence_after();
-      if (*s_fail) break;
+      if (__syncthreads_or(lf)) {
+        *s_fail = 1;
+        break;
+      }
       const float* bias = sBias + 256 * layer;
       if (layer < 2) {
         // epilogue: bias, ReLU, bf16 -> A (K = 256 layout: 32 core matrices per
@@ -375,6 +381,195 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                  "r"((uint32_t)kTmemCols)
                  : "memory");
 }
+
+// ---------------------------------------------------------------------------
+// General BF16 GEMM on the tensor cores for the surrogate's training:
+//   C[M][N] = op(A)[M][K] op(B)[K][N] (+ bias, ReLU), FP32 accumulation in
+//   tensor memory; op(A) = A [M][K] (row-major, lda) or, TA, A^T with A
+//   [K][M]; op(B) = B [K][N] or, TB, B^T with B [N][K].
+// A CTA computes a 128 x 128 tile over the K range of its grid z slice:
+// 128 threads stage 64-column K chunks of both operands into shared memory
+// in the canonical K-major layout (transposing as they load), two stages
+// deep; one thread issues four tcgen05.mma (K = 16) per chunk and commits
+// them to the stage's barrier; the epilogue reads the accumulator back
+// (warp w: lanes 32w..32w+31) and stores FP32 and / or BF16, or adds FP32
+// partial sums atomically when the K range is split.  Waits are bounded as
+// in the fused forward.
+// ---------------------------------------------------------------------------
+constexpr int kGM = 128, kGN = 128, kGK = 64;
+constexpr int kGTile = kGM * kGK * 2;               // 16 KB per operand tile
+constexpr int kGStage = 2 * kGTile;                 // A and B
+constexpr int kGSmem = 2 * kGStage + 64;            // two stages + barriers
+constexpr uint32_t kGIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                             ((uint32_t)(kGN >> 3) << 17) | ((uint32_t)(kGM >> 4) << 24);
+
+__device__ __forceinline__ void umma_g(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kGIdesc), "r"(acc)
+      : "memory");
+}
+
+// byte offset of element (row, k) of a 128 x 64 tile in the canonical
+// K-major layout: 8 x 8 core matrices of 128 B, K-adjacent ones 128 B apart,
+// 8-row groups 1024 B apart
+__device__ __forceinline__ int g_off(int row, int k) {
+  return ((row >> 3) * (kGK / 8) + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(128, 1)
+    k_gemm_tc(int M, int N, int K, int kslice, const bf16* __restrict__ A, int lda,
+              const bf16* __restrict__ B, int ldb, const float* __restrict__ bias, int relu,
+              int accumulate, int atomic, float* __restrict__ Cf, int ldcf, bf16* __restrict__ Cb,
+              int ldcb, int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * kGM, n0 = blockIdx.x * kGN;
+  const int k0 = blockIdx.z * kslice, k1 = min(K, k0 + kslice);
+  if (k0 >= k1) return;                              // block-uniform, before any barrier
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * kGStage);
+  volatile uint32_t* s_tmem = reinterpret_cast<volatile uint32_t*>(smem + 2 * kGStage + 32);
+  volatile int* s_fail = reinterpret_cast<volatile int*>(smem + 2 * kGStage + 36);
+  const uint32_t base = su32(smem), bar0 = su32(bars);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     su32((const void*)s_tmem)),
+                 "r"((uint32_t)kGN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(bar0, 1);
+    mbar_init(bar0 + 8, 1);
+    *s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+  const bf16 zero = __float2bfloat16_rn(0.f);
+  const int nk = (k1 - k0 + kGK - 1) / kGK;
+  for (int c = 0; c < nk; ++c) {
+    const int st = c & 1;
+    // the MMAs that read this stage two chunks ago must be done (a block
+    // vote keeps the decision uniform, so no thread is left at a barrier)
+    const bool f = c >= 2 && !mbar_wait(bar0 + 8 * st, ((c - 2) >> 1) & 1);
+    if (__syncthreads_or(f)) {
+      *s_fail = 1;
+      break;
+    }
+    uint8_t* sa = smem + st * kGStage;
+    uint8_t* sb = sa + kGTile;
+    const int kc = k0 + c * kGK;
+    // A tile: (row m, col k); the contiguous global index fastest
+    for (int t = tid; t < kGM * kGK; t += 128) {
+      int r, k;
+      if (TA) { r = t & (kGM - 1); k = t >> 7; } else { r = t >> 6; k = t & (kGK - 1); }
+      const int gm = m0 + r, gk = kc + k;
+      bf16 v = zero;
+      if (gm < M && gk < k1) v = TA ? A[(long)gk * lda + gm] : A[(long)gm * lda + gk];
+      *reinterpret_cast<bf16*>(sa + g_off(r, k)) = v;
+    }
+    // B tile: (row n, col k)
+    for (int t = tid; t < kGN * kGK; t += 128) {
+      int r, k;
+      if (TB) { r = t >> 6; k = t & (kGK - 1); } else { r = t & (kGN - 1); k = t >> 7; }
+      const int gn = n0 + r, gk = kc + k;
+      bf16 v = zero;
+      if (gn < N && gk < k1) v = TB ? B[(long)gn * ldb + gk] : B[(long)gk * ldb + gn];
+      *reinterpret_cast<bf16*>(sb + g_off(r, k)) = v;
+    }
+    proxy_fence();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a = base + st * kGStage, b = a + kGTile;
+#pragma unroll
+      for (int j = 0; j < kGK / 16; ++j)
+        umma_g(tmem, sdesc(a + j * 256, 128, (kGK / 8) * 128), sdesc(b + j * 256, 128, (kGK / 8) * 128),
+               (c | j) != 0);
+      umma_commit(bar0 + 8 * st);
+    }
+  }
+  // the last chunk's MMAs (every earlier one completes before it)
+  const int last = nk - 1;
+  const bool bad = *s_fail || !mbar_wait(bar0 + 8 * (last & 1), (last >> 1) & 1);
+  if (__syncthreads_or(bad)) *s_fail = 1;
+  tc_fence_after();
+  if (!*s_fail) {
+    const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int cb = 0; cb < kGN / 32; ++cb) {
+      uint32_t v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + cb * 32, v);
+      if (row < M) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = n0 + cb * 32 + j;
+          if (col >= N) continue;
+          float x = __uint_as_float(v[j]) + (bias ? bias[col] : 0.f);
+          if (relu) x = fmaxf(x, 0.f);
+          if (Cf) {
+            float* o = Cf + (long)row * ldcf + col;
+            if (atomic) atomicAdd(o, x);
+            else *o = accumulate ? *o + x : x;
+          }
+          if (Cb) Cb[(long)row * ldcb + col] = __float2bfloat16_rn(x);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (*s_fail && tid == 0) atomicExch(err, 1);
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"((uint32_t)kGN)
+                 : "memory");
+}
+
+template <bool TA, bool TB>
+void gemm_tc(int M, int N, int K, const bf16* A, int lda, const bf16* B, int ldb,
+             const float* bias, bool relu, bool accumulate, float* Cf, int ldcf, bf16* Cb,
+             int ldcb, int* err, cudaStream_t st) {
+  static bool attr[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr[dev]) {
+    cudaFuncSetAttribute(k_gemm_tc<TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem);
+    attr[dev] = true;
+  }
+  const int gx = (N + kGN - 1) / kGN, gy = (M + kGM - 1) / kGM;
+  // split a long K over the grid's z so that every SM gets a CTA; the
+  // slices add FP32 partial sums atomically into a zeroed C
+  int slices = 1;
+  const int want = num_sms() / std::max(1, gx * gy);
+  if (want > 1 && K > 8 * kGK && !Cb && Cf && !bias && !relu) {
+    slices = std::min(want, (K + 4 * kGK - 1) / (4 * kGK));
+    if (slices > 1 && !accumulate) {
+      if (ldcf == N)
+        cudaMemsetAsync(Cf, 0, sizeof(float) * (size_t)M * N, st);
+      else
+        for (int r = 0; r < M; ++r) cudaMemsetAsync(Cf + (long)r * ldcf, 0, sizeof(float) * N, st);
+    }
+  }
+  const int kslice = slices > 1 ? ((K + slices - 1) / slices + kGK - 1) / kGK * kGK : K;
+  slices = (K + kslice - 1) / kslice;
+  k_gemm_tc<TA, TB><<<dim3(gx, gy, slices), 128, kGSmem, st>>>(
+      M, N, K, kslice, A, lda, B, ldb, bias, relu ? 1 : 0, accumulate ? 1 : 0, slices > 1 ? 1 : 0,
+      Cf, ldcf, Cb, ldcb, err);
+}
+
+template void gemm_tc<false, false>(int, int, int, const bf16*, int, const bf16*, int, const float*,
+                                    bool, bool, float*, int, bf16*, int, int*, cudaStream_t);
+template void gemm_tc<true, false>(int, int, int, const bf16*, int, const bf16*, int, const float*,
+                                   bool, bool, float*, int, bf16*, int, int*, cudaStream_t);
+template void gemm_tc<false, true>(int, int, int, const bf16*, int, const bf16*, int, const float*,
+                                   bool, bool, float*, int, bf16*, int, int*, cudaStream_t);
 
 void mlp_tc_pack(const bf16* W, int K, int Kt, bf16* out, cudaStream_t st) {
   const long n = (long)K * kTcN;

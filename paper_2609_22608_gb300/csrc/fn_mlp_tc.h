@@ -36,6 +36,17 @@ fn_status mlp_tc_forward(const ArmK& A, const float* s0, const float* s1, int E,
                          const float* b4, float* Y, int* err, cudaStream_t st,
                          const int* E_dev = nullptr);
 
+// General BF16 GEMM on the tensor cores (FP32 accumulation):
+// C = op(A) op(B) (+ bias, ReLU), op = transpose when TA / TB (see
+// fn_mlp_tc.cu); C as FP32 (Cf, overwritten or, `accumulate`, added to) and
+// / or BF16 (Cb).  A long K without bias, ReLU or BF16 output is split over
+// CTAs whose FP32 partial sums are added atomically.  *err is set to 1 if a
+// wait on the tensor core timed out.
+template <bool TA, bool TB>
+void gemm_tc(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
+             const float* bias, bool relu, bool accumulate, float* Cf, int ldcf,
+             __nv_bfloat16* Cb, int ldcb, int* err, cudaStream_t st);
+
 }  // namespace fn
 
 struct fn_mlp;
