@@ -154,13 +154,14 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K,
         }
 }
 
-// The training GEMMs with a 256-wide output run on the tensor cores
-// (tcgen05, gemm_tc); the two-column ones of layer 4 on mma.sync tiles.
+// The training GEMMs with a 256-wide output (and 16-byte aligned rows) run
+// on the tensor cores (tcgen05, gemm_tc); the two-column ones of layer 4 on
+// mma.sync tiles.
 template <bool TA, bool TB>
 static void gemm(int M, int N, int K, const bf16* A, int lda, const bf16* B, int ldb,
                  const float* bias, bool relu, bool accumulate, float* Cf, int ldcf, bf16* Cb,
                  int ldcb, int* err, cudaStream_t st) {
-  if (N >= 128) {
+  if (N >= 128 && lda % 8 == 0 && ldb % 8 == 0 && aligned16(A) && aligned16(B)) {
     gemm_tc<TA, TB>(M, N, K, A, lda, B, ldb, bias, relu, accumulate, Cf, ldcf, Cb, ldcb, err, st);
     return;
   }

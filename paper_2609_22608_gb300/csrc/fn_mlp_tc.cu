@@ -389,8 +389,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 //   [K][M]; op(B) = B [K][N] or, TB, B^T with B [N][K].
 // A CTA computes a 128 x 128 tile over the K range of its grid z slice:
 // 128 threads stage 64-column K chunks of both operands into shared memory
-// in the canonical K-major layout (transposing as they load), two stages
-// deep; one thread issues four tcgen05.mma (K = 16) per chunk and commits
+// in the canonical K-major layout with 16-byte loads (stage_tile), two
+// stages deep; one thread issues four tcgen05.mma (K = 16) per chunk and commits
 // them to the stage's barrier; the epilogue reads the accumulator back
 // (warp w: lanes 32w..32w+31) and stores FP32 and / or BF16, or adds FP32
 // partial sums atomically when the K range is split.  Waits are bounded as
@@ -399,7 +399,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 constexpr int kGM = 128, kGN = 128, kGK = 64;
 constexpr int kGTile = kGM * kGK * 2;               // 16 KB per operand tile
 constexpr int kGStage = 2 * kGTile;                 // A and B
-constexpr int kGSmem = 2 * kGStage + 64;            // two stages + barriers
+constexpr int kGScrW = kGM + 8;                     // transpose scratch row (bf16), padded
+constexpr int kGScr = kGK * kGScrW * 2;             // 17 KB
+constexpr int kGSmem = 2 * kGStage + kGScr + 64;    // two stages, scratch, barriers
 constexpr uint32_t kGIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
                              ((uint32_t)(kGN >> 3) << 17) | ((uint32_t)(kGM >> 4) << 24);
 
@@ -418,6 +420,67 @@ __device__ __forceinline__ int g_off(int row, int k) {
   return ((row >> 3) * (kGK / 8) + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2;
 }
 
+// Stage one 128 x 64 operand tile (rows r0.., columns kc..) into the
+// canonical layout at dst.  KC: the source is contiguous along K (element
+// (r, k) at src[r * ld + k]): 16-byte vectors are whole core-matrix rows.
+// Otherwise (element (r, k) at src[k * ld + r]) 16-byte vectors along r go
+// to a padded row-major scratch, and each thread then gathers 8 K values of
+// one row into a 16-byte store.  Elements past R rows or k1 columns are 0.
+// Rows of 8 elements must be 16-byte aligned (ld % 8 == 0, aligned base).
+template <bool KC>
+__device__ __forceinline__ void stage_tile(uint8_t* dst, const bf16* __restrict__ src, int ld,
+                                           int r0, int R, int kc, int k1, bf16* scr, int tid) {
+  const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
+  if (KC) {
+    for (int v = tid; v < kGM * (kGK / 8); v += 128) {
+      const int r = v >> 3, k = (v & 7) * 8;
+      const int gr = r0 + r, gk = kc + k;
+      uint4 x = z4;
+      if (gr < R && gk < k1) {
+        const bf16* p = src + (long)gr * ld + gk;
+        if (gk + 8 <= k1) {
+          x = *reinterpret_cast<const uint4*>(p);
+        } else {
+          alignas(16) bf16 e[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) e[i] = gk + i < k1 ? p[i] : __float2bfloat16_rn(0.f);
+          x = *reinterpret_cast<const uint4*>(e);
+        }
+      }
+      *reinterpret_cast<uint4*>(dst + g_off(r, k)) = x;
+    }
+  } else {
+    for (int v = tid; v < kGK * (kGM / 8); v += 128) {
+      const int k = v >> 4, rv = (v & 15) * 8;
+      const int gk = kc + k, gr = r0 + rv;
+      uint4 x = z4;
+      if (gk < k1 && gr < R) {
+        const bf16* p = src + (long)gk * ld + gr;
+        if (gr + 8 <= R) {
+          x = *reinterpret_cast<const uint4*>(p);
+        } else {
+          alignas(16) bf16 e[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) e[i] = gr + i < R ? p[i] : __float2bfloat16_rn(0.f);
+          x = *reinterpret_cast<const uint4*>(e);
+        }
+      }
+      *reinterpret_cast<uint4*>(scr + k * kGScrW + rv) = x;
+    }
+    __syncthreads();
+    for (int v = tid; v < kGM * (kGK / 8); v += 128) {
+      const int r = v & (kGM - 1), k = (v >> 7) * 8;
+      uint32_t w[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        w[i] = (uint32_t)__bfloat16_as_ushort(scr[(k + 2 * i) * kGScrW + r]) |
+               ((uint32_t)__bfloat16_as_ushort(scr[(k + 2 * i + 1) * kGScrW + r]) << 16);
+      *reinterpret_cast<uint4*>(dst + g_off(r, k)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    __syncthreads();   // the scratch is reused by the next tile
+  }
+}
+
 template <bool TA, bool TB>
 __global__ void __launch_bounds__(128, 1)
     k_gemm_tc(int M, int N, int K, int kslice, const bf16* __restrict__ A, int lda,
@@ -429,9 +492,10 @@ __global__ void __launch_bounds__(128, 1)
   const int m0 = blockIdx.y * kGM, n0 = blockIdx.x * kGN;
   const int k0 = blockIdx.z * kslice, k1 = min(K, k0 + kslice);
   if (k0 >= k1) return;                              // block-uniform, before any barrier
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * kGStage);
-  volatile uint32_t* s_tmem = reinterpret_cast<volatile uint32_t*>(smem + 2 * kGStage + 32);
-  volatile int* s_fail = reinterpret_cast<volatile int*>(smem + 2 * kGStage + 36);
+  bf16* scr = reinterpret_cast<bf16*>(smem + 2 * kGStage);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * kGStage + kGScr);
+  volatile uint32_t* s_tmem = reinterpret_cast<volatile uint32_t*>(smem + 2 * kGStage + kGScr + 32);
+  volatile int* s_fail = reinterpret_cast<volatile int*>(smem + 2 * kGStage + kGScr + 36);
   const uint32_t base = su32(smem), bar0 = su32(bars);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
@@ -464,24 +528,8 @@ __global__ void __launch_bounds__(128, 1)
     uint8_t* sa = smem + st * kGStage;
     uint8_t* sb = sa + kGTile;
     const int kc = k0 + c * kGK;
-    // A tile: (row m, col k); the contiguous global index fastest
-    for (int t = tid; t < kGM * kGK; t += 128) {
-      int r, k;
-      if (TA) { r = t & (kGM - 1); k = t >> 7; } else { r = t >> 6; k = t & (kGK - 1); }
-      const int gm = m0 + r, gk = kc + k;
-      bf16 v = zero;
-      if (gm < M && gk < k1) v = TA ? A[(long)gk * lda + gm] : A[(long)gm * lda + gk];
-      *reinterpret_cast<bf16*>(sa + g_off(r, k)) = v;
-    }
-    // B tile: (row n, col k)
-    for (int t = tid; t < kGN * kGK; t += 128) {
-      int r, k;
-      if (TB) { r = t >> 6; k = t & (kGK - 1); } else { r = t & (kGN - 1); k = t >> 7; }
-      const int gn = n0 + r, gk = kc + k;
-      bf16 v = zero;
-      if (gn < N && gk < k1) v = TB ? B[(long)gn * ldb + gk] : B[(long)gk * ldb + gn];
-      *reinterpret_cast<bf16*>(sb + g_off(r, k)) = v;
-    }
+    stage_tile<!TA>(sa, A, lda, m0, M, kc, k1, scr, tid);   // (m, k)
+    stage_tile<TB>(sb, B, ldb, n0, N, kc, k1, scr, tid);    // (n, k)
     proxy_fence();
     __syncthreads();
     if (tid == 0) {
