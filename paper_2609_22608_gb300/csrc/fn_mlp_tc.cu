@@ -430,51 +430,56 @@ __device__ __forceinline__ int g_off(int row, int k) {
 template <bool KC>
 __device__ __forceinline__ void stage_tile(uint8_t* dst, const bf16* __restrict__ src, int ld,
                                            int r0, int R, int kc, int k1, bf16* scr, int tid) {
-  const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
-  if (KC) {
-    for (int v = tid; v < kGM * (kGK / 8); v += 128) {
-      const int r = v >> 3, k = (v & 7) * 8;
-      const int gr = r0 + r, gk = kc + k;
-      uint4 x = z4;
-      if (gr < R && gk < k1) {
-        const bf16* p = src + (long)gr * ld + gk;
-        if (gk + 8 <= k1) {
-          x = *reinterpret_cast<const uint4*>(p);
-        } else {
-          alignas(16) bf16 e[8];
+  constexpr int kPer = kGM * (kGK / 8) / 128;   // 16-byte vectors per thread (8)
+  uint4 x[kPer];
+  // all loads first, so that the eight are in flight together
 #pragma unroll
-          for (int i = 0; i < 8; ++i) e[i] = gk + i < k1 ? p[i] : __float2bfloat16_rn(0.f);
-          x = *reinterpret_cast<const uint4*>(e);
-        }
+  for (int i = 0; i < kPer; ++i) {
+    const int v = tid + 128 * i;
+    int gr, gk, lim;   // the vector's first element and its extent along the contiguous index
+    if (KC) {
+      gr = r0 + (v >> 3);
+      gk = kc + (v & 7) * 8;
+    } else {
+      gk = kc + (v >> 4);
+      gr = r0 + (v & 15) * 8;
+    }
+    x[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (gr < R && gk < k1) {
+      const bf16* p = KC ? src + (long)gr * ld + gk : src + (long)gk * ld + gr;
+      lim = KC ? k1 - gk : R - gr;
+      if (lim >= 8) {
+        x[i] = *reinterpret_cast<const uint4*>(p);
+      } else {
+        alignas(16) bf16 e[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) e[j] = j < lim ? p[j] : __float2bfloat16_rn(0.f);
+        x[i] = *reinterpret_cast<const uint4*>(e);
       }
-      *reinterpret_cast<uint4*>(dst + g_off(r, k)) = x;
+    }
+  }
+  if (KC) {
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int v = tid + 128 * i;
+      *reinterpret_cast<uint4*>(dst + g_off(v >> 3, (v & 7) * 8)) = x[i];
     }
   } else {
-    for (int v = tid; v < kGK * (kGM / 8); v += 128) {
-      const int k = v >> 4, rv = (v & 15) * 8;
-      const int gk = kc + k, gr = r0 + rv;
-      uint4 x = z4;
-      if (gk < k1 && gr < R) {
-        const bf16* p = src + (long)gk * ld + gr;
-        if (gr + 8 <= R) {
-          x = *reinterpret_cast<const uint4*>(p);
-        } else {
-          alignas(16) bf16 e[8];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) e[i] = gr + i < R ? p[i] : __float2bfloat16_rn(0.f);
-          x = *reinterpret_cast<const uint4*>(e);
-        }
-      }
-      *reinterpret_cast<uint4*>(scr + k * kGScrW + rv) = x;
+    for (int i = 0; i < kPer; ++i) {
+      const int v = tid + 128 * i;
+      *reinterpret_cast<uint4*>(scr + (v >> 4) * kGScrW + (v & 15) * 8) = x[i];
     }
     __syncthreads();
-    for (int v = tid; v < kGM * (kGK / 8); v += 128) {
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int v = tid + 128 * i;
       const int r = v & (kGM - 1), k = (v >> 7) * 8;
       uint32_t w[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-        w[i] = (uint32_t)__bfloat16_as_ushort(scr[(k + 2 * i) * kGScrW + r]) |
-               ((uint32_t)__bfloat16_as_ushort(scr[(k + 2 * i + 1) * kGScrW + r]) << 16);
+      for (int q = 0; q < 4; ++q)
+        w[q] = (uint32_t)__bfloat16_as_ushort(scr[(k + 2 * q) * kGScrW + r]) |
+               ((uint32_t)__bfloat16_as_ushort(scr[(k + 2 * q + 1) * kGScrW + r]) << 16);
       *reinterpret_cast<uint4*>(dst + g_off(r, k)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
     __syncthreads();   // the scratch is reused by the next tile
