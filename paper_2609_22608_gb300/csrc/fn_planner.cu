@@ -41,6 +41,9 @@
 #define PL_KNN_QW 1                           // queries per warp
 #define PL_KNN_SPAN 4096                      // nodes per split (at least)
 #define PL_KNN_SPAN_GOAL 512                  // the same for goal queries (few, and late)
+#ifndef PL_KNN_SPAN_MIN
+#define PL_KNN_SPAN_MIN 1024                  // smallest split of a free query's search
+#endif
 #define PL_MAX_P 1024
 #define PL_MAX_KEV 40                         // launches traced per iteration
 #define PL_NCOUNT 8   // work counters: probe, verify, mid-probe, kNN pairs, IK starts,
@@ -88,6 +91,7 @@ struct Sched {
 
 struct PlanDev {  // device pointers, passed by value to the kernels
   int P, NC, BM, KP, KN, KM, K, S, S_clear, G;
+  int knn_slots;      // resident warps of the parent search's persistent grid
   float w_vel, vel_frac, margin;
   float* st;          // [P][NC][16]
   float* t;           // [P][NC]
@@ -230,6 +234,16 @@ __global__ void k_plan_schedule(PlanDev D) {
   pdl_begin();
   if (threadIdx.x != 0) return;
   Sched* S = D.sched;
+  // free queries over all problems: with fewer query groups than resident
+  // warps of the parent search, each query's nodes are split further so
+  // that every warp gets an item (splits of at least PL_KNN_SPAN_MIN nodes)
+  int qf = 0;
+  for (int p = 0; p < D.P; ++p) {
+    const int B = min(max(D.prob[p].batch, 0), D.BM);
+    const int G = min(max(D.prob[p].n_goal, 0), B);
+    if (D.KN > 0 && D.n_nodes[p] > 1) qf += (B - G + PL_KNN_QW - 1) / PL_KNN_QW;
+  }
+  const int fill = qf > 0 ? max(1, D.knn_slots / qf) : 1;
   int fo = 0, go = 0, ko = 0, kg = 0, po = 0, nsg_max = 1;
   for (int p = 0; p < D.P; ++p) {
     const fn_problem_t& P = D.prob[p];
@@ -244,7 +258,8 @@ __global__ void k_plan_schedule(PlanDev D) {
     const int span = D.n_nodes[p] - 1;  // non-root nodes
     int ns = 1, nsg = 1;
     if (D.KN > 0 && span > 0) {
-      ns = min(PL_NSPLIT_MAX, (span + PL_KNN_SPAN - 1) / PL_KNN_SPAN);
+      ns = max((span + PL_KNN_SPAN - 1) / PL_KNN_SPAN, min(fill, span / PL_KNN_SPAN_MIN));
+      ns = min(PL_NSPLIT_MAX, ns);
       nsg = min(PL_NSPLIT_MAX, (span + PL_KNN_SPAN_GOAL - 1) / PL_KNN_SPAN_GOAL);
     }
     S->nsplit[0][p] = ns;
@@ -487,7 +502,8 @@ __device__ __forceinline__ void sample_goal(const PlanDev& D, const ArmK& A, int
 // split's nodes 64 at a time; the k best
 // (d, index) pairs live across lanes 0..KM-1 in ascending order, and only
 // nodes that beat the current k-th pair enter the list, one at a time (a
-// ballot finds them; a shuffle-up opens their slot).
+// ballot finds them; a shuffle-up opens their slot), or by a warp merge
+// when a ballot holds many of them.
 // ---------------------------------------------------------------------------
 
 template <int KM>
@@ -518,6 +534,42 @@ struct WarpTopK {
       td = __shfl_sync(0xffffffffu, d, KM - 1);
       ti = __shfl_sync(0xffffffffu, i, KM - 1);
     }
+  }
+  // The same for many candidates at once (the first block of a split fills
+  // an empty list): the KM smallest of the list and the offered candidates
+  // by KM rounds of a warp argmin, each winner taken out by its owner (node
+  // indices are distinct; the empty entries (inf, max) are all alike).
+  __device__ __forceinline__ void merge(unsigned m, float cd, int ci) {
+    const int lane = threadIdx.x & 31;
+    const bool mine = (m >> lane) & 1u;
+    float ld = lane < KM ? d : INFINITY, xd = mine ? cd : INFINITY;
+    int li = lane < KM ? i : 0x7fffffff, xi = mine ? ci : 0x7fffffff;
+    float nd = INFINITY;
+    int ni = 0x7fffffff;
+#pragma unroll
+    for (int r = 0; r < KM; ++r) {
+      const bool fl = knn_less(ld, li, xd, xi);
+      float bd = fl ? ld : xd;
+      int bi = fl ? li : xi;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float od = __shfl_xor_sync(0xffffffffu, bd, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (knn_less(od, oi, bd, bi)) { bd = od; bi = oi; }
+      }
+      if (lane == r) { nd = bd; ni = bi; }
+      if (ld == bd && li == bi) { ld = INFINITY; li = 0x7fffffff; }
+      else if (xd == bd && xi == bi) { xd = INFINITY; xi = 0x7fffffff; }
+    }
+    d = nd;
+    i = ni;
+    td = __shfl_sync(0xffffffffu, d, KM - 1);
+    ti = __shfl_sync(0xffffffffu, i, KM - 1);
+  }
+  // one at a time for a few candidates, else the merge
+  __device__ __forceinline__ void offer(unsigned m, float cd, int ci) {
+    if (__popc(m) >= 2 * KM) merge(m, cd, ci);
+    else insert(m, cd, ci);
   }
 };
 
@@ -568,7 +620,9 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+#ifndef PL_KNN_RING
 #define PL_KNN_RING 3   // mirror blocks per warp in flight (shared-memory ring)
+#endif
 constexpr int kKnnSmem = PL_KNN_WARPS * PL_KNN_RING * 7 * 32 * 16;
 
 // One warp per (query group, split): lane j takes nodes 2j and 2j+1 of each
@@ -678,10 +732,10 @@ __global__ void __launch_bounds__(32 * PL_KNN_WARPS) k_plan_knn(PlanDev D, int k
       }
 #pragma unroll
       for (int a = 0; a < PL_KNN_QW; ++a) {
-        top[a].insert(__ballot_sync(0xffffffffu, v0 && knn_less(d[a].x, n0, top[a].td, top[a].ti)),
-                      d[a].x, n0);
-        top[a].insert(__ballot_sync(0xffffffffu, v1 && knn_less(d[a].y, n0 + 1, top[a].td, top[a].ti)),
-                      d[a].y, n0 + 1);
+        top[a].offer(__ballot_sync(0xffffffffu, v0 && knn_less(d[a].x, n0, top[a].td, top[a].ti)),
+                     d[a].x, n0);
+        top[a].offer(__ballot_sync(0xffffffffu, v1 && knn_less(d[a].y, n0 + 1, top[a].td, top[a].ti)),
+                     d[a].y, n0 + 1);
       }
     }
     cp_async_wait<0>();
@@ -2111,6 +2165,7 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
   memset(&D, 0, sizeof(D));
   D.P = c.P; D.NC = c.n_cap; D.BM = c.b_max; D.KP = c.k; D.KN = std::max(c.k - 1, 1);
   D.KM = (c.k - 1) <= 8 ? 8 : 16;
+  D.knn_slots = (D.KM == 8 ? knn_blocks<8>(pl) : knn_blocks<16>(pl)) * PL_KNN_WARPS;
   D.K = c.K; D.S = c.S; D.S_clear = c.S_clear; D.G = c.reach_grid;
   D.w_vel = c.w_vel; D.vel_frac = c.vel_frac; D.margin = c.clear_margin;
   const size_t P = c.P, NC = c.n_cap, BM = c.b_max, KP = c.k, KN = D.KN, KM = D.KM;
