@@ -339,9 +339,10 @@ FLOP_PER_IK_START = 25987      # one damped-least-squares start, 24 iterations +
 
 # DRAM bytes (read + written) per launch from one ncu capture of the kernel on
 # this workload, the mean over its launches in one iteration, as `achieved`
-# is (profiles/plan_kernels_tree4096_batch2048.md); an entry is removed when
-# its kernel changes, and the roofline then reports null
-MEASURED_DRAM_BYTES = {"k_plan_knn": 287104, "k_plan_sample": 213888, "k_plan_probe": 1097472}
+# is (profiles/plan_kernels_tree4096_batch2048.md; the parent search from
+# profiles/plan_knn_tree4096_batch2048.md); an entry is removed when its
+# kernel changes, and the roofline then reports null
+MEASURED_DRAM_BYTES = {"k_plan_knn": 308608, "k_plan_sample": 213888, "k_plan_probe": 1097472}
 # algorithmic bytes of one parent-search launch on this workload: the 4096
 # tree rows and the 2048 queries at 56 B (14 floats), the 2048 lists of 7
 # parents at 8 B per entry, halved over the iteration's two launches

@@ -38,9 +38,13 @@
 
 #define PL_NSPLIT_MAX 32
 #define PL_KNN_WARPS 4
+#ifndef PL_KNN_QW
 #define PL_KNN_QW 1                           // queries per warp
+#endif
 #define PL_KNN_SPAN 4096                      // nodes per split (at least)
+#ifndef PL_KNN_SPAN_GOAL
 #define PL_KNN_SPAN_GOAL 512                  // the same for goal queries (few, and late)
+#endif
 #ifndef PL_KNN_SPAN_MIN
 #define PL_KNN_SPAN_MIN 1024                  // smallest split of a free query's search
 #endif
@@ -2066,7 +2070,13 @@ static void enqueue_front(fn_planner* pl, unsigned flags, cudaStream_t st, Mark&
   search(1);
 }
 
-#define PL_VSTAGES 2
+// Packed verification stages before the sequential tail: two where the
+// view holds many edges (each stage pair is two dependent launches, which
+// pay off when thousands of edges fail their first duration), else one.
+// At least one: goal edges, verified at their fixed duration, are decided
+// by the first stage and never reach the tail.
+#define PL_VSTAGE_EDGES 65536
+static int vstages(const PlanDev& D) { return D.Emax >= PL_VSTAGE_EDGES ? 2 : 1; }
 
 // the packed edge phase after the per-edge prep: item scan, probe, verify
 // (over the edges of the view D; mark(i) records the phase boundaries when
@@ -2088,7 +2098,7 @@ static void enqueue_edge_body(fn_planner* pl, const PlanDev& D, int v, int block
   pl_launch(k_plan_vinit, tb, 256, 0, st, D);
   trace(pl, st, "k_plan_vinit");
   int list = 0;
-  for (int stage = 0; stage < PL_VSTAGES; ++stage) {
+  for (int stage = 0; stage < vstages(D); ++stage) {
     pl_launch(plan_vstage_variant(v), blocks, 32 * PL_EDGE_WARPS, 0, st, D, pl->arm, pl->grid, list);
     trace(pl, st, "k_plan_vstage");
     pl_launch(k_plan_vselect, tb, 128, 0, st, D, pl->arm, pl->grid, list);
