@@ -342,7 +342,7 @@ FLOP_PER_IK_START = 25987      # one damped-least-squares start, 24 iterations +
 # is (profiles/plan_kernels_tree4096_batch2048.md; the parent search from
 # profiles/plan_knn_tree4096_batch2048.md); an entry is removed when its
 # kernel changes, and the roofline then reports null
-MEASURED_DRAM_BYTES = {"k_plan_knn": 308608, "k_plan_sample": 213888, "k_plan_probe": 1097472}
+MEASURED_DRAM_BYTES = {"k_plan_knn": 308608, "k_plan_sample": 213888}
 # algorithmic bytes of one parent-search launch on this workload: the 4096
 # tree rows and the 2048 queries at 56 B (14 floats), the 2048 lists of 7
 # parents at 8 B per entry, halved over the iteration's two launches
@@ -364,7 +364,8 @@ def roofline_from_trace(traced, work, workload="iteration"):
     iteration: its algorithmic FLOP (work counter x FLOP per unit) over its
     own event-timed duration, against the derived FP32 peak."""
     tab = kernel_table(traced)
-    units = {"k_plan_probe": (work["probe"], FLOP_PER_SAMPLE, "torque evaluations"),
+    units = {"k_plan_expand": (work["probe"], FLOP_PER_SAMPLE,
+                               "torque evaluations (the end-sample split, three per edge end)"),
              "k_plan_mprobe": (work["mprobe"], FLOP_PER_SAMPLE, "torque evaluations"),
              "k_plan_vstage": (None, FLOP_PER_SAMPLE, "torque evaluations"),
              "k_plan_knn": (work["knn_pairs"], FLOP_PER_PAIR, "(query, node) pairs"),
@@ -393,7 +394,7 @@ def roofline_from_trace(traced, work, workload="iteration"):
                     "flop_per_unit": f})
     # the edge-timing kernels (the RNEA hot path) for reference
     edge = {}
-    for k in ("k_plan_probe", "k_plan_mprobe"):
+    for k in ("k_plan_expand", "k_plan_mprobe"):
         if k in tab:
             n, f, _ = units[k]
             edge[k] = {"ms": tab[k]["ms"], "tflops": n * f / (tab[k]["ms"] / 1e3) / 1e12}

@@ -485,7 +485,8 @@ fn_status fn_planner_autotune(fn_planner_t* pl, const fn_problem_t* probs, int i
 
 /* Durations in ms of the last fn_plan_iteration's phases, from CUDA events
  * recorded on its stream: [0] schedule, [1] sample, [2] parents (kNN),
- * [3] edge prep + item scan, [4] probe (both end samples of every admissible
+ * [3] edge prep + item scan, [4] probe (the end-sample torque split of every
+ * edge with admissible durations, then both end samples of every admissible
  * (edge, duration) item), [5] verify (surviving durations, rho_v, Clear),
  * [6] attach + score, [7] prune, [8] output.  ms: host [9].  FN_EINVAL
  * before the first fn_plan_iteration. */
@@ -506,7 +507,10 @@ fn_status fn_planner_kernel_ms(fn_planner_t* pl, float* ms, const char** names, 
 fn_status fn_planner_sample_count(fn_planner_t* pl, unsigned long long* count, int reset);
 
 /* All work counters of the planner's kernels since creation or the last
- * reset: [0] torque evaluations of the end-sample probe, [1] of the verify
+ * reset: [0] torque evaluations of the end-sample probe (three per end of
+ * every edge with admissible durations: the split of Eq. (torque) into
+ * alpha / T^2 + beta / T + gamma that the per-duration checks then use), [1]
+ * of the verify
  * stages, [2] of the interior-sample probe, [3] (query, node) distance
  * evaluations of the parent search, [4] IK starts run by the goal sampler,
  * [5] edges timed by the surrogate's window pass, [6] of those rescanned

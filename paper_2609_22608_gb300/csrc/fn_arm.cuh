@@ -224,14 +224,16 @@ struct LaneWrench {
   }
 };
 
+// gs, fs: scale of the gravity and friction terms (1 for Eq. (torque); 0
+// gives the mass-matrix-plus-armature product when the velocity is zero)
 template <class Coef, class Sink, class Wr = RegWrench>
 __device__ __forceinline__ void torque_at(const ArmK& A, const Coef& c, float u, Sink&& sink,
-                                          Wr W = Wr()) {
+                                          Wr W = Wr(), float gs = 1.f, float fs = 1.f) {
   float qd[7], ex[7];
   float ct[7], st[7];
   float wx = 0.f, wy = 0.f, wz = 0.f;
   float dwx = 0.f, dwy = 0.f, dwz = 0.f;
-  float ax = A.g0x, ay = A.g0y, az = A.g0z;
+  float ax = A.g0x * gs, ay = A.g0y * gs, az = A.g0z * gs;
 #pragma unroll
   for (int j = 0; j < 7; ++j) {
     float q, v, acc;
@@ -239,7 +241,7 @@ __device__ __forceinline__ void torque_at(const ArmK& A, const Coef& c, float u,
     qd[j] = v;
     // armature and friction (logistic with an IEEE division)
     const float e = expf(-A.f2[j] * (v + A.f3[j]));
-    ex[j] = fmaf(A.arma[j], acc, A.f1[j] / (1.0f + e) - A.foff[j]);
+    ex[j] = fmaf(A.arma[j], acc, fs * (A.f1[j] / (1.0f + e) - A.foff[j]));
     sincosf(q + A.th0[j], &st[j], &ct[j]);
     const float ca = A.ca[j], sa = A.sa[j];
     const float c_ = ct[j], s_ = st[j];
@@ -313,6 +315,53 @@ __device__ __forceinline__ void torque_at(const ArmK& A, const Coef& c, float u,
     nz = Nz + Rnz + cFz + pRz;
     sink(j, nz + ex[j], qd[j]);
   }
+}
+
+// one configuration (q, qd, qdd) handed to torque_at as its "sample"
+struct PointCoef {
+  float q[7], qd[7], qdd[7];
+};
+
+__device__ __forceinline__ void cubic_eval(const PointCoef& c, int j, float, float& q, float& v,
+                                           float& a) {
+  q = c.q[j];
+  v = c.qd[j];
+  a = c.qdd[j];
+}
+
+// Eq. (torque) at an end of the cubic as a function of the duration T.  At
+// u = 0 and u = 1 the position and velocity are the edge's end state,
+// whatever T; only the acceleration depends on T, and it is
+//   u = 0:  qdd = 6 (q1 - q0) / T^2 - (4 qd0 + 2 qd1) / T,
+//   u = 1:  qdd = -6 (q1 - q0) / T^2 + (4 qd1 + 2 qd0) / T.
+// Eq. (torque) is affine in qdd (mass matrix plus armature times qdd, plus
+// the velocity, gravity and friction terms at the end state), so
+//   tau(T) = alpha / T^2 + beta / T + gamma
+// with alpha = (M(q) + I_m) a and beta = (M(q) + I_m) b for the two vectors
+// above, and gamma = tau(q, qd, 0).  One part per call: part 0 writes gamma
+// to out[14..20] and the end velocity to out[21..27]; parts 1 and 2 write
+// alpha to out[0..6] and beta to out[7..13], evaluated with the gravity and
+// friction terms scaled to zero, so that the torque of (q, 0, x) is
+// (M(q) + I_m) x.
+__device__ __forceinline__ void end_torque_part(const ArmK& A, const float* q0, const float* qd0,
+                                                const float* q1, const float* qd1, int end,
+                                                int part, float* out) {
+  PointCoef pc;
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    const float d = q1[j] - q0[j];
+    const float a = end ? -6.0f * d : 6.0f * d;
+    const float b = end ? fmaf(4.0f, qd1[j], 2.0f * qd0[j]) : -fmaf(4.0f, qd0[j], 2.0f * qd1[j]);
+    pc.q[j] = end ? q1[j] : q0[j];
+    pc.qd[j] = part == 0 ? (end ? qd1[j] : qd0[j]) : 0.f;
+    pc.qdd[j] = part == 0 ? 0.f : (part == 1 ? a : b);
+  }
+  const int o = part == 0 ? 14 : 7 * (part - 1);
+  const float on = part == 0 ? 1.f : 0.f;
+  torque_at(A, pc, 0.f, [&](int j, float t, float) { out[o + j] = t; }, RegWrench(), on, on);
+  if (part == 0)
+#pragma unroll
+    for (int j = 0; j < 7; ++j) out[21 + j] = pc.qd[j];
 }
 
 // ratios of one sample at normalised time u: rho_tau(s) and rho_P(s)

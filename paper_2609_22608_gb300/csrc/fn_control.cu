@@ -16,18 +16,6 @@
 
 namespace fn {
 
-// one configuration (q, qd, qdd) handed to torque_at as its "sample"
-struct PointCoef {
-  float q[7], qd[7], qdd[7];
-};
-
-__device__ __forceinline__ void cubic_eval(const PointCoef& c, int j, float, float& q, float& v,
-                                           float& a) {
-  q = c.q[j];
-  v = c.qd[j];
-  a = c.qdd[j];
-}
-
 // the limits the controller clips to, exactly as given (ArmK keeps only
 // their reciprocals)
 struct CtrlK {

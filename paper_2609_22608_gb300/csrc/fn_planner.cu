@@ -76,6 +76,7 @@ struct Sched {
   int n_items;        // probe items of the packed edge phase
   int n_pend[2];      // lengths of the two pending-edge lists
   int n_surv;         // probe survivors appended (may exceed surv_cap)
+  int n_dyn;          // edges with probe items listed by the prep (zero between bodies)
   int n_free_edges;   // free edges of all problems (the queue's first part)
   int n_edges;        // all edges
   // parent-search items (problem, query group, split), one per warp, in two
@@ -147,6 +148,8 @@ struct PlanDev {  // device pointers, passed by value to the kernels
   uint32_t* fail;     // [E] a sample of cur_k violated a limit
   int32_t* pend;      // [2][E] edges pending verification (ping-pong lists)
   int2* surv;         // [surv_cap] probe survivors (edge, grid index)
+  float* edyn;        // [Emax][2][28] end-sample torque split (alpha, beta, gamma, qd) per end
+  int32_t* dyn_list;  // [Emax] edges with probe items (order of listing)
   int Emax, Kmax, surv_cap;
   // duration surrogate: free edges with admissible durations routed to the
   // window pass (sur != 0), listed in sur_list (count *sur_n)
@@ -295,6 +298,7 @@ __global__ void k_plan_schedule(PlanDev D) {
   S->nsg_max = nsg_max;
   if (D.sur_n) *D.sur_n = 0;
   S->queue_head = 0u;
+  S->n_dyn = 0;
 }
 
 // largest p with off[p] <= x (off ascending, off[0] = 0)
@@ -879,6 +883,18 @@ __device__ __forceinline__ void decode_edge(const PlanDev& D, const Sched* S, in
   b = goal ? slot : G + slot;
 }
 
+// lists the block's edges with probe items (warp-aggregated append) for the
+// end-sample torque split; every thread of the block calls it
+__device__ __forceinline__ void list_dyn_edge(const PlanDev& D, int e, bool has_items) {
+  const unsigned m = __ballot_sync(0xffffffffu, has_items);
+  if (!m) return;
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == __ffs(m) - 1) base = atomicAdd(&D.sched->n_dyn, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+  if (has_items) D.dyn_list[base + __popc(m & ((1u << lane) - 1u))] = e;
+}
+
 __global__ void __launch_bounds__(PL_SCAN) k_plan_eprep(PlanDev D, GridKP Gr) {
   pdl_begin();
   __shared__ float sT[FN_MAX_GRID];
@@ -934,6 +950,7 @@ __global__ void __launch_bounds__(PL_SCAN) k_plan_eprep(PlanDev D, GridKP Gr) {
       D.e_k[ei] = -1;
     }
   }
+  list_dyn_edge(D, e, e < E && cnt > 0);
   // block-local exclusive scan of the item counts
   int tot;
   const int ex = block_scan(cnt, sh, &tot);
@@ -968,66 +985,97 @@ __device__ __forceinline__ int item_off(const PlanDev& D, int e) {
   return D.e_cnt[e] + D.blk_off[e / PL_SCAN];
 }
 
-// item -> owning edge, one warp per edge
-__global__ void __launch_bounds__(256) k_plan_expand(PlanDev D) {
+// For every listed edge with probe items, one lane per (edge, end, part):
+// the item -> owning edge map (the edge's six lanes share its items) and the
+// end-sample torque split (end_torque_part): three torque evaluations per
+// end replace two per item.  Sized to the resident blocks.
+__global__ void __launch_bounds__(256) k_plan_expand(PlanDev D, ArmK A) {
   pdl_begin();
   const Sched* S = D.sched;
-  const int E = S->n_edges, lane = threadIdx.x & 31;
-  const long W = (long)gridDim.x * (blockDim.x >> 5);
-  for (long e = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < E; e += W) {
-    const int o = item_off(D, (int)e);
-    const int c = ((int)e + 1 < E ? item_off(D, (int)e + 1) : S->n_items) - o;
-    for (int t = lane; t < c; t += 32) D.owner[o + t] = (int)e;
+  const int E = S->n_edges;
+  const int nd = min(S->n_dyn, E);
+  unsigned nsamp = 0;
+  const long L = (long)gridDim.x * blockDim.x;
+  for (long x = (long)blockIdx.x * blockDim.x + threadIdx.x; x < 6L * nd; x += L) {
+    const int r = (int)(x % 6), end = r / 3, part = r - 3 * end;
+    const int e = D.dyn_list[x / 6];
+    const int o = item_off(D, e);
+    const int c = (e + 1 < E ? item_off(D, e + 1) : S->n_items) - o;
+    for (int t = r; t < c; t += 6) D.owner[o + t] = e;
+    const int p = D.e_ci[e] / D.BM;
+    const float4* r0 = reinterpret_cast<const float4*>(D.st + ((long)p * D.NC + D.e_par[e]) * 16);
+    const float4* r1 = reinterpret_cast<const float4*>(D.cand + (long)D.e_ci[e] * 16);
+    float q0[7], qd0[7], q1[7], qd1[7];
+    load_state(r0, q0, qd0);
+    load_state(r1, q1, qd1);
+    end_torque_part(A, q0, qd0, q1, qd1, end, part, D.edyn + (2L * e + end) * 28);
+    ++nsamp;
   }
+  if (D.samples && nsamp) atomicAdd(D.samples + 0, (unsigned long long)nsamp);
 }
 
-// Probe: one lane per (edge, grid duration) item evaluates both end samples
-// (u = 0, u = 1) with plain FP32 coefficients; a duration whose ends pass is
-// marked in the edge's survivor mask.  Goal edges have one item: their fixed
-// duration.
+static int expand_blocks() {
+  static int blocks[64] = {0};   // per device: resident blocks of k_plan_expand
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (blocks[dev] == 0) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_plan_expand, 256, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    blocks[dev] = per_sm * num_sms();
+  }
+  return blocks[dev];
+}
+
+// Probe: one lane per (edge, grid duration) item checks both end samples
+// (u = 0, u = 1) from the edge's end-sample torque split: tau = alpha / T^2
+// + beta / T + gamma per joint, then rho_tau and rho_P at the end velocity;
+// a duration whose ends pass is marked in the edge's survivor mask.  Goal
+// edges have one item: their fixed duration.
 template <int MINB>
 __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_probe(PlanDev D, ArmK A,
                                                                          GridKP Gr) {
   pdl_begin();
   __shared__ float sT[FN_MAX_GRID];
-  __shared__ float sCoef[PL_EDGE_WARPS][FN_CUBIC_WORDS * 32];
-  __shared__ float sWr[PL_EDGE_WARPS][FN_WRENCH_WORDS * 32];
   for (int i = threadIdx.x; i < D.K; i += blockDim.x) sT[i] = Gr.T[i];
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const CubicLane cb{&sCoef[w][lane]};
-  const LaneWrench wr{&sWr[w][lane]};
   const Sched* S = D.sched;
   const int n_items = S->n_items;
-  unsigned nsamp = 0;
   const long W = (long)gridDim.x * PL_EDGE_WARPS;
   for (long c = (long)blockIdx.x * PL_EDGE_WARPS + w; c * 32 < n_items; c += W) {
     const int i = (int)(c * 32) + lane;
     const bool live = i < n_items;
     int e = 0, k = 0;
+    bool pass = live;
     if (live) {
       e = D.owner[i];
       k = D.e_klo[e] + (i - item_off(D, e));
       const bool goal = D.e_j[e] & 0x80;
       const float T = goal ? D.e_Tp[e] : sT[k];
-      const int p = D.e_ci[e] / D.BM;
-      const float* r0 = D.st + ((long)p * D.NC + D.e_par[e]) * 16;
-      const float* r1 = D.cand + (long)D.e_ci[e] * 16;
-      float es[32];
+      const float iT = 1.0f / T, iT2 = iT * iT;
 #pragma unroll
-      for (int m = 0; m < 16; ++m) { es[m] = __ldg(r0 + m); es[16 + m] = __ldg(r1 + m); }
-      Cubic cc;
-      cubic_coef_sh<false>(es, T, cc);
-      cb.store(cc);
+      for (int end = 0; end < 2; ++end) {
+        const float4* c4 = reinterpret_cast<const float4*>(D.edyn) + (2L * e + end) * 7;
+        float f[28];
+#pragma unroll
+        for (int v = 0; v < 7; ++v) {
+          const float4 t = __ldg(c4 + v);
+          f[4 * v] = t.x; f[4 * v + 1] = t.y; f[4 * v + 2] = t.z; f[4 * v + 3] = t.w;
+        }
+        float r = 0.f, pw = 0.f;
+#pragma unroll
+        for (int j = 0; j < 7; ++j) {
+          const float tau = fmaf(f[j], iT2, fmaf(f[7 + j], iT, f[14 + j]));
+          r = fmaxf(r, fabsf(tau) * A.inv_tau[j]);
+          pw = fmaf(tau, f[21 + j], pw);
+        }
+        pass = pass && r <= 1.f && fabsf(pw) * A.inv_w <= 1.f;
+      }
     }
-    bool pass = live;
-#pragma unroll 1
-    for (int end = 0; end < 2; ++end) {   // single torque call site
-      float a = 0.f, b = 0.f;
-      if (live) sample_ratios(A, cb, (float)end, a, b, wr);
-      pass = pass && a <= 1.f && b <= 1.f;
-    }
-    nsamp += 2u * __popc(__ballot_sync(0xffffffffu, live));
     const unsigned pm = __ballot_sync(0xffffffffu, pass);
     int slot0 = 0;
     if (lane == 0 && pm) slot0 = atomicAdd(&D.sched->n_surv, __popc(pm));
@@ -1038,7 +1086,6 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_probe(PlanDev
       if (slot < D.surv_cap) D.surv[slot] = make_int2(e, k);
     }
   }
-  if (D.samples && lane == 0 && nsamp) atomicAdd(D.samples + 0, (unsigned long long)nsamp);
 }
 
 // Mid-probe: lanes = (survivor, interior probe sample) items; a violation
@@ -1112,6 +1159,7 @@ __global__ void k_plan_vinit(PlanDev D) {
   pdl_begin();
   Sched* S = D.sched;
   const int E = S->n_edges;
+  if (blockIdx.x == 0 && threadIdx.x == 0) S->n_dyn = 0;   // the expand consumed the list
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
     const int c = (e + 1 < E ? item_off(D, e + 1) : S->n_items) - item_off(D, e);
     if (c == 0) continue;   // decided in prep
@@ -2086,7 +2134,7 @@ static void enqueue_edge_body(fn_planner* pl, const PlanDev& D, int v, int block
                               Mark&& mark) {
   pl_launch(k_plan_escan, 1, PL_SCAN, 0, st, D);
   trace(pl, st, "k_plan_escan");
-  pl_launch(k_plan_expand, 4 * num_sms(), 256, 0, st, D);
+  pl_launch(k_plan_expand, expand_blocks(), 256, 0, st, D, pl->arm);
   trace(pl, st, "k_plan_expand");
   mark(4);
   pl_launch(plan_probe_variant(v), blocks, 32 * PL_EDGE_WARPS, 0, st, D, pl->arm, pl->grid);
@@ -2189,6 +2237,7 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
   A_(D.e_T, P * BM * KP); A_(D.e_rv, P * BM * KP); A_(D.e_ok, P * BM * KP);
   A_(D.e_k, P * BM * KP);
   A_(D.inc, P); A_(D.prob, P); A_(D.sched, 1); A_(D.out, P); A_(D.iter, 1);
+  if (rc == FN_OK && cudaMemset(D.sched, 0, sizeof(Sched)) != cudaSuccess) rc = FN_ECUDA;
   A_(D.added, P); A_(D.status, P);
   A_(D.ptr, P * NC); A_(D.newidx, P * NC); A_(D.alive, P * NC);
   A_(D.tmp_st, P * NC * 16); A_(D.tmp_f, P * NC * 4); A_(D.tmp_par, P * NC);
@@ -2201,6 +2250,8 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
   A_(D.mask, (size_t)D.Emax * 8);
   D.Kmax = c.K;
   A_(D.owner, (size_t)D.Emax * c.K);
+  A_(D.edyn, (size_t)D.Emax * 56);
+  A_(D.dyn_list, (size_t)D.Emax);
   A_(D.cur_k, (size_t)D.Emax);
   A_(D.fail, (size_t)D.Emax);
   A_(D.pend, (size_t)D.Emax * 2);
@@ -2771,6 +2822,7 @@ __global__ void __launch_bounds__(PL_SCAN) k_edges_prep(PlanDev D, GridKP Gr, in
       D.e_k[src] = finite ? -1 : -2;
     }
   }
+  list_dyn_edge(D, e, e < n && cnt > 0);
   int tot;
   const int ex = block_scan(cnt, sh, &tot);
   if (e < n) D.e_cnt[e] = ex;
