@@ -185,3 +185,33 @@ def test_torque_adds_armature_and_friction(orc, arm):
         diff = d_full - d_rigid
         expect = np.zeros(7); expect[j] = arm["armature"][j]
         assert np.allclose(diff, expect, atol=1e-12)
+
+
+def test_end_sample_torque_is_affine_in_inverse_duration(orc, arm):
+    """At the ends of the cubic (t = 0 and t = T) the position and velocity
+    are the edge's end states for every T, and Eq. (torque) there is
+    alpha / T^2 + beta / T + gamma: alpha and beta the torque increments of
+    the accelerations +-6 (q1 - q0) and -(4 qd0 + 2 qd1) or (4 qd1 + 2 qd0)
+    at zero velocity, gamma the torque at the end state with zero
+    acceleration.  The probe of the edge pipeline checks durations from
+    this split."""
+    rng = np.random.default_rng(17)
+    s0, s1 = synth.random_edges(arm, 6, 23)
+    for e in range(6):
+        q0, qd0 = s0[e, :7].astype(np.float64), s0[e, 8:15].astype(np.float64)
+        q1, qd1 = s1[e, :7].astype(np.float64), s1[e, 8:15].astype(np.float64)
+        d = q1 - q0
+        for end, (q, qd, a, b) in enumerate([(q0, qd0, 6 * d, -(4 * qd0 + 2 * qd1)),
+                                             (q1, qd1, -6 * d, 4 * qd1 + 2 * qd0)]):
+            z = np.zeros(7)
+            g0 = orc.torque(arm, q, z, z)
+            alpha = orc.torque(arm, q, z, a) - g0
+            beta = orc.torque(arm, q, z, b) - g0
+            gamma = orc.torque(arm, q, qd, z)
+            for T in rng.uniform(0.05, 1.5, 4):
+                pos, vel, acc = orc.cubic(q0, qd0, q1, qd1, T, end * T)
+                assert np.allclose(pos, q, rtol=0, atol=1e-12)
+                assert np.allclose(vel, qd, rtol=0, atol=1e-12)
+                tau = orc.torque(arm, pos, vel, acc)
+                split = alpha / T ** 2 + beta / T + gamma
+                assert np.allclose(split, tau, rtol=1e-10, atol=1e-9 * np.abs(tau).max())
