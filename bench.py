@@ -268,13 +268,17 @@ def run_ours(args, rank, world):
         torch.distributed.barrier()
     step_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
 
-    # end to end through the public API with host buffers: the tree and the
-    # problem go host -> device, the rendezvous comes back, every step
+    # end to end through the public API with host buffers: the tree (from
+    # pinned host memory) and the problem go host -> device, the rendezvous
+    # comes back, every step
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+              for a in (w["tree"], w["t_node"], w["parent"])]
+    h_tree, h_t, h_par = (x.numpy() for x in pinned)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(args.steps):
         pl.reset([prob], stream=stream)
-        pl.load_tree(0, w["tree"], w["t_node"], w["parent"], stream=stream)
+        pl.load_tree(0, h_tree, h_t, h_par, stream=stream)
         pl.replay([prob], 0, stream=stream)
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
