@@ -2123,7 +2123,9 @@ static void enqueue_front(fn_planner* pl, unsigned flags, cudaStream_t st, Mark&
 // pay off when thousands of edges fail their first duration), else one.
 // At least one: goal edges, verified at their fixed duration, are decided
 // by the first stage and never reach the tail.
+#ifndef PL_VSTAGE_EDGES
 #define PL_VSTAGE_EDGES 65536
+#endif
 static int vstages(const PlanDev& D) { return D.Emax >= PL_VSTAGE_EDGES ? 2 : 1; }
 
 // the packed edge phase after the per-edge prep: item scan, probe, verify
