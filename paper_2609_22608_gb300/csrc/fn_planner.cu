@@ -97,6 +97,7 @@ struct Sched {
 struct PlanDev {  // device pointers, passed by value to the kernels
   int P, NC, BM, KP, KN, KM, K, S, S_clear, G;
   int knn_slots;      // resident warps of the parent search's persistent grid
+  int vstages;        // packed verification stages (1 or 2)
   float w_vel, vel_frac, margin;
   float* st;          // [P][NC][16]
   float* t;           // [P][NC]
@@ -2118,15 +2119,17 @@ static void enqueue_front(fn_planner* pl, unsigned flags, cudaStream_t st, Mark&
   search(1);
 }
 
-// Packed verification stages before the sequential tail: two where the
-// view holds many edges (each stage pair is two dependent launches, which
-// pay off when thousands of edges fail their first duration), else one.
-// At least one: goal edges, verified at their fixed duration, are decided
-// by the first stage and never reach the tail.
+// Packed verification stages before the sequential tail (PlanDev::vstages):
+// each stage pair is two dependent launches, which pay off when thousands of
+// edges fail their first duration.  Planners whose edge capacity is at least
+// PL_VSTAGE_EDGES run two (a batch of many problems), smaller ones one; the
+// packed engine runs two (uncapped caller edges scan many durations).  At
+// least one: goal edges, verified at their fixed duration, are decided by
+// the first stage and never reach the tail.
 #ifndef PL_VSTAGE_EDGES
-#define PL_VSTAGE_EDGES 65536
+#define PL_VSTAGE_EDGES 262144
 #endif
-static int vstages(const PlanDev& D) { return D.Emax >= PL_VSTAGE_EDGES ? 2 : 1; }
+static int vstages(const PlanDev& D) { return D.vstages >= 2 ? 2 : 1; }
 
 // the packed edge phase after the per-edge prep: item scan, probe, verify
 // (over the edges of the view D; mark(i) records the phase boundaries when
@@ -2226,6 +2229,7 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
   D.P = c.P; D.NC = c.n_cap; D.BM = c.b_max; D.KP = c.k; D.KN = std::max(c.k - 1, 1);
   D.KM = (c.k - 1) <= 8 ? 8 : 16;
   D.knn_slots = (D.KM == 8 ? knn_blocks<8>(pl) : knn_blocks<16>(pl)) * PL_KNN_WARPS;
+  D.vstages = (long)c.P * c.b_max * c.k >= PL_VSTAGE_EDGES ? 2 : 1;
   D.K = c.K; D.S = c.S; D.S_clear = c.S_clear; D.G = c.reach_grid;
   D.w_vel = c.w_vel; D.vel_frac = c.vel_frac; D.margin = c.clear_margin;
   const size_t P = c.P, NC = c.n_cap, BM = c.b_max, KP = c.k, KN = D.KN, KM = D.KM;
@@ -2962,6 +2966,7 @@ extern "C" fn_status fn_edges_create(const fn_arm_t* arm, const float* T_grid, i
     return rc;
   }
   for (int k = 0; k < K; ++k) eg->pl->grid.T[k] = T_grid[k];
+  eg->pl->D.vstages = 2;
   eg->logT0 = std::log(T_grid[0]);
   eg->dlog = (std::log(T_grid[K - 1]) - eg->logT0) / (float)(K - 1);
   fn_problem_t prob = {};   // no obstacles: the clearance check is off
