@@ -215,3 +215,34 @@ def test_end_sample_torque_is_affine_in_inverse_duration(orc, arm):
                 tau = orc.torque(arm, pos, vel, acc)
                 split = alpha / T ** 2 + beta / T + gamma
                 assert np.allclose(split, tau, rtol=1e-10, atol=1e-9 * np.abs(tau).max())
+
+
+def test_end_sample_split_does_not_cancel_near_decisions(orc, arm):
+    """Near a probe decision (the largest end-sample torque ratio within
+    [0.5, 2]), the three terms of alpha / T^2 + beta / T + gamma add up to
+    at most a few torque limits, so the single-precision rounding of the
+    split (relative ~1e-7 per term and operation) moves a ratio by far less
+    than the 1e-4 margin within which decisions may differ."""
+    grid = synth.duration_grid(128)
+    s0, s1 = synth.random_edges(arm, 120, 5)
+    tm = np.asarray(arm["tau_max"], np.float64)
+    worst, near = 0.0, 0
+    for e in range(s0.shape[0]):
+        q0, qd0 = s0[e, :7].astype(np.float64), s0[e, 8:15].astype(np.float64)
+        q1, qd1 = s1[e, :7].astype(np.float64), s1[e, 8:15].astype(np.float64)
+        d = q1 - q0
+        z = np.zeros(7)
+        for q, qd, a, b in [(q0, qd0, 6 * d, -(4 * qd0 + 2 * qd1)),
+                            (q1, qd1, -6 * d, 4 * qd1 + 2 * qd0)]:
+            g0 = orc.torque(arm, q, z, z)
+            alpha = orc.torque(arm, q, z, a) - g0
+            beta = orc.torque(arm, q, z, b) - g0
+            gamma = orc.torque(arm, q, qd, z)
+            for T in grid:
+                ratio = np.abs(alpha / T ** 2 + beta / T + gamma) / tm
+                if 0.5 <= ratio.max() <= 2.0:
+                    near += 1
+                    amp = (np.abs(alpha) / T ** 2 + np.abs(beta) / T + np.abs(gamma)) / tm
+                    worst = max(worst, float(amp.max()))
+    assert near > 1000
+    assert worst < 20.0          # x ~1e-6 relative rounding << 1e-4
