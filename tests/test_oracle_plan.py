@@ -188,3 +188,53 @@ def test_incumbent_tie_goes_to_lower_id(orc, arm):
     assert b_best in rows and G in rows
     assert out.J[rows[b_best]] == out.J[rows[G]] == inc2["J"]
     assert inc2["id"] == rows[b_best]
+
+
+def test_prune_rules(orc, arm):
+    """Eq. (reach) pruning: the root and the incumbent's path stay; any other
+    node stays only if its reach time exists, is no later than t_best and
+    its parent stays; the kept nodes keep their order and their parents are
+    re-indexed; the incumbent id follows its node."""
+    toss = synth.random_toss(arm, 9)
+    root = synth.random_states(arm, 1, 59)[0]
+    pr = synth.make_problem(toss, root=root)
+    states, parent, t = synth.random_tree(arm, 150, 9, root=root)
+    tree = OP.Tree(states, t, parent)
+    # the incumbent: a deep node
+    depth = np.zeros(tree.n, int)
+    for i in range(1, tree.n):
+        depth[i] = depth[tree.parent[i]] + 1
+    inc_id = int(np.argmax(depth))
+    path = set()
+    c = inc_id
+    while c > 0:
+        path.add(c)
+        c = int(tree.parent[c])
+    reach = {}
+    for i in range(1, tree.n):
+        g, Tn = orc.reach_time(arm, pr, tree.states[i, :7].astype(np.float64), float(tree.t[i]), 64)
+        reach[i] = (g, Tn)
+    t_best = float(np.median([Tn for g, Tn in reach.values() if g >= 0]))
+    inc = dict(id=inc_id, J=1.0, t_best=t_best)
+    out, inc2, alive = OP.prune_tree(arm, pr, tree, inc, G=64)
+
+    def stays(i):
+        if i == 0 or i in path:
+            return True
+        g, Tn = reach[i]
+        return g >= 0 and Tn <= t_best and stays(int(tree.parent[i]))
+
+    expect = np.array([stays(i) for i in range(tree.n)])
+    assert np.array_equal(alive, expect)
+    assert 0 < expect.sum() < tree.n
+    assert any(not (reach[i][0] >= 0 and reach[i][1] <= t_best) for i in path)   # kept by the path rule
+    assert any(reach[i][0] >= 0 and reach[i][1] <= t_best and not expect[i]
+               for i in range(1, tree.n))                                       # removed with an ancestor
+    idx = np.nonzero(expect)[0]
+    assert np.array_equal(out.states, tree.states[idx]) and np.array_equal(out.t, tree.t[idx])
+    for new, old in enumerate(idx):
+        if old == 0:
+            assert out.parent[new] == -1
+        else:
+            assert idx[out.parent[new]] == tree.parent[old]
+    assert idx[inc2["id"]] == inc_id
