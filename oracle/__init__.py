@@ -109,13 +109,13 @@ def lib():
         L.or_jacobian_point.argtypes = [P(OrArm), C.c_void_p, C.c_void_p, C.c_void_p]
         L.or_philox4x32.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         L.or_goal_chart.argtypes = [P(OrArm), P(OrProblem), C.c_void_p, C.c_void_p, C.c_void_p,
-                                    C.c_void_p, C.c_void_p]
+                                    C.c_void_p, C.c_void_p, C.c_void_p]
         L.or_goal_chart.restype = C.c_int
         L.or_sample_uniform.argtypes = [P(OrArm), C.c_ulonglong, C.c_int, C.c_int, C.c_int,
                                         C.c_int, C.c_double, C.c_void_p]
         L.or_sample_goals.argtypes = [P(OrArm), P(OrProblem), C.c_ulonglong, C.c_int, C.c_int,
                                       C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
-                                      C.c_void_p]
+                                      C.c_void_p, C.c_void_p]
         L.or_objective.argtypes = [P(OrProblem), C.c_double, C.c_double, C.c_double]
         L.or_objective.restype = C.c_double
         L.or_reach_time.argtypes = [P(OrArm), P(OrProblem), C.c_void_p, C.c_double, C.c_int,
@@ -430,7 +430,9 @@ def goal_chart(arm, pr, z):
     Tq = np.zeros(1)
     vr = np.zeros(1)
     vb = np.zeros(3)
-    ok = lib().or_goal_chart(C.byref(A), C.byref(P), _p(z), _p(st), _p(Tq), _p(vr), _p(vb))
+    why = np.zeros(1, np.int32)
+    ok = lib().or_goal_chart(C.byref(A), C.byref(P), _p(z), _p(st), _p(Tq), _p(vr), _p(vb),
+                             _p(why))
     return bool(ok), st, float(Tq[0]), float(vr[0]), vb
 
 
@@ -442,15 +444,24 @@ def sample_uniform(arm, seed, it, problem, first_index, n, vel_frac=0.5):
     return out
 
 
-def sample_goals(arm, pr, seed, it, problem, first_index, n):
+# why a goal draw is undefined (or_goal_chart's reason codes)
+CHART_REASONS = ("defined", "speed", "ik", "box", "singular", "taper")
+
+
+def sample_goals(arm, pr, seed, it, problem, first_index, n, reasons=False):
+    """Goal draws decoded by the chart: (states, T_req, v_rel, valid), plus
+    the reason code of every draw (CHART_REASONS) when `reasons`."""
     A = arm_struct(arm)
     P = problem_struct(pr)
     st = np.zeros((n, 16))
     Tq = np.zeros(n)
     vr = np.zeros(n)
     valid = np.zeros(n, np.int32)
+    why = np.zeros(n, np.int32)
     lib().or_sample_goals(C.byref(A), C.byref(P), int(seed), int(it), int(problem),
-                          int(first_index), int(n), _p(st), _p(Tq), _p(vr), _p(valid))
+                          int(first_index), int(n), _p(st), _p(Tq), _p(vr), _p(valid), _p(why))
+    if reasons:
+        return st, Tq, vr, valid, why
     return st, Tq, vr, valid
 
 

@@ -619,23 +619,26 @@ static void complete_basis(const double* u, double* e1, double* e2) {
 #define OR_IK_LAMBDA 5e-2
 #define OR_IK_POS_TOL 1e-4
 #define OR_IK_ROT_TOL 1e-3
-#define OR_IK_STARTS 3
+#define OR_IK_STARTS 4
 
 /* One damped-least-squares IK run on joints 1-6 with q7 fixed.  Start `st`
- * is the box centre shifted by a fixed fraction of each half-range (three
- * postures: centre, and the shoulder/elbow/wrist pattern +-(0,.5,0,-.5,0,.5)),
- * with joint 1 turned towards the target's azimuth; each iterate is
- * projected onto the joint box.  Returns 1 when the pose residuals are under
- * tolerance and the rotation error is under 90 degrees (trace > 1; the
- * cross-product residual also vanishes at a half turn). */
+ * is the box centre shifted by a fixed fraction of each half-range (four
+ * postures: centre, the shoulder/elbow/wrist pattern +-(0,.5,0,-.5,0,.5),
+ * and (0,-.5,0,-.5,0,-.5)), with joint 1 turned towards the target's
+ * azimuth; each iterate is projected onto the joint box.  Returns 1 when the
+ * pose residuals are under tolerance and the rotation error is under 90
+ * degrees (trace > 1; the cross-product residual also vanishes at a half
+ * turn). */
 static int ik_solve(const or_arm* arm, double Rg[3][3], const double* pg, double z6, int st,
                     double* q) {
-  static const double pattern[6] = {0.0, 0.5, 0.0, -0.5, 0.0, 0.5};
-  double sgn = st == 0 ? 0.0 : (st == 1 ? 1.0 : -1.0);
+  static const double pattern[2][6] = {{0.0, 0.5, 0.0, -0.5, 0.0, 0.5},
+                                       {0.0, -0.5, 0.0, -0.5, 0.0, -0.5}};
+  double sgn = st == 0 ? 0.0 : (st == 2 ? -1.0 : 1.0);
+  const double* pat = pattern[st == 3 ? 1 : 0];
   for (int j = 0; j < 7; ++j) {
     double c = 0.5 * (arm->q_lo[j] + arm->q_hi[j]);
     double h = 0.5 * (arm->q_hi[j] - arm->q_lo[j]);
-    q[j] = j < 6 ? c + sgn * pattern[j] * h : c;
+    q[j] = j < 6 ? c + sgn * pat[j] * h : c;
   }
   q[6] = arm->q_lo[6] + z6 * (arm->q_hi[6] - arm->q_lo[6]);
   q[0] = fmin(fmax(atan2(pg[1], pg[0]), arm->q_lo[0]), arm->q_hi[0]);
@@ -691,12 +694,20 @@ static int ik_solve(const or_arm* arm, double Rg[3][3], const double* pg, double
  *  z7 -> contact at arclength z7 * blade_len along the edge
  *  z6 -> q7 = q7_lo + z6 (q7_hi - q7_lo)
  *  q_g by damped least squares on joints 1-6 (the paper's closed-form FR3 IK
- *  does not apply to a synthetic arm): up to three starts (ik_solve), 24
+ *  does not apply to a synthetic arm): up to four starts (ik_solve), 24
  *  iterations each, lambda = 0.05; the first start that converges wins
- *  qd_g = J^+ [v_b; 0] at the contact point, J^+ = J^T (J J^T)^-1; undefined
- *  if any |qd_g,i| exceeds the taper at q_g. */
+ *  qd_g = J_p^+ v_b with J_p the 3x7 Jacobian of the contact point's linear
+ *  velocity, J_p^+ = J_p^T (J_p J_p^T)^-1: v_ee is a linear velocity, so the
+ *  minimum-norm joint velocity that gives the blade v_b at the contact;
+ *  undefined if any |qd_g,i| exceeds the taper at q_g.
+ * Returns 1 where phi is defined, else 0; `reason` (may be NULL) receives
+ * OR_CHART_OK or the first condition that left phi undefined. */
 int or_goal_chart(const or_arm* arm, const or_problem* pr, const double* z,
-                  double* out_state, double* T_req, double* vrel_out, double* vb_out) {
+                  double* out_state, double* T_req, double* vrel_out, double* vb_out,
+                  int* reason) {
+  int why_dummy;
+  int* why = reason ? reason : &why_dummy;
+  *why = OR_CHART_SPEED;
   double T = pr->t_enter + z[0] * (pr->t_fall - pr->t_enter);
   double tf = T + pr->t_offset;
   double c[3], xd[3];
@@ -756,44 +767,50 @@ int or_goal_chart(const or_arm* arm, const or_problem* pr, const double* z,
   int found = 0;
   for (int st = 0; st < OR_IK_STARTS && !found; ++st)
     found = ik_solve(arm, Rg, pg, z[6], st, q);
+  *why = OR_CHART_IK;
   if (!found) return 0;
+  *why = OR_CHART_BOX;
   for (int j = 0; j < 7; ++j)
     if (!(q[j] >= arm->q_lo[j] && q[j] <= arm->q_hi[j])) return 0;
+  /* rows 0-2 of the point Jacobian: the contact point's linear velocity */
   double J[6][7];
   or_jacobian_point(arm, q, c, J);
   double A[6][6];
-  for (int i = 0; i < 6; ++i)
-    for (int j = 0; j < 6; ++j) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
       double sacc = 0.0;
       for (int m = 0; m < 7; ++m) sacc += J[i][m] * J[j][m];
       A[i][j] = sacc;
     }
-  double vt[6] = {vb[0], vb[1], vb[2], 0.0, 0.0, 0.0};
-  double y[6];
-  if (!solve_gepp(6, A, vt, y)) return 0;
+  double y[3];
+  *why = OR_CHART_SINGULAR;
+  if (!solve_gepp(3, A, vb, y)) return 0;
   double qd[7];
   for (int m = 0; m < 7; ++m) {
     double acc = 0.0;
-    for (int i = 0; i < 6; ++i) acc += J[i][m] * y[i];
+    for (int i = 0; i < 3; ++i) acc += J[i][m] * y[i];
     qd[m] = acc;
   }
+  *why = OR_CHART_TAPER;
   for (int j = 0; j < 7; ++j)
     if (!(fabs(qd[j]) <= or_taper(arm, j, q[j]))) return 0;
   for (int i = 0; i < 16; ++i) out_state[i] = 0.0;
   for (int j = 0; j < 7; ++j) { out_state[j] = q[j]; out_state[8 + j] = qd[j]; }
+  *why = OR_CHART_OK;
   return 1;
 }
 
 /* Goal candidates: z from Philox streams 8..10 of the candidate's counter. */
 void or_sample_goals(const or_arm* arm, const or_problem* pr, unsigned long long seed,
                      int iter, int problem, int first_index, int n, double* states,
-                     double* T_req, double* vrel, int* valid) {
+                     double* T_req, double* vrel, int* valid, int* reason) {
 #pragma omp parallel for schedule(dynamic, 4)
   for (int c = 0; c < n; ++c) {
     double u[12], z[9], vb[3];
     for (int s = 0; s < 3; ++s) philox_uniforms(seed, first_index + c, iter, problem, 8 + s, u + 4 * s);
     for (int i = 0; i < 9; ++i) z[i] = u[i];
-    valid[c] = or_goal_chart(arm, pr, z, states + 16 * (size_t)c, &T_req[c], &vrel[c], vb);
+    valid[c] = or_goal_chart(arm, pr, z, states + 16 * (size_t)c, &T_req[c], &vrel[c], vb,
+                             reason ? reason + c : NULL);
     if (!valid[c])
       for (int i = 0; i < 16; ++i) states[16 * (size_t)c + i] = 0.0;
   }
@@ -1065,7 +1082,7 @@ void or_sample_goals_density(const or_arm* arm, const or_problem* pr, const or_d
     or_density_z(th, seed, first_index + c, iter, problem, z);
     if (zs)
       for (int i = 0; i < 9; ++i) zs[9 * (size_t)c + i] = z[i];
-    valid[c] = or_goal_chart(arm, pr, z, states + 16 * (size_t)c, &T_req[c], &vrel[c], vb);
+    valid[c] = or_goal_chart(arm, pr, z, states + 16 * (size_t)c, &T_req[c], &vrel[c], vb, NULL);
     if (!valid[c])
       for (int i = 0; i < 16; ++i) states[16 * (size_t)c + i] = 0.0;
   }

@@ -115,17 +115,20 @@ void or_jacobian_point(const or_arm* arm, const double* q, const double* p, doub
 /* Philox4x32-10 (Salmon et al., SC'11) */
 void or_philox4x32(const unsigned int ctr[4], const unsigned int key[2], unsigned int out[4]);
 
+/* why phi(z) is undefined (the first failing condition), or OR_CHART_OK */
+enum { OR_CHART_OK = 0, OR_CHART_SPEED = 1, OR_CHART_IK = 2, OR_CHART_BOX = 3,
+       OR_CHART_SINGULAR = 4, OR_CHART_TAPER = 5 };
 /* goal chart phi(z): out_state[16] (q, pad, qd, pad), T_req, |v_rel|, v_b[3];
- * returns 1 if defined, 0 otherwise.  ik_iters / lam are the IK schedule. */
+ * returns 1 if defined, 0 otherwise; reason (may be NULL) gets an OR_CHART_* code */
 int or_goal_chart(const or_arm* arm, const or_problem* pr, const double* z,
-                  double* out_state, double* T_req, double* vrel, double* vb);
+                  double* out_state, double* T_req, double* vrel, double* vb, int* reason);
 
 /* samplers drawing Philox uniforms with counter (index, iter, problem, stream) */
 void or_sample_uniform(const or_arm* arm, unsigned long long seed, int iter, int problem,
                        int first_index, int n, double vel_frac, double* states);
 void or_sample_goals(const or_arm* arm, const or_problem* pr, unsigned long long seed,
                      int iter, int problem, int first_index, int n, double* states,
-                     double* T_req, double* vrel, int* valid);
+                     double* T_req, double* vrel, int* valid, int* reason);
 
 /* Eq. (objective) of a rendezvous at arrival T with relative speed vrel and
  * peak velocity fraction nu */

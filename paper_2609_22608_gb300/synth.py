@@ -123,19 +123,37 @@ def random_edges(arm: dict, E: int, seed: int, vel_frac: float = 0.5):
     return s0, s1
 
 
-def random_tree(arm: dict, N: int, seed: int, root: np.ndarray | None = None):
+def random_tree(arm: dict, N: int, seed: int, root: np.ndarray | None = None,
+                t_max: float | None = None):
     """Synthetic tree: random states, parent uniform among earlier nodes,
-    t = t_parent + U(0.05, 0.3).  Node 0 is the root with t = 0."""
+    t = t_parent + U(0.05, 0.3).  Node 0 is the root with t = 0.
+
+    With `t_max` (a planning tree: every node was attached no later than
+    t_best <= t_fall), the parent is uniform among the earlier nodes with
+    t <= t_max - 0.05 and the increment is U(0.05, min(0.3, t_max - t_parent)),
+    so every node's time lies in [0, t_max]."""
     rng = np.random.default_rng([0x7EE, seed])
     states = random_states(arm, N, 1000 + seed)
     if root is not None:
         states[0] = root
     parent = np.full(N, -1, np.int32)
     t = np.zeros(N, np.float64)
+    if t_max is None:
+        for i in range(1, N):
+            p = int(rng.integers(0, i))
+            parent[i] = p
+            t[i] = t[p] + rng.uniform(0.05, 0.3)
+        return states, parent, t.astype(F32)
+    t_max = float(t_max)
+    if t_max < 0.1:
+        raise ValueError("t_max must leave room for a 0.05 s increment")
+    open_nodes = [0]                      # nodes that can still take a child
     for i in range(1, N):
-        p = int(rng.integers(0, i))
+        p = open_nodes[int(rng.integers(0, len(open_nodes)))]
         parent[i] = p
-        t[i] = t[p] + rng.uniform(0.05, 0.3)
+        t[i] = t[p] + rng.uniform(0.05, min(0.3, t_max - t[p]))
+        if t[i] <= t_max - 0.05:
+            open_nodes.append(i)
     return states, parent, t.astype(F32)
 
 
@@ -147,14 +165,44 @@ class Toss:
     t_fall: float
 
 
+# the object counts as within the arm's reach (Sec. III: the window
+# [t_enter, t_fall] is when it is) while it is above the base plane and no
+# farther than REACH from the shoulder, the common origin of frames 1 and 2
+# at height d_1
+REACH = 0.7
+MIN_WINDOW = 0.1
+
+
+def reach_window(arm: dict, x0, v0, t_lo: float, t_hi: float, reach: float = REACH):
+    """First and last time in [t_lo, t_hi] (1 ms steps) at which the flight
+    x0 + v0 t + g t^2 / 2 is within `reach` of the shoulder and above z = 0;
+    None if it never is.  The window is taken as one interval."""
+    g = arm["gravity"].astype(np.float64)
+    ts = np.linspace(t_lo, t_hi, int(round((t_hi - t_lo) / 1e-3)) + 1)
+    x = np.asarray(x0, np.float64)[None] + np.asarray(v0, np.float64)[None] * ts[:, None] \
+        + 0.5 * g[None] * ts[:, None] ** 2
+    sh = np.array([0.0, 0.0, float(arm["dh_d"][0])])
+    inside = (np.linalg.norm(x - sh, axis=1) <= reach) & (x[:, 2] > 0.0)
+    if not inside.any():
+        return None
+    i = np.nonzero(inside)[0]
+    return float(ts[i[0]]), float(ts[i[-1]])
+
+
 def random_toss(arm: dict, seed: int, t_enter: float = 0.2, t_fall: float = 0.9,
-                target: np.ndarray | None = None) -> Toss:
+                target: np.ndarray | None = None, reach: float | None = REACH) -> Toss:
     """A ballistic toss that crosses the arm's workspace inside the window.
 
     Launch from radius U(1.2, 1.6) m at azimuth in {-30, 0, 30} deg (Sec. V-A)
     and height 1.0 m, with speed ~ N(3, 0.5) m/s aimed so that the flight
     passes `target` (default: a point 0.45-0.65 m from the base at height
     0.35-0.6 m) at a time inside [t_enter + 0.1, t_fall - 0.1].
+
+    With `reach` (default REACH), the toss's window is the part of
+    [t_enter, t_fall] during which the object is within the arm's reach
+    (reach_window), as the problem statement defines the window; tosses whose
+    window is shorter than MIN_WINDOW are redrawn.  reach=None keeps
+    [t_enter, t_fall] as given.
     """
     rng = np.random.default_rng([0x7055, seed])
     g = arm["gravity"].astype(np.float64)
@@ -175,7 +223,12 @@ def random_toss(arm: dict, seed: int, t_enter: float = 0.2, t_fall: float = 0.9,
         sp = np.linalg.norm(v, axis=1)
         j = int(np.argmin(np.abs(sp - speed)))
         if abs(sp[j] - speed) < 0.05:
-            return Toss(_f32(x0), _f32(v[j]), float(t_enter), float(t_fall))
+            x0f, v0f = _f32(x0), _f32(v[j])
+            if reach is None:
+                return Toss(x0f, v0f, float(t_enter), float(t_fall))
+            win = reach_window(arm, x0f, v0f, t_enter, t_fall, reach)
+            if win is not None and win[1] - win[0] >= MIN_WINDOW:
+                return Toss(x0f, v0f, float(F32(win[0])), float(F32(win[1])))
     raise RuntimeError("no toss found")
 
 

@@ -103,8 +103,8 @@ def test_fk_matches_homogeneous_transforms(orc, arm):
             assert np.allclose(J[0:3, j], dp, atol=1e-6)
 
 
-def _tosses(arm, n=6):
-    return [synth.make_problem(synth.random_toss(arm, s)) for s in range(n)]
+def _tosses(arm, n=6, reach=synth.REACH):
+    return [synth.make_problem(synth.random_toss(arm, s, reach=reach)) for s in range(n)]
 
 
 def test_goal_chart_samples_lie_on_manifold(orc, arm):
@@ -126,7 +126,12 @@ def test_goal_chart_samples_lie_on_manifold(orc, arm):
             assert np.linalg.norm(b0 + u * (b1 - b0) - x) < 6e-4
             J = orc.jacobian_point(arm, q, x)
             v6 = J @ qd
-            assert np.abs(v6[3:]).max() < 1e-8           # zero angular velocity
+            # minimum-norm joint velocity for the contact point's linear
+            # velocity: qd lies in the row space of the 3x7 point Jacobian
+            # (orthogonal to its null space, from an SVD)
+            Jp = J[:3]
+            null = np.linalg.svd(Jp)[2][3:]
+            assert np.abs(null @ qd).max() < 1e-9 * max(1.0, np.abs(qd).max())
             vrel = v6[:3] - xd
             assert np.linalg.norm(vrel) >= pr["v_min"] - 1e-9
             assert np.linalg.norm(vrel) == pytest.approx(vr[c], rel=1e-9)
@@ -137,6 +142,27 @@ def test_goal_chart_samples_lie_on_manifold(orc, arm):
             assert np.all(q >= arm["q_lo"]) and np.all(q <= arm["q_hi"])
             assert all(abs(qd[j]) <= orc.taper(arm, j, q[j]) for j in range(7))
     assert n_acc >= 20
+
+
+def test_goal_chart_reason_codes(orc, arm):
+    """Every draw is either defined (then it also decodes) or carries the
+    condition that left phi undefined; raising v_min turns every draw into
+    a speed rejection, and a zero taper (joint boxes of width zero keep the
+    IK from converging or the velocity under its bound) leaves none
+    defined."""
+    pr = _tosses(arm, 1)[0]
+    st, Tq, vr, valid, why = orc.sample_goals(arm, pr, 31, 0, 0, 0, 512, reasons=True)
+    assert np.array_equal(valid == 1, why == 0)
+    assert set(np.unique(why)) <= set(range(len(orc.CHART_REASONS)))
+    slow = dict(pr)
+    slow["v_min"] = 1e3
+    _, _, _, valid, why = orc.sample_goals(arm, slow, 31, 0, 0, 0, 256, reasons=True)
+    assert not valid.any() and np.all(why == orc.CHART_REASONS.index("speed"))
+    tight = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in arm.items()}
+    tight["qd_taper_a"] = np.zeros(7, np.float32)
+    _, _, _, valid, why = orc.sample_goals(tight, pr, 31, 0, 0, 0, 256, reasons=True)
+    assert not valid.any()
+    assert np.all((why == orc.CHART_REASONS.index("ik")) | (why == orc.CHART_REASONS.index("taper")))
 
 
 def test_goal_chart_rejects_slow_contacts(orc, arm):
@@ -170,7 +196,7 @@ def _J_ref(pr, T, vrel, nu):
 
 
 def test_objective_values_and_special_cases(orc, arm):
-    pr = _tosses(arm, 1)[0]
+    pr = _tosses(arm, 1, reach=None)[0]      # window [0.2, 0.9] s: T = 0.9 at its end
     for T in (0.2, 0.5, 0.9):
         for vrel, nu in ((4.0, 0.5), (12.0, 0.95), (6.0, 1.0)):
             assert orc.objective(pr, T, vrel, nu) == pytest.approx(_J_ref(pr, T, vrel, nu), rel=1e-12, abs=1e-12)
