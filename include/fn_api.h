@@ -515,8 +515,12 @@ fn_status fn_planner_sample_count(fn_planner_t* pl, unsigned long long* count, i
  * evaluations of the parent search, [4] IK starts run by the goal sampler,
  * [5] edges timed by the surrogate's window pass, [6] of those rescanned
  * in full (certificate failed), [7] torque evaluations of the N-ary
- * refinement (FN_PLAN_NARY).  count: host [n] (n <= 8 written).  reset != 0
- * zeroes them all. */
+ * refinement (FN_PLAN_NARY), [8..13] goal-chart draws by outcome (Def. "Goal
+ * chart": phi is undefined where the IK has no solution or qd_g exceeds its
+ * bounds): [8] defined, [9] |v_rel| below v_min, [10] no IK start converged,
+ * [11] IK solution outside the joint box, [12] singular contact-point
+ * Jacobian, [13] qd_g over the velocity taper.  count: host [n] (n <= 14
+ * written).  reset != 0 zeroes them all. */
 fn_status fn_planner_work_counts(fn_planner_t* pl, unsigned long long* count, int n, int reset);
 
 /* Copy problem p's tree to host (any pointer may be NULL): states [n][16],
@@ -535,6 +539,18 @@ fn_status fn_planner_get_tree(fn_planner_t* pl, int p, float* states, float* t,
  * Errors: FN_EINVAL unless eps > 0 finite and 0 <= max_rounds <= 16.
  */
 fn_status fn_planner_set_refine(fn_planner_t* pl, float eps, int max_rounds);
+
+/*
+ * fn_planner_set_grid -- replace the planner's duration grid (Def. "Minimum
+ * feasible time" searched over the N-ary slots laid out on one grid) by the
+ * caller's K values, host T_grid[K] in seconds, positive, finite and strictly
+ * ascending (K = the planner's K).  fn_planner_create builds the log grid
+ * T_lo (T_hi/T_lo)^(k/(K-1)) itself; callers that hold the exact single-
+ * precision grid another component uses give it here so that both examine
+ * the same durations.  A captured iteration is discarded (capture again).
+ * Errors: FN_EINVAL for a bad argument.
+ */
+fn_status fn_planner_set_grid(fn_planner_t* pl, const float* T_grid, int K);
 
 /*
  * The sampling densities of Sec. IV-E ("Batched expansion").
@@ -646,6 +662,25 @@ fn_status fn_planner_get_candidates(fn_planner_t* pl, int p, float* states, floa
  * where the tree has fewer nodes).  The root, parent slot 0, is implicit.
  * Rows beyond the batch of the last iteration are stale.  Synchronous. */
 fn_status fn_planner_get_parents(fn_planner_t* pl, int p, int32_t* nn, int cap);
+/* Copy problem p's per-edge results of the last iteration to host, row b
+ * slot j = the edge from candidate b's parent j (slot 0 the root, slot j > 0
+ * the node nn[b][j-1] of fn_planner_get_parents) to the candidate; arrays
+ * [cap][k], any pointer may be NULL:
+ *   k_star  free edge: the first feasible grid index with t(p) + T_k <=
+ *           t_best (Def. "Minimum feasible time" under Algorithm 1's bound),
+ *           -1 if none; goal edge: 0 if rho_tau, rho_P <= 1 at T_p, else -1;
+ *           -2 for non-finite states (the edge is invalid);
+ *   T       free edge: T_{k*} (+inf if none); goal edge: T_p = T_req - t(p)
+ *           in single precision (NaN where the candidate or the parent does
+ *           not exist);
+ *   rho_v   Eq. (rho)'s velocity term at T (NaN where not evaluated);
+ *   ok      1 iff the edge passed every check of Def. "Feasibility Check"
+ *           at T and the clearance (Algorithm 1's Clear): the edges the
+ *           attach chooses from.
+ * Rows beyond the batch of the last iteration are stale.  Synchronous.
+ * Errors: FN_EINVAL for a bad argument, FN_ECUDA for a failed copy. */
+fn_status fn_planner_get_edges(fn_planner_t* pl, int p, int32_t* k_star, float* T, float* rho_v,
+                               uint8_t* ok, int cap);
 
 /* Routes the free edges of the following iterations (those with an
  * admissible duration) through the duration surrogate: the model predicts a

@@ -139,45 +139,6 @@ __device__ __forceinline__ void seg_closest(const float* a, const float* b, cons
   p[2] = fmaf(u, ab[2], a[2]);
 }
 
-// ---------------------------------------------------------------------------
-// 6x6 symmetric positive definite solve by Cholesky (A packed full 6x6).
-// Returns false if a pivot is not positive.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ bool chol_solve6(float (&A)[6][6], const float* b, float* x) {
-  float L[6][6];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-#pragma unroll
-    for (int j = 0; j <= i; ++j) {
-      float s = A[i][j];
-#pragma unroll
-      for (int m = 0; m < j; ++m) s = fmaf(-L[i][m], L[j][m], s);
-      if (i == j) {
-        if (!(s > 0.f)) return false;
-        L[i][i] = sqrtf(s);
-      } else {
-        L[i][j] = s / L[j][j];
-      }
-    }
-  }
-  float y[6];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    float s = b[i];
-#pragma unroll
-    for (int m = 0; m < i; ++m) s = fmaf(-L[i][m], y[m], s);
-    y[i] = s / L[i][i];
-  }
-#pragma unroll
-  for (int i = 5; i >= 0; --i) {
-    float s = y[i];
-#pragma unroll
-    for (int m = i + 1; m < 6; ++m) s = fmaf(-L[m][i], x[m], s);
-    x[i] = s / L[i][i];
-  }
-  return true;
-}
-
 // hardware reciprocal approximation (rcp.approx, relative error ~2^-23)
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
@@ -235,14 +196,15 @@ __device__ __forceinline__ void complete_basis(const float* u, float* e1, float*
 }
 
 #define FN_IK_ITERS 24
-#define FN_IK_STARTS 3
+#define FN_IK_STARTS 4
 #define FN_IK_LAMBDA 5e-2f
 #define FN_IK_POS_TOL 1e-4f
 #define FN_IK_ROT_TOL 1e-3f
 
 // One damped-least-squares IK run on joints 1-6, q7 fixed: start `st` is the
-// box centre shifted by +-(0, .5, 0, -.5, 0, .5) half-ranges (st = 1, 2) with
-// joint 1 turned towards the target's azimuth; iterates are projected onto
+// box centre shifted by +-(0, .5, 0, -.5, 0, .5) half-ranges (st = 1, 2) or
+// by (0, -.5, 0, -.5, 0, -.5) (st = 3), with joint 1 turned towards the
+// target's azimuth; iterates are projected onto
 // the box; accepted when the position residual < 1e-4 m, the rotation
 // residual (half the sum of column cross products) < 1e-3 and the rotation
 // error is under 90 degrees (trace > 1).  The damped system
@@ -263,8 +225,9 @@ __device__ __forceinline__ void complete_basis(const float* u, float* e1, float*
 __device__ __forceinline__ bool ik_solve_group(const ArmK& A, const float* Rg, const float* pg,
                                                float q7, int st, float& qs) {
   const int s = threadIdx.x & 7;
-  const float sgn = st == 0 ? 0.f : (st == 1 ? 1.f : -1.f);
-  const float pat = (s & 1) ? (s == 3 ? -0.5f : 0.5f) : 0.f;   // (0, .5, 0, -.5, 0, .5)
+  const float sgn = st == 0 ? 0.f : (st == 2 ? -1.f : 1.f);
+  // (0, .5, 0, -.5, 0, .5) for starts 1 and 2, (0, -.5, 0, -.5, 0, -.5) for start 3
+  const float pat = (s & 1) ? (st == 3 ? -0.5f : (s == 3 ? -0.5f : 0.5f)) : 0.f;
   float qj = 0.f;
   if (s < 6) {
     const float c = 0.5f * (A.q_lo[s] + A.q_hi[s]);
@@ -461,50 +424,67 @@ __device__ __forceinline__ bool chart_pose(const ArmK& A, const fn_problem_t& P,
   return true;
 }
 
+// why a goal draw is undefined: the first failing condition of phi(z)
+enum ChartWhy { CHART_OK = 0, CHART_SPEED = 1, CHART_IK = 2, CHART_BOX = 3, CHART_SINGULAR = 4,
+                CHART_TAPER = 5 };
+
 // Goal chart phi(z), velocity part after the IK: the box check, then
-// qd_g = J^T (J J^T)^-1 [v_b; 0] at the contact point (all 7 joints),
-// undefined if any |qd_g,j| exceeds the taper.
-__device__ __forceinline__ bool chart_velocity(const ArmK& A, const ChartPose& o, const float* q,
-                                               float* qd) {
+// qd_g = J_p^T (J_p J_p^T)^-1 v_b with J_p the 3x7 Jacobian of the contact
+// point's linear velocity (v_ee is a linear velocity: the minimum-norm joint
+// velocity that moves the blade at v_b at the contact), undefined if any
+// |qd_g,j| exceeds the taper.  Returns CHART_OK or the failing condition.
+__device__ __forceinline__ int chart_velocity(const ArmK& A, const ChartPose& o, const float* q,
+                                              float* qd) {
 #pragma unroll
   for (int j = 0; j < 7; ++j)
-    if (!(q[j] >= A.q_lo[j] && q[j] <= A.q_hi[j])) return false;
+    if (!(q[j] >= A.q_lo[j] && q[j] <= A.q_hi[j])) return CHART_BOX;
   Axes ax;
   float Ree[9], oee[3];
   fk_axes(A, q, ax, Ree, oee);
-  float J[6][7];
+  float J[3][7];
 #pragma unroll
   for (int m = 0; m < 7; ++m) {
     const float r[3] = {o.c[0] - ax.o[m][0], o.c[1] - ax.o[m][1], o.c[2] - ax.o[m][2]};
     float v[3];
     cross3(ax.z[m], r, v);
     J[0][m] = v[0]; J[1][m] = v[1]; J[2][m] = v[2];
-    J[3][m] = ax.z[m][0]; J[4][m] = ax.z[m][1]; J[5][m] = ax.z[m][2];
   }
-  float M[6][6];
+  // M = J_p J_p^T (symmetric positive definite unless J_p loses rank),
+  // solved by Cholesky
+  float M[3][3];
 #pragma unroll
-  for (int i = 0; i < 6; ++i)
+  for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int j = 0; j < 6; ++j) {
+    for (int j = 0; j < 3; ++j) {
       float sacc = 0.f;
 #pragma unroll
       for (int m = 0; m < 7; ++m) sacc = fmaf(J[i][m], J[j][m], sacc);
       M[i][j] = sacc;
     }
-  const float vt[6] = {o.vb[0], o.vb[1], o.vb[2], 0.f, 0.f, 0.f};
-  float y[6];
-  if (!chol_solve6(M, vt, y)) return false;
+  const float l00sq = M[0][0];
+  if (!(l00sq > 0.f)) return CHART_SINGULAR;
+  const float l00 = sqrtf(l00sq);
+  const float l10 = M[1][0] / l00, l20 = M[2][0] / l00;
+  const float l11sq = fmaf(-l10, l10, M[1][1]);
+  if (!(l11sq > 0.f)) return CHART_SINGULAR;
+  const float l11 = sqrtf(l11sq);
+  const float l21 = fmaf(-l20, l10, M[2][1]) / l11;
+  const float l22sq = fmaf(-l21, l21, fmaf(-l20, l20, M[2][2]));
+  if (!(l22sq > 0.f)) return CHART_SINGULAR;
+  const float l22 = sqrtf(l22sq);
+  const float w0 = o.vb[0] / l00;
+  const float w1 = fmaf(-l10, w0, o.vb[1]) / l11;
+  const float w2 = fmaf(-l21, w1, fmaf(-l20, w0, o.vb[2])) / l22;
+  float y[3];
+  y[2] = w2 / l22;
+  y[1] = fmaf(-l21, y[2], w1) / l11;
+  y[0] = fmaf(-l20, y[2], fmaf(-l10, y[1], w0)) / l00;
 #pragma unroll
-  for (int m = 0; m < 7; ++m) {
-    float acc = 0.f;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) acc = fmaf(J[i][m], y[i], acc);
-    qd[m] = acc;
-  }
+  for (int m = 0; m < 7; ++m) qd[m] = fmaf(J[0][m], y[0], fmaf(J[1][m], y[1], J[2][m] * y[2]));
 #pragma unroll
   for (int j = 0; j < 7; ++j)
-    if (!(fabsf(qd[j]) <= taper(A, j, q[j]))) return false;
-  return true;
+    if (!(fabsf(qd[j]) <= taper(A, j, q[j]))) return CHART_TAPER;
+  return CHART_OK;
 }
 
 // Eq. (objective) with Eq. (terms); flight quantities at T + t_offset,

@@ -24,6 +24,7 @@
 //   output   : rendezvous per problem
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -50,8 +51,9 @@
 #endif
 #define PL_MAX_P 1024
 #define PL_MAX_KEV 40                         // launches traced per iteration
-#define PL_NCOUNT 8   // work counters: probe, verify, mid-probe, kNN pairs, IK starts,
-                      // surrogate-routed edges, surrogate rescans, refine evaluations
+#define PL_NCOUNT 14  // work counters: probe, verify, mid-probe, kNN pairs, IK starts,
+                      // surrogate-routed edges, surrogate rescans, refine evaluations,
+                      // goal draws by outcome (defined, speed, IK, box, singular, taper)
 #define PL_CHORD_THREADS 1024  // block_scan spans 32 warps
 
 namespace fn {
@@ -447,10 +449,11 @@ __global__ void __launch_bounds__(128) k_plan_sample(PlanDev D, ArmK A, long nsl
   if (late) pdl_wait();
 }
 
-// A goal slot: every lane decodes the chart pose, lane groups 0-2 (8 lanes
-// each) run the three IK starts in parallel (ik_solve_group) and the lowest
-// start that converges wins, the same result as trying the starts in order;
-// group 3 repeats start 0 and is ignored.
+// A goal slot: every lane decodes the chart pose, lane groups 0-3 (8 lanes
+// each) run the four IK starts in parallel (ik_solve_group) and the lowest
+// start that converges wins, the same result as trying the starts in order.
+// The draw's outcome (defined, or the condition that left phi undefined) is
+// counted in work counters 8..13.
 __device__ __forceinline__ void sample_goal(const PlanDev& D, const ArmK& A, int p, int b,
                                             int dens) {
   const int lane = threadIdx.x & 31, grp = lane >> 3;
@@ -473,6 +476,7 @@ __device__ __forceinline__ void sample_goal(const PlanDev& D, const ArmK& A, int
   if (defined) {
     if (D.samples && lane == 0) atomicAdd(D.samples + 4, (unsigned long long)FN_IK_STARTS);
     float qs;
+    static_assert(FN_IK_STARTS <= 4, "one 8-lane group per IK start");
     const bool found = ik_solve_group(A, o.Rg, o.pg, o.q7, grp < FN_IK_STARTS ? grp : 0, qs);
     const unsigned won = __ballot_sync(0xffffffffu, found && (lane & 7) == 0 && grp < FN_IK_STARTS);
     winner = won ? (__ffs(won) - 1) : -1;             // first lane of the winning group
@@ -481,6 +485,7 @@ __device__ __forceinline__ void sample_goal(const PlanDev& D, const ArmK& A, int
   }
   if (lane != 0) return;
   if (winner < 0) {   // undefined: |v_rel| too small or no IK start converged
+    if (D.samples) atomicAdd(D.samples + 8 + (defined ? CHART_IK : CHART_SPEED), 1ull);
     D.treq[ci] = o.T;
     D.vrel[ci] = o.vrel;
     D.valid[ci] = 0;
@@ -490,7 +495,9 @@ __device__ __forceinline__ void sample_goal(const PlanDev& D, const ArmK& A, int
     return;
   }
   float qd[7];
-  const bool ok = chart_velocity(A, o, q, qd);
+  const int why = chart_velocity(A, o, q, qd);
+  if (D.samples) atomicAdd(D.samples + 8 + why, 1ull);
+  const bool ok = why == CHART_OK;
   if (!ok)
 #pragma unroll
     for (int j = 0; j < 7; ++j) q[j] = qd[j] = 0.f;
@@ -2553,6 +2560,19 @@ extern "C" fn_status fn_planner_get_tree(fn_planner_t* pl, int p, float* states,
   return ok ? FN_OK : FN_ECUDA;
 }
 
+extern "C" fn_status fn_planner_set_grid(fn_planner_t* pl, const float* T_grid, int K) {
+  if (!pl || !T_grid || K != pl->cfg.K) return FN_EINVAL;
+  for (int k = 0; k < K; ++k) {
+    if (!(T_grid[k] > 0.f) || !std::isfinite(T_grid[k])) return FN_EINVAL;
+    if (k > 0 && !(T_grid[k] > T_grid[k - 1])) return FN_EINVAL;
+  }
+  for (int k = 0; k < K; ++k) pl->grid.T[k] = T_grid[k];
+  // a captured iteration holds the old grid in its launch parameters
+  if (pl->graph_exec) { cudaGraphExecDestroy(pl->graph_exec); pl->graph_exec = nullptr; }
+  if (pl->graph) { cudaGraphDestroy(pl->graph); pl->graph = nullptr; }
+  return FN_OK;
+}
+
 extern "C" fn_status fn_planner_set_refine(fn_planner_t* pl, float eps, int max_rounds) {
   if (!pl || !(eps > 0.f) || !std::isfinite(eps) || max_rounds < 0 || max_rounds > 16)
     return FN_EINVAL;
@@ -2670,6 +2690,22 @@ extern "C" fn_status fn_planner_get_parents(fn_planner_t* pl, int p, int32_t* nn
                     cudaMemcpyDeviceToHost) == cudaSuccess
              ? FN_OK
              : FN_ECUDA;
+}
+
+extern "C" fn_status fn_planner_get_edges(fn_planner_t* pl, int p, int32_t* k_star, float* T,
+                                          float* rho_v, uint8_t* ok, int cap) {
+  if (!pl || p < 0 || p >= pl->cfg.P || cap < 0) return FN_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return FN_ECUDA;
+  const long KP = pl->D.KP;
+  const long m = (long)std::min(cap, pl->cfg.b_max) * KP;
+  const long e0 = (long)p * pl->cfg.b_max * KP;
+  if (m == 0) return FN_OK;
+  bool good = true;
+  if (k_star) good &= cudaMemcpy(k_star, pl->D.e_k + e0, sizeof(int32_t) * m, cudaMemcpyDeviceToHost) == cudaSuccess;
+  if (T) good &= cudaMemcpy(T, pl->D.e_T + e0, sizeof(float) * m, cudaMemcpyDeviceToHost) == cudaSuccess;
+  if (rho_v) good &= cudaMemcpy(rho_v, pl->D.e_rv + e0, sizeof(float) * m, cudaMemcpyDeviceToHost) == cudaSuccess;
+  if (ok) good &= cudaMemcpy(ok, pl->D.e_ok + e0, m, cudaMemcpyDeviceToHost) == cudaSuccess;
+  return good ? FN_OK : FN_ECUDA;
 }
 
 // work counters of the edge kernels (torque evaluations since the last

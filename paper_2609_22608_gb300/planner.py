@@ -11,6 +11,7 @@ import numpy as np
 import torch
 
 from ._lib import arm_struct, check, lib
+from .synth import duration_grid
 
 FN_PLAN_EXTERNAL = 1
 FN_PLAN_PRUNE = 2
@@ -97,6 +98,7 @@ def _bind():
     L.fn_planner_get_tree.argtypes = [vp, i32, vp, vp, vp, vp, vp, C.POINTER(C.c_int), i32]
     L.fn_planner_get_candidates.argtypes = [vp, i32, vp, vp, vp, vp, i32]
     L.fn_planner_get_parents.argtypes = [vp, i32, vp, i32]
+    L.fn_planner_get_edges.argtypes = [vp, i32, vp, vp, vp, vp, i32]
     L.fn_planner_sample_count.argtypes = [vp, vp, i32]
     L.fn_planner_phase_ms.argtypes = [vp, vp]
     L.fn_planner_kernel_ms.argtypes = [vp, vp, vp, i32, C.POINTER(C.c_int)]
@@ -110,15 +112,17 @@ def _bind():
     L.fn_planner_set_candidate_params.argtypes = [vp, i32, vp, i32, vp]
     L.fn_planner_get_candidate_params.argtypes = [vp, i32, vp, i32]
     L.fn_planner_set_refine.argtypes = [vp, C.c_float, i32]
+    L.fn_planner_set_grid.argtypes = [vp, vp, i32]
     for n in ("fn_planner_create", "fn_planner_destroy", "fn_planner_reset", "fn_planner_load_tree",
               "fn_planner_set_candidates", "fn_plan_iteration", "fn_planner_capture",
               "fn_plan_replay", "fn_planner_get_tree", "fn_planner_get_candidates",
-              "fn_planner_get_parents",
+              "fn_planner_get_parents", "fn_planner_get_edges",
               "fn_planner_sample_count", "fn_planner_phase_ms", "fn_planner_autotune",
               "fn_planner_kernel_ms", "fn_planner_work_counts", "fn_planner_set_surrogate",
               "fn_planner_incumbent_path", "fn_planner_set_sampler", "fn_planner_set_density",
               "fn_planner_get_density", "fn_planner_set_candidate_params",
-              "fn_planner_get_candidate_params", "fn_planner_set_refine"):
+              "fn_planner_get_candidate_params", "fn_planner_set_refine",
+              "fn_planner_set_grid"):
         getattr(L, n).restype = i32
     L._planner_bound = True
     return L
@@ -173,6 +177,16 @@ class Planner:
         self.P = P
         self._probs = (FnProblem * P)()
         self._out = (FnRendezvous * P)()
+        # the duration grid of Sec. IV-D as every other component builds it
+        # (FP64 log spacing of the exact endpoints, rounded to FP32)
+        self.set_grid(duration_grid(K, T_lo, T_hi))
+
+    def set_grid(self, grid):
+        """fn_planner_set_grid: the planner's K grid durations (ascending)."""
+        g = np.ascontiguousarray(grid, np.float32)
+        check(lib().fn_planner_set_grid(self.h, g.ctypes.data, int(g.shape[0])),
+              "fn_planner_set_grid")
+        self.grid = g
 
     def close(self):
         if self.h:
@@ -263,6 +277,19 @@ class Planner:
         check(_bind().fn_planner_get_parents(self.h, int(p), nn.ctypes.data, int(B)),
               "fn_planner_get_parents")
         return nn
+
+    def get_edges(self, p, B):
+        """fn_planner_get_edges: per (candidate, parent slot) results [B][k]
+        of the last iteration: dict(k_star, T, rho_v, ok)."""
+        k = self.cfg.k
+        ks = np.zeros((B, k), np.int32)
+        T = np.zeros((B, k), np.float32)
+        rv = np.zeros((B, k), np.float32)
+        ok = np.zeros((B, k), np.uint8)
+        check(_bind().fn_planner_get_edges(self.h, int(p), ks.ctypes.data, T.ctypes.data,
+                                           rv.ctypes.data, ok.ctypes.data, int(B)),
+              "fn_planner_get_edges")
+        return dict(k_star=ks, T=T, rho_v=rv, ok=ok)
 
     def autotune(self, probs, it=0, flags=0, reps=3, stream=None):
         """fn_planner_autotune: returns (chosen variant, ms per variant)."""
@@ -378,12 +405,14 @@ class Planner:
         return [(names[i].decode(), float(ms[i])) for i in range(min(n.value, cap))]
 
     WORK = ("probe", "verify", "mprobe", "knn_pairs", "ik_starts", "surrogate_edges",
-            "surrogate_rescans", "refine")
+            "surrogate_rescans", "refine", "goal_defined", "goal_speed", "goal_ik", "goal_box",
+            "goal_singular", "goal_taper")
 
     def work_counts(self, reset=False):
         """fn_planner_work_counts: dict of the planner's work counters."""
-        c = (C.c_ulonglong * 8)()
-        check(_bind().fn_planner_work_counts(self.h, c, 8, int(bool(reset))),
+        n = len(self.WORK)
+        c = (C.c_ulonglong * n)()
+        check(_bind().fn_planner_work_counts(self.h, c, n, int(bool(reset))),
               "fn_planner_work_counts")
         return dict(zip(self.WORK, [int(x) for x in c]))
 
