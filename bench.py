@@ -115,6 +115,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def gpu_smi_index():
+    """nvidia-smi index of the current CUDA device (through CUDA_VISIBLE_DEVICES)."""
+    import torch
+    i = torch.cuda.current_device()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    if vis and all(x.strip().isdigit() for x in vis.split(",")):
+        return int(vis.split(",")[i])
+    return i
+
+
 # ----------------------------------------------------------------------------
 # workload
 # ----------------------------------------------------------------------------
@@ -255,11 +265,7 @@ def run_ours(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    gpu_index = torch.cuda.current_device()
-    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
-    if vis and vis.split(",")[0].isdigit():
-        gpu_index = int(vis.split(",")[gpu_index])
-    with ClockSampler(gpu_index) as clk:
+    with ClockSampler(gpu_smi_index()) as clk:
         for i in range(args.steps):
             reset_tree()                              # restore the input tree (untimed)
             with torch.cuda.stream(stream):
@@ -525,18 +531,23 @@ def run_surrogate(args):
     ops.time_edges(arm, d0, d1, grid, S, out=full, sample_count=cf)
     surrogate.time_edges_window(arm, d0, d1, grid, S, Y, W=Wn, out=win, sample_count=cw)
 
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
     def timeit(fn):
         for _ in range(args.warmup):
             fn()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
-        for e0, e1 in ev:
+        ms = []
+        for _ in range(args.steps):
+            flush.zero_()                      # L2 flushed between timed calls (untimed)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             fn()
             e1.record(stream)
-        torch.cuda.synchronize()
-        return np.array([x.elapsed_time(y) for x, y in ev])
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return np.array(ms)
 
+    clk = ClockSampler(gpu_smi_index()).__enter__()
     # warp-per-edge kernels (fn_time_edges, fn_time_edges_window)
     ms_full_w = timeit(lambda: ops.time_edges(arm, d0, d1, grid, S, out=full))
     ms_pred = timeit(lambda: mlp.predict(arm, d0, d1, out=Y))
@@ -555,6 +566,7 @@ def run_surrogate(args):
     samp_win = c["probe"] + c["mprobe"] + c["verify"]
     ms_full = timeit(lambda: eng.time(d0, d1))
     ms_win = timeit(lambda: (mlp.predict(arm, d0, d1, out=Y), eng.time_window(d0, d1, Y, W=Wn)))
+    clk.__exit__()
     pw = eng.time_window(d0, d1, Y, W=Wn)
     torch.cuda.synchronize()
     eng.close()
@@ -579,7 +591,9 @@ def run_surrogate(args):
                                "window 16 (+1 certificate index)",
                    "train_edges": ntr, "label_s": label_s, "train_s": train_s,
                    "loss_per_epoch": hist,
-                   "engine": "packed (fn_edges_time / fn_edges_time_window)"},
+                   "engine": "packed (fn_edges_time / fn_edges_time_window)",
+                   "l2": "flushed between timed calls"},
+        "clocks": clk.summary(),
         "full_scan": {"edges_per_s": v_full, "ms": best_full,
                       "packed": {"ms": float(np.mean(ms_full)), "samples": samp_full,
                                  "tflops": samp_full * FLOP_PER_SAMPLE / (np.mean(ms_full) / 1e3) / 1e12,
@@ -637,7 +651,7 @@ def run_nary(args):
             ms.append(e0.elapsed_time(e1))
         return np.array(ms)
 
-    with ClockSampler(torch.cuda.current_device()) as clk:
+    with ClockSampler(gpu_smi_index()) as clk:
         ms_grid = timeit(lambda: ops.time_edges(arm, d0, d1, grid, S, out=full))
         ms_nary = timeit(lambda: ops.time_edges_nary(arm, d0, d1, grid, S, args.eps, out=nary))
     k = nary["k_star"].cpu().numpy()
@@ -701,7 +715,7 @@ def run_control(args):
     rng = np.random.default_rng(args.seed)
     rate = np.full(7, 1000.0, np.float32)
     ctrl = {}
-    with ClockSampler(torch.cuda.current_device()) as clk:
+    with ClockSampler(gpu_smi_index()) as clk:
         for B in (64, 65536):
             x = synth.random_states(arm, B, 11 + B)
             g = synth.random_states(arm, B, 12 + B)
@@ -739,19 +753,22 @@ def run_control(args):
 
 
 def _timed_replays(pl, probs, n, stream, first_it=0, between=None):
+    """n graph replays timed one by one with CUDA events on the stream;
+    returns (ms [n], last rendezvous, clocks sampled meanwhile)."""
     import torch
     ms = []
-    for i in range(n):
-        if between is not None:
-            between(i)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        out = pl.replay(probs, first_it + i, stream=stream)
-        b.record(stream)
-        b.synchronize()
-        ms.append(a.elapsed_time(b))
-    return np.array(ms), out
+    with ClockSampler(gpu_smi_index()) as clk:
+        for i in range(n):
+            if between is not None:
+                between(i)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            out = pl.replay(probs, first_it + i, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+    return np.array(ms), out, clk.summary()
 
 
 def train_surrogate(arm, n_edges, seed):
@@ -797,7 +814,7 @@ def run_batched(args, surrogate_W=0, densities=False, nary=False):
         toss = synth.random_toss(arm, 300 + p)
         root = synth.random_states(arm, 1, 8000 + p)[0]
         pr = synth.make_problem(toss, root=root)
-        st, par, t = synth.random_tree(arm, int(N[p]), 300 + p, root=root)
+        st, par, t = synth.random_tree(arm, int(N[p]), 300 + p, root=root, t_max=pr["t_fall"])
         trees.append((st, t, par))
         probs.append(P.problem_struct(pr, int(B[p]), int(B[p]) // 2, root=root, seed=900 + p))
     pl = P.Planner(arm, P=Pn, n_cap=int(N.max()) + 5 * 4096, b_max=4096, k=8, K=128, S=64)
@@ -825,7 +842,7 @@ def run_batched(args, surrogate_W=0, densities=False, nary=False):
     extra = {}
     if surrogate_W > 0:
         t0 = time.perf_counter()
-        ms_plain, _ = timed()
+        ms_plain, _, clk_plain = timed()
         plain_s = time.perf_counter() - t0
         t0 = time.perf_counter()
         mlp = train_surrogate(arm, args.train_edges // 4, args.seed)
@@ -833,7 +850,7 @@ def run_batched(args, surrogate_W=0, densities=False, nary=False):
         mlp.error(reset=True)
         pl.set_surrogate(mlp, surrogate_W)
         t0 = time.perf_counter()
-        ms, out = timed()
+        ms, out, clk = timed()
         sur_s = time.perf_counter() - t0
         wc = pl.work_counts()
         mlp_err = bool(mlp.error())
@@ -846,13 +863,13 @@ def run_batched(args, surrogate_W=0, densities=False, nary=False):
                                "routed_edges_per_step": wc["surrogate_edges"] / steps,
                                "rescanned_fraction": wc["surrogate_rescans"] / max(1, wc["surrogate_edges"])},
                  "plain": {"ms_per_step": float(np.mean(ms_plain)),
-                           "p99_ms": float(np.percentile(ms_plain, 99))},
+                           "p99_ms": float(np.percentile(ms_plain, 99)), "clocks": clk_plain},
                  "speedup_vs_plain": float(np.mean(ms_plain) / np.mean(ms))}
     elif nary:
-        ms_plain, out_plain = timed()
+        ms_plain, out_plain, clk_plain = timed()
         wc_plain = pl.work_counts()
         pl.set_refine(args.eps, 8)
-        ms, out = timed(P.FN_PLAN_NARY)
+        ms, out, clk = timed(P.FN_PLAN_NARY)
         wc = pl.work_counts()
         extra = {"refine": {"eps_s": args.eps, "max_rounds": 8,
                             "refine_torque_evaluations_per_step": wc["refine"] / steps,
@@ -861,10 +878,11 @@ def run_batched(args, surrogate_W=0, densities=False, nary=False):
                             "nodes_added_last": int(sum(o["n_added"] for o in out))},
                  "plain": {"ms_per_step": float(np.mean(ms_plain)),
                            "p99_ms": float(np.percentile(ms_plain, 99)),
-                           "nodes_added_last": int(sum(o["n_added"] for o in out_plain))},
+                           "nodes_added_last": int(sum(o["n_added"] for o in out_plain)),
+                           "clocks": clk_plain},
                  "cost_vs_plain": float(np.mean(ms) / np.mean(ms_plain))}
     elif densities:
-        ms_plain, out_plain = timed()
+        ms_plain, out_plain, clk_plain = timed()
         wc_plain = pl.work_counts()
         drng = np.random.default_rng([0xD5, args.seed])
         for p in range(Pn):
@@ -872,7 +890,7 @@ def run_batched(args, surrogate_W=0, densities=False, nary=False):
                                    mu=drng.uniform(0.1, 0.9, (4, 9)).astype(np.float32),
                                    sd=np.full((4, 9), 0.08, np.float32)))
         flags = P.FN_PLAN_DENSITY | P.FN_PLAN_CHORD | P.FN_PLAN_REFIT
-        ms, out = timed(flags)
+        ms, out, clk = timed(flags)
         wc = pl.work_counts()
 
         def evals(w):
@@ -885,10 +903,12 @@ def run_batched(args, surrogate_W=0, densities=False, nary=False):
                  "plain": {"ms_per_step": float(np.mean(ms_plain)),
                            "p99_ms": float(np.percentile(ms_plain, 99)),
                            "torque_evaluations_per_step": evals(wc_plain),
-                           "nodes_added_last": int(sum(o["n_added"] for o in out_plain))},
+                           "nodes_added_last": int(sum(o["n_added"] for o in out_plain)),
+                           "clocks": clk_plain},
                  "cost_vs_plain": float(np.mean(ms) / np.mean(ms_plain))}
     else:
-        ms, out = timed()
+        ms, out, clk = timed()
+    wc_last = pl.work_counts()
     pl.close()
     edges = int(B.sum()) * 8
     return {
@@ -905,6 +925,7 @@ def run_batched(args, surrogate_W=0, densities=False, nary=False):
                    "edges_per_step": edges, "edge_variant": tuned[0],
                    "edge_variant_ms": tuned[1]},
         "nodes_added_last": int(sum(o["n_added"] for o in out)),
+        "clocks": clk,
         **extra,
     }
 
@@ -931,6 +952,7 @@ def run_anytime(args):
     pl.capture(P.FN_PLAN_PRUNE, stream=stream)
     cycles = 200
     ms, nodes, added = [], [], []
+    clk = ClockSampler(gpu_smi_index()).__enter__()
     for c in range(cycles):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -941,6 +963,7 @@ def run_anytime(args):
         ms.append(a.elapsed_time(b))
         nodes.append(out["n_nodes"])
         added.append(out["n_added"])
+    clk.__exit__()
     pl.close()
     ms = np.array(ms)
     edges = 8192 * 16
@@ -958,6 +981,7 @@ def run_anytime(args):
         "tree_nodes": {"final": nodes[-1], "max": int(max(nodes)),
                        "added_mean": float(np.mean(added))},
         "incumbent_J": out["J"], "t_best": out["t_best"],
+        "clocks": clk.summary(),
     }
 
 

@@ -3,11 +3,17 @@
 //
 // One warp times one edge.  The edge's two states sit in the warp's shared
 // slot `es` (32 floats); every lane owns a column of the warp's coefficient
-// buffer `cb` ([FN_CUBIC_WORDS][32] floats).
-//   probe : lanes take 32 consecutive grid durations and evaluate the end
-//           samples u = 0 and u = 1, then four interior samples (plain FP32
-//           coefficients); a violation at any probed sample proves the
-//           duration infeasible;
+// buffer `cb` ([FN_CUBIC_WORDS][32] floats); `split` is the warp's slot of
+// FN_SPLIT_WORDS floats for the end-sample torque split.
+//   split : once per edge, lanes 0..5 = (end, part) evaluate Eq. (torque) at
+//           the edge's two end states: tau(T) = alpha / T^2 + beta / T + gamma
+//           at u = 0 and u = 1 (end_torque_part's decomposition), because the
+//           end states do not depend on T and the acceleration enters
+//           Eq. (torque) affinely;
+//   probe : lanes take 32 consecutive grid durations and check both end
+//           samples from the split (no torque evaluation), then four
+//           interior samples (plain FP32 coefficients); a violation at any
+//           probed sample proves the duration infeasible;
 //   verify: surviving durations in ascending order, all S samples with lanes
 //           = samples (compensated coefficients), warp-ballot exit at the first
 //           violating batch; the first duration that passes is k*, every lower
@@ -46,46 +52,126 @@ __device__ __forceinline__ int mid_probe_index(int j, int S) {
   return (int)((2 * (j + 1) * (S - 1) + 5) / 10);  // round((j+1)(S-1)/5)
 }
 
+// The warp's end-sample split: per end (u = 0, u = 1) 28 floats, alpha[7],
+// beta[7], gamma[7] and the end velocity qd[7] (16-byte aligned slot).
+#define FN_SPLIT_WORDS 56
+
+// es[7] (a pad slot of the first state) marks whether `split` holds the
+// staged edge's split: stage_rows clears it, the scan sets it.
+#define FN_SPLIT_MARK 7
+
 // Stage edge (row0, row1) in the warp's shared slot; returns whether all 28
-// state values are finite.  `pad` lanes (index 7 of each half-row) are ignored.
+// state values are finite.  `pad` lanes (index 7 of each half-row) are
+// ignored; slot 7 is cleared (no split computed for this edge yet).
 __device__ __forceinline__ bool stage_rows(const float* row0, const float* row1, float* es) {
   const int lane = threadIdx.x & 31;
   const float v = lane < 16 ? __ldg(row0 + lane) : __ldg(row1 + (lane - 16));
   __syncwarp();
-  es[lane] = v;
+  es[lane] = lane == FN_SPLIT_MARK ? 0.f : v;
   __syncwarp();
   const bool pad = (lane & 7) == 7;
   return __all_sync(0xffffffffu, pad || isfinite(v));
 }
 
+// joint j's entry of a per-joint table of the robot, for a lane-dependent j
+// (a select chain over the seven constants: the table stays an immediate
+// operand instead of an indexed load from the parameter space)
+__device__ __forceinline__ float joint_pick(const float (&t)[7], int j) {
+  float v = t[0];
+#pragma unroll
+  for (int i = 1; i < 7; ++i) v = j == i ? t[i] : v;
+  return v;
+}
+
+// rho_v at duration T: lane j < 7 takes joint j's exact velocity extremum
+// (rho_v_joint's arithmetic with the joint's coefficients built from the
+// staged edge), one code path for every lane; the warp maximum is returned
+// to all lanes.
 __device__ __forceinline__ float warp_rho_v(const ArmK& A, const float* es, float T) {
   const int lane = threadIdx.x & 31;
-  float r = 0.f;
+  float best = 0.f;
   if (lane < 7) {
-    Cubic c;
-    cubic_coef_sh<true>(es, T, c);
+    const int j = lane;
+    float b1, b2, b3;
+    joint_coef<true>(es[j], es[8 + j], es[16 + j], es[24 + j], T, b1, b2, b3);
+    const float q0 = es[j], iT = 1.0f / T;
+    const float lo = joint_pick(A.q_lo, j), hi = joint_pick(A.q_hi, j);
+    const float vmax = joint_pick(A.qd_max, j), t2a = joint_pick(A.taper2a, j);
+    float cand[3] = {0.f, 1.f, -1.f};
+    if (b3 != 0.f) {
+      const float us = -b2 / (3.0f * b3);
+      if (us > 0.f && us < 1.f) cand[2] = us;
+    }
 #pragma unroll
-    for (int j = 0; j < 7; ++j)
-      if (lane == j) r = rho_v_joint(A, c, j);
+    for (int i = 0; i < 3; ++i) {
+      const float u = cand[i];
+      if (u < 0.f) continue;
+      const float pos = fmaf(fmaf(fmaf(b3, u, b2), u, b1), u, q0);
+      const float vel = fmaf(fmaf(3.0f * b3, u, 2.0f * b2), u, b1) * iT;
+      const float m = fmaxf(fminf(pos - lo, hi - pos), 0.f);
+      const float bound = fminf(vmax, sqrtf(t2a * m));
+      float r;
+      if (bound > 0.f) r = fabsf(vel) / bound;
+      else r = (vel != 0.f) ? INFINITY : 0.f;
+      best = fmaxf(best, r);
+    }
   }
-  return warp_max(r);
+  return warp_max(best);
+}
+
+// Both end samples of duration T from the split: tau = alpha / T^2 +
+// beta / T + gamma per joint, rho_tau and rho_P at the end velocity.
+// Returns whether both pass; fail0: the u = 0 end failed.
+__device__ __forceinline__ bool end_probe_pass(const ArmK& A, const float* split, float T,
+                                               bool& fail0) {
+  const float iT = 1.0f / T, iT2 = iT * iT;
+  bool pass = true;
+#pragma unroll
+  for (int end = 0; end < 2; ++end) {
+    const float4* c4 = reinterpret_cast<const float4*>(split + 28 * end);
+    float f[28];
+#pragma unroll
+    for (int v = 0; v < 7; ++v) {
+      const float4 t = c4[v];
+      f[4 * v] = t.x; f[4 * v + 1] = t.y; f[4 * v + 2] = t.z; f[4 * v + 3] = t.w;
+    }
+    float r = 0.f, pw = 0.f;
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      const float tau = fmaf(f[j], iT2, fmaf(f[7 + j], iT, f[14 + j]));
+      r = fmaxf(r, fabsf(tau) * A.inv_tau[j]);
+      pw = fmaf(tau, f[21 + j], pw);
+    }
+    const bool pe = r <= 1.f && fabsf(pw) * A.inv_w <= 1.f;
+    if (end == 0) fail0 = !pe;
+    pass = pass && pe;
+  }
+  return pass;
 }
 
 // Edge scan with a single torque-evaluation call site (the RNEA body is
-// ~1.2k instructions; inlining it at several call sites overflowed the
-// instruction cache).  Each pass evaluates at most one sample per lane:
-//   PROBE_LO : lanes = grid durations base+lane, sample u = 0
-//   PROBE_HI : the lanes whose u = 0 passed, sample u = 1
+// ~1k instructions; inlining it at several call sites overflowed the
+// instruction cache) and a single coefficient-build site.  Passes:
+//   SPLIT    : (once per staged edge) lanes 0..5 = (end, part) evaluate the
+//              end-sample split into `split`; part 0 is Eq. (torque) at the
+//              end state with zero acceleration (gamma), parts 1 and 2 the
+//              mass matrix plus armature times the two acceleration vectors
+//              (alpha, beta: gravity, velocity and friction off)
+//   PROBE_END: lanes = grid durations base+lane, both end samples from the
+//              split (no torque evaluation)
+//   PROBE_W  : (wmode 2) one sample, the witness, at the remaining survivors
+//              (plain coefficients): after a failed verify, that duration's
+//              first violating sample; on the first chunk, the caller's w_in
 //   PROBE_MID: the lanes still passing, interior samples mid_probe_index(j)
 //   VERIFY   : lanes = samples (s0 + lane) of one duration, compensated
 //              coefficients, until a violating batch or all S samples pass
-//   PROBE_W  : (wmode 2) one sample, the witness, at the remaining survivors
-//              (plain coefficients): after a failed verify, that duration's
-//              first violating sample; at the start, the caller's w_in
 // Grid mode (fixed = false): returns the first feasible index in
-// [k_begin, Kadm) (k_begin = 0 unless a caller scans a sub-range).
+// [k_begin, Kadm) (k_begin = 0 unless a caller scans a sub-range); `split`
+// is the warp's FN_SPLIT_WORDS slot (16-byte aligned), reused across calls
+// on the same staged edge.
 // Fixed mode: one duration Tfix is verified (all S samples when exact,
-// else up to the first violating batch); returns 0 if it passes, else -1.
+// else up to the first violating batch); returns 0 if it passes, else -1;
+// `split` may be null.
 // Witness modes (grid mode only; callers other than the N-ary refinement
 // pass 0 and the code folds away):
 //   wmode 1: record, per duration, the sample that proved it infeasible, and
@@ -93,112 +179,181 @@ __device__ __forceinline__ float warp_rho_v(const ArmK& A, const float* es, floa
 //            (of the last admissible duration if none passes; -1 if it was
 //            not in the result's chunk of 32);
 //   wmode 2: as 1, plus the witness probes (PROBE_W), starting with w_in
-//            (if >= 0) at every duration in place of the end probes.
-__device__ __forceinline__ int edge_scan(const ArmK& A, const float* es, CubicLane cb,
-                                         LaneWrench wr, const float* sT, int Kadm, int S,
+//            (if it is an interior sample) after the first chunk's end probes.
+__device__ __forceinline__ int edge_scan(const ArmK& A, float* es, CubicLane cb, LaneWrench wr,
+                                         float* split, const float* sT, int Kadm, int S,
                                          bool fixed, float Tfix, bool exact, float& rt, float& rp,
                                          unsigned& nsamp, int k_begin = 0, int wmode = 0,
                                          int w_in = -1, int* w_out = nullptr) {
-  enum { PROBE_LO = 0, PROBE_HI = 1, VERIFY = 2, PROBE_MID = 3, PROBE_W = 4 };
+  enum { SPLIT = 0, PROBE_END = 1, PROBE_W = 2, PROBE_MID = 3, VERIFY = 4 };
+  enum { COEF_NONE = 0, COEF_PLAIN = 1, COEF_EXACT = 2, COEF_SPLIT = 3 };
   const int lane = threadIdx.x & 31;
-  int mode = PROBE_LO, base = k_begin, kk = 0, s0 = 0, mj = 0, sw = 0;
+  int mode = PROBE_END, base = k_begin, kk = 0, s0 = 0, mj = 0, sw = 0, coef = COEF_NONE;
   int kill = -1;        // wmode > 0: sample that proved duration base + lane infeasible
-  unsigned cand = 0u;   // PROBE_HI: lanes to evaluate; VERIFY: durations left in the chunk
+  unsigned cand = 0u;   // probes: durations still passing; VERIFY: durations left in the chunk
   float mt = 0.f, mp = 0.f;
   bool bad = false;
+  bool w_pending = wmode == 2 && w_in > 0 && w_in < S - 1;   // interior witness of the caller
+  bool mid_done = false;                // this chunk's survivors had their interior probes
   if (w_out) *w_out = -1;
   if (fixed) {
     mode = VERIFY;
-    Cubic c;
-    cubic_coef_sh<true>(es, Tfix, c);
-    cb.store(c);
+    coef = COEF_EXACT;
   } else {
     if (Kadm <= k_begin) return -1;
-    Cubic c;
-    if (base + lane < Kadm) cubic_coef_sh<false>(es, sT[base + lane], c);
-    cb.store(c);
-    if (wmode == 2 && w_in >= 0) {
-      mode = PROBE_W;
-      sw = w_in;
-      cand = __ballot_sync(0xffffffffu, base + lane < Kadm);
+    if (es[FN_SPLIT_MARK] == 0.f) {
+      mode = SPLIT;
+      coef = COEF_SPLIT;
     }
   }
   for (;;) {
-    bool active;
-    int si;               // sample index of this pass (probes)
-    if (mode == VERIFY) {
-      active = s0 + lane < S;
-      si = s0 + lane;
-    } else if (mode == PROBE_MID || mode == PROBE_W) {
-      active = (cand >> lane) & 1u;
-      si = mode == PROBE_MID ? mid_probe_index(mj, S) : sw;
-    } else {
-      active = mode == PROBE_LO ? (base + lane < Kadm) : ((cand >> lane) & 1u);
-      si = mode == PROBE_LO ? 0 : S - 1;
+    if (coef != COEF_NONE) {           // the single coefficient-build site
+      Cubic c;
+      if (coef == COEF_SPLIT) {
+        // lane l < 6: end l / 3, part l % 3, as a cubic whose u = 0 sample
+        // is (q, qd, qdd) exactly (iT = iT2 = 1, b1 = qd, b2 = qdd / 2)
+        const int end = lane >= 3 ? 1 : 0, part = lane - 3 * end;
+        c.iT = 1.f;
+        c.iT2 = 1.f;
+#pragma unroll
+        for (int j = 0; j < 7; ++j) {
+          const float d = es[16 + j] - es[j];
+          const float qa = end ? -6.0f * d : 6.0f * d;
+          const float qb = end ? fmaf(4.0f, es[24 + j], 2.0f * es[8 + j])
+                               : -fmaf(4.0f, es[8 + j], 2.0f * es[24 + j]);
+          c.q0[j] = es[16 * end + j];
+          c.b1[j] = part == 0 ? es[16 * end + 8 + j] : 0.f;
+          c.b2[j] = 0.5f * (part == 0 ? 0.f : (part == 1 ? qa : qb));
+          c.b3[j] = 0.f;
+        }
+      } else if (coef == COEF_PLAIN) {
+        if (base + lane < Kadm) cubic_coef_sh<false>(es, sT[base + lane], c);
+      } else {
+        cubic_coef_sh<true>(es, fixed ? Tfix : sT[kk], c);
+      }
+      cb.store(c);
+      coef = COEF_NONE;
     }
-    const float u = sample_u(si, S);
-    float a = 0.f, b = 0.f;
-    if (active) sample_ratios(A, cb, u, a, b, wr);   // the single call site
-    const bool pass = active && a <= 1.f && b <= 1.f;
-    const unsigned act = __ballot_sync(0xffffffffu, active);
-    const unsigned ok = __ballot_sync(0xffffffffu, pass);
-    nsamp += __popc(act);
-    if (wmode > 0 && mode != VERIFY && active && !pass) kill = si;
     int next_dur = -1;  // duration to verify next, if any
-    if (mode == PROBE_LO) {
-      if (ok) {
-        cand = ok;
-        mode = PROBE_HI;
-        continue;
+    if (mode == PROBE_END) {
+      const int k = base + lane;
+      const bool active = k < Kadm;
+      bool f0 = false;
+      const bool pass = active && end_probe_pass(A, split, sT[active ? k : base], f0);
+      if (wmode > 0 && active && !pass) kill = f0 ? 0 : S - 1;
+      cand = __ballot_sync(0xffffffffu, pass);
+      if (cand) {
+        if (w_pending) {
+          w_pending = false;
+          mode = PROBE_W;
+          sw = w_in;
+          coef = COEF_PLAIN;
+          continue;
+        }
+        if (S > 2) {
+          mode = PROBE_MID;
+          mj = 0;
+          coef = COEF_PLAIN;
+          continue;
+        }
+        next_dur = base + __ffs(cand) - 1;
       }
-    } else if (mode == PROBE_HI || mode == PROBE_MID || mode == PROBE_W) {
-      cand = ok;                       // durations whose probes so far pass
-      if (cand && mode == PROBE_HI && S > 2) {
-        mode = PROBE_MID;
-        mj = 0;
-        continue;
-      }
-      if (cand && mode == PROBE_MID && ++mj < FN_MID_PROBES) continue;
-      if (cand) next_dur = base + __ffs(cand) - 1;
     } else {
-      if (active) { mt = fmaxf(mt, a); mp = fmaxf(mp, b); }
-      const bool viol = (act & ~ok) != 0u;
-      if (fixed) {
-        bad = bad || viol;
-        if ((!viol || exact) && s0 + 32 < S) {
+      bool active;
+      int si;               // sample index of this pass (probes)
+      if (mode == VERIFY) {
+        active = s0 + lane < S;
+        si = s0 + lane;
+      } else if (mode == SPLIT) {
+        active = lane < 6;
+        si = 0;
+      } else {
+        active = (cand >> lane) & 1u;
+        si = mode == PROBE_MID ? mid_probe_index(mj, S) : sw;
+      }
+      const float u = sample_u(si, S);
+      const bool sp = mode == SPLIT;
+      const float on = (sp && lane != 0 && lane != 3) ? 0.f : 1.f;   // parts 1, 2: M + I_m only
+      const int so = lane >= 3 ? 28 : 0;
+      const int sj = (lane == 0 || lane == 3) ? 14 : (lane == 1 || lane == 4 ? 0 : 7);
+      float a = 0.f, b = 0.f;
+      if (active) {                    // the single torque-evaluation call site
+        float r = 0.f, pw = 0.f;
+        torque_at(
+            A, cb, u,
+            [&](int j, float tau, float v) {
+              if (sp) split[so + sj + j] = tau;
+              r = fmaxf(r, fabsf(tau) * A.inv_tau[j]);
+              pw = fmaf(tau, v, pw);
+            },
+            wr, on, on);
+        a = r;
+        b = fabsf(pw) * A.inv_w;
+      }
+      const bool pass = active && a <= 1.f && b <= 1.f;
+      const unsigned act = __ballot_sync(0xffffffffu, active);
+      const unsigned ok = __ballot_sync(0xffffffffu, pass);
+      nsamp += __popc(act);
+      if (sp) {                        // end velocities; the split is ready
+        if (lane < 7) {
+          split[21 + lane] = es[8 + lane];
+          split[49 + lane] = es[24 + lane];
+        }
+        __syncwarp();
+        if (lane == 0) es[FN_SPLIT_MARK] = 1.f;
+        __syncwarp();
+        mode = PROBE_END;
+        continue;
+      }
+      if (wmode > 0 && mode != VERIFY && active && !pass) kill = si;
+      if (mode == PROBE_W || mode == PROBE_MID) {
+        cand = ok;                     // durations whose probes so far pass
+        if (cand && mode == PROBE_W && S > 2 && !mid_done) {
+          mode = PROBE_MID;            // the chunk's interior probes, once
+          mj = 0;
+          continue;
+        }
+        if (mode == PROBE_MID) mid_done = true;
+        if (cand && mode == PROBE_MID && ++mj < FN_MID_PROBES) continue;
+        if (cand) next_dur = base + __ffs(cand) - 1;
+      } else {                         // VERIFY
+        if (active) { mt = fmaxf(mt, a); mp = fmaxf(mp, b); }
+        const bool viol = (act & ~ok) != 0u;
+        if (fixed) {
+          bad = bad || viol;
+          if ((!viol || exact) && s0 + 32 < S) {
+            s0 += 32;
+            continue;
+          }
+          rt = warp_max(mt);
+          rp = warp_max(mp);
+          return bad ? -1 : 0;
+        }
+        if (viol) {                    // kk is infeasible
+          if (wmode > 0) {
+            sw = s0 + __ffs(act & ~ok) - 1;
+            if (lane == kk - base) kill = sw;
+          }
+          cand &= cand - 1;
+          if (cand && wmode == 2) {    // probe its witness sample at the rest
+            mode = PROBE_W;
+            coef = COEF_PLAIN;
+            continue;
+          }
+          if (cand) next_dur = base + __ffs(cand) - 1;
+        } else if (s0 + 32 < S) {
           s0 += 32;
           continue;
+        } else {
+          rt = warp_max(mt);
+          rp = warp_max(mp);
+          if (w_out) {
+            const int below = kk - 1 - base;
+            const int w = __shfl_sync(0xffffffffu, kill, below >= 0 ? below : 0);
+            *w_out = below >= 0 ? w : -1;
+          }
+          return kk;
         }
-        rt = warp_max(mt);
-        rp = warp_max(mp);
-        return bad ? -1 : 0;
-      }
-      if (viol) {                      // kk is infeasible
-        if (wmode > 0) {
-          sw = s0 + __ffs(act & ~ok) - 1;
-          if (lane == kk - base) kill = sw;
-        }
-        cand &= cand - 1;
-        if (cand && wmode == 2) {      // probe its witness sample at the rest
-          mode = PROBE_W;
-          Cubic c;
-          if (base + lane < Kadm) cubic_coef_sh<false>(es, sT[base + lane], c);
-          cb.store(c);
-          continue;
-        }
-        if (cand) next_dur = base + __ffs(cand) - 1;
-      } else if (s0 + 32 < S) {
-        s0 += 32;
-        continue;
-      } else {
-        rt = warp_max(mt);
-        rp = warp_max(mp);
-        if (w_out) {
-          const int below = kk - 1 - base;
-          const int w = __shfl_sync(0xffffffffu, kill, below >= 0 ? below : 0);
-          *w_out = below >= 0 ? w : -1;
-        }
-        return kk;
       }
     }
     if (next_dur >= 0) {               // (re)start VERIFY on the next survivor
@@ -206,9 +361,7 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, const float* es, CubicLa
       s0 = 0;
       mt = mp = 0.f;
       mode = VERIFY;
-      Cubic c;
-      cubic_coef_sh<true>(es, sT[kk], c);
-      cb.store(c);
+      coef = COEF_EXACT;
       continue;
     }
     // nothing left in this chunk of 32 durations: probe the next one
@@ -220,11 +373,9 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, const float* es, CubicLa
     base += 32;
     if (base >= Kadm) return -1;
     kill = -1;
-    mode = PROBE_LO;
+    mode = PROBE_END;
+    mid_done = false;
     cand = 0u;
-    Cubic c;
-    if (base + lane < Kadm) cubic_coef_sh<false>(es, sT[base + lane], c);
-    cb.store(c);
   }
 }
 
@@ -244,10 +395,10 @@ __device__ __forceinline__ int grid_prefix(const float* sT, int K, float cap) {
 // (Tp = +inf for no cap).
 // exact = false lets a fixed-duration check stop at the first violating batch
 // (its ratios are then lower bounds; ok is exact either way).
-__device__ __forceinline__ EdgeResult time_edge(const ArmK& A, const float* es, CubicLane cb,
-                                                LaneWrench wr, bool finite, bool fixed, float Tp,
-                                                const float* sT, int K, int S, bool exact,
-                                                unsigned& nsamp) {
+__device__ __forceinline__ EdgeResult time_edge(const ArmK& A, float* es, CubicLane cb,
+                                                LaneWrench wr, float* split, bool finite,
+                                                bool fixed, float Tp, const float* sT, int K,
+                                                int S, bool exact, unsigned& nsamp) {
   EdgeResult r;
   r.rt = r.rp = r.rv = NAN;
   r.ok = false;
@@ -257,7 +408,8 @@ __device__ __forceinline__ EdgeResult time_edge(const ArmK& A, const float* es, 
       r.T = NAN;
       return r;
     }
-    const bool pass = edge_scan(A, es, cb, wr, sT, 0, S, true, Tp, exact, r.rt, r.rp, nsamp) == 0;
+    const bool pass =
+        edge_scan(A, es, cb, wr, split, sT, 0, S, true, Tp, exact, r.rt, r.rp, nsamp) == 0;
     if (exact || pass) r.rv = warp_rho_v(A, es, Tp);
     r.k = pass ? 0 : -1;
     r.T = Tp;
@@ -270,7 +422,7 @@ __device__ __forceinline__ EdgeResult time_edge(const ArmK& A, const float* es, 
     return r;
   }
   const int Kadm = grid_prefix(sT, K, Tp);
-  r.k = edge_scan(A, es, cb, wr, sT, Kadm, S, false, 0.f, false, r.rt, r.rp, nsamp);
+  r.k = edge_scan(A, es, cb, wr, split, sT, Kadm, S, false, 0.f, false, r.rt, r.rp, nsamp);
   if (r.k >= 0) {
     r.T = sT[r.k];
     r.rv = warp_rho_v(A, es, r.T);

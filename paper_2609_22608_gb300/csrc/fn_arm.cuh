@@ -181,6 +181,56 @@ __device__ __forceinline__ void cubic_eval(const CubicLane& c, int j, float u, f
 }
 
 // ---------------------------------------------------------------------------
+// Elementary functions of the torque evaluation, branch-free and inlined
+// once per use (the library versions carry a large-argument path whose code
+// is replicated at every call site of the unrolled link loop).
+//
+// fn_sincos: Cody-Waite reduction x = k pi/2 + r with pi/2 split into a
+// single-precision head and tail, |r| <= pi/4, then the Taylor polynomials
+// of sin (to r^9) and cos (to r^10), whose truncation errors on |r| <= pi/4
+// are below (pi/4)^11/11! = 1.8e-9 and (pi/4)^12/12! = 1.2e-10, far below
+// the single-precision rounding of the result (~6e-8); the quadrant k mod 4
+// swaps and negates.  Valid for |x| < 2^10 (the reduction's k * tail stays
+// exact to a few ulp); joint angles plus offsets are a few radians.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void fn_sincos(float x, float* s, float* c) {
+  const float k = rintf(x * 0.636619772367581343f);            // x / (pi/2), nearest
+  float r = fmaf(-k, 1.57079637050628662109375f, x);           // pi/2 head (nearest float)
+  r = fmaf(-k, -4.37113900018624283e-8f, r);                   // pi/2 - head
+  const float r2 = r * r;
+  float sp = fmaf(r2, 2.75573192239858906526e-6f, -1.98412698412698412698e-4f);   // 1/9!, -1/7!
+  sp = fmaf(r2, sp, 8.33333333333333333333e-3f);                                   // 1/5!
+  sp = fmaf(r2, sp, -1.66666666666666666667e-1f);                                  // -1/3!
+  const float sr = fmaf(r * r2, sp, r);
+  float cp = fmaf(r2, -2.75573192239858906526e-7f, 2.48015873015873015873e-5f);   // -1/10!, 1/8!
+  cp = fmaf(r2, cp, -1.38888888888888888889e-3f);                                  // -1/6!
+  cp = fmaf(r2, cp, 4.16666666666666666667e-2f);                                   // 1/4!
+  cp = fmaf(r2, cp, -0.5f);                                                        // -1/2!
+  const float cr = fmaf(r2, cp, 1.0f);
+  const int q = __float2int_rn(k) & 3;
+  const float a = (q & 1) ? cr : sr;        // sin: q = 0 sr, 1 cr, 2 -sr, 3 -cr
+  const float b = (q & 1) ? sr : cr;        // cos: q = 0 cr, 1 -sr, 2 -cr, 3 sr
+  *s = (q & 2) ? -a : a;
+  *c = ((q + 1) & 2) ? -b : b;
+}
+
+// exp(x) = 2^(x log2 e) on the hardware base-2 exponential (ex2.approx,
+// relative error ~2^-22 on its argument's exact value); the product
+// x log2 e adds |x| ulp of relative error, 6e-6 at |x| = 100
+__device__ __forceinline__ float fn_exp(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x * 1.44269504088896340736f));
+  return y;
+}
+
+// 1/x on the hardware reciprocal (rcp.approx, relative error ~2^-23)
+__device__ __forceinline__ float fn_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// ---------------------------------------------------------------------------
 // Eq. (torque) at one sample of the cubic.
 //   forward (links 1..7):
 //     w_j   = R^T w_{j-1} + qd_j z
@@ -239,10 +289,11 @@ __device__ __forceinline__ void torque_at(const ArmK& A, const Coef& c, float u,
     float q, v, acc;
     cubic_eval(c, j, u, q, v, acc);
     qd[j] = v;
-    // armature and friction (logistic with an IEEE division)
-    const float e = expf(-A.f2[j] * (v + A.f3[j]));
-    ex[j] = fmaf(A.arma[j], acc, fs * (A.f1[j] / (1.0f + e) - A.foff[j]));
-    sincosf(q + A.th0[j], &st[j], &ct[j]);
+    // armature and friction (logistic; ex2 / rcp: relative errors ~1e-6 on a
+    // term of at most psi1 N m, far inside the torque tolerance)
+    const float e = fn_exp(-A.f2[j] * (v + A.f3[j]));
+    ex[j] = fmaf(A.arma[j], acc, fs * fmaf(A.f1[j], fn_rcp(1.0f + e), -A.foff[j]));
+    fn_sincos(q + A.th0[j], &st[j], &ct[j]);
     const float ca = A.ca[j], sa = A.sa[j];
     const float c_ = ct[j], s_ = st[j];
     // u = dw_prev x p + w_prev x (w_prev x p) + dv_prev   (frame j-1)

@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(32 * CHECK_WARPS, 3)
       continue;
     }
     float rt = NAN, rp = NAN;
-    edge_scan(A, es, cb, wr, nullptr, 0, S, true, T, true, rt, rp, nsamp);
+    edge_scan(A, es, cb, wr, nullptr, nullptr, 0, S, true, T, true, rt, rp, nsamp);
     const float rv = warp_rho_v(A, es, T);
     float cl = INFINITY;
     if (P.n_obs > 0) {

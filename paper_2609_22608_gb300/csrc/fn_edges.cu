@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(32 * EDGE_WARPS, MINB)
   __shared__ float sEdge[EDGE_WARPS][32];
   __shared__ float sCoef[EDGE_WARPS][FN_CUBIC_WORDS * 32];
   __shared__ float sWr[EDGE_WARPS][FN_WRENCH_WORDS * 32];
+  __shared__ __align__(16) float sSplit[EDGE_WARPS][FN_SPLIT_WORDS];
   if (mode == FN_MODE_FULL)
     for (int i = threadIdx.x; i < K; i += blockDim.x) sT[i] = G.T[i];
   __syncthreads();
@@ -47,7 +48,8 @@ __global__ void __launch_bounds__(32 * EDGE_WARPS, MINB)
     const bool finite = stage_rows(s0 + 16 * e, s1 + 16 * e, es);
     const bool fixed = mode == FN_MODE_FIXED;
     const float Tp = Tparam ? __ldg(Tparam + e) : INFINITY;
-    const EdgeResult r = time_edge(A, es, cb, wr, finite, fixed, Tp, sT, K, S, true, nsamp);
+    const EdgeResult r =
+        time_edge(A, es, cb, wr, sSplit[w], finite, fixed, Tp, sT, K, S, true, nsamp);
     if (lane == 0) {
       k_star[e] = r.k;
       T_star[e] = r.T;

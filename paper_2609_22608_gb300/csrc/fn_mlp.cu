@@ -633,6 +633,7 @@ __global__ void __launch_bounds__(128, 3) k_time_window(ArmK A, GridW G, int K, 
   __shared__ float sEdge[4][32];
   __shared__ float sCoef[4][FN_CUBIC_WORDS * 32];
   __shared__ float sWr[4][FN_WRENCH_WORDS * 32];
+  __shared__ __align__(16) float sSplit[4][FN_SPLIT_WORDS];
   for (int i = threadIdx.x; i < K; i += blockDim.x) sT[i] = G.T[i];
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -659,7 +660,7 @@ __global__ void __launch_bounds__(128, 3) k_time_window(ArmK A, GridW G, int K, 
       float rt_alt = NAN, rp_alt = NAN;
       while (step != DONE) {
         float t1 = NAN, t2 = NAN;
-        const int k = (b1 > b0) ? edge_scan(A, es, cb, wr, sT, b1, S, false, 0.f, false, t1, t2,
+        const int k = (b1 > b0) ? edge_scan(A, es, cb, wr, sSplit[w], sT, b1, S, false, 0.f, false, t1, t2,
                                             nsamp, b0)
                                 : -1;
         if (step == WIN) {

@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(32 * NARY_WARPS, MINB)
   __shared__ float sEdge[NARY_WARPS][32];
   __shared__ float sCoef[NARY_WARPS][FN_CUBIC_WORDS * 32];
   __shared__ float sWr[NARY_WARPS][FN_WRENCH_WORDS * 32];
+  __shared__ __align__(16) float sSplit[NARY_WARPS][FN_SPLIT_WORDS];
   for (int i = threadIdx.x; i < K; i += blockDim.x) sT[i] = G.T[i];
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -66,7 +67,7 @@ __global__ void __launch_bounds__(32 * NARY_WARPS, MINB)
         float t_rt = NAN, t_rp = NAN;
         int w_out = -1;
         const bool grid = dur == sT;
-        const int idx = edge_scan(A, es, cb, wr, dur, n, S, false, 0.f, false, t_rt, t_rp, nsamp,
+        const int idx = edge_scan(A, es, cb, wr, sSplit[w], dur, n, S, false, 0.f, false, t_rt, t_rp, nsamp,
                                   0, grid ? 1 : 2, wit, &w_out);
         if (grid) {
           k = idx;

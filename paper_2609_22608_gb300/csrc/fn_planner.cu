@@ -780,7 +780,10 @@ __global__ void __launch_bounds__(32 * PL_KNN_WARPS) k_plan_knn(PlanDev D, int k
       for (int a = 0; a < PL_KNN_QW; ++a) {
         const int b = b0 + a;
         if (b >= B) continue;
+        // every lane's split-list stores are fenced, and the warp has passed
+        // its fences, before lane 0 counts the split as finished
         __threadfence();
+        __syncwarp();
         int last = 0;
         if (lane == 0) {
           int* cnt = D.knn_cnt + (long)p * D.BM + b;
@@ -1338,7 +1341,7 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_vseq(PlanDev 
   __shared__ float sEdge[32];
   __shared__ float sCoef[PL_EDGE_WARPS][FN_CUBIC_WORDS * 32];
   __shared__ float sWr[PL_EDGE_WARPS][FN_WRENCH_WORDS * 32];
-  __shared__ int s_item, s_k[PL_EDGE_WARPS], s_pass[PL_EDGE_WARPS];
+  __shared__ int s_item, s_k[PL_EDGE_WARPS], s_pass[PL_EDGE_WARPS], s_from, s_kres, s_done;
   for (int i = threadIdx.x; i < D.K; i += blockDim.x) sT[i] = Gr.T[i];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const CubicLane cb{&sCoef[w][lane]};
@@ -1356,21 +1359,24 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_vseq(PlanDev 
     const int e = pend[i];
     const int p = D.e_ci[e] / D.BM;
     if (w == 0) stage_rows(D.st + ((long)p * D.NC + D.e_par[e]) * 16, D.cand + (long)D.e_ci[e] * 16, sEdge);
-    int from = D.cur_k[e], kres = -1;
-    __syncthreads();
-    while (from >= 0 && kres < 0) {
-      // the group's survivors: warp r takes the r-th survivor at or after `from`
-      if (threadIdx.x == 0) {
-        int k = from;
-        for (int r = 0; r < PL_EDGE_WARPS; ++r) {
-          s_k[r] = k;
-          if (k >= 0) k = next_survivor(D, e, k + 1);
-        }
-        from = k;  // first survivor of the next group (or -1)
-        s_pass[0] = from;  // carried through shared memory below
+    // Groups of four survivors: warp r verifies the r-th survivor at or after
+    // s_from.  Thread 0 alone writes the group state (s_k, s_from, s_kres,
+    // s_done), and only between the barriers B1 and B2 of a group; every
+    // other thread reads it after B2 (or before the loop), so no write lands
+    // while another thread may still read the previous value, and the block
+    // leaves the loop together.
+    if (threadIdx.x == 0) {
+      int k = D.cur_k[e];
+      for (int r = 0; r < PL_EDGE_WARPS; ++r) {
+        s_k[r] = k;
+        if (k >= 0) k = next_survivor(D, e, k + 1);
       }
-      __syncthreads();
-      const int next_from = s_pass[0];
+      s_from = k;   // first survivor of the next group (or -1)
+      s_kres = -1;
+      s_done = 0;
+    }
+    __syncthreads();
+    for (;;) {
       const int k = s_k[w];
       bool pass = false;
       if (k >= 0) {
@@ -1390,13 +1396,26 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_vseq(PlanDev 
         }
         pass = !bad;
       }
-      __syncthreads();
       if (lane == 0) s_pass[w] = pass ? 1 : 0;
-      __syncthreads();
-      for (int r = 0; r < PL_EDGE_WARPS && kres < 0; ++r)
-        if (s_pass[r] && s_k[r] >= 0) kres = s_k[r];
-      from = next_from;
+      __syncthreads();                                      // B1
+      if (threadIdx.x == 0) {
+        for (int r = 0; r < PL_EDGE_WARPS && s_kres < 0; ++r)   // lowest passing survivor
+          if (s_pass[r] && s_k[r] >= 0) s_kres = s_k[r];
+        const int done = s_kres >= 0 || s_from < 0;
+        if (!done) {                                        // the next group
+          int kn = s_from;
+          for (int r = 0; r < PL_EDGE_WARPS; ++r) {
+            s_k[r] = kn;
+            if (kn >= 0) kn = next_survivor(D, e, kn + 1);
+          }
+          s_from = kn;
+        }
+        s_done = done;
+      }
+      __syncthreads();                                      // B2
+      if (s_done) break;
     }
+    const int kres = s_kres;
     if (w == 0 && kres >= 0) finish_edge(D, A, e, kres, sT[kres], sEdge);
     if (threadIdx.x == 0) {
       if (kres < 0) {
@@ -1480,6 +1499,7 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, 3)
   __shared__ float sSub[PL_EDGE_WARPS][32];
   __shared__ float sCoef[PL_EDGE_WARPS][FN_CUBIC_WORDS * 32];
   __shared__ float sWr[PL_EDGE_WARPS][FN_WRENCH_WORDS * 32];
+  __shared__ __align__(16) float sSplit[PL_EDGE_WARPS][FN_SPLIT_WORDS];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const CubicLane cb{&sCoef[w][lane]};
   const LaneWrench wr{&sWr[w][lane]};
@@ -1496,7 +1516,8 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, 3)
     stage_rows(D.st + ((long)p * D.NC + D.e_par[e]) * 16, D.cand + (long)ci * 16, sEs[w]);
     float a = k > 0 ? Gr.T[k - 1] : 0.f, b = Gr.T[k];
     float rt = NAN, rp = NAN;
-    nary_rounds(A, sEs[w], cb, wr, sSub[w], D.S, eps, max_rounds, a, b, -1, rt, rp, nsamp);
+    nary_rounds(A, sEs[w], cb, wr, sSplit[w], sSub[w], D.S, eps, max_rounds, a, b, -1, rt, rp,
+                nsamp);
     const float rv = warp_rho_v(A, sEs[w], b);
     bool ok = rv <= 1.f;
     const fn_problem_t& P = D.prob[p];
@@ -1772,8 +1793,10 @@ __global__ void __launch_bounds__(PL_ATTACH_THREADS) k_plan_prune(PlanDev D, Arm
   const long nb = (long)p * D.NC;
   const Incumbent in = D.inc[p];
   (void)A;
-  if (threadIdx.x == 0) {
-    for (int c = in.id; c > 0; c = D.par[nb + c]) D.alive[nb + c] = 1;
+  if (threadIdx.x == 0) {   // parent links point to lower ids: at most N steps
+    int steps = 0;
+    for (int c = in.id; c > 0 && c < N && steps < N; c = D.par[nb + c], ++steps)
+      D.alive[nb + c] = 1;
   }
   __syncthreads();
   // descendants of pruned nodes are removed: alive_i &= alive_{ancestors},
