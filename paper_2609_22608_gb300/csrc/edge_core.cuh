@@ -149,6 +149,24 @@ __device__ __forceinline__ bool end_probe_pass(const ArmK& A, const float* split
   return pass;
 }
 
+// position of the i-th lowest set bit of x (i = 0: the lowest); -1 if x has
+// at most i set bits
+__device__ __forceinline__ int nth_bit(unsigned x, int i) {
+  for (int t = 0; t < i && x; ++t) x &= x - 1u;
+  return __ffs(x) - 1;
+}
+
+// the lowest (up to) n set bits of x
+__device__ __forceinline__ unsigned lowest_bits(unsigned x, int n) {
+  unsigned r = 0u;
+  for (int t = 0; t < n && x; ++t) {
+    const unsigned bit = x & (0u - x);
+    r |= bit;
+    x ^= bit;
+  }
+  return r;
+}
+
 // Edge scan with a single torque-evaluation call site (the RNEA body is
 // ~1k instructions; inlining it at several call sites overflowed the
 // instruction cache) and a single coefficient-build site.  Passes:
@@ -159,12 +177,19 @@ __device__ __forceinline__ bool end_probe_pass(const ArmK& A, const float* split
 //              (alpha, beta: gravity, velocity and friction off)
 //   PROBE_END: lanes = grid durations base+lane, both end samples from the
 //              split (no torque evaluation)
+//   PROBE_MID: interior samples mid_probe_index(j), j < 4, of the lowest
+//              survivors not yet probed there: packed (wmode 0), the lowest
+//              eight survivors x four samples in one pass, lane = 4 i + j;
+//              otherwise lanes = durations, one sample per pass
 //   PROBE_W  : (wmode 2) one sample, the witness, at the remaining survivors
 //              (plain coefficients): after a failed verify, that duration's
 //              first violating sample; on the first chunk, the caller's w_in
-//   PROBE_MID: the lanes still passing, interior samples mid_probe_index(j)
-//   VERIFY   : lanes = samples (s0 + lane) of one duration, compensated
-//              coefficients, until a violating batch or all S samples pass
+//   VERIFY   : lanes = samples (s0 + lane) of the lowest survivor once it
+//              passed its interior probes, compensated coefficients, until
+//              a violating batch or all S samples pass
+// A survivor is verified only after its interior probes, and the lowest
+// survivor first, so the first duration that passes is k*: every lower
+// index was shown infeasible by a violating sample.
 // Grid mode (fixed = false): returns the first feasible index in
 // [k_begin, Kadm) (k_begin = 0 unless a caller scans a sub-range); `split`
 // is the warp's FN_SPLIT_WORDS slot (16-byte aligned), reused across calls
@@ -188,13 +213,16 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, float* es, CubicLane cb,
   enum { SPLIT = 0, PROBE_END = 1, PROBE_W = 2, PROBE_MID = 3, VERIFY = 4 };
   enum { COEF_NONE = 0, COEF_PLAIN = 1, COEF_EXACT = 2, COEF_SPLIT = 3 };
   const int lane = threadIdx.x & 31;
+  const bool packed = wmode == 0;       // interior probes of 8 survivors x 4 samples per pass
   int mode = PROBE_END, base = k_begin, kk = 0, s0 = 0, mj = 0, sw = 0, coef = COEF_NONE;
+  int cdur = -1;        // COEF_PLAIN: this lane's grid index (-1: none)
   int kill = -1;        // wmode > 0: sample that proved duration base + lane infeasible
-  unsigned cand = 0u;   // probes: durations still passing; VERIFY: durations left in the chunk
+  unsigned cand = 0u;   // durations (bits relative to base) still in the running
+  unsigned mpr = 0u;    // of those, the ones whose interior probes passed
+  unsigned sel = 0u;    // PROBE_MID: the durations being probed
   float mt = 0.f, mp = 0.f;
   bool bad = false;
   bool w_pending = wmode == 2 && w_in > 0 && w_in < S - 1;   // interior witness of the caller
-  bool mid_done = false;                // this chunk's survivors had their interior probes
   if (w_out) *w_out = -1;
   if (fixed) {
     mode = VERIFY;
@@ -227,14 +255,14 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, float* es, CubicLane cb,
           c.b3[j] = 0.f;
         }
       } else if (coef == COEF_PLAIN) {
-        if (base + lane < Kadm) cubic_coef_sh<false>(es, sT[base + lane], c);
+        if (cdur >= 0) cubic_coef_sh<false>(es, sT[cdur], c);
       } else {
         cubic_coef_sh<true>(es, fixed ? Tfix : sT[kk], c);
       }
       cb.store(c);
       coef = COEF_NONE;
     }
-    int next_dur = -1;  // duration to verify next, if any
+    bool decide = false;  // choose the next step from (cand, mpr)
     if (mode == PROBE_END) {
       const int k = base + lane;
       const bool active = k < Kadm;
@@ -242,33 +270,30 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, float* es, CubicLane cb,
       const bool pass = active && end_probe_pass(A, split, sT[active ? k : base], f0);
       if (wmode > 0 && active && !pass) kill = f0 ? 0 : S - 1;
       cand = __ballot_sync(0xffffffffu, pass);
-      if (cand) {
-        if (w_pending) {
-          w_pending = false;
-          mode = PROBE_W;
-          sw = w_in;
-          coef = COEF_PLAIN;
-          continue;
-        }
-        if (S > 2) {
-          mode = PROBE_MID;
-          mj = 0;
-          coef = COEF_PLAIN;
-          continue;
-        }
-        next_dur = base + __ffs(cand) - 1;
+      mpr = S > 2 ? 0u : 0xffffffffu;   // S <= 2: no interior samples
+      if (cand && w_pending) {
+        w_pending = false;
+        mode = PROBE_W;
+        sw = w_in;
+        cdur = ((cand >> lane) & 1u) ? base + lane : -1;
+        coef = COEF_PLAIN;
+        continue;
       }
+      decide = true;
     } else {
       bool active;
-      int si;               // sample index of this pass (probes)
+      int si;               // sample index of this pass
       if (mode == VERIFY) {
         active = s0 + lane < S;
         si = s0 + lane;
       } else if (mode == SPLIT) {
         active = lane < 6;
         si = 0;
-      } else {
-        active = (cand >> lane) & 1u;
+      } else if (mode == PROBE_MID && packed) {
+        active = cdur >= 0;
+        si = mid_probe_index(lane & 3, S);
+      } else {              // PROBE_W, or PROBE_MID one sample per pass
+        active = ((mode == PROBE_W ? cand : (sel & cand)) >> lane) & 1u;
         si = mode == PROBE_MID ? mid_probe_index(mj, S) : sw;
       }
       const float u = sample_u(si, S);
@@ -305,17 +330,25 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, float* es, CubicLane cb,
         mode = PROBE_END;
         continue;
       }
-      if (wmode > 0 && mode != VERIFY && active && !pass) kill = si;
-      if (mode == PROBE_W || mode == PROBE_MID) {
-        cand = ok;                     // durations whose probes so far pass
-        if (cand && mode == PROBE_W && S > 2 && !mid_done) {
-          mode = PROBE_MID;            // the chunk's interior probes, once
-          mj = 0;
-          continue;
-        }
-        if (mode == PROBE_MID) mid_done = true;
-        if (cand && mode == PROBE_MID && ++mj < FN_MID_PROBES) continue;
-        if (cand) next_dur = base + __ffs(cand) - 1;
+      if (mode == PROBE_W) {
+        if (wmode > 0 && active && !pass) kill = si;
+        cand &= ok;
+        decide = true;
+      } else if (mode == PROBE_MID && packed) {
+        // survivor i (the i-th set bit of sel) passes iff its 4 lanes pass
+        const int ns = __popc(sel);
+        unsigned failed = 0u;
+        for (int i = 0; i < ns; ++i)
+          if (((ok >> (4 * i)) & 0xFu) != 0xFu) failed |= 1u << nth_bit(sel, i);
+        cand &= ~failed;
+        mpr |= sel;
+        decide = true;
+      } else if (mode == PROBE_MID) {
+        if (wmode > 0 && active && !pass) kill = si;
+        cand &= ~(act & ~ok);
+        if (++mj < FN_MID_PROBES && (sel & cand)) continue;
+        mpr |= sel;
+        decide = true;
       } else {                         // VERIFY
         if (active) { mt = fmaxf(mt, a); mp = fmaxf(mp, b); }
         const bool viol = (act & ~ok) != 0u;
@@ -334,13 +367,14 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, float* es, CubicLane cb,
             sw = s0 + __ffs(act & ~ok) - 1;
             if (lane == kk - base) kill = sw;
           }
-          cand &= cand - 1;
+          cand &= ~(1u << (kk - base));
           if (cand && wmode == 2) {    // probe its witness sample at the rest
             mode = PROBE_W;
+            cdur = ((cand >> lane) & 1u) ? base + lane : -1;
             coef = COEF_PLAIN;
             continue;
           }
-          if (cand) next_dur = base + __ffs(cand) - 1;
+          decide = true;
         } else if (s0 + 32 < S) {
           s0 += 32;
           continue;
@@ -356,12 +390,28 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, float* es, CubicLane cb,
         }
       }
     }
-    if (next_dur >= 0) {               // (re)start VERIFY on the next survivor
-      kk = next_dur;
-      s0 = 0;
-      mt = mp = 0.f;
-      mode = VERIFY;
-      coef = COEF_EXACT;
+    if (decide && cand) {
+      const int low = __ffs(cand) - 1;
+      if ((mpr >> low) & 1u) {         // verify the lowest survivor
+        kk = base + low;
+        s0 = 0;
+        mt = mp = 0.f;
+        mode = VERIFY;
+        coef = COEF_EXACT;
+        continue;
+      }
+      // interior probes of the lowest survivors not yet probed
+      mode = PROBE_MID;
+      mj = 0;
+      if (packed) {
+        sel = lowest_bits(cand & ~mpr, 8);
+        const int i = lane >> 2;
+        cdur = i < __popc(sel) ? base + nth_bit(sel, i) : -1;
+      } else {
+        sel = cand & ~mpr;
+        cdur = ((sel >> lane) & 1u) ? base + lane : -1;
+      }
+      coef = COEF_PLAIN;
       continue;
     }
     // nothing left in this chunk of 32 durations: probe the next one
@@ -374,7 +424,6 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, float* es, CubicLane cb,
     if (base >= Kadm) return -1;
     kill = -1;
     mode = PROBE_END;
-    mid_done = false;
     cand = 0u;
   }
 }
