@@ -205,8 +205,8 @@ __device__ __forceinline__ unsigned lowest_bits(unsigned x, int n) {
 //            not in the result's chunk of 32);
 //   wmode 2: as 1, plus the witness probes (PROBE_W), starting with w_in
 //            (if it is an interior sample) after the first chunk's end probes.
-__device__ __forceinline__ int edge_scan(const ArmK& A, float* es, CubicLane cb, LaneWrench wr,
-                                         float* split, const float* sT, int Kadm, int S,
+__device__ __forceinline__ int edge_scan(const ArmK& A, LinkTab L, float* es, CubicLane cb,
+                                         LaneLink wr, float* split, const float* sT, int Kadm, int S,
                                          bool fixed, float Tfix, bool exact, float& rt, float& rp,
                                          unsigned& nsamp, int k_begin = 0, int wmode = 0,
                                          int w_in = -1, int* w_out = nullptr) {
@@ -304,11 +304,11 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, float* es, CubicLane cb,
       float a = 0.f, b = 0.f;
       if (active) {                    // the single torque-evaluation call site
         float r = 0.f, pw = 0.f;
-        torque_at(
-            A, cb, u,
-            [&](int j, float tau, float v) {
+        torque_at_rolled(
+            A, L, cb, u,
+            [&](int j, float tau, float v, float inv_tau) {
               if (sp) split[so + sj + j] = tau;
-              r = fmaxf(r, fabsf(tau) * A.inv_tau[j]);
+              r = fmaxf(r, fabsf(tau) * inv_tau);
               pw = fmaf(tau, v, pw);
             },
             wr, on, on);
@@ -444,8 +444,8 @@ __device__ __forceinline__ int grid_prefix(const float* sT, int K, float cap) {
 // (Tp = +inf for no cap).
 // exact = false lets a fixed-duration check stop at the first violating batch
 // (its ratios are then lower bounds; ok is exact either way).
-__device__ __forceinline__ EdgeResult time_edge(const ArmK& A, float* es, CubicLane cb,
-                                                LaneWrench wr, float* split, bool finite,
+__device__ __forceinline__ EdgeResult time_edge(const ArmK& A, LinkTab L, float* es, CubicLane cb,
+                                                LaneLink wr, float* split, bool finite,
                                                 bool fixed, float Tp, const float* sT, int K,
                                                 int S, bool exact, unsigned& nsamp) {
   EdgeResult r;
@@ -458,7 +458,7 @@ __device__ __forceinline__ EdgeResult time_edge(const ArmK& A, float* es, CubicL
       return r;
     }
     const bool pass =
-        edge_scan(A, es, cb, wr, split, sT, 0, S, true, Tp, exact, r.rt, r.rp, nsamp) == 0;
+        edge_scan(A, L, es, cb, wr, split, sT, 0, S, true, Tp, exact, r.rt, r.rp, nsamp) == 0;
     if (exact || pass) r.rv = warp_rho_v(A, es, Tp);
     r.k = pass ? 0 : -1;
     r.T = Tp;
@@ -471,7 +471,7 @@ __device__ __forceinline__ EdgeResult time_edge(const ArmK& A, float* es, CubicL
     return r;
   }
   const int Kadm = grid_prefix(sT, K, Tp);
-  r.k = edge_scan(A, es, cb, wr, split, sT, Kadm, S, false, 0.f, false, r.rt, r.rp, nsamp);
+  r.k = edge_scan(A, L, es, cb, wr, split, sT, Kadm, S, false, 0.f, false, r.rt, r.rp, nsamp);
   if (r.k >= 0) {
     r.T = sT[r.k];
     r.rv = warp_rho_v(A, es, r.T);

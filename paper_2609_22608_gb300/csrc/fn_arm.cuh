@@ -368,6 +368,129 @@ __device__ __forceinline__ void torque_at(const ArmK& A, const Coef& c, float u,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Eq. (torque) with the link loops rolled: the same recursion and the same
+// arithmetic per link as torque_at, one copy of the link body instead of
+// seven, for the warp-per-edge kernels whose state machine around the torque
+// evaluation does not fit the instruction cache next to seven unrolled
+// links.  The per-link constants come from a shared-memory table (LinkTab,
+// warp-uniform addresses: broadcast loads); the outward pass leaves, per
+// link, the wrench, cos / sin of the joint angle, the joint velocity and the
+// armature-plus-friction term in the lane's column of a LaneLink buffer for
+// the inward pass.  The base link is evaluated with the general formulas on
+// zero velocities (exactly the base case's values).
+// ---------------------------------------------------------------------------
+#define FN_LINK_F4 5   // float4 per link in the table
+struct LinkTab {
+  const float4* p;     // [7][FN_LINK_F4] in shared memory
+  // (ca, sa, px, py) (pz, th0, m, cx) (cy, cz, Ix, Iy) (Iz, arma, f1, f2) (f3, foff, inv_tau, 0)
+};
+
+// fill the table (thread 0 of the block; the caller synchronises)
+__device__ __forceinline__ void fill_links(const ArmK& A, float4* t) {
+  if (threadIdx.x != 0) return;
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    t[FN_LINK_F4 * j + 0] = make_float4(A.ca[j], A.sa[j], A.px[j], A.py[j]);
+    t[FN_LINK_F4 * j + 1] = make_float4(A.pz[j], A.th0[j], A.m[j], A.cx[j]);
+    t[FN_LINK_F4 * j + 2] = make_float4(A.cy[j], A.cz[j], A.Ix[j], A.Iy[j]);
+    t[FN_LINK_F4 * j + 3] = make_float4(A.Iz[j], A.arma[j], A.f1[j], A.f2[j]);
+    t[FN_LINK_F4 * j + 4] = make_float4(A.f3[j], A.foff[j], A.inv_tau[j], 0.f);
+  }
+}
+
+#define FN_LINK_WORDS 70   // 10 per link: F (3), N (3), cos, sin, qd, armature + friction
+struct LaneLink {
+  float* p;  // &buf[lane] of a [FN_LINK_WORDS][32] per-warp buffer
+  __device__ __forceinline__ void put(int j, int k, float v) const { p[32 * (10 * j + k)] = v; }
+  __device__ __forceinline__ float get(int j, int k) const { return p[32 * (10 * j + k)]; }
+};
+
+// sink(j, tau_j, qd_j, 1 / tau_max_j) in the inward order j = 6..0
+template <class Coef, class Sink>
+__device__ __forceinline__ void torque_at_rolled(const ArmK& A, LinkTab L, const Coef& c, float u,
+                                                 Sink&& sink, LaneLink W, float gs = 1.f,
+                                                 float fs = 1.f) {
+  float wx = 0.f, wy = 0.f, wz = 0.f;
+  float dwx = 0.f, dwy = 0.f, dwz = 0.f;
+  float ax = A.g0x * gs, ay = A.g0y * gs, az = A.g0z * gs;
+#pragma unroll 1
+  for (int j = 0; j < 7; ++j) {
+    const float4 l0 = L.p[FN_LINK_F4 * j + 0], l1 = L.p[FN_LINK_F4 * j + 1];
+    const float4 l2 = L.p[FN_LINK_F4 * j + 2], l3 = L.p[FN_LINK_F4 * j + 3];
+    const float4 l4 = L.p[FN_LINK_F4 * j + 4];
+    const float ca = l0.x, sa = l0.y, px = l0.z, py = l0.w, pz = l1.x;
+    float q, v, acc;
+    cubic_eval(c, j, u, q, v, acc);
+    const float e = fn_exp(-l3.w * (v + l4.x));
+    W.put(j, 9, fmaf(l3.y, acc, fs * fmaf(l3.z, fn_rcp(1.0f + e), -l4.y)));
+    W.put(j, 8, v);
+    float s_, c_;
+    fn_sincos(q + l1.y, &s_, &c_);
+    W.put(j, 6, c_);
+    W.put(j, 7, s_);
+    // u = dw_prev x p + w_prev x (w_prev x p) + dv_prev   (frame j-1)
+    const float tx = wy * pz - wz * py, ty = wz * px - wx * pz, tz = wx * py - wy * px;
+    const float ux = (dwy * pz - dwz * py) + (wy * tz - wz * ty) + ax;
+    const float uy = (dwz * px - dwx * pz) + (wz * tx - wx * tz) + ay;
+    const float uz = (dwx * py - dwy * px) + (wx * ty - wy * tx) + az;
+    // R^T v = Rz(-theta) Rx(-alpha) v
+    float r1 = fmaf(ca, uy, sa * uz);
+    float r2 = fmaf(-sa, uy, ca * uz);
+    ax = fmaf(c_, ux, s_ * r1);
+    ay = fmaf(-s_, ux, c_ * r1);
+    az = r2;
+    r1 = fmaf(ca, wy, sa * wz);
+    r2 = fmaf(-sa, wy, ca * wz);
+    const float Rwx = fmaf(c_, wx, s_ * r1), Rwy = fmaf(-s_, wx, c_ * r1), Rwz = r2;
+    r1 = fmaf(ca, dwy, sa * dwz);
+    r2 = fmaf(-sa, dwy, ca * dwz);
+    const float Rdx = fmaf(c_, dwx, s_ * r1), Rdy = fmaf(-s_, dwx, c_ * r1), Rdz = r2;
+    wx = Rwx; wy = Rwy; wz = Rwz + v;
+    dwx = fmaf(Rwy, v, Rdx);
+    dwy = fmaf(-Rwx, v, Rdy);
+    dwz = Rdz + acc;
+    // COM acceleration and link wrench
+    const float cx = l1.w, cy = l2.x, cz = l2.y;
+    const float wcx = wy * cz - wz * cy, wcy = wz * cx - wx * cz, wcz = wx * cy - wy * cx;
+    const float vcx = (dwy * cz - dwz * cy) + (wy * wcz - wz * wcy) + ax;
+    const float vcy = (dwz * cx - dwx * cz) + (wz * wcx - wx * wcz) + ay;
+    const float vcz = (dwx * cy - dwy * cx) + (wx * wcy - wy * wcx) + az;
+    const float m = l1.z, Ix = l2.z, Iy = l2.w, Iz = l3.x;
+    const float Iwx = Ix * wx, Iwy = Iy * wy, Iwz = Iz * wz;
+    W.put(j, 0, m * vcx);
+    W.put(j, 1, m * vcy);
+    W.put(j, 2, m * vcz);
+    W.put(j, 3, fmaf(Ix, dwx, wy * Iwz - wz * Iwy));
+    W.put(j, 4, fmaf(Iy, dwy, wz * Iwx - wx * Iwz));
+    W.put(j, 5, fmaf(Iz, dwz, wx * Iwy - wy * Iwx));
+  }
+  float fx = 0.f, fy = 0.f, fz = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
+#pragma unroll 1
+  for (int j = 6; j >= 0; --j) {
+    // R_{j+1} (f, n) and p_{j+1} x R_{j+1} f; zero for the last link (f = n = 0)
+    const int jc = j < 6 ? j + 1 : 6;
+    const float4 k0 = L.p[FN_LINK_F4 * jc + 0], k1 = L.p[FN_LINK_F4 * jc + 1];
+    const float ca = k0.x, sa = k0.y, c_ = W.get(jc, 6), s_ = W.get(jc, 7);
+    float u0 = fmaf(c_, fx, -s_ * fy), u1 = fmaf(s_, fx, c_ * fy), u2 = fz;
+    const float Rfx = u0, Rfy = fmaf(ca, u1, -sa * u2), Rfz = fmaf(sa, u1, ca * u2);
+    u0 = fmaf(c_, nx, -s_ * ny); u1 = fmaf(s_, nx, c_ * ny); u2 = nz;
+    const float Rnx = u0, Rny = fmaf(ca, u1, -sa * u2), Rnz = fmaf(sa, u1, ca * u2);
+    const float px = k0.z, py = k0.w, pz = k1.x;
+    const float pRx = py * Rfz - pz * Rfy, pRy = pz * Rfx - px * Rfz, pRz = px * Rfy - py * Rfx;
+    const float4 m1 = L.p[FN_LINK_F4 * j + 1], m2 = L.p[FN_LINK_F4 * j + 2];
+    const float cx = m1.w, cy = m2.x, cz = m2.y;
+    const float Fx = W.get(j, 0), Fy = W.get(j, 1), Fz = W.get(j, 2);
+    const float Nx = W.get(j, 3), Ny = W.get(j, 4), Nz = W.get(j, 5);
+    const float cFx = cy * Fz - cz * Fy, cFy = cz * Fx - cx * Fz, cFz = cx * Fy - cy * Fx;
+    fx = Fx + Rfx; fy = Fy + Rfy; fz = Fz + Rfz;
+    nx = Nx + Rnx + cFx + pRx;
+    ny = Ny + Rny + cFy + pRy;
+    nz = Nz + Rnz + cFz + pRz;
+    sink(j, nz + W.get(j, 9), W.get(j, 8), L.p[FN_LINK_F4 * j + 4].z);
+  }
+}
+
 // one configuration (q, qd, qdd) handed to torque_at as its "sample"
 struct PointCoef {
   float q[7], qd[7], qdd[7];

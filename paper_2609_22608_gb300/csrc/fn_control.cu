@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(128) k_controller(ArmK A, CtrlK L, int B,
   }
 }
 
-#define CHECK_WARPS 4
+#define CHECK_WARPS 3  // as the grid scan: static shared memory within 48 KB
 
 // one warp per edge: the exact fixed-duration check (all S samples), rho_v,
 // then the clearance (lane = point)
@@ -127,12 +127,16 @@ __global__ void __launch_bounds__(32 * CHECK_WARPS, 3)
                   uint8_t* __restrict__ ok) {
   __shared__ float sEdge[CHECK_WARPS][32];
   __shared__ float sCoef[CHECK_WARPS][FN_CUBIC_WORDS * 32];
-  __shared__ float sWr[CHECK_WARPS][FN_WRENCH_WORDS * 32];
+  __shared__ float sWr[CHECK_WARPS][FN_LINK_WORDS * 32];
+  __shared__ float4 sLink[7 * FN_LINK_F4];
+  fill_links(A, sLink);
+  __syncthreads();
   if (E_dev) E = min(E, max(*E_dev, 0));
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   float* es = sEdge[w];
   const CubicLane cb{&sCoef[w][lane]};
-  const LaneWrench wr{&sWr[w][lane]};
+  const LaneLink wr{&sWr[w][lane]};
+  const LinkTab L{sLink};
   unsigned nsamp = 0;
   for (long e = (long)blockIdx.x * CHECK_WARPS + w; e < E; e += (long)gridDim.x * CHECK_WARPS) {
     const bool finite = stage_rows(s0 + 16 * e, s1 + 16 * e, es);
@@ -146,7 +150,7 @@ __global__ void __launch_bounds__(32 * CHECK_WARPS, 3)
       continue;
     }
     float rt = NAN, rp = NAN;
-    edge_scan(A, es, cb, wr, nullptr, nullptr, 0, S, true, T, true, rt, rp, nsamp);
+    edge_scan(A, L, es, cb, wr, nullptr, nullptr, 0, S, true, T, true, rt, rp, nsamp);
     const float rv = warp_rho_v(A, es, T);
     float cl = INFINITY;
     if (P.n_obs > 0) {

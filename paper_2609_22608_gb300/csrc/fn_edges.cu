@@ -18,7 +18,9 @@ struct GridK {
   float T[FN_MAX_GRID];
 };
 
-#define EDGE_WARPS 4
+// three warps per block keep the per-warp coefficient and link buffers
+// (~12.6 KB) within a block's 48 KB of static shared memory
+#define EDGE_WARPS 3
 
 // Persistent: the grid is sized to the resident capacity and warp w takes
 // edges w, w + W, w + 2W, ...  MINB sets the register budget (and so the
@@ -33,15 +35,18 @@ __global__ void __launch_bounds__(32 * EDGE_WARPS, MINB)
   __shared__ float sT[FN_MAX_GRID];
   __shared__ float sEdge[EDGE_WARPS][32];
   __shared__ float sCoef[EDGE_WARPS][FN_CUBIC_WORDS * 32];
-  __shared__ float sWr[EDGE_WARPS][FN_WRENCH_WORDS * 32];
+  __shared__ float sWr[EDGE_WARPS][FN_LINK_WORDS * 32];
   __shared__ __align__(16) float sSplit[EDGE_WARPS][FN_SPLIT_WORDS];
+  __shared__ float4 sLink[7 * FN_LINK_F4];
+  fill_links(A, sLink);
   if (mode == FN_MODE_FULL)
     for (int i = threadIdx.x; i < K; i += blockDim.x) sT[i] = G.T[i];
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   float* es = sEdge[w];
   const CubicLane cb{&sCoef[w][lane]};
-  const LaneWrench wr{&sWr[w][lane]};
+  const LaneLink wr{&sWr[w][lane]};
+  const LinkTab L{sLink};
   const long W = (long)gridDim.x * EDGE_WARPS;
   unsigned nsamp = 0;
   for (long e = (long)blockIdx.x * EDGE_WARPS + w; e < E; e += W) {
@@ -49,7 +54,7 @@ __global__ void __launch_bounds__(32 * EDGE_WARPS, MINB)
     const bool fixed = mode == FN_MODE_FIXED;
     const float Tp = Tparam ? __ldg(Tparam + e) : INFINITY;
     const EdgeResult r =
-        time_edge(A, es, cb, wr, sSplit[w], finite, fixed, Tp, sT, K, S, true, nsamp);
+        time_edge(A, L, es, cb, wr, sSplit[w], finite, fixed, Tp, sT, K, S, true, nsamp);
     if (lane == 0) {
       k_star[e] = r.k;
       T_star[e] = r.T;

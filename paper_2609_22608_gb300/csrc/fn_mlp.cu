@@ -618,7 +618,8 @@ __device__ __forceinline__ int window_lo(float y0, float y1, float logT0, float 
 // under monotone rho_tau, rho_P); accept "none" if the window and T_{K-1}
 // are infeasible.  Otherwise fall back to the exact scan of the indices not
 // yet examined ([0, lo-1) then [lo+W, K)).
-__global__ void __launch_bounds__(128, 3) k_time_window(ArmK A, GridW G, int K, int S,
+#define WIN_WARPS 3   // as the grid scan: static shared memory within 48 KB
+__global__ void __launch_bounds__(32 * WIN_WARPS, 4) k_time_window(ArmK A, GridW G, int K, int S,
                                                      const float* __restrict__ s0,
                                                      const float* __restrict__ s1, int E,
                                                      const float* __restrict__ Y, int Wn,
@@ -630,19 +631,22 @@ __global__ void __launch_bounds__(128, 3) k_time_window(ArmK A, GridW G, int K, 
                                                      uint8_t* __restrict__ path,
                                                      unsigned long long* __restrict__ counter) {
   __shared__ float sT[FN_MAX_GRID];
-  __shared__ float sEdge[4][32];
-  __shared__ float sCoef[4][FN_CUBIC_WORDS * 32];
-  __shared__ float sWr[4][FN_WRENCH_WORDS * 32];
-  __shared__ __align__(16) float sSplit[4][FN_SPLIT_WORDS];
+  __shared__ float sEdge[WIN_WARPS][32];
+  __shared__ float sCoef[WIN_WARPS][FN_CUBIC_WORDS * 32];
+  __shared__ float sWr[WIN_WARPS][FN_LINK_WORDS * 32];
+  __shared__ __align__(16) float sSplit[WIN_WARPS][FN_SPLIT_WORDS];
+  __shared__ float4 sLink[7 * FN_LINK_F4];
+  fill_links(A, sLink);
   for (int i = threadIdx.x; i < K; i += blockDim.x) sT[i] = G.T[i];
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   float* es = sEdge[w];
   const CubicLane cb{&sCoef[w][lane]};
-  const LaneWrench wr{&sWr[w][lane]};
+  const LaneLink wr{&sWr[w][lane]};
+  const LinkTab L{sLink};
   unsigned nsamp = 0;
-  const long NW = (long)gridDim.x * 4;
-  for (long e = (long)blockIdx.x * 4 + w; e < E; e += NW) {
+  const long NW = (long)gridDim.x * WIN_WARPS;
+  for (long e = (long)blockIdx.x * WIN_WARPS + w; e < E; e += NW) {
     const bool finite = stage_rows(s0 + 16 * e, s1 + 16 * e, es);
     int kres = -2, route = 1;
     float rt = NAN, rp = NAN;
@@ -660,7 +664,7 @@ __global__ void __launch_bounds__(128, 3) k_time_window(ArmK A, GridW G, int K, 
       float rt_alt = NAN, rp_alt = NAN;
       while (step != DONE) {
         float t1 = NAN, t2 = NAN;
-        const int k = (b1 > b0) ? edge_scan(A, es, cb, wr, sSplit[w], sT, b1, S, false, 0.f, false, t1, t2,
+        const int k = (b1 > b0) ? edge_scan(A, L, es, cb, wr, sSplit[w], sT, b1, S, false, 0.f, false, t1, t2,
                                             nsamp, b0)
                                 : -1;
         if (step == WIN) {
@@ -739,8 +743,8 @@ extern "C" fn_status fn_time_edges_window(const fn_arm_t* arm, const float* s0, 
   // one edge per warp and no grid stride: the block scheduler hands out
   // blocks as others finish, which balances the few edges that fall back to
   // the full scan
-  const long blocks = std::min<long>(((long)E + 3) / 4, 0x7fffffffL);
-  k_time_window<<<(unsigned)blocks, 128, 0, (cudaStream_t)stream>>>(
+  const long blocks = std::min<long>(((long)E + WIN_WARPS - 1) / WIN_WARPS, 0x7fffffffL);
+  k_time_window<<<(unsigned)blocks, 32 * WIN_WARPS, 0, (cudaStream_t)stream>>>(
       A, G, K, S, s0, s1, E, Y, std::min(W, K), logT0, dlog, k_star, T_star, rho3, ok, path,
       sample_count);
   return launch_status();

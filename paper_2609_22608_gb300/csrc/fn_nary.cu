@@ -26,7 +26,7 @@ struct NaryGrid {
   float T[FN_MAX_GRID];
 };
 
-#define NARY_WARPS 4
+#define NARY_WARPS 3   // as the grid scan: static shared memory within 48 KB
 #define NARY_MAX_ROUNDS 16
 
 // Persistent: warp w takes edges w, w + W, ...  MINB sets the register
@@ -43,15 +43,18 @@ __global__ void __launch_bounds__(32 * NARY_WARPS, MINB)
   __shared__ float sSub[NARY_WARPS][32];
   __shared__ float sEdge[NARY_WARPS][32];
   __shared__ float sCoef[NARY_WARPS][FN_CUBIC_WORDS * 32];
-  __shared__ float sWr[NARY_WARPS][FN_WRENCH_WORDS * 32];
+  __shared__ float sWr[NARY_WARPS][FN_LINK_WORDS * 32];
   __shared__ __align__(16) float sSplit[NARY_WARPS][FN_SPLIT_WORDS];
+  __shared__ float4 sLink[7 * FN_LINK_F4];
+  fill_links(A, sLink);
   for (int i = threadIdx.x; i < K; i += blockDim.x) sT[i] = G.T[i];
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   float* es = sEdge[w];
   float* sub = sSub[w];
   const CubicLane cb{&sCoef[w][lane]};
-  const LaneWrench wr{&sWr[w][lane]};
+  const LaneLink wr{&sWr[w][lane]};
+  const LinkTab L{sLink};
   const long W = (long)gridDim.x * NARY_WARPS;
   unsigned nsamp = 0;
   for (long e = (long)blockIdx.x * NARY_WARPS + w; e < E; e += W) {
@@ -67,7 +70,7 @@ __global__ void __launch_bounds__(32 * NARY_WARPS, MINB)
         float t_rt = NAN, t_rp = NAN;
         int w_out = -1;
         const bool grid = dur == sT;
-        const int idx = edge_scan(A, es, cb, wr, sSplit[w], dur, n, S, false, 0.f, false, t_rt, t_rp, nsamp,
+        const int idx = edge_scan(A, L, es, cb, wr, sSplit[w], dur, n, S, false, 0.f, false, t_rt, t_rp, nsamp,
                                   0, grid ? 1 : 2, wit, &w_out);
         if (grid) {
           k = idx;

@@ -1492,20 +1492,25 @@ __global__ void __launch_bounds__(PL_CHORD_THREADS) k_plan_chord(PlanDev D, ArmK
 // which replaces the grid value (Algorithm 1: T_p = min{T <= t_best :
 // rho(T) <= 1}, then Clear at T_p).  Persistent warps stride over the free
 // edges.
-__global__ void __launch_bounds__(32 * PL_EDGE_WARPS, 3)
+#define PL_REFINE_WARPS 3   // static shared memory of the rolled scan within 48 KB
+__global__ void __launch_bounds__(32 * PL_REFINE_WARPS, 4)
     k_plan_refine(PlanDev D, ArmK A, GridKP Gr, float eps, int max_rounds) {
   pdl_begin();
-  __shared__ float sEs[PL_EDGE_WARPS][32];
-  __shared__ float sSub[PL_EDGE_WARPS][32];
-  __shared__ float sCoef[PL_EDGE_WARPS][FN_CUBIC_WORDS * 32];
-  __shared__ float sWr[PL_EDGE_WARPS][FN_WRENCH_WORDS * 32];
-  __shared__ __align__(16) float sSplit[PL_EDGE_WARPS][FN_SPLIT_WORDS];
+  __shared__ float sEs[PL_REFINE_WARPS][32];
+  __shared__ float sSub[PL_REFINE_WARPS][32];
+  __shared__ float sCoef[PL_REFINE_WARPS][FN_CUBIC_WORDS * 32];
+  __shared__ float sWr[PL_REFINE_WARPS][FN_LINK_WORDS * 32];
+  __shared__ __align__(16) float sSplit[PL_REFINE_WARPS][FN_SPLIT_WORDS];
+  __shared__ float4 sLink[7 * FN_LINK_F4];
+  fill_links(A, sLink);
+  __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const CubicLane cb{&sCoef[w][lane]};
-  const LaneWrench wr{&sWr[w][lane]};
+  const LaneLink wr{&sWr[w][lane]};
+  const LinkTab L{sLink};
   const int nfree = D.sched->n_free_edges;
   unsigned nsamp = 0;
-  for (int e = blockIdx.x * PL_EDGE_WARPS + w; e < nfree; e += gridDim.x * PL_EDGE_WARPS) {
+  for (int e = blockIdx.x * PL_REFINE_WARPS + w; e < nfree; e += gridDim.x * PL_REFINE_WARPS) {
     long ei;
     bool goal;
     edge_slot(D, e, ei, goal);
@@ -1516,7 +1521,7 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, 3)
     stage_rows(D.st + ((long)p * D.NC + D.e_par[e]) * 16, D.cand + (long)ci * 16, sEs[w]);
     float a = k > 0 ? Gr.T[k - 1] : 0.f, b = Gr.T[k];
     float rt = NAN, rp = NAN;
-    nary_rounds(A, sEs[w], cb, wr, sSplit[w], sSub[w], D.S, eps, max_rounds, a, b, -1, rt, rp,
+    nary_rounds(A, L, sEs[w], cb, wr, sSplit[w], sSub[w], D.S, eps, max_rounds, a, b, -1, rt, rp,
                 nsamp);
     const float rv = warp_rho_v(A, sEs[w], b);
     bool ok = rv <= 1.f;
@@ -2451,7 +2456,7 @@ static fn_status enqueue_iteration(fn_planner* pl, unsigned flags, cudaStream_t 
   enqueue_edges(pl, pl->edge_variant, pl->edge_blocks, st, mark);
   if (pl->sur_mlp) enqueue_surrogate(pl, st);
   if (flags & FN_PLAN_NARY) {
-    pl_launch(k_plan_refine, 3 * num_sms(), 32 * PL_EDGE_WARPS, 0, st, D, pl->arm, pl->grid,
+    pl_launch(k_plan_refine, 4 * num_sms(), 32 * PL_REFINE_WARPS, 0, st, D, pl->arm, pl->grid,
               pl->nary_eps, pl->nary_rounds);
     trace(pl, st, "k_plan_refine");
   }
