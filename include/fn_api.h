@@ -310,7 +310,13 @@ fn_status fn_knn_tree(const float* tree, int N, int first, const float* queries,
  *    Within the limit the number of node splits is reduced to what fits.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress, once per device, with that device current).
- *    Make that first call before any stream capture.
+ *    Make that first call before any stream capture.  The address is kept
+ *    for the life of the process: after cudaDeviceReset (or any teardown of
+ *    the device's primary context) the library must be unloaded and loaded
+ *    again before this entry point is called on that device.
+ *  - The split pass uses at most nsplit * B * (8 or 16) * 8 bytes of the
+ *    array (about 5 MiB for any B: the split count falls as B grows); the
+ *    array is sized for two splits of the largest B.
  *  - All calls share the one array.  Calls that overlap on the GPU (other
  *    streams, other host threads) race on it and must be serialised by the
  *    caller.  The array keeps the last call's contents; nothing in it needs
@@ -390,6 +396,13 @@ typedef struct {
 } fn_problem_t;
 
 /* Output of one iteration per problem (Algorithm 1's return value, D9). */
+/* fn_rendezvous_t.status bits: candidates dropped because the tree reached
+ * n_cap; a duration search hit its pass bound (an internal error, never
+ * expected: the search state machine progresses every pass, and the bound
+ * stops a scan that would not, leaving that edge's grid result in place) */
+#define FN_PLAN_TREE_FULL 1
+#define FN_PLAN_ERR_SCAN 2
+
 typedef struct {
   float q_g[7], qd_g[7];  /* end state of the incumbent plan's first edge  */
   float T;                /* that edge's duration from the root            */
@@ -398,7 +411,7 @@ typedef struct {
   int incumbent;          /* incumbent node id (-1 if none)                */
   int n_nodes;            /* tree size after the iteration                 */
   int n_added;            /* nodes attached in this iteration              */
-  int status;             /* 0, or bit 1: tree full (candidates dropped)   */
+  int status;             /* 0, or FN_PLAN_TREE_FULL | FN_PLAN_ERR_SCAN     */
 } fn_rendezvous_t;
 
 typedef struct fn_planner fn_planner_t;

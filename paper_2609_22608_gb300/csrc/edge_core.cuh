@@ -156,6 +156,17 @@ __device__ __forceinline__ int nth_bit(unsigned x, int i) {
   return __ffs(x) - 1;
 }
 
+// Upper bound on the passes of one edge_scan call over n admissible
+// durations: per chunk of 32, one end probe plus, for each of its 32
+// durations at most, one witness pass, four interior-probe passes and
+// ceil(S/32) verification passes; plus the split and the final chunk step.
+// Reaching it means the state machine failed to progress: the scan returns
+// FN_SCAN_ABORT instead of looping on.
+#define FN_SCAN_ABORT (-3)
+__host__ __device__ __forceinline__ int scan_pass_cap(int n, int S) {
+  return ((n + 31) / 32 + 1) * (2 + 32 * (5 + (S + 31) / 32)) + 2;
+}
+
 // the lowest (up to) n set bits of x
 __device__ __forceinline__ unsigned lowest_bits(unsigned x, int n) {
   unsigned r = 0u;
@@ -223,6 +234,8 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, LinkTab L, float* es, Cu
   float mt = 0.f, mp = 0.f;
   bool bad = false;
   bool w_pending = wmode == 2 && w_in > 0 && w_in < S - 1;   // interior witness of the caller
+  const int cap = scan_pass_cap(fixed ? 1 : max(Kadm - k_begin, 1), S);
+  int passes = 0;
   if (w_out) *w_out = -1;
   if (fixed) {
     mode = VERIFY;
@@ -235,6 +248,7 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, LinkTab L, float* es, Cu
     }
   }
   for (;;) {
+    if (++passes > cap) return FN_SCAN_ABORT;   // warp-uniform
     if (coef != COEF_NONE) {           // the single coefficient-build site
       Cubic c;
       if (coef == COEF_SPLIT) {
@@ -457,8 +471,13 @@ __device__ __forceinline__ EdgeResult time_edge(const ArmK& A, LinkTab L, float*
       r.T = NAN;
       return r;
     }
-    const bool pass =
-        edge_scan(A, L, es, cb, wr, split, sT, 0, S, true, Tp, exact, r.rt, r.rp, nsamp) == 0;
+    const int res = edge_scan(A, L, es, cb, wr, split, sT, 0, S, true, Tp, exact, r.rt, r.rp, nsamp);
+    if (res == FN_SCAN_ABORT) {
+      r.k = FN_SCAN_ABORT;
+      r.T = NAN;
+      return r;
+    }
+    const bool pass = res == 0;
     if (exact || pass) r.rv = warp_rho_v(A, es, Tp);
     r.k = pass ? 0 : -1;
     r.T = Tp;
@@ -472,7 +491,10 @@ __device__ __forceinline__ EdgeResult time_edge(const ArmK& A, LinkTab L, float*
   }
   const int Kadm = grid_prefix(sT, K, Tp);
   r.k = edge_scan(A, L, es, cb, wr, split, sT, Kadm, S, false, 0.f, false, r.rt, r.rp, nsamp);
-  if (r.k >= 0) {
+  if (r.k == FN_SCAN_ABORT) {
+    r.T = NAN;
+    r.rt = r.rp = NAN;
+  } else if (r.k >= 0) {
     r.T = sT[r.k];
     r.rv = warp_rho_v(A, es, r.T);
     r.ok = r.rv <= 1.f;

@@ -667,7 +667,9 @@ __global__ void __launch_bounds__(32 * WIN_WARPS, 4) k_time_window(ArmK A, GridW
         const int k = (b1 > b0) ? edge_scan(A, L, es, cb, wr, sSplit[w], sT, b1, S, false, 0.f, false, t1, t2,
                                             nsamp, b0)
                                 : -1;
-        if (step == WIN) {
+        if (k == FN_SCAN_ABORT) {          // the scan's pass bound (never expected)
+          kres = FN_SCAN_ABORT; step = DONE;
+        } else if (step == WIN) {
           if (k >= 0 && (k >= lo || lo == 0)) {
             kres = k; rt = t1; rp = t2; route = 0; step = DONE;
           } else if (k >= 0) {             // T_{lo-1} feasible: look below it
@@ -699,7 +701,7 @@ __global__ void __launch_bounds__(32 * WIN_WARPS, 4) k_time_window(ArmK A, GridW
         }
       }
     }
-    float rv = NAN, Ts = kres == -2 ? NAN : INFINITY;
+    float rv = NAN, Ts = kres <= -2 ? NAN : INFINITY;
     if (kres >= 0) {
       Ts = sT[kres];
       rv = warp_rho_v(A, es, Ts);

@@ -72,6 +72,10 @@ __global__ void __launch_bounds__(32 * NARY_WARPS, MINB)
         const bool grid = dur == sT;
         const int idx = edge_scan(A, L, es, cb, wr, sSplit[w], dur, n, S, false, 0.f, false, t_rt, t_rp, nsamp,
                                   0, grid ? 1 : 2, wit, &w_out);
+        if (idx == FN_SCAN_ABORT) {          // the scan's pass bound (never expected)
+          k = FN_SCAN_ABORT;
+          break;
+        }
         if (grid) {
           k = idx;
           if (idx < 0) break;
@@ -93,7 +97,7 @@ __global__ void __launch_bounds__(32 * NARY_WARPS, MINB)
     }
     if (lane == 0) {
       k_star[e] = k;
-      T_star[e] = k >= 0 ? b : (k == -1 ? INFINITY : NAN);
+      T_star[e] = k >= 0 ? b : (k == -1 ? INFINITY : NAN);   // -2 invalid, -3 aborted
       if (T_lo) T_lo[e] = k >= 0 ? a : NAN;
       rho3[3 * e + 0] = k >= 0 ? rt : NAN;
       rho3[3 * e + 1] = k >= 0 ? rp : NAN;

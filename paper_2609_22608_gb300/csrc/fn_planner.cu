@@ -1341,7 +1341,8 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_vseq(PlanDev 
   __shared__ float sEdge[32];
   __shared__ float sCoef[PL_EDGE_WARPS][FN_CUBIC_WORDS * 32];
   __shared__ float sWr[PL_EDGE_WARPS][FN_WRENCH_WORDS * 32];
-  __shared__ int s_item, s_k[PL_EDGE_WARPS], s_pass[PL_EDGE_WARPS], s_from, s_kres, s_done;
+  __shared__ int s_item, s_k[PL_EDGE_WARPS], s_pass[PL_EDGE_WARPS], s_from, s_kres, s_done,
+      s_groups;
   for (int i = threadIdx.x; i < D.K; i += blockDim.x) sT[i] = Gr.T[i];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const CubicLane cb{&sCoef[w][lane]};
@@ -1374,6 +1375,7 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_vseq(PlanDev 
       s_from = k;   // first survivor of the next group (or -1)
       s_kres = -1;
       s_done = 0;
+      s_groups = 1;
     }
     __syncthreads();
     for (;;) {
@@ -1401,7 +1403,11 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_vseq(PlanDev 
       if (threadIdx.x == 0) {
         for (int r = 0; r < PL_EDGE_WARPS && s_kres < 0; ++r)   // lowest passing survivor
           if (s_pass[r] && s_k[r] >= 0) s_kres = s_k[r];
-        const int done = s_kres >= 0 || s_from < 0;
+        // next_survivor strictly increases, so an edge has at most
+        // ceil(K / 4) groups; the bound stops a loop that would not progress
+        const bool stuck = ++s_groups > (D.K + PL_EDGE_WARPS - 1) / PL_EDGE_WARPS + 1;
+        if (stuck) atomicOr(D.status + D.e_ci[e] / D.BM, FN_PLAN_ERR_SCAN);
+        const int done = s_kres >= 0 || s_from < 0 || stuck;
         if (!done) {                                        // the next group
           int kn = s_from;
           for (int r = 0; r < PL_EDGE_WARPS; ++r) {
@@ -1521,8 +1527,13 @@ __global__ void __launch_bounds__(32 * PL_REFINE_WARPS, 4)
     stage_rows(D.st + ((long)p * D.NC + D.e_par[e]) * 16, D.cand + (long)ci * 16, sEs[w]);
     float a = k > 0 ? Gr.T[k - 1] : 0.f, b = Gr.T[k];
     float rt = NAN, rp = NAN;
-    nary_rounds(A, L, sEs[w], cb, wr, sSplit[w], sSub[w], D.S, eps, max_rounds, a, b, -1, rt, rp,
-                nsamp);
+    const int rounds = nary_rounds(A, L, sEs[w], cb, wr, sSplit[w], sSub[w], D.S, eps, max_rounds,
+                                   a, b, -1, rt, rp, nsamp);
+    if (rounds == FN_SCAN_ABORT) {                      // keep the grid duration; flag it
+      a = k > 0 ? Gr.T[k - 1] : 0.f;
+      b = Gr.T[k];
+      if (lane == 0) atomicOr(D.status + p, FN_PLAN_ERR_SCAN);
+    }
     const float rv = warp_rho_v(A, sEs[w], b);
     bool ok = rv <= 1.f;
     const fn_problem_t& P = D.prob[p];
@@ -1583,7 +1594,7 @@ __global__ void __launch_bounds__(PL_ATTACH_THREADS) k_plan_attach(PlanDev D) {
     const int node = N0 + r;
     ++r;
     if (node >= D.NC) {
-      atomicOr(&D.status[p], 1);
+      atomicOr(&D.status[p], FN_PLAN_TREE_FULL);
       continue;
     }
     const long nd = nb + node;

@@ -46,7 +46,8 @@ __device__ __forceinline__ void nary_bracket(const float* sub, int idx, int w_ou
 
 // Rounds on the staged edge es while b - a > eps, at most max_rounds (wit:
 // the sample that proved a infeasible, -1 if unknown).  Returns the rounds
-// run.  One edge_scan call site.
+// run, or FN_SCAN_ABORT if a round's scan hit its pass bound.  One edge_scan
+// call site.
 __device__ __forceinline__ int nary_rounds(const ArmK& A, LinkTab L, float* es, CubicLane cb,
                                            LaneLink wr, float* split, float* sub, int S, float eps,
                                            int max_rounds, float& a, float& b, int wit, float& rt,
@@ -58,6 +59,7 @@ __device__ __forceinline__ int nary_rounds(const ArmK& A, LinkTab L, float* es, 
     int w_out = -1;
     const int idx = edge_scan(A, L, es, cb, wr, split, sub, NARY_N - 1, S, false, 0.f, false, t_rt, t_rp,
                               nsamp, 0, 2, wit, &w_out);
+    if (idx == FN_SCAN_ABORT) return FN_SCAN_ABORT;   // the scan's pass bound
     nary_bracket(sub, idx, w_out, t_rt, t_rp, a, b, wit, rt, rp);
     ++r;
   }
