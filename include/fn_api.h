@@ -450,6 +450,8 @@ fn_status fn_planner_set_candidates(fn_planner_t* pl, int p, const float* states
                                round (the last round of an anytime iteration)       */
 #define FN_PLAN_NARY 32u    /* refine the free edges' durations by the N-ary search
                                (fn_planner_set_refine)                              */
+#define FN_PLAN_GREFINE 64u /* gradient refinement of the incumbent rendezvous
+                               (fn_planner_set_grefine)                             */
 
 /*
  * fn_plan_iteration -- one round of Algorithm 1 for all P problems:
@@ -552,6 +554,29 @@ fn_status fn_planner_get_tree(fn_planner_t* pl, int p, float* states, float* t,
  * Errors: FN_EINVAL unless eps > 0 finite and 0 <= max_rounds <= 16.
  */
 fn_status fn_planner_set_refine(fn_planner_t* pl, float eps, int max_rounds);
+
+/*
+ * fn_planner_set_grefine -- parameters of the rounds run with
+ * FN_PLAN_GREFINE: after attach, the incumbent rendezvous node of each
+ * problem is refined by gradient ascent on its chart parameters z (the
+ * paper's conclusion: the checks and the chart decoder are smooth in the
+ * trajectory parameters, and gradient-based refinement of tree nodes is the
+ * next step; it fixes no objective, variables or step rule).  Reading:
+ * F(z) = J of Eq. (objective) for phi(z) attached to the node's parent
+ * (T_p = T_req(z) - t(p), nu = max(nu(parent), rho_v at T_p)) where phi(z)
+ * is defined, T_p > 0 and the edge passes Def. "Feasibility Check" at T_p
+ * and the clearance, -inf elsewhere; the gradient is the central difference
+ * of the same J without the check, step h per coordinate (z2..z4 wrap, the
+ * others are clamped); iteration t moves z by eta0 2^-t along the normalised
+ * gradient (folded into the cube) and keeps the move when F improves; a zero
+ * gradient stops.  A node that improved is appended with the original's
+ * parent (the original stays: it may have children) and becomes the
+ * incumbent, which the rendezvous then reports.  Nothing happens without an
+ * incumbent whose chart parameters are known, or with a full tree.
+ * Defaults: iters 8, eta0 0.05, h 1e-3.  Set before fn_planner_capture.
+ * Errors: FN_EINVAL unless 0 <= iters <= 64, 0 < eta0 <= 1, 0 < h <= 0.1.
+ */
+fn_status fn_planner_set_grefine(fn_planner_t* pl, int iters, float eta0, float h);
 
 /*
  * fn_planner_set_grid -- replace the planner's duration grid (Def. "Minimum
@@ -694,6 +719,11 @@ fn_status fn_planner_get_parents(fn_planner_t* pl, int p, int32_t* nn, int cap);
  * Errors: FN_EINVAL for a bad argument, FN_ECUDA for a failed copy. */
 fn_status fn_planner_get_edges(fn_planner_t* pl, int p, int32_t* k_star, float* T, float* rho_v,
                                uint8_t* ok, int cap);
+/* Copy problem p's per-node chart parameters to host: z [cap][9] f32, row n
+ * the z of rendezvous node n (Def. "Goal chart"), NaN for free nodes and
+ * for goal nodes whose z is unknown (candidates given without parameters).
+ * Synchronous.  Errors: FN_EINVAL for a bad argument, FN_ECUDA. */
+fn_status fn_planner_get_node_params(fn_planner_t* pl, int p, float* z, int cap);
 
 /* Routes the free edges of the following iterations (those with an
  * admissible duration) through the duration surrogate: the model predicts a

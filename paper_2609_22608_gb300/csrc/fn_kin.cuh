@@ -487,6 +487,28 @@ __device__ __forceinline__ int chart_velocity(const ArmK& A, const ChartPose& o,
   return CHART_OK;
 }
 
+// phi(z) on a whole warp (all 32 lanes call it): the chart pose on every
+// lane, the FN_IK_STARTS starts on 8-lane groups (the lowest start that
+// converges wins, the same result as trying them in order), then the
+// velocity part on every lane.  Returns CHART_OK or the condition that left
+// phi undefined (warp-uniform); q and qd hold the goal state on every lane
+// when CHART_OK; o holds T, |v_rel| and the pose.
+__device__ __forceinline__ int warp_decode_goal(const ArmK& A, const fn_problem_t& P,
+                                                const float* z, ChartPose& o, float* q,
+                                                float* qd) {
+  const int lane = threadIdx.x & 31, grp = lane >> 3;
+  if (!chart_pose(A, P, z, o)) return CHART_SPEED;   // warp-uniform
+  float qs;
+  static_assert(FN_IK_STARTS <= 4, "one 8-lane group per IK start");
+  const bool found = ik_solve_group(A, o.Rg, o.pg, o.q7, grp < FN_IK_STARTS ? grp : 0, qs);
+  const unsigned won = __ballot_sync(0xffffffffu, found && (lane & 7) == 0 && grp < FN_IK_STARTS);
+  if (!won) return CHART_IK;
+  const int winner = __ffs(won) - 1;                 // first lane of the winning group
+#pragma unroll
+  for (int j = 0; j < 7; ++j) q[j] = __shfl_sync(0xffffffffu, qs, winner + j);
+  return chart_velocity(A, o, q, qd);
+}
+
 // Eq. (objective) with Eq. (terms); flight quantities at T + t_offset,
 // probabilities clamped to >= 1e-30 before the log.
 __device__ __forceinline__ float objective(const fn_problem_t& P, float T, float vrel, float nu) {

@@ -456,7 +456,7 @@ __global__ void __launch_bounds__(128) k_plan_sample(PlanDev D, ArmK A, long nsl
 // counted in work counters 8..13.
 __device__ __forceinline__ void sample_goal(const PlanDev& D, const ArmK& A, int p, int b,
                                             int dens) {
-  const int lane = threadIdx.x & 31, grp = lane >> 3;
+  const int lane = threadIdx.x & 31;
   const fn_problem_t& P = D.prob[p];
   const long ci = (long)p * D.BM + b;
   const int it = *D.iter;
@@ -470,22 +470,14 @@ __device__ __forceinline__ void sample_goal(const PlanDev& D, const ArmK& A, int
   for (int i = 0; i < 9; ++i)
     if (lane == i) D.cz[ci * 9 + i] = z[i];
   ChartPose o;
-  const bool defined = chart_pose(A, P, z, o);        // warp-uniform
-  int winner = -1;
-  float q[7];
-  if (defined) {
-    if (D.samples && lane == 0) atomicAdd(D.samples + 4, (unsigned long long)FN_IK_STARTS);
-    float qs;
-    static_assert(FN_IK_STARTS <= 4, "one 8-lane group per IK start");
-    const bool found = ik_solve_group(A, o.Rg, o.pg, o.q7, grp < FN_IK_STARTS ? grp : 0, qs);
-    const unsigned won = __ballot_sync(0xffffffffu, found && (lane & 7) == 0 && grp < FN_IK_STARTS);
-    winner = won ? (__ffs(won) - 1) : -1;             // first lane of the winning group
-#pragma unroll
-    for (int j = 0; j < 7; ++j) q[j] = __shfl_sync(0xffffffffu, qs, winner < 0 ? j : winner + j);
-  }
+  float q[7], qd[7];
+  const int why = warp_decode_goal(A, P, z, o, q, qd);
   if (lane != 0) return;
-  if (winner < 0) {   // undefined: |v_rel| too small or no IK start converged
-    if (D.samples) atomicAdd(D.samples + 8 + (defined ? CHART_IK : CHART_SPEED), 1ull);
+  if (D.samples) {
+    if (why != CHART_SPEED) atomicAdd(D.samples + 4, (unsigned long long)FN_IK_STARTS);
+    atomicAdd(D.samples + 8 + why, 1ull);
+  }
+  if (why == CHART_SPEED || why == CHART_IK) {   // undefined before the velocity part
     D.treq[ci] = o.T;
     D.vrel[ci] = o.vrel;
     D.valid[ci] = 0;
@@ -494,9 +486,6 @@ __device__ __forceinline__ void sample_goal(const PlanDev& D, const ArmK& A, int
     goal_query(D, p, b, false);
     return;
   }
-  float qd[7];
-  const int why = chart_velocity(A, o, q, qd);
-  if (D.samples) atomicAdd(D.samples + 8 + why, 1ull);
   const bool ok = why == CHART_OK;
   if (!ok)
 #pragma unroll
@@ -1773,6 +1762,189 @@ __global__ void __launch_bounds__(PL_DENSITY_THREADS) k_plan_density(PlanDev D, 
 }
 
 // ---------------------------------------------------------------------------
+// Gradient refinement of the incumbent rendezvous (FN_PLAN_GREFINE; the next
+// step the paper's conclusion names: its checks and chart decoder are smooth
+// in the trajectory parameters).  Reading: the variables are the node's
+// chart parameters z; the objective F(z) is J of Eq. (objective) for phi(z)
+// attached to the node's parent (T_p = T_req - t(p) in FP32, nu = max(nu(p),
+// rho_v at T_p), J at t(p) + T_p) where phi is defined, T_p > 0 and the edge
+// passes Def. "Feasibility Check" and the clearance, -inf elsewhere; the
+// gradient is the central difference of the same J (without the check) with
+// step h (angle coordinates z2..z4 wrap, the others are clamped, the
+// difference divided by the clamped span, 0 where a side is undefined); the
+// step is z' = fold(z + eta0 2^-t g / |g|), accepted when F(z') > F(z); a
+// zero gradient ends the iterations.  One block per problem: warps 0..17
+// take the 18 difference points in parallel, thread 0 forms the step, warp 0
+// evaluates z' with the exact check.  An improved node is appended beside
+// the original (same parent; a node may already have children) and becomes
+// the incumbent.
+// ---------------------------------------------------------------------------
+#define PL_GR_WARPS 18   // one warp per central-difference point (9 coordinates x 2)
+
+__device__ __forceinline__ bool z_angle(int i) { return i == 2 || i == 3 || i == 4; }
+
+__device__ __forceinline__ float z_clamp_fold(int i, float v) {
+  return z_angle(i) ? v - floorf(v) : fminf(fmaxf(v, 0.f), 1.f);
+}
+
+// F (check = true) or J (check = false) of phi(z) with the parent state ps
+// (global [16]), time tp and nu nup; warp-wide.  es: the warp's staging slot.
+// On success with check, q, qd (lane-replicated), Tp and rv describe the node.
+__device__ __forceinline__ float warp_node_value(const PlanDev& D, const ArmK& A, LinkTab L,
+                                                 CubicLane cb, LaneLink wr,
+                                                 const fn_problem_t& P, const float* z,
+                                                 const float* ps, float tp, float nup, bool check,
+                                                 float* es, float* q, float* qd, float& Tp,
+                                                 float& rv) {
+  const int lane = threadIdx.x & 31;
+  ChartPose o;
+  if (warp_decode_goal(A, P, z, o, q, qd) != CHART_OK) return -INFINITY;   // warp-uniform
+  Tp = __fsub_rn(o.T, tp);
+  if (!(Tp > 0.f)) return -INFINITY;
+  // stage the edge (parent state, goal state) as the edge kernels do
+  float gv = 0.f;
+  const int j = (lane - 16) & 7;
+#pragma unroll
+  for (int m = 0; m < 7; ++m) {
+    if (j == m && lane >= 16 && lane < 24) gv = q[m];
+    if (j == m && lane >= 24) gv = qd[m];
+  }
+  const float v = lane < 16 ? ps[lane] : ((lane & 7) == 7 ? 0.f : gv);
+  __syncwarp();
+  es[lane] = lane == FN_SPLIT_MARK ? 0.f : v;
+  __syncwarp();
+  rv = warp_rho_v(A, es, Tp);
+  const float J = objective(P, __fadd_rn(tp, Tp), o.vrel, fmaxf(nup, rv));
+  if (check) {
+    float rt = NAN, rp = NAN;
+    unsigned ns = 0;
+    bool ok = edge_scan(A, L, es, cb, wr, nullptr, nullptr, 0, D.S, true, Tp, true, rt, rp, ns) == 0;
+    ok = ok && rv <= 1.f;
+    if (ok && P.n_obs > 0) ok = warp_clearance(D, A, P, es, Tp) >= D.margin;
+    if (!ok) return -INFINITY;
+  }
+  return J;
+}
+
+__global__ void __launch_bounds__(32 * PL_GR_WARPS) k_plan_grefine(PlanDev D, ArmK A, int iters,
+                                                                   float eta0, float h) {
+  pdl_begin();
+  __shared__ float sEs[PL_GR_WARPS][32];
+  __shared__ float sCoef[FN_CUBIC_WORDS * 32];     // warp 0's exact check
+  __shared__ float sLk[FN_LINK_WORDS * 32];
+  __shared__ float4 sLink[7 * FN_LINK_F4];
+  __shared__ float sz[9], szn[9], sJ[PL_GR_WARPS], sSpan[9], sF, sq[7], sqd[7], sTp, srv;
+  __shared__ int s_go, s_acc;
+  fill_links(A, sLink);
+  const int p = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const fn_problem_t& P = D.prob[p];
+  const long nb = (long)p * D.NC;
+  const int N = D.n_nodes[p];
+  const int node = D.inc[p].id;
+  // the incumbent: a rendezvous node with known chart parameters, and room
+  // for one more node
+  bool go = node > 0 && node < N && N < D.NC;
+  if (go)
+    for (int i = 0; i < 9; ++i) go = go && isfinite(D.zn[(nb + node) * 9 + i]);
+  if (!go) return;                                   // uniform over the block
+  const int par = D.par[nb + node];
+  const float tp = D.t[nb + par], nup = D.nu[nb + par];
+  const float* ps = D.st + (nb + par) * 16;
+  const LinkTab L{sLink};
+  const CubicLane cb{&sCoef[lane]};
+  const LaneLink wr{&sLk[lane]};
+  if (threadIdx.x < 9) sz[threadIdx.x] = D.zn[(nb + node) * 9 + threadIdx.x];
+  if (threadIdx.x == 0) s_acc = 0;
+  __syncthreads();
+  float q[7], qd[7], Tp = 0.f, rv = 0.f;
+  if (w == 0) {
+    float z[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) z[i] = sz[i];
+    const float F = warp_node_value(D, A, L, cb, wr, P, z, ps, tp, nup, true, sEs[0], q, qd, Tp, rv);
+    if (lane == 0) sF = F;
+  }
+  __syncthreads();
+  for (int t = 0; t < iters; ++t) {
+    {   // central differences: warp w takes coordinate w / 2, side + for even w
+      const int i = w >> 1;
+      float z[9];
+#pragma unroll
+      for (int m = 0; m < 9; ++m) z[m] = sz[m];
+      float span;
+      if (z_angle(i)) {
+        z[i] = z_clamp_fold(i, (w & 1) ? z[i] - h : z[i] + h);
+        span = 2.f * h;
+      } else {
+        const float zp = fminf(z[i] + h, 1.f), zm = fmaxf(z[i] - h, 0.f);
+        z[i] = (w & 1) ? zm : zp;
+        span = zp - zm;
+      }
+      float q2[7], qd2[7], Tp2, rv2;
+      const float J = warp_node_value(D, A, L, cb, wr, P, z, ps, tp, nup, false, sEs[w], q2, qd2,
+                                      Tp2, rv2);
+      if (lane == 0) {
+        sJ[w] = J;
+        if ((w & 1) == 0) sSpan[i] = span;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float g[9], n2 = 0.f;
+      for (int i = 0; i < 9; ++i) {
+        const float jp = sJ[2 * i], jm = sJ[2 * i + 1];
+        g[i] = (isfinite(jp) && isfinite(jm) && sSpan[i] > 0.f) ? (jp - jm) / sSpan[i] : 0.f;
+        n2 = fmaf(g[i], g[i], n2);
+      }
+      const float n = sqrtf(n2);
+      s_go = n > 0.f;
+      const float step = ldexpf(eta0, -t) / n;
+      for (int i = 0; i < 9; ++i) szn[i] = s_go ? z_clamp_fold(i, fmaf(step, g[i], sz[i])) : sz[i];
+    }
+    __syncthreads();
+    if (!s_go) break;                                // uniform: read after the barrier
+    if (w == 0) {
+      float z[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) z[i] = szn[i];
+      float Tn = 0.f, rvn = 0.f;
+      const float Fn = warp_node_value(D, A, L, cb, wr, P, z, ps, tp, nup, true, sEs[0], q, qd, Tn,
+                                       rvn);
+      if (lane == 0 && Fn > sF) {
+        sF = Fn;
+        for (int i = 0; i < 9; ++i) sz[i] = z[i];
+        for (int m = 0; m < 7; ++m) { sq[m] = q[m]; sqd[m] = qd[m]; }
+        sTp = Tn;
+        srv = rvn;
+        ++s_acc;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && s_acc > 0) {               // append the refined rendezvous
+    const long nd = nb + N;
+    float* s = D.st + nd * 16;
+    for (int m = 0; m < 7; ++m) { s[m] = sq[m]; s[8 + m] = sqd[m]; }
+    s[7] = 0.f;
+    s[15] = 0.f;
+    D.t[nd] = __fadd_rn(tp, sTp);
+    D.par[nd] = par;
+    D.J[nd] = sF;
+    D.nu[nd] = fmaxf(nup, srv);
+    D.eT[nd] = sTp;
+    for (int i = 0; i < 9; ++i) D.zn[nd * 9 + i] = sz[i];
+    D.n_nodes[p] = N + 1;
+    D.added[p] += 1;
+    Incumbent in = D.inc[p];
+    in.id = N;
+    in.J = sF;
+    in.t_best = D.t[nd];
+    D.inc[p] = in;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // prune (Eq. (reach)): one block per problem
 // ---------------------------------------------------------------------------
 // Eq. (reach) for every node of every problem (one thread per node): keep
@@ -1994,6 +2166,9 @@ struct fn_planner {
   // N-ary refinement of the free edges (fn_planner_set_refine)
   float nary_eps = 1e-4f;
   int nary_rounds = 8;
+  // gradient refinement of the incumbent (fn_planner_set_grefine)
+  int gr_iters = 8;
+  float gr_eta0 = 0.05f, gr_h = 1e-3f;
   // per-launch events of a timed iteration (kev[0] before the first launch)
   cudaEvent_t kev[PL_MAX_KEV + 1] = {};
   const char* kname[PL_MAX_KEV] = {};
@@ -2478,6 +2653,11 @@ static fn_status enqueue_iteration(fn_planner* pl, unsigned flags, cudaStream_t 
     pl_launch(k_plan_density, P, PL_DENSITY_THREADS, 0, st, D, (flags & FN_PLAN_REFIT) ? 1 : 0);
     trace(pl, st, "k_plan_density");
   }
+  if (flags & FN_PLAN_GREFINE) {
+    pl_launch(k_plan_grefine, P, 32 * PL_GR_WARPS, 0, st, D, pl->arm, pl->gr_iters, pl->gr_eta0,
+              pl->gr_h);
+    trace(pl, st, "k_plan_grefine");
+  }
   mark(7);
   if (flags & FN_PLAN_PRUNE) {
     const long nn = (long)P * D.NC;
@@ -2612,6 +2792,16 @@ extern "C" fn_status fn_planner_set_grid(fn_planner_t* pl, const float* T_grid, 
   return FN_OK;
 }
 
+extern "C" fn_status fn_planner_set_grefine(fn_planner_t* pl, int iters, float eta0, float h) {
+  if (!pl || iters < 0 || iters > 64 || !(eta0 > 0.f) || !(eta0 <= 1.f) || !(h > 0.f) ||
+      !(h <= 0.1f))
+    return FN_EINVAL;
+  pl->gr_iters = iters;
+  pl->gr_eta0 = eta0;
+  pl->gr_h = h;
+  return FN_OK;
+}
+
 extern "C" fn_status fn_planner_set_refine(fn_planner_t* pl, float eps, int max_rounds) {
   if (!pl || !(eps > 0.f) || !std::isfinite(eps) || max_rounds < 0 || max_rounds > 16)
     return FN_EINVAL;
@@ -2726,6 +2916,17 @@ extern "C" fn_status fn_planner_get_parents(fn_planner_t* pl, int p, int32_t* nn
   const long m = std::min(cap, pl->cfg.b_max);
   if (KN == 0 || m == 0) return FN_OK;
   return cudaMemcpy(nn, pl->D.nn + (long)p * pl->cfg.b_max * KN, sizeof(int32_t) * m * KN,
+                    cudaMemcpyDeviceToHost) == cudaSuccess
+             ? FN_OK
+             : FN_ECUDA;
+}
+
+extern "C" fn_status fn_planner_get_node_params(fn_planner_t* pl, int p, float* z, int cap) {
+  if (!pl || !z || p < 0 || p >= pl->cfg.P || cap < 0) return FN_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return FN_ECUDA;
+  const long m = std::min(cap, pl->cfg.n_cap);
+  if (m == 0) return FN_OK;
+  return cudaMemcpy(z, pl->D.zn + (long)p * pl->cfg.n_cap * 9, sizeof(float) * 9 * m,
                     cudaMemcpyDeviceToHost) == cudaSuccess
              ? FN_OK
              : FN_ECUDA;

@@ -19,6 +19,7 @@ FN_PLAN_DENSITY = 4
 FN_PLAN_CHORD = 8
 FN_PLAN_REFIT = 16
 FN_PLAN_NARY = 32
+FN_PLAN_GREFINE = 64
 FN_DENSITY_MAX_C = 4
 FN_ARCHIVE_MAX = 64
 FN_MAX_OBS = 8
@@ -99,6 +100,7 @@ def _bind():
     L.fn_planner_get_candidates.argtypes = [vp, i32, vp, vp, vp, vp, i32]
     L.fn_planner_get_parents.argtypes = [vp, i32, vp, i32]
     L.fn_planner_get_edges.argtypes = [vp, i32, vp, vp, vp, vp, i32]
+    L.fn_planner_get_node_params.argtypes = [vp, i32, vp, i32]
     L.fn_planner_sample_count.argtypes = [vp, vp, i32]
     L.fn_planner_phase_ms.argtypes = [vp, vp]
     L.fn_planner_kernel_ms.argtypes = [vp, vp, vp, i32, C.POINTER(C.c_int)]
@@ -113,16 +115,17 @@ def _bind():
     L.fn_planner_get_candidate_params.argtypes = [vp, i32, vp, i32]
     L.fn_planner_set_refine.argtypes = [vp, C.c_float, i32]
     L.fn_planner_set_grid.argtypes = [vp, vp, i32]
+    L.fn_planner_set_grefine.argtypes = [vp, i32, C.c_float, C.c_float]
     for n in ("fn_planner_create", "fn_planner_destroy", "fn_planner_reset", "fn_planner_load_tree",
               "fn_planner_set_candidates", "fn_plan_iteration", "fn_planner_capture",
               "fn_plan_replay", "fn_planner_get_tree", "fn_planner_get_candidates",
-              "fn_planner_get_parents", "fn_planner_get_edges",
+              "fn_planner_get_parents", "fn_planner_get_edges", "fn_planner_get_node_params",
               "fn_planner_sample_count", "fn_planner_phase_ms", "fn_planner_autotune",
               "fn_planner_kernel_ms", "fn_planner_work_counts", "fn_planner_set_surrogate",
               "fn_planner_incumbent_path", "fn_planner_set_sampler", "fn_planner_set_density",
               "fn_planner_get_density", "fn_planner_set_candidate_params",
               "fn_planner_get_candidate_params", "fn_planner_set_refine",
-              "fn_planner_set_grid"):
+              "fn_planner_set_grid", "fn_planner_set_grefine"):
         getattr(L, n).restype = i32
     L._planner_bound = True
     return L
@@ -291,6 +294,14 @@ class Planner:
               "fn_planner_get_edges")
         return dict(k_star=ks, T=T, rho_v=rv, ok=ok)
 
+    def get_node_params(self, p, n):
+        """fn_planner_get_node_params: chart parameters [n][9] of the first n
+        nodes (NaN where unknown)."""
+        z = np.zeros((n, 9), np.float32)
+        check(_bind().fn_planner_get_node_params(self.h, int(p), z.ctypes.data, int(n)),
+              "fn_planner_get_node_params")
+        return z
+
     def autotune(self, probs, it=0, flags=0, reps=3, stream=None):
         """fn_planner_autotune: returns (chosen variant, ms per variant)."""
         self._stage(probs)
@@ -313,6 +324,11 @@ class Planner:
         """fn_planner_set_refine (set before capture)."""
         check(lib().fn_planner_set_refine(self.h, float(eps), int(max_rounds)),
               "fn_planner_set_refine")
+
+    def set_grefine(self, iters=8, eta0=0.05, h=1e-3):
+        """fn_planner_set_grefine (set before capture)."""
+        check(lib().fn_planner_set_grefine(self.h, int(iters), float(eta0), float(h)),
+              "fn_planner_set_grefine")
 
     def set_sampler(self, w_u=0.25, C=4, n_fit=32, em_iters=8, sd_floor=0.02, sd_init=0.1,
                     w_chord=0.5, chord_sigma=0.1):
