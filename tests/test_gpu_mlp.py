@@ -37,6 +37,20 @@ def relerr(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30))
 
 
+def elementwise_ok(Y, ref):
+    """Per output element against the FP64 reference with the same bf16
+    rounding points.  The GPU accumulates in FP32 in another order, so a
+    hidden activation that sits at a bf16 rounding boundary can round to the
+    neighbouring value (one bf16 ulp, 2^-8 relative), which moves an output
+    by at most ~1e-2 of the output scale; every element must be within that,
+    and 99 % of them within 2e-3 of the scale (no such flip upstream)."""
+    Y = np.asarray(Y, np.float64)
+    scale = max(1.0, float(np.abs(ref).max()))
+    err = np.abs(Y - ref)
+    return bool(err.max() <= 1e-2 * scale and np.quantile(err, 0.99) <= 2e-3 * scale), \
+        float(err.max() / scale)
+
+
 def load(mlp, ps):
     for l, (W, b) in enumerate(ps):
         mlp.set_params(l, W, b)
@@ -51,6 +65,8 @@ def test_forward_parity(S, arm):
     ref, _ = M.forward([(W.astype(np.float64), b.astype(np.float64)) for W, b in ps],
                        M.features(arm, s0, s1))
     assert relerr(Y, ref) < 1e-3
+    ok, worst = elementwise_ok(Y, ref)
+    assert ok, worst
     mlp.close()
 
 
@@ -70,6 +86,8 @@ def test_tensor_core_forward(S, arm, E):
     ref, _ = M.forward([(W.astype(np.float64), b.astype(np.float64)) for W, b in ps],
                        M.features(arm, s0, s1))
     assert relerr(Y, ref) < 1e-3, relerr(Y, ref)
+    ok, worst = elementwise_ok(Y, ref)
+    assert ok, worst
     assert relerr(Y, Yr) < 1e-3, relerr(Y, Yr)
     # per edge: the two GPU paths differ only by FP32 summation order (and
     # the bf16 roundings that order can flip)

@@ -409,9 +409,9 @@ def test_plan_round_nary_refinement(P, orc, arm):
     search before the attach.  Every attached free node must carry a valid
     refined duration (its check passes in FP64 within the margin, eps below
     it fails within the margin, and it is not above the grid duration), and
-    the round must match the oracle's refined round on nearly every
-    candidate (refined decisions sit within the margin of the boundary, so
-    a few may legitimately differ)."""
+    the round must match the oracle's refined round candidate by candidate,
+    except where one of the candidate's edges has a refined decision within
+    the margin class (refined points sit within ~3e-5 T of the boundary)."""
     case = make_case(arm, orc, 3, N=400, n_goal_draw=256, n_free=192)
     # free candidates near the root, so that short free edges exist
     G = case["n_goal"]
@@ -455,10 +455,17 @@ def test_plan_round_nary_refinement(P, orc, arm):
         assert kg < len(grid) and T <= float(grid[kg]) + 1e-6
         if T - eps > 1e-3:
             assert max(r_lo[0], r_lo[1]) > 1 - 1e-4
-    # against the oracle's refined round: parent and time per candidate
+    # against the oracle's refined round, candidate by candidate: the same
+    # parent and a time within the refined bracket, or else one of the
+    # candidate's edges has its refined decision within the margin class:
+    # some duration the oracle's N-ary search checked has max(rho_tau,
+    # rho_P) within 1e-4 of 1 (its `margin` output), or rho_v at the refined
+    # duration lies in its joint-box band
+    from tests.parity import RHO_MARGIN, rho_v_ambiguous
     g_new = {gtree["states"][i].tobytes(): i for i in range(N, gtree["n"])}
     r_new = {rtree.states[i].tobytes(): i for i in range(N, rtree.n)}
-    same, total = 0, 0
+    par, tree_t = det["parents"], t
+    same, explained, total = 0, 0, 0
     for b in range(G, B):
         key = case["cand"][b].tobytes()
         gi, ri = g_new.get(key), r_new.get(key)
@@ -468,4 +475,20 @@ def test_plan_round_nary_refinement(P, orc, arm):
         if gi is not None and ri is not None and gtree["parent"][gi] == rtree.parent[ri] and \
                 abs(float(gtree["t"][gi]) - float(rtree.t[ri])) <= eps + 1e-4 * float(rtree.t[ri]):
             same += 1
-    assert total >= 10 and same >= 0.95 * total, (same, total)
+            continue
+        ok = False
+        for j in range(k):
+            pj = int(par[b, j])
+            if pj < 0:
+                continue
+            cap = np.array([np.float32(np.float32(inc["t_best"]) - np.float32(tree_t[pj]))])
+            s0, s1 = states[pj][None], case["cand"][b][None]
+            rn = orc.time_edges_nary(arm, s0, s1, grid, S_COLL, eps, 8, T_cap=cap)
+            if rn["margin"][0] <= RHO_MARGIN or (
+                    rn["k_star"][0] >= 0 and
+                    rho_v_ambiguous(orc, arm, s0[0], s1[0], float(rn["T_star"][0]), S_COLL)):
+                ok = True
+                break
+        explained += ok
+        assert ok, f"candidate {b} differs from the oracle's refined round outside the margin class"
+    assert total >= 10 and same + explained == total, (same, explained, total)
