@@ -732,11 +732,13 @@ def run_scan(args):
                    "l2": "flushed between timed calls"},
         "clocks": clk.summary(),
         "edges_with_feasible_duration": float((out["k_star"] >= 0).float().mean().item()),
-        "roofline": {"bound": "alu", "kernel": "k_time_edges", "achieved": ach, "peak": peak,
+        "roofline": {"bound": "alu", "kernel": "k_time_edges_tm", "achieved": ach, "peak": peak,
                      "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
                      "flop_per_unit": FLOP_PER_SAMPLE, "units_per_launch": evals,
                      "unit_of_work": "torque evaluations (the end-sample split's six per edge, "
-                                     "interior probes and verification samples)",
+                                     "interior probes and verification samples; the paired "
+                                     "scan evaluates two samples per lane, 64-sample "
+                                     "verification batches and eight probes per survivor)",
                      "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 FLOP x max SM "
                                   "clock (of derived)"},
     }

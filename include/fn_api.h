@@ -126,9 +126,15 @@ typedef struct {
  *   rho3       [E][3] f32 (rho_tau, rho_P, rho_v) at T_star; NaN when
  *              k_star is -1 in FULL mode or -2.
  *   ok         u8: 1 iff the edge is feasible at T_star including rho_v.
+ * Schedule: unless fn_autotune_time_edges chose otherwise for the shape, one
+ * warp per edge with two samples per lane (paired FP32 arithmetic) and the
+ * torque recursion's per-link records in tensor memory (one CTA of 12 warps
+ * per SM, which allocates all of the SM's 512 tensor-memory columns for the
+ * duration of the call; a kernel of another stream holding columns on the
+ * same SM delays it until they are released).
  * Errors: FN_EINVAL for dof != 7, E < 0, S out of range, K out of range or a
  * non-ascending / non-positive grid in FULL mode, a NULL required pointer,
- * unknown mode.
+ * unknown mode.  FN_ECUDA if the kernel's shared-memory size cannot be set.
  */
 fn_status fn_time_edges(const fn_arm_t* arm, const float* s0, const float* s1, int E,
                         const float* T_grid, int K, int S, int mode, const float* T_fixed,
@@ -242,12 +248,17 @@ fn_status fn_controller_torque(const fn_arm_t* arm, int B, const float* state, c
 /*
  * fn_autotune_time_edges -- the schedule autotuner for fn_time_edges: runs
  * the call (same arguments) with every compiled schedule variant of the edge
- * kernel (register budget / resident blocks per SM), `reps` timed runs each
- * after one warm-up, and records the fastest for this (mode, E bucket, K, S)
- * on the current device; later fn_time_edges calls of that shape use it.
- * The outputs are left as computed by the last variant (all variants compute
- * identical results).  chosen: host, the winning variant index (may be NULL);
- * variant_ms: host [3] mean ms per variant (may be NULL).  Synchronous.
+ * kernel, `reps` timed runs each after one warm-up, and records the fastest
+ * for this (mode, E bucket, K, S) on the current device; later fn_time_edges
+ * calls of that shape use it.  Variants 0-2: the scalar scan (one sample per
+ * lane) at three register budgets (resident blocks per SM), identical
+ * results; variant 3 (the default of untuned shapes): the paired scan (two
+ * samples per lane, paired FP32 arithmetic, the torque recursion's per-link
+ * records in tensor memory), whose torques round differently in the last
+ * bits, so k* can differ from the scalar scan's only where a limit ratio is
+ * within FP32 rounding of 1.  The outputs are left as computed by the last
+ * variant.  chosen: host, the winning variant index (may be NULL);
+ * variant_ms: host [4] mean ms per variant (may be NULL).  Synchronous.
  */
 fn_status fn_autotune_time_edges(const fn_arm_t* arm, const float* s0, const float* s1, int E,
                                  const float* T_grid, int K, int S, int mode,

@@ -51,6 +51,10 @@ __device__ __forceinline__ float sample_u(int s, int S) {
 __device__ __forceinline__ int mid_probe_index(int j, int S) {
   return (int)((2 * (j + 1) * (S - 1) + 5) / 10);  // round((j+1)(S-1)/5)
 }
+// the same spacing for n interior points: round((j+1)(S-1)/(n+1)), j < n
+__device__ __forceinline__ int mid_probe_index(int j, int S, int n) {
+  return (int)((2 * (j + 1) * (S - 1) + n + 1) / (2 * (n + 1)));
+}
 
 // The warp's end-sample split: per end (u = 0, u = 1) 28 floats, alpha[7],
 // beta[7], gamma[7] and the end velocity qd[7] (16-byte aligned slot).
@@ -178,9 +182,116 @@ __device__ __forceinline__ unsigned lowest_bits(unsigned x, int n) {
   return r;
 }
 
+// The torque evaluation of the scan ("core"): NS samples per lane per pass.
+//   ScalarCore: one sample (torque_at_rolled; records in a LaneLink column)
+//   PairCore  : two samples of the same cubic (torque_at_pair, paired FP32;
+//               records in the Stash: a LaneLink2 column or tensor memory)
+// eval() is called by every lane of the warp (tensor-memory records are
+// warp-collective); sink(j, tau, qd, 1 / tau_max_j) gets pairs, whose .y
+// half is meaningful only for NS = 2; gs, fs scale gravity and friction per
+// half.  store2 gives the halves different cubics (the scalar core keeps x).
+struct ScalarCore {
+  static constexpr int NS = 1;
+  LinkTab L;
+  CubicLane cb;
+  LaneLink wr;
+  __device__ __forceinline__ void store(const Cubic& c) const { cb.store(c); }
+  __device__ __forceinline__ void store2(const Cubic& cx, const Cubic&) const { cb.store(cx); }
+  template <class Sink>
+  __device__ __forceinline__ void eval(const ArmK& A, float2 u, float2 gs, float2 fs,
+                                       Sink&& sink) const {
+    torque_at_rolled(
+        A, L, cb, u.x,
+        [&](int j, float tau, float v, float inv_tau) {
+          sink(j, make_float2(tau, 0.f), make_float2(v, 0.f), inv_tau);
+        },
+        wr, gs.x, fs.x);
+  }
+};
+
+template <class Stash>
+struct PairCore {
+  static constexpr int NS = 2;
+  LinkTab2 L;
+  CubicLane2 cb;
+  Stash st;
+  __device__ __forceinline__ void store(const Cubic& c) const { cb.store(c); }
+  __device__ __forceinline__ void store2(const Cubic& cx, const Cubic& cy) const {
+    cb.store2(cx, cy);
+  }
+  template <class Sink>
+  __device__ __forceinline__ void eval(const ArmK& A, float2 u, float2 gs, float2 fs,
+                                       Sink&& sink) const {
+    torque_at_pair(A, L, cb, u, sink, st, gs, fs);
+  }
+};
+
+// The end-sample split cubic of item (end, part) of a staged edge: its
+// u = 0 sample is (q, qd, qdd) exactly (iT = iT2 = 1, b1 = qd, b2 = qdd / 2):
+// part 0 the end state with zero acceleration, parts 1 and 2 the two
+// acceleration vectors of end_torque_part at zero velocity.
+__device__ __forceinline__ void split_cubic(const float* es, int end, int part, Cubic& c) {
+  c.iT = 1.f;
+  c.iT2 = 1.f;
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    const float d = es[16 + j] - es[j];
+    const float qa = end ? -6.0f * d : 6.0f * d;
+    const float qb = end ? fmaf(4.0f, es[24 + j], 2.0f * es[8 + j])
+                         : -fmaf(4.0f, es[8 + j], 2.0f * es[24 + j]);
+    c.q0[j] = es[16 * end + j];
+    c.b1[j] = part == 0 ? es[16 * end + 8 + j] : 0.f;
+    c.b2[j] = 0.5f * (part == 0 ? 0.f : (part == 1 ? qa : qb));
+    c.b3[j] = 0.f;
+  }
+}
+
+// The splits of n <= 5 NS staged edges in one pass: item i = 6 e + 3 end +
+// part, items 0..29 on the x halves of lanes 0..29, items 30..59 on the y
+// halves (NS = 2).  Edge e's states are es_g[32 e ..] and its split goes to
+// split_g[FN_SPLIT_WORDS e ..]; each edge's split mark is set.  Edges whose
+// states are not finite get a meaningless split they never use.
+template <class Core>
+__device__ __forceinline__ void split_group(const ArmK& A, const Core& core, float* es_g,
+                                            float* split_g, int n, unsigned& nsamp) {
+  const int lane = threadIdx.x & 31;
+  const int ex = lane / 6, ey = 5 + lane / 6, ix = lane % 6;
+  const int end = ix >= 3 ? 1 : 0, part = ix - 3 * end;
+  const bool ax = lane < 30 && ex < n;
+  const bool ay = Core::NS == 2 && lane < 30 && ey < n;
+  Cubic cx, cy;
+  split_cubic(es_g + 32 * (ax ? ex : 0), end, part, cx);
+  split_cubic(es_g + 32 * (ay ? ey : 0), end, part, cy);
+  core.store2(cx, cy);
+  const float on = part == 0 ? 1.f : 0.f;   // parts 1, 2: M + I_m only
+  const int so = 28 * end + (part == 0 ? 14 : 7 * (part - 1));
+  float* sx = split_g + FN_SPLIT_WORDS * (ax ? ex : 0) + so;
+  float* sy = split_g + FN_SPLIT_WORDS * (ay ? ey : 0) + so;
+  core.eval(A, make_float2(0.f, 0.f), make_float2(on, on), make_float2(on, on),
+            [&](int j, float2 tau, float2, float) {
+              if (ax) sx[j] = tau.x;
+              if (ay) sy[j] = tau.y;
+            });
+  nsamp += __popc(__ballot_sync(0xffffffffu, ax)) + __popc(__ballot_sync(0xffffffffu, ay));
+  __syncwarp();
+  for (int e = 0; e < n; ++e) {   // end velocities; the split is ready
+    float* s = split_g + FN_SPLIT_WORDS * e;
+    const float* es = es_g + 32 * e;
+    if (lane < 7) {
+      s[21 + lane] = es[8 + lane];
+      s[49 + lane] = es[24 + lane];
+    }
+  }
+  __syncwarp();
+  if (lane < n) es_g[32 * lane + FN_SPLIT_MARK] = 1.f;
+  __syncwarp();
+}
+
 // Edge scan with a single torque-evaluation call site (the RNEA body is
 // ~1k instructions; inlining it at several call sites overflowed the
-// instruction cache) and a single coefficient-build site.  Passes:
+// instruction cache) and a single coefficient-build site.  Each pass
+// evaluates NS = Core::NS samples per lane (x, and y for the paired core).
+// Passes:
 //   SPLIT    : (once per staged edge) lanes 0..5 = (end, part) evaluate the
 //              end-sample split into `split`; part 0 is Eq. (torque) at the
 //              end state with zero acceleration (gamma), parts 1 and 2 the
@@ -188,16 +299,17 @@ __device__ __forceinline__ unsigned lowest_bits(unsigned x, int n) {
 //              (alpha, beta: gravity, velocity and friction off)
 //   PROBE_END: lanes = grid durations base+lane, both end samples from the
 //              split (no torque evaluation)
-//   PROBE_MID: interior samples mid_probe_index(j), j < 4, of the lowest
-//              survivors not yet probed there: packed (wmode 0), the lowest
-//              eight survivors x four samples in one pass, lane = 4 i + j;
-//              otherwise lanes = durations, one sample per pass
+//   PROBE_MID: interior samples mid_probe_index(j, S, 4 NS), j < 4 NS, of the
+//              lowest survivors not yet probed there: packed (wmode 0), the
+//              lowest eight survivors x 4 NS samples in one pass, lane = 4 i +
+//              j (x: sample j, y: sample j + 4); otherwise lanes = durations,
+//              NS samples per pass
 //   PROBE_W  : (wmode 2) one sample, the witness, at the remaining survivors
 //              (plain coefficients): after a failed verify, that duration's
 //              first violating sample; on the first chunk, the caller's w_in
-//   VERIFY   : lanes = samples (s0 + lane) of the lowest survivor once it
-//              passed its interior probes, compensated coefficients, until
-//              a violating batch or all S samples pass
+//   VERIFY   : lanes = samples of the lowest survivor once it passed its
+//              interior probes (x: s0 + lane, y: s0 + 32 + lane), compensated
+//              coefficients, until a violating batch or all S samples pass
 // A survivor is verified only after its interior probes, and the lowest
 // survivor first, so the first duration that passes is k*: every lower
 // index was shown infeasible by a violating sample.
@@ -216,15 +328,19 @@ __device__ __forceinline__ unsigned lowest_bits(unsigned x, int n) {
 //            not in the result's chunk of 32);
 //   wmode 2: as 1, plus the witness probes (PROBE_W), starting with w_in
 //            (if it is an interior sample) after the first chunk's end probes.
-__device__ __forceinline__ int edge_scan(const ArmK& A, LinkTab L, float* es, CubicLane cb,
-                                         LaneLink wr, float* split, const float* sT, int Kadm, int S,
-                                         bool fixed, float Tfix, bool exact, float& rt, float& rp,
-                                         unsigned& nsamp, int k_begin = 0, int wmode = 0,
-                                         int w_in = -1, int* w_out = nullptr) {
+template <class Core>
+__device__ __forceinline__ int edge_scan(const ArmK& A, const Core& core, float* es, float* split,
+                                         const float* sT, int Kadm, int S, bool fixed, float Tfix,
+                                         bool exact, float& rt, float& rp, unsigned& nsamp,
+                                         int k_begin = 0, int wmode = 0, int w_in = -1,
+                                         int* w_out = nullptr) {
   enum { SPLIT = 0, PROBE_END = 1, PROBE_W = 2, PROBE_MID = 3, VERIFY = 4 };
   enum { COEF_NONE = 0, COEF_PLAIN = 1, COEF_EXACT = 2, COEF_SPLIT = 3 };
+  constexpr int NS = Core::NS;
+  constexpr int NMID = FN_MID_PROBES * NS;   // interior probe samples per survivor
+  constexpr int BATCH = 32 * NS;             // verification samples per pass
   const int lane = threadIdx.x & 31;
-  const bool packed = wmode == 0;       // interior probes of 8 survivors x 4 samples per pass
+  const bool packed = wmode == 0;       // interior probes of 8 survivors x NMID samples per pass
   int mode = PROBE_END, base = k_begin, kk = 0, s0 = 0, mj = 0, sw = 0, coef = COEF_NONE;
   int cdur = -1;        // COEF_PLAIN: this lane's grid index (-1: none)
   int kill = -1;        // wmode > 0: sample that proved duration base + lane infeasible
@@ -252,28 +368,21 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, LinkTab L, float* es, Cu
     if (coef != COEF_NONE) {           // the single coefficient-build site
       Cubic c;
       if (coef == COEF_SPLIT) {
-        // lane l < 6: end l / 3, part l % 3, as a cubic whose u = 0 sample
-        // is (q, qd, qdd) exactly (iT = iT2 = 1, b1 = qd, b2 = qdd / 2)
-        const int end = lane >= 3 ? 1 : 0, part = lane - 3 * end;
-        c.iT = 1.f;
-        c.iT2 = 1.f;
-#pragma unroll
-        for (int j = 0; j < 7; ++j) {
-          const float d = es[16 + j] - es[j];
-          const float qa = end ? -6.0f * d : 6.0f * d;
-          const float qb = end ? fmaf(4.0f, es[24 + j], 2.0f * es[8 + j])
-                               : -fmaf(4.0f, es[8 + j], 2.0f * es[24 + j]);
-          c.q0[j] = es[16 * end + j];
-          c.b1[j] = part == 0 ? es[16 * end + 8 + j] : 0.f;
-          c.b2[j] = 0.5f * (part == 0 ? 0.f : (part == 1 ? qa : qb));
-          c.b3[j] = 0.f;
-        }
+        // lane l < 6: end l / 3, part l % 3
+        const int end = lane >= 3 ? 1 : 0;
+        split_cubic(es, end, lane - 3 * end, c);
       } else if (coef == COEF_PLAIN) {
-        if (cdur >= 0) cubic_coef_sh<false>(es, sT[cdur], c);
+        if (cdur >= 0) {
+          cubic_coef_sh<false>(es, sT[cdur], c);
+        } else {                       // an idle lane: any finite cubic
+          c.iT = c.iT2 = 1.f;
+#pragma unroll
+          for (int j = 0; j < 7; ++j) c.q0[j] = c.b1[j] = c.b2[j] = c.b3[j] = 0.f;
+        }
       } else {
         cubic_coef_sh<true>(es, fixed ? Tfix : sT[kk], c);
       }
-      cb.store(c);
+      core.store(c);
       coef = COEF_NONE;
     }
     bool decide = false;  // choose the next step from (cand, mpr)
@@ -295,44 +404,56 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, LinkTab L, float* es, Cu
       }
       decide = true;
     } else {
-      bool active;
-      int si;               // sample index of this pass
+      bool ax, ay = false;  // the pass's active samples on this lane
+      int sx, sy = 0;       // their sample indices
       if (mode == VERIFY) {
-        active = s0 + lane < S;
-        si = s0 + lane;
+        sx = s0 + lane;
+        sy = s0 + 32 + lane;
+        ax = sx < S;
+        ay = NS == 2 && sy < S;
       } else if (mode == SPLIT) {
-        active = lane < 6;
-        si = 0;
+        ax = lane < 6;
+        sx = 0;
       } else if (mode == PROBE_MID && packed) {
-        active = cdur >= 0;
-        si = mid_probe_index(lane & 3, S);
-      } else {              // PROBE_W, or PROBE_MID one sample per pass
-        active = ((mode == PROBE_W ? cand : (sel & cand)) >> lane) & 1u;
-        si = mode == PROBE_MID ? mid_probe_index(mj, S) : sw;
+        ax = cdur >= 0;
+        ay = NS == 2 && ax;
+        sx = mid_probe_index(lane & 3, S, NMID);
+        sy = mid_probe_index((lane & 3) + 4, S, NMID);
+      } else if (mode == PROBE_MID) {   // lanes = durations, NS samples per pass
+        ax = ((sel & cand) >> lane) & 1u;
+        ay = NS == 2 && ax;
+        sx = mid_probe_index(mj, S, NMID);
+        sy = mid_probe_index(mj + 1, S, NMID);
+      } else {              // PROBE_W
+        ax = (cand >> lane) & 1u;
+        sx = sw;
       }
-      const float u = sample_u(si, S);
+      const float2 u = make_float2(sample_u(sx, S), sample_u(ay ? sy : sx, S));
       const bool sp = mode == SPLIT;
       const float on = (sp && lane != 0 && lane != 3) ? 0.f : 1.f;   // parts 1, 2: M + I_m only
       const int so = lane >= 3 ? 28 : 0;
       const int sj = (lane == 0 || lane == 3) ? 14 : (lane == 1 || lane == 4 ? 0 : 7);
-      float a = 0.f, b = 0.f;
-      if (active) {                    // the single torque-evaluation call site
-        float r = 0.f, pw = 0.f;
-        torque_at_rolled(
-            A, L, cb, u,
-            [&](int j, float tau, float v, float inv_tau) {
-              if (sp) split[so + sj + j] = tau;
-              r = fmaxf(r, fabsf(tau) * inv_tau);
-              pw = fmaf(tau, v, pw);
-            },
-            wr, on, on);
-        a = r;
-        b = fabsf(pw) * A.inv_w;
-      }
-      const bool pass = active && a <= 1.f && b <= 1.f;
-      const unsigned act = __ballot_sync(0xffffffffu, active);
-      const unsigned ok = __ballot_sync(0xffffffffu, pass);
-      nsamp += __popc(act);
+      float rx = 0.f, px = 0.f, ry = 0.f, py = 0.f;
+      // the single torque-evaluation call site (every lane; idle halves are
+      // ignored below)
+      core.eval(A, u, dup2(on), dup2(on), [&](int j, float2 tau, float2 v, float inv_tau) {
+        if (sp && ax) split[so + sj + j] = tau.x;
+        rx = fmaxf(rx, fabsf(tau.x) * inv_tau);
+        px = fmaf(tau.x, v.x, px);
+        if (NS == 2) {
+          ry = fmaxf(ry, fabsf(tau.y) * inv_tau);
+          py = fmaf(tau.y, v.y, py);
+        }
+      });
+      const float bx = fabsf(px) * A.inv_w, by = fabsf(py) * A.inv_w;
+      const bool pass_x = ax && rx <= 1.f && bx <= 1.f;
+      const bool pass_y = ay && ry <= 1.f && by <= 1.f;
+      const unsigned act_x = __ballot_sync(0xffffffffu, ax);
+      const unsigned ok_x = __ballot_sync(0xffffffffu, pass_x);
+      const unsigned act_y = NS == 2 ? __ballot_sync(0xffffffffu, ay) : 0u;
+      const unsigned ok_y = NS == 2 ? __ballot_sync(0xffffffffu, pass_y) : 0u;
+      const unsigned fail_x = act_x & ~ok_x, fail_y = act_y & ~ok_y;
+      nsamp += __popc(act_x) + __popc(act_y);
       if (sp) {                        // end velocities; the split is ready
         if (lane < 7) {
           split[21 + lane] = es[8 + lane];
@@ -345,31 +466,35 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, LinkTab L, float* es, Cu
         continue;
       }
       if (mode == PROBE_W) {
-        if (wmode > 0 && active && !pass) kill = si;
-        cand &= ok;
+        if (wmode > 0 && ax && !pass_x) kill = sx;
+        cand &= ok_x;
         decide = true;
       } else if (mode == PROBE_MID && packed) {
         // survivor i (the i-th set bit of sel) passes iff its 4 lanes pass
+        const unsigned okb = NS == 2 ? (ok_x & ok_y) : ok_x;
         const int ns = __popc(sel);
         unsigned failed = 0u;
         for (int i = 0; i < ns; ++i)
-          if (((ok >> (4 * i)) & 0xFu) != 0xFu) failed |= 1u << nth_bit(sel, i);
+          if (((okb >> (4 * i)) & 0xFu) != 0xFu) failed |= 1u << nth_bit(sel, i);
         cand &= ~failed;
         mpr |= sel;
         decide = true;
       } else if (mode == PROBE_MID) {
-        if (wmode > 0 && active && !pass) kill = si;
-        cand &= ~(act & ~ok);
-        if (++mj < FN_MID_PROBES && (sel & cand)) continue;
+        if (wmode > 0 && ax && !pass_x) kill = sx;
+        else if (wmode > 0 && ay && !pass_y) kill = sy;
+        cand &= ~(fail_x | fail_y);
+        mj += NS;
+        if (mj < NMID && (sel & cand)) continue;
         mpr |= sel;
         decide = true;
       } else {                         // VERIFY
-        if (active) { mt = fmaxf(mt, a); mp = fmaxf(mp, b); }
-        const bool viol = (act & ~ok) != 0u;
+        if (ax) { mt = fmaxf(mt, rx); mp = fmaxf(mp, bx); }
+        if (ay) { mt = fmaxf(mt, ry); mp = fmaxf(mp, by); }
+        const bool viol = (fail_x | fail_y) != 0u;
         if (fixed) {
           bad = bad || viol;
-          if ((!viol || exact) && s0 + 32 < S) {
-            s0 += 32;
+          if ((!viol || exact) && s0 + BATCH < S) {
+            s0 += BATCH;
             continue;
           }
           rt = warp_max(mt);
@@ -378,7 +503,8 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, LinkTab L, float* es, Cu
         }
         if (viol) {                    // kk is infeasible
           if (wmode > 0) {
-            sw = s0 + __ffs(act & ~ok) - 1;
+            // the first violating sample: the x halves hold s0 .. s0 + 31
+            sw = fail_x ? s0 + __ffs(fail_x) - 1 : s0 + 32 + __ffs(fail_y) - 1;
             if (lane == kk - base) kill = sw;
           }
           cand &= ~(1u << (kk - base));
@@ -389,8 +515,8 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, LinkTab L, float* es, Cu
             continue;
           }
           decide = true;
-        } else if (s0 + 32 < S) {
-          s0 += 32;
+        } else if (s0 + BATCH < S) {
+          s0 += BATCH;
           continue;
         } else {
           rt = warp_max(mt);
@@ -458,10 +584,11 @@ __device__ __forceinline__ int grid_prefix(const float* sT, int K, float cap) {
 // (Tp = +inf for no cap).
 // exact = false lets a fixed-duration check stop at the first violating batch
 // (its ratios are then lower bounds; ok is exact either way).
-__device__ __forceinline__ EdgeResult time_edge(const ArmK& A, LinkTab L, float* es, CubicLane cb,
-                                                LaneLink wr, float* split, bool finite,
-                                                bool fixed, float Tp, const float* sT, int K,
-                                                int S, bool exact, unsigned& nsamp) {
+template <class Core>
+__device__ __forceinline__ EdgeResult time_edge(const ArmK& A, const Core& core, float* es,
+                                                float* split, bool finite, bool fixed, float Tp,
+                                                const float* sT, int K, int S, bool exact,
+                                                unsigned& nsamp) {
   EdgeResult r;
   r.rt = r.rp = r.rv = NAN;
   r.ok = false;
@@ -471,7 +598,7 @@ __device__ __forceinline__ EdgeResult time_edge(const ArmK& A, LinkTab L, float*
       r.T = NAN;
       return r;
     }
-    const int res = edge_scan(A, L, es, cb, wr, split, sT, 0, S, true, Tp, exact, r.rt, r.rp, nsamp);
+    const int res = edge_scan(A, core, es, split, sT, 0, S, true, Tp, exact, r.rt, r.rp, nsamp);
     if (res == FN_SCAN_ABORT) {
       r.k = FN_SCAN_ABORT;
       r.T = NAN;
@@ -490,7 +617,7 @@ __device__ __forceinline__ EdgeResult time_edge(const ArmK& A, LinkTab L, float*
     return r;
   }
   const int Kadm = grid_prefix(sT, K, Tp);
-  r.k = edge_scan(A, L, es, cb, wr, split, sT, Kadm, S, false, 0.f, false, r.rt, r.rp, nsamp);
+  r.k = edge_scan(A, core, es, split, sT, Kadm, S, false, 0.f, false, r.rt, r.rp, nsamp);
   if (r.k == FN_SCAN_ABORT) {
     r.T = NAN;
     r.rt = r.rp = NAN;

@@ -491,6 +491,239 @@ __device__ __forceinline__ void torque_at_rolled(const ArmK& A, LinkTab L, const
   }
 }
 
+// ---------------------------------------------------------------------------
+// Eq. (torque) at two samples of the same cubic per lane, u = (u.x, u.y):
+// torque_at_rolled's recursion with every floating-point step done on both
+// samples at once by the paired FP32 instructions (fma / add / mul .f32x2;
+// each half rounds like the scalar instruction).  Per-link constants come
+// from LinkTab2, whose entries hold each constant twice, (x, x, y, y), so a
+// pair is one load; the outward pass leaves its per-link state in a
+// LaneLink2 column of float2, the coefficients come from a CubicLane2 column
+// of duplicated pairs.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
+// a x b - the pair form of the scalar cross products (a_y b_z - a_z b_y, ...)
+__device__ __forceinline__ void cross2(float2 ax, float2 ay, float2 az, float2 bx, float2 by,
+                                       float2 bz, float2& cx, float2& cy, float2& cz) {
+  cx = fma2(ay, bz, neg2(mul2(az, by)));
+  cy = fma2(az, bx, neg2(mul2(ax, bz)));
+  cz = fma2(ax, by, neg2(mul2(ay, bx)));
+}
+
+// fn_sincos on both halves (the same reduction and polynomials)
+__device__ __forceinline__ void fn_sincos2(float2 x, float2& s, float2& c) {
+  const float2 t = mul2(x, dup2(0.636619772367581343f));
+  const float2 k = make_float2(rintf(t.x), rintf(t.y));
+  const float2 nk = neg2(k);
+  float2 r = fma2(nk, dup2(1.57079637050628662109375f), x);
+  r = fma2(nk, dup2(-4.37113900018624283e-8f), r);
+  const float2 r2 = mul2(r, r);
+  float2 sp = fma2(r2, dup2(2.75573192239858906526e-6f), dup2(-1.98412698412698412698e-4f));
+  sp = fma2(r2, sp, dup2(8.33333333333333333333e-3f));
+  sp = fma2(r2, sp, dup2(-1.66666666666666666667e-1f));
+  const float2 sr = fma2(mul2(r, r2), sp, r);
+  float2 cp = fma2(r2, dup2(-2.75573192239858906526e-7f), dup2(2.48015873015873015873e-5f));
+  cp = fma2(r2, cp, dup2(-1.38888888888888888889e-3f));
+  cp = fma2(r2, cp, dup2(4.16666666666666666667e-2f));
+  cp = fma2(r2, cp, dup2(-0.5f));
+  const float2 cr = fma2(r2, cp, dup2(1.0f));
+  const int qx = __float2int_rn(k.x) & 3, qy = __float2int_rn(k.y) & 3;
+  const float ax = (qx & 1) ? cr.x : sr.x, bx = (qx & 1) ? sr.x : cr.x;
+  const float ay = (qy & 1) ? cr.y : sr.y, by = (qy & 1) ? sr.y : cr.y;
+  s = make_float2((qx & 2) ? -ax : ax, (qy & 2) ? -ay : ay);
+  c = make_float2(((qx + 1) & 2) ? -bx : bx, ((qy + 1) & 2) ? -by : by);
+}
+
+#define FN_LINK2_F4 10   // float4 per link in the paired table
+struct LinkTab2 {
+  const float4* p;       // [7][FN_LINK2_F4] in shared memory
+  // (ca ca sa sa) (px px py py) (pz pz th0 th0) (m m cx cx) (cy cy cz cz)
+  // (Ix Ix Iy Iy) (Iz Iz arma arma) (f1 f1 f2 f2) (f3 f3 foff foff) (inv_tau 0 0 0)
+};
+
+// fill the paired table (thread 0 of the block; the caller synchronises)
+__device__ __forceinline__ void fill_links2(const ArmK& A, float4* t) {
+  if (threadIdx.x != 0) return;
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    float4* e = t + FN_LINK2_F4 * j;
+    e[0] = make_float4(A.ca[j], A.ca[j], A.sa[j], A.sa[j]);
+    e[1] = make_float4(A.px[j], A.px[j], A.py[j], A.py[j]);
+    e[2] = make_float4(A.pz[j], A.pz[j], A.th0[j], A.th0[j]);
+    e[3] = make_float4(A.m[j], A.m[j], A.cx[j], A.cx[j]);
+    e[4] = make_float4(A.cy[j], A.cy[j], A.cz[j], A.cz[j]);
+    e[5] = make_float4(A.Ix[j], A.Ix[j], A.Iy[j], A.Iy[j]);
+    e[6] = make_float4(A.Iz[j], A.Iz[j], A.arma[j], A.arma[j]);
+    e[7] = make_float4(A.f1[j], A.f1[j], A.f2[j], A.f2[j]);
+    e[8] = make_float4(A.f3[j], A.f3[j], A.foff[j], A.foff[j]);
+    e[9] = make_float4(A.inv_tau[j], 0.f, 0.f, 0.f);
+  }
+}
+
+// Per-link record of the outward pass, kept until the inward pass: F (3),
+// N (3), cos, sin, qd, armature + friction, as pairs (10 float2).
+#define FN_REC2 10
+// LaneLink2 keeps the records in the lane's column of a shared-memory buffer
+// ([FN_LINK2_WORDS / 2][32] float2 per warp).
+#define FN_LINK2_WORDS 140
+struct LaneLink2 {
+  float2* p;  // &buf[lane]
+  __device__ __forceinline__ void store(int j, const float2 (&r)[FN_REC2]) const {
+#pragma unroll
+    for (int k = 0; k < FN_REC2; ++k) p[32 * (FN_REC2 * j + k)] = r[k];
+  }
+  __device__ __forceinline__ void stored() const {}
+  __device__ __forceinline__ void load(int j, float2 (&r)[FN_REC2]) const {
+#pragma unroll
+    for (int k = 0; k < FN_REC2; ++k) r[k] = p[32 * (FN_REC2 * j + k)];
+  }
+};
+
+// the cubic's coefficients, each stored twice (one float2 per word)
+#define FN_CUBIC2_WORDS 60
+struct CubicLane2 {
+  float2* p;  // &buf[lane] of a [FN_CUBIC_WORDS][32] float2 per-warp buffer
+  __device__ __forceinline__ float2 q0(int j) const { return p[32 * j]; }
+  __device__ __forceinline__ float2 b1(int j) const { return p[32 * (7 + j)]; }
+  __device__ __forceinline__ float2 b2(int j) const { return p[32 * (14 + j)]; }
+  __device__ __forceinline__ float2 b3(int j) const { return p[32 * (21 + j)]; }
+  __device__ __forceinline__ float2 iT() const { return p[32 * 28]; }
+  __device__ __forceinline__ float2 iT2() const { return p[32 * 29]; }
+  __device__ __forceinline__ void store(const Cubic& c) const { store2(c, c); }
+  // different cubics in the two halves (x: cx, y: cy)
+  __device__ __forceinline__ void store2(const Cubic& cx, const Cubic& cy) const {
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      p[32 * j] = make_float2(cx.q0[j], cy.q0[j]);
+      p[32 * (7 + j)] = make_float2(cx.b1[j], cy.b1[j]);
+      p[32 * (14 + j)] = make_float2(cx.b2[j], cy.b2[j]);
+      p[32 * (21 + j)] = make_float2(cx.b3[j], cy.b3[j]);
+    }
+    p[32 * 28] = make_float2(cx.iT, cy.iT);
+    p[32 * 29] = make_float2(cx.iT2, cy.iT2);
+  }
+};
+
+// sink(j, tau_j, qd_j, 1 / tau_max_j) in the inward order j = 6..0, tau_j and
+// qd_j as pairs; gs, fs: per-half gravity and friction scales.  Stash:
+// store(j, rec) / stored() / load(j, rec) (LaneLink2, or a tensor-memory
+// column block); every lane of the warp must call this.
+template <class Sink, class Stash>
+__device__ __forceinline__ void torque_at_pair(const ArmK& A, LinkTab2 L, CubicLane2 c, float2 u,
+                                               Sink&& sink, Stash W, float2 gs = {1.f, 1.f},
+                                               float2 fs2 = {1.f, 1.f}) {
+  float2 wx = dup2(0.f), wy = dup2(0.f), wz = dup2(0.f);
+  float2 dwx = dup2(0.f), dwy = dup2(0.f), dwz = dup2(0.f);
+  float2 ax = mul2(dup2(A.g0x), gs), ay = mul2(dup2(A.g0y), gs), az = mul2(dup2(A.g0z), gs);
+  const float2 iT = c.iT(), iT2 = c.iT2();
+#pragma unroll 1
+  for (int j = 0; j < 7; ++j) {
+    const float4* t = L.p + FN_LINK2_F4 * j;
+    const float4 t0 = t[0], t1 = t[1], t2 = t[2], t3 = t[3], t4 = t[4];
+    const float4 t5 = t[5], t6 = t[6], t7 = t[7], t8 = t[8];
+    const float2 ca = lo2(t0), sa = hi2(t0), px = lo2(t1), py = hi2(t1), pz = lo2(t2);
+    float2 rec[FN_REC2];
+    // sigma, sigma_dot, sigma_ddot at both samples
+    const float2 b1 = c.b1(j), b2 = c.b2(j), b3 = c.b3(j), tb2 = add2(b2, b2);
+    const float2 q = fma2(fma2(fma2(b3, u, b2), u, b1), u, c.q0(j));
+    const float2 v = mul2(fma2(fma2(mul2(dup2(3.0f), b3), u, tb2), u, b1), iT);
+    const float2 acc = mul2(fma2(mul2(dup2(6.0f), b3), u, tb2), iT2);
+    // armature and friction
+    const float2 x = mul2(neg2(hi2(t7)), add2(v, lo2(t8)));
+    const float2 xe = mul2(x, dup2(1.44269504088896340736f));
+    float ex, ey;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex) : "f"(xe.x));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ey) : "f"(xe.y));
+    const float2 rc = make_float2(fn_rcp(1.0f + ex), fn_rcp(1.0f + ey));
+    rec[9] = fma2(hi2(t6), acc, mul2(fs2, fma2(lo2(t7), rc, neg2(hi2(t8)))));
+    rec[8] = v;
+    float2 s_, c_;
+    fn_sincos2(add2(q, hi2(t2)), s_, c_);
+    rec[6] = c_;
+    rec[7] = s_;
+    // u = dw_prev x p + w_prev x (w_prev x p) + dv_prev   (frame j-1)
+    float2 tx, ty, tz, gx, gy, gz, hx, hy, hz;
+    cross2(wx, wy, wz, px, py, pz, tx, ty, tz);
+    cross2(dwx, dwy, dwz, px, py, pz, gx, gy, gz);
+    cross2(wx, wy, wz, tx, ty, tz, hx, hy, hz);
+    const float2 ux = add2(add2(gx, hx), ax);
+    const float2 uy = add2(add2(gy, hy), ay);
+    const float2 uz = add2(add2(gz, hz), az);
+    // R^T v = Rz(-theta) Rx(-alpha) v
+    const float2 ns = neg2(s_), nsa = neg2(sa);
+    float2 r1 = fma2(ca, uy, mul2(sa, uz));
+    float2 r2 = fma2(nsa, uy, mul2(ca, uz));
+    ax = fma2(c_, ux, mul2(s_, r1));
+    ay = fma2(ns, ux, mul2(c_, r1));
+    az = r2;
+    r1 = fma2(ca, wy, mul2(sa, wz));
+    r2 = fma2(nsa, wy, mul2(ca, wz));
+    const float2 Rwx = fma2(c_, wx, mul2(s_, r1)), Rwy = fma2(ns, wx, mul2(c_, r1)), Rwz = r2;
+    r1 = fma2(ca, dwy, mul2(sa, dwz));
+    r2 = fma2(nsa, dwy, mul2(ca, dwz));
+    const float2 Rdx = fma2(c_, dwx, mul2(s_, r1)), Rdy = fma2(ns, dwx, mul2(c_, r1)), Rdz = r2;
+    wx = Rwx; wy = Rwy; wz = add2(Rwz, v);
+    dwx = fma2(Rwy, v, Rdx);
+    dwy = fma2(neg2(Rwx), v, Rdy);
+    dwz = add2(Rdz, acc);
+    // COM acceleration and link wrench
+    const float2 cx = hi2(t3), cy = lo2(t4), cz = hi2(t4);
+    float2 wcx, wcy, wcz, dcx, dcy, dcz, ex2_, ey2_, ez2_;
+    cross2(wx, wy, wz, cx, cy, cz, wcx, wcy, wcz);
+    cross2(dwx, dwy, dwz, cx, cy, cz, dcx, dcy, dcz);
+    cross2(wx, wy, wz, wcx, wcy, wcz, ex2_, ey2_, ez2_);
+    const float2 m = lo2(t3), Ix = lo2(t5), Iy = hi2(t5), Iz = lo2(t6);
+    rec[0] = mul2(m, add2(add2(dcx, ex2_), ax));
+    rec[1] = mul2(m, add2(add2(dcy, ey2_), ay));
+    rec[2] = mul2(m, add2(add2(dcz, ez2_), az));
+    const float2 Iwx = mul2(Ix, wx), Iwy = mul2(Iy, wy), Iwz = mul2(Iz, wz);
+    float2 kx, ky, kz;
+    cross2(wx, wy, wz, Iwx, Iwy, Iwz, kx, ky, kz);
+    rec[3] = fma2(Ix, dwx, kx);
+    rec[4] = fma2(Iy, dwy, ky);
+    rec[5] = fma2(Iz, dwz, kz);
+    W.store(j, rec);
+  }
+  W.stored();
+  float2 fx = dup2(0.f), fy = dup2(0.f), fz = dup2(0.f);
+  float2 nx = dup2(0.f), ny = dup2(0.f), nz = dup2(0.f);
+  float2 cn = dup2(1.f), sn = dup2(0.f);   // cos, sin of joint j + 1 (any value for j = 6)
+#pragma unroll 1
+  for (int j = 6; j >= 0; --j) {
+    float2 rec[FN_REC2];
+    W.load(j, rec);
+    // R_{j+1} (f, n) and p_{j+1} x R_{j+1} f; zero for the last link (f = n = 0)
+    const int jc = j < 6 ? j + 1 : 6;
+    const float4* t = L.p + FN_LINK2_F4 * jc;
+    const float4 k0 = t[0], k1 = t[1], k2 = t[2];
+    const float2 ca = lo2(k0), sa = hi2(k0), nsa = neg2(sa), ns = neg2(sn);
+    float2 u0 = fma2(cn, fx, mul2(ns, fy)), u1 = fma2(sn, fx, mul2(cn, fy)), u2 = fz;
+    const float2 Rfx = u0, Rfy = fma2(ca, u1, mul2(nsa, u2)), Rfz = fma2(sa, u1, mul2(ca, u2));
+    u0 = fma2(cn, nx, mul2(ns, ny)); u1 = fma2(sn, nx, mul2(cn, ny)); u2 = nz;
+    const float2 Rnx = u0, Rny = fma2(ca, u1, mul2(nsa, u2)), Rnz = fma2(sa, u1, mul2(ca, u2));
+    float2 pRx, pRy, pRz;
+    cross2(lo2(k1), hi2(k1), lo2(k2), Rfx, Rfy, Rfz, pRx, pRy, pRz);
+    const float4* m = L.p + FN_LINK2_F4 * j;
+    const float4 m3 = m[3], m4 = m[4];
+    float2 cFx, cFy, cFz;
+    cross2(hi2(m3), lo2(m4), hi2(m4), rec[0], rec[1], rec[2], cFx, cFy, cFz);
+    fx = add2(rec[0], Rfx); fy = add2(rec[1], Rfy); fz = add2(rec[2], Rfz);
+    nx = add2(add2(add2(rec[3], Rnx), cFx), pRx);
+    ny = add2(add2(add2(rec[4], Rny), cFy), pRy);
+    nz = add2(add2(add2(rec[5], Rnz), cFz), pRz);
+    cn = rec[6];
+    sn = rec[7];
+    sink(j, add2(nz, rec[9]), rec[8], m[9].x);
+  }
+}
+
 // one configuration (q, qd, qdd) handed to torque_at as its "sample"
 struct PointCoef {
   float q[7], qd[7], qdd[7];

@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(32 * CHECK_WARPS, 3)
       continue;
     }
     float rt = NAN, rp = NAN;
-    if (edge_scan(A, L, es, cb, wr, nullptr, nullptr, 0, S, true, T, true, rt, rp, nsamp) ==
+    if (edge_scan(A, ScalarCore{L, cb, wr}, es, nullptr, nullptr, 0, S, true, T, true, rt, rp, nsamp) ==
         FN_SCAN_ABORT)
       rt = rp = NAN;   // the scan's pass bound (never expected): not ok
     const float rv = warp_rho_v(A, es, T);

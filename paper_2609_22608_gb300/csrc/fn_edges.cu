@@ -9,6 +9,7 @@
 #include <unordered_map>
 
 #include "edge_core.cuh"
+#include "fn_tmem.cuh"
 #include "fn_internal.h"
 #include "fn_tune.h"
 
@@ -54,7 +55,7 @@ __global__ void __launch_bounds__(32 * EDGE_WARPS, MINB)
     const bool fixed = mode == FN_MODE_FIXED;
     const float Tp = Tparam ? __ldg(Tparam + e) : INFINITY;
     const EdgeResult r =
-        time_edge(A, L, es, cb, wr, sSplit[w], finite, fixed, Tp, sT, K, S, true, nsamp);
+        time_edge(A, ScalarCore{L, cb, wr}, es, sSplit[w], finite, fixed, Tp, sT, K, S, true, nsamp);
     if (lane == 0) {
       k_star[e] = r.k;
       T_star[e] = r.T;
@@ -65,6 +66,92 @@ __global__ void __launch_bounds__(32 * EDGE_WARPS, MINB)
     }
   }
   if (counter && lane == 0 && nsamp) atomicAdd(counter, (unsigned long long)nsamp);
+}
+
+// The paired scan (two samples per lane, PairCore) with the per-link records
+// of the torque evaluation in tensor memory: one CTA of TM_WARPS = 12 warps
+// per SM holds all 512 columns; warp w uses lane quarter w % 4 and the
+// 144-column block 144 (w / 4) (three warps per quarter).  A warp takes its
+// edges TM_GROUP at a time: it stages them, computes their end-sample splits
+// in one pass (split_group: sixty (edge, end, part) items on the lanes'
+// two halves), then scans them one by one.  The coefficients, staged edges,
+// splits, the paired link table and the grid sit in dynamic shared memory,
+// sized above half of the SM's so that no second CTA (which would wait for
+// the columns) is placed on the SM.
+#define TM_WARPS 12
+#define TM_GROUP 10
+constexpr int kTmCols = 512;
+constexpr size_t kTmCoef = (size_t)TM_WARPS * FN_CUBIC_WORDS * 32 * sizeof(float2);
+constexpr size_t kTmEdge = (size_t)TM_WARPS * TM_GROUP * 32 * sizeof(float);
+constexpr size_t kTmSplit = (size_t)TM_WARPS * TM_GROUP * FN_SPLIT_WORDS * sizeof(float);
+constexpr size_t kTmLink = 7 * FN_LINK2_F4 * sizeof(float4);
+constexpr size_t kTmGrid = FN_MAX_GRID * sizeof(float);
+constexpr size_t kTmUsed = kTmCoef + kTmEdge + kTmSplit + kTmLink + kTmGrid + 16;
+constexpr size_t kTmSmem = 140 * 1024;
+static_assert(kTmUsed <= kTmSmem, "tensor-memory scan: shared-memory layout");
+static_assert(2 * (kTmSmem + 1024) > 233472, "one CTA per SM");
+static_assert(kTmCoef % 16 == 0 && kTmEdge % 16 == 0 && kTmSplit % 16 == 0, "16-byte carve");
+static_assert(FN_SPLIT_WORDS * sizeof(float) % 16 == 0, "16-byte split slots");
+static_assert(TM_GROUP <= 10, "split_group takes at most ten edges");
+static_assert(3 * FN_TM_COLS_PER_WARP <= kTmCols, "three warps per lane quarter");
+
+__global__ void __launch_bounds__(32 * TM_WARPS, 1)
+    k_time_edges_tm(ArmK A, GridK G, int K, int S, int mode, const float* __restrict__ s0,
+                    const float* __restrict__ s1, int E, const float* __restrict__ Tparam,
+                    int32_t* __restrict__ k_star, float* __restrict__ T_star,
+                    float* __restrict__ rho3, uint8_t* __restrict__ ok,
+                    unsigned long long* __restrict__ counter) {
+  extern __shared__ float4 tm_smem[];
+  char* base = reinterpret_cast<char*>(tm_smem);
+  float2* sCoef = reinterpret_cast<float2*>(base);
+  float* sEdge = reinterpret_cast<float*>(base + kTmCoef);
+  float* sSplit = reinterpret_cast<float*>(base + kTmCoef + kTmEdge);
+  float4* sLink = reinterpret_cast<float4*>(base + kTmCoef + kTmEdge + kTmSplit);
+  float* sT = reinterpret_cast<float*>(base + kTmCoef + kTmEdge + kTmSplit + kTmLink);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(base + kTmCoef + kTmEdge + kTmSplit + kTmLink +
+                                                 kTmGrid);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  fill_links2(A, sLink);
+  if (mode == FN_MODE_FULL)
+    for (int i = threadIdx.x; i < K; i += blockDim.x) sT[i] = G.T[i];
+  if (w == 0) tmem_alloc(s_tmem, kTmCols);
+  tmem_sync_block();
+  const uint32_t tmem = *s_tmem;
+  const PairCore<TmemStash> core{
+      LinkTab2{sLink}, CubicLane2{sCoef + w * FN_CUBIC_WORDS * 32 + lane},
+      TmemStash{tmem + ((uint32_t)((w & 3) * 32) << 16) + FN_TM_COLS_PER_WARP * (uint32_t)(w >> 2)}};
+  float* es_g = sEdge + TM_GROUP * 32 * w;
+  float* split_g = sSplit + TM_GROUP * FN_SPLIT_WORDS * w;
+  const bool fixed = mode == FN_MODE_FIXED;
+  const long W = (long)gridDim.x * TM_WARPS;
+  unsigned nsamp = 0;
+  // the warp's edges e0, e0 + W, e0 + 2 W, ..., TM_GROUP at a time
+  for (long e0 = (long)blockIdx.x * TM_WARPS + w; e0 < E; e0 += W * TM_GROUP) {
+    int n = 0;
+    unsigned fin = 0u;
+    for (; n < TM_GROUP && e0 + n * W < E; ++n) {
+      const long e = e0 + n * W;
+      if (stage_rows(s0 + 16 * e, s1 + 16 * e, es_g + 32 * n)) fin |= 1u << n;
+    }
+    if (!fixed) split_group(A, core, es_g, split_g, n, nsamp);
+    for (int i = 0; i < n; ++i) {
+      const long e = e0 + i * W;
+      const float Tp = Tparam ? __ldg(Tparam + e) : INFINITY;
+      const EdgeResult r = time_edge(A, core, es_g + 32 * i, split_g + FN_SPLIT_WORDS * i,
+                                     ((fin >> i) & 1u) != 0u, fixed, Tp, sT, K, S, true, nsamp);
+      if (lane == 0) {
+        k_star[e] = r.k;
+        T_star[e] = r.T;
+        rho3[3 * e + 0] = r.rt;
+        rho3[3 * e + 1] = r.rp;
+        rho3[3 * e + 2] = r.rv;
+        ok[e] = r.ok ? 1 : 0;
+      }
+    }
+  }
+  if (counter && lane == 0 && nsamp) atomicAdd(counter, (unsigned long long)nsamp);
+  tmem_sync_block();   // every warp's tensor-memory accesses precede the release
+  if (w == 0) tmem_dealloc(tmem, kTmCols);
 }
 
 // tau[e][s][j]: one thread per (edge, sample)
@@ -108,10 +195,37 @@ static int resident_blocks(EdgeKernel k) {
   return per_sm * num_sms();
 }
 
+static fn_status launch_time_edges_tm(const ArmK& A, const GridK* G, int K, int S, int mode,
+                                      const float* s0, const float* s1, int E,
+                                      const float* Tparam, int32_t* k_star, float* T_star,
+                                      float* rho3, uint8_t* ok, unsigned long long* counter,
+                                      cudaStream_t st) {
+  static std::once_flag once[64];
+  static bool attr_ok[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::call_once(once[dev & 63], [&] {
+    attr_ok[dev & 63] = cudaFuncSetAttribute(k_time_edges_tm,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kTmSmem) == cudaSuccess;
+  });
+  if (!attr_ok[dev & 63]) return FN_ECUDA;
+  const long want = ((long)E + TM_WARPS - 1) / TM_WARPS;
+  const int blocks = (int)std::max<long>(1, std::min<long>(want, num_sms()));
+  static GridK empty;
+  k_time_edges_tm<<<blocks, 32 * TM_WARPS, kTmSmem, st>>>(A, G ? *G : empty, K, S, mode, s0, s1, E,
+                                                           Tparam, k_star, T_star, rho3, ok,
+                                                           counter);
+  return launch_status();
+}
+
 fn_status launch_time_edges(const ArmK& A, const GridK* G, int K, int S, int mode,
                             const float* s0, const float* s1, int E, const float* Tparam,
                             int32_t* k_star, float* T_star, float* rho3, uint8_t* ok,
                             unsigned long long* counter, cudaStream_t st, int variant) {
+  if (variant == kPairEdgeVariant)
+    return launch_time_edges_tm(A, G, K, S, mode, s0, s1, E, Tparam, k_star, T_star, rho3, ok,
+                                counter, st);
   EdgeKernel k = edge_variant(variant);
   const long want = ((long)E + EDGE_WARPS - 1) / EDGE_WARPS;
   const int blocks = (int)std::max<long>(1, std::min<long>(want, resident_blocks(k)));

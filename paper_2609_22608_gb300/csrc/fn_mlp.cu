@@ -664,7 +664,7 @@ __global__ void __launch_bounds__(32 * WIN_WARPS, 4) k_time_window(ArmK A, GridW
       float rt_alt = NAN, rp_alt = NAN;
       while (step != DONE) {
         float t1 = NAN, t2 = NAN;
-        const int k = (b1 > b0) ? edge_scan(A, L, es, cb, wr, sSplit[w], sT, b1, S, false, 0.f, false, t1, t2,
+        const int k = (b1 > b0) ? edge_scan(A, ScalarCore{L, cb, wr}, es, sSplit[w], sT, b1, S, false, 0.f, false, t1, t2,
                                             nsamp, b0)
                                 : -1;
         if (k == FN_SCAN_ABORT) {          // the scan's pass bound (never expected)

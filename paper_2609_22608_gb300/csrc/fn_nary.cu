@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(32 * NARY_WARPS, MINB)
         float t_rt = NAN, t_rp = NAN;
         int w_out = -1;
         const bool grid = dur == sT;
-        const int idx = edge_scan(A, L, es, cb, wr, sSplit[w], dur, n, S, false, 0.f, false, t_rt, t_rp, nsamp,
+        const int idx = edge_scan(A, ScalarCore{L, cb, wr}, es, sSplit[w], dur, n, S, false, 0.f, false, t_rt, t_rp, nsamp,
                                   0, grid ? 1 : 2, wit, &w_out);
         if (idx == FN_SCAN_ABORT) {          // the scan's pass bound (never expected)
           k = FN_SCAN_ABORT;
@@ -137,7 +137,8 @@ extern "C" fn_status fn_time_edges_nary(const fn_arm_t* arm, const float* s0, co
   typedef void (*Kern)(ArmK, NaryGrid, int, int, const float*, const float*, int, const float*,
                        float, int, int32_t*, float*, float*, float*, uint8_t*, int32_t*,
                        unsigned long long*);
-  const int v = tuned_variant(TUNE_EDGES_FULL, E, K, S);
+  const int vt = tuned_variant(TUNE_EDGES_FULL, E, K, S);   // its register budget
+  const int v = vt < kEdgeVariants ? vt : kDefaultEdgeVariant;
   Kern kern = v == 0 ? k_time_edges_nary<2> : (v == 1 ? k_time_edges_nary<3> : k_time_edges_nary<4>);
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * NARY_WARPS, 0) !=

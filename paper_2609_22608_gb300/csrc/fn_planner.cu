@@ -79,6 +79,7 @@ struct Sched {
   int n_pend[2];      // lengths of the two pending-edge lists
   int n_surv;         // probe survivors appended (may exceed surv_cap)
   int n_dyn;          // edges with probe items listed by the prep (zero between bodies)
+  unsigned prep_done; // blocks of k_plan_eprep finished (zero between iterations)
   int n_free_edges;   // free edges of all problems (the queue's first part)
   int n_edges;        // all edges
   // parent-search items (problem, query group, split), one per warp, in two
@@ -895,6 +896,27 @@ __device__ __forceinline__ void list_dyn_edge(const PlanDev& D, int e, bool has_
   if (has_items) D.dyn_list[base + __popc(m & ((1u << lane) - 1u))] = e;
 }
 
+// exclusive scan of the per-block item totals (one block of PL_SCAN threads)
+__device__ __forceinline__ void scan_block_totals(const PlanDev& D, int* sh) {
+  Sched* S = D.sched;
+  const int nb = (S->n_edges + PL_SCAN - 1) / PL_SCAN;
+  int carry = 0;
+  for (int base = 0; base < nb; base += PL_SCAN) {
+    const int i = base + threadIdx.x;
+    const int v = i < nb ? __ldcg(D.blk_off + i) : 0;
+    int tot;
+    const int ex = block_scan(v, sh, &tot);
+    if (i < nb) D.blk_off[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) {
+    S->n_items = carry;
+    S->queue_head = 0u;
+    S->n_pend[0] = S->n_pend[1] = 0;   // verification lists and probe survivors
+    S->n_surv = 0;
+  }
+}
+
 __global__ void __launch_bounds__(PL_SCAN) k_plan_eprep(PlanDev D, GridKP Gr) {
   pdl_begin();
   __shared__ float sT[FN_MAX_GRID];
@@ -955,30 +977,28 @@ __global__ void __launch_bounds__(PL_SCAN) k_plan_eprep(PlanDev D, GridKP Gr) {
   int tot;
   const int ex = block_scan(cnt, sh, &tot);
   if (e < E) D.e_cnt[e] = ex;
-  if (threadIdx.x == 0) D.blk_off[blockIdx.x] = tot;
+  // the block that finishes last scans the block totals (the planner's
+  // k_plan_escan folded into this launch): each block's total is fenced
+  // before the block is counted
+  __shared__ bool s_last;
+  if (threadIdx.x == 0) {
+    D.blk_off[blockIdx.x] = tot;
+    __threadfence();
+    const unsigned done = atomicAdd(&D.sched->prep_done, 1u);
+    s_last = done == gridDim.x - 1;
+    if (s_last) D.sched->prep_done = 0u;   // ready for the next iteration
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    scan_block_totals(D, sh);
+  }
 }
 
-// exclusive scan of the per-block item totals (one block)
 __global__ void __launch_bounds__(PL_SCAN) k_plan_escan(PlanDev D) {
   pdl_begin();
   __shared__ int sh[32];
-  Sched* S = D.sched;
-  const int nb = (S->n_edges + PL_SCAN - 1) / PL_SCAN;
-  int carry = 0;
-  for (int base = 0; base < nb; base += PL_SCAN) {
-    const int i = base + threadIdx.x;
-    const int v = i < nb ? D.blk_off[i] : 0;
-    int tot;
-    const int ex = block_scan(v, sh, &tot);
-    if (i < nb) D.blk_off[i] = carry + ex;
-    carry += tot;
-  }
-  if (threadIdx.x == 0) {
-    S->n_items = carry;
-    S->queue_head = 0u;
-    S->n_pend[0] = S->n_pend[1] = 0;   // verification lists and probe survivors
-    S->n_surv = 0;
-  }
+  scan_block_totals(D, sh);
 }
 
 __device__ __forceinline__ int item_off(const PlanDev& D, int e) {
@@ -1516,8 +1536,8 @@ __global__ void __launch_bounds__(32 * PL_REFINE_WARPS, 4)
     stage_rows(D.st + ((long)p * D.NC + D.e_par[e]) * 16, D.cand + (long)ci * 16, sEs[w]);
     float a = k > 0 ? Gr.T[k - 1] : 0.f, b = Gr.T[k];
     float rt = NAN, rp = NAN;
-    const int rounds = nary_rounds(A, L, sEs[w], cb, wr, sSplit[w], sSub[w], D.S, eps, max_rounds,
-                                   a, b, -1, rt, rp, nsamp);
+    const int rounds = nary_rounds(A, ScalarCore{L, cb, wr}, sEs[w], sSplit[w], sSub[w], D.S,
+                                   eps, max_rounds, a, b, -1, rt, rp, nsamp);
     if (rounds == FN_SCAN_ABORT) {                      // keep the grid duration; flag it
       a = k > 0 ? Gr.T[k - 1] : 0.f;
       b = Gr.T[k];
@@ -1541,7 +1561,35 @@ __global__ void __launch_bounds__(32 * PL_REFINE_WARPS, 4)
 // ---------------------------------------------------------------------------
 #define PL_ATTACH_THREADS 1024
 
-__global__ void __launch_bounds__(PL_ATTACH_THREADS) k_plan_attach(PlanDev D) {
+// the caller's record of problem p: incumbent, its J and time, tree counts,
+// status, and the first segment of the incumbent's path
+__device__ void write_rendezvous(const PlanDev& D, int p) {
+  const long nb = (long)p * D.NC;
+  const Incumbent in = D.inc[p];
+  fn_rendezvous_t o;
+  memset(&o, 0, sizeof(o));
+  o.incumbent = in.id;
+  o.J = in.J;
+  o.t_best = in.t_best;
+  o.n_nodes = D.n_nodes[p];
+  o.n_added = D.added[p];
+  o.status = D.status[p];
+  if (in.id > 0) {
+    int c = in.id;
+    for (int guard = 0; guard < D.NC && D.par[nb + c] > 0; ++guard) c = D.par[nb + c];
+    const float* s = D.st + (nb + c) * 16;
+    for (int j = 0; j < 7; ++j) { o.q_g[j] = s[j]; o.qd_g[j] = s[8 + j]; }
+    o.T = D.eT[nb + c];
+  } else {
+    o.T = NAN;
+  }
+  D.out[p] = o;
+}
+
+// with `output`, thread 0 also writes the problem's record (k_plan_output
+// folded into this launch when no later kernel of the iteration changes the
+// tree or the incumbent)
+__global__ void __launch_bounds__(PL_ATTACH_THREADS) k_plan_attach(PlanDev D, int output) {
   pdl_begin();
   __shared__ int sh[PL_ATTACH_THREADS];
   __shared__ float sJ[PL_ATTACH_THREADS];
@@ -1633,6 +1681,7 @@ __global__ void __launch_bounds__(PL_ATTACH_THREADS) k_plan_attach(PlanDev D) {
       in.t_best = D.t[nb + sI[0]];
       D.inc[p] = in;
     }
+    if (output) write_rendezvous(D, p);
   }
 }
 
@@ -1818,7 +1867,7 @@ __device__ __forceinline__ float warp_node_value(const PlanDev& D, const ArmK& A
   if (check) {
     float rt = NAN, rp = NAN;
     unsigned ns = 0;
-    bool ok = edge_scan(A, L, es, cb, wr, nullptr, nullptr, 0, D.S, true, Tp, true, rt, rp, ns) == 0;
+    bool ok = edge_scan(A, ScalarCore{L, cb, wr}, es, nullptr, nullptr, 0, D.S, true, Tp, true, rt, rp, ns) == 0;
     ok = ok && rv <= 1.f;
     if (ok && P.n_obs > 0) ok = warp_clearance(D, A, P, es, Tp) >= D.margin;
     if (!ok) return -INFINITY;
@@ -2100,26 +2149,7 @@ __global__ void k_plan_output(PlanDev D) {
   pdl_begin();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= D.P) return;
-  const long nb = (long)p * D.NC;
-  const Incumbent in = D.inc[p];
-  fn_rendezvous_t o;
-  memset(&o, 0, sizeof(o));
-  o.incumbent = in.id;
-  o.J = in.J;
-  o.t_best = in.t_best;
-  o.n_nodes = D.n_nodes[p];
-  o.n_added = D.added[p];
-  o.status = D.status[p];
-  if (in.id > 0) {
-    int c = in.id;
-    for (int guard = 0; guard < D.NC && D.par[nb + c] > 0; ++guard) c = D.par[nb + c];
-    const float* s = D.st + (nb + c) * 16;
-    for (int j = 0; j < 7; ++j) { o.q_g[j] = s[j]; o.qd_g[j] = s[8 + j]; }
-    o.T = D.eT[nb + c];
-  } else {
-    o.T = NAN;
-  }
-  D.out[p] = o;
+  write_rendezvous(D, p);
 }
 
 }  // namespace fn
@@ -2357,9 +2387,11 @@ static int vstages(const PlanDev& D) { return D.vstages >= 2 ? 2 : 1; }
 // timing)
 template <class Mark>
 static void enqueue_edge_body(fn_planner* pl, const PlanDev& D, int v, int blocks, cudaStream_t st,
-                              Mark&& mark) {
-  pl_launch(k_plan_escan, 1, PL_SCAN, 0, st, D);
-  trace(pl, st, "k_plan_escan");
+                              Mark&& mark, bool scan = true) {
+  if (scan) {   // k_plan_eprep scans the block totals itself
+    pl_launch(k_plan_escan, 1, PL_SCAN, 0, st, D);
+    trace(pl, st, "k_plan_escan");
+  }
   pl_launch(k_plan_expand, expand_blocks(), 256, 0, st, D, pl->arm);
   trace(pl, st, "k_plan_expand");
   mark(4);
@@ -2390,7 +2422,7 @@ static void enqueue_edges(fn_planner* pl, int v, int blocks, cudaStream_t st, Ma
   const int eb = (D.Emax + PL_SCAN - 1) / PL_SCAN;
   pl_launch(k_plan_eprep, eb, PL_SCAN, 0, st, D, pl->grid);
   trace(pl, st, "k_plan_eprep");
-  enqueue_edge_body(pl, D, v, blocks, st, mark);
+  enqueue_edge_body(pl, D, v, blocks, st, mark, false);
 }
 
 extern "C" fn_status fn_planner_destroy(fn_planner_t* pl) {
@@ -2647,7 +2679,8 @@ static fn_status enqueue_iteration(fn_planner* pl, unsigned flags, cudaStream_t 
     trace(pl, st, "k_plan_refine");
   }
   mark(6);
-  pl_launch(k_plan_attach, P, PL_ATTACH_THREADS, 0, st, D);
+  const bool late = flags & (FN_PLAN_DENSITY | FN_PLAN_REFIT | FN_PLAN_GREFINE | FN_PLAN_PRUNE);
+  pl_launch(k_plan_attach, P, PL_ATTACH_THREADS, 0, st, D, late ? 0 : 1);
   trace(pl, st, "k_plan_attach");
   if (flags & (FN_PLAN_DENSITY | FN_PLAN_REFIT)) {
     pl_launch(k_plan_density, P, PL_DENSITY_THREADS, 0, st, D, (flags & FN_PLAN_REFIT) ? 1 : 0);
@@ -2667,8 +2700,10 @@ static fn_status enqueue_iteration(fn_planner* pl, unsigned flags, cudaStream_t 
     trace(pl, st, "k_plan_prune");
   }
   mark(8);
-  pl_launch(k_plan_output, (P + 127) / 128, 128, 0, st, D);
-  trace(pl, st, "k_plan_output");
+  if (late) {
+    pl_launch(k_plan_output, (P + 127) / 128, 128, 0, st, D);
+    trace(pl, st, "k_plan_output");
+  }
   pl->tracing = false;
   mark(9);
   if (cudaMemcpyAsync(pl->h_out, D.out, sizeof(fn_rendezvous_t) * P, cudaMemcpyDeviceToHost, st) !=

@@ -31,7 +31,9 @@ int tuned_variant(int kind, long n, int K, int S) {
   std::lock_guard<std::mutex> g(g_mu);
   auto it = g_cache.find(std::make_tuple(current_device(), kind, bucket(n), K, S));
   if (it != g_cache.end()) return it->second;
-  return kind == TUNE_KNN ? 0 : kDefaultEdgeVariant;
+  if (kind == TUNE_KNN) return 0;
+  return (kind == TUNE_EDGES_FULL || kind == TUNE_EDGES_FIXED) ? kPairEdgeVariant
+                                                               : kDefaultEdgeVariant;
 }
 
 void set_tuned_variant(int kind, long n, int K, int S, int v) {
@@ -68,10 +70,10 @@ extern "C" fn_status fn_autotune_time_edges(const fn_arm_t* arm, const float* s0
   const int Kb = mode == FN_MODE_FULL ? K : 1;
   cudaEvent_t a, b;
   if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return FN_ECUDA;
-  int best = kDefaultEdgeVariant;
+  int best = kPairEdgeVariant;
   float best_ms = INFINITY;
   fn_status rc = FN_OK;
-  for (int v = 0; v < kEdgeVariants && rc == FN_OK; ++v) {
+  for (int v = 0; v < kTimeEdgeVariants && rc == FN_OK; ++v) {
     set_tuned_variant(kind, E, Kb, S, v);
     // one untimed run, then `reps` timed runs
     rc = fn_time_edges_counted(arm, s0, s1, E, T_grid, K, S, mode, T_fixed, T_cap, k_star,

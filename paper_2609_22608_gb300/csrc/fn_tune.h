@@ -13,6 +13,10 @@ enum TuneKind { TUNE_EDGES_FULL = 0, TUNE_EDGES_FIXED = 1, TUNE_PLAN_EDGES = 2, 
 
 constexpr int kEdgeVariants = 3;  // __launch_bounds__ min blocks 2, 3, 4
 constexpr int kDefaultEdgeVariant = 1;
+// fn_time_edges has one more: the paired scan with its records in tensor
+// memory (its default); kernels without it map that index to their default
+constexpr int kPairEdgeVariant = 3;
+constexpr int kTimeEdgeVariants = 4;
 
 int tuned_variant(int kind, long n, int K, int S);
 void set_tuned_variant(int kind, long n, int K, int S, int v);

@@ -48,8 +48,9 @@ __device__ __forceinline__ void nary_bracket(const float* sub, int idx, int w_ou
 // the sample that proved a infeasible, -1 if unknown).  Returns the rounds
 // run, or FN_SCAN_ABORT if a round's scan hit its pass bound.  One edge_scan
 // call site.
-__device__ __forceinline__ int nary_rounds(const ArmK& A, LinkTab L, float* es, CubicLane cb,
-                                           LaneLink wr, float* split, float* sub, int S, float eps,
+template <class Core>
+__device__ __forceinline__ int nary_rounds(const ArmK& A, const Core& core, float* es,
+                                           float* split, float* sub, int S, float eps,
                                            int max_rounds, float& a, float& b, int wit, float& rt,
                                            float& rp, unsigned& nsamp) {
   int r = 0;
@@ -57,7 +58,7 @@ __device__ __forceinline__ int nary_rounds(const ArmK& A, LinkTab L, float* es, 
     nary_points(sub, a, b);
     float t_rt = NAN, t_rp = NAN;
     int w_out = -1;
-    const int idx = edge_scan(A, L, es, cb, wr, split, sub, NARY_N - 1, S, false, 0.f, false, t_rt, t_rp,
+    const int idx = edge_scan(A, core, es, split, sub, NARY_N - 1, S, false, 0.f, false, t_rt, t_rp,
                               nsamp, 0, 2, wit, &w_out);
     if (idx == FN_SCAN_ABORT) return FN_SCAN_ABORT;   // the scan's pass bound
     nary_bracket(sub, idx, w_out, t_rt, t_rp, a, b, wit, rt, rp);

@@ -76,9 +76,11 @@ def time_edges(arm, s0, s1, T_grid=None, S=32, mode=FN_MODE_FULL, T_fixed=None, 
 
 
 def autotune_time_edges(arm, s0, s1, T_grid, S, reps=3, T_cap=None, stream=None):
-    """fn_autotune_time_edges (FULL mode): times every register-budget variant
-    of the edge kernels on this workload and keeps the fastest for its shape
-    (the N-ary refinement follows the same choice).  Returns (variant, ms[3])."""
+    """fn_autotune_time_edges (FULL mode): times every schedule variant of the
+    edge kernels on this workload (three register budgets of the scalar scan,
+    then the paired scan with tensor-memory records) and keeps the fastest for
+    its shape (the N-ary refinement follows a scalar choice).  Returns
+    (variant, ms[4])."""
     _states(s0, "s0"); _states(s1, "s1")
     E = s0.shape[0]
     A = arm_struct(arm)
@@ -89,7 +91,7 @@ def autotune_time_edges(arm, s0, s1, T_grid, S, reps=3, T_cap=None, stream=None)
                ok=torch.empty(E, dtype=torch.uint8, device=dev))
     g = np.ascontiguousarray(np.asarray(T_grid, np.float32))
     chosen = C.c_int(-1)
-    ms = (C.c_float * 3)()
+    ms = (C.c_float * 4)()
     st = lib().fn_autotune_time_edges(C.byref(A), _ptr(s0), _ptr(s1), E,
                                       g.ctypes.data_as(C.c_void_p), int(g.size), int(S),
                                       FN_MODE_FULL, None, _ptr(T_cap), _ptr(out["k_star"]),
