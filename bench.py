@@ -898,6 +898,13 @@ def run_batched(args, surrogate_W=0, densities=False, nary=False):
         pl.work_counts(reset=True)
         return _timed_replays(pl, probs, steps, stream, 100, restore)
 
+    def traced(flags=0):
+        """one plain (un-timed) iteration with a CUDA event after every launch"""
+        restore()
+        pl.iterate(probs, 0, flags, stream=stream)
+        torch.cuda.synchronize()
+        return kernel_table(pl.kernel_ms())
+
     extra = {}
     if surrogate_W > 0:
         t0 = time.perf_counter()
@@ -912,6 +919,7 @@ def run_batched(args, surrogate_W=0, densities=False, nary=False):
         ms, out, clk = timed()
         sur_s = time.perf_counter() - t0
         wc = pl.work_counts()
+        kernels = traced()
         mlp_err = bool(mlp.error())
         pl.set_surrogate(None)
         mlp.close()
@@ -930,6 +938,7 @@ def run_batched(args, surrogate_W=0, densities=False, nary=False):
         pl.set_refine(args.eps, 8)
         ms, out, clk = timed(P.FN_PLAN_NARY)
         wc = pl.work_counts()
+        kernels = traced(P.FN_PLAN_NARY)
         extra = {"refine": {"eps_s": args.eps, "max_rounds": 8,
                             "refine_torque_evaluations_per_step": wc["refine"] / steps,
                             "edge_torque_evaluations_per_step":
@@ -951,6 +960,7 @@ def run_batched(args, surrogate_W=0, densities=False, nary=False):
         flags = P.FN_PLAN_DENSITY | P.FN_PLAN_CHORD | P.FN_PLAN_REFIT
         ms, out, clk = timed(flags)
         wc = pl.work_counts()
+        kernels = traced(flags)
 
         def evals(w):
             return (w["probe"] + w["mprobe"] + w["verify"]) / steps
@@ -967,6 +977,7 @@ def run_batched(args, surrogate_W=0, densities=False, nary=False):
                  "cost_vs_plain": float(np.mean(ms) / np.mean(ms_plain))}
     else:
         ms, out, clk = timed()
+        kernels = traced()
     wc_last = pl.work_counts()
     # formed edges of the last timed replay: decoded goal draws and free
     # candidates of every problem, times k (read back after the timed region)
@@ -991,6 +1002,9 @@ def run_batched(args, surrogate_W=0, densities=False, nary=False):
                    "edge_variant_ms": tuned[1]},
         "nodes_added_last": int(sum(o["n_added"] for o in out)),
         "clocks": clk,
+        "kernels_ms": kernels,
+        "kernels_note": "one traced iteration after the timed replays (events after every "
+                        "launch, serialised; a replay overlaps some of them)",
         **extra,
     }
 
