@@ -267,6 +267,18 @@ fn_status fn_autotune_time_edges(const fn_arm_t* arm, const float* s0, const flo
                                  float* variant_ms, void* stream);
 
 /*
+ * fn_time_edges_set_variant -- pin the schedule variant (0..3, as listed
+ * under fn_autotune_time_edges) that fn_time_edges uses for calls of this
+ * shape (mode, E's bucket, K, S) on the current device, e.g. to restore a
+ * choice fn_autotune_time_edges made in an earlier process.  The N-ary
+ * refinement follows a FULL-mode choice of 0-2 (its default otherwise).
+ * Every variant's k* equals the oracle's up to the feasibility margin.
+ * Errors: FN_EINVAL for an unknown mode, a
+ * variant outside 0..3, E < 1, S out of range or (FULL) K out of range.
+ */
+fn_status fn_time_edges_set_variant(int mode, int E, int K, int S, int variant);
+
+/*
  * fn_rnea_dump -- torques of Eq. (torque) along each edge (diagnostic hook
  * for torque parity).  tau[e][s][j] = tau_j(t_s) of the cubic from s0[e] to
  * s1[e] with duration T[e], t_s = s T[e]/(S-1).

@@ -58,6 +58,16 @@ extern "C" fn_status fn_time_edges_counted(const fn_arm_t* arm, const float* s0,
                                            uint8_t* ok, unsigned long long* sample_count,
                                            void* stream);
 
+extern "C" fn_status fn_time_edges_set_variant(int mode, int E, int K, int S, int variant) {
+  if (mode != FN_MODE_FULL && mode != FN_MODE_FIXED) return FN_EINVAL;
+  if (variant < 0 || variant >= kTimeEdgeVariants) return FN_EINVAL;
+  if (E < 1 || S < 2 || S > FN_MAX_S) return FN_EINVAL;
+  if (mode == FN_MODE_FULL && (K < 1 || K > FN_MAX_GRID)) return FN_EINVAL;
+  const bool full = mode == FN_MODE_FULL;
+  set_tuned_variant(full ? TUNE_EDGES_FULL : TUNE_EDGES_FIXED, E, full ? K : 1, S, variant);
+  return FN_OK;
+}
+
 extern "C" fn_status fn_autotune_time_edges(const fn_arm_t* arm, const float* s0,
                                             const float* s1, int E, const float* T_grid, int K,
                                             int S, int mode, const float* T_fixed,

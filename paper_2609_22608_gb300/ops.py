@@ -14,7 +14,7 @@ import torch
 from . import _lib
 from ._lib import FN_MODE_FIXED, FN_MODE_FULL, arm_struct, check, lib
 
-__all__ = ["time_edges", "time_edges_nary", "autotune_time_edges", "check_edges_full",
+__all__ = ["time_edges", "time_edges_nary", "autotune_time_edges", "set_time_edges_variant", "check_edges_full",
            "controller_torque", "rnea_dump", "knn_tree", "knn_workspace_bytes", "make_edges", "EdgeEngine",
            "FN_MODE_FULL", "FN_MODE_FIXED", "version"]
 
@@ -99,6 +99,17 @@ def autotune_time_edges(arm, s0, s1, T_grid, S, reps=3, T_cap=None, stream=None)
                                       int(reps), C.byref(chosen), ms, _stream(stream))
     check(st, "fn_autotune_time_edges")
     return int(chosen.value), [float(x) for x in ms]
+
+
+def set_time_edges_variant(mode, E, K, S, variant):
+    """fn_time_edges_set_variant: pin the schedule variant (0-2 scalar
+    register budgets, 3 paired with tensor-memory records) that time_edges
+    uses for this shape on the current device."""
+    L = lib()
+    L.fn_time_edges_set_variant.argtypes = [C.c_int] * 5
+    L.fn_time_edges_set_variant.restype = C.c_int
+    check(L.fn_time_edges_set_variant(int(mode), int(E), int(K), int(S), int(variant)),
+          "fn_time_edges_set_variant")
 
 
 def time_edges_nary(arm, s0, s1, T_grid, S, eps, max_rounds=8, T_cap=None, out=None,

@@ -105,6 +105,10 @@ def test_fixed_mode(ops, orc, arm):
     rng = np.random.default_rng(9)
     T = rng.uniform(0.05, 2.0, 260).astype(np.float32)
     T[:4] = [0.0, -0.5, np.nan, np.inf]
+    _check_fixed(ops, orc, arm, s0, s1, T)
+
+
+def _check_fixed(ops, orc, arm, s0, s1, T):
     r = ops.time_edges(arm, dev(s0), dev(s1), None, 64, mode=ops.FN_MODE_FIXED, T_fixed=dev(T))
     ref = orc.time_edges(arm, s0, s1, synth.duration_grid(2), 64, mode=1, T_fixed=T)
     k = r["k_star"].cpu().numpy()
@@ -119,6 +123,65 @@ def test_fixed_mode(ops, orc, arm):
     clear = valid & (np.abs(m - 1) > 1e-4) & (np.abs(ref["rho3"][:, 2] - 1) > 1e-3)
     assert np.array_equal(k[clear], ref["k_star"][clear])
     assert np.array_equal(r["ok"].cpu().numpy()[clear], ref["ok"][clear])
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_every_schedule_variant(ops, orc, arm, variant):
+    """Each compiled schedule of fn_time_edges, pinned for the shape (0-2: one
+    sample per lane at three register budgets; 3: two samples per lane with
+    the recursion's records in tensor memory): FULL mode with a cap and FIXED
+    mode against the oracle."""
+    E, K, S = 300, 128, 64
+    s0, s1 = synth.random_edges(arm, E, 300 + variant)
+    rng = np.random.default_rng(300 + variant)
+    cap = rng.uniform(0.3, 2.5, E).astype(np.float32)
+    T = rng.uniform(0.05, 2.0, E).astype(np.float32)
+    T[:4] = [0.0, -0.5, np.nan, np.inf]
+    try:
+        ops.set_time_edges_variant(ops.FN_MODE_FULL, E, K, S, variant)
+        ops.set_time_edges_variant(ops.FN_MODE_FIXED, E, 1, S, variant)
+        _check_full(ops, orc, arm, s0, s1, synth.duration_grid(K), S, T_cap=cap)
+        _check_fixed(ops, orc, arm, s0, s1, T)
+    finally:
+        ops.set_time_edges_variant(ops.FN_MODE_FULL, E, K, S, 3)
+        ops.set_time_edges_variant(ops.FN_MODE_FIXED, E, 1, S, 3)
+
+
+def test_scalar_variants_identical(ops, arm):
+    """Variants 0-2 differ only in their register budget: bit-identical outputs."""
+    E, K, S = 500, 128, 64
+    s0, s1 = synth.random_edges(arm, E, 77)
+    grid = synth.duration_grid(K)
+    outs = []
+    try:
+        for v in (0, 1, 2):
+            ops.set_time_edges_variant(ops.FN_MODE_FULL, E, K, S, v)
+            r = ops.time_edges(arm, dev(s0), dev(s1), grid, S)
+            outs.append({k: t.cpu().numpy() for k, t in r.items()})
+    finally:
+        ops.set_time_edges_variant(ops.FN_MODE_FULL, E, K, S, 3)
+    for o in outs[1:]:
+        for k in o:
+            assert np.array_equal(o[k], outs[0][k], equal_nan=True), k
+
+
+def test_autotune_time_edges(ops, orc, arm):
+    """The tuner times the four schedules and keeps one; later calls of the
+    shape use it, and its results match the oracle."""
+    E, K, S = 400, 128, 64
+    s0, s1 = synth.random_edges(arm, E, 91)
+    grid = synth.duration_grid(K)
+    try:
+        chosen, ms = ops.autotune_time_edges(arm, dev(s0), dev(s1), grid, S, reps=1)
+        assert 0 <= chosen < 4 and len(ms) == 4 and all(m > 0 for m in ms)
+        assert ms[chosen] == min(ms)
+        _check_full(ops, orc, arm, s0, s1, grid, S)
+    finally:
+        ops.set_time_edges_variant(ops.FN_MODE_FULL, E, K, S, 3)
+    for bad in ((ops.FN_MODE_FULL, E, K, S, 4), (ops.FN_MODE_FULL, E, K, S, -1),
+                (7, E, K, S, 0), (ops.FN_MODE_FULL, 0, K, S, 0), (ops.FN_MODE_FULL, E, 0, S, 0)):
+        with pytest.raises(Exception):
+            ops.set_time_edges_variant(*bad)
 
 
 def test_invalid_edges_and_arguments(ops, orc, arm):
