@@ -71,10 +71,14 @@ __global__ void __launch_bounds__(32 * EDGE_WARPS, MINB)
 // The paired scan (two samples per lane, PairCore) with the per-link records
 // of the torque evaluation in tensor memory: one CTA of TM_WARPS = 12 warps
 // per SM holds all 512 columns; warp w uses lane quarter w % 4 and the
-// 144-column block 144 (w / 4) (three warps per quarter).  A warp takes its
-// edges TM_GROUP at a time: it stages them, computes their end-sample splits
-// in one pass (split_group: sixty (edge, end, part) items on the lanes'
-// two halves), then scans them one by one.  The coefficients, staged edges,
+// 144-column block 144 (w / 4) (three warps per quarter).  CTA b owns a
+// contiguous range of the edges, which its warps claim from a shared counter
+// in runs of up to TM_GROUP, shorter towards the end (a run is the range
+// left over twice the CTA's warps, at least two edges): an edge's cost
+// varies with the passes it needs, and shrinking runs keep the warps busy
+// until the range is done.  A warp stages its run, computes the end-sample
+// splits in one pass (split_group: up to sixty (edge, end, part) items on
+// the lanes' two halves), then scans the edges one by one.  The coefficients, staged edges,
 // splits, the paired link table and the grid sit in dynamic shared memory,
 // sized above half of the SM's so that no second CTA (which would wait for
 // the columns) is placed on the SM.
@@ -86,7 +90,7 @@ constexpr size_t kTmEdge = (size_t)TM_WARPS * TM_GROUP * 32 * sizeof(float);
 constexpr size_t kTmSplit = (size_t)TM_WARPS * TM_GROUP * FN_SPLIT_WORDS * sizeof(float);
 constexpr size_t kTmLink = 7 * FN_LINK2_F4 * sizeof(float4);
 constexpr size_t kTmGrid = FN_MAX_GRID * sizeof(float);
-constexpr size_t kTmUsed = kTmCoef + kTmEdge + kTmSplit + kTmLink + kTmGrid + 16;
+constexpr size_t kTmUsed = kTmCoef + kTmEdge + kTmSplit + kTmLink + kTmGrid + 16;   // + s_tmem, s_next
 constexpr size_t kTmSmem = 140 * 1024;
 static_assert(kTmUsed <= kTmSmem, "tensor-memory scan: shared-memory layout");
 static_assert(2 * (kTmSmem + 1024) > 233472, "one CTA per SM");
@@ -110,8 +114,12 @@ __global__ void __launch_bounds__(32 * TM_WARPS, 1)
   float* sT = reinterpret_cast<float*>(base + kTmCoef + kTmEdge + kTmSplit + kTmLink);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(base + kTmCoef + kTmEdge + kTmSplit + kTmLink +
                                                  kTmGrid);
+  int* s_next = reinterpret_cast<int*>(s_tmem + 1);   // next unclaimed edge of the CTA's range
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   fill_links2(A, sLink);
+  const long per = ((long)E + gridDim.x - 1) / gridDim.x;
+  const long r_lo = std::min<long>((long)blockIdx.x * per, E), r_hi = std::min<long>(r_lo + per, E);
+  if (threadIdx.x == 0) *s_next = 0;
   if (mode == FN_MODE_FULL)
     for (int i = threadIdx.x; i < K; i += blockDim.x) sT[i] = G.T[i];
   if (w == 0) tmem_alloc(s_tmem, kTmCols);
@@ -123,19 +131,26 @@ __global__ void __launch_bounds__(32 * TM_WARPS, 1)
   float* es_g = sEdge + TM_GROUP * 32 * w;
   float* split_g = sSplit + TM_GROUP * FN_SPLIT_WORDS * w;
   const bool fixed = mode == FN_MODE_FIXED;
-  const long W = (long)gridDim.x * TM_WARPS;
+  const int len = (int)(r_hi - r_lo);
   unsigned nsamp = 0;
-  // the warp's edges e0, e0 + W, e0 + 2 W, ..., TM_GROUP at a time
-  for (long e0 = (long)blockIdx.x * TM_WARPS + w; e0 < E; e0 += W * TM_GROUP) {
-    int n = 0;
-    unsigned fin = 0u;
-    for (; n < TM_GROUP && e0 + n * W < E; ++n) {
-      const long e = e0 + n * W;
-      if (stage_rows(s0 + 16 * e, s1 + 16 * e, es_g + 32 * n)) fin |= 1u << n;
+  for (;;) {
+    int first = 0, n = 0;
+    if (lane == 0) {   // claim a run: about (range left) / (2 TM_WARPS), 2..TM_GROUP edges
+      const int seen = atomicAdd(s_next, 0);
+      const int want = std::min(TM_GROUP, std::max(2, (len - seen) / (2 * TM_WARPS)));
+      first = atomicAdd(s_next, want);
+      n = std::max(0, std::min(want, len - first));
     }
+    first = __shfl_sync(0xffffffffu, first, 0);
+    n = __shfl_sync(0xffffffffu, n, 0);
+    if (n == 0) break;                               // warp-uniform
+    const long e0 = r_lo + first;
+    unsigned fin = 0u;
+    for (int i = 0; i < n; ++i)
+      if (stage_rows(s0 + 16 * (e0 + i), s1 + 16 * (e0 + i), es_g + 32 * i)) fin |= 1u << i;
     if (!fixed) split_group(A, core, es_g, split_g, n, nsamp);
     for (int i = 0; i < n; ++i) {
-      const long e = e0 + i * W;
+      const long e = e0 + i;
       const float Tp = Tparam ? __ldg(Tparam + e) : INFINITY;
       const EdgeResult r = time_edge(A, core, es_g + 32 * i, split_g + FN_SPLIT_WORDS * i,
                                      ((fin >> i) & 1u) != 0u, fixed, Tp, sT, K, S, true, nsamp);
