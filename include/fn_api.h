@@ -509,6 +509,26 @@ fn_status fn_planner_capture(fn_planner_t* pl, unsigned flags, void* stream);
 fn_status fn_plan_replay(fn_planner_t* pl, const fn_problem_t* probs, int iter,
                          fn_rendezvous_t* out, void* stream);
 
+/*
+ * fn_plan_replay_async -- fn_plan_replay without waiting: stages `probs` and
+ * `iter` and launches the captured graph on `stream`, then returns; the
+ * rendezvous records are read with fn_plan_result.  The staging is pinned
+ * host memory that the graph's own copies read, so a call waits (on the host)
+ * for the previous asynchronous replay's graph to finish before staging
+ * again; fn_plan_iteration, fn_plan_replay and fn_planner_reset do the same.
+ * Everything else is as fn_plan_replay (Algorithm 1's loop body, one
+ * iteration per call).  Errors as fn_plan_replay.
+ */
+fn_status fn_plan_replay_async(fn_planner_t* pl, const fn_problem_t* probs, int iter,
+                               void* stream);
+
+/*
+ * fn_plan_result -- wait for the last fn_plan_replay_async and copy its
+ * rendezvous records (host [P]) to `out`.  FN_EINVAL if no asynchronous
+ * replay was launched on this planner.
+ */
+fn_status fn_plan_result(fn_planner_t* pl, fn_rendezvous_t* out);
+
 /* Schedule autotuner of the planner (the work pattern of an iteration is
  * data dependent, so variants are timed on the caller's own problems): runs
  * the iteration's sampling and parent search once, then times every compiled

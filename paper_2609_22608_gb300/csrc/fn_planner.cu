@@ -2169,6 +2169,8 @@ struct fn_planner {
   fn_problem_t* h_prob = nullptr;      // pinned staging
   fn_rendezvous_t* h_out = nullptr;    // pinned
   int* h_iter = nullptr;               // pinned
+  cudaEvent_t replay_done = nullptr;   // the last asynchronous replay (its staging and output)
+  bool replay_pending = false;         // an asynchronous replay may still read the staging
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   unsigned graph_flags = 0;
@@ -2434,6 +2436,10 @@ extern "C" fn_status fn_planner_destroy(fn_planner_t* pl) {
   if (pl->graph_exec) cudaGraphExecDestroy(pl->graph_exec);
   if (pl->graph) cudaGraphDestroy(pl->graph);
   for (void* p : pl->allocs) cudaFree(p);
+  if (pl->replay_done) {
+    cudaEventSynchronize(pl->replay_done);
+    cudaEventDestroy(pl->replay_done);
+  }
   if (pl->h_prob) cudaFreeHost(pl->h_prob);
   if (pl->h_out) cudaFreeHost(pl->h_out);
   if (pl->h_iter) cudaFreeHost(pl->h_iter);
@@ -2569,6 +2575,8 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
   return FN_OK;
 }
 
+static fn_status wait_staging(fn_planner* pl);
+
 static fn_status stage_problems(fn_planner* pl, const fn_problem_t* probs, cudaStream_t st) {
   for (int p = 0; p < pl->cfg.P; ++p) {
     const fn_problem_t& q = probs[p];
@@ -2576,6 +2584,8 @@ static fn_status stage_problems(fn_planner* pl, const fn_problem_t* probs, cudaS
         q.n_obs < 0 || q.n_obs > FN_MAX_OBS || !(q.t_fall >= q.t_enter) || !(q.v_tip > 0.f))
       return FN_EINVAL;
   }
+  const fn_status rc = wait_staging(pl);
+  if (rc != FN_OK) return rc;
   memcpy(pl->h_prob, probs, sizeof(fn_problem_t) * pl->cfg.P);
   if (cudaMemcpyAsync(pl->D.prob, pl->h_prob, sizeof(fn_problem_t) * pl->cfg.P,
                       cudaMemcpyHostToDevice, st) != cudaSuccess)
@@ -2777,16 +2787,60 @@ extern "C" fn_status fn_planner_capture(fn_planner_t* pl, unsigned flags, void* 
   return FN_OK;
 }
 
-extern "C" fn_status fn_plan_replay(fn_planner_t* pl, const fn_problem_t* probs, int iter,
-                                    fn_rendezvous_t* out, void* stream) {
-  if (!pl || !probs || !out || !pl->graph_exec) return FN_EINVAL;
-  cudaStream_t st = (cudaStream_t)stream;
+// the pinned staging is read by the copies of an asynchronous replay still
+// in flight: wait for it before writing the staging again
+static fn_status wait_staging(fn_planner* pl) {
+  if (!pl->replay_pending) return FN_OK;
+  if (cudaEventSynchronize(pl->replay_done) != cudaSuccess) return FN_ECUDA;
+  pl->replay_pending = false;
+  return FN_OK;
+}
+
+static bool replay_probs_ok(const fn_planner* pl, const fn_problem_t* probs) {
   for (int p = 0; p < pl->cfg.P; ++p) {
     const fn_problem_t& q = probs[p];
     if (q.batch < 0 || q.batch > pl->cfg.b_max || q.n_goal < 0 || q.n_goal > q.batch ||
         q.n_obs < 0 || q.n_obs > FN_MAX_OBS)
-      return FN_EINVAL;
+      return false;
   }
+  return true;
+}
+
+extern "C" fn_status fn_plan_replay_async(fn_planner_t* pl, const fn_problem_t* probs, int iter,
+                                          void* stream) {
+  if (!pl || !probs || !pl->graph_exec) return FN_EINVAL;
+  if (!replay_probs_ok(pl, probs)) return FN_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!pl->replay_done &&
+      cudaEventCreateWithFlags(&pl->replay_done, cudaEventDisableTiming) != cudaSuccess) {
+    pl->replay_done = nullptr;
+    return FN_ECUDA;
+  }
+  fn_status rc = wait_staging(pl);
+  if (rc != FN_OK) return rc;
+  memcpy(pl->h_prob, probs, sizeof(fn_problem_t) * pl->cfg.P);
+  *pl->h_iter = iter;
+  if (cudaGraphLaunch(pl->graph_exec, st) != cudaSuccess) return FN_ECUDA;
+  if (cudaEventRecord(pl->replay_done, st) != cudaSuccess) return FN_ECUDA;
+  pl->replay_pending = true;
+  return FN_OK;
+}
+
+extern "C" fn_status fn_plan_result(fn_planner_t* pl, fn_rendezvous_t* out) {
+  if (!pl || !out || !pl->replay_done) return FN_EINVAL;
+  if (cudaEventSynchronize(pl->replay_done) != cudaSuccess) return FN_ECUDA;
+  pl->replay_pending = false;
+  memcpy(out, pl->h_out, sizeof(fn_rendezvous_t) * pl->cfg.P);
+  return FN_OK;
+}
+
+extern "C" fn_status fn_plan_replay(fn_planner_t* pl, const fn_problem_t* probs, int iter,
+                                    fn_rendezvous_t* out, void* stream) {
+  if (!pl || !probs || !out || !pl->graph_exec) return FN_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!replay_probs_ok(pl, probs)) return FN_EINVAL;
+  fn_status rc = wait_staging(pl);
+  if (rc != FN_OK) return rc;
   memcpy(pl->h_prob, probs, sizeof(fn_problem_t) * pl->cfg.P);
   *pl->h_iter = iter;
   if (cudaGraphLaunch(pl->graph_exec, st) != cudaSuccess) return FN_ECUDA;

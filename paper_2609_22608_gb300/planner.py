@@ -96,6 +96,8 @@ def _bind():
     L.fn_plan_iteration.argtypes = [vp, vp, i32, C.c_uint, vp, vp]
     L.fn_planner_capture.argtypes = [vp, C.c_uint, vp]
     L.fn_plan_replay.argtypes = [vp, vp, i32, vp, vp]
+    L.fn_plan_replay_async.argtypes = [vp, vp, i32, vp]
+    L.fn_plan_result.argtypes = [vp, vp]
     L.fn_planner_get_tree.argtypes = [vp, i32, vp, vp, vp, vp, vp, C.POINTER(C.c_int), i32]
     L.fn_planner_get_candidates.argtypes = [vp, i32, vp, vp, vp, vp, i32]
     L.fn_planner_get_parents.argtypes = [vp, i32, vp, i32]
@@ -118,7 +120,7 @@ def _bind():
     L.fn_planner_set_grefine.argtypes = [vp, i32, C.c_float, C.c_float]
     for n in ("fn_planner_create", "fn_planner_destroy", "fn_planner_reset", "fn_planner_load_tree",
               "fn_planner_set_candidates", "fn_plan_iteration", "fn_planner_capture",
-              "fn_plan_replay", "fn_planner_get_tree", "fn_planner_get_candidates",
+              "fn_plan_replay", "fn_plan_replay_async", "fn_plan_result", "fn_planner_get_tree", "fn_planner_get_candidates",
               "fn_planner_get_parents", "fn_planner_get_edges", "fn_planner_get_node_params",
               "fn_planner_sample_count", "fn_planner_phase_ms", "fn_planner_autotune",
               "fn_planner_kernel_ms", "fn_planner_work_counts", "fn_planner_set_surrogate",
@@ -248,6 +250,18 @@ class Planner:
         self._stage(probs)
         check(lib().fn_plan_replay(self.h, self._probs, int(it), self._out, self._stream(stream)),
               "fn_plan_replay")
+        return [rendezvous_dict(self._out[i]) for i in range(self.P)]
+
+    def replay_async(self, probs, it=0, stream=None):
+        """fn_plan_replay_async: enqueue the captured graph and return; the
+        rendezvous records come from result()."""
+        self._stage(probs)
+        check(lib().fn_plan_replay_async(self.h, self._probs, int(it), self._stream(stream)),
+              "fn_plan_replay_async")
+
+    def result(self):
+        """fn_plan_result: wait for the last replay_async and return its records."""
+        check(lib().fn_plan_result(self.h, self._out), "fn_plan_result")
         return [rendezvous_dict(self._out[i]) for i in range(self.P)]
 
     def get_tree(self, p, cap=None):

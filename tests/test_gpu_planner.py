@@ -329,7 +329,7 @@ def test_graph_replay_matches_iteration(P, orc, arm):
     N = states.shape[0]
     B = 512
     res = []
-    for mode in ("iterate", "graph"):
+    for mode in ("iterate", "graph", "async"):
         pl = P.Planner(arm, P=2, n_cap=N + 4 * B, b_max=B, k=8, K=64, S=32)
         probs = [P.problem_struct(case["pr"], B, B // 2, root=case["root"], seed=11 + i)
                  for i in range(2)]
@@ -342,17 +342,33 @@ def test_graph_replay_matches_iteration(P, orc, arm):
             pl.capture(0, stream=s)
             for it in range(3):
                 outs.append(pl.replay(probs, it, stream=s))
+        elif mode == "async":
+            from paper_2609_22608_gb300._lib import FnError
+            with pytest.raises(FnError):
+                pl.result()                              # nothing launched yet
+            pl.capture(0, stream=s)
+            pl.replay_async(probs, 0, stream=s)
+            outs.append(pl.result())
+            pl.replay_async(probs, 1, stream=s)          # back to back: the second call
+            pl.replay_async(probs, 2, stream=s)          # waits for the first's staging
+            outs.append(None)
+            outs.append(pl.result())
         else:
             for it in range(3):
                 outs.append(pl.iterate(probs, it, 0, stream=s))
         res.append((outs, [pl.get_tree(p) for p in range(2)]))
         pl.close()
-    (o1, t1), (o2, t2) = res
-    for a, b in zip(o1, o2):
-        for x, y in zip(a, b):
-            assert x["n_nodes"] == y["n_nodes"] and x["incumbent"] == y["incumbent"]
-    for x, y in zip(t1, t2):
-        assert np.array_equal(x["states"], y["states"]) and np.array_equal(x["parent"], y["parent"])
+    (o1, t1) = res[0]
+    for o2, t2 in res[1:]:
+        for a, b in zip(o1, o2):
+            if b is None:
+                continue
+            for x, y in zip(a, b):
+                assert x["n_nodes"] == y["n_nodes"] and x["incumbent"] == y["incumbent"]
+                assert x["J"] == y["J"] or (np.isnan(x["J"]) and np.isnan(y["J"]))
+        for x, y in zip(t1, t2):
+            assert np.array_equal(x["states"], y["states"])
+            assert np.array_equal(x["parent"], y["parent"])
 
 
 def test_batched_uneven_problems(P, orc, arm):
