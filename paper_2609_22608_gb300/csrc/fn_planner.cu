@@ -189,6 +189,23 @@ __device__ __forceinline__ void pdl_wait() {
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
 }
 
+// A slot in a list that every thread appends to: the lanes of a warp that
+// call this together get consecutive slots from one atomic on the counter
+// (a single lane's atomic per entry would serialise at the L2 when tens of
+// thousands of entries arrive at once).  *n (if non-null) gets the group's
+// size on the group's first lane, for a counter kept beside the list.
+__device__ __forceinline__ int warp_append(int* counter, unsigned long long* n = nullptr) {
+  const unsigned m = __activemask();
+  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) {
+    base = atomicAdd(counter, __popc(m));
+    if (n) atomicAdd(n, (unsigned long long)__popc(m));
+  }
+  base = __shfl_sync(m, base, leader);
+  return base + __popc(m & ((1u << lane) - 1u));
+}
+
 struct GridKP {
   float T[FN_MAX_GRID];
 };
@@ -951,7 +968,7 @@ __global__ void __launch_bounds__(PL_SCAN) k_plan_eprep(PlanDev D, GridKP Gr) {
         }
         cnt = lo;
         if (D.sur && cnt > 0) {   // timed by the surrogate pass instead
-          const int slot = atomicAdd(D.sur_n, 1);
+          const int slot = warp_append(D.sur_n);
           if (slot < D.Emax) D.sur_list[slot] = e;
           cnt = 0;
           routed = true;
@@ -1007,31 +1024,81 @@ __device__ __forceinline__ int item_off(const PlanDev& D, int e) {
 
 // For every listed edge with probe items, one lane per (edge, end, part):
 // the item -> owning edge map (the edge's six lanes share its items) and the
-// end-sample torque split (end_torque_part): three torque evaluations per
-// end replace two per item.  Sized to the resident blocks.
-__global__ void __launch_bounds__(256) k_plan_expand(PlanDev D, ArmK A) {
+// end-sample torque split (end_torque_part's decomposition): three torque
+// evaluations per end replace two per item.  The evaluation is the rolled
+// recursion (torque_at_rolled) of a cubic whose u = 0 sample is the item's
+// (q, qd, qdd), with its coefficients and per-link records in the lane's
+// shared-memory columns: each lane evaluates Eq. (torque) about once, so
+// the one-link body, fetched once, replaces seven unrolled links the
+// instruction cache would fetch cold.  Warps loop in step (every lane of a
+// warp makes the same calls); sized to the resident blocks.
+#define PL_EXP_WARPS 3
+__global__ void __launch_bounds__(32 * PL_EXP_WARPS) k_plan_expand(PlanDev D, ArmK A) {
   pdl_begin();
+  __shared__ float sCoef[PL_EXP_WARPS][FN_CUBIC_WORDS * 32];
+  __shared__ float sWr[PL_EXP_WARPS][FN_LINK_WORDS * 32];
+  __shared__ float4 sLink[7 * FN_LINK_F4];
+  fill_links(A, sLink);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const CubicLane cb{&sCoef[w][lane]};
+  const LaneLink wr{&sWr[w][lane]};
+  const LinkTab L{sLink};
   const Sched* S = D.sched;
   const int E = S->n_edges;
   const int nd = min(S->n_dyn, E);
+  const long n = 6L * nd;
   unsigned nsamp = 0;
-  const long L = (long)gridDim.x * blockDim.x;
-  for (long x = (long)blockIdx.x * blockDim.x + threadIdx.x; x < 6L * nd; x += L) {
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long x0 = (long)blockIdx.x * blockDim.x + 32 * w; x0 < n; x0 += stride) {
+    const long x = x0 + lane;
+    const bool act = x < n;
     const int r = (int)(x % 6), end = r / 3, part = r - 3 * end;
-    const int e = D.dyn_list[x / 6];
-    const int o = item_off(D, e);
-    const int c = (e + 1 < E ? item_off(D, e + 1) : S->n_items) - o;
-    for (int t = r; t < c; t += 6) D.owner[o + t] = e;
-    const int p = D.e_ci[e] / D.BM;
-    const float4* r0 = reinterpret_cast<const float4*>(D.st + ((long)p * D.NC + D.e_par[e]) * 16);
-    const float4* r1 = reinterpret_cast<const float4*>(D.cand + (long)D.e_ci[e] * 16);
-    float q0[7], qd0[7], q1[7], qd1[7];
-    load_state(r0, q0, qd0);
-    load_state(r1, q1, qd1);
-    end_torque_part(A, q0, qd0, q1, qd1, end, part, D.edyn + (2L * e + end) * 28);
-    ++nsamp;
+    Cubic c;
+    float* out = nullptr;
+    c.iT = c.iT2 = 1.f;
+    if (act) {
+      const int e = D.dyn_list[x / 6];
+      const int o = item_off(D, e);
+      const int cnt = (e + 1 < E ? item_off(D, e + 1) : S->n_items) - o;
+      for (int t = r; t < cnt; t += 6) D.owner[o + t] = e;
+      const int p = D.e_ci[e] / D.BM;
+      const float4* r0 = reinterpret_cast<const float4*>(D.st + ((long)p * D.NC + D.e_par[e]) * 16);
+      const float4* r1 = reinterpret_cast<const float4*>(D.cand + (long)D.e_ci[e] * 16);
+      float q0[7], qd0[7], q1[7], qd1[7];
+      load_state(r0, q0, qd0);
+      load_state(r1, q1, qd1);
+      out = D.edyn + (2L * e + end) * 28;
+#pragma unroll
+      for (int j = 0; j < 7; ++j) {   // end_torque_part's (q, qd, qdd) as a cubic at u = 0
+        const float d = q1[j] - q0[j];
+        const float qa = end ? -6.0f * d : 6.0f * d;
+        const float qb = end ? fmaf(4.0f, qd1[j], 2.0f * qd0[j]) : -fmaf(4.0f, qd0[j], 2.0f * qd1[j]);
+        c.q0[j] = end ? q1[j] : q0[j];
+        c.b1[j] = part == 0 ? (end ? qd1[j] : qd0[j]) : 0.f;
+        c.b2[j] = 0.5f * (part == 0 ? 0.f : (part == 1 ? qa : qb));
+        c.b3[j] = 0.f;
+        if (part == 0) out[21 + j] = c.b1[j];   // the end velocity
+      }
+      ++nsamp;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 7; ++j) c.q0[j] = c.b1[j] = c.b2[j] = c.b3[j] = 0.f;
+    }
+    cb.store(c);
+    const float on = part == 0 ? 1.f : 0.f;   // parts 1, 2: M + I_m only
+    const int o = part == 0 ? 14 : 7 * (part - 1);
+    torque_at_rolled(
+        A, L, cb, 0.f,
+        [&](int j, float tau, float, float) {
+          if (act) out[o + j] = tau;
+        },
+        wr, on, on);
   }
-  if (D.samples && nsamp) atomicAdd(D.samples + 0, (unsigned long long)nsamp);
+  // one counter update per warp (tens of thousands of same-address atomics
+  // from single lanes would serialise at the L2)
+  const unsigned tot = __reduce_add_sync(0xffffffffu, nsamp);
+  if (D.samples && lane == 0 && tot) atomicAdd(D.samples + 0, (unsigned long long)tot);
 }
 
 static int expand_blocks() {
@@ -1041,8 +1108,8 @@ static int expand_blocks() {
   if (dev < 0 || dev >= 64) dev = 0;
   if (blocks[dev] == 0) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_plan_expand, 256, 0) !=
-            cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_plan_expand, 32 * PL_EXP_WARPS,
+                                                      0) != cudaSuccess ||
         per_sm < 1)
       per_sm = 1;
     blocks[dev] = per_sm * num_sms();
@@ -1101,7 +1168,10 @@ __global__ void __launch_bounds__(32 * PL_EDGE_WARPS, MINB) k_plan_probe(PlanDev
     if (lane == 0 && pm) slot0 = atomicAdd(&D.sched->n_surv, __popc(pm));
     slot0 = __shfl_sync(0xffffffffu, slot0, 0);
     if (pass) {
-      atomicOr(&D.mask[8L * e + (k >> 5)], 1u << (k & 31));
+      // one atomic per mask word among the warp's passing lanes
+      const unsigned grp = __match_any_sync(pm, (unsigned long long)(8L * e + (k >> 5)));
+      const unsigned bits = __reduce_or_sync(grp, 1u << (k & 31));
+      if (lane == __ffs(grp) - 1) atomicOr(&D.mask[8L * e + (k >> 5)], bits);
       const int slot = slot0 + __popc(pm & ((1u << lane) - 1u));
       if (slot < D.surv_cap) D.surv[slot] = make_int2(e, k);
     }
@@ -1196,7 +1266,7 @@ __global__ void k_plan_vinit(PlanDev D) {
       continue;
     }
     D.cur_k[e] = k;
-    D.pend[atomicAdd(&S->n_pend[0], 1)] = e;
+    D.pend[warp_append(&S->n_pend[0])] = e;
   }
 }
 
@@ -1332,7 +1402,7 @@ __global__ void __launch_bounds__(128) k_plan_vselect(PlanDev D, ArmK A, GridKP 
       continue;
     }
     D.cur_k[e] = k2;
-    next[atomicAdd(&S->n_pend[list ^ 1], 1)] = e;
+    next[warp_append(&S->n_pend[list ^ 1])] = e;
   }
 }
 
@@ -2394,7 +2464,7 @@ static void enqueue_edge_body(fn_planner* pl, const PlanDev& D, int v, int block
     pl_launch(k_plan_escan, 1, PL_SCAN, 0, st, D);
     trace(pl, st, "k_plan_escan");
   }
-  pl_launch(k_plan_expand, expand_blocks(), 256, 0, st, D, pl->arm);
+  pl_launch(k_plan_expand, expand_blocks(), 32 * PL_EXP_WARPS, 0, st, D, pl->arm);
   trace(pl, st, "k_plan_expand");
   mark(4);
   pl_launch(plan_probe_variant(v), blocks, 32 * PL_EDGE_WARPS, 0, st, D, pl->arm, pl->grid);
@@ -3221,10 +3291,7 @@ __global__ void k_edges_cert(PlanDev D, int E, int W, const int2* __restrict__ w
       else cert = klo < khi && khi == Kadm;
     }
     if (path) path[e] = cert ? 0 : 1;
-    if (!cert) {
-      list[atomicAdd(n_list, 1)] = e;
-      if (D.samples) atomicAdd(D.samples + 6, 1ull);
-    }
+    if (!cert) list[warp_append(n_list, D.samples ? D.samples + 6 : nullptr)] = e;
   }
 }
 
