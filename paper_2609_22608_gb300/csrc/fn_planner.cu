@@ -126,6 +126,12 @@ struct PlanDev {  // device pointers, passed by value to the kernels
   Sched* sched;
   fn_rendezvous_t* out;  // [P]
   int* iter;
+  // mapped pinned host memory: the staged problems and iteration number
+  // (read by k_plan_schedule) and the rendezvous records (written by the
+  // kernel that finishes them), so a replay needs no copy nodes
+  const fn_problem_t* hprob;
+  const int* hiter;
+  fn_rendezvous_t* hout;
   int32_t* added;     // [P]
   int32_t* status;    // [P]
   // prune scratch
@@ -258,8 +264,18 @@ __global__ void k_plan_loaded(PlanDev D, int p, int n) {
 // ---------------------------------------------------------------------------
 // schedule: per-problem offsets of every flattened work list
 // ---------------------------------------------------------------------------
+static_assert(sizeof(fn_problem_t) % 16 == 0, "problems copied in 16-byte words");
+
 __global__ void k_plan_schedule(PlanDev D) {
   pdl_begin();
+  {   // the staged problems and iteration number, from mapped host memory
+    const int nw = D.P * (int)(sizeof(fn_problem_t) / 16);
+    const uint4* src = reinterpret_cast<const uint4*>(D.hprob);
+    uint4* dst = reinterpret_cast<uint4*>(D.prob);
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = __ldcv(src + i);
+    if (threadIdx.x == 0) *D.iter = __ldcv(D.hiter);
+  }
+  __syncthreads();
   if (threadIdx.x != 0) return;
   Sched* S = D.sched;
   // free queries over all problems: with fewer query groups than resident
@@ -1654,6 +1670,7 @@ __device__ void write_rendezvous(const PlanDev& D, int p) {
     o.T = NAN;
   }
   D.out[p] = o;
+  if (D.hout) D.hout[p] = o;
 }
 
 // with `output`, thread 0 also writes the problem's record (k_plan_output
@@ -1673,11 +1690,17 @@ __global__ void __launch_bounds__(PL_ATTACH_THREADS) k_plan_attach(PlanDev D, in
   const int per = (B + blockDim.x - 1) / blockDim.x;
   const int c0 = threadIdx.x * per, c1 = min(B, c0 + per);
   // pass 1: count attachable candidates of this thread's contiguous chunk
+  // (the flags of a candidate's edges are loaded together, no early exit)
   int cnt = 0;
   for (int b = c0; b < c1; ++b) {
     const long ci = (long)p * D.BM + b;
-    for (int j = 0; j < D.KP; ++j)
-      if (D.e_ok[ci * D.KP + j]) { ++cnt; break; }
+    int any = 0;
+    for (int j0 = 0; j0 < D.KP; j0 += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (j0 + u < D.KP) any |= D.e_ok[ci * D.KP + j0 + u];
+    }
+    cnt += any != 0;
   }
   int total;
   const int base = block_scan(cnt, sh, &total);
@@ -1690,12 +1713,25 @@ __global__ void __launch_bounds__(PL_ATTACH_THREADS) k_plan_attach(PlanDev D, in
     const long ci = (long)p * D.BM + b;
     int bj = -1, bpar = -1;
     float bt = INFINITY;
-    for (int j = 0; j < D.KP; ++j) {
-      const long ei = ci * D.KP + j;
-      if (!D.e_ok[ei]) continue;
-      const int pr = j == 0 ? 0 : D.nn[ci * D.KN + (j - 1)];
-      const float tt = __fadd_rn(D.t[nb + pr], D.e_T[ei]);
-      if (tt < bt) { bt = tt; bj = j; bpar = pr; }
+    for (int j0 = 0; j0 < D.KP; j0 += 8) {   // eight edges' loads in flight at once
+      bool ok[8];
+      int pr[8];
+      float te[8], tp[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = j0 + u;
+        const long ei = ci * D.KP + j;
+        ok[u] = j < D.KP && D.e_ok[ei];
+        pr[u] = j == 0 ? 0 : (ok[u] ? D.nn[ci * D.KN + (j - 1)] : 0);
+        te[u] = ok[u] ? D.e_T[ei] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) tp[u] = ok[u] ? D.t[nb + pr[u]] : 0.f;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float tt = __fadd_rn(tp[u], te[u]);
+        if (ok[u] && tt < bt) { bt = tt; bj = j0 + u; bpar = pr[u]; }
+      }
     }
     if (bj < 0) continue;
     const int node = N0 + r;
@@ -2617,10 +2653,15 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
   if (rc == FN_OK && cudaMemset(D.packed, 0, sizeof(int32_t) * P) != cudaSuccess) rc = FN_ECUDA;
 #undef A_
   if (rc == FN_OK) {
-    if (cudaMallocHost(&pl->h_prob, P * sizeof(fn_problem_t)) != cudaSuccess ||
-        cudaMallocHost(&pl->h_out, P * sizeof(fn_rendezvous_t)) != cudaSuccess ||
-        cudaMallocHost(&pl->h_iter, sizeof(int)) != cudaSuccess)
+    if (cudaHostAlloc(&pl->h_prob, P * sizeof(fn_problem_t), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostAlloc(&pl->h_out, P * sizeof(fn_rendezvous_t), cudaHostAllocMapped) !=
+            cudaSuccess ||
+        cudaHostAlloc(&pl->h_iter, sizeof(int), cudaHostAllocMapped) != cudaSuccess)
       rc = FN_ENOMEM;
+    else if (cudaHostGetDevicePointer((void**)&D.hprob, pl->h_prob, 0) != cudaSuccess ||
+             cudaHostGetDevicePointer((void**)&D.hout, pl->h_out, 0) != cudaSuccess ||
+             cudaHostGetDevicePointer((void**)&D.hiter, pl->h_iter, 0) != cudaSuccess)
+      rc = FN_ECUDA;
   }
   if (rc == FN_OK && (cudaMemset(D.n_nodes, 0, P * sizeof(int)) != cudaSuccess ||
                       cudaMemset(D.samples, 0, PL_NCOUNT * sizeof(unsigned long long)) != cudaSuccess))
@@ -2746,7 +2787,7 @@ static fn_status enqueue_iteration(fn_planner* pl, unsigned flags, cudaStream_t 
   pl->tracing = timed;
   pl->nk = 0;
   if (timed) cudaEventRecord(pl->kev[0], st);
-  k_plan_schedule<<<1, 32, 0, st>>>(D);
+  k_plan_schedule<<<1, 256, 0, st>>>(D);
   trace(pl, st, "k_plan_schedule");
   mark(1);
   enqueue_front(pl, flags, st, mark);
@@ -2786,9 +2827,6 @@ static fn_status enqueue_iteration(fn_planner* pl, unsigned flags, cudaStream_t 
   }
   pl->tracing = false;
   mark(9);
-  if (cudaMemcpyAsync(pl->h_out, D.out, sizeof(fn_rendezvous_t) * P, cudaMemcpyDeviceToHost, st) !=
-      cudaSuccess)
-    return FN_ECUDA;
   return launch_status();
 }
 
@@ -2840,10 +2878,8 @@ extern "C" fn_status fn_planner_capture(fn_planner_t* pl, unsigned flags, void* 
   if (pl->graph_exec) { cudaGraphExecDestroy(pl->graph_exec); pl->graph_exec = nullptr; }
   if (pl->graph) { cudaGraphDestroy(pl->graph); pl->graph = nullptr; }
   if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return FN_ECUDA;
-  // the staged problems and iteration counter are copied inside the graph
-  cudaMemcpyAsync(pl->D.prob, pl->h_prob, sizeof(fn_problem_t) * pl->cfg.P, cudaMemcpyHostToDevice,
-                  st);
-  cudaMemcpyAsync(pl->D.iter, pl->h_iter, sizeof(int), cudaMemcpyHostToDevice, st);
+  // the staged problems and iteration counter are read by the graph's first
+  // kernel from mapped host memory; the rendezvous goes back the same way
   fn_status rc = enqueue_iteration(pl, flags, st, false);
   cudaGraph_t g = nullptr;
   if (cudaStreamEndCapture(st, &g) != cudaSuccess || rc != FN_OK) {
@@ -3149,7 +3185,7 @@ extern "C" fn_status fn_planner_autotune(fn_planner_t* pl, const fn_problem_t* p
       cudaSuccess)
     return FN_ECUDA;
   PlanDev& D = pl->D;
-  k_plan_schedule<<<1, 32, 0, st>>>(D);
+  k_plan_schedule<<<1, 256, 0, st>>>(D);
   enqueue_front(pl, flags, st, [](int) {});
   if ((rc = launch_status()) != FN_OK) return rc;
   float best_ms = INFINITY;
