@@ -54,7 +54,7 @@
 #define PL_NCOUNT 14  // work counters: probe, verify, mid-probe, kNN pairs, IK starts,
                       // surrogate-routed edges, surrogate rescans, refine evaluations,
                       // goal draws by outcome (defined, speed, IK, box, singular, taper)
-#define PL_CHORD_THREADS 1024  // block_scan spans 32 warps
+#define PL_CHORD_THREADS 1024
 
 namespace fn {
 
@@ -151,7 +151,7 @@ struct PlanDev {  // device pointers, passed by value to the kernels
   uint8_t* e_j;       // [E] parent slot | 0x80 for goal edges
   int32_t* e_cnt;     // [E] probe items; then local exclusive offsets
   int32_t* e_klo;     // [E] grid index of the edge's first probe item
-  int32_t* blk_off;   // [ceil(E/1024)] block offsets of the item scan
+  int32_t* blk_off;   // [ceil(E/PL_SCAN)] block offsets of the item scan
   uint32_t* mask;     // [E][8] surviving grid indices of the probe
   int32_t* owner;     // [E*K] probe item -> edge
   int32_t* cur_k;     // [E] duration under verification (grid index; 0 for goals)
@@ -867,9 +867,9 @@ __device__ __forceinline__ void parents_prep(const PlanDev& D, long i, long stri
 // packed edge phase: prep -> item scan -> probe (lanes = (edge, duration)
 // items) -> verify (warp per edge, lanes = samples)
 // ---------------------------------------------------------------------------
-#define PL_SCAN 1024
+#define PL_SCAN 256
 
-// exclusive prefix sum over a block of PL_SCAN threads (shuffles within the
+// exclusive prefix sum over a block of whole warps, at most 32 (shuffles within the
 // warps, one shared pass across them); *total = the block's sum
 __device__ __forceinline__ int block_scan(int v, int* sh, int* total) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -882,8 +882,9 @@ __device__ __forceinline__ int block_scan(int v, int* sh, int* total) {
   __syncthreads();
   if (lane == 31) sh[w] = x;
   __syncthreads();
+  const int nw = blockDim.x >> 5;   // whole warps, at most 32
   if (w == 0) {
-    int t = sh[lane];
+    int t = lane < nw ? sh[lane] : 0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, t, o);
@@ -892,7 +893,7 @@ __device__ __forceinline__ int block_scan(int v, int* sh, int* total) {
     sh[lane] = t;
   }
   __syncthreads();
-  *total = sh[31];
+  *total = sh[nw - 1];
   const int ex = (w > 0 ? sh[w - 1] : 0) + x - v;
   __syncthreads();   // sh may be reused as soon as this returns
   return ex;
