@@ -1040,6 +1040,10 @@ def _anytime_run(arm, pr, prob, flags, cycles=200):
         status |= out["status"]
         formed.append(int(pl.get_candidates(0, 8192)["valid"].sum()) * 16)
     clk.__exit__()
+    # one traced (un-timed) cycle on the final tree: the duration of every launch
+    pl.iterate([prob], cycles, flags, stream=stream)
+    torch.cuda.synchronize()
+    kernels = kernel_table(pl.kernel_ms())
     pl.close()
     ms = np.array(ms)
     nodes = np.array(nodes)
@@ -1050,6 +1054,7 @@ def _anytime_run(arm, pr, prob, flags, cycles=200):
             bins[f"{lo}-{hi - 1}"] = {"cycles": int(sel.sum()), "ms_mean": float(ms[sel].mean()),
                                       "p99_ms": float(np.percentile(ms[sel], 99))}
     return dict(ms=ms, nodes=nodes, added=np.array(added), formed=np.array(formed), out=out,
+                kernels=kernels,
                 clocks=clk.summary(), bins=bins, tuned=tuned, status=status)
 
 
@@ -1092,6 +1097,9 @@ def run_anytime(args):
         "tree_nodes": {"final": int(paper["nodes"][-1]), "max": int(paper["nodes"].max()),
                        "added_mean": float(paper["added"].mean())},
         "p99_by_tree_size": paper["bins"],
+        "kernels_ms_final_tree": paper["kernels"],
+        "kernels_note": "one traced (un-timed) cycle on the final tree, an event after every "
+                        "launch (serialised)",
         "status_bits": paper["status"],
         "incumbent_J": out["J"], "t_best": out["t_best"],
         "uniform_sampler": {"ms_per_step": float(np.mean(uni["ms"])),

@@ -80,6 +80,7 @@ struct Sched {
   int n_surv;         // probe survivors appended (may exceed surv_cap)
   int n_dyn;          // edges with probe items listed by the prep (zero between bodies)
   unsigned prep_done; // blocks of k_plan_eprep finished (zero between iterations)
+  unsigned prune_done;  // blocks of k_prune_walk finished (zero between iterations)
   int n_free_edges;   // free edges of all problems (the queue's first part)
   int n_edges;        // all edges
   // parent-search items (problem, query group, split), one per warp, in two
@@ -141,6 +142,10 @@ struct PlanDev {  // device pointers, passed by value to the kernels
   float* tmp_st;      // [P][NC][16]
   float* tmp_f;       // [P][NC][4]  (t, J, nu, eT)
   int32_t* tmp_par;   // [P][NC]
+  float* tmp_z;       // [P][NC][9]  (chart parameters)
+  int32_t* prune_blk; // [P][ceil(NC/PL_PRUNE_T)] kept nodes per chunk, then their offsets
+  int32_t* prune_tot; // [P] nodes kept
+  int32_t* prune_deep;  // [P] a parent chain longer than PL_PRUNE_WALK: single-block prune
   unsigned long long* samples;  // work counters: torque evaluations [0] probe, [1] verify,
                                 // [2] mid-probe; [3] kNN (query, node) pairs; [4] IK starts;
                                 // [5] edges timed by the surrogate pass, [6] of them rescanned
@@ -868,6 +873,7 @@ __device__ __forceinline__ void parents_prep(const PlanDev& D, long i, long stri
 // items) -> verify (warp per edge, lanes = samples)
 // ---------------------------------------------------------------------------
 #define PL_SCAN 256
+#define PL_PRUNE_T 256   // threads (and nodes) per block of the multi-block prune
 
 // exclusive prefix sum over a block of whole warps, at most 32 (shuffles within the
 // warps, one shared pass across them); *total = the block's sum
@@ -2128,11 +2134,147 @@ __global__ void __launch_bounds__(128) k_plan_reach(PlanDev D, ArmK A) {
   D.ptr[nb + i] = D.par[nb + i];
 }
 
+// Multi-block prune after k_plan_reach (which leaves alive_i = the node's
+// own Eq. (reach) test and the root): k_prune_path keeps the incumbent's
+// ancestors; k_prune_walk gives each node the AND of alive over its parent
+// chain (parents have lower ids, so a chain ends at the root), and numbers the
+// kept nodes of its chunk of PL_PRUNE_T (the block that finishes last turns
+// the chunk counts into offsets); k_prune_scatter writes the kept nodes,
+// parents remapped, to the scratch arrays and k_prune_copy moves them back.
+// A chain longer than PL_PRUNE_WALK steps flags its problem, whose prune the
+// single-block k_plan_prune then does instead (pointer jumping).
+#define PL_PRUNE_WALK 64
+
+__global__ void k_prune_path(PlanDev D) {
+  pdl_begin();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= D.P) return;
+  const int N = D.n_nodes[p];
+  const long nb = (long)p * D.NC;
+  int steps = 0;   // parent links point to lower ids: at most N steps
+  for (int c = D.inc[p].id; c > 0 && c < N && steps < N; c = D.par[nb + c], ++steps)
+    D.alive[nb + c] = 1;
+  D.prune_deep[p] = 0;
+}
+
+__device__ __forceinline__ int prune_chunks(const PlanDev& D) {
+  return (D.NC + PL_PRUNE_T - 1) / PL_PRUNE_T;
+}
+
+__global__ void __launch_bounds__(PL_PRUNE_T) k_prune_walk(PlanDev D) {
+  pdl_begin();
+  __shared__ int sh[32];
+  __shared__ bool s_last;
+  const int chunks = prune_chunks(D);
+  const int p = blockIdx.x / chunks, ch = blockIdx.x - p * chunks;
+  const int i = ch * PL_PRUNE_T + threadIdx.x;
+  const int N = D.n_nodes[p];
+  const long nb = (long)p * D.NC;
+  int keep = 0;
+  if (i < N) {
+    int a = D.alive[nb + i];
+    int c = D.par[nb + i];
+    for (int steps = 0; a && c > 0 && steps < PL_PRUNE_WALK; ++steps) {
+      a &= D.alive[nb + c];
+      c = D.par[nb + c];
+    }
+    if (a && c > 0) atomicOr(D.prune_deep + p, 1);   // longer than the walk: fallback
+    keep = a;
+  }
+  int tot;
+  const int ex = block_scan(keep, sh, &tot);
+  if (i < N) D.newidx[nb + i] = keep ? ex : -1;   // index within the chunk
+  if (threadIdx.x == 0) {
+    D.prune_blk[(long)p * chunks + ch] = tot;
+    __threadfence();
+    const unsigned done = atomicAdd(&D.sched->prune_done, 1u);
+    s_last = done == gridDim.x - 1;
+    if (s_last) D.sched->prune_done = 0u;   // ready for the next iteration
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int q = 0; q < D.P; ++q) {   // chunk counts -> offsets, per problem
+    const int nq = (D.n_nodes[q] + PL_PRUNE_T - 1) / PL_PRUNE_T;
+    int carry = 0;
+    for (int base = 0; base < nq; base += PL_PRUNE_T) {
+      const int j = base + threadIdx.x;
+      const int v = j < nq ? __ldcg(D.prune_blk + (long)q * chunks + j) : 0;
+      int t;
+      const int e = block_scan(v, sh, &t);
+      if (j < nq) D.prune_blk[(long)q * chunks + j] = carry + e;
+      carry += t;
+    }
+    if (threadIdx.x == 0) D.prune_tot[q] = carry;
+    __syncthreads();
+  }
+}
+
+// new index of kept node i of problem p (chunk offset + index within the chunk)
+__device__ __forceinline__ int prune_newidx(const PlanDev& D, int p, int i) {
+  const long nb = (long)p * D.NC;
+  return D.prune_blk[(long)p * prune_chunks(D) + i / PL_PRUNE_T] + D.newidx[nb + i];
+}
+
+__global__ void __launch_bounds__(PL_PRUNE_T) k_prune_scatter(PlanDev D) {
+  pdl_begin();
+  const int chunks = prune_chunks(D);
+  const int p = blockIdx.x / chunks, ch = blockIdx.x - p * chunks;
+  const int i = ch * PL_PRUNE_T + threadIdx.x;
+  const long nb = (long)p * D.NC;
+  if (D.prune_deep[p] || i >= D.n_nodes[p] || D.newidx[nb + i] < 0) return;
+  const int ni = prune_newidx(D, p, i);
+  const float4* src = reinterpret_cast<const float4*>(D.st + (nb + i) * 16);
+  float4* dst = reinterpret_cast<float4*>(D.tmp_st + (nb + ni) * 16);
+  dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2]; dst[3] = src[3];
+  const int pa = D.par[nb + i];
+  D.tmp_par[nb + ni] = pa >= 0 ? prune_newidx(D, p, pa) : -1;   // a kept node's parent is kept
+  float* tf = D.tmp_f + (nb + ni) * 4;
+  tf[0] = D.t[nb + i]; tf[1] = D.J[nb + i]; tf[2] = D.nu[nb + i]; tf[3] = D.eT[nb + i];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) D.tmp_z[(nb + ni) * 9 + k] = D.zn[(nb + i) * 9 + k];
+}
+
+__global__ void __launch_bounds__(PL_PRUNE_T) k_prune_copy(PlanDev D) {
+  pdl_begin();
+  const int chunks = prune_chunks(D);
+  const int p = blockIdx.x / chunks, ch = blockIdx.x - p * chunks;
+  const int i = ch * PL_PRUNE_T + threadIdx.x;
+  const long nb = (long)p * D.NC;
+  if (D.prune_deep[p]) return;
+  const int total = D.prune_tot[p];
+  if (i < total) {
+    const float4* src = reinterpret_cast<const float4*>(D.tmp_st + (nb + i) * 16);
+    float4* dst = reinterpret_cast<float4*>(D.st + (nb + i) * 16);
+    dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2]; dst[3] = src[3];
+    D.par[nb + i] = D.tmp_par[nb + i];
+    const float* tf = D.tmp_f + (nb + i) * 4;
+    D.t[nb + i] = tf[0]; D.J[nb + i] = tf[1]; D.nu[nb + i] = tf[2]; D.eT[nb + i] = tf[3];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) D.zn[(nb + i) * 9 + k] = D.tmp_z[(nb + i) * 9 + k];
+  }
+  if (ch == 0 && threadIdx.x == 0) {
+    const int N = D.n_nodes[p];
+    D.n_nodes[p] = total;
+    if (total != N) D.packed[p] = 0;   // indices moved: repack the mirror
+    const Incumbent in = D.inc[p];
+    if (in.id >= 0 && in.id < N) {
+      Incumbent o = in;
+      o.id = D.newidx[nb + in.id] >= 0 ? prune_newidx(D, p, in.id) : -1;
+      D.inc[p] = o;
+    }
+  }
+}
+
+// The single-block prune (one block per problem), for problems whose walk
+// met a parent chain longer than PL_PRUNE_WALK: pointer jumping, then a
+// stable compaction with parent remap (through the scratch arrays).
 __global__ void __launch_bounds__(PL_ATTACH_THREADS) k_plan_prune(PlanDev D, ArmK A) {
   pdl_begin();
   __shared__ int sh[PL_ATTACH_THREADS];
   __shared__ int s_flag;
   const int p = blockIdx.x;
+  if (!D.prune_deep[p]) return;   // block-uniform: the multi-block prune did it
   const int N = D.n_nodes[p];
   const long nb = (long)p * D.NC;
   const Incumbent in = D.inc[p];
@@ -2183,6 +2325,8 @@ __global__ void __launch_bounds__(PL_ATTACH_THREADS) k_plan_prune(PlanDev D, Arm
     D.tmp_par[nb + ni] = pa >= 0 ? D.newidx[nb + pa] : -1;
     float* tf = D.tmp_f + (nb + ni) * 4;
     tf[0] = D.t[nb + i]; tf[1] = D.J[nb + i]; tf[2] = D.nu[nb + i]; tf[3] = D.eT[nb + i];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) D.tmp_z[(nb + ni) * 9 + k] = D.zn[(nb + i) * 9 + k];
   }
   __syncthreads();
   for (int i = threadIdx.x; i < total; i += blockDim.x) {
@@ -2192,6 +2336,8 @@ __global__ void __launch_bounds__(PL_ATTACH_THREADS) k_plan_prune(PlanDev D, Arm
     D.par[nb + i] = D.tmp_par[nb + i];
     const float* tf = D.tmp_f + (nb + i) * 4;
     D.t[nb + i] = tf[0]; D.J[nb + i] = tf[1]; D.nu[nb + i] = tf[2]; D.eT[nb + i] = tf[3];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) D.zn[(nb + i) * 9 + k] = D.tmp_z[(nb + i) * 9 + k];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -2613,6 +2759,9 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
   A_(D.added, P); A_(D.status, P);
   A_(D.ptr, P * NC); A_(D.newidx, P * NC); A_(D.alive, P * NC);
   A_(D.tmp_st, P * NC * 16); A_(D.tmp_f, P * NC * 4); A_(D.tmp_par, P * NC);
+  A_(D.tmp_z, P * NC * 9);
+  A_(D.prune_blk, P * ((NC + PL_PRUNE_T - 1) / PL_PRUNE_T)); A_(D.prune_tot, P);
+  A_(D.prune_deep, P);
   A_(D.samples, PL_NCOUNT);
   D.Emax = (int)(P * BM * KP);
   A_(D.e_ci, (size_t)D.Emax); A_(D.e_par, (size_t)D.Emax); A_(D.e_Tp, (size_t)D.Emax);
@@ -2818,7 +2967,16 @@ static fn_status enqueue_iteration(fn_planner* pl, unsigned flags, cudaStream_t 
     const long nn = (long)P * D.NC;
     pl_launch(k_plan_reach, (unsigned)((nn + 127) / 128), 128, 0, st, D, pl->arm);
     trace(pl, st, "k_plan_reach");
-    pl_launch(k_plan_prune, P, PL_ATTACH_THREADS, 0, st, D, pl->arm);
+    pl_launch(k_prune_path, (unsigned)((P + 127) / 128), 128, 0, st, D);
+    trace(pl, st, "k_plan_prune");
+    const unsigned pb = (unsigned)((long)P * ((D.NC + PL_PRUNE_T - 1) / PL_PRUNE_T));
+    pl_launch(k_prune_walk, pb, PL_PRUNE_T, 0, st, D);
+    trace(pl, st, "k_plan_prune");
+    pl_launch(k_prune_scatter, pb, PL_PRUNE_T, 0, st, D);
+    trace(pl, st, "k_plan_prune");
+    pl_launch(k_prune_copy, pb, PL_PRUNE_T, 0, st, D);
+    trace(pl, st, "k_plan_prune");
+    pl_launch(k_plan_prune, P, PL_ATTACH_THREADS, 0, st, D, pl->arm);   // deep chains only
     trace(pl, st, "k_plan_prune");
   }
   mark(8);

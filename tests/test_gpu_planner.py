@@ -169,10 +169,22 @@ def test_plan_round_with_obstacles(P, orc, arm):
     assert not bad
 
 
-def test_plan_prune_parity(P, orc, arm):
+@pytest.mark.parametrize("chain", [0, 150])
+def test_plan_prune_parity(P, orc, arm, chain):
+    """Eq. (reach) pruning against the oracle's prune_tree.  chain = 150: the
+    first 150 nodes form one path, longer than the multi-block prune's parent
+    walk, so the single-block prune takes the problem.  In both, every kept
+    node keeps its chart parameters."""
     case = make_case(arm, orc, 3, N=400)
     grid = synth.duration_grid(K_GRID)
     states, t, parent = case["tree"]
+    if chain:
+        t, parent = t.copy(), parent.copy()
+        for i in range(1, chain):
+            parent[i] = i - 1
+            t[i] = np.float32(t[i - 1] + 0.003)
+        for i in range(chain, len(t)):   # keep t increasing along every parent link
+            t[i] = max(t[i], np.float32(t[parent[i]] + 0.003))
     N, B = states.shape[0], case["cand"].shape[0]
     pl = P.Planner(arm, P=1, n_cap=N + B + 8, b_max=B, k=5, K=K_GRID, S=S_COLL)
     prob = P.problem_struct(case["pr"], B, case["n_goal"], root=case["root"])
@@ -181,10 +193,12 @@ def test_plan_prune_parity(P, orc, arm):
     pl.set_candidates(0, case["cand"], case["n_goal"], case["T_req"], case["v_rel"])
     pl.iterate([prob], 0, P.FN_PLAN_EXTERNAL)
     before = pl.get_tree(0)
+    z_before = pl.get_node_params(0, before["n"])
     # prune the tree as it stands: an iteration with no candidates and the prune flag
     prob0 = P.problem_struct(case["pr"], 0, 0, root=case["root"])
     out = pl.iterate([prob0], 1, P.FN_PLAN_EXTERNAL | P.FN_PLAN_PRUNE)[0]
     after = pl.get_tree(0)
+    z_after = pl.get_node_params(0, after["n"])
     pl.close()
     tree = OP.Tree(before["states"], before["t"], before["parent"], before["J"], before["nu"])
     inc = dict(id=out["incumbent"], J=out["J"], t_best=out["t_best"])
@@ -204,6 +218,17 @@ def test_plan_prune_parity(P, orc, arm):
         g, Tn = orc.reach_time(arm, case["pr"], tree.states[i, :7].astype(float), float(tree.t[i]))
         assert g >= 0 and abs(Tn - inc["t_best"]) < 5e-3, (i, g, Tn, inc["t_best"])
     assert len(diff) <= max(2, 0.01 * tree.n)
+    # the kept nodes moved with their parents, times and chart parameters
+    old = {before["states"][i].tobytes(): i for i in range(before["n"])}
+    for j in range(after["n"]):
+        i = old[after["states"][j].tobytes()]
+        assert after["t"][j] == before["t"][i]
+        pj, pi = after["parent"][j], before["parent"][i]
+        if pi >= 0:
+            assert np.array_equal(after["states"][pj], before["states"][pi])
+        assert np.array_equal(z_after[j], z_before[i], equal_nan=True)
+    if out["incumbent"] >= 0:
+        assert np.array_equal(after["states"][out["incumbent"]], before["states"][inc["id"]])
 
 
 @pytest.mark.parametrize("N,B,k,bm", [(300, 97, 5, None), (4097, 64, 8, None),
