@@ -49,6 +49,15 @@
 #ifndef PL_KNN_SPAN_MIN
 #define PL_KNN_SPAN_MIN 1024                  // smallest split of a free query's search
 #endif
+#ifndef PL_KNN_TW
+#define PL_KNN_TW 8                           // tiled search: free queries (one per warp) per CTA
+#endif
+#ifndef PL_KNN_TRING
+#define PL_KNN_TRING 4                        // tiled search: mirror blocks in the CTA's ring
+#endif
+#ifndef PL_KNN_TILE_NODES
+#define PL_KNN_TILE_NODES 32768               // tree capacity from which the tiled search is used
+#endif
 #define PL_MAX_P 1024
 #define PL_MAX_KEV 40                         // launches traced per iteration
 #define PL_NCOUNT 14  // work counters: probe, verify, mid-probe, kNN pairs, IK starts,
@@ -100,7 +109,8 @@ struct Sched {
 
 struct PlanDev {  // device pointers, passed by value to the kernels
   int P, NC, BM, KP, KN, KM, K, S, S_clear, G;
-  int knn_slots;      // resident warps of the parent search's persistent grid
+  int knn_slots;      // resident warps (CTAs when tiled) of the free queries' search grid
+  int knn_tile;       // 1: the free queries' search is tiled (PL_KNN_TW queries share a CTA)
   int vstages;        // packed verification stages (1 or 2)
   float w_vel, vel_frac, margin;
   float* st;          // [P][NC][16]
@@ -286,11 +296,13 @@ __global__ void k_plan_schedule(PlanDev D) {
   // free queries over all problems: with fewer query groups than resident
   // warps of the parent search, each query's nodes are split further so
   // that every warp gets an item (splits of at least PL_KNN_SPAN_MIN nodes)
+  // (groups of PL_KNN_TW queries, one CTA item each, when the search is tiled)
+  const int qg = D.knn_tile ? PL_KNN_TW : PL_KNN_QW;
   int qf = 0;
   for (int p = 0; p < D.P; ++p) {
     const int B = min(max(D.prob[p].batch, 0), D.BM);
     const int G = min(max(D.prob[p].n_goal, 0), B);
-    if (D.KN > 0 && D.n_nodes[p] > 1) qf += (B - G + PL_KNN_QW - 1) / PL_KNN_QW;
+    if (D.KN > 0 && D.n_nodes[p] > 1) qf += (B - G + qg - 1) / qg;
   }
   const int fill = qf > 0 ? max(1, D.knn_slots / qf) : 1;
   int fo = 0, go = 0, ko = 0, kg = 0, po = 0, nsg_max = 1;
@@ -315,7 +327,7 @@ __global__ void k_plan_schedule(PlanDev D) {
     S->nsplit[1][p] = nsg;
     nsg_max = max(nsg_max, nsg);
     if (D.KN > 0 && span > 0) {
-      ko += ((B - G + PL_KNN_QW - 1) / PL_KNN_QW) * ns;
+      ko += ((B - G + qg - 1) / qg) * ns;
       kg += ((G + PL_KNN_QW - 1) / PL_KNN_QW) * nsg;
     }
     D.added[p] = 0;
@@ -822,6 +834,127 @@ __global__ void __launch_bounds__(32 * PL_KNN_WARPS) k_plan_knn(PlanDev D, int k
           __threadfence();
           knn_merge_query<KM>(D, p, b, ns);
         }
+      }
+    }
+  }
+}
+
+
+// Tiled search of the free queries (planners whose tree capacity is at
+// least PL_KNN_TILE_NODES): a CTA of PL_KNN_TW warps claims (problem, group
+// of PL_KNN_TW queries, split) items, warp w takes query w of the group.
+// The CTA's threads copy each 64-node mirror block of the split once into a
+// shared ring (cp.async, PL_KNN_TRING - 1 blocks ahead, one barrier per
+// block) and every warp scores it from there as k_plan_knn does (the same
+// paired arithmetic, list and tie rule), so a split's nodes leave L2 once
+// per PL_KNN_TW queries: on large trees the per-warp search is bound by the
+// L2 reads of every query streaming the whole split.  Warps whose query is
+// not valid keep to the copies and barriers.
+constexpr int kKnnTileSmem = PL_KNN_TRING * 7 * 32 * 16;
+
+template <int KM>
+__global__ void __launch_bounds__(32 * PL_KNN_TW) k_plan_knn_tile(PlanDev D) {
+  pdl_begin();
+  extern __shared__ float4 knn_tring[];   // [slot][7][32]
+  __shared__ int s_item;
+  const Sched* S = D.sched;
+  const int items = S->knn_items[0];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const float2 w2 = make_float2(D.w_vel, D.w_vel);
+  Sched* Sw = D.sched;
+  for (;;) {
+    __syncthreads();   // the last item's ring reads and s_item reads are done
+    if (threadIdx.x == 0) s_item = atomicAdd(&Sw->knn_head[0], 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= items) break;                  // block-uniform
+    const int p = find_problem(S->knn_off[0], D.P, item);
+    const int local = item - S->knn_off[0][p];
+    const int ns = S->nsplit[0][p];
+    const int g = local / ns, split = local - g * ns;
+    const int B = min(max(D.prob[p].batch, 0), D.BM);
+    const int b = min(max(D.prob[p].n_goal, 0), B) + g * PL_KNN_TW + w;
+    const bool mine = b < B;                                    // warp-uniform
+    const bool wact = mine && D.valid[(long)p * D.BM + b];     // warp-uniform
+    const int N = D.n_nodes[p];
+    const int span = N - 1;
+    const int per = (span + ns - 1) / ns;
+    const int lo = 1 + split * per, hi = min(N, lo + per);
+    float2 q2[14];
+    {
+      float qv[14];
+      load_query(reinterpret_cast<const float4*>(D.cand) + 4 * ((long)p * D.BM + (mine ? b : B - 1)),
+                 qv);
+#pragma unroll
+      for (int c = 0; c < 14; ++c) q2[c] = make_float2(qv[c], qv[c]);
+    }
+    WarpTopK<KM> top;
+    const float4* mir = D.mir + (long)p * D.NB * 7 * 32;
+    const int blk0 = lo >> 6, nblk = hi > lo ? ((hi + 63) >> 6) - blk0 : 0;   // block-uniform
+    auto issue = [&](int r) {   // block r of the split into ring slot r % PL_KNN_TRING
+      if (r < nblk) {
+        const float4* src = mir + (long)(blk0 + r) * 7 * 32;
+        float4* dst = knn_tring + (r % PL_KNN_TRING) * 7 * 32;
+        for (int i = threadIdx.x; i < 7 * 32; i += 32 * PL_KNN_TW) cp_async16(dst + i, src + i);
+      }
+      cp_async_commit();
+    };
+#pragma unroll
+    for (int r = 0; r < PL_KNN_TRING - 1; ++r) issue(r);
+    for (int r = 0; r < nblk; ++r) {
+      cp_async_wait<PL_KNN_TRING - 2>();   // this thread's copies of block r landed
+      __syncthreads();                     // everyone's copies of block r; slot of r - 1 read
+      issue(r + PL_KNN_TRING - 1);         // into the slot block r - 1 held
+      if (wact) {
+        const float4* sl = knn_tring + (r % PL_KNN_TRING) * 7 * 32 + lane;
+        float4 x[7];
+#pragma unroll
+        for (int cc = 0; cc < 7; ++cc) x[cc] = sl[cc * 32];
+        const int n0 = (blk0 + r) * 64 + 2 * lane;
+        const bool v0 = n0 >= lo && n0 < hi, v1 = n0 + 1 >= lo && n0 + 1 < hi;
+        float2 dq = make_float2(0.f, 0.f), dv = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < 14; ++c) {
+          const float4 v = x[c >> 1];
+          const float2 nv = (c & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+          const float2 t = __fadd2_rn(q2[c], nv);
+          if (c < 7) dq = __ffma2_rn(t, t, dq);
+          else dv = __ffma2_rn(t, t, dv);
+        }
+        const float2 d = __ffma2_rn(w2, dv, dq);
+        top.offer(__ballot_sync(0xffffffffu, v0 && knn_less(d.x, n0, top.td, top.ti)), d.x, n0);
+        top.offer(__ballot_sync(0xffffffffu, v1 && knn_less(d.y, n0 + 1, top.td, top.ti)), d.y,
+                  n0 + 1);
+      }
+    }
+    cp_async_wait<0>();
+    if (D.samples && lane == 0 && wact)
+      atomicAdd(D.samples + 3, (unsigned long long)max(hi - lo, 0));
+    if (!mine) continue;                       // warp-uniform
+    if (lane < KM) {
+      const int id = wact ? top.i : 0x7fffffff;
+      if (ns == 1) {
+        if (lane < D.KN) D.nn[((long)p * D.BM + b) * D.KN + lane] = id == 0x7fffffff ? -1 : id;
+      } else {
+        const long off = (((long)p * PL_NSPLIT_MAX + split) * D.BM + b) * KM + lane;
+        D.part_d[off] = top.d;
+        D.part_i[off] = id;
+      }
+    }
+    if (ns > 1) {
+      // every lane's split-list stores are fenced, and the warp has passed
+      // its fences, before lane 0 counts the split as finished
+      __threadfence();
+      __syncwarp();
+      int last = 0;
+      if (lane == 0) {
+        int* cnt = D.knn_cnt + (long)p * D.BM + b;
+        last = atomicAdd(cnt, 1) == ns - 1;
+        if (last) *cnt = 0;   // ready for the next iteration
+      }
+      if (__shfl_sync(0xffffffffu, last, 0)) {
+        __threadfence();
+        knn_merge_query<KM>(D, p, b, ns);
       }
     }
   }
@@ -2573,6 +2706,25 @@ static int knn_blocks(fn_planner* pl) {
   return blocks[dev];
 }
 
+// resident CTAs of the tiled free-query search (its persistent grid)
+template <int KM>
+static int knn_tile_blocks() {
+  static int blocks[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (blocks[dev] == 0) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_plan_knn_tile<KM>,
+                                                      32 * PL_KNN_TW, kKnnTileSmem) !=
+            cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    blocks[dev] = per_sm * num_sms();
+  }
+  return blocks[dev];
+}
+
 // sampling and parents: candidates of every problem (unless given by the
 // caller), then their nearest tree nodes (mark(2) between the two)
 template <class Mark>
@@ -2588,12 +2740,19 @@ static void enqueue_front(fn_planner* pl, unsigned flags, cudaStream_t st, Mark&
     if (!knn) return;
     // the goal list is short (the decoded goals): a small grid claims it
     const int gb = 2 * num_sms();
-    if (D.KM == 8)
+    if (kind == 0 && D.knn_tile) {   // large trees: the tiled search
+      if (D.KM == 8)
+        pl_launch(k_plan_knn_tile<8>, knn_tile_blocks<8>(), 32 * PL_KNN_TW, kKnnTileSmem, st, D);
+      else
+        pl_launch(k_plan_knn_tile<16>, knn_tile_blocks<16>(), 32 * PL_KNN_TW, kKnnTileSmem, st,
+                  D);
+    } else if (D.KM == 8) {
       pl_launch(k_plan_knn<8>, kind == 0 ? knn_blocks<8>(pl) : std::min(gb, knn_blocks<8>(pl)),
                 32 * PL_KNN_WARPS, kKnnSmem, st, D, kind);
-    else
+    } else {
       pl_launch(k_plan_knn<16>, kind == 0 ? knn_blocks<16>(pl) : std::min(gb, knn_blocks<16>(pl)),
                 32 * PL_KNN_WARPS, kKnnSmem, st, D, kind);
+    }
     trace(pl, st, "k_plan_knn");
   };
   auto goals = [&](int late) {
@@ -2740,7 +2899,9 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
   memset(&D, 0, sizeof(D));
   D.P = c.P; D.NC = c.n_cap; D.BM = c.b_max; D.KP = c.k; D.KN = std::max(c.k - 1, 1);
   D.KM = (c.k - 1) <= 8 ? 8 : 16;
-  D.knn_slots = (D.KM == 8 ? knn_blocks<8>(pl) : knn_blocks<16>(pl)) * PL_KNN_WARPS;
+  D.knn_tile = c.n_cap >= PL_KNN_TILE_NODES ? 1 : 0;
+  D.knn_slots = D.knn_tile ? (D.KM == 8 ? knn_tile_blocks<8>() : knn_tile_blocks<16>())
+                           : (D.KM == 8 ? knn_blocks<8>(pl) : knn_blocks<16>(pl)) * PL_KNN_WARPS;
   D.vstages = (long)c.P * c.b_max * c.k >= PL_VSTAGE_EDGES ? 2 : 1;
   D.K = c.K; D.S = c.S; D.S_clear = c.S_clear; D.G = c.reach_grid;
   D.w_vel = c.w_vel; D.vel_frac = c.vel_frac; D.margin = c.clear_margin;

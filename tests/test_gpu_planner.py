@@ -231,16 +231,19 @@ def test_plan_prune_parity(P, orc, arm, chain):
         assert np.array_equal(after["states"][out["incumbent"]], before["states"][inc["id"]])
 
 
-@pytest.mark.parametrize("N,B,k,bm", [(300, 97, 5, None), (4097, 64, 8, None),
-                                      (13001, 150, 8, None), (9000, 40, 17, None),
-                                      (300, 97, 5, 8192), (4097, 300, 8, 8192),
-                                      (13001, 150, 8, 8192), (9000, 70, 17, 8192)])
-def test_parents_match_brute_force(P, orc, arm, N, B, k, bm):
+@pytest.mark.parametrize("N,B,k,bm,cap", [(300, 97, 5, None, None), (4097, 64, 8, None, None),
+                                          (13001, 150, 8, None, None), (9000, 40, 17, None, None),
+                                          (300, 97, 5, 8192, None), (4097, 300, 8, 8192, None),
+                                          (13001, 150, 8, 8192, None), (9000, 70, 17, 8192, None),
+                                          (300, 97, 5, None, 40000), (4097, 300, 8, None, 40000),
+                                          (13001, 150, 8, None, 40000), (9000, 70, 17, None, 40000)])
+def test_parents_match_brute_force(P, orc, arm, N, B, k, bm, cap):
     """The planner's parent lists equal the oracle's brute-force kNN over the
     non-root nodes (one split of the tree and several, k-1 = 4, 7, 16),
     up to swaps among near-equal exact distances.  bm = 8192: a planner sized
     for 8192 candidates (a larger persistent grid share per query, more
-    splits merged)."""
+    splits merged); cap = 40000: a planner for large trees, whose free
+    queries take the tiled search (eight queries per CTA, ragged groups)."""
     from tests.parity import knn_mismatches
     toss = synth.random_toss(arm, 21)
     root = synth.random_states(arm, 1, 77)[0]
@@ -248,7 +251,7 @@ def test_parents_match_brute_force(P, orc, arm, N, B, k, bm):
     states, parent, t = synth.random_tree(arm, N, 31, root=root)
     cand = synth.random_states(arm, B, 32)
     w_vel = 0.1
-    pl = P.Planner(arm, P=1, n_cap=N + B + 8, b_max=bm or B, k=k, K=16, S=8, w_vel=w_vel)
+    pl = P.Planner(arm, P=1, n_cap=cap or N + B + 8, b_max=bm or B, k=k, K=16, S=8, w_vel=w_vel)
     prob = P.problem_struct(pr, B, 0, root=root)
     pl.reset([prob])
     pl.load_tree(0, states, t, parent)
