@@ -89,6 +89,7 @@ struct Sched {
   int n_surv;         // probe survivors appended (may exceed surv_cap)
   int n_dyn;          // edges with probe items listed by the prep (zero between bodies)
   unsigned prep_done; // blocks of k_plan_eprep finished (zero between iterations)
+  unsigned att_done;  // blocks of k_attach_scan finished (zero between iterations)
   unsigned prune_done;  // blocks of k_prune_walk finished (zero between iterations)
   int n_free_edges;   // free edges of all problems (the queue's first part)
   int n_edges;        // all edges
@@ -111,6 +112,11 @@ struct PlanDev {  // device pointers, passed by value to the kernels
   int P, NC, BM, KP, KN, KM, K, S, S_clear, G;
   int knn_slots;      // resident warps (CTAs when tiled) of the free queries' search grid
   int knn_tile;       // 1: the free queries' search is tiled (PL_KNN_TW queries share a CTA)
+  int att_wide;       // 1: attach over many blocks per problem (large batches, few problems)
+  int32_t* att_idx;   // [P][BM] a candidate's index among its chunk's attached ones, or -1
+  int32_t* att_blk;   // [P][ceil(BM/PL_ATT_T)] attached per chunk, then their offsets
+  int32_t* att_tot;   // [P] candidates attached
+  unsigned long long* att_key;  // [P] best new rendezvous: ordered J (high), ~node (low)
   int vstages;        // packed verification stages (1 or 2)
   float w_vel, vel_frac, margin;
   float* st;          // [P][NC][16]
@@ -1786,6 +1792,11 @@ __global__ void __launch_bounds__(32 * PL_REFINE_WARPS, 4)
 // attach + score + incumbent: one block per problem
 // ---------------------------------------------------------------------------
 #define PL_ATTACH_THREADS 1024
+#define PL_ATT_T 256             // candidates per block of the multi-block attach
+#ifndef PL_ATT_WIDE_B
+#define PL_ATT_WIDE_B 4096       // b_max from which (with at most PL_ATT_WIDE_P problems) attach is multi-block
+#endif
+#define PL_ATT_WIDE_P 16
 
 // the caller's record of problem p: incumbent, its J and time, tree counts,
 // status, and the first segment of the incumbent's path
@@ -1929,6 +1940,171 @@ __global__ void __launch_bounds__(PL_ATTACH_THREADS) k_plan_attach(PlanDev D, in
     }
     if (output) write_rendezvous(D, p);
   }
+}
+
+// Multi-block attach (planners with large batches and few problems): the
+// same attach as k_plan_attach over PL_ATT_T candidates per block.
+// k_attach_scan numbers the attachable candidates of each chunk (the block
+// that finishes last turns chunk counts into per-problem offsets, so node
+// ids follow candidate order); k_attach_write attaches every candidate to its
+// ok parent of least t(p) + T_p (ties to the lower slot) and offers each new
+// rendezvous node's (J, id) as one 64-bit key, larger J first, then the lower
+// id, to a per-problem atomicMax; k_attach_final sets the tree size and
+// replaces the incumbent if the best key's J is strictly better.
+__device__ __forceinline__ int att_chunks(const PlanDev& D) {
+  return (D.BM + PL_ATT_T - 1) / PL_ATT_T;
+}
+
+__global__ void __launch_bounds__(PL_ATT_T) k_attach_scan(PlanDev D) {
+  pdl_begin();
+  __shared__ int sh[32];
+  __shared__ bool s_last;
+  const int chunks = att_chunks(D);
+  const int p = blockIdx.x / chunks, ch = blockIdx.x - p * chunks;
+  const int b = ch * PL_ATT_T + threadIdx.x;
+  const int B = min(max(D.prob[p].batch, 0), D.BM);
+  int any = 0;
+  if (b < B) {
+    const long ci = (long)p * D.BM + b;
+    for (int j0 = 0; j0 < D.KP; j0 += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (j0 + u < D.KP) any |= D.e_ok[ci * D.KP + j0 + u];
+    }
+  }
+  int tot;
+  const int ex = block_scan(any != 0, sh, &tot);
+  if (b < B) D.att_idx[(long)p * D.BM + b] = any ? ex : -1;
+  if (threadIdx.x == 0) {
+    D.att_blk[(long)p * chunks + ch] = tot;
+    __threadfence();
+    const unsigned done = atomicAdd(&D.sched->att_done, 1u);
+    s_last = done == gridDim.x - 1;
+    if (s_last) D.sched->att_done = 0u;   // ready for the next iteration
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int q = 0; q < D.P; ++q) {   // chunk counts -> offsets, per problem
+    const int nq = (min(max(D.prob[q].batch, 0), D.BM) + PL_ATT_T - 1) / PL_ATT_T;
+    int carry = 0;
+    for (int base = 0; base < nq; base += PL_ATT_T) {
+      const int j = base + threadIdx.x;
+      const int v = j < nq ? __ldcg(D.att_blk + (long)q * chunks + j) : 0;
+      int t;
+      const int e = block_scan(v, sh, &t);
+      if (j < nq) D.att_blk[(long)q * chunks + j] = carry + e;
+      carry += t;
+    }
+    if (threadIdx.x == 0) {
+      D.att_tot[q] = carry;
+      D.att_key[q] = 0ull;   // no new rendezvous node yet
+    }
+    __syncthreads();
+  }
+}
+
+// J, ordered as an unsigned integer (larger J -> larger key)
+__device__ __forceinline__ unsigned ordered_f32(float x) {
+  const unsigned u = __float_as_uint(x);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__global__ void __launch_bounds__(PL_ATT_T) k_attach_write(PlanDev D) {
+  pdl_begin();
+  __shared__ unsigned long long s_key[PL_ATT_T / 32];
+  const int chunks = att_chunks(D);
+  const int p = blockIdx.x / chunks, ch = blockIdx.x - p * chunks;
+  const int b = ch * PL_ATT_T + threadIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const fn_problem_t& P = D.prob[p];
+  const int B = min(max(P.batch, 0), D.BM);
+  const int G = min(max(P.n_goal, 0), B);
+  const int N0 = D.n_nodes[p];
+  const long nb = (long)p * D.NC;
+  unsigned long long key = 0ull;
+  const int li = b < B ? D.att_idx[(long)p * D.BM + b] : -1;
+  if (li >= 0) {
+    const long ci = (long)p * D.BM + b;
+    int bj = -1, bpar = -1;
+    float bt = INFINITY;
+    for (int j0 = 0; j0 < D.KP; j0 += 8) {   // eight edges' loads in flight at once
+      bool ok[8];
+      int pr[8];
+      float te[8], tp[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = j0 + u;
+        const long ei = ci * D.KP + j;
+        ok[u] = j < D.KP && D.e_ok[ei];
+        pr[u] = j == 0 ? 0 : (ok[u] ? D.nn[ci * D.KN + (j - 1)] : 0);
+        te[u] = ok[u] ? D.e_T[ei] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) tp[u] = ok[u] ? D.t[nb + pr[u]] : 0.f;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float tt = __fadd_rn(tp[u], te[u]);
+        if (ok[u] && tt < bt) { bt = tt; bj = j0 + u; bpar = pr[u]; }
+      }
+    }
+    const int node = N0 + D.att_blk[(long)p * chunks + ch] + li;
+    if (node >= D.NC) {
+      atomicOr(&D.status[p], FN_PLAN_TREE_FULL);
+    } else {
+      const long nd = nb + node;
+      const float4* src = reinterpret_cast<const float4*>(D.cand + ci * 16);
+      float4* dst = reinterpret_cast<float4*>(D.st + nd * 16);
+      dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2]; dst[3] = src[3];
+      D.t[nd] = bt;
+      D.par[nd] = bpar;
+      const float nu = fmaxf(D.nu[nb + bpar], D.e_rv[ci * D.KP + bj]);
+      D.nu[nd] = nu;
+      D.eT[nd] = D.e_T[ci * D.KP + bj];
+      float Jv = NAN;
+      if (b < G) {
+        Jv = objective(P, bt, D.vrel[ci], nu);
+        key = ((unsigned long long)ordered_f32(Jv) << 32) | (unsigned)(0xffffffffu - (unsigned)node);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) D.zn[nd * 9 + i] = D.cz[ci * 9 + i];
+      }
+      D.J[nd] = Jv;
+    }
+  }
+  // the block's best key, one atomic per block
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, o));
+  if (lane == 0) s_key[w] = key;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long k = 0ull;
+    for (int i = 0; i < PL_ATT_T / 32; ++i) k = max(k, s_key[i]);
+    if (k) atomicMax(D.att_key + p, k);
+  }
+}
+
+__global__ void k_attach_final(PlanDev D, int output) {
+  pdl_begin();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= D.P) return;
+  const long nb = (long)p * D.NC;
+  const int N0 = D.n_nodes[p];
+  const int add = min(D.att_tot[p], D.NC - N0);
+  D.n_nodes[p] = N0 + add;
+  D.added[p] = add;
+  const unsigned long long key = D.att_key[p];
+  if (key) {
+    const int node = (int)(0xffffffffu - (unsigned)(key & 0xffffffffull));
+    const float J = D.J[nb + node];
+    Incumbent in = D.inc[p];
+    if (J > in.J) {
+      in.id = node;
+      in.J = J;
+      in.t_best = D.t[nb + node];
+      D.inc[p] = in;
+    }
+  }
+  if (output) write_rendezvous(D, p);
 }
 
 // ---------------------------------------------------------------------------
@@ -2900,6 +3076,7 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
   D.P = c.P; D.NC = c.n_cap; D.BM = c.b_max; D.KP = c.k; D.KN = std::max(c.k - 1, 1);
   D.KM = (c.k - 1) <= 8 ? 8 : 16;
   D.knn_tile = c.n_cap >= PL_KNN_TILE_NODES ? 1 : 0;
+  D.att_wide = c.b_max >= PL_ATT_WIDE_B && c.P <= PL_ATT_WIDE_P ? 1 : 0;
   D.knn_slots = D.knn_tile ? (D.KM == 8 ? knn_tile_blocks<8>() : knn_tile_blocks<16>())
                            : (D.KM == 8 ? knn_blocks<8>(pl) : knn_blocks<16>(pl)) * PL_KNN_WARPS;
   D.vstages = (long)c.P * c.b_max * c.k >= PL_VSTAGE_EDGES ? 2 : 1;
@@ -2921,6 +3098,8 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
   A_(D.ptr, P * NC); A_(D.newidx, P * NC); A_(D.alive, P * NC);
   A_(D.tmp_st, P * NC * 16); A_(D.tmp_f, P * NC * 4); A_(D.tmp_par, P * NC);
   A_(D.tmp_z, P * NC * 9);
+  A_(D.att_idx, P * BM); A_(D.att_blk, P * ((BM + PL_ATT_T - 1) / PL_ATT_T)); A_(D.att_tot, P);
+  A_(D.att_key, P);
   A_(D.prune_blk, P * ((NC + PL_PRUNE_T - 1) / PL_PRUNE_T)); A_(D.prune_tot, P);
   A_(D.prune_deep, P);
   A_(D.samples, PL_NCOUNT);
@@ -3112,8 +3291,18 @@ static fn_status enqueue_iteration(fn_planner* pl, unsigned flags, cudaStream_t 
   }
   mark(6);
   const bool late = flags & (FN_PLAN_DENSITY | FN_PLAN_REFIT | FN_PLAN_GREFINE | FN_PLAN_PRUNE);
-  pl_launch(k_plan_attach, P, PL_ATTACH_THREADS, 0, st, D, late ? 0 : 1);
-  trace(pl, st, "k_plan_attach");
+  if (D.att_wide) {
+    const unsigned ab = (unsigned)((long)P * ((D.BM + PL_ATT_T - 1) / PL_ATT_T));
+    pl_launch(k_attach_scan, ab, PL_ATT_T, 0, st, D);
+    trace(pl, st, "k_plan_attach");
+    pl_launch(k_attach_write, ab, PL_ATT_T, 0, st, D);
+    trace(pl, st, "k_plan_attach");
+    pl_launch(k_attach_final, (unsigned)((P + 127) / 128), 128, 0, st, D, late ? 0 : 1);
+    trace(pl, st, "k_plan_attach");
+  } else {
+    pl_launch(k_plan_attach, P, PL_ATTACH_THREADS, 0, st, D, late ? 0 : 1);
+    trace(pl, st, "k_plan_attach");
+  }
   if (flags & (FN_PLAN_DENSITY | FN_PLAN_REFIT)) {
     pl_launch(k_plan_density, P, PL_DENSITY_THREADS, 0, st, D, (flags & FN_PLAN_REFIT) ? 1 : 0);
     trace(pl, st, "k_plan_density");

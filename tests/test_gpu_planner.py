@@ -40,12 +40,12 @@ def make_case(arm, orc, seed, N=300, n_goal_draw=512, n_free=96, obstacles=None)
                 T_req=T_req, v_rel=v_rel, obstacles=obstacles)
 
 
-def run_pair(P, orc, arm, case, k=5, prune=False, obstacles=None):
+def run_pair(P, orc, arm, case, k=5, prune=False, obstacles=None, bm=None):
     grid = synth.duration_grid(K_GRID)
     states, t, parent = case["tree"]
     N = states.shape[0]
     B = case["cand"].shape[0]
-    pl = P.Planner(arm, P=1, n_cap=N + B + 8, b_max=B, k=k, K=K_GRID, S=S_COLL, S_clear=8)
+    pl = P.Planner(arm, P=1, n_cap=N + B + 8, b_max=bm or B, k=k, K=K_GRID, S=S_COLL, S_clear=8)
     prob = P.problem_struct(case["pr"], B, case["n_goal"], root=case["root"], obstacles=obstacles)
     pl.reset([prob])
     pl.load_tree(0, states, t, parent)
@@ -62,11 +62,13 @@ def run_pair(P, orc, arm, case, k=5, prune=False, obstacles=None):
     return out, gtree, rtree, rinc, det, grid
 
 
-@pytest.mark.parametrize("seed", [0, 1])
-def test_plan_round_parity(P, orc, arm, seed):
+@pytest.mark.parametrize("seed,bm", [(0, None), (1, None), (0, 4096), (1, 4096)])
+def test_plan_round_parity(P, orc, arm, seed, bm):
+    """One round of Algorithm 1's body against the oracle.  bm = 4096: a
+    planner for large batches, whose attach runs over many blocks."""
     case = make_case(arm, orc, seed)
     assert case["n_goal"] >= 3
-    out, gtree, rtree, rinc, det, grid = run_pair(P, orc, arm, case)
+    out, gtree, rtree, rinc, det, grid = run_pair(P, orc, arm, case, bm=bm)
     N = case["tree"][0].shape[0]
     bad = compare_round(orc, arm, case, gtree, rtree, det, N, grid)
     assert not bad, f"candidates attached differently without a near-margin edge: {bad[:5]}"
