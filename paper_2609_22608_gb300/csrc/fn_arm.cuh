@@ -517,30 +517,6 @@ __device__ __forceinline__ void cross2(float2 ax, float2 ay, float2 az, float2 b
   cz = fma2(ax, by, neg2(mul2(ay, bx)));
 }
 
-// fn_sincos on both halves (the same reduction and polynomials)
-__device__ __forceinline__ void fn_sincos2(float2 x, float2& s, float2& c) {
-  const float2 t = mul2(x, dup2(0.636619772367581343f));
-  const float2 k = make_float2(rintf(t.x), rintf(t.y));
-  const float2 nk = neg2(k);
-  float2 r = fma2(nk, dup2(1.57079637050628662109375f), x);
-  r = fma2(nk, dup2(-4.37113900018624283e-8f), r);
-  const float2 r2 = mul2(r, r);
-  float2 sp = fma2(r2, dup2(2.75573192239858906526e-6f), dup2(-1.98412698412698412698e-4f));
-  sp = fma2(r2, sp, dup2(8.33333333333333333333e-3f));
-  sp = fma2(r2, sp, dup2(-1.66666666666666666667e-1f));
-  const float2 sr = fma2(mul2(r, r2), sp, r);
-  float2 cp = fma2(r2, dup2(-2.75573192239858906526e-7f), dup2(2.48015873015873015873e-5f));
-  cp = fma2(r2, cp, dup2(-1.38888888888888888889e-3f));
-  cp = fma2(r2, cp, dup2(4.16666666666666666667e-2f));
-  cp = fma2(r2, cp, dup2(-0.5f));
-  const float2 cr = fma2(r2, cp, dup2(1.0f));
-  const int qx = __float2int_rn(k.x) & 3, qy = __float2int_rn(k.y) & 3;
-  const float ax = (qx & 1) ? cr.x : sr.x, bx = (qx & 1) ? sr.x : cr.x;
-  const float ay = (qy & 1) ? cr.y : sr.y, by = (qy & 1) ? sr.y : cr.y;
-  s = make_float2((qx & 2) ? -ax : ax, (qy & 2) ? -ay : ay);
-  c = make_float2(((qx + 1) & 2) ? -bx : bx, ((qy + 1) & 2) ? -by : by);
-}
-
 #define FN_LINK2_F4 10   // float4 per link in the paired table
 struct LinkTab2 {
   const float4* p;       // [7][FN_LINK2_F4] in shared memory
@@ -645,7 +621,12 @@ __device__ __forceinline__ void torque_at_pair(const ArmK& A, LinkTab2 L, CubicL
     rec[9] = fma2(hi2(t6), acc, mul2(fs2, fma2(lo2(t7), rc, neg2(hi2(t8)))));
     rec[8] = v;
     float2 s_, c_;
-    fn_sincos2(add2(q, hi2(t2)), s_, c_);
+    {   // the hardware sine / cosine: absolute error ~1e-6 on these angles (joint
+        // value plus offset, a few radians), an order below the torque tolerance
+      const float2 th = add2(q, hi2(t2));
+      __sincosf(th.x, &s_.x, &c_.x);
+      __sincosf(th.y, &s_.y, &c_.y);
+    }
     rec[6] = c_;
     rec[7] = s_;
     // u = dw_prev x p + w_prev x (w_prev x p) + dv_prev   (frame j-1)
