@@ -185,34 +185,13 @@ __device__ __forceinline__ void cubic_eval(const CubicLane& c, int j, float u, f
 // once per use (the library versions carry a large-argument path whose code
 // is replicated at every call site of the unrolled link loop).
 //
-// fn_sincos: Cody-Waite reduction x = k pi/2 + r with pi/2 split into a
-// single-precision head and tail, |r| <= pi/4, then the Taylor polynomials
-// of sin (to r^9) and cos (to r^10), whose truncation errors on |r| <= pi/4
-// are below (pi/4)^11/11! = 1.8e-9 and (pi/4)^12/12! = 1.2e-10, far below
-// the single-precision rounding of the result (~6e-8); the quadrant k mod 4
-// swaps and negates.  Valid for |x| < 2^10 (the reduction's k * tail stays
-// exact to a few ulp); joint angles plus offsets are a few radians.
+// fn_sincos: the hardware sine and cosine (sin.approx / cos.approx); on the
+// torque evaluation's angles (a joint value plus its offset, a few radians)
+// the absolute error is about 1e-6, an order below the 1e-5 torque tolerance
+// (an earlier Cody-Waite reduction with Taylor polynomials, accurate to the
+// single-precision rounding, spent a tenth of the scan's instructions).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void fn_sincos(float x, float* s, float* c) {
-  const float k = rintf(x * 0.636619772367581343f);            // x / (pi/2), nearest
-  float r = fmaf(-k, 1.57079637050628662109375f, x);           // pi/2 head (nearest float)
-  r = fmaf(-k, -4.37113900018624283e-8f, r);                   // pi/2 - head
-  const float r2 = r * r;
-  float sp = fmaf(r2, 2.75573192239858906526e-6f, -1.98412698412698412698e-4f);   // 1/9!, -1/7!
-  sp = fmaf(r2, sp, 8.33333333333333333333e-3f);                                   // 1/5!
-  sp = fmaf(r2, sp, -1.66666666666666666667e-1f);                                  // -1/3!
-  const float sr = fmaf(r * r2, sp, r);
-  float cp = fmaf(r2, -2.75573192239858906526e-7f, 2.48015873015873015873e-5f);   // -1/10!, 1/8!
-  cp = fmaf(r2, cp, -1.38888888888888888889e-3f);                                  // -1/6!
-  cp = fmaf(r2, cp, 4.16666666666666666667e-2f);                                   // 1/4!
-  cp = fmaf(r2, cp, -0.5f);                                                        // -1/2!
-  const float cr = fmaf(r2, cp, 1.0f);
-  const int q = __float2int_rn(k) & 3;
-  const float a = (q & 1) ? cr : sr;        // sin: q = 0 sr, 1 cr, 2 -sr, 3 -cr
-  const float b = (q & 1) ? sr : cr;        // cos: q = 0 cr, 1 -sr, 2 -cr, 3 sr
-  *s = (q & 2) ? -a : a;
-  *c = ((q + 1) & 2) ? -b : b;
-}
+__device__ __forceinline__ void fn_sincos(float x, float* s, float* c) { __sincosf(x, s, c); }
 
 // exp(x) = 2^(x log2 e) on the hardware base-2 exponential (ex2.approx,
 // relative error ~2^-22 on its argument's exact value); the product
@@ -621,11 +600,10 @@ __device__ __forceinline__ void torque_at_pair(const ArmK& A, LinkTab2 L, CubicL
     rec[9] = fma2(hi2(t6), acc, mul2(fs2, fma2(lo2(t7), rc, neg2(hi2(t8)))));
     rec[8] = v;
     float2 s_, c_;
-    {   // the hardware sine / cosine: absolute error ~1e-6 on these angles (joint
-        // value plus offset, a few radians), an order below the torque tolerance
+    {
       const float2 th = add2(q, hi2(t2));
-      __sincosf(th.x, &s_.x, &c_.x);
-      __sincosf(th.y, &s_.y, &c_.y);
+      fn_sincos(th.x, &s_.x, &c_.x);
+      fn_sincos(th.y, &s_.y, &c_.y);
     }
     rec[6] = c_;
     rec[7] = s_;
