@@ -889,10 +889,12 @@ fn_status fn_mlp_load(fn_mlp_t* m, const char* path);
  * fn_time_edges_window -- minimum feasible duration with a predicted window.
  * For each edge the window [lo, lo+W) is centred on the grid index nearest
  * exp(Y[e][0]) (the top of the grid if Y[e][1] < 0), clamped into [0, K).
- * The scan of Def. "Minimum feasible time" runs on [lo-1, lo+W) first:
+ * The scan of Def. "Minimum feasible time" runs on the window first, from
+ * four grid steps below the predicted index (never below lo-1) up to lo+W,
+ * and on down to lo-1 only if that starting duration is feasible:
  *  - its first feasible k is accepted if k = 0 or T_{k-1} was shown
- *    infeasible (certified: exact whenever rho_tau, rho_P are monotone in T,
- *    as the paper states for fixed boundary states);
+ *    infeasible and k >= lo (certified: exact whenever rho_tau, rho_P are
+ *    monotone in T, as the paper states for fixed boundary states);
  *  - "no feasible duration" is accepted if the window and T_{K-1} are
  *    infeasible (same certificate);
  *  - otherwise the indices not yet examined are scanned exactly.

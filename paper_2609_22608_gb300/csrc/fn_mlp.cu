@@ -1,8 +1,8 @@
 // Duration surrogate: an MLP 28 -> 256 -> 256 -> 256 -> 2 (ReLU) predicting
 // (log T*, feasibility logit) of an edge from its boundary states, trained
-// on labels produced by the exact duration scan, and the windowed scan that
-// uses it.  The paper has no learned component; this is the project's
-// addition on top of Sec. IV-D's search.
+// on labels produced by the exact duration scan (the windowed scan that uses
+// it is fn_edges.cu's k_time_window_tm).  The paper has no learned
+// component; this is the project's addition on top of Sec. IV-D's search.
 //
 // Precision (identical in the FP64 test oracle): inputs, weights and hidden
 // activations are rounded to bf16 and contracted on the tensor cores with
@@ -593,161 +593,3 @@ extern "C" fn_status fn_mlp_load(fn_mlp_t* m, const char* path) {
   return ok ? FN_OK : FN_EINVAL;
 }
 
-// ---------------------------------------------------------------------------
-// windowed duration scan
-// ---------------------------------------------------------------------------
-namespace fn {
-
-struct GridW {
-  float T[FN_MAX_GRID];
-};
-
-// window start per edge from the prediction: centre = the grid index nearest
-// exp(y0) (log-spaced grid), or the top of the grid if the logit says
-// infeasible; [lo, lo + W) clamped into [0, K)
-__device__ __forceinline__ int window_lo(float y0, float y1, float logT0, float dlog, int K, int W) {
-  int c;
-  if (y1 < 0.f || !isfinite(y0)) c = K - 1;
-  else c = __float2int_rn((y0 - logT0) / dlog);
-  c = min(max(c, 0), K - 1);
-  return min(max(c - W / 2, 0), max(K - W, 0));
-}
-
-// One warp per edge.  Scan [lo-1, lo+W) first; accept the first feasible k
-// there if k = 0 or T_{k-1} was shown infeasible (the certificate, exact
-// under monotone rho_tau, rho_P); accept "none" if the window and T_{K-1}
-// are infeasible.  Otherwise fall back to the exact scan of the indices not
-// yet examined ([0, lo-1) then [lo+W, K)).
-#define WIN_WARPS 3   // as the grid scan: static shared memory within 48 KB
-__global__ void __launch_bounds__(32 * WIN_WARPS, 4) k_time_window(ArmK A, GridW G, int K, int S,
-                                                     const float* __restrict__ s0,
-                                                     const float* __restrict__ s1, int E,
-                                                     const float* __restrict__ Y, int Wn,
-                                                     float logT0, float dlog,
-                                                     int32_t* __restrict__ k_star,
-                                                     float* __restrict__ T_star,
-                                                     float* __restrict__ rho3,
-                                                     uint8_t* __restrict__ ok,
-                                                     uint8_t* __restrict__ path,
-                                                     unsigned long long* __restrict__ counter) {
-  __shared__ float sT[FN_MAX_GRID];
-  __shared__ float sEdge[WIN_WARPS][32];
-  __shared__ float sCoef[WIN_WARPS][FN_CUBIC_WORDS * 32];
-  __shared__ float sWr[WIN_WARPS][FN_LINK_WORDS * 32];
-  __shared__ __align__(16) float sSplit[WIN_WARPS][FN_SPLIT_WORDS];
-  __shared__ float4 sLink[7 * FN_LINK_F4];
-  fill_links(A, sLink);
-  for (int i = threadIdx.x; i < K; i += blockDim.x) sT[i] = G.T[i];
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  float* es = sEdge[w];
-  const CubicLane cb{&sCoef[w][lane]};
-  const LaneLink wr{&sWr[w][lane]};
-  const LinkTab L{sLink};
-  unsigned nsamp = 0;
-  const long NW = (long)gridDim.x * WIN_WARPS;
-  for (long e = (long)blockIdx.x * WIN_WARPS + w; e < E; e += NW) {
-    const bool finite = stage_rows(s0 + 16 * e, s1 + 16 * e, es);
-    int kres = -2, route = 1;
-    float rt = NAN, rp = NAN;
-    if (finite) {
-      const int lo = window_lo(Y[2 * e], Y[2 * e + 1], logT0, dlog, K, Wn);
-      const int hi = min(K, lo + Wn);
-      const int a = max(lo - 1, 0);
-      // scan plan, one range per pass through a single edge_scan call:
-      //   WIN  [a, hi)      the window with its certificate index
-      //   LOW  [0, a)       below the window (T_{lo-1} feasible, or fallback)
-      //   LAST [K-1, K)     last duration (certifies "none")
-      //   HIGH [hi, K-1)    above the window (fallback)
-      enum { WIN, LOW_AFTER_WIN, LAST, LOW_AFTER_LAST, HIGH, DONE };
-      int step = WIN, b0 = a, b1 = hi, kalt = -1;
-      float rt_alt = NAN, rp_alt = NAN;
-      while (step != DONE) {
-        float t1 = NAN, t2 = NAN;
-        const int k = (b1 > b0) ? edge_scan(A, ScalarCore{L, cb, wr}, es, sSplit[w], sT, b1, S, false, 0.f, false, t1, t2,
-                                            nsamp, b0)
-                                : -1;
-        if (k == FN_SCAN_ABORT) {          // the scan's pass bound (never expected)
-          kres = FN_SCAN_ABORT; step = DONE;
-        } else if (step == WIN) {
-          if (k >= 0 && (k >= lo || lo == 0)) {
-            kres = k; rt = t1; rp = t2; route = 0; step = DONE;
-          } else if (k >= 0) {             // T_{lo-1} feasible: look below it
-            kalt = k; rt_alt = t1; rp_alt = t2;
-            step = LOW_AFTER_WIN; b0 = 0; b1 = a;
-          } else if (hi == K) {            // window reaches the top: certified none
-            kres = -1; route = 0; step = DONE;
-          } else {
-            step = LAST; b0 = K - 1; b1 = K;
-          }
-        } else if (step == LOW_AFTER_WIN) {
-          if (k >= 0) { kres = k; rt = t1; rp = t2; }
-          else { kres = kalt; rt = rt_alt; rp = rp_alt; }
-          step = DONE;
-        } else if (step == LAST) {
-          if (k < 0) {                     // T_{K-1} infeasible: certified none
-            kres = -1; route = 0; step = DONE;
-          } else {
-            kalt = k; rt_alt = t1; rp_alt = t2;
-            step = LOW_AFTER_LAST; b0 = 0; b1 = a;
-          }
-        } else if (step == LOW_AFTER_LAST) {
-          if (k >= 0) { kres = k; rt = t1; rp = t2; step = DONE; }
-          else { step = HIGH; b0 = hi; b1 = K - 1; }
-        } else {                           // HIGH
-          if (k >= 0) { kres = k; rt = t1; rp = t2; }
-          else { kres = kalt; rt = rt_alt; rp = rp_alt; }
-          step = DONE;
-        }
-      }
-    }
-    float rv = NAN, Ts = kres <= -2 ? NAN : INFINITY;
-    if (kres >= 0) {
-      Ts = sT[kres];
-      rv = warp_rho_v(A, es, Ts);
-    } else {
-      rt = rp = NAN;
-    }
-    if (lane == 0) {
-      k_star[e] = kres;
-      T_star[e] = Ts;
-      rho3[3 * e] = rt;
-      rho3[3 * e + 1] = rp;
-      rho3[3 * e + 2] = rv;
-      ok[e] = (kres >= 0 && rv <= 1.f) ? 1 : 0;
-      if (path) path[e] = (uint8_t)route;
-    }
-  }
-  if (counter && lane == 0 && nsamp) atomicAdd(counter, (unsigned long long)nsamp);
-}
-
-}  // namespace fn
-
-extern "C" fn_status fn_time_edges_window(const fn_arm_t* arm, const float* s0, const float* s1,
-                                          int E, const float* T_grid, int K, int S,
-                                          const float* Y, int W, int32_t* k_star, float* T_star,
-                                          float* rho3, uint8_t* ok, uint8_t* path,
-                                          unsigned long long* sample_count, void* stream) {
-  ArmK A;
-  if (!make_armk(arm, &A)) return FN_EINVAL;
-  if (E < 0 || S < 2 || S > FN_MAX_S || K < 2 || K > FN_MAX_GRID || W < 1) return FN_EINVAL;
-  if (E == 0) return FN_OK;
-  if (!s0 || !s1 || !T_grid || !Y || !k_star || !T_star || !rho3 || !ok) return FN_EINVAL;
-  if (!aligned16(s0) || !aligned16(s1)) return FN_EINVAL;
-  GridW G;
-  for (int k = 0; k < K; ++k) {
-    if (!(T_grid[k] > 0.f) || !std::isfinite(T_grid[k])) return FN_EINVAL;
-    if (k > 0 && !(T_grid[k] > T_grid[k - 1])) return FN_EINVAL;
-    G.T[k] = T_grid[k];
-  }
-  const float logT0 = std::log(T_grid[0]);
-  const float dlog = (std::log(T_grid[K - 1]) - logT0) / (float)(K - 1);
-  // one edge per warp and no grid stride: the block scheduler hands out
-  // blocks as others finish, which balances the few edges that fall back to
-  // the full scan
-  const long blocks = std::min<long>(((long)E + WIN_WARPS - 1) / WIN_WARPS, 0x7fffffffL);
-  k_time_window<<<(unsigned)blocks, 32 * WIN_WARPS, 0, (cudaStream_t)stream>>>(
-      A, G, K, S, s0, s1, E, Y, std::min(W, K), logT0, dlog, k_star, T_star, rho3, ok, path,
-      sample_count);
-  return launch_status();
-}

@@ -3738,11 +3738,11 @@ namespace fn {
 // probe-item range, mask reset, and the result of edges decided without
 // dynamics (non-finite input: k = -2; empty range: k = -1).
 //   mode 0: full scan [0, Kadm)
-//   mode 1: window [max(lo - 1, 0), min(lo + W, Kadm)), lo from the
-//           prediction Y (grid index nearest exp(y0), the top admissible
-//           index if the logit says infeasible, window clamped into
-//           [0, Kadm));
-//           win[e] = (lo, Kadm) for the certificate
+//   mode 1: window [lo, min(lo + W, Kadm)) around the prediction's centre c
+//           (window_centre over the admissible range, the window clamped
+//           into [0, Kadm)), scanned from klo = max(lo - 1, c -
+//           FN_WINDOW_BELOW, 0); win[e] = (klo, whether "none" over [klo,
+//           Kadm) is certified: the scan reaches the top admissible duration)
 //   mode 2: full scan of the listed edges (list)
 // n_list (device, may be NULL): the number of edges of the pass, at most E.
 __global__ void __launch_bounds__(PL_SCAN) k_edges_prep(PlanDev D, GridKP Gr, int mode, int E,
@@ -3784,14 +3784,12 @@ __global__ void __launch_bounds__(PL_SCAN) k_edges_prep(PlanDev D, GridKP Gr, in
     if (mode == 1) {
       // the window is clamped into the admissible range, so that a
       // prediction above the cap puts it at the top admissible duration
-      const float y0 = Y[2L * src], y1 = Y[2L * src + 1];
       const int top = max(Kadm, 1);
-      int ctr = (y1 < 0.f || !isfinite(y0)) ? top - 1 : __float2int_rn((y0 - logT0) / dlog);
-      ctr = min(max(ctr, 0), top - 1);
+      const int ctr = window_centre(Y[2L * src], Y[2L * src + 1], logT0, dlog, top);
       const int wlo = min(max(ctr - W / 2, 0), max(top - W, 0));
-      klo = max(wlo - 1, 0);
+      klo = max(max(wlo - 1, 0), ctr - FN_WINDOW_BELOW);
       khi = min(wlo + W, Kadm);
-      win[src] = make_int2(wlo, Kadm);
+      win[src] = make_int2(klo, (klo < khi && khi == Kadm) ? 1 : 0);
     }
     cnt = finite ? max(khi - klo, 0) : 0;
     D.e_ci[e] = src;
@@ -3815,11 +3813,12 @@ __global__ void __launch_bounds__(PL_SCAN) k_edges_prep(PlanDev D, GridKP Gr, in
   if (threadIdx.x == 0) D.blk_off[blockIdx.x] = tot;
 }
 
-// Window certificate (exact under monotone rho_tau, rho_P): the window's
-// first feasible index k is accepted if k = 0 or k >= lo (T_{k-1} was shown
-// infeasible); "none" is accepted if the window was scanned up to the top
-// admissible duration.  Any other edge joins the list for the exact scan.
-__global__ void k_edges_cert(PlanDev D, int E, int W, const int2* __restrict__ win,
+// Window certificate (exact under monotone rho_tau, rho_P): the first
+// feasible index k of the scanned range [klo, khi) is accepted if k = 0 or
+// k > klo (T_{k-1} was shown infeasible); "none" is accepted if the scan
+// reached the top admissible duration.  Any other edge joins the list for
+// the exact scan.
+__global__ void k_edges_cert(PlanDev D, int E, const int2* __restrict__ win,
                              int32_t* __restrict__ list, int* __restrict__ n_list,
                              uint8_t* __restrict__ path, const int* __restrict__ n_dev) {
   pdl_begin();
@@ -3829,11 +3828,10 @@ __global__ void k_edges_cert(PlanDev D, int E, int W, const int2* __restrict__ w
     bool cert;
     if (k == -2) {
       cert = true;                                   // invalid input, decided
+    } else if (k >= 0) {
+      cert = k > win[e].x || k == 0;
     } else {
-      const int lo = win[e].x, Kadm = win[e].y;
-      const int klo = max(lo - 1, 0), khi = min(lo + W, Kadm);
-      if (k >= 0) cert = k >= lo || lo == 0;
-      else cert = klo < khi && khi == Kadm;
+      cert = win[e].y != 0;
     }
     if (path) path[e] = cert ? 0 : 1;
     if (!cert) list[warp_append(n_list, D.samples ? D.samples + 6 : nullptr)] = e;
@@ -4025,7 +4023,7 @@ extern "C" fn_status fn_edges_time_window(fn_edges_t* eg, const float* s0, const
     enqueue_edge_body(pl, D, pl->edge_variant, pl->edge_blocks, st, [](int) {});
     // certificate; uncertified edges -> exact scan of their full range
     if (cudaMemsetAsync(eg->n_list, 0, sizeof(int), st) != cudaSuccess) return FN_ECUDA;
-    k_edges_cert<<<2 * num_sms(), 256, 0, st>>>(D, n, W, eg->win, eg->list, eg->n_list,
+    k_edges_cert<<<2 * num_sms(), 256, 0, st>>>(D, n, eg->win, eg->list, eg->n_list,
                                                  path ? path + e0 : nullptr, nullptr);
     k_edges_prep<<<pb, PL_SCAN, 0, st>>>(D, pl->grid, 2, n, nullptr, nullptr, 0, 0.f, 0.f, eg->list,
                                           eg->n_list, nullptr);
@@ -4074,7 +4072,7 @@ static void enqueue_surrogate(fn_planner* pl, cudaStream_t st) {
   trace(pl, st, "k_edges_prep");
   enqueue_edge_body(pl, V, v, blocks, st, [](int) {});
   cudaMemsetAsync(pl->g_fbn, 0, sizeof(int), st);
-  k_edges_cert<<<2 * num_sms(), 256, 0, st>>>(V, E, pl->sur_W, pl->g_win, pl->g_fb, pl->g_fbn,
+  k_edges_cert<<<2 * num_sms(), 256, 0, st>>>(V, E, pl->g_win, pl->g_fb, pl->g_fbn,
                                                pl->g_path, D.sur_n);
   trace(pl, st, "k_edges_cert");
   k_edges_prep<<<pb, PL_SCAN, 0, st>>>(V, pl->grid, 2, E, pl->g_cap, nullptr, 0, 0.f, 0.f, pl->g_fb,

@@ -233,16 +233,14 @@ def test_training_reduces_loss_and_window_hits(S, arm):
 
 
 def test_trained_window_saves_work(S, arm):
-    """What training buys, and what the window costs against the exact scan:
+    """What training buys, and what the window saves against the exact scan:
     on the same edges, with identical chosen durations, the trained
     network's window pass needs fewer torque evaluations than the window of
-    an untrained network (whose misses fall back to the full scan).  Against
-    the full scan the window no longer saves work: the scan's end probes come
-    from the end-sample torque split (no evaluation per duration) and its
-    interior probes cover the lowest eight survivors in one pass, so what
-    remains is verifying k* and proving T_{k*-1} infeasible, which the window
-    pays too, plus its certificate scans; it stays within a quarter of the
-    scan's evaluations."""
+    an untrained network (whose misses fall back to the full scan), and
+    fewer than the full scan: the window's scan starts a few grid steps
+    below the predicted index, so the interior probes of the end-sample
+    survivors far below k* (a pass per eight of them in the full scan) are
+    skipped."""
     import torch
     from paper_2609_22608_gb300 import ops
     E, K, Sc = 32768, 128, 32
@@ -251,7 +249,7 @@ def test_trained_window_saves_work(S, arm):
     grid = synth.duration_grid(K)
     lab = S.label_edges(arm, d0, d1, grid, Sc)
     trained = S.MLP(max_batch=4096, seed=0)
-    S.train(trained, arm, d0, d1, lab, grid, epochs=3, batch=4096, lr=2e-3)
+    S.train(trained, arm, d0, d1, lab, grid, epochs=12, batch=2048, lr=2e-3)
     untrained = S.MLP(max_batch=4096, seed=0)
     t0, t1 = synth.random_edges(arm, 4096, 21)
     e0, e1 = dev(t0), dev(t1)
@@ -272,4 +270,4 @@ def test_trained_window_saves_work(S, arm):
     assert (w_tr["k_star"] == full["k_star"]).float().mean().item() > 0.99
     assert (w_un["k_star"] == full["k_star"]).float().mean().item() > 0.99
     assert n_tr < n_un, (n_tr, n_un)
-    assert n_tr <= 1.25 * n_full, (n_tr, n_full)
+    assert n_tr < n_full, (n_tr, n_full)
