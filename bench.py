@@ -368,10 +368,11 @@ def whole_job_rate(units_per_rank, world, ms):
 
 # algorithmic work per unit of each kernel (FLOP; FMA = 2): a distance is
 # 14 subtractions, 14 FMAs and one FMA for the weight; an IK start is 24
-# iterations of (FK 475, residual 48, Jacobian 72, J J^T 237, LDL^T 91,
-# solves 66, update 72) plus a final FK and residual (523)
+# iterations of (FK 475, residual 48, Jacobian 72, J^T J 237, J^T e 72,
+# Gauss-Jordan over the six rows 246, update 6) plus a final FK and residual
+# (523)
 FLOP_PER_PAIR = 44             # one (query, node) distance of the parent search
-FLOP_PER_IK_START = 25987      # one damped-least-squares start, 24 iterations + final check
+FLOP_PER_IK_START = 28267      # one damped-least-squares start, 24 iterations + final check
 
 # DRAM bytes (read + written) per launch from one ncu capture of the kernel on
 # this workload (dram__bytes_read.sum + dram__bytes_write.sum, the mean over

@@ -146,45 +146,6 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
-// 6x6 symmetric positive definite solve by LDL^T (lower triangle of A read),
-// pivots inverted with the hardware reciprocal.  Returns false if a pivot is
-// not positive.
-__device__ __forceinline__ bool ldlt_solve6(const float (&A)[6][6], const float* b, float* x) {
-  float L[6][6], W[6][6], r[6];
-#pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    float d = A[j][j];
-#pragma unroll
-    for (int k = 0; k < j; ++k) d = fmaf(-L[j][k], W[j][k], d);
-    if (!(d > 0.f)) return false;
-    r[j] = rcp_approx(d);
-#pragma unroll
-    for (int i = j + 1; i < 6; ++i) {
-      float w = A[i][j];
-#pragma unroll
-      for (int k = 0; k < j; ++k) w = fmaf(-L[i][k], W[j][k], w);
-      W[i][j] = w;            // L_ij d_j
-      L[i][j] = w * r[j];
-    }
-  }
-  float z[6];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    float t = b[i];
-#pragma unroll
-    for (int k = 0; k < i; ++k) t = fmaf(-L[i][k], z[k], t);
-    z[i] = t;
-  }
-#pragma unroll
-  for (int i = 5; i >= 0; --i) {
-    float t = z[i] * r[i];
-#pragma unroll
-    for (int k = i + 1; k < 6; ++k) t = fmaf(-L[k][i], x[k], t);
-    x[i] = t;
-  }
-  return true;
-}
-
 // unit vectors (e1, e2) completing u to a right-handed frame
 __device__ __forceinline__ void complete_basis(const float* u, float* e1, float* e2) {
   float h[3] = {0.f, 0.f, 1.f};
@@ -207,21 +168,25 @@ __device__ __forceinline__ void complete_basis(const float* u, float* e1, float*
 // target's azimuth; iterates are projected onto
 // the box; accepted when the position residual < 1e-4 m, the rotation
 // residual (half the sum of column cross products) < 1e-3 and the rotation
-// error is under 90 degrees (trace > 1).  The damped system
-// (J J^T + lambda^2 I) y = e is solved by an LDL^T factorisation (six
-// hardware reciprocals on the critical path instead of square roots and
-// divisions); the link rotations use the hardware sine/cosine.  Both are a
-// few ulp from the rounded values, three orders below the residual
-// tolerances that accept a start.
+// error is under 90 degrees (trace > 1).  The damped step
+// dq = J^T (J J^T + lambda^2 I)^-1 e is taken in its equal form
+// (J^T J + lambda^2 I)^-1 J^T e (J is square here: joints 1-6 against the
+// six pose residuals), whose rows belong to the joints; the system is
+// solved by Gauss-Jordan elimination without pivoting (symmetric positive
+// definite), with the hardware reciprocal of each pivot, and the link
+// rotations use the hardware sine/cosine.  Both are a few ulp from the
+// rounded values, three orders below the residual tolerances that accept a
+// start.
 //
 // The work of one iteration is spread over a group of 8 lanes (aligned in
 // the warp; all 32 lanes must call this): lane s < 7 owns joint s, lane 7
 // the flange offset.  The frames are
 // the inclusive product scan of the 8 local transforms [Rx(alpha) Rz(theta),
 // p] (three shuffle steps), lanes 0..5 form the Jacobian columns and share
-// them, and every lane of the group solves the same 6x6 system; lane s < 6
-// then updates its own joint.  Returns (uniformly in the group) whether the
-// start converged; qs is the lane's own final joint value.
+// them, lane s < 6 forms row s of J^T J + lambda^2 I and entry s of J^T e,
+// the six elimination steps take their pivot row from lane k by shuffles,
+// and lane s then updates its own joint.  Returns (uniformly in the group)
+// whether the start converged; qs is the lane's own final joint value.
 __device__ __forceinline__ bool ik_solve_group(const ArmK& A, const float* Rg, const float* pg,
                                                float q7, int st, float& qs) {
   const int s = threadIdx.x & 7;
@@ -295,7 +260,7 @@ __device__ __forceinline__ bool ik_solve_group(const ArmK& A, const float* Rg, c
       er[0] = fmaf(0.5f, x[0], er[0]); er[1] = fmaf(0.5f, x[1], er[1]); er[2] = fmaf(0.5f, x[2], er[2]);
     }
     if (it == FN_IK_ITERS || failed) break;
-    // own Jacobian column (joints 0..5), then everyone's
+    // own Jacobian column c_s (joints 0..5), then everyone's
     float Jc[6];
     {
       const float z[3] = {R[2], R[5], R[8]};
@@ -309,28 +274,43 @@ __device__ __forceinline__ bool ik_solve_group(const ArmK& A, const float* Rg, c
     for (int m = 0; m < 6; ++m)
 #pragma unroll
       for (int i = 0; i < 6; ++i) J[i][m] = __shfl_sync(0xffffffffu, Jc[i], m, 8);
-    float M[6][6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-      for (int j = 0; j <= i; ++j) {
-        float sacc = 0.f;
-#pragma unroll
-        for (int m = 0; m < 6; ++m) sacc = fmaf(J[i][m], J[j][m], sacc);
-        M[i][j] = sacc + (i == j ? FN_IK_LAMBDA * FN_IK_LAMBDA : 0.f);
-      }
+    // lane s < 6 owns row s of N = J^T J + lambda^2 I and g_s = c_s . e
     const float e[6] = {ep[0], ep[1], ep[2], er[0], er[1], er[2]};
-    float y[6];
-    if (!ldlt_solve6(M, e, y)) {
+    float Nr[6], gr = 0.f;
+#pragma unroll
+    for (int n = 0; n < 6; ++n) {
+      float sacc = n == s ? FN_IK_LAMBDA * FN_IK_LAMBDA : 0.f;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) sacc = fmaf(Jc[i], J[i][n], sacc);
+      Nr[n] = sacc;
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) gr = fmaf(Jc[i], e[i], gr);
+    // Gauss-Jordan on the rows: step k takes pivot row k from lane k and
+    // clears column k in every other row (columns below k are no longer
+    // read); every lane sees the same pivots, so a non-positive one fails
+    // the whole group
+    bool pos = true;
+    float piv = 1.f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const float pkk = __shfl_sync(0xffffffffu, Nr[k], k, 8);
+      const float pg = __shfl_sync(0xffffffffu, gr, k, 8);
+      float pr[6];
+#pragma unroll
+      for (int j = k + 1; j < 6; ++j) pr[j] = __shfl_sync(0xffffffffu, Nr[j], k, 8);
+      pos = pos && pkk > 0.f;
+      if (s == k) piv = pkk;
+      const float f = s == k ? 0.f : Nr[k] * rcp_approx(pkk);
+#pragma unroll
+      for (int j = k + 1; j < 6; ++j) Nr[j] = fmaf(-f, pr[j], Nr[j]);
+      gr = fmaf(-f, pg, gr);
+    }
+    if (!pos) {
       failed = true;
       break;
     }
-    if (s < 6) {
-      float dq = 0.f;
-#pragma unroll
-      for (int i = 0; i < 6; ++i) dq = fmaf(Jc[i], y[i], dq);
-      qj = fminf(fmaxf(qj + dq, lo), hi);
-    }
+    if (s < 6) qj = fminf(fmaxf(fmaf(gr, rcp_approx(piv), qj), lo), hi);
   }
   qs = qj;
   if (failed || !(norm3(ep) < FN_IK_POS_TOL && norm3(er) < FN_IK_ROT_TOL)) return false;
