@@ -404,6 +404,8 @@ def roofline_from_trace(traced, work, workload="iteration"):
     units = {"k_plan_expand": (work["probe"], FLOP_PER_SAMPLE,
                                "torque evaluations (the end-sample split, three per edge end)"),
              "k_plan_mprobe": (work["mprobe"], FLOP_PER_SAMPLE, "torque evaluations"),
+             "k_plan_edges_tm": (work["probe"] + work["mprobe"] + work["verify"], FLOP_PER_SAMPLE,
+                                 "torque evaluations (splits, probes and checks)"),
              "k_plan_vstage": (None, FLOP_PER_SAMPLE, "torque evaluations"),
              "k_plan_knn": (work["knn_pairs"], FLOP_PER_PAIR, "(query, node) pairs"),
              "k_plan_sample": (work["ik_starts"], FLOP_PER_IK_START,
@@ -431,7 +433,7 @@ def roofline_from_trace(traced, work, workload="iteration"):
                     "flop_per_unit": f})
     # the edge-timing kernels (the RNEA hot path) for reference
     edge = {}
-    for k in ("k_plan_expand", "k_plan_mprobe"):
+    for k in ("k_plan_expand", "k_plan_mprobe", "k_plan_edges_tm"):
         if k in tab:
             n, f, _ = units[k]
             edge[k] = {"ms": tab[k]["ms"], "tflops": n * f / (tab[k]["ms"] / 1e3) / 1e12}
@@ -1044,8 +1046,15 @@ def _anytime_run(arm, pr, prob, flags, cycles=200):
     if flags & (P.FN_PLAN_DENSITY | P.FN_PLAN_CHORD):
         pl.set_sampler()
     stream = torch.cuda.Stream()
+    # the schedule is tuned on a grown tree (a tree of one node lists few
+    # edges, where a single warp-per-edge launch wins but the steady state's
+    # edge batches do not): grow it for a quarter of the run, tune, restart
     pl.reset([prob], stream=stream)
-    tuned = pl.autotune([prob], 0, 0, reps=2, stream=stream)
+    pl.capture(flags, stream=stream)
+    for c in range(cycles // 4):
+        pl.replay_async([prob], c, stream=stream)
+        pl.result()
+    tuned = pl.autotune([prob], cycles // 4, 0, reps=2, stream=stream)
     pl.reset([prob], stream=stream)
     pl.capture(flags, stream=stream)
     ms, nodes, added, formed, status = [], [], [], [], 0

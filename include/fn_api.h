@@ -531,15 +531,24 @@ fn_status fn_plan_result(fn_planner_t* pl, fn_rendezvous_t* out);
 
 /* Schedule autotuner of the planner (the work pattern of an iteration is
  * data dependent, so variants are timed on the caller's own problems): runs
- * the iteration's sampling and parent search once, then times every compiled
- * register-budget variant of the persistent edge kernel on that edge batch
- * (`reps` runs each after a warm-up) and keeps the fastest for this planner
- * and later planners of the same shape.  The trees are not modified.
- * chosen: host (may be NULL); variant_ms: host [3] (may be NULL).
+ * the iteration's sampling and parent search once, then times every
+ * schedule of the edge phase on that edge batch (`reps` runs each after a
+ * warm-up) and keeps the fastest for this planner and later planners of the
+ * same shape.  Schedules 0-2: the packed stages (lanes over probe and
+ * verification items) at three register budgets; 3: one warp per edge on
+ * the paired core with its records in tensor memory, one launch.  The trees
+ * are not modified.  chosen: host (may be NULL); variant_ms: host [4] (may
+ * be NULL).
  * Synchronous. */
 fn_status fn_planner_autotune(fn_planner_t* pl, const fn_problem_t* probs, int iter,
                               unsigned flags, int reps, int* chosen, float* variant_ms,
                               void* stream);
+
+/* Sets the planner's edge-phase schedule (the index fn_planner_autotune
+ * reports: 0-2 the packed stages, 3 one warp per edge on the paired core)
+ * for its later iterations and captures; a graph captured earlier keeps the
+ * schedule it was captured with.  FN_EINVAL for an index outside [0, 4). */
+fn_status fn_planner_set_schedule(fn_planner_t* pl, int variant);
 
 /* Durations in ms of the last fn_plan_iteration's phases, from CUDA events
  * recorded on its stream: [0] schedule, [1] sample, [2] parents (kNN),

@@ -10,7 +10,7 @@
 #include <unordered_map>
 
 #include "edge_core.cuh"
-#include "fn_tmem.cuh"
+#include "tm_scan.cuh"
 #include "fn_internal.h"
 #include "fn_tune.h"
 
@@ -70,36 +70,14 @@ __global__ void __launch_bounds__(32 * EDGE_WARPS, MINB)
 }
 
 // The paired scan (two samples per lane, PairCore) with the per-link records
-// of the torque evaluation in tensor memory: one CTA of TM_WARPS = 12 warps
-// per SM holds all 512 columns; warp w uses lane quarter w % 4 and the
-// 144-column block 144 (w / 4) (three warps per quarter).  CTA b owns a
-// contiguous range of the edges, which its warps claim from a shared counter
-// in runs of up to TM_GROUP, shorter towards the end (a run is the range
-// left over twice the CTA's warps, at least two edges): an edge's cost
-// varies with the passes it needs, and shrinking runs keep the warps busy
-// until the range is done.  A warp stages its run, computes the end-sample
-// splits in one pass (split_group: up to sixty (edge, end, part) items on
-// the lanes' two halves), then scans the edges one by one.  The coefficients, staged edges,
-// splits, the paired link table and the grid sit in dynamic shared memory,
-// sized above half of the SM's so that no second CTA (which would wait for
-// the columns) is placed on the SM.
-#define TM_WARPS 12
-#define TM_GROUP 10
-constexpr int kTmCols = 512;
-constexpr size_t kTmCoef = (size_t)TM_WARPS * FN_CUBIC_WORDS * 32 * sizeof(float2);
-constexpr size_t kTmEdge = (size_t)TM_WARPS * TM_GROUP * 32 * sizeof(float);
-constexpr size_t kTmSplit = (size_t)TM_WARPS * TM_GROUP * FN_SPLIT_WORDS * sizeof(float);
-constexpr size_t kTmLink = 7 * FN_LINK2_F4 * sizeof(float4);
-constexpr size_t kTmGrid = FN_MAX_GRID * sizeof(float);
-constexpr size_t kTmUsed = kTmCoef + kTmEdge + kTmSplit + kTmLink + kTmGrid + 16;   // + s_tmem, s_next
-constexpr size_t kTmSmem = 140 * 1024;
-static_assert(kTmUsed <= kTmSmem, "tensor-memory scan: shared-memory layout");
-static_assert(2 * (kTmSmem + 1024) > 233472, "one CTA per SM");
-static_assert(kTmCoef % 16 == 0 && kTmEdge % 16 == 0 && kTmSplit % 16 == 0, "16-byte carve");
-static_assert(FN_SPLIT_WORDS * sizeof(float) % 16 == 0, "16-byte split slots");
-static_assert(TM_GROUP <= 10, "split_group takes at most ten edges");
-static_assert(3 * FN_TM_COLS_PER_WARP <= kTmCols, "three warps per lane quarter");
-
+// of the torque evaluation in tensor memory, on tm_scan.cuh's block layout
+// (one CTA of TM_WARPS warps per SM).  CTA b owns a contiguous range of the
+// edges, which its warps claim in runs that shrink towards the end of the
+// range (tm_claim): an edge's cost varies with the passes it needs, and
+// shrinking runs keep the warps busy until the range is done.  A warp
+// stages its run, computes the end-sample splits in one pass (split_group:
+// up to sixty (edge, end, part) items on the lanes' two halves), then scans
+// the edges one by one.
 __global__ void __launch_bounds__(32 * TM_WARPS, 1)
     k_time_edges_tm(ArmK A, GridK G, int K, int S, int mode, const float* __restrict__ s0,
                     const float* __restrict__ s1, int E, const float* __restrict__ Tparam,
@@ -107,43 +85,27 @@ __global__ void __launch_bounds__(32 * TM_WARPS, 1)
                     float* __restrict__ rho3, uint8_t* __restrict__ ok,
                     unsigned long long* __restrict__ counter) {
   extern __shared__ float4 tm_smem[];
-  char* base = reinterpret_cast<char*>(tm_smem);
-  float2* sCoef = reinterpret_cast<float2*>(base);
-  float* sEdge = reinterpret_cast<float*>(base + kTmCoef);
-  float* sSplit = reinterpret_cast<float*>(base + kTmCoef + kTmEdge);
-  float4* sLink = reinterpret_cast<float4*>(base + kTmCoef + kTmEdge + kTmSplit);
-  float* sT = reinterpret_cast<float*>(base + kTmCoef + kTmEdge + kTmSplit + kTmLink);
-  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(base + kTmCoef + kTmEdge + kTmSplit + kTmLink +
-                                                 kTmGrid);
-  int* s_next = reinterpret_cast<int*>(s_tmem + 1);   // next unclaimed edge of the CTA's range
+  const TmBlock blk(tm_smem);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  fill_links2(A, sLink);
+  float* sT = blk.grid;
+  fill_links2(A, blk.link);
   const long per = ((long)E + gridDim.x - 1) / gridDim.x;
   const long r_lo = std::min<long>((long)blockIdx.x * per, E), r_hi = std::min<long>(r_lo + per, E);
-  if (threadIdx.x == 0) *s_next = 0;
+  if (threadIdx.x == 0) *blk.next = 0;
   if (mode == FN_MODE_FULL)
     for (int i = threadIdx.x; i < K; i += blockDim.x) sT[i] = G.T[i];
-  if (w == 0) tmem_alloc(s_tmem, kTmCols);
+  if (w == 0) tmem_alloc(blk.tmem, kTmCols);
   tmem_sync_block();
-  const uint32_t tmem = *s_tmem;
-  const PairCore<TmemStash> core{
-      LinkTab2{sLink}, CubicLane2{sCoef + w * FN_CUBIC_WORDS * 32 + lane},
-      TmemStash{tmem + ((uint32_t)((w & 3) * 32) << 16) + FN_TM_COLS_PER_WARP * (uint32_t)(w >> 2)}};
-  float* es_g = sEdge + TM_GROUP * 32 * w;
-  float* split_g = sSplit + TM_GROUP * FN_SPLIT_WORDS * w;
+  const uint32_t tmem = *blk.tmem;
+  const PairCore<TmemStash> core = blk.core(tmem, w, lane);
+  float* es_g = blk.edges_of(w);
+  float* split_g = blk.splits_of(w);
   const bool fixed = mode == FN_MODE_FIXED;
   const int len = (int)(r_hi - r_lo);
   unsigned nsamp = 0;
   for (;;) {
-    int first = 0, n = 0;
-    if (lane == 0) {   // claim a run: about (range left) / (2 TM_WARPS), 2..TM_GROUP edges
-      const int seen = atomicAdd(s_next, 0);
-      const int want = std::min(TM_GROUP, std::max(2, (len - seen) / (2 * TM_WARPS)));
-      first = atomicAdd(s_next, want);
-      n = std::max(0, std::min(want, len - first));
-    }
-    first = __shfl_sync(0xffffffffu, first, 0);
-    n = __shfl_sync(0xffffffffu, n, 0);
+    int n;
+    const int first = tm_claim(blk.next, len, n);
     if (n == 0) break;                               // warp-uniform
     const long e0 = r_lo + first;
     unsigned fin = 0u;
@@ -199,41 +161,25 @@ __global__ void __launch_bounds__(32 * TM_WARPS, 1)
                      uint8_t* __restrict__ ok, uint8_t* __restrict__ path,
                      unsigned long long* __restrict__ counter) {
   extern __shared__ float4 tm_smem[];
-  char* base = reinterpret_cast<char*>(tm_smem);
-  float2* sCoef = reinterpret_cast<float2*>(base);
-  float* sEdge = reinterpret_cast<float*>(base + kTmCoef);
-  float* sSplit = reinterpret_cast<float*>(base + kTmCoef + kTmEdge);
-  float4* sLink = reinterpret_cast<float4*>(base + kTmCoef + kTmEdge + kTmSplit);
-  float* sT = reinterpret_cast<float*>(base + kTmCoef + kTmEdge + kTmSplit + kTmLink);
-  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(base + kTmCoef + kTmEdge + kTmSplit + kTmLink +
-                                                 kTmGrid);
-  int* s_next = reinterpret_cast<int*>(s_tmem + 1);
+  const TmBlock blk(tm_smem);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  fill_links2(A, sLink);
+  float* sT = blk.grid;
+  fill_links2(A, blk.link);
   const long per = ((long)E + gridDim.x - 1) / gridDim.x;
   const long r_lo = std::min<long>((long)blockIdx.x * per, E), r_hi = std::min<long>(r_lo + per, E);
-  if (threadIdx.x == 0) *s_next = 0;
+  if (threadIdx.x == 0) *blk.next = 0;
   for (int i = threadIdx.x; i < K; i += blockDim.x) sT[i] = G.T[i];
-  if (w == 0) tmem_alloc(s_tmem, kTmCols);
+  if (w == 0) tmem_alloc(blk.tmem, kTmCols);
   tmem_sync_block();
-  const uint32_t tmem = *s_tmem;
-  const PairCore<TmemStash> core{
-      LinkTab2{sLink}, CubicLane2{sCoef + w * FN_CUBIC_WORDS * 32 + lane},
-      TmemStash{tmem + ((uint32_t)((w & 3) * 32) << 16) + FN_TM_COLS_PER_WARP * (uint32_t)(w >> 2)}};
-  float* es_g = sEdge + TM_GROUP * 32 * w;
-  float* split_g = sSplit + TM_GROUP * FN_SPLIT_WORDS * w;
+  const uint32_t tmem = *blk.tmem;
+  const PairCore<TmemStash> core = blk.core(tmem, w, lane);
+  float* es_g = blk.edges_of(w);
+  float* split_g = blk.splits_of(w);
   const int len = (int)(r_hi - r_lo);
   unsigned nsamp = 0;
   for (;;) {
-    int first = 0, n = 0;
-    if (lane == 0) {   // claim a run as k_time_edges_tm does
-      const int seen = atomicAdd(s_next, 0);
-      const int want = std::min(TM_GROUP, std::max(2, (len - seen) / (2 * TM_WARPS)));
-      first = atomicAdd(s_next, want);
-      n = std::max(0, std::min(want, len - first));
-    }
-    first = __shfl_sync(0xffffffffu, first, 0);
-    n = __shfl_sync(0xffffffffu, n, 0);
+    int n;
+    const int first = tm_claim(blk.next, len, n);
     if (n == 0) break;                               // warp-uniform
     const long e0 = r_lo + first;
     unsigned fin = 0u;

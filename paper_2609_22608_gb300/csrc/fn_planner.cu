@@ -27,10 +27,12 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "edge_core.cuh"
 #include "fn_internal.h"
+#include "tm_scan.cuh"
 #include "fn_kin.cuh"
 #include "nary_core.cuh"
 #include "fn_mlp_tc.h"
@@ -91,6 +93,7 @@ struct Sched {
   unsigned prep_done; // blocks of k_plan_eprep finished (zero between iterations)
   unsigned att_done;  // blocks of k_attach_scan finished (zero between iterations)
   unsigned prune_done;  // blocks of k_prune_walk finished (zero between iterations)
+  unsigned tm_done;    // CTAs of k_plan_edges_tm finished (zero between bodies)
   int n_free_edges;   // free edges of all problems (the queue's first part)
   int n_edges;        // all edges
   // parent-search items (problem, query group, split), one per warp, in two
@@ -704,10 +707,16 @@ __global__ void __launch_bounds__(32 * PL_KNN_WARPS) k_plan_knn(PlanDev D, int k
   float4* ring = knn_ring + (long)w * PL_KNN_RING * 7 * 32 + lane;
   const float2 w2 = make_float2(D.w_vel, D.w_vel);
   Sched* Sw = D.sched;
-  for (;;) {   // each warp claims items until none are left
-    int item = 0;
-    if (lane == 0) item = atomicAdd(&Sw->knn_head[kind], 1);
-    item = __shfl_sync(0xffffffffu, item, 0);
+  // warp g's first item is g; later ones are claimed from a counter past the
+  // grid's warps (a claim per warp at launch would queue every warp on one
+  // address)
+  const int nw = gridDim.x * PL_KNN_WARPS;
+  for (int round = 0;; ++round) {
+    int item = blockIdx.x * PL_KNN_WARPS + w;
+    if (round > 0) {
+      if (lane == 0) item = nw + atomicAdd(&Sw->knn_head[kind], 1);
+      item = __shfl_sync(0xffffffffu, item, 0);
+    }
     if (item >= items) break;
     int p, ns, split, b0, B;
     if (kind == 0) {   // free queries [G, B) of problem p, PL_KNN_QW per item
@@ -1565,6 +1574,97 @@ __global__ void __launch_bounds__(128) k_plan_vselect(PlanDev D, ArmK A, GridKP 
     }
     D.cur_k[e] = k2;
     next[warp_append(&S->n_pend[list ^ 1])] = e;
+  }
+}
+
+// The warp-per-edge edge body (schedule variant kPairEdgeVariant): the
+// edges k_plan_eprep listed for dynamics are timed on the paired core with
+// its records in tensor memory (tm_scan.cuh), a warp per edge in shrinking
+// runs as the standalone k_time_edges_tm: the end-sample splits of a run in
+// one pass, then per edge the scan of Def. "Minimum feasible time" over its
+// admissible prefix (free edges: T_k <= the cap T_p) or the check at its
+// fixed duration T_p (goal edges, Algorithm 1), and finish_edge's velocity
+// and clearance tests.  One launch stands for the packed body's stages
+// (expand, probes, verification stages, leftovers); the autotuner takes it
+// where an iteration's edges are few enough that the stages' chain of
+// launches, not their work, sets the time.  The CTA that finishes last
+// empties the dynamics list for the next body.
+__global__ void __launch_bounds__(32 * TM_WARPS, 1) k_plan_edges_tm(PlanDev D, ArmK A,
+                                                                   GridKP Gr) {
+  pdl_begin();
+  extern __shared__ float4 tm_smem[];
+  const TmBlock blk(tm_smem);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  Sched* S = D.sched;
+  const int E = min(S->n_dyn, D.Emax);
+  float* sT = blk.grid;
+  fill_links2(A, blk.link);
+  for (int i = threadIdx.x; i < D.K; i += blockDim.x) sT[i] = Gr.T[i];
+  const int per = (E + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int r_lo = min((int)blockIdx.x * per, E), r_hi = min(r_lo + per, E);
+  if (threadIdx.x == 0) *blk.next = 0;
+  if (w == 0) tmem_alloc(blk.tmem, kTmCols);
+  tmem_sync_block();
+  const uint32_t tmem = *blk.tmem;
+  const PairCore<TmemStash> core = blk.core(tmem, w, lane);
+  float* es_g = blk.edges_of(w);
+  float* split_g = blk.splits_of(w);
+  unsigned nsplit = 0, nscan = 0;
+  for (;;) {
+    int n;
+    const int first = tm_claim(blk.next, r_hi - r_lo, n);
+    if (n == 0) break;                               // warp-uniform
+    const int32_t* run = D.dyn_list + r_lo + first;
+    unsigned fin = 0u;
+    for (int i = 0; i < n; ++i) {
+      const int e = run[i];
+      const int p = D.e_ci[e] / D.BM;
+      if (stage_rows(D.st + ((long)p * D.NC + D.e_par[e]) * 16, D.cand + (long)D.e_ci[e] * 16,
+                     es_g + 32 * i))
+        fin |= 1u << i;
+    }
+    split_group(A, core, es_g, split_g, n, nsplit);
+    for (int i = 0; i < n; ++i) {
+      const int e = run[i];
+      float* es = es_g + 32 * i;
+      const bool goal = D.e_j[e] & 0x80;
+      const float Tp = D.e_Tp[e];
+      int k = -1;
+      float rt, rp;
+      if ((fin >> i) & 1u) {
+        k = goal ? edge_scan(A, core, es, nullptr, sT, 0, D.S, true, Tp, false, rt, rp, nscan)
+                 : edge_scan(A, core, es, split_g + FN_SPLIT_WORDS * i, sT,
+                             grid_prefix(sT, D.K, Tp), D.S, false, 0.f, false, rt, rp, nscan);
+      }
+      if (k == FN_SCAN_ABORT) {
+        if (lane == 0) atomicOr(D.status + D.e_ci[e] / D.BM, FN_PLAN_ERR_SCAN);
+        k = -1;
+      }
+      if (k >= 0) {
+        finish_edge(D, A, e, k, goal ? Tp : sT[k], es);
+      } else if (lane == 0) {
+        long ei;
+        bool g;
+        edge_slot(D, e, ei, g);
+        D.e_ok[ei] = 0;
+        D.e_T[ei] = goal ? Tp : INFINITY;
+        D.e_rv[ei] = NAN;
+        D.e_k[ei] = -1;
+      }
+    }
+  }
+  if (D.samples && lane == 0) {
+    if (nsplit) atomicAdd(D.samples + 0, (unsigned long long)nsplit);
+    if (nscan) atomicAdd(D.samples + 1, (unsigned long long)nscan);
+  }
+  tmem_sync_block();   // every warp's tensor-memory accesses precede the release
+  if (w == 0) tmem_dealloc(tmem, kTmCols);
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&S->tm_done, 1u) == gridDim.x - 1) {   // every CTA has read the list
+      S->n_dyn = 0;
+      S->tm_done = 0u;
+    }
   }
 }
 
@@ -2975,6 +3075,19 @@ static int vstages(const PlanDev& D) { return D.vstages >= 2 ? 2 : 1; }
 // the packed edge phase after the per-edge prep: item scan, probe, verify
 // (over the edges of the view D; mark(i) records the phase boundaries when
 // timing)
+// the warp-per-edge body's shared-memory request, set once per device
+static bool plan_edges_tm_ready() {
+  static std::once_flag once[64];
+  static bool ok[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::call_once(once[dev & 63], [&] {
+    ok[dev & 63] = cudaFuncSetAttribute(k_plan_edges_tm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kTmSmem) == cudaSuccess;
+  });
+  return ok[dev & 63];
+}
+
 template <class Mark>
 static void enqueue_edge_body(fn_planner* pl, const PlanDev& D, int v, int blocks, cudaStream_t st,
                               Mark&& mark, bool scan = true) {
@@ -3012,6 +3125,13 @@ static void enqueue_edges(fn_planner* pl, int v, int blocks, cudaStream_t st, Ma
   const int eb = (D.Emax + PL_SCAN - 1) / PL_SCAN;
   pl_launch(k_plan_eprep, eb, PL_SCAN, 0, st, D, pl->grid);
   trace(pl, st, "k_plan_eprep");
+  if (v == kPairEdgeVariant && plan_edges_tm_ready()) {   // the warp-per-edge body
+    mark(4);
+    pl_launch(k_plan_edges_tm, num_sms(), 32 * TM_WARPS, kTmSmem, st, D, pl->arm, pl->grid);
+    trace(pl, st, "k_plan_edges_tm");
+    mark(5);
+    return;
+  }
   enqueue_edge_body(pl, D, v, blocks, st, mark, false);
 }
 
@@ -3682,6 +3802,13 @@ extern "C" fn_status fn_planner_sample_count(fn_planner_t* pl, unsigned long lon
 // batch (`reps` runs each, after one warm-up) and keeps the fastest for this
 // planner and for planners created later with the same shape.  The tree is
 // not modified.  chosen: host (may be NULL); variant_ms: host [3] (may be NULL).
+extern "C" fn_status fn_planner_set_schedule(fn_planner_t* pl, int variant) {
+  if (!pl || variant < 0 || variant >= kPlanEdgeVariants) return FN_EINVAL;
+  pl->edge_variant = variant;
+  pl->edge_blocks = pl->cfg.edge_blocks > 0 ? pl->cfg.edge_blocks : plan_edge_blocks(pl, variant);
+  return FN_OK;
+}
+
 extern "C" fn_status fn_planner_autotune(fn_planner_t* pl, const fn_problem_t* probs, int iter,
                                          unsigned flags, int reps, int* chosen,
                                          float* variant_ms, void* stream) {
@@ -3699,7 +3826,7 @@ extern "C" fn_status fn_planner_autotune(fn_planner_t* pl, const fn_problem_t* p
   if ((rc = launch_status()) != FN_OK) return rc;
   float best_ms = INFINITY;
   int best = pl->edge_variant;
-  for (int v = 0; v < kEdgeVariants; ++v) {
+  for (int v = 0; v < kPlanEdgeVariants; ++v) {
     const int blocks = pl->cfg.edge_blocks > 0 ? pl->cfg.edge_blocks : plan_edge_blocks(pl, v);
     float tot = 0.f;
     for (int r = 0; r <= reps; ++r) {

@@ -17,6 +17,9 @@ constexpr int kDefaultEdgeVariant = 1;
 // memory (its default); kernels without it map that index to their default
 constexpr int kPairEdgeVariant = 3;
 constexpr int kTimeEdgeVariants = 4;
+// the planner's edge body: the packed stages at the three register budgets,
+// and (kPairEdgeVariant) one warp-per-edge launch on the paired core
+constexpr int kPlanEdgeVariants = 4;
 
 int tuned_variant(int kind, long n, int K, int S);
 void set_tuned_variant(int kind, long n, int K, int S, int v);

@@ -109,6 +109,7 @@ def _bind():
     L.fn_planner_set_surrogate.argtypes = [vp, vp, i32]
     L.fn_planner_work_counts.argtypes = [vp, vp, i32, i32]
     L.fn_planner_autotune.argtypes = [vp, vp, i32, C.c_uint, i32, vp, vp, vp]
+    L.fn_planner_set_schedule.argtypes = [vp, i32]
     L.fn_planner_incumbent_path.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp]
     L.fn_planner_set_sampler.argtypes = [vp, C.POINTER(FnSamplerCfg)]
     L.fn_planner_set_density.argtypes = [vp, i32, C.POINTER(FnDensity), vp]
@@ -123,6 +124,7 @@ def _bind():
               "fn_plan_replay", "fn_plan_replay_async", "fn_plan_result", "fn_planner_get_tree", "fn_planner_get_candidates",
               "fn_planner_get_parents", "fn_planner_get_edges", "fn_planner_get_node_params",
               "fn_planner_sample_count", "fn_planner_phase_ms", "fn_planner_autotune",
+              "fn_planner_set_schedule",
               "fn_planner_kernel_ms", "fn_planner_work_counts", "fn_planner_set_surrogate",
               "fn_planner_incumbent_path", "fn_planner_set_sampler", "fn_planner_set_density",
               "fn_planner_get_density", "fn_planner_set_candidate_params",
@@ -320,11 +322,15 @@ class Planner:
         """fn_planner_autotune: returns (chosen variant, ms per variant)."""
         self._stage(probs)
         chosen = C.c_int()
-        ms = (C.c_float * 3)()
+        ms = (C.c_float * 4)()
         check(lib().fn_planner_autotune(self.h, self._probs, int(it), int(flags), int(reps),
                                         C.byref(chosen), ms, self._stream(stream)),
               "fn_planner_autotune")
         return chosen.value, [float(x) for x in ms]
+
+    def set_schedule(self, variant):
+        """fn_planner_set_schedule: the edge phase's schedule for later iterations."""
+        check(lib().fn_planner_set_schedule(self.h, int(variant)), "fn_planner_set_schedule")
 
     PHASES = ("schedule", "sample", "parents", "edge_prep", "probe", "verify", "attach",
               "prune", "output")

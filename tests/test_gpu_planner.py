@@ -40,12 +40,14 @@ def make_case(arm, orc, seed, N=300, n_goal_draw=512, n_free=96, obstacles=None)
                 T_req=T_req, v_rel=v_rel, obstacles=obstacles)
 
 
-def run_pair(P, orc, arm, case, k=5, prune=False, obstacles=None, bm=None):
+def run_pair(P, orc, arm, case, k=5, prune=False, obstacles=None, bm=None, sched=None):
     grid = synth.duration_grid(K_GRID)
     states, t, parent = case["tree"]
     N = states.shape[0]
     B = case["cand"].shape[0]
     pl = P.Planner(arm, P=1, n_cap=N + B + 8, b_max=bm or B, k=k, K=K_GRID, S=S_COLL, S_clear=8)
+    if sched is not None:
+        pl.set_schedule(sched)
     prob = P.problem_struct(case["pr"], B, case["n_goal"], root=case["root"], obstacles=obstacles)
     pl.reset([prob])
     pl.load_tree(0, states, t, parent)
@@ -62,13 +64,17 @@ def run_pair(P, orc, arm, case, k=5, prune=False, obstacles=None, bm=None):
     return out, gtree, rtree, rinc, det, grid
 
 
-@pytest.mark.parametrize("seed,bm", [(0, None), (1, None), (0, 4096), (1, 4096)])
-def test_plan_round_parity(P, orc, arm, seed, bm):
+@pytest.mark.parametrize("seed,bm,sched", [(0, None, None), (1, None, None), (0, 4096, None),
+                                           (1, 4096, None), (0, None, 3), (1, None, 3),
+                                           (2, None, 0)])
+def test_plan_round_parity(P, orc, arm, seed, bm, sched):
     """One round of Algorithm 1's body against the oracle.  bm = 4096: a
-    planner for large batches, whose attach runs over many blocks."""
+    planner for large batches, whose attach runs over many blocks; sched: the
+    edge phase's schedule (3: one warp per edge on the paired core, 0: the
+    packed stages at the largest register budget)."""
     case = make_case(arm, orc, seed)
     assert case["n_goal"] >= 3
-    out, gtree, rtree, rinc, det, grid = run_pair(P, orc, arm, case, bm=bm)
+    out, gtree, rtree, rinc, det, grid = run_pair(P, orc, arm, case, bm=bm, sched=sched)
     N = case["tree"][0].shape[0]
     bad = compare_round(orc, arm, case, gtree, rtree, det, N, grid)
     assert not bad, f"candidates attached differently without a near-margin edge: {bad[:5]}"
@@ -162,10 +168,11 @@ def test_surrogate_round_matches_plain_round(P, orc, arm, trained):
     mlp.close()
 
 
-def test_plan_round_with_obstacles(P, orc, arm):
+@pytest.mark.parametrize("sched", [None, 3])
+def test_plan_round_with_obstacles(P, orc, arm, sched):
     obs = synth.obstacles(5, 3)
     case = make_case(arm, orc, 2, N=200, n_free=64)
-    out, gtree, rtree, rinc, det, grid = run_pair(P, orc, arm, case, obstacles=obs)
+    out, gtree, rtree, rinc, det, grid = run_pair(P, orc, arm, case, obstacles=obs, sched=sched)
     N = case["tree"][0].shape[0]
     bad = compare_round(orc, arm, case, gtree, rtree, det, N, grid)
     assert not bad
@@ -446,7 +453,7 @@ def test_autotune_keeps_results(P, orc, arm):
         pl.load_tree(0, states, t, parent)
         if tune:
             chosen, ms = pl.autotune([prob], 0, 0, reps=2)
-            assert 0 <= chosen < 3 and all(m > 0 for m in ms)
+            assert 0 <= chosen < 4 and len(ms) == 4 and all(m > 0 for m in ms)
         pl.iterate([prob], 0, 0)
         trees.append(pl.get_tree(0))
         pl.close()
