@@ -121,6 +121,7 @@ struct PlanDev {  // device pointers, passed by value to the kernels
   int32_t* att_tot;   // [P] candidates attached
   unsigned long long* att_key;  // [P] best new rendezvous: ordered J (high), ~node (low)
   int vstages;        // packed verification stages (1 or 2)
+  int goal_split;     // 1: goal edges are checked by k_plan_goal_edges, not the packed body
   float w_vel, vel_frac, margin;
   float* st;          // [P][NC][16]
   float* t;           // [P][NC]
@@ -352,7 +353,7 @@ __global__ void k_plan_schedule(PlanDev D) {
   S->knn_off[0][D.P] = ko;
   S->knn_off[1][D.P] = kg;
   S->n_free_edges = fo;
-  S->n_edges = fo + go;
+  S->n_edges = fo + (D.goal_split ? 0 : go);
   S->knn_items[0] = ko;
   S->knn_items[1] = kg;
   S->knn_head[0] = 0;
@@ -470,15 +471,9 @@ __device__ __forceinline__ void goal_query(const PlanDev& D, int p, int b, bool 
 //   role 0: a free slot is drawn by lane 0; the warps past the slots prepare
 //           the parent search (parents_prep: tree mirror, empty lists);
 //   role 1: a goal slot is decoded by the whole warp (sample_goal).
-// With `late`, a role-1 launch triggers its dependents at once and waits for
-// its predecessor (the free queries' parent search, which it neither reads
-// nor writes) only before it exits, so that the goal chart's IK runs beside
-// that search while the next launch still sees both complete.
 __global__ void __launch_bounds__(128) k_plan_sample(PlanDev D, ArmK A, long nslots,
-                                                     int prep_warps, int dens, int role,
-                                                     int late) {
-  if (late) pdl_trigger();
-  else pdl_begin();
+                                                     int prep_warps, int dens, int role) {
+  pdl_begin();
   const long gid = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (role == 0) {
@@ -506,7 +501,6 @@ __global__ void __launch_bounds__(128) k_plan_sample(PlanDev D, ArmK A, long nsl
     const int B = min(max(D.prob[p].batch, 0), D.BM);
     if (b < min(max(D.prob[p].n_goal, 0), B)) sample_goal(D, A, p, b, dens);   // warp-uniform
   }
-  if (late) pdl_wait();
 }
 
 // A goal slot: every lane decodes the chart pose, lane groups 0-3 (8 lanes
@@ -1517,13 +1511,9 @@ __device__ __forceinline__ float warp_clearance(const PlanDev& D, const ArmK& A,
 // warp-wide end of an edge whose duration T passed (es: its two states
 // staged in shared memory): rho_v at T (lane = joint), the clearance samples
 // (lane = sample), then Clear
-__device__ __forceinline__ void finish_edge(const PlanDev& D, const ArmK& A, int e, int k, float T,
-                                            const float* es) {
+__device__ __forceinline__ void finish_slot(const PlanDev& D, const ArmK& A, long ei, int p, int k,
+                                            float T, const float* es) {
   const int lane = threadIdx.x & 31;
-  long ei;
-  bool goal;
-  edge_slot(D, e, ei, goal);
-  const int p = D.e_ci[e] / D.BM;
   const float rv = warp_rho_v(A, es, T);
   bool ok = rv <= 1.f;
   const fn_problem_t& P = D.prob[p];
@@ -1534,6 +1524,13 @@ __device__ __forceinline__ void finish_edge(const PlanDev& D, const ArmK& A, int
     D.e_rv[ei] = rv;
     D.e_k[ei] = k;
   }
+}
+__device__ __forceinline__ void finish_edge(const PlanDev& D, const ArmK& A, int e, int k, float T,
+                                            const float* es) {
+  long ei;
+  bool goal;
+  edge_slot(D, e, ei, goal);
+  finish_slot(D, A, ei, D.e_ci[e] / D.BM, k, T, es);
 }
 
 // after a stage: edges whose duration passed are finished; the others move
@@ -1575,6 +1572,74 @@ __global__ void __launch_bounds__(128) k_plan_vselect(PlanDev D, ArmK A, GridKP 
     D.cur_k[e] = k2;
     next[warp_append(&S->n_pend[list ^ 1])] = e;
   }
+}
+
+// Goal edges (Algorithm 1's goal branch: the cubic from parent p to a
+// decoded goal at the fixed duration T_p = T_req - t(p)) checked apart from
+// the packed body: every (goal candidate, parent slot) of the round, a warp
+// per edge on the paired core with its records in tensor memory
+// (tm_scan.cuh), the full check at T_p up to its first violating batch, then
+// finish_slot's velocity and clearance tests.  The edge list is the queue's
+// goal part (goal_off); an edge whose parent is missing, whose candidate
+// did not decode, or whose T_p is not positive and finite is decided without
+// dynamics, as k_plan_eprep decides it.  Launched after the goal queries'
+// parent search; it needs nothing of the free edges' phase, which runs
+// beside it.
+__global__ void __launch_bounds__(32 * TM_WARPS, 1) k_plan_goal_edges(PlanDev D, ArmK A) {
+  pdl_begin();
+  extern __shared__ float4 tm_smem[];
+  const TmBlock blk(tm_smem);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const Sched* S = D.sched;
+  const int E = S->goal_off[D.P];
+  fill_links2(A, blk.link);
+  const int per = (E + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int r_lo = min((int)blockIdx.x * per, E), r_hi = min(r_lo + per, E);
+  if (threadIdx.x == 0) *blk.next = 0;
+  if (w == 0) tmem_alloc(blk.tmem, kTmCols);
+  tmem_sync_block();
+  const uint32_t tmem = *blk.tmem;
+  const PairCore<TmemStash> core = blk.core(tmem, w, lane);
+  float* es = blk.edges_of(w);
+  unsigned nscan = 0;
+  for (;;) {
+    int n;
+    const int first = tm_claim(blk.next, r_hi - r_lo, n);
+    if (n == 0) break;                               // warp-uniform
+    for (int i = 0; i < n; ++i) {
+      const int x = r_lo + first + i;
+      const int p = find_problem(S->goal_off, D.P, x);
+      const int local = x - S->goal_off[p];
+      const int G = min(max(D.prob[p].n_goal, 0), min(max(D.prob[p].batch, 0), D.BM));
+      const int j = local / G, b = local - j * G;
+      const long ci = (long)p * D.BM + b;
+      const long ei = ci * D.KP + j;
+      const int pr = j == 0 ? 0 : D.nn[ci * D.KN + (j - 1)];
+      const bool valid = pr >= 0 && D.valid[ci];
+      const float Tp = valid ? __fsub_rn(D.treq[ci], D.t[(long)p * D.NC + pr]) : NAN;
+      int k = -1;
+      if (valid && isfinite(Tp) && Tp > 0.f &&
+          stage_rows(D.st + ((long)p * D.NC + pr) * 16, D.cand + ci * 16, es)) {
+        float rt, rp;
+        k = edge_scan(A, core, es, nullptr, blk.grid, 0, D.S, true, Tp, false, rt, rp, nscan);
+        if (k == FN_SCAN_ABORT) {
+          if (lane == 0) atomicOr(D.status + p, FN_PLAN_ERR_SCAN);
+          k = -1;
+        }
+      }
+      if (k >= 0) {
+        finish_slot(D, A, ei, p, 0, Tp, es);
+      } else if (lane == 0) {
+        D.e_ok[ei] = 0;
+        D.e_T[ei] = Tp;
+        D.e_rv[ei] = NAN;
+        D.e_k[ei] = -1;
+      }
+    }
+  }
+  if (D.samples && lane == 0 && nscan) atomicAdd(D.samples + 1, (unsigned long long)nscan);
+  tmem_sync_block();   // every warp's tensor-memory accesses precede the release
+  if (w == 0) tmem_dealloc(tmem, kTmCols);
 }
 
 // The warp-per-edge edge body (schedule variant kPairEdgeVariant): the
@@ -2868,6 +2933,13 @@ struct fn_planner {
   const char* kname[PL_MAX_KEV] = {};
   int nk = 0;
   bool tracing = false;
+  // the goal branch of a captured iteration (goal IK, goal queries' parent
+  // search, goal edges) runs on a side stream, forked after the sampling
+  // launch and joined before the attach
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool allow_fork = false;   // set by the iteration's enqueue when it is not traced
+  bool forked = false;       // a fork is open (the iteration's enqueue joins it)
 };
 
 // record the end of the launch just issued (timed iterations only)
@@ -2948,8 +3020,8 @@ static int plan_edge_blocks(fn_planner* pl, int v) {
 // Launch with programmatic stream serialization (see pdl_begin): the
 // kernel may be scheduled while the previous kernel on the stream drains.
 template <class... KArgs, class... Args>
-static void pl_launch(void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem,
-                      cudaStream_t st, Args... args) {
+static void pl_launch_pdl(bool pdl, void (*k)(KArgs...), unsigned grid, unsigned block,
+                          size_t smem, cudaStream_t st, Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
@@ -2959,8 +3031,13 @@ static void pl_launch(void (*k)(KArgs...), unsigned grid, unsigned block, size_t
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = pdl ? 1 : 0;
   cudaLaunchKernelEx(&cfg, k, args...);
+}
+template <class... KArgs, class... Args>
+static void pl_launch(void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                      cudaStream_t st, Args... args) {
+  pl_launch_pdl(true, k, grid, block, smem, st, args...);
 }
 
 template <int KM>
@@ -3003,6 +3080,23 @@ static int knn_tile_blocks() {
 
 // sampling and parents: candidates of every problem (unless given by the
 // caller), then their nearest tree nodes (mark(2) between the two)
+// the shared-memory request of the planner's tensor-memory kernels (the
+// warp-per-edge body, the goal edges), set once per device
+static bool plan_tm_ready() {
+  static std::once_flag once[64];
+  static bool ok[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::call_once(once[dev & 63], [&] {
+    ok[dev & 63] =
+        cudaFuncSetAttribute(k_plan_edges_tm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kTmSmem) == cudaSuccess &&
+        cudaFuncSetAttribute(k_plan_goal_edges, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kTmSmem) == cudaSuccess;
+  });
+  return ok[dev & 63];
+}
+
 template <class Mark>
 static void enqueue_front(fn_planner* pl, unsigned flags, cudaStream_t st, Mark&& mark) {
   PlanDev& D = pl->D;
@@ -3012,52 +3106,74 @@ static void enqueue_front(fn_planner* pl, unsigned flags, cudaStream_t st, Mark&
   const long n = (flags & FN_PLAN_EXTERNAL) ? 0 : (long)P * D.BM;
   const int prep = knn ? 4 * num_sms() : 0;
   const int dens = (flags & FN_PLAN_DENSITY) ? 1 : 0;
-  auto search = [&](int kind) {
+  // launches on the side stream are plain: an early-launched (programmatic)
+  // grid would hold its blocks' shared memory and warps on the SMs while it
+  // waits, in the way of the free edges' launches on the other stream
+  auto search = [&](int kind, cudaStream_t s) {
     if (!knn) return;
+    const bool pdl = s != pl->side;
     // the goal list is short (the decoded goals): a small grid claims it
     const int gb = 2 * num_sms();
     if (kind == 0 && D.knn_tile) {   // large trees: the tiled search
       if (D.KM == 8)
-        pl_launch(k_plan_knn_tile<8>, knn_tile_blocks<8>(), 32 * PL_KNN_TW, kKnnTileSmem, st, D);
+        pl_launch_pdl(pdl, k_plan_knn_tile<8>, knn_tile_blocks<8>(), 32 * PL_KNN_TW, kKnnTileSmem,
+                      s, D);
       else
-        pl_launch(k_plan_knn_tile<16>, knn_tile_blocks<16>(), 32 * PL_KNN_TW, kKnnTileSmem, st,
-                  D);
+        pl_launch_pdl(pdl, k_plan_knn_tile<16>, knn_tile_blocks<16>(), 32 * PL_KNN_TW,
+                      kKnnTileSmem, s, D);
     } else if (D.KM == 8) {
-      pl_launch(k_plan_knn<8>, kind == 0 ? knn_blocks<8>(pl) : std::min(gb, knn_blocks<8>(pl)),
-                32 * PL_KNN_WARPS, kKnnSmem, st, D, kind);
+      pl_launch_pdl(pdl, k_plan_knn<8>,
+                    kind == 0 ? knn_blocks<8>(pl) : std::min(gb, knn_blocks<8>(pl)),
+                    32 * PL_KNN_WARPS, kKnnSmem, s, D, kind);
     } else {
-      pl_launch(k_plan_knn<16>, kind == 0 ? knn_blocks<16>(pl) : std::min(gb, knn_blocks<16>(pl)),
-                32 * PL_KNN_WARPS, kKnnSmem, st, D, kind);
+      pl_launch_pdl(pdl, k_plan_knn<16>,
+                    kind == 0 ? knn_blocks<16>(pl) : std::min(gb, knn_blocks<16>(pl)),
+                    32 * PL_KNN_WARPS, kKnnSmem, s, D, kind);
     }
-    trace(pl, st, "k_plan_knn");
+    trace(pl, s, "k_plan_knn");
   };
-  auto goals = [&](int late) {
-    pl_launch(k_plan_sample, (unsigned)((32 * n + 127) / 128), 128, 0, st, D, pl->arm, n, 0, dens,
-              1, late);
-    trace(pl, st, "k_plan_sample");
+  auto goals = [&](cudaStream_t s) {
+    pl_launch_pdl(s != pl->side, k_plan_sample, (unsigned)((32 * n + 127) / 128), 128, 0, s, D,
+                  pl->arm, n, 0, dens, 1);
+    trace(pl, s, "k_plan_sample");
+  };
+  auto goal_edges = [&](cudaStream_t s) {   // after the goal queries' parent search
+    if (!D.goal_split) return;
+    pl_launch_pdl(s != pl->side, k_plan_goal_edges, num_sms(), 32 * TM_WARPS, kTmSmem, s, D,
+                  pl->arm);
+    trace(pl, s, "k_plan_goal_edges");
   };
   if (n + prep > 0) {
     const long warps = (n + 31) / 32 + prep;
     pl_launch(k_plan_sample, (unsigned)((32 * warps + 127) / 128), 128, 0, st, D, pl->arm, n,
-              prep, dens, 0, 0);
+              prep, dens, 0);
     trace(pl, st, "k_plan_prep");
   }
-  if (n > 0 && knn && !(flags & FN_PLAN_CHORD) && !pl->tracing) {
-    // the free queries' parent search runs beside the goal chart's IK
+  if (n > 0 && knn && D.goal_split && !(flags & FN_PLAN_CHORD) && pl->allow_fork) {
+    // two branches: the free queries' parent search (and, after this
+    // function, the free edges) on the caller's stream; the goal chart's IK,
+    // the goal queries' search and the goal edges on the side stream, joined
+    // before the attach
     mark(2);
-    search(0);
-    goals(1);
-    search(1);
+    cudaEventRecord(pl->ev_fork, st);
+    cudaStreamWaitEvent(pl->side, pl->ev_fork, 0);
+    search(0, st);
+    goals(pl->side);
+    search(1, pl->side);
+    goal_edges(pl->side);
+    cudaEventRecord(pl->ev_join, pl->side);
+    pl->forked = true;
     return;
   }
-  if (n > 0) goals(0);
+  if (n > 0) goals(st);
   if (n > 0 && (flags & FN_PLAN_CHORD)) {
     pl_launch(k_plan_chord, P, PL_CHORD_THREADS, 0, st, D, pl->arm);
     trace(pl, st, "k_plan_chord");
   }
   mark(2);
-  search(0);
-  search(1);
+  search(0, st);
+  search(1, st);
+  goal_edges(st);
 }
 
 // Packed verification stages before the sequential tail (PlanDev::vstages):
@@ -3075,19 +3191,6 @@ static int vstages(const PlanDev& D) { return D.vstages >= 2 ? 2 : 1; }
 // the packed edge phase after the per-edge prep: item scan, probe, verify
 // (over the edges of the view D; mark(i) records the phase boundaries when
 // timing)
-// the warp-per-edge body's shared-memory request, set once per device
-static bool plan_edges_tm_ready() {
-  static std::once_flag once[64];
-  static bool ok[64];
-  int dev = 0;
-  cudaGetDevice(&dev);
-  std::call_once(once[dev & 63], [&] {
-    ok[dev & 63] = cudaFuncSetAttribute(k_plan_edges_tm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)kTmSmem) == cudaSuccess;
-  });
-  return ok[dev & 63];
-}
-
 template <class Mark>
 static void enqueue_edge_body(fn_planner* pl, const PlanDev& D, int v, int blocks, cudaStream_t st,
                               Mark&& mark, bool scan = true) {
@@ -3125,7 +3228,7 @@ static void enqueue_edges(fn_planner* pl, int v, int blocks, cudaStream_t st, Ma
   const int eb = (D.Emax + PL_SCAN - 1) / PL_SCAN;
   pl_launch(k_plan_eprep, eb, PL_SCAN, 0, st, D, pl->grid);
   trace(pl, st, "k_plan_eprep");
-  if (v == kPairEdgeVariant && plan_edges_tm_ready()) {   // the warp-per-edge body
+  if (v == kPairEdgeVariant && plan_tm_ready()) {   // the warp-per-edge body
     mark(4);
     pl_launch(k_plan_edges_tm, num_sms(), 32 * TM_WARPS, kTmSmem, st, D, pl->arm, pl->grid);
     trace(pl, st, "k_plan_edges_tm");
@@ -3151,6 +3254,9 @@ extern "C" fn_status fn_planner_destroy(fn_planner_t* pl) {
   if (pl->h_prob) cudaFreeHost(pl->h_prob);
   if (pl->h_out) cudaFreeHost(pl->h_out);
   if (pl->h_iter) cudaFreeHost(pl->h_iter);
+  if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
+  if (pl->ev_join) cudaEventDestroy(pl->ev_join);
+  if (pl->side) cudaStreamDestroy(pl->side);
   delete pl;
   return FN_OK;
 }
@@ -3200,6 +3306,7 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
   D.knn_slots = D.knn_tile ? (D.KM == 8 ? knn_tile_blocks<8>() : knn_tile_blocks<16>())
                            : (D.KM == 8 ? knn_blocks<8>(pl) : knn_blocks<16>(pl)) * PL_KNN_WARPS;
   D.vstages = (long)c.P * c.b_max * c.k >= PL_VSTAGE_EDGES ? 2 : 1;
+  D.goal_split = 1;
   D.K = c.K; D.S = c.S; D.S_clear = c.S_clear; D.G = c.reach_grid;
   D.w_vel = c.w_vel; D.vel_frac = c.vel_frac; D.margin = c.clear_margin;
   const size_t P = c.P, NC = c.n_cap, BM = c.b_max, KP = c.k, KN = D.KN, KM = D.KM;
@@ -3290,6 +3397,13 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
       fn_planner_destroy(pl);
       return FN_ECUDA;
     }
+  if (cudaStreamCreateWithFlags(&pl->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      !plan_tm_ready()) {
+    fn_planner_destroy(pl);
+    return FN_ECUDA;
+  }
   pl->edge_variant = tuned_variant(TUNE_PLAN_EDGES, (long)c.P * c.b_max * c.k, c.K, c.S);
   pl->edge_blocks = c.edge_blocks > 0 ? c.edge_blocks : plan_edge_blocks(pl, pl->edge_variant);
   *out = pl;
@@ -3395,6 +3509,8 @@ static fn_status enqueue_iteration(fn_planner* pl, unsigned flags, cudaStream_t 
   };
   mark(0);
   pl->tracing = timed;
+  pl->allow_fork = !timed;
+  pl->forked = false;
   pl->nk = 0;
   if (timed) cudaEventRecord(pl->kev[0], st);
   k_plan_schedule<<<1, 256, 0, st>>>(D);
@@ -3404,6 +3520,11 @@ static fn_status enqueue_iteration(fn_planner* pl, unsigned flags, cudaStream_t 
   mark(3);
   enqueue_edges(pl, pl->edge_variant, pl->edge_blocks, st, mark);
   if (pl->sur_mlp) enqueue_surrogate(pl, st);
+  if (pl->forked) {            // the goal branch's edges precede the attach
+    cudaStreamWaitEvent(st, pl->ev_join, 0);
+    pl->forked = false;
+  }
+  pl->allow_fork = false;
   if (flags & FN_PLAN_NARY) {
     pl_launch(k_plan_refine, 4 * num_sms(), 32 * PL_REFINE_WARPS, 0, st, D, pl->arm, pl->grid,
               pl->nary_eps, pl->nary_rounds);
