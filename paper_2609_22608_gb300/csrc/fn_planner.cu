@@ -1576,15 +1576,53 @@ __global__ void __launch_bounds__(128) k_plan_vselect(PlanDev D, ArmK A, GridKP 
 
 // Goal edges (Algorithm 1's goal branch: the cubic from parent p to a
 // decoded goal at the fixed duration T_p = T_req - t(p)) checked apart from
-// the packed body: every (goal candidate, parent slot) of the round, a warp
-// per edge on the paired core with its records in tensor memory
-// (tm_scan.cuh), the full check at T_p up to its first violating batch, then
-// finish_slot's velocity and clearance tests.  The edge list is the queue's
-// goal part (goal_off); an edge whose parent is missing, whose candidate
-// did not decode, or whose T_p is not positive and finite is decided without
-// dynamics, as k_plan_eprep decides it.  Launched after the goal queries'
-// parent search; it needs nothing of the free edges' phase, which runs
-// beside it.
+// the packed body: every (goal candidate, parent slot) of the round, on the
+// paired core with its records in tensor memory (tm_scan.cuh).  CTA b owns a
+// contiguous range of the queue's goal part (goal_off).  Its threads decode
+// the range a chunk at a time, one edge each: an edge whose parent is
+// missing, whose candidate did not decode, or whose T_p is not positive and
+// finite is decided there without dynamics (as k_plan_eprep decides it), the
+// others join the CTA's list of live edges.  The warps then claim the live
+// edges in groups of up to eight, shrinking towards the end of the list so
+// that the warps finish together: with more than one edge to a group, one
+// probe pass first evaluates eight collocation points of each (both ends and
+// six between; lane 4 q + j takes points j and j + 4 of edge q, compensated
+// coefficients as the full check, so a violation there is one of the check),
+// and only the edges whose probes all pass get the full check at T_p (a warp
+// pass per 64 samples, up to the first violating batch).  Then finish_slot's
+// velocity and clearance tests.  Launched after the goal queries' parent
+// search; it needs nothing of the free edges' phase, which runs beside it.
+__device__ __forceinline__ int goal_probe_index(int j, int S) {
+  return (int)((2 * j * (S - 1) + 7) / 14);   // round(j (S - 1) / 7), j < 8
+}
+struct GoalEdge {
+  long ei;      // result slot
+  int p;        // problem
+  int pr;       // parent node (-1: none)
+  long ci;      // candidate slot
+  float Tp;     // fixed duration (NaN when not valid)
+  bool live;    // needs dynamics
+};
+__device__ __forceinline__ GoalEdge decode_goal_edge(const PlanDev& D, const Sched* S, int x) {
+  GoalEdge g;
+  g.p = find_problem(S->goal_off, D.P, x);
+  const int local = x - S->goal_off[g.p];
+  const int G = min(max(D.prob[g.p].n_goal, 0), min(max(D.prob[g.p].batch, 0), D.BM));
+  const int j = local / G, b = local - j * G;
+  g.ci = (long)g.p * D.BM + b;
+  g.ei = g.ci * D.KP + j;
+  g.pr = j == 0 ? 0 : D.nn[g.ci * D.KN + (j - 1)];
+  const bool valid = g.pr >= 0 && D.valid[g.ci];
+  g.Tp = valid ? __fsub_rn(D.treq[g.ci], D.t[(long)g.p * D.NC + g.pr]) : NAN;
+  g.live = valid && isfinite(g.Tp) && g.Tp > 0.f;
+  return g;
+}
+__device__ __forceinline__ void goal_edge_fail(const PlanDev& D, const GoalEdge& g) {
+  D.e_ok[g.ei] = 0;
+  D.e_T[g.ei] = g.Tp;
+  D.e_rv[g.ei] = NAN;
+  D.e_k[g.ei] = -1;
+}
 __global__ void __launch_bounds__(32 * TM_WARPS, 1) k_plan_goal_edges(PlanDev D, ArmK A) {
   pdl_begin();
   extern __shared__ float4 tm_smem[];
@@ -1595,47 +1633,112 @@ __global__ void __launch_bounds__(32 * TM_WARPS, 1) k_plan_goal_edges(PlanDev D,
   fill_links2(A, blk.link);
   const int per = (E + (int)gridDim.x - 1) / (int)gridDim.x;
   const int r_lo = min((int)blockIdx.x * per, E), r_hi = min(r_lo + per, E);
-  if (threadIdx.x == 0) *blk.next = 0;
+  int* list = reinterpret_cast<int*>(blk.split);   // the live edges (the splits' room)
+  constexpr int kChunk = (int)(kTmSplit / sizeof(int));
+  int* s_n = blk.aux;
   if (w == 0) tmem_alloc(blk.tmem, kTmCols);
   tmem_sync_block();
   const uint32_t tmem = *blk.tmem;
   const PairCore<TmemStash> core = blk.core(tmem, w, lane);
-  float* es = blk.edges_of(w);
+  float* es_g = blk.edges_of(w);
   unsigned nscan = 0;
-  for (;;) {
-    int n;
-    const int first = tm_claim(blk.next, r_hi - r_lo, n);
-    if (n == 0) break;                               // warp-uniform
-    for (int i = 0; i < n; ++i) {
-      const int x = r_lo + first + i;
-      const int p = find_problem(S->goal_off, D.P, x);
-      const int local = x - S->goal_off[p];
-      const int G = min(max(D.prob[p].n_goal, 0), min(max(D.prob[p].batch, 0), D.BM));
-      const int j = local / G, b = local - j * G;
-      const long ci = (long)p * D.BM + b;
-      const long ei = ci * D.KP + j;
-      const int pr = j == 0 ? 0 : D.nn[ci * D.KN + (j - 1)];
-      const bool valid = pr >= 0 && D.valid[ci];
-      const float Tp = valid ? __fsub_rn(D.treq[ci], D.t[(long)p * D.NC + pr]) : NAN;
-      int k = -1;
-      if (valid && isfinite(Tp) && Tp > 0.f &&
-          stage_rows(D.st + ((long)p * D.NC + pr) * 16, D.cand + ci * 16, es)) {
-        float rt, rp;
-        k = edge_scan(A, core, es, nullptr, blk.grid, 0, D.S, true, Tp, false, rt, rp, nscan);
-        if (k == FN_SCAN_ABORT) {
-          if (lane == 0) atomicOr(D.status + p, FN_PLAN_ERR_SCAN);
-          k = -1;
+  for (int c0 = r_lo; c0 < r_hi; c0 += kChunk) {     // CTA-uniform
+    const int c1 = min(c0 + kChunk, r_hi);
+    if (threadIdx.x == 0) *s_n = 0;
+    __syncthreads();
+    for (int base = c0; base < c1; base += blockDim.x) {
+      const int x = base + threadIdx.x;
+      bool lv = false;
+      if (x < c1) {
+        const GoalEdge g = decode_goal_edge(D, S, x);
+        lv = g.live;
+        if (!lv) goal_edge_fail(D, g);
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, lv);   // one atomic per warp
+      int at = 0;
+      if (m && lane == __ffs(m) - 1) at = atomicAdd(s_n, __popc(m));
+      at = __shfl_sync(0xffffffffu, at, m ? __ffs(m) - 1 : 0);
+      if (lv) list[at + __popc(m & ((1u << lane) - 1u))] = x;
+    }
+    if (threadIdx.x == 0) *blk.next = 0;
+    __syncthreads();
+    const int nl = *s_n;
+    for (;;) {   // groups claimed from a shared counter, shrinking towards the end of the list
+      int g0 = 0, gs = 0;
+      if (lane == 0) {
+        const int seen = atomicAdd(blk.next, 0);
+        gs = min(8, max(1, (nl - seen) / (2 * TM_WARPS)));
+        g0 = atomicAdd(blk.next, gs);
+      }
+      g0 = __shfl_sync(0xffffffffu, g0, 0);
+      gs = __shfl_sync(0xffffffffu, gs, 0);
+      if (g0 >= nl) break;                           // warp-uniform
+      const int n = min(gs, nl - g0);
+      long my_ei = 0;
+      int my_p = 0;
+      float my_Tp = 0.f;
+      for (int i = 0; i < n; ++i) {
+        const GoalEdge g = decode_goal_edge(D, S, list[g0 + i]);
+        stage_rows(D.st + ((long)g.p * D.NC + g.pr) * 16, D.cand + g.ci * 16, es_g + 32 * i);
+        if (lane == i) { my_ei = g.ei; my_p = g.p; my_Tp = g.Tp; }
+      }
+      unsigned probed = n > 1 ? 0u : 1u;   // a lone edge goes straight to its check
+      if (n > 1) {
+        const int q = lane >> 2;
+        const bool act = q < n;
+        const float T = __shfl_sync(0xffffffffu, my_Tp, act ? q : 0);
+        {
+          Cubic c;
+          if (act) {
+            cubic_coef_sh<true>(es_g + 32 * q, T, c);
+          } else {                                   // an idle lane: any finite cubic
+            c.iT = c.iT2 = 1.f;
+#pragma unroll
+            for (int m = 0; m < 7; ++m) c.q0[m] = c.b1[m] = c.b2[m] = c.b3[m] = 0.f;
+          }
+          core.store(c);
+        }
+        const float2 u = make_float2(sample_u(goal_probe_index(lane & 3, D.S), D.S),
+                                     sample_u(goal_probe_index((lane & 3) + 4, D.S), D.S));
+        float rx = 0.f, px = 0.f, ry = 0.f, py = 0.f;
+        core.eval(A, u, dup2(1.f), dup2(1.f), [&](int m, float2 tau, float2 v, float inv_tau) {
+          rx = fmaxf(rx, fabsf(tau.x) * inv_tau);
+          px = fmaf(tau.x, v.x, px);
+          ry = fmaxf(ry, fabsf(tau.y) * inv_tau);
+          py = fmaf(tau.y, v.y, py);
+        });
+        const bool okl = act && rx <= 1.f && fabsf(px) * A.inv_w <= 1.f && ry <= 1.f &&
+                         fabsf(py) * A.inv_w <= 1.f;
+        const unsigned ok = __ballot_sync(0xffffffffu, okl);
+        nscan += 8u * n;
+        for (int qq = 0; qq < n; ++qq)
+          if (((ok >> (4 * qq)) & 0xFu) == 0xFu) probed |= 1u << qq;
+      }
+      for (int i = 0; i < n; ++i) {
+        const long ei = __shfl_sync(0xffffffffu, my_ei, i);
+        const int p = __shfl_sync(0xffffffffu, my_p, i);
+        const float Tp = __shfl_sync(0xffffffffu, my_Tp, i);
+        int k = -1;
+        if ((probed >> i) & 1u) {
+          float rt, rp;
+          k = edge_scan(A, core, es_g + 32 * i, nullptr, blk.grid, 0, D.S, true, Tp, false, rt,
+                        rp, nscan);
+          if (k == FN_SCAN_ABORT) {
+            if (lane == 0) atomicOr(D.status + p, FN_PLAN_ERR_SCAN);
+            k = -1;
+          }
+        }
+        if (k >= 0) {
+          finish_slot(D, A, ei, p, 0, Tp, es_g + 32 * i);
+        } else if (lane == 0) {
+          D.e_ok[ei] = 0;
+          D.e_T[ei] = Tp;
+          D.e_rv[ei] = NAN;
+          D.e_k[ei] = -1;
         }
       }
-      if (k >= 0) {
-        finish_slot(D, A, ei, p, 0, Tp, es);
-      } else if (lane == 0) {
-        D.e_ok[ei] = 0;
-        D.e_T[ei] = Tp;
-        D.e_rv[ei] = NAN;
-        D.e_k[ei] = -1;
-      }
     }
+    __syncthreads();   // the list is read before the next chunk refills it
   }
   if (D.samples && lane == 0 && nscan) atomicAdd(D.samples + 1, (unsigned long long)nscan);
   tmem_sync_block();   // every warp's tensor-memory accesses precede the release
