@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--edge-schedule", type=int, default=-1,
+                    help="pin the planner's edge schedule (0-3) instead of autotuning it "
+                         "(under a profiler the autotuner's timings are not the run's)")
     ap.add_argument("--workload", default="iteration",
                     choices=["iteration", "surrogate", "batched", "batched-surrogate", "anytime",
                              "nary", "control", "batched-density", "batched-nary", "scan"],
@@ -241,7 +244,11 @@ def run_ours(args, rank, world):
         pl.load_tree(0, w["tree"], w["t_node"], w["parent"], stream=stream)
 
     reset_tree()
-    tuned = pl.autotune([prob], 0, 0, reps=3, stream=stream)   # schedule autotuner
+    if args.edge_schedule >= 0:
+        pl.set_schedule(args.edge_schedule)
+        tuned = (args.edge_schedule, None)
+    else:
+        tuned = pl.autotune([prob], 0, 0, reps=3, stream=stream)   # schedule autotuner
     for i in range(args.warmup):
         reset_tree()
         pl.iterate([prob], i, 0, stream=stream)
