@@ -3331,6 +3331,14 @@ static void enqueue_edges(fn_planner* pl, int v, int blocks, cudaStream_t st, Ma
   const int eb = (D.Emax + PL_SCAN - 1) / PL_SCAN;
   pl_launch(k_plan_eprep, eb, PL_SCAN, 0, st, D, pl->grid);
   trace(pl, st, "k_plan_eprep");
+  // with the duration surrogate every free edge with an admissible duration
+  // goes to the surrogate pass and the goal edges to k_plan_goal_edges: the
+  // body would find no edge
+  if (pl->sur_mlp && D.goal_split) {
+    mark(4);
+    mark(5);
+    return;
+  }
   if (v == kPairEdgeVariant && plan_tm_ready()) {   // the warp-per-edge body
     mark(4);
     pl_launch(k_plan_edges_tm, num_sms(), 32 * TM_WARPS, kTmSmem, st, D, pl->arm, pl->grid);
