@@ -4221,7 +4221,7 @@ __global__ void k_sur_gather(PlanDev D, float* __restrict__ s0, float* __restric
   }
 }
 
-// results of the surrogate pass into the edges' slots (warp per edge), with
+// results of the surrogate pass into the edges' slots (a lane per edge), with
 // the clearance check of the edge's own problem for accepted durations
 __global__ void __launch_bounds__(128) k_sur_scatter(PlanDev D, ArmK A, const int32_t* __restrict__ gk,
                                                      const float* __restrict__ gT,
@@ -4235,16 +4235,31 @@ __global__ void __launch_bounds__(128) k_sur_scatter(PlanDev D, ArmK A, const in
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int n = min(*D.sur_n, D.Emax);
   if (D.samples && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(D.samples + 5, (unsigned long long)n);
-  for (int i = blockIdx.x * 4 + w; i < n; i += gridDim.x * 4) {
-    const long ei = slot[i];
-    bool ok = gok[i] != 0;
-    const float T = gT[i];
-    const fn_problem_t& P = D.prob[ei / ((long)D.KP * D.BM)];
-    if (ok && P.n_obs > 0) {           // warp-uniform
-      stage_rows(s0 + 16L * i, s1 + 16L * i, sEs[w]);
-      ok = warp_clearance(D, A, P, sEs[w], T) >= D.margin;
+  // a warp takes 32 edges, a lane each; the accepted edges of problems with
+  // obstacles then get the warp-wide clearance check one at a time
+  for (int i0 = (blockIdx.x * 4 + w) * 32; i0 < n; i0 += gridDim.x * 4 * 32) {
+    const int i = i0 + lane;
+    long ei = 0;
+    bool ok = false;
+    float T = 0.f;
+    bool clear = false;
+    if (i < n) {
+      ei = slot[i];
+      ok = gok[i] != 0;
+      T = gT[i];
+      clear = ok && D.prob[ei / ((long)D.KP * D.BM)].n_obs > 0;
     }
-    if (lane == 0) {
+    for (unsigned m = __ballot_sync(0xffffffffu, clear); m; m &= m - 1u) {
+      const int l = __ffs(m) - 1;
+      const int il = i0 + l;
+      const long el = __shfl_sync(0xffffffffu, ei, l);
+      const float Tl = __shfl_sync(0xffffffffu, T, l);
+      const fn_problem_t& P = D.prob[el / ((long)D.KP * D.BM)];
+      stage_rows(s0 + 16L * il, s1 + 16L * il, sEs[w]);
+      const bool okl = warp_clearance(D, A, P, sEs[w], Tl) >= D.margin;
+      if (lane == l) ok = okl;
+    }
+    if (i < n) {
       D.e_ok[ei] = ok ? 1 : 0;
       D.e_T[ei] = T;
       D.e_rv[ei] = grv[i];
