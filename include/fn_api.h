@@ -447,12 +447,18 @@ fn_status fn_planner_destroy(fn_planner_t* pl);
 
 /* Algorithm 1, first line: each problem's tree becomes its root
  * (q0, qd0, t = 0); the incumbent is cleared and t_best = t_fall.
- * probs: host [P]. */
+ * probs: host [P], copied into the reset's own pinned staging before the
+ * call returns.  Asynchronous on `stream`: the call returns once the work is
+ * enqueued (the next reset waits, on the host, for this one's copy). */
 fn_status fn_planner_reset(fn_planner_t* pl, const fn_problem_t* probs, void* stream);
 
 /* Replace problem p's tree with n host nodes (states [n][16], time-to-come
  * t[n], parent[n] with parent[0] = -1 and parent[i] < i): used to start an
- * iteration from a given tree.  Nodes carry no score and nu = 0. */
+ * iteration from a given tree.  Nodes carry no score and nu = 0.
+ * Asynchronous on `stream`: the copies are enqueued and the call returns, as
+ * cudaMemcpyAsync does; host arrays in page-locked memory must stay
+ * unchanged until the stream has executed the copies (pageable arrays may be
+ * reused at once). */
 fn_status fn_planner_load_tree(fn_planner_t* pl, int p, const float* states, const float* t,
                                const int32_t* parent, int n, void* stream);
 
@@ -515,7 +521,8 @@ fn_status fn_plan_replay(fn_planner_t* pl, const fn_problem_t* probs, int iter,
  * rendezvous records are read with fn_plan_result.  The staging is pinned
  * host memory that the graph's own copies read, so a call waits (on the host)
  * for the previous asynchronous replay's graph to finish before staging
- * again; fn_plan_iteration, fn_plan_replay and fn_planner_reset do the same.
+ * again; fn_plan_iteration and fn_plan_replay do the same (fn_planner_reset
+ * stages into its own buffer).
  * Everything else is as fn_plan_replay (Algorithm 1's loop body, one
  * iteration per call).  Errors as fn_plan_replay.
  */

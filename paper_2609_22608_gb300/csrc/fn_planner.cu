@@ -2997,10 +2997,13 @@ struct fn_planner {
   int device;
   std::vector<void*> allocs;
   fn_problem_t* h_prob = nullptr;      // pinned staging
+  fn_problem_t* h_reset = nullptr;     // pinned staging of fn_planner_reset (its own copy)
   fn_rendezvous_t* h_out = nullptr;    // pinned
   int* h_iter = nullptr;               // pinned
   cudaEvent_t replay_done = nullptr;   // the last asynchronous replay (its staging and output)
   bool replay_pending = false;         // an asynchronous replay may still read the staging
+  cudaEvent_t reset_done = nullptr;    // the last reset's copy of the staged problems
+  bool reset_pending = false;          // that copy may still read the staging
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   unsigned graph_flags = 0;
@@ -3363,8 +3366,13 @@ extern "C" fn_status fn_planner_destroy(fn_planner_t* pl) {
     cudaEventDestroy(pl->replay_done);
   }
   if (pl->h_prob) cudaFreeHost(pl->h_prob);
+  if (pl->h_reset) cudaFreeHost(pl->h_reset);
   if (pl->h_out) cudaFreeHost(pl->h_out);
   if (pl->h_iter) cudaFreeHost(pl->h_iter);
+  if (pl->reset_done) {
+    cudaEventSynchronize(pl->reset_done);
+    cudaEventDestroy(pl->reset_done);
+  }
   if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
   if (pl->ev_join) cudaEventDestroy(pl->ev_join);
   if (pl->side) cudaStreamDestroy(pl->side);
@@ -3482,6 +3490,8 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
 #undef A_
   if (rc == FN_OK) {
     if (cudaHostAlloc(&pl->h_prob, P * sizeof(fn_problem_t), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostAlloc(&pl->h_reset, P * sizeof(fn_problem_t), cudaHostAllocDefault) !=
+            cudaSuccess ||
         cudaHostAlloc(&pl->h_out, P * sizeof(fn_rendezvous_t), cudaHostAllocMapped) !=
             cudaSuccess ||
         cudaHostAlloc(&pl->h_iter, sizeof(int), cudaHostAllocMapped) != cudaSuccess)
@@ -3509,6 +3519,7 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
       return FN_ECUDA;
     }
   if (cudaStreamCreateWithFlags(&pl->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&pl->reset_done, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       !plan_tm_ready()) {
@@ -3523,13 +3534,18 @@ extern "C" fn_status fn_planner_create(const fn_planner_cfg_t* cfg, const fn_arm
 
 static fn_status wait_staging(fn_planner* pl);
 
-static fn_status stage_problems(fn_planner* pl, const fn_problem_t* probs, cudaStream_t st) {
+static bool problems_ok(const fn_planner* pl, const fn_problem_t* probs) {
   for (int p = 0; p < pl->cfg.P; ++p) {
     const fn_problem_t& q = probs[p];
     if (q.batch < 0 || q.batch > pl->cfg.b_max || q.n_goal < 0 || q.n_goal > q.batch ||
         q.n_obs < 0 || q.n_obs > FN_MAX_OBS || !(q.t_fall >= q.t_enter) || !(q.v_tip > 0.f))
-      return FN_EINVAL;
+      return false;
   }
+  return true;
+}
+
+static fn_status stage_problems(fn_planner* pl, const fn_problem_t* probs, cudaStream_t st) {
+  if (!problems_ok(pl, probs)) return FN_EINVAL;
   const fn_status rc = wait_staging(pl);
   if (rc != FN_OK) return rc;
   memcpy(pl->h_prob, probs, sizeof(fn_problem_t) * pl->cfg.P);
@@ -3541,12 +3557,24 @@ static fn_status stage_problems(fn_planner* pl, const fn_problem_t* probs, cudaS
 
 extern "C" fn_status fn_planner_reset(fn_planner_t* pl, const fn_problem_t* probs, void* stream) {
   if (!pl || !probs) return FN_EINVAL;
+  if (!problems_ok(pl, probs)) return FN_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  fn_status rc = stage_problems(pl, probs, st);
-  if (rc != FN_OK) return rc;
+  // the reset's own pinned copy of the problems (the replays' staging is
+  // left alone); the previous reset's copy must have been read first
+  if (pl->reset_pending) {
+    if (cudaEventSynchronize(pl->reset_done) != cudaSuccess) return FN_ECUDA;
+    pl->reset_pending = false;
+  }
+  memcpy(pl->h_reset, probs, sizeof(fn_problem_t) * pl->cfg.P);
+  if (cudaMemcpyAsync(pl->D.prob, pl->h_reset, sizeof(fn_problem_t) * pl->cfg.P,
+                      cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return FN_ECUDA;
   k_plan_reset<<<(pl->cfg.P + 127) / 128, 128, 0, st>>>(pl->D);
-  rc = launch_status();
-  if (rc == FN_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = FN_ECUDA;
+  fn_status rc = launch_status();
+  if (rc == FN_OK) {
+    if (cudaEventRecord(pl->reset_done, st) != cudaSuccess) return FN_ECUDA;
+    pl->reset_pending = true;
+  }
   return rc;
 }
 
@@ -3568,9 +3596,7 @@ extern "C" fn_status fn_planner_load_tree(fn_planner_t* pl, int p, const float* 
           cudaSuccess)
     return FN_ECUDA;
   k_plan_loaded<<<(n + 255) / 256, 256, 0, st>>>(D, p, n);
-  fn_status rc = launch_status();
-  if (rc == FN_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = FN_ECUDA;
-  return rc;
+  return launch_status();
 }
 
 extern "C" fn_status fn_planner_set_candidates(fn_planner_t* pl, int p, const float* states,
