@@ -3277,6 +3277,19 @@ static void enqueue_front(fn_planner* pl, unsigned flags, cudaStream_t st, Mark&
     trace(pl, st, "k_plan_chord");
   }
   mark(2);
+  if (knn && D.goal_split && pl->allow_fork) {
+    // the free candidates wait for the goal chart (chord states, external
+    // candidates); the goal queries' search and the goal edges still run
+    // beside the free queries' search and the free edges
+    cudaEventRecord(pl->ev_fork, st);
+    cudaStreamWaitEvent(pl->side, pl->ev_fork, 0);
+    search(0, st);
+    search(1, pl->side);
+    goal_edges(pl->side);
+    cudaEventRecord(pl->ev_join, pl->side);
+    pl->forked = true;
+    return;
+  }
   search(0, st);
   search(1, st);
   goal_edges(st);
