@@ -3278,9 +3278,9 @@ static void enqueue_front(fn_planner* pl, unsigned flags, cudaStream_t st, Mark&
   }
   mark(2);
   if (knn && D.goal_split && pl->allow_fork) {
-    // the free candidates wait for the goal chart (chord states, external
-    // candidates); the goal queries' search and the goal edges still run
-    // beside the free queries' search and the free edges
+    // chord states make the free candidates wait for the goal chart (and
+    // caller-given candidates have none): the goal queries' search and the
+    // goal edges still run beside the free queries' search and free edges
     cudaEventRecord(pl->ev_fork, st);
     cudaStreamWaitEvent(pl->side, pl->ev_fork, 0);
     search(0, st);
