@@ -364,15 +364,22 @@ def test_sampler_goal_chart_on_manifold(P, orc, arm):
         assert np.all(q >= arm["q_lo"] - 1e-6) and np.all(q <= arm["q_hi"] + 1e-6)
 
 
-def test_graph_replay_matches_iteration(P, orc, arm):
+@pytest.mark.parametrize("chord", [False, True])
+def test_graph_replay_matches_iteration(P, orc, arm, chord):
+    """A captured iteration (two branches: the goal branch on a side stream)
+    computes what the same iteration computes launch by launch in one stream;
+    with chord states the fork comes after the goal chart."""
     import torch
     case = make_case(arm, orc, 6, N=500)
     states, t, parent = case["tree"]
     N = states.shape[0]
     B = 512
+    flags = P.FN_PLAN_CHORD if chord else 0
     res = []
     for mode in ("iterate", "graph", "async"):
         pl = P.Planner(arm, P=2, n_cap=N + 4 * B, b_max=B, k=8, K=64, S=32)
+        if chord:
+            pl.set_sampler(w_chord=0.6, chord_sigma=0.15)
         probs = [P.problem_struct(case["pr"], B, B // 2, root=case["root"], seed=11 + i)
                  for i in range(2)]
         pl.reset(probs)
@@ -381,14 +388,14 @@ def test_graph_replay_matches_iteration(P, orc, arm):
         s = torch.cuda.Stream()
         outs = []
         if mode == "graph":
-            pl.capture(0, stream=s)
+            pl.capture(flags, stream=s)
             for it in range(3):
                 outs.append(pl.replay(probs, it, stream=s))
         elif mode == "async":
             from paper_2609_22608_gb300._lib import FnError
             with pytest.raises(FnError):
                 pl.result()                              # nothing launched yet
-            pl.capture(0, stream=s)
+            pl.capture(flags, stream=s)
             pl.replay_async(probs, 0, stream=s)
             outs.append(pl.result())
             pl.replay_async(probs, 1, stream=s)          # back to back: the second call
@@ -397,7 +404,7 @@ def test_graph_replay_matches_iteration(P, orc, arm):
             outs.append(pl.result())
         else:
             for it in range(3):
-                outs.append(pl.iterate(probs, it, 0, stream=s))
+                outs.append(pl.iterate(probs, it, flags, stream=s))
         res.append((outs, [pl.get_tree(p) for p in range(2)]))
         pl.close()
     (o1, t1) = res[0]
