@@ -3298,14 +3298,21 @@ static void enqueue_front(fn_planner* pl, unsigned flags, cudaStream_t st, Mark&
 // Packed verification stages before the sequential tail (PlanDev::vstages):
 // each stage pair is two dependent launches, which pay off when thousands of
 // edges fail their first duration.  Planners whose edge capacity is at least
-// PL_VSTAGE_EDGES run two (a batch of many problems), smaller ones one; the
+// PL_VSTAGE_EDGES run two (a batch of many problems), smaller ones
+// PL_VSTAGES_SMALL (the tail alone measured within 2 % at C2 and C5); the
 // packed engine runs two (uncapped caller edges scan many durations).  At
-// least one: goal edges, verified at their fixed duration, are decided by
-// the first stage and never reach the tail.
+// least one whenever goal edges are in the body (planners whose goal edges
+// have their own kernel have none): they are verified at their fixed
+// duration by the first stage and must not reach the tail.
 #ifndef PL_VSTAGE_EDGES
 #define PL_VSTAGE_EDGES 262144
 #endif
-static int vstages(const PlanDev& D) { return D.vstages >= 2 ? 2 : 1; }
+#ifndef PL_VSTAGES_SMALL
+#define PL_VSTAGES_SMALL 1   // stages of the smaller planners
+#endif
+static int vstages(const PlanDev& D) {
+  return D.vstages >= 2 ? 2 : (D.goal_split ? PL_VSTAGES_SMALL : 1);
+}
 
 // the packed edge phase after the per-edge prep: item scan, probe, verify
 // (over the edges of the view D; mark(i) records the phase boundaries when
