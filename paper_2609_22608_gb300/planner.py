@@ -218,10 +218,13 @@ class Planner:
         return C.c_void_p(s.cuda_stream)
 
     def reset(self, probs, stream=None):
+        """fn_planner_reset (asynchronous on the stream)."""
         self._stage(probs)
         check(lib().fn_planner_reset(self.h, self._probs, self._stream(stream)), "fn_planner_reset")
 
     def load_tree(self, p, states, t, parent, stream=None):
+        """fn_planner_load_tree (asynchronous on the stream: arrays in page-locked
+        memory must stay unchanged until the stream has executed the copies)."""
         st = np.ascontiguousarray(states, np.float32)
         t = np.ascontiguousarray(t, np.float32)
         par = np.ascontiguousarray(parent, np.int32)
